@@ -1,0 +1,36 @@
+"""Compile the oracle (plain C++17, FP64) into ``oracle/liboracle.so``.
+
+Test infrastructure only: building the checker is not using it.
+"""
+import os
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SOURCES = ["oracle_api.cpp"]
+HEADERS = ["oracle.h", "quadrature.hpp", "mesh.hpp", "euler.hpp", "scheme.hpp"]
+LIB = os.path.join(HERE, "liboracle.so")
+
+
+def _stale():
+    if not os.path.exists(LIB):
+        return True
+    t = os.path.getmtime(LIB)
+    return any(os.path.getmtime(os.path.join(HERE, f)) > t for f in SOURCES + HEADERS)
+
+
+def build(force=False, verbose=False):
+    """Build liboracle.so if it is missing or older than its sources."""
+    if not force and not _stale():
+        return LIB
+    cmd = ["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-o", LIB + ".tmp"]
+    cmd += [os.path.join(HERE, s) for s in SOURCES]
+    if verbose:
+        print(" ".join(cmd))
+    subprocess.run(cmd, check=True)
+    os.replace(LIB + ".tmp", LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    build(force="--force" in sys.argv, verbose=True)
