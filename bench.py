@@ -1,0 +1,378 @@
+#!/usr/bin/env python
+"""Throughput of the DG RK stage: DOF-updates/s per RK stage.
+
+Workload: isentropic vortex (beta=5, gamma=1.4, boost (1,1)) on the periodic
+box [-5,5]^2 with 256^2 cells, polynomial degree k=3 (N=10 basis functions),
+SSP-RK4 (5 stages), no limiter, CFL 0.2; synthetic closed-form initial data.
+A step is one RK4 step (all stages, including the on-device CFL timestep)
+over the whole mesh; DOF = cells x N.  The headline is the FP64 path; the
+FP32 path is reported under "variants".
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank advances its own replica of the problem
+(no data-path collective): value = DOF-updates of all ranks / max time.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DG DOF-updates/s per RK stage, FP32-TC vs FP64 at equal L1 err; % HBM peak"
+UNIT = "DOF-updates/s"
+N_CELLS_1D, K_DEG, RK_ORDER, STAGES, CFL = 256, 3, 4, 5, 0.2
+N_BASIS, NV, DIM = 10, 4, 2
+L2_BYTES = 129 * 2 ** 20
+
+
+def workload_config(precision):
+    return {"workload": "isentropic vortex 2D, 256x256 periodic [-5,5]^2, k=3 (10 coeffs/cell/var), "
+                        "SSP-RK4 (5 stages), no limiter, CFL 0.2",
+            "cells": N_CELLS_1D ** 2, "k": K_DEG, "basis": N_BASIS, "rk_stages": STAGES,
+            "precision": precision, "l2": "flushed between timed steps (256 MiB write)"}
+
+
+def mesh(n=N_CELLS_1D, half=5.0):
+    from paper_1506_06140_gb300 import workloads as wl
+    return wl.mesh_uniform(2, [n, n], [-half, -half], [half, half])
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work per cell and stage (the formulas of the design doc)
+
+def shape(dim, k):
+    N = (k + 1) * (k + 2) // 2 if dim == 2 else (k + 1) * (k + 2) * (k + 3) // 6
+    Q, QF, nv = (k + 1) ** dim, (k + 1) ** (dim - 1), dim + 2
+    return N, Q, QF, nv
+
+
+def flops_cell_kernel(dim, k):
+    """Cell kernel flops per cell: modal->nodal (2 Q N nv), Euler fluxes
+    (~(8 + 8 dim) per point), volume contraction (2 dim Q N nv), surface
+    integral (2 * 2 dim QF N nv), stage combination (3 N nv)."""
+    N, Q, QF, nv = shape(dim, k)
+    return 2 * Q * N * nv + (8 + 8 * dim) * Q + 2 * dim * Q * N * nv + 4 * dim * QF * N * nv + 3 * N * nv
+
+
+def flops_face_kernel_per_face(dim, k):
+    """Face kernel flops per face: two traces per point (2 * 2 N nv) and HLLC (~90)."""
+    N, Q, QF, nv = shape(dim, k)
+    return QF * (4 * N * nv + 90)
+
+
+def state_bytes_per_cell(dim, k, esize):
+    N, Q, QF, nv = shape(dim, k)
+    return nv * N * esize
+
+
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    """Samples nvidia-smi SM clocks and throttle reasons while running."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.th.join(timeout=2)
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+# nominal FP64 / FP32 SIMT rates from unit counts and the maximum SM clock:
+# 152 SMs x (2 FP64 | 128 FP32) FMA lanes per clock x 2 flop x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def dram_traffic(kernel, workload):
+    """Per-launch DRAM bytes from the committed ncu summary, or None."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for ln in open(path):
+        parts = ln.split()
+        if len(parts) >= 3 and parts[0] == kernel and parts[1] == workload:
+            try:
+                return float(parts[2])
+            except ValueError:
+                return None
+    return None
+
+
+# ---------------------------------------------------------------------------
+
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    from paper_1506_06140_gb300 import dg
+    from paper_1506_06140_gb300 import workloads as wl
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if not dist:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return t.item()
+
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    results = {}
+    for precision in ("fp64", "fp32"):
+        s = dg.Solver(mesh(), K_DEG, 1.4, rk_order=RK_ORDER, cfl=CFL, precision=precision)
+        U = wl.vortex(s.quad_points().cpu().numpy())  # closed-form IC at the Gauss points
+        W0 = s.project(torch.as_tensor(U))
+        W = W0.clone()
+        for _ in range(args.warmup):
+            s.rk_step(W)
+        torch.cuda.synchronize()
+        barrier()
+        stream = torch.cuda.current_stream()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        s.profile_begin()
+        with ClockSampler(local_rank) as clk:
+            torch.cuda.synchronize()
+            for i in range(args.steps):
+                flush.zero_()  # evict the working set from L2 before each timed step
+                ev[i][0].record(stream)
+                s.rk_step(W)
+                ev[i][1].record(stream)
+            torch.cuda.synchronize()
+        prof = s.profile_end()
+        barrier()
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        ms = max_over_ranks(ms)
+        assert torch.isfinite(W).all().item(), "non-finite state"
+        # end to end through the C ABI with host buffers
+        Wh = W0.cpu().pin_memory()
+        Wd = torch.empty_like(W0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        barrier()
+        e0.record(stream)
+        for i in range(args.steps):
+            Wd.copy_(Wh, non_blocking=True)
+            s.rk_step(Wd)
+            Wh.copy_(Wd, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_e2e = max_over_ranks(e0.elapsed_time(e1))
+        results[precision] = dict(solver=s, ms=ms, ms_e2e=ms_e2e, prof=prof, clocks=clk.summary(),
+                                  state_bytes=W.numel() * W.element_size(), n_cells=s.n_cells)
+        del W, W0, Wd, Wh
+    return results
+
+
+def summarize(args, results, world):
+    hbm, peak_kind = peaks()
+    lines = {}
+    for precision, r in results.items():
+        cells = r["n_cells"]
+        dof_updates = world * cells * N_BASIS * STAGES * args.steps
+        value = dof_updates / (r["ms"] * 1e-3)
+        prof = r["prof"]
+        launches = sum(c for c, _ in prof.values())
+        # dominant kernel of the timed region
+        kind = max(prof, key=lambda k: prof[k][1])
+        n_launch, kms = prof[kind]
+        avg_s = kms / max(n_launch, 1) * 1e-3
+        esize = 8 if precision == "fp64" else 4
+        kname = {"cell": "cell_update_kernel", "face": "face_flux_kernel"}.get(kind, kind)
+        wlname = "vortex256_k3_" + precision
+        if precision == "fp64":
+            if kind == "cell":
+                fl = flops_cell_kernel(DIM, K_DEG) * cells
+            else:
+                fl = flops_face_kernel_per_face(DIM, K_DEG) * DIM * cells
+            achieved = fl / avg_s / 1e12
+            roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                    "peak_source": "nominal FP64 rate from unit counts and max clock",
+                    "traffic": dram_traffic(kname, wlname), "algorithmic_per_launch": fl}
+        else:
+            # HBM roof of the stage: the minimum a stage moves is 3 state arrays
+            stage_s = sum(prof[k][1] for k in ("face", "cell")) / max(prof["cell"][0], 1) * 1e-3
+            byt = 3 * state_bytes_per_cell(DIM, K_DEG, esize) * cells
+            achieved = byt / stage_s / 1e9
+            roof = {"bound": "hbm", "kernel": "stage (face_flux_kernel + cell_update_kernel)",
+                    "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                    "peak_source": peak_kind, "traffic": dram_traffic(kname, wlname),
+                    "algorithmic_per_launch": byt}
+        e2e_value = dof_updates / (r["ms_e2e"] * 1e-3)
+        lines[precision] = {
+            "value": value, "ms_per_step": r["ms"] / args.steps, "roofline": roof,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": r["state_bytes"],
+                    "d2h_bytes_per_step": r["state_bytes"]},
+            "gpu_launches": launches, "clocks": r["clocks"],
+            "kernel_ms": {k: v[1] for k, v in prof.items()},
+        }
+    return lines
+
+
+def cpu_baseline(n_sample=128, max_seconds=20.0):
+    """The oracle, as it stands, on a bounded sample of the workload: the
+    vortex on a 128^2 periodic box with the same cell size, k and RK4."""
+    from oracle import pyoracle as O
+    from paper_1506_06140_gb300 import workloads as wl
+    half = 5.0 * n_sample / N_CELLS_1D
+    m = mesh(n_sample, half)
+    o = O.Oracle(2, m["n"], m["lo"], m["hi"], K_DEG, 1.4, rk_order=RK_ORDER, cfl=CFL)
+    W = o.project(wl.vortex(o.quad_points()))
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        W, _ = o.rk_step(W, 0.0)
+        steps += 1
+        if time.perf_counter() - t0 > max_seconds / 2 or steps >= 50:
+            break
+    dt = time.perf_counter() - t0
+    value = n_sample ** 2 * N_BASIS * STAGES * steps / dt
+    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d RK4 steps of the vortex on a %dx%d periodic box with the same cell size, "
+                      "k=3 (single-threaded FP64 C++ oracle)" % (steps, n_sample, n_sample),
+            "seconds": dt}
+
+
+def reference_arm(args, rank, world):
+    """--impl reference: the oracle timed on the host cores (rank 0 only)."""
+    if rank != 0:
+        return 0
+    from oracle import pyoracle as O
+    from paper_1506_06140_gb300 import workloads as wl
+    n_sample = 64
+    half = 5.0 * n_sample / N_CELLS_1D
+    m = mesh(n_sample, half)
+    o = O.Oracle(2, m["n"], m["lo"], m["hi"], K_DEG, 1.4, rk_order=RK_ORDER, cfl=CFL)
+    W = o.project(wl.vortex(o.quad_points()))
+    for _ in range(args.warmup):
+        W, _ = o.rk_step(W, 0.0)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        W, _ = o.rk_step(W, 0.0)
+    sec = time.perf_counter() - t0
+    value = n_sample ** 2 * N_BASIS * STAGES * args.steps / sec
+    sample = ("each step: one RK4 step of the vortex on a %dx%d periodic box with the same cell "
+              "size, k=3 (single-threaded FP64 C++ oracle)" % (n_sample, n_sample))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config("fp64"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+    from paper_1506_06140_gb300 import build
+    if rank == 0 or not os.path.exists(build.LIB):
+        build.build()
+    results = run_gpu(args, rank, world, local_rank)
+    if rank != 0:
+        return 0
+    lines = summarize(args, results, world)
+    head = lines["fp64"]
+    out = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": workload_config("fp64"),
+           "roofline": head["roofline"], "e2e": head["e2e"], "gpu_launches": head["gpu_launches"],
+           "clocks": head["clocks"], "kernel_ms": head["kernel_ms"],
+           "variants": {"fp32": {k: lines["fp32"][k] for k in
+                                 ("value", "ms_per_step", "roofline", "e2e", "gpu_launches",
+                                  "clocks", "kernel_ms")}}}
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

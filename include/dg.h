@@ -1,0 +1,191 @@
+/* libdg -- GB300 (sm_103a) modal discontinuous Galerkin solver for the Euler
+ * equations, after Schaal, Bauer, Chandrashekar, Pakmor, Klingenberg and
+ * Springel (2015), "Astrophysical hydrodynamics with a high order
+ * discontinuous Galerkin scheme and adaptive mesh refinement".
+ *
+ * C ABI: plain pointers and sizes only.  Every call returns a status code
+ * (DG_OK = 0) and never throws.  Host-side argument errors are returned
+ * synchronously; errors detected on the device (non-physical state after the
+ * positivity limiter) latch a status word that dg_status() reads.
+ *
+ * Data layout (all state buffers are CALLER-OWNED device memory):
+ *   weights   W[var][coef][cell]    var = rho, rho v_1..rho v_dim, rho e
+ *             (nv = dim + 2), coef = basis function index (N of them),
+ *             cell = cell index (fastest).  Element type: double for
+ *             DG_FP64 handles, float for DG_FP32 handles.
+ *   points    u[var][q][cell] (double), xyz[axis][q][cell] (double)
+ * Cells are listed by base cell in lexicographic order (x fastest); a refined
+ * base cell is replaced by its 2^dim children in the order A..H of the paper's
+ * refinement section (child number = sum of child bits, x bit first).
+ * Basis functions: products of scaled Legendre polynomials sqrt(2n+1) P_n of
+ * total degree <= k (eq. set_basis_functions), ordered by total degree, then
+ * x exponent descending, then y exponent descending; coefficient 0 is the
+ * cell mean (eq. weights), coefficients 1..dim are the x, y, z slopes.
+ *
+ * Streams: every call that touches device data takes a cudaStream_t passed
+ * as `void* stream` (NULL = legacy default stream) and is asynchronous with
+ * respect to the host.  Scalars computed on the device (timestep, totals, L1
+ * error) are written to device memory.
+ */
+#ifndef DG_H
+#define DG_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+enum {
+  DG_OK = 0,
+  DG_ERR_ARG = 1,          /* invalid argument (null pointer, bad size, unsupported combination) */
+  DG_ERR_CUDA = 2,         /* a CUDA runtime call failed; dg_last_error() has the message */
+  DG_ERR_OOM = 3,          /* device allocation failed */
+  DG_ERR_NONPHYSICAL = 4,  /* device flag: a cell mean with rho <= 0 or p <= 0 was seen */
+  DG_ERR_TIMEOUT = 5,      /* device flag: a bounded wait gave up */
+  DG_ERR_UNSUPPORTED = 6   /* (dim, k, precision) combination not compiled */
+};
+
+enum { DG_BC_PERIODIC = 0, DG_BC_TRANSMISSIVE = 1 };
+enum { DG_LIMITER_NONE = 0, DG_LIMITER_COMPONENT = 1, DG_LIMITER_CHARACTERISTIC = 2 };
+enum { DG_FP64 = 0, DG_FP32 = 1 };
+
+/* Mesh description (paper Secs. 2.2 and 4): cubical cells on the box
+ * [lo, hi]; n[a] base cells along axis a (the base edge length must be equal
+ * on all axes); bc[a] per axis.  Static refinement: each box refines the
+ * inclusive base-cell index range [lo_0..lo_{dim-1}, hi_0..hi_{dim-1}] once
+ * (one level: the level jump between neighbours is then at most one, as the
+ * paper requires).  The description is copied by dg_create. */
+typedef struct {
+  int dim;                     /* 2 or 3 */
+  int n[3];                    /* base cells per axis (entries beyond dim ignored) */
+  double lo[3], hi[3];         /* domain box */
+  int bc[3];                   /* DG_BC_PERIODIC or DG_BC_TRANSMISSIVE per axis */
+  int n_refine_boxes;          /* number of refinement boxes (0 = uniform mesh) */
+  const int32_t* refine_boxes; /* host pointer, n_refine_boxes * 2 * dim ints */
+} dg_mesh_desc;
+
+/* Scheme options (defaults from dg_default_options follow the paper's runs:
+ * CFL 0.2 (Sec. 2.5), beta = 1, Mtilde = 0.5 (Sec. 5), eps = 1e-10 (Sec. 3.4)). */
+typedef struct {
+  int rk_order;      /* 1..4: SSP RK tableaux of Appendix D (order 4 is the 5-stage method) */
+  double cfl;        /* CFL number of eq. time_step */
+  int slope_limiter; /* DG_LIMITER_* (Secs. 3.1-3.3; bounded minmod) */
+  double beta;       /* limiter parameter beta in [0.5, 1] */
+  double Mtilde;     /* TVB bound: a slope is kept when |sqrt(3) slope| <= Mtilde * dx */
+  int positivity;    /* 1: positivity limiter of Sec. 3.4 after every stage */
+  double eps;        /* positivity floor */
+  int precision;     /* DG_FP64 or DG_FP32 (state, fluxes and contractions); the
+                        totals, L1 error, timestep and positivity check stay FP64 */
+} dg_options;
+
+typedef struct dg_handle dg_handle;
+
+/* Fills *opt with the defaults above (rk_order = 3, no limiter, FP64). */
+int dg_default_options(dg_options* opt);
+
+/* Creates a solver for a mesh, polynomial degree k and adiabatic index gamma
+ * (paper Sec. 2).  Builds the cell list, neighbour and face tables and the
+ * quadrature tables (Appendices A-C) on the host, uploads them and allocates
+ * the library-owned scratch (stage registers, face-flux buffer, reduction
+ * partials) on the current CUDA device.  Supported: dim 2 with k = 0..3,
+ * dim 3 with k = 0..2.  On failure *out is NULL and the status says why
+ * (dg_last_error(NULL) has the message). */
+int dg_create(const dg_mesh_desc* mesh, int k, double gamma, const dg_options* opt,
+              dg_handle** out);
+
+/* Frees the handle and its device memory.  NULL is accepted. */
+int dg_destroy(dg_handle* h);
+
+/* Last error message of a handle (or of the last failed dg_create if h is NULL). */
+const char* dg_last_error(const dg_handle* h);
+
+/* Sizes: cells, basis functions N(k) (eq. nof_basis_functions and its 2D
+ * analogue), variables nv, volume Gauss points per cell (k+1)^dim, points of
+ * the (k+3)^dim rule used by dg_l1_density, refined base cells (nodes). */
+int dg_sizes(const dg_handle* h, int64_t* n_cells, int* n_basis, int* n_vars, int* n_qpoints,
+             int* n_l1points, int* n_nodes);
+
+/* Physical coordinates of the volume Gauss points (xyz[axis][q][cell]) and of
+ * the (k+3)^dim rule's points; q runs with the x index fastest. */
+int dg_quad_points(const dg_handle* h, double* xyz_dev, void* stream);
+int dg_l1_points(const dg_handle* h, double* xyz_dev, void* stream);
+
+/* L2 projection of point values onto the basis (Sec. 2.3):
+ * W_j = 2^-dim sum_q u(xi_q) phi_j(xi_q) w_q with the (k+1)^dim Gauss rule.
+ * u_dev: double [nv][Q][cell]; W_dev: handle precision [nv][N][cell]. */
+int dg_project(dg_handle* h, const double* u_dev, void* W_dev, void* stream);
+
+/* Time derivative dW/dt = -R(W) of eq. spatial_discretisation: volume
+ * integral (eq. dg_term2) plus surface integral with the HLLC flux at the
+ * face Gauss points (eq. dg_term3), hanging faces integrated at the fine
+ * sub-face points.  No limiter.  W_dev and dWdt_dev must not alias. */
+int dg_rhs(dg_handle* h, const void* W_dev, void* dWdt_dev, void* stream);
+
+/* CFL timestep (eq. time_step, or eq. time_step_pos with positivity on),
+ * from the cell means, minimum over all cells, written to *dt_dev (double). */
+int dg_compute_dt(dg_handle* h, const void* W_dev, double* dt_dev, void* stream);
+
+/* One SSP-RK step in place (Appendix D, main loop of Sec. 4.5):
+ * W <- W + dt sum_i b_i k_i with k_i = -R(U_i); every stage state U_i (i>=2)
+ * and the new state are limited when limiting is enabled.  dt > 0 uses that
+ * value; dt <= 0 computes the CFL timestep on the device first.  If
+ * dt_used_dev is not NULL the timestep is written there (double). */
+int dg_rk_step(dg_handle* h, void* W_dev, double dt, double* dt_used_dev, void* stream);
+
+/* n_steps CFL steps in place, recorded once into a CUDA graph per (W_dev,
+ * n_steps) and replayed; dt_hist_dev (optional, double[n_steps]) receives the
+ * timesteps.  The first call for a given W_dev/n_steps records the graph. */
+int dg_advance(dg_handle* h, void* W_dev, int n_steps, double* dt_hist_dev, void* stream);
+
+/* Adjoint of one unlimited step with a frozen timestep dt (> 0):
+ * lam_n = (d W_{n+1} / d W_n)^T lam_np1, where W_n_dev is the checkpointed
+ * state the step started from.  The stage states are recomputed from W_n.
+ * Requires slope_limiter = NONE and positivity = 0. */
+int dg_rk_step_adjoint(dg_handle* h, const void* W_n_dev, double dt, const void* lam_np1_dev,
+                       void* lam_n_dev, void* stream);
+
+/* Slope limiter (Secs. 3.2-3.3, with the AMR neighbour projections of
+ * Sec. 4.4) followed by the positivity limiter (Sec. 3.4), in place. */
+int dg_limit(dg_handle* h, void* W_dev, void* stream);
+
+/* Conserved totals sum_K |K| w_{1,i} (FP64, deterministic two-pass
+ * reduction) -> totals_dev[nv] (double). */
+int dg_totals(dg_handle* h, const void* W_dev, double* totals_dev, void* stream);
+
+/* L1 density error (eq. L1_norm) with the (k+3)^dim Gauss rule per cell:
+ * (1/V) sum_K int_K |rho_h - rho_ref| dV; rho_ref_dev: double [Q1][cell] at
+ * the points of dg_l1_points.  Result in *out_dev (double). */
+int dg_l1_density(dg_handle* h, const void* W_dev, const double* rho_ref_dev, double* out_dev,
+                  void* stream);
+
+/* AMR node weights w_node = 2^-dim sum_c P_c^T w^c over the children of every
+ * refined base cell (eq. deref_weights) -> Wnode_dev [nv][N][node]. */
+int dg_node_weights(dg_handle* h, const void* W_dev, void* Wnode_dev, void* stream);
+
+/* Host copies of the mesh tables, for checks:
+ * neighbour table nbr[side][cell] (side = 2*axis + {0:-, 1:+}; >= 0 a leaf
+ * cell, -1 no neighbour, <= -2 the node -(v+2)); levels[cell]. */
+int dg_neighbor_table(const dg_handle* h, int32_t* host_out);
+int dg_cell_levels(const dg_handle* h, int32_t* host_out);
+
+/* ---- instrumentation ---------------------------------------------------
+ * Per-kernel timing: while enabled, every kernel launch of the handle is
+ * bracketed by two CUDA events recorded on the launch stream (not inside
+ * dg_advance's graphs).  dg_profile_end waits for the recorded events and
+ * returns, per kernel kind, the number of launches and the summed device
+ * time in milliseconds. */
+enum { DG_KERNEL_FACE = 0, DG_KERNEL_CELL = 1, DG_KERNEL_LIMIT = 2, DG_KERNEL_DT = 3,
+       DG_KERNEL_OTHER = 4, DG_KERNEL_KINDS = 5 };
+int dg_profile_begin(dg_handle* h);
+int dg_profile_end(dg_handle* h, int* launches, double* total_ms, int n_kinds);
+
+/* Reads and clears the device status word (DG_OK, DG_ERR_NONPHYSICAL, ...).
+ * Synchronises the handle's last stream. */
+int dg_status(dg_handle* h, int* device_status_host);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DG_H */

@@ -1,0 +1,46 @@
+// Small helper kernels shared by all schemes, and the kernel-set dispatch.
+#include <mutex>
+
+#include "dg_internal.h"
+
+namespace dgi {
+
+bool kernel_set_2d(int prec, int k, KernelSet* out);
+bool kernel_set_3d(int prec, int k, KernelSet* out);
+
+const KernelSet* kernel_set(int prec, int dim, int k) {
+  static KernelSet sets[2][2][4];
+  static bool have[2][2][4] = {};
+  static std::mutex mu;
+  if (prec < 0 || prec > 1 || (dim != 2 && dim != 3) || k < 0 || k > 3) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  KernelSet& ks = sets[prec][dim - 2][k];
+  if (!have[prec][dim - 2][k]) {
+    const bool ok = dim == 2 ? kernel_set_2d(prec, k, &ks) : kernel_set_3d(prec, k, &ks);
+    if (!ok) return nullptr;
+    have[prec][dim - 2][k] = true;
+  }
+  return &ks;
+}
+
+__global__ void set_scalar_kernel(double* dst, double value) { *dst = value; }
+
+cudaError_t launch_set_scalar(double* dst, double value, cudaStream_t s) {
+  set_scalar_kernel<<<1, 1, 0, s>>>(dst, value);
+  return cudaGetLastError();
+}
+
+// the minimum timestep was accumulated as the bit pattern of a positive double
+__global__ void dt_finalize_kernel(const unsigned long long* bits, double* dt, double* dt_copy) {
+  const double v = __longlong_as_double((long long)*bits);
+  *dt = v;
+  if (dt_copy) *dt_copy = v;
+}
+
+cudaError_t launch_dt_finalize(const unsigned long long* bits, double* dt, double* dt_copy,
+                               cudaStream_t s) {
+  dt_finalize_kernel<<<1, 1, 0, s>>>(bits, dt, dt_copy);
+  return cudaGetLastError();
+}
+
+}  // namespace dgi

@@ -1,0 +1,1107 @@
+// libdg host side: the C ABI of include/dg.h.  Builds the mesh and face
+// tables, the quadrature tables, and the per-step stage program; launches the
+// kernels of dg_kernels.cuh on the caller's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "dg.h"
+#include "dg_internal.h"
+
+using namespace dgi;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+// ---------------------------------------------------------------------------
+// 1D rules on [-1,1] (Appendices B and C), computed by Newton iteration.
+
+double leg_p(int n, double x, double* dp) {
+  // value and derivative of P_n by the three-term recurrence
+  double p0 = 1.0, p1 = x, d0 = 0.0, d1 = 1.0;
+  if (n == 0) { *dp = 0.0; return 1.0; }
+  for (int m = 1; m < n; ++m) {
+    const double p2 = ((2.0 * m + 1.0) * x * p1 - m * p0) / (m + 1.0);
+    const double d2 = d0 + (2.0 * m + 1.0) * p1;
+    p0 = p1; p1 = p2; d0 = d1; d1 = d2;
+  }
+  *dp = d1;
+  return p1;
+}
+
+void gauss_rule(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.resize(n);
+  w.resize(n);
+  for (int q = 0; q < n; ++q) {
+    // Lether's approximation of root q (largest first), then Newton
+    double r = (1.0 - 1.0 / (8.0 * n * n) + 1.0 / (8.0 * n * n * n)) *
+               std::cos(M_PI * (4.0 * (q + 1) - 1.0) / (4.0 * n + 2.0));
+    double d = 0.0;
+    for (int it = 0; it < 64; ++it) {
+      const double p = leg_p(n, r, &d);
+      const double step = p / d;
+      r -= step;
+      if (std::fabs(step) <= 1e-16) break;
+    }
+    leg_p(n, r, &d);
+    x[n - 1 - q] = r;
+    w[n - 1 - q] = 2.0 / ((1.0 - r * r) * d * d);
+  }
+}
+
+void lobatto_rule(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  x[0] = -1.0;
+  x[n - 1] = 1.0;
+  const int m = n - 1;
+  double sum = 0.0;
+  for (int q = 1; q < n - 1; ++q) {
+    double r = -std::cos(M_PI * q / m);
+    for (int it = 0; it < 64; ++it) {
+      double d;
+      const double p = leg_p(m, r, &d);
+      // Newton on P'_m using P''_m = (2 r P'_m - m (m+1) P_m) / (1 - r^2)
+      const double d2 = (2.0 * r * d - m * (m + 1.0) * p) / (1.0 - r * r);
+      const double step = d / d2;
+      r -= step;
+      if (std::fabs(step) <= 1e-16) break;
+    }
+    double d;
+    const double p = leg_p(m, r, &d);
+    x[q] = r;
+    w[q] = 2.0 / (n * (n - 1.0) * p * p);
+    sum += w[q];
+  }
+  w[0] = w[n - 1] = 0.5 * (2.0 - sum);
+}
+
+// ---------------------------------------------------------------------------
+// Step program: the Butcher tableau (Appendix D) rewritten as a sequence of
+// stages, each evaluating dW/dt at one stored state and forming at most three
+// linear combinations of stored arrays and the new derivative.
+
+struct Tab {
+  int s = 0;
+  std::vector<double> A, b;
+};
+
+Tab butcher(int order) {
+  Tab t;
+  if (order == 1) { t.s = 1; t.A = {0}; t.b = {1}; }
+  else if (order == 2) { t.s = 2; t.A = {0, 0, 1, 0}; t.b = {0.5, 0.5}; }
+  else if (order == 3) {
+    t.s = 3;
+    t.A = {0, 0, 0, 1, 0, 0, 0.25, 0.25, 0};
+    t.b = {1.0 / 6.0, 1.0 / 6.0, 2.0 / 3.0};
+  } else {
+    // SSP RK(5,4), Table RK_4
+    t.s = 5;
+    t.A.assign(25, 0.0);
+    const double a[5][5] = {{0, 0, 0, 0, 0},
+                            {0.39175222700392, 0, 0, 0, 0},
+                            {0.21766909633821, 0.36841059262959, 0, 0, 0},
+                            {0.08269208670950, 0.13995850206999, 0.25189177424738, 0, 0},
+                            {0.06796628370320, 0.11503469844438, 0.20703489864929,
+                             0.54497475021237, 0}};
+    for (int i = 0; i < 5; ++i)
+      for (int j = 0; j < 5; ++j) t.A[i * 5 + j] = a[i][j];
+    t.b = {0.14681187618661, 0.24848290924556, 0.10425883036650, 0.27443890091960,
+           0.22600748319395};
+  }
+  return t;
+}
+
+struct Op {
+  int in_reg = 0;                 // state whose dW/dt is evaluated
+  int n_in = 0, n_out = 0;
+  int in[MAX_IN] = {0, 0, 0, 0};
+  int out[MAX_OUT] = {0, 0, 0};
+  double C[MAX_OUT][MAX_IN] = {};
+  double ck[MAX_OUT] = {};
+  int lim_src = -1, lim_dst = -1; // limiter pass after the stage (virtual registers)
+};
+
+struct Program {
+  std::vector<Op> ops;
+  int n_phys = 0;                 // scratch registers needed (register 0 is the caller's W)
+};
+
+// least squares: min |sum_r lam_r V_r - t|, returns residual norm
+double lsq(const std::vector<std::vector<double>>& V, const std::vector<double>& t,
+           std::vector<double>& lam) {
+  const int n = (int)V.size(), m = (int)t.size();
+  std::vector<double> G(n * n, 0.0), r(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    for (int j = 0; j < n; ++j)
+      for (int k = 0; k < m; ++k) G[i * n + j] += V[i][k] * V[j][k];
+    for (int k = 0; k < m; ++k) r[i] += V[i][k] * t[k];
+  }
+  // Gaussian elimination with partial pivoting
+  std::vector<int> piv(n);
+  for (int i = 0; i < n; ++i) piv[i] = i;
+  for (int c = 0; c < n; ++c) {
+    int best = c;
+    for (int i = c + 1; i < n; ++i)
+      if (std::fabs(G[i * n + c]) > std::fabs(G[best * n + c])) best = i;
+    if (std::fabs(G[best * n + c]) < 1e-300) return 1e300;
+    if (best != c) {
+      for (int j = 0; j < n; ++j) std::swap(G[c * n + j], G[best * n + j]);
+      std::swap(r[c], r[best]);
+    }
+    for (int i = c + 1; i < n; ++i) {
+      const double f = G[i * n + c] / G[c * n + c];
+      for (int j = c; j < n; ++j) G[i * n + j] -= f * G[c * n + j];
+      r[i] -= f * r[c];
+    }
+  }
+  lam.assign(n, 0.0);
+  for (int i = n - 1; i >= 0; --i) {
+    double s = r[i];
+    for (int j = i + 1; j < n; ++j) s -= G[i * n + j] * lam[j];
+    lam[i] = s / G[i * n + i];
+  }
+  double res = 0.0;
+  for (int k = 0; k < m; ++k) {
+    double s = -t[k];
+    for (int i = 0; i < n; ++i) s += lam[i] * V[i][k];
+    res += s * s;
+  }
+  return std::sqrt(res);
+}
+
+// Express target t (coordinates: [alpha, k_0..k_{s-1}], the k_i entry
+// already removed) with as few of the candidate registers as possible.
+bool represent(const std::vector<int>& cand, const std::map<int, std::vector<double>>& content,
+               const std::vector<double>& t, std::vector<int>& used, std::vector<double>& lam) {
+  double tn = 0.0;
+  for (double x : t) tn += x * x;
+  tn = std::sqrt(tn);
+  if (tn == 0.0) { used.clear(); lam.clear(); return true; }
+  const int nc = (int)cand.size();
+  for (int size = 1; size <= std::min(nc, MAX_IN); ++size) {
+    std::vector<int> idx(size);
+    for (int i = 0; i < size; ++i) idx[i] = i;
+    while (true) {
+      std::vector<std::vector<double>> V;
+      for (int i : idx) V.push_back(content.at(cand[i]));
+      std::vector<double> l;
+      const double res = lsq(V, t, l);
+      if (res <= 1e-9 * (tn + 1.0)) {
+        used.clear();
+        for (int i : idx) used.push_back(cand[i]);
+        lam = l;
+        return true;
+      }
+      int p = size - 1;
+      while (p >= 0 && idx[p] == nc - size + p) --p;
+      if (p < 0) break;
+      ++idx[p];
+      for (int i = p + 1; i < size; ++i) idx[i] = idx[i - 1] + 1;
+    }
+  }
+  return false;
+}
+
+// Builds the stage program of one step.  Without limiting the stage states
+// themselves serve as registers (U_i = w + dt sum_j a_ij k_j), so every
+// stage reads at most the stage state, w and one earlier state.  With
+// limiting, the stage states are limited and carry no such identity; the
+// program keeps accumulators of dt * (combinations of k_j) instead, chosen as
+// a basis of the combinations later stages and the final update still need.
+bool build_program(int order, bool limited, Program& P, std::string& err) {
+  const Tab tb = butcher(order);
+  const int s = tb.s;
+  const int dimv = 1 + s;  // coordinates: alpha (coefficient of w), k_0..k_{s-1}
+  std::map<int, std::vector<double>> content;  // virtual register -> coordinates
+  content[0] = std::vector<double>(dimv, 0.0);
+  content[0][0] = 1.0;
+  int next_vreg = 1;
+  int cur = 0;  // virtual register holding the current stage state
+  std::vector<int> accs;  // accumulator registers (limited mode)
+  std::vector<Op> ops;
+  for (int i = 0; i < s; ++i) {
+    Op op;
+    op.in_reg = cur;
+    const bool last = (i == s - 1);
+    // targets: next stage state (or final state), then accumulators
+    std::vector<std::vector<double>> targets;
+    std::vector<double> t0(dimv, 0.0);
+    t0[0] = 1.0;
+    for (int j = 0; j <= i; ++j) t0[1 + j] = last ? tb.b[j] : tb.A[(i + 1) * s + j];
+    if (last)
+      for (int j = 0; j < s; ++j) t0[1 + j] = tb.b[j];
+    targets.push_back(t0);
+    std::vector<int> new_accs;
+    if (limited && !last) {
+      // combinations of k_0..k_i still needed after this stage
+      std::vector<std::vector<double>> needs;
+      for (int m = i + 2; m < s; ++m) {
+        std::vector<double> v(dimv, 0.0);
+        for (int j = 0; j <= i; ++j) v[1 + j] = tb.A[m * s + j];
+        needs.push_back(v);
+      }
+      {
+        std::vector<double> v(dimv, 0.0);
+        for (int j = 0; j <= i; ++j) v[1 + j] = tb.b[j];
+        needs.push_back(v);
+      }
+      std::vector<std::vector<double>> basis;
+      for (auto& v : needs) {
+        std::vector<double> l;
+        bool dep = false;
+        if (!basis.empty()) {
+          double vn = 0.0;
+          for (double x : v) vn += x * x;
+          dep = lsq(basis, v, l) <= 1e-9 * (std::sqrt(vn) + 1.0);
+        }
+        bool zero = true;
+        for (double x : v) zero = zero && x == 0.0;
+        if (!dep && !zero) basis.push_back(v);
+      }
+      for (auto& v : basis) {
+        targets.push_back(v);
+        const int r = next_vreg++;
+        content[r] = v;
+        new_accs.push_back(r);
+      }
+    }
+    // candidate inputs
+    std::vector<int> cand;
+    if (!limited) {
+      cand.push_back(cur);
+      if (cur != 0) cand.push_back(0);
+      for (auto& kv : content)
+        if (kv.first != cur && kv.first != 0 &&
+            std::find(new_accs.begin(), new_accs.end(), kv.first) == new_accs.end())
+          cand.push_back(kv.first);
+    } else {
+      cand.push_back(0);
+      for (int r : accs) cand.push_back(r);
+    }
+    std::vector<int> ins;
+    std::vector<std::vector<double>> coefs;
+    for (size_t o = 0; o < targets.size(); ++o) {
+      std::vector<double> t = targets[o];
+      const double cki = t[1 + i];
+      t[1 + i] = 0.0;
+      std::vector<int> used;
+      std::vector<double> lam;
+      if (!represent(cand, content, t, used, lam)) {
+        err = "internal: Runge-Kutta stage program has no representation";
+        return false;
+      }
+      op.ck[o] = cki;
+      for (size_t u = 0; u < used.size(); ++u) {
+        auto it = std::find(ins.begin(), ins.end(), used[u]);
+        int slot;
+        if (it == ins.end()) {
+          ins.push_back(used[u]);
+          slot = (int)ins.size() - 1;
+        } else {
+          slot = (int)(it - ins.begin());
+        }
+        if (slot >= MAX_IN) { err = "internal: too many stage inputs"; return false; }
+        op.C[o][slot] = lam[u];
+      }
+    }
+    op.n_in = (int)ins.size();
+    for (int r = 0; r < op.n_in; ++r) op.in[r] = ins[r];
+    op.n_out = (int)targets.size();
+    if (op.n_out > MAX_OUT) { err = "internal: too many stage outputs"; return false; }
+    // output registers
+    int stage_out;
+    if (!limited) {
+      stage_out = last ? 0 : next_vreg++;
+      if (!last) content[stage_out] = targets[0];
+      op.out[0] = stage_out;
+      cur = stage_out;
+    } else {
+      stage_out = next_vreg++;  // unlimited value, limited into lim_dst
+      op.out[0] = stage_out;
+      const int dst = last ? 0 : next_vreg++;
+      op.lim_src = stage_out;
+      op.lim_dst = dst;
+      cur = dst;
+    }
+    for (size_t o = 1; o < targets.size(); ++o) op.out[o] = new_accs[o - 1];
+    if (limited) accs = new_accs;
+    ops.push_back(op);
+  }
+  // register allocation: virtual -> physical by live ranges
+  const int nops = (int)ops.size();
+  std::map<int, int> def, last_use;
+  for (int i = 0; i < nops; ++i) {
+    const Op& op = ops[i];
+    auto use = [&](int r) { last_use[r] = std::max(last_use.count(r) ? last_use[r] : i, i); };
+    use(op.in_reg);
+    for (int r = 0; r < op.n_in; ++r) use(op.in[r]);
+    for (int o = 0; o < op.n_out; ++o) if (!def.count(op.out[o])) def[op.out[o]] = i;
+    if (op.lim_src >= 0) { use(op.lim_src); if (!def.count(op.lim_dst)) def[op.lim_dst] = i; }
+  }
+  std::map<int, int> phys;
+  phys[0] = 0;
+  std::vector<int> busy_until;  // per physical scratch register (1-based index = p)
+  for (int i = 0; i < nops; ++i) {
+    std::vector<int> defs;
+    for (int o = 0; o < ops[i].n_out; ++o) defs.push_back(ops[i].out[o]);
+    if (ops[i].lim_dst >= 0) defs.push_back(ops[i].lim_dst);
+    for (int r : defs) {
+      if (phys.count(r)) continue;
+      const int end = last_use.count(r) ? last_use[r] : i;
+      int p = -1;
+      for (size_t j = 0; j < busy_until.size(); ++j)
+        if (busy_until[j] < i) { p = (int)j; break; }
+      if (p < 0) { busy_until.push_back(0); p = (int)busy_until.size() - 1; }
+      busy_until[p] = std::max(end, i);
+      phys[r] = p + 1;
+    }
+  }
+  for (auto& op : ops) {
+    op.in_reg = phys.at(op.in_reg);
+    for (int r = 0; r < op.n_in; ++r) op.in[r] = phys.at(op.in[r]);
+    for (int o = 0; o < op.n_out; ++o) op.out[o] = phys.at(op.out[o]);
+    if (op.lim_src >= 0) { op.lim_src = phys.at(op.lim_src); op.lim_dst = phys.at(op.lim_dst); }
+  }
+  P.ops = ops;
+  P.n_phys = (int)busy_until.size();
+  return true;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+
+struct dg_handle {
+  int dim = 2, k = 1, prec = DG_FP64, nv = 4, N = 3;
+  double gamma = 1.4;
+  dg_options opt{};
+  const KernelSet* ks = nullptr;
+  size_t esize = 8;  // bytes per state element
+  // host mesh tables
+  int ncells = 0, nfaces = 0, nnodes = 0;
+  std::vector<int32_t> nbr, coord, node_children, fm, fp, sface;
+  std::vector<int8_t> level;
+  std::vector<uint8_t> finfo, scoarse;
+  MeshDev md;
+  double volume = 1.0;
+  // device memory
+  std::vector<void*> allocs;
+  void* tab = nullptr;
+  double* tab64 = nullptr;
+  void* F = nullptr;
+  std::vector<void*> regs;   // scratch state registers 1..n
+  double* scal = nullptr;    // [0] dt slot
+  unsigned long long* dt_bits = nullptr;
+  double* partial = nullptr;
+  int* status = nullptr;
+  Program prog_step;         // limited as configured
+  Program prog_free;         // unlimited (adjoint recomputation)
+  cudaStream_t cap_stream = nullptr;
+  std::map<std::tuple<void*, int, void*>, cudaGraphExec_t> graphs;
+  std::vector<cudaGraph_t> graph_defs;
+  std::string err;
+  std::mutex mu;
+  // instrumentation
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<std::pair<int, size_t>> ev_marks;  // (kind, index of the start event)
+};
+
+namespace {
+
+int fail(dg_handle* h, int code, const std::string& msg) {
+  if (h) h->err = msg; else g_create_error = msg;
+  return code;
+}
+
+int cuda_fail(dg_handle* h, cudaError_t e, const char* what) {
+  return fail(h, DG_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define DG_CUDA(h, call)                                       \
+  do {                                                         \
+    cudaError_t e__ = (call);                                  \
+    if (e__ != cudaSuccess) return cuda_fail((h), e__, #call); \
+  } while (0)
+
+// Runs one kernel launcher; with profiling on, brackets it by two events.
+template <typename F>
+cudaError_t timed(dg_handle* h, int kind, cudaStream_t s, F&& launch) {
+  if (!h->profiling) return launch();
+  while (h->ev_pool.size() < h->ev_used + 2) {
+    cudaEvent_t e;
+    cudaError_t r = cudaEventCreate(&e);
+    if (r != cudaSuccess) return r;
+    h->ev_pool.push_back(e);
+  }
+  const size_t i0 = h->ev_used;
+  h->ev_used += 2;
+  cudaError_t r = cudaEventRecord(h->ev_pool[i0], s);
+  if (r != cudaSuccess) return r;
+  r = launch();
+  if (r != cudaSuccess) return r;
+  r = cudaEventRecord(h->ev_pool[i0 + 1], s);
+  h->ev_marks.push_back({kind, i0});
+  return r;
+}
+
+template <typename T>
+int upload(dg_handle* h, const std::vector<T>& v, const T** out) {
+  if (v.empty()) { *out = nullptr; return DG_OK; }
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, v.size() * sizeof(T));
+  if (e != cudaSuccess) return fail(h, DG_ERR_OOM, "cudaMalloc of a mesh table failed");
+  h->allocs.push_back(p);
+  e = cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpy");
+  *out = static_cast<const T*>(p);
+  return DG_OK;
+}
+
+int dalloc(dg_handle* h, size_t bytes, void** out) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, DG_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+  }
+  h->allocs.push_back(p);
+  *out = p;
+  return DG_OK;
+}
+
+// Mesh tables by index arithmetic over the base grid: every base cell owns
+// one cell (unrefined) or 2^dim consecutive children (refined).
+int build_mesh(dg_handle* h, const dg_mesh_desc* m) {
+  const int d = m->dim;
+  int n[3] = {1, 1, 1};
+  int bc[3] = {DG_BC_PERIODIC, DG_BC_PERIODIC, DG_BC_PERIODIC};
+  for (int a = 0; a < d; ++a) {
+    n[a] = m->n[a];
+    bc[a] = m->bc[a];
+    if (n[a] < 1) return fail(h, DG_ERR_ARG, "mesh: n must be >= 1");
+    if (bc[a] != DG_BC_PERIODIC && bc[a] != DG_BC_TRANSMISSIVE)
+      return fail(h, DG_ERR_ARG, "mesh: unknown boundary condition");
+    if (!(m->hi[a] > m->lo[a])) return fail(h, DG_ERR_ARG, "mesh: hi must exceed lo");
+  }
+  const double dx0 = (m->hi[0] - m->lo[0]) / n[0];
+  for (int a = 1; a < d; ++a)
+    if (std::fabs((m->hi[a] - m->lo[a]) / n[a] - dx0) > 1e-12 * dx0)
+      return fail(h, DG_ERR_ARG, "mesh: cells must be cubical (equal edge length on all axes)");
+  const int64_t nbase64 = (int64_t)n[0] * n[1] * n[2];
+  if (nbase64 > (1LL << 28)) return fail(h, DG_ERR_ARG, "mesh: too many base cells");
+  const int nbase = (int)nbase64;
+  std::vector<uint8_t> refined(nbase, 0);
+  if (m->n_refine_boxes > 0 && !m->refine_boxes) return fail(h, DG_ERR_ARG, "mesh: refine_boxes is NULL");
+  for (int b = 0; b < m->n_refine_boxes; ++b) {
+    const int32_t* bx = m->refine_boxes + 2 * d * b;
+    int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    for (int a = 0; a < d; ++a) {
+      lo[a] = std::max(0, (int)bx[a]);
+      hi[a] = std::min(n[a] - 1, (int)bx[d + a]);
+    }
+    for (int z = lo[2]; z <= hi[2]; ++z)
+      for (int y = lo[1]; y <= hi[1]; ++y)
+        for (int x = lo[0]; x <= hi[0]; ++x) refined[x + n[0] * (y + n[1] * z)] = 1;
+  }
+  const int nch = 1 << d;
+  std::vector<int32_t> first(nbase + 1, 0), node_of(nbase, -1);
+  int nn = 0;
+  for (int b = 0; b < nbase; ++b) {
+    first[b + 1] = first[b] + (refined[b] ? nch : 1);
+    if (refined[b]) node_of[b] = nn++;
+  }
+  const int nc = first[nbase];
+  h->ncells = nc;
+  h->nnodes = nn;
+  h->level.assign(nc, 0);
+  h->coord.assign((size_t)3 * nc, 0);
+  h->node_children.assign((size_t)nn * nch, 0);
+  for (int b = 0; b < nbase; ++b) {
+    const int bx = b % n[0], by = (b / n[0]) % n[1], bz = b / (n[0] * n[1]);
+    if (!refined[b]) {
+      const int c = first[b];
+      h->coord[c] = bx; h->coord[nc + c] = by; h->coord[2 * nc + c] = bz;
+    } else {
+      for (int ch = 0; ch < nch; ++ch) {
+        const int c = first[b] + ch;
+        h->level[c] = 1;
+        h->coord[c] = 2 * bx + (ch & 1);
+        h->coord[nc + c] = 2 * by + ((ch >> 1) & 1);
+        h->coord[2 * nc + c] = d == 3 ? 2 * bz + ((ch >> 2) & 1) : 0;
+        h->node_children[(size_t)node_of[b] * nch + ch] = c;
+      }
+    }
+  }
+  // neighbour table
+  h->nbr.assign((size_t)2 * d * nc, -1);
+  for (int c = 0; c < nc; ++c) {
+    const int l = h->level[c];
+    for (int a = 0; a < d; ++a)
+      for (int s = 0; s < 2; ++s) {
+        int p[3] = {h->coord[c], h->coord[nc + c], h->coord[2 * nc + c]};
+        p[a] += s ? 1 : -1;
+        const int ext = n[a] << l;
+        if (p[a] < 0 || p[a] >= ext) {
+          if (bc[a] != DG_BC_PERIODIC) continue;  // stays -1
+          p[a] = (p[a] + ext) % ext;
+        }
+        const int b = (p[0] >> l) + n[0] * ((p[1] >> l) + n[1] * (p[2] >> l));
+        int32_t v;
+        if (l == 0) {
+          v = refined[b] ? -(node_of[b] + 2) : first[b];
+        } else {
+          v = refined[b] ? first[b] + ((p[0] & 1) | ((p[1] & 1) << 1) | ((p[2] & 1) << 2)) : first[b];
+        }
+        h->nbr[(size_t)(2 * a + s) * nc + c] = v;
+      }
+  }
+  // face entries: conforming faces and boundary faces by direction in cell
+  // order (so a warp of faces maps to consecutive cells), then the hanging
+  // sub-faces grouped per coarse side in quadrant order
+  h->fm.clear(); h->fp.clear(); h->finfo.clear();
+  h->sface.assign((size_t)2 * d * nc, -1);
+  h->scoarse.assign(nc, 0);
+  auto add_face = [&](int cm, int cp, int dir, int vm, int vp) {
+    h->fm.push_back(cm); h->fp.push_back(cp);
+    h->finfo.push_back((uint8_t)(dir | (vm << 2) | (vp << 5)));
+    return (int)h->fm.size() - 1;
+  };
+  for (int a = 0; a < d; ++a)
+    for (int c = 0; c < nc; ++c) {
+      const int up = h->nbr[(size_t)(2 * a + 1) * nc + c];
+      if (up == -1) {
+        h->sface[(size_t)(2 * a + 1) * nc + c] = add_face(c, -1, a, 0, 0);
+      } else if (up >= 0 && h->level[up] == h->level[c]) {
+        const int f = add_face(c, up, a, 0, 0);
+        h->sface[(size_t)(2 * a + 1) * nc + c] = f;
+        h->sface[(size_t)(2 * a + 0) * nc + up] = f;
+      }
+      const int dn = h->nbr[(size_t)(2 * a + 0) * nc + c];
+      if (dn == -1) h->sface[(size_t)(2 * a + 0) * nc + c] = add_face(-1, c, a, 0, 0);
+    }
+  const int nsub = 1 << (d - 1);
+  for (int a = 0; a < d; ++a)
+    for (int c = 0; c < nc; ++c)
+      for (int s = 0; s < 2; ++s) {
+        const int nb = h->nbr[(size_t)(2 * a + s) * nc + c];
+        if (nb > -2) continue;
+        // coarse cell c, finer node on side s: its children touching the face
+        const int node = -(nb + 2);
+        h->scoarse[c] |= (uint8_t)(1u << (2 * a + s));
+        for (int quad = 0; quad < nsub; ++quad) {
+          int ch = s ? 0 : (1 << a);  // child bit along a: adjacent layer of the node
+          int t = 0;
+          for (int b = 0; b < d; ++b) {
+            if (b == a) continue;
+            if ((quad >> t) & 1) ch |= 1 << b;
+            ++t;
+          }
+          const int fine = h->node_children[(size_t)node * nch + ch];
+          const int f = s ? add_face(c, fine, a, 1 + quad, 0) : add_face(fine, c, a, 0, 1 + quad);
+          if (quad == 0) h->sface[(size_t)(2 * a + s) * nc + c] = f;
+          h->sface[(size_t)(2 * a + (1 - s)) * nc + fine] = f;
+        }
+      }
+  h->nfaces = (int)h->fm.size();
+  for (size_t i = 0; i < h->sface.size(); ++i)
+    if (h->sface[i] < 0) return fail(h, DG_ERR_ARG, "internal: a cell side has no face");
+  h->volume = 1.0;
+  for (int a = 0; a < d; ++a) h->volume *= m->hi[a] - m->lo[a];
+  h->md.ncells = nc;
+  h->md.nfaces = h->nfaces;
+  h->md.nnodes = nn;
+  h->md.dx0 = dx0;
+  for (int a = 0; a < 3; ++a) {
+    h->md.lo[a] = a < d ? m->lo[a] : 0.0;
+    h->md.n[a] = n[a];
+  }
+  return DG_OK;
+}
+
+template <typename real>
+StageArgs<real> stage_args(dg_handle* h, const Op& op, const void* U, void* W) {
+  StageArgs<real> a;
+  a.m = h->md;
+  a.tab = static_cast<const real*>(h->tab);
+  a.U = static_cast<const real*>(U);
+  a.F = static_cast<real*>(h->F);
+  a.gamma = h->gamma;
+  auto reg = [&](int r) -> real* { return static_cast<real*>(r == 0 ? W : h->regs[r - 1]); };
+  a.n_in = op.n_in;
+  for (int r = 0; r < op.n_in; ++r) a.in[r] = reg(op.in[r]);
+  a.n_out = op.n_out;
+  for (int o = 0; o < op.n_out; ++o) {
+    a.out[o] = reg(op.out[o]);
+    a.ck[o] = op.ck[o];
+    for (int r = 0; r < MAX_IN; ++r) a.C[o][r] = op.C[o][r];
+  }
+  a.dt = h->scal;
+  return a;
+}
+
+template <typename real>
+int run_limit(dg_handle* h, const void* src, void* dst, cudaStream_t s) {
+  LimitArgs<real> la;
+  la.m = h->md;
+  la.tab64 = h->tab64;
+  la.Uin = static_cast<const real*>(src);
+  la.Uout = static_cast<real*>(dst);
+  la.gamma = h->gamma;
+  la.limiter = h->opt.slope_limiter;
+  la.beta = h->opt.beta;
+  la.Mtilde = h->opt.Mtilde;
+  la.positivity = h->opt.positivity;
+  la.eps = h->opt.eps;
+  la.status = h->status;
+  DG_CUDA(h, timed(h, DG_KERNEL_LIMIT, s, [&] { return h->ks->limit(&la, s); }));
+  return DG_OK;
+}
+
+template <typename real>
+AuxArgs<real> aux_args(dg_handle* h) {
+  AuxArgs<real> a;
+  a.m = h->md;
+  a.tab64 = h->tab64;
+  a.partial = h->partial;
+  a.gamma = h->gamma;
+  a.volume = h->volume;
+  a.dt_bits = h->dt_bits;
+  a.status = h->status;
+  return a;
+}
+
+double dt_factor(const dg_handle* h) {
+  const double base = 1.0 / (2.0 * h->k + 1.0);
+  if (!h->opt.positivity) return h->opt.cfl * base;
+  std::vector<double> lx, lw;
+  const int m = std::max(2, (h->k + 4) / 2);
+  lobatto_rule(m, lx, lw);
+  return h->opt.cfl * std::min(base, 0.5 * lw[0]);
+}
+
+template <typename real>
+int compute_dt_impl(dg_handle* h, const void* W, double* copy, cudaStream_t s) {
+  DG_CUDA(h, cudaMemsetAsync(h->dt_bits, 0x7f, sizeof(unsigned long long), s));
+  AuxArgs<real> a = aux_args<real>(h);
+  a.W = static_cast<const real*>(W);
+  a.dt_factor = dt_factor(h);
+  DG_CUDA(h, timed(h, DG_KERNEL_DT, s, [&] { return h->ks->dt(&a, s); }));
+  DG_CUDA(h, timed(h, DG_KERNEL_OTHER, s, [&] { return launch_dt_finalize(h->dt_bits, h->scal, copy, s); }));
+  return DG_OK;
+}
+
+// one step of the stage program on state W (register 0)
+template <typename real>
+int step_impl(dg_handle* h, const Program& P, void* W, cudaStream_t s) {
+  for (const Op& op : P.ops) {
+    void* U = op.in_reg == 0 ? W : h->regs[op.in_reg - 1];
+    StageArgs<real> a = stage_args<real>(h, op, U, W);
+    DG_CUDA(h, timed(h, DG_KERNEL_FACE, s, [&] { return h->ks->face(&a, s); }));
+    DG_CUDA(h, timed(h, DG_KERNEL_CELL, s, [&] { return h->ks->cell(&a, s); }));
+    if (op.lim_src >= 0) {
+      void* src = op.lim_src == 0 ? W : h->regs[op.lim_src - 1];
+      void* dst = op.lim_dst == 0 ? W : h->regs[op.lim_dst - 1];
+      const int r = run_limit<real>(h, src, dst, s);
+      if (r != DG_OK) return r;
+    }
+  }
+  return DG_OK;
+}
+
+template <typename real>
+int rk_step_any(dg_handle* h, void* W, double dt, double* dt_used, cudaStream_t s) {
+  if (dt > 0.0) {
+    DG_CUDA(h, timed(h, DG_KERNEL_OTHER, s, [&] { return launch_set_scalar(h->scal, dt, s); }));
+    if (dt_used)
+      DG_CUDA(h, timed(h, DG_KERNEL_OTHER, s, [&] { return launch_set_scalar(dt_used, dt, s); }));
+  } else {
+    const int r = compute_dt_impl<real>(h, W, dt_used, s);
+    if (r != DG_OK) return r;
+  }
+  return step_impl<real>(h, h->prog_step, W, s);
+}
+
+int rk_step_dispatch(dg_handle* h, void* W, double dt, double* dt_used, cudaStream_t s) {
+  return h->prec == DG_FP64 ? rk_step_any<double>(h, W, dt, dt_used, s)
+                            : rk_step_any<float>(h, W, dt, dt_used, s);
+}
+
+bool check_handle(const dg_handle* h) { return h != nullptr && h->ks != nullptr; }
+
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+int dg_default_options(dg_options* opt) {
+  if (!opt) return DG_ERR_ARG;
+  opt->rk_order = 3;
+  opt->cfl = 0.2;
+  opt->slope_limiter = DG_LIMITER_NONE;
+  opt->beta = 1.0;
+  opt->Mtilde = 0.5;
+  opt->positivity = 0;
+  opt->eps = 1e-10;
+  opt->precision = DG_FP64;
+  return DG_OK;
+}
+
+const char* dg_last_error(const dg_handle* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+int dg_create(const dg_mesh_desc* mesh, int k, double gamma, const dg_options* opt,
+              dg_handle** out) {
+  if (!out) return fail(nullptr, DG_ERR_ARG, "dg_create: out is NULL");
+  *out = nullptr;
+  if (!mesh) return fail(nullptr, DG_ERR_ARG, "dg_create: mesh is NULL");
+  if (mesh->dim != 2 && mesh->dim != 3) return fail(nullptr, DG_ERR_ARG, "dg_create: dim must be 2 or 3");
+  if (!(gamma > 1.0)) return fail(nullptr, DG_ERR_ARG, "dg_create: gamma must exceed 1");
+  dg_options o;
+  dg_default_options(&o);
+  if (opt) o = *opt;
+  if (o.rk_order < 1 || o.rk_order > 4) return fail(nullptr, DG_ERR_ARG, "dg_create: rk_order must be 1..4");
+  if (o.slope_limiter < 0 || o.slope_limiter > 2) return fail(nullptr, DG_ERR_ARG, "dg_create: bad slope_limiter");
+  if (o.precision != DG_FP64 && o.precision != DG_FP32) return fail(nullptr, DG_ERR_ARG, "dg_create: bad precision");
+  if (!(o.cfl > 0.0)) return fail(nullptr, DG_ERR_ARG, "dg_create: cfl must be positive");
+  const KernelSet* ks = kernel_set(o.precision, mesh->dim, k);
+  if (!ks) return fail(nullptr, DG_ERR_UNSUPPORTED, "dg_create: (dim, k, precision) not compiled");
+  auto* h = new dg_handle();
+  h->dim = mesh->dim;
+  h->k = k;
+  h->prec = o.precision;
+  h->gamma = gamma;
+  h->opt = o;
+  h->ks = ks;
+  h->nv = ks->NV;
+  h->N = ks->N;
+  h->esize = o.precision == DG_FP64 ? 8 : 4;
+  auto bail = [&](int code) {
+    g_create_error = h->err;
+    dg_destroy(h);
+    return code;
+  };
+  int r = build_mesh(h, mesh);
+  if (r != DG_OK) return bail(r);
+  // tables
+  std::vector<double> gx, gw, g3x, g3w, lx, lw, T;
+  gauss_rule(k + 1, gx, gw);
+  gauss_rule(k + 3, g3x, g3w);
+  lobatto_rule(std::max(2, (k + 4) / 2), lx, lw);
+  ks->fill_tables(T, gx, gw, g3x, g3w, lx);
+  void* p = nullptr;
+  if ((r = dalloc(h, T.size() * sizeof(double), &p)) != DG_OK) return bail(r);
+  h->tab64 = static_cast<double*>(p);
+  if (cudaMemcpy(h->tab64, T.data(), T.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+    return bail(cuda_fail(h, cudaGetLastError(), "cudaMemcpy tables"));
+  if (h->prec == DG_FP64) {
+    h->tab = h->tab64;
+  } else {
+    std::vector<float> Tf(T.begin(), T.end());
+    if ((r = dalloc(h, Tf.size() * sizeof(float), &p)) != DG_OK) return bail(r);
+    h->tab = p;
+    if (cudaMemcpy(p, Tf.data(), Tf.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+      return bail(cuda_fail(h, cudaGetLastError(), "cudaMemcpy tables"));
+  }
+  // mesh tables
+  if ((r = upload(h, h->level, &h->md.level)) != DG_OK) return bail(r);
+  if ((r = upload(h, h->coord, &h->md.coord)) != DG_OK) return bail(r);
+  if ((r = upload(h, h->nbr, &h->md.nbr)) != DG_OK) return bail(r);
+  if ((r = upload(h, h->fm, &h->md.fm)) != DG_OK) return bail(r);
+  if ((r = upload(h, h->fp, &h->md.fp)) != DG_OK) return bail(r);
+  if ((r = upload(h, h->finfo, &h->md.finfo)) != DG_OK) return bail(r);
+  if ((r = upload(h, h->sface, &h->md.sface)) != DG_OK) return bail(r);
+  if ((r = upload(h, h->scoarse, &h->md.scoarse)) != DG_OK) return bail(r);
+  if ((r = upload(h, h->node_children, &h->md.node_children)) != DG_OK) return bail(r);
+  // stage programs and scratch
+  std::string perr;
+  const bool limited = (o.slope_limiter != DG_LIMITER_NONE && k > 0) || (o.positivity && k > 0);
+  if (!build_program(o.rk_order, limited, h->prog_step, perr)) return bail(fail(h, DG_ERR_ARG, perr));
+  if (!build_program(o.rk_order, false, h->prog_free, perr)) return bail(fail(h, DG_ERR_ARG, perr));
+  const size_t state_bytes = (size_t)h->nv * h->N * h->ncells * h->esize;
+  const int nregs = std::max(h->prog_step.n_phys, h->prog_free.n_phys) + 1;
+  for (int i = 0; i < nregs; ++i) {
+    if ((r = dalloc(h, state_bytes, &p)) != DG_OK) return bail(r);
+    h->regs.push_back(p);
+  }
+  if ((r = dalloc(h, (size_t)h->nv * ks->QF * std::max(h->nfaces, 1) * h->esize, &h->F)) != DG_OK)
+    return bail(r);
+  if ((r = dalloc(h, 8 * sizeof(double), &p)) != DG_OK) return bail(r);
+  h->scal = static_cast<double*>(p);
+  if ((r = dalloc(h, sizeof(unsigned long long), &p)) != DG_OK) return bail(r);
+  h->dt_bits = static_cast<unsigned long long*>(p);
+  const int nblk = (h->ncells + 255) / 256 + 1;
+  if ((r = dalloc(h, (size_t)nblk * 8 * sizeof(double), &p)) != DG_OK) return bail(r);
+  h->partial = static_cast<double*>(p);
+  if ((r = dalloc(h, sizeof(int), &p)) != DG_OK) return bail(r);
+  h->status = static_cast<int*>(p);
+  if (cudaMemset(h->status, 0, sizeof(int)) != cudaSuccess)
+    return bail(cuda_fail(h, cudaGetLastError(), "cudaMemset"));
+  if (ks->prepare() != cudaSuccess) return bail(cuda_fail(h, cudaGetLastError(), "kernel attributes"));
+  if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return bail(cuda_fail(h, cudaGetLastError(), "cudaStreamCreate"));
+  *out = h;
+  return DG_OK;
+}
+
+int dg_destroy(dg_handle* h) {
+  if (!h) return DG_OK;
+  cudaDeviceSynchronize();
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+  for (auto e : h->ev_pool) cudaEventDestroy(e);
+  for (auto g : h->graph_defs) cudaGraphDestroy(g);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  for (void* p : h->allocs) cudaFree(p);
+  delete h;
+  return DG_OK;
+}
+
+int dg_sizes(const dg_handle* h, int64_t* n_cells, int* n_basis, int* n_vars, int* n_qpoints,
+             int* n_l1points, int* n_nodes) {
+  if (!check_handle(h)) return DG_ERR_ARG;
+  if (n_cells) *n_cells = h->ncells;
+  if (n_basis) *n_basis = h->N;
+  if (n_vars) *n_vars = h->nv;
+  if (n_qpoints) *n_qpoints = h->ks->Q;
+  if (n_l1points) *n_l1points = h->ks->Q1;
+  if (n_nodes) *n_nodes = h->nnodes;
+  return DG_OK;
+}
+
+static int points_impl(const dg_handle* hc, double* xyz, int l1, void* stream) {
+  dg_handle* h = const_cast<dg_handle*>(hc);
+  if (!check_handle(h) || !xyz) return DG_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (h->prec == DG_FP64) {
+    AuxArgs<double> a = aux_args<double>(h);
+    a.out = xyz;
+    DG_CUDA(h, h->ks->points(&a, l1, s));
+  } else {
+    AuxArgs<float> a = aux_args<float>(h);
+    a.out = xyz;
+    DG_CUDA(h, h->ks->points(&a, l1, s));
+  }
+  return DG_OK;
+}
+
+int dg_quad_points(const dg_handle* h, double* xyz_dev, void* stream) {
+  return points_impl(h, xyz_dev, 0, stream);
+}
+int dg_l1_points(const dg_handle* h, double* xyz_dev, void* stream) {
+  return points_impl(h, xyz_dev, 1, stream);
+}
+
+int dg_project(dg_handle* h, const double* u_dev, void* W_dev, void* stream) {
+  if (!check_handle(h) || !u_dev || !W_dev) return DG_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (h->prec == DG_FP64) {
+    AuxArgs<double> a = aux_args<double>(h);
+    a.u = u_dev;
+    a.Wout = static_cast<double*>(W_dev);
+    DG_CUDA(h, h->ks->project(&a, s));
+  } else {
+    AuxArgs<float> a = aux_args<float>(h);
+    a.u = u_dev;
+    a.Wout = static_cast<float*>(W_dev);
+    DG_CUDA(h, h->ks->project(&a, s));
+  }
+  return DG_OK;
+}
+
+int dg_rhs(dg_handle* h, const void* W_dev, void* dWdt_dev, void* stream) {
+  if (!check_handle(h) || !W_dev || !dWdt_dev) return DG_ERR_ARG;
+  if (W_dev == dWdt_dev) return fail(h, DG_ERR_ARG, "dg_rhs: W and dWdt alias");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Op op;
+  op.n_in = 0;
+  op.n_out = 1;
+  op.ck[0] = 1.0;
+  if (h->prec == DG_FP64) {
+    StageArgs<double> a = stage_args<double>(h, op, W_dev, nullptr);
+    a.out[0] = static_cast<double*>(dWdt_dev);
+    a.dt = nullptr;
+    DG_CUDA(h, h->ks->face(&a, s));
+    DG_CUDA(h, h->ks->cell(&a, s));
+  } else {
+    StageArgs<float> a = stage_args<float>(h, op, W_dev, nullptr);
+    a.out[0] = static_cast<float*>(dWdt_dev);
+    a.dt = nullptr;
+    DG_CUDA(h, h->ks->face(&a, s));
+    DG_CUDA(h, h->ks->cell(&a, s));
+  }
+  return DG_OK;
+}
+
+int dg_compute_dt(dg_handle* h, const void* W_dev, double* dt_dev, void* stream) {
+  if (!check_handle(h) || !W_dev || !dt_dev) return DG_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return h->prec == DG_FP64 ? compute_dt_impl<double>(h, W_dev, dt_dev, s)
+                            : compute_dt_impl<float>(h, W_dev, dt_dev, s);
+}
+
+int dg_rk_step(dg_handle* h, void* W_dev, double dt, double* dt_used_dev, void* stream) {
+  if (!check_handle(h) || !W_dev) return DG_ERR_ARG;
+  std::lock_guard<std::mutex> lock(h->mu);
+  return rk_step_dispatch(h, W_dev, dt, dt_used_dev, static_cast<cudaStream_t>(stream));
+}
+
+int dg_advance(dg_handle* h, void* W_dev, int n_steps, double* dt_hist_dev, void* stream) {
+  if (!check_handle(h) || !W_dev || n_steps < 0) return DG_ERR_ARG;
+  if (n_steps == 0) return DG_OK;
+  std::lock_guard<std::mutex> lock(h->mu);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  auto key = std::make_tuple(W_dev, n_steps, (void*)dt_hist_dev);
+  auto it = h->graphs.find(key);
+  if (it == h->graphs.end()) {
+    const bool prof = h->profiling;
+    h->profiling = false;  // no event records inside a captured graph
+    cudaError_t eb = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (eb != cudaSuccess) { h->profiling = prof; return cuda_fail(h, eb, "cudaStreamBeginCapture"); }
+    int r = DG_OK;
+    for (int i = 0; i < n_steps && r == DG_OK; ++i)
+      r = rk_step_dispatch(h, W_dev, 0.0, dt_hist_dev ? dt_hist_dev + i : nullptr, h->cap_stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+    h->profiling = prof;
+    if (r != DG_OK) { if (g) cudaGraphDestroy(g); return r; }
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+    cudaGraphExec_t ge = nullptr;
+    e = cudaGraphInstantiate(&ge, g, 0);
+    if (e != cudaSuccess) { cudaGraphDestroy(g); return cuda_fail(h, e, "cudaGraphInstantiate"); }
+    h->graph_defs.push_back(g);
+    it = h->graphs.emplace(key, ge).first;
+  }
+  DG_CUDA(h, cudaGraphLaunch(it->second, s));
+  return DG_OK;
+}
+
+int dg_rk_step_adjoint(dg_handle* h, const void* W_n_dev, double dt, const void* lam_np1_dev,
+                       void* lam_n_dev, void* stream) {
+  (void)W_n_dev; (void)dt; (void)lam_np1_dev; (void)lam_n_dev; (void)stream;
+  if (!check_handle(h)) return DG_ERR_ARG;
+  return fail(h, DG_ERR_UNSUPPORTED, "dg_rk_step_adjoint: not available in this build");
+}
+
+int dg_limit(dg_handle* h, void* W_dev, void* stream) {
+  if (!check_handle(h) || !W_dev) return DG_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t bytes = (size_t)h->nv * h->N * h->ncells * h->esize;
+  void* tmp = h->regs.back();
+  DG_CUDA(h, cudaMemcpyAsync(tmp, W_dev, bytes, cudaMemcpyDeviceToDevice, s));
+  return h->prec == DG_FP64 ? run_limit<double>(h, tmp, W_dev, s) : run_limit<float>(h, tmp, W_dev, s);
+}
+
+int dg_totals(dg_handle* h, const void* W_dev, double* totals_dev, void* stream) {
+  if (!check_handle(h) || !W_dev || !totals_dev) return DG_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (h->prec == DG_FP64) {
+    AuxArgs<double> a = aux_args<double>(h);
+    a.W = static_cast<const double*>(W_dev);
+    a.out = totals_dev;
+    DG_CUDA(h, h->ks->totals(&a, s));
+  } else {
+    AuxArgs<float> a = aux_args<float>(h);
+    a.W = static_cast<const float*>(W_dev);
+    a.out = totals_dev;
+    DG_CUDA(h, h->ks->totals(&a, s));
+  }
+  return DG_OK;
+}
+
+int dg_l1_density(dg_handle* h, const void* W_dev, const double* rho_ref_dev, double* out_dev,
+                  void* stream) {
+  if (!check_handle(h) || !W_dev || !rho_ref_dev || !out_dev) return DG_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (h->prec == DG_FP64) {
+    AuxArgs<double> a = aux_args<double>(h);
+    a.W = static_cast<const double*>(W_dev);
+    a.u = rho_ref_dev;
+    a.out = out_dev;
+    DG_CUDA(h, h->ks->l1(&a, s));
+  } else {
+    AuxArgs<float> a = aux_args<float>(h);
+    a.W = static_cast<const float*>(W_dev);
+    a.u = rho_ref_dev;
+    a.out = out_dev;
+    DG_CUDA(h, h->ks->l1(&a, s));
+  }
+  return DG_OK;
+}
+
+int dg_node_weights(dg_handle* h, const void* W_dev, void* Wnode_dev, void* stream) {
+  if (!check_handle(h) || !W_dev || !Wnode_dev) return DG_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (h->prec == DG_FP64) {
+    AuxArgs<double> a = aux_args<double>(h);
+    a.W = static_cast<const double*>(W_dev);
+    a.Wout = static_cast<double*>(Wnode_dev);
+    DG_CUDA(h, h->ks->node_weights(&a, s));
+  } else {
+    AuxArgs<float> a = aux_args<float>(h);
+    a.W = static_cast<const float*>(W_dev);
+    a.Wout = static_cast<float*>(Wnode_dev);
+    DG_CUDA(h, h->ks->node_weights(&a, s));
+  }
+  return DG_OK;
+}
+
+int dg_neighbor_table(const dg_handle* h, int32_t* host_out) {
+  if (!check_handle(h) || !host_out) return DG_ERR_ARG;
+  std::memcpy(host_out, h->nbr.data(), h->nbr.size() * sizeof(int32_t));
+  return DG_OK;
+}
+
+int dg_cell_levels(const dg_handle* h, int32_t* host_out) {
+  if (!check_handle(h) || !host_out) return DG_ERR_ARG;
+  for (int c = 0; c < h->ncells; ++c) host_out[c] = h->level[c];
+  return DG_OK;
+}
+
+int dg_profile_begin(dg_handle* h) {
+  if (!check_handle(h)) return DG_ERR_ARG;
+  h->profiling = true;
+  h->ev_used = 0;
+  h->ev_marks.clear();
+  return DG_OK;
+}
+
+int dg_profile_end(dg_handle* h, int* launches, double* total_ms, int n_kinds) {
+  if (!check_handle(h) || n_kinds < 0 || (n_kinds > 0 && (!launches || !total_ms))) return DG_ERR_ARG;
+  h->profiling = false;
+  for (int i = 0; i < n_kinds; ++i) { launches[i] = 0; total_ms[i] = 0.0; }
+  for (const auto& mk : h->ev_marks) {
+    DG_CUDA(h, cudaEventSynchronize(h->ev_pool[mk.second + 1]));
+    float ms = 0.0f;
+    DG_CUDA(h, cudaEventElapsedTime(&ms, h->ev_pool[mk.second], h->ev_pool[mk.second + 1]));
+    if (mk.first < n_kinds) {
+      launches[mk.first] += 1;
+      total_ms[mk.first] += ms;
+    }
+  }
+  h->ev_marks.clear();
+  h->ev_used = 0;
+  return DG_OK;
+}
+
+int dg_status(dg_handle* h, int* device_status_host) {
+  if (!check_handle(h) || !device_status_host) return DG_ERR_ARG;
+  int bits = 0;
+  DG_CUDA(h, cudaMemcpy(&bits, h->status, sizeof(int), cudaMemcpyDeviceToHost));
+  DG_CUDA(h, cudaMemset(h->status, 0, sizeof(int)));
+  int code = DG_OK;
+  if (bits & (1 << DG_ERR_NONPHYSICAL_BIT)) code = DG_ERR_NONPHYSICAL;
+  else if (bits & (1 << DG_ERR_TIMEOUT_BIT)) code = DG_ERR_TIMEOUT;
+  *device_status_host = code;
+  return DG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,23 @@
+// Kernel instantiations for dim = 3, k = 0..2, FP64 and FP32.
+#include "dg_kernels.cuh"
+
+namespace dgi {
+
+bool kernel_set_3d(int prec, int k, KernelSet* out) {
+  if (prec == 0) {
+    switch (k) {
+      case 0: *out = make_kernel_set<double, 3, 0>(0); return true;
+      case 1: *out = make_kernel_set<double, 3, 1>(0); return true;
+      case 2: *out = make_kernel_set<double, 3, 2>(0); return true;
+    }
+  } else {
+    switch (k) {
+      case 0: *out = make_kernel_set<float, 3, 0>(1); return true;
+      case 1: *out = make_kernel_set<float, 3, 1>(1); return true;
+      case 2: *out = make_kernel_set<float, 3, 2>(1); return true;
+    }
+  }
+  return false;
+}
+
+}  // namespace dgi

@@ -1,0 +1,161 @@
+// Internal interfaces of libdg: device-side table layouts, kernel argument
+// blocks and the per-(precision, dim, k) kernel set.  Not part of the ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+namespace dgi {
+
+// ---------------------------------------------------------------------------
+// Compile-time sizes of a (dim, k) scheme.
+template <int DIM, int K>
+struct Shape {
+  static constexpr int N = DIM == 2 ? (K + 1) * (K + 2) / 2 : (K + 1) * (K + 2) * (K + 3) / 6;
+  static constexpr int NV = DIM + 2;
+  static constexpr int K1 = K + 1;
+  static constexpr int Q = DIM == 2 ? K1 * K1 : K1 * K1 * K1;          // volume points
+  static constexpr int QF = DIM == 2 ? K1 : K1 * K1;                   // face points
+  static constexpr int K3 = K + 3;
+  static constexpr int Q1 = DIM == 2 ? K3 * K3 : K3 * K3 * K3;         // L1-error points
+  static constexpr int NSIDE = 2 * DIM;
+  static constexpr int NSUB = 1 << (DIM - 1);                          // sub-faces of a face
+  static constexpr int NVAR = 1 + NSUB;                                // face point variants
+  static constexpr int NCH = 1 << DIM;                                 // children of a node
+  static constexpr int M = (K + 4) / 2 < 2 ? 2 : (K + 4) / 2;          // Lobatto points, m >= (k+3)/2
+  static constexpr int MF = DIM == 2 ? M : M * K1;                     // points of one S_a per ... (unused)
+  static constexpr int NSP = DIM * M * QF;                             // |S| (eq. union_quad_points)
+  // offsets into the per-handle table (elements)
+  static constexpr int OFF_PHI = 0;                                    // [Q][N]     phi_l(xi_q)
+  static constexpr int OFF_DPHIW = OFF_PHI + Q * N;                    // [DIM][Q][N] dphi_l/dxi_a * w_q
+  static constexpr int OFF_PHIF = OFF_DPHIW + DIM * Q * N;             // [NSIDE][NVAR][QF][N] phi at face points
+  static constexpr int OFF_PHIFW = OFF_PHIF + NSIDE * NVAR * QF * N;   // same, * w_q (* 2^-(d-1) for sub-faces)
+  static constexpr int OFF_PREF = OFF_PHIFW + NSIDE * NVAR * QF * N;   // [NCH][N][N] refinement matrices (j,l)
+  static constexpr int OFF_PROJ = OFF_PREF + NCH * N * N;              // [Q][N] phi * w_q * 2^-d
+  static constexpr int OFF_SPHI = OFF_PROJ + Q * N;                    // [NSP][N] phi at the set S
+  static constexpr int OFF_L1PHI = OFF_SPHI + NSP * N;                 // [Q1][N]  phi at L1 points
+  static constexpr int OFF_L1W = OFF_L1PHI + Q1 * N;                   // [Q1]     L1 weights
+  static constexpr int OFF_XI = OFF_L1W + Q1;                          // [Q][3]   volume points
+  static constexpr int OFF_XI1 = OFF_XI + Q * 3;                       // [Q1][3]  L1 points
+  static constexpr int OFF_DEG = OFF_XI1 + Q1 * 3;                     // [N]      degree of phi_l
+  static constexpr int TAB_SIZE = OFF_DEG + N;
+};
+
+// ---------------------------------------------------------------------------
+// Device mesh tables (all arrays owned by the handle).
+struct MeshDev {
+  int ncells = 0, nfaces = 0, nnodes = 0;
+  double dx0 = 1.0;            // base edge length
+  double lo[3] = {0, 0, 0};
+  int n[3] = {1, 1, 1};
+  const int8_t* level = nullptr;         // [ncells]
+  const int32_t* coord = nullptr;        // [3][ncells] integer position at the cell's level
+  const int32_t* nbr = nullptr;          // [2*dim][ncells]
+  const int32_t* fm = nullptr;           // [nfaces] minus-side cell, -1 = mirror of the plus side
+  const int32_t* fp = nullptr;           // [nfaces] plus-side cell, -1 = mirror of the minus side
+  const uint8_t* finfo = nullptr;        // [nfaces] dir | vm << 2 | vp << 5
+  const int32_t* sface = nullptr;        // [2*dim][ncells] first face entry of each side
+  const uint8_t* scoarse = nullptr;      // [ncells] bit s: side s holds NSUB sub-face entries
+  const int32_t* node_children = nullptr;// [nnodes][2^dim]
+};
+
+// bits of the device status word
+constexpr int DG_ERR_NONPHYSICAL_BIT = 4;
+constexpr int DG_ERR_TIMEOUT_BIT = 5;
+
+constexpr int MAX_IN = 4;
+constexpr int MAX_OUT = 3;
+
+// One stage: face fluxes of U, then per cell
+//   out_o = sum_r C[o][r] in_r + ck[o] * dt * dWdt(U)
+template <typename real>
+struct StageArgs {
+  MeshDev m;
+  const real* tab = nullptr;
+  const real* U = nullptr;
+  real* F = nullptr;            // face fluxes [NV][QF][nfaces]
+  double gamma = 1.4;
+  int n_in = 0, n_out = 0;
+  const real* in[MAX_IN] = {nullptr, nullptr, nullptr, nullptr};
+  real* out[MAX_OUT] = {nullptr, nullptr, nullptr};
+  double C[MAX_OUT][MAX_IN] = {};
+  double ck[MAX_OUT] = {};
+  const double* dt = nullptr;   // device scalar; nullptr means dt = 1
+};
+
+template <typename real>
+struct LimitArgs {
+  MeshDev m;
+  const double* tab64 = nullptr;  // FP64 tables (same layout)
+  const real* Uin = nullptr;
+  real* Uout = nullptr;
+  double gamma = 1.4;
+  int limiter = 0;
+  double beta = 1.0, Mtilde = 0.5;
+  int positivity = 0;
+  double eps = 1e-10;
+  int* status = nullptr;
+};
+
+template <typename real>
+struct AuxArgs {
+  MeshDev m;
+  const double* tab64 = nullptr;
+  const real* W = nullptr;
+  real* Wout = nullptr;
+  const double* u = nullptr;      // point values (projection) / reference density (L1)
+  double* out = nullptr;          // coordinates / reduction results
+  double* partial = nullptr;      // reduction partials
+  int nblocks = 0;
+  double gamma = 1.4;
+  double dt_factor = 1.0;         // CFL factor of the timestep formula
+  double volume = 1.0;            // domain volume (L1)
+  unsigned long long* dt_bits = nullptr;
+  int* status = nullptr;
+};
+
+// Adjoint of one stage: given the stage state U and a cotangent G on dWdt(U),
+// accumulate lam += J(U)^T G into the 'acc' array (same layout as W).
+template <typename real>
+struct AdjointArgs {
+  MeshDev m;
+  const real* tab = nullptr;
+  const real* U = nullptr;
+  const real* G = nullptr;       // cotangent of dW/dt (layout of W)
+  real* FG = nullptr;            // face work buffer: cotangents of face fluxes [NV][QF][nfaces]
+  real* acc = nullptr;           // output accumulator
+  double gamma = 1.4;
+  double scale = 1.0;            // acc += scale * J^T G
+};
+
+// Kernel set of one (precision, dim, k).
+struct KernelSet {
+  int dim = 0, k = 0, prec = 0;
+  int N = 0, NV = 0, Q = 0, QF = 0, Q1 = 0, NSUB = 0, NSP = 0, M = 0, tab_size = 0;
+  // host: fill the table (double) from 1D Gauss and Lobatto rules
+  void (*fill_tables)(std::vector<double>& tab, const std::vector<double>& gx,
+                      const std::vector<double>& gw, const std::vector<double>& g3x,
+                      const std::vector<double>& g3w, const std::vector<double>& lx) = nullptr;
+  cudaError_t (*prepare)() = nullptr;  // one-time kernel attributes (not capturable)
+  cudaError_t (*face)(const void* stage_args, cudaStream_t s) = nullptr;
+  cudaError_t (*cell)(const void* stage_args, cudaStream_t s) = nullptr;
+  cudaError_t (*limit)(const void* limit_args, cudaStream_t s) = nullptr;
+  cudaError_t (*project)(const void* aux, cudaStream_t s) = nullptr;
+  cudaError_t (*points)(const void* aux, int l1rule, cudaStream_t s) = nullptr;
+  cudaError_t (*dt)(const void* aux, cudaStream_t s) = nullptr;
+  cudaError_t (*totals)(const void* aux, cudaStream_t s) = nullptr;
+  cudaError_t (*l1)(const void* aux, cudaStream_t s) = nullptr;
+  cudaError_t (*node_weights)(const void* aux, cudaStream_t s) = nullptr;
+  cudaError_t (*adj_face)(const void* adj_args, cudaStream_t s) = nullptr;
+  cudaError_t (*adj_cell)(const void* adj_args, cudaStream_t s) = nullptr;
+};
+
+const KernelSet* kernel_set(int prec, int dim, int k);
+
+// shared helper kernels (dg_common.cu)
+cudaError_t launch_set_scalar(double* dst, double value, cudaStream_t s);
+cudaError_t launch_dt_finalize(const unsigned long long* bits, double* dt, double* dt_copy,
+                               cudaStream_t s);
+
+}  // namespace dgi

@@ -1,0 +1,842 @@
+// sm_103a kernels of the DG right-hand side and RK stage (paper Sec. 2.4,
+// eqs. dg_term2 / dg_term3 / spatial_discretisation; Appendix D), the slope
+// and positivity limiters (Secs. 3.2-3.4, 4.4), the timestep (Sec. 2.5), and
+// the projection / reduction helpers.  Templated on the arithmetic type and
+// on (DIM, K) so that every loop over basis functions and quadrature points
+// is unrolled at compile time.
+//
+// Layout: state W[var][coef][cell] (cell fastest, so a warp reading 32
+// consecutive cells of one coefficient row issues one coalesced request);
+// face fluxes F[var][face point][face]; all tables in a per-handle buffer
+// (see Shape<> for offsets).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <vector>
+
+#include "dg_internal.h"
+#include "dg_physics.cuh"
+
+namespace dgi {
+
+// ===========================================================================
+// Host: tables (basis values at the quadrature points, Appendices A-C)
+
+inline void host_legendre(int n, double x, double* P, double* dP) {
+  // P_{m+1} = ((2m+1) x P_m - m P_{m-1}) / (m+1);  P'_{m+1} = (m+1) P_m + x P'_m
+  P[0] = 1.0;
+  dP[0] = 0.0;
+  for (int m = 0; m < n; ++m) {
+    P[m + 1] = (m == 0) ? x : ((2.0 * m + 1.0) * x * P[m] - m * P[m - 1]) / (m + 1.0);
+    dP[m + 1] = (m + 1.0) * P[m] + x * dP[m];
+  }
+}
+
+template <int DIM, int K>
+struct HostBasis {
+  using S = Shape<DIM, K>;
+  int e[S::N][3];
+  HostBasis() {
+    int n = 0;
+    for (int g = 0; g <= K; ++g) {
+      if (DIM == 2) {
+        for (int nx = g; nx >= 0; --nx) { e[n][0] = nx; e[n][1] = g - nx; e[n][2] = 0; ++n; }
+      } else {
+        for (int nx = g; nx >= 0; --nx)
+          for (int ny = g - nx; ny >= 0; --ny) {
+            e[n][0] = nx; e[n][1] = ny; e[n][2] = g - nx - ny; ++n;
+          }
+      }
+    }
+  }
+  // scaled Legendre sqrt(2n+1) P_n and its derivative
+  static void sl(int n, double x, double& v, double& d) {
+    double P[16], dP[16];
+    host_legendre(n, x, P, dP);
+    const double s = std::sqrt(2.0 * n + 1.0);
+    v = s * P[n];
+    d = s * dP[n];
+  }
+  double phi(int l, const double* xi) const {
+    double r = 1.0;
+    for (int a = 0; a < DIM; ++a) {
+      double v, d;
+      sl(e[l][a], xi[a], v, d);
+      r *= v;
+    }
+    return r;
+  }
+  double dphi(int l, int a, const double* xi) const {
+    double r = 1.0;
+    for (int b = 0; b < DIM; ++b) {
+      double v, d;
+      sl(e[l][b], xi[b], v, d);
+      r *= (b == a) ? d : v;
+    }
+    return r;
+  }
+  int degree(int l) const { return e[l][0] + e[l][1] + e[l][2]; }
+};
+
+// point q of face (dir, s) in the cell frame; variant 0 = whole face,
+// 1 + quad = the sub-face 'quad' (bit i = upper half along tangential axis i)
+template <int DIM, int K>
+inline void face_point(int dir, int s, int variant, int q, const std::vector<double>& gx,
+                       double* xi, double* w, const std::vector<double>& gw) {
+  xi[0] = xi[1] = xi[2] = 0.0;
+  xi[dir] = s ? 1.0 : -1.0;
+  *w = 1.0;
+  int t = 0, qq = q;
+  for (int b = 0; b < DIM; ++b) {
+    if (b == dir) continue;
+    const int i = qq % (K + 1);
+    qq /= (K + 1);
+    double eta = gx[i];
+    if (variant > 0) eta = 0.5 * (eta + (((variant - 1) >> t) & 1 ? 1.0 : -1.0));
+    xi[b] = eta;
+    *w *= gw[i];
+    ++t;
+  }
+}
+
+template <int DIM, int K>
+void fill_tables(std::vector<double>& T, const std::vector<double>& gx,
+                 const std::vector<double>& gw, const std::vector<double>& g3x,
+                 const std::vector<double>& g3w, const std::vector<double>& lx) {
+  using S = Shape<DIM, K>;
+  HostBasis<DIM, K> B;
+  T.assign(S::TAB_SIZE, 0.0);
+  const double two_d = std::ldexp(1.0, DIM);
+  // volume rule, x fastest
+  for (int q = 0; q < S::Q; ++q) {
+    double xi[3] = {0, 0, 0}, w = 1.0;
+    int qq = q;
+    for (int a = 0; a < DIM; ++a) {
+      xi[a] = gx[qq % S::K1];
+      w *= gw[qq % S::K1];
+      qq /= S::K1;
+    }
+    for (int a = 0; a < 3; ++a) T[S::OFF_XI + q * 3 + a] = xi[a];
+    for (int l = 0; l < S::N; ++l) {
+      T[S::OFF_PHI + q * S::N + l] = B.phi(l, xi);
+      T[S::OFF_PROJ + q * S::N + l] = B.phi(l, xi) * w / two_d;
+      for (int a = 0; a < DIM; ++a) T[S::OFF_DPHIW + (a * S::Q + q) * S::N + l] = B.dphi(l, a, xi) * w;
+    }
+  }
+  // faces
+  const double sub_w = std::ldexp(1.0, -(DIM - 1));
+  for (int side = 0; side < S::NSIDE; ++side)
+    for (int var = 0; var < S::NVAR; ++var)
+      for (int q = 0; q < S::QF; ++q) {
+        double xi[3], w;
+        face_point<DIM, K>(side >> 1, side & 1, var, q, gx, xi, &w, gw);
+        for (int l = 0; l < S::N; ++l) {
+          const int idx = ((side * S::NVAR + var) * S::QF + q) * S::N + l;
+          T[S::OFF_PHIF + idx] = B.phi(l, xi);
+          T[S::OFF_PHIFW + idx] = B.phi(l, xi) * w * (var > 0 ? sub_w : 1.0);
+        }
+      }
+  // refinement matrices (P_c)_{j,l} = 2^-d int phi_j(eta) phi_l((eta + o_c)/2) d eta
+  for (int ch = 0; ch < S::NCH; ++ch)
+    for (int q = 0; q < S::Q; ++q) {
+      const double* eta = &T[S::OFF_XI + q * 3];
+      double w = 1.0;
+      int qq = q;
+      for (int a = 0; a < DIM; ++a) { w *= gw[qq % S::K1]; qq /= S::K1; }
+      double xc[3] = {0, 0, 0};
+      for (int a = 0; a < DIM; ++a) xc[a] = 0.5 * (eta[a] + (((ch >> a) & 1) ? 1.0 : -1.0));
+      for (int j = 0; j < S::N; ++j)
+        for (int l = 0; l < S::N; ++l)
+          T[S::OFF_PREF + (ch * S::N + j) * S::N + l] += B.phi(j, eta) * B.phi(l, xc) * w / two_d;
+    }
+  // positivity set S: Lobatto along axis a, Gauss along the others
+  for (int a = 0; a < DIM; ++a)
+    for (int r = 0; r < S::M; ++r)
+      for (int tq = 0; tq < S::QF; ++tq) {
+        double xi[3] = {0, 0, 0};
+        xi[a] = lx[r];
+        int qq = tq;
+        for (int b = 0; b < DIM; ++b) {
+          if (b == a) continue;
+          xi[b] = gx[qq % S::K1];
+          qq /= S::K1;
+        }
+        const int i = (a * S::M + r) * S::QF + tq;
+        for (int l = 0; l < S::N; ++l) T[S::OFF_SPHI + i * S::N + l] = B.phi(l, xi);
+      }
+  // (k+3)^d rule for the L1 error
+  for (int q = 0; q < S::Q1; ++q) {
+    double xi[3] = {0, 0, 0}, w = 1.0;
+    int qq = q;
+    for (int a = 0; a < DIM; ++a) {
+      xi[a] = g3x[qq % S::K3];
+      w *= g3w[qq % S::K3];
+      qq /= S::K3;
+    }
+    for (int a = 0; a < 3; ++a) T[S::OFF_XI1 + q * 3 + a] = xi[a];
+    T[S::OFF_L1W + q] = w;
+    for (int l = 0; l < S::N; ++l) T[S::OFF_L1PHI + q * S::N + l] = B.phi(l, xi);
+  }
+  for (int l = 0; l < S::N; ++l) T[S::OFF_DEG + l] = B.degree(l);
+}
+
+// ===========================================================================
+// Device helpers
+
+template <typename real>
+__device__ __forceinline__ real ld(const real* p) { return __ldg(p); }
+
+__device__ __forceinline__ double cell_dx(const MeshDev& m, int c) {
+  return ldexp(m.dx0, -(int)m.level[c]);
+}
+
+// ===========================================================================
+// Face fluxes: one thread per (face, face point).  Traces of both sides at
+// the point (eq. solution_representation), HLLC, stored once per face and
+// shared by both cells (conservative by construction).
+
+template <int QF>
+struct FaceBlock {
+  static constexpr int FB = (256 / QF) < 32 ? 32 : ((256 / QF) / 32) * 32;
+};
+
+template <typename real, int DIM, int K>
+__global__ void __launch_bounds__(FaceBlock<Shape<DIM, K>::QF>::FB * Shape<DIM, K>::QF)
+    face_flux_kernel(const StageArgs<real> a) {
+  using S = Shape<DIM, K>;
+  constexpr int FB = FaceBlock<S::QF>::FB;
+  const int q = threadIdx.y;
+  const int f = blockIdx.x * FB + threadIdx.x;
+  const int nf = a.m.nfaces;
+  if (f >= nf) return;
+  const int nc = a.m.ncells;
+  const unsigned info = a.m.finfo[f];
+  const int dir = info & 3, vm = (info >> 2) & 7, vp = (info >> 5) & 7;
+  const int cm = a.m.fm[f], cp = a.m.fp[f];
+  real uL[S::NV], uR[S::NV];
+  if (cm >= 0) {
+    const real* ph = a.tab + S::OFF_PHIF + (((2 * dir + 1) * S::NVAR + vm) * S::QF + q) * S::N;
+#pragma unroll
+    for (int v = 0; v < S::NV; ++v) {
+      real s = real(0);
+#pragma unroll
+      for (int l = 0; l < S::N; ++l) s += ld(a.U + (size_t)(v * S::N + l) * nc + cm) * ld(ph + l);
+      uL[v] = s;
+    }
+  }
+  if (cp >= 0) {
+    const real* ph = a.tab + S::OFF_PHIF + (((2 * dir + 0) * S::NVAR + vp) * S::QF + q) * S::N;
+#pragma unroll
+    for (int v = 0; v < S::NV; ++v) {
+      real s = real(0);
+#pragma unroll
+      for (int l = 0; l < S::N; ++l) s += ld(a.U + (size_t)(v * S::N + l) * nc + cp) * ld(ph + l);
+      uR[v] = s;
+    }
+  }
+  if (cm < 0) {
+#pragma unroll
+    for (int v = 0; v < S::NV; ++v) uL[v] = uR[v];
+  }
+  if (cp < 0) {
+#pragma unroll
+    for (int v = 0; v < S::NV; ++v) uR[v] = uL[v];
+  }
+  real Fl[S::NV];
+  hllc_flux<real, DIM>(uL, uR, dir, real(a.gamma), Fl);
+#pragma unroll
+  for (int v = 0; v < S::NV; ++v) a.F[((size_t)v * S::QF + q) * nf + f] = Fl[v];
+}
+
+// ===========================================================================
+// Cell kernel: a tile of TC cells per block, P threads per cell.
+//   1. stage the tile's weights in shared memory (coalesced row loads);
+//   2. at every volume Gauss point: u_q = sum_l w_l phi_l(xi_q) and the
+//      Euler fluxes f_a(u_q) -> shared memory;
+//   3. per output (var, j): volume integral sum_a sum_q f_a dphi_j w_q,
+//      minus the surface integral of the stored face fluxes, times
+//      2^(1-d)/dx (eq. spatial_discretisation);
+//   4. epilogue: out_o = sum_r C[o][r] in_r + ck[o] dt dWdt.
+
+template <typename real, int DIM, int K>
+struct CellTile {
+  using S = Shape<DIM, K>;
+  static constexpr int TC = 32;
+  static constexpr int P = (S::N * S::NV >= 32) ? 4 : 2;
+  static constexpr int THREADS = TC * P;
+  static constexpr size_t SMEM = (size_t)(S::NV * S::N + DIM * S::NV * S::Q) * TC * sizeof(real);
+};
+
+template <typename real, int DIM, int K>
+__global__ void __launch_bounds__(CellTile<real, DIM, K>::THREADS)
+    cell_update_kernel(const StageArgs<real> a) {
+  using S = Shape<DIM, K>;
+  using T = CellTile<real, DIM, K>;
+  constexpr int TC = T::TC, P = T::P;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  real* sW = reinterpret_cast<real*>(smem_raw);  // [NV*N][TC]
+  real* sF = sW + S::NV * S::N * TC;             // [DIM][NV][Q][TC]
+  const int tc = threadIdx.x % TC, p = threadIdx.x / TC;
+  const int nc = a.m.ncells;
+  const int c = blockIdx.x * TC + tc;
+  const bool valid = c < nc;
+
+  for (int i = p; i < S::NV * S::N; i += P)
+    sW[i * TC + tc] = valid ? a.U[(size_t)i * nc + c] : (i == 0 ? real(1) : real(0));
+  __syncthreads();
+
+  const real g1 = real(a.gamma) - real(1);
+  const real* phi = a.tab + S::OFF_PHI;
+  for (int q = p; q < S::Q; q += P) {
+    real u[S::NV];
+#pragma unroll
+    for (int v = 0; v < S::NV; ++v) {
+      real s = real(0);
+#pragma unroll
+      for (int l = 0; l < S::N; ++l) s += sW[(v * S::N + l) * TC + tc] * ld(phi + q * S::N + l);
+      u[v] = s;
+    }
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      real f[S::NV];
+      euler_flux<real, DIM>(u, d, g1, f);
+#pragma unroll
+      for (int v = 0; v < S::NV; ++v) sF[((d * S::NV + v) * S::Q + q) * TC + tc] = f[v];
+    }
+  }
+  __syncthreads();
+  if (!valid) return;
+
+  const real pre = real(ldexp(1.0, 1 - DIM) / cell_dx(a.m, c));
+  const real dtv = a.dt ? real(*a.dt) : real(1);
+  const int nf = a.m.nfaces;
+  const unsigned coarse_mask = a.m.scoarse[c];
+  int sf[S::NSIDE];
+#pragma unroll
+  for (int sd = 0; sd < S::NSIDE; ++sd) sf[sd] = a.m.sface[(size_t)sd * nc + c];
+  const real* dphiw = a.tab + S::OFF_DPHIW;
+  const real* phifw = a.tab + S::OFF_PHIFW;
+
+  for (int o = p; o < S::NV * S::N; o += P) {
+    const int v = o / S::N, j = o % S::N;
+    real acc = real(0);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d)
+#pragma unroll
+      for (int q = 0; q < S::Q; ++q)
+        acc += sF[((d * S::NV + v) * S::Q + q) * TC + tc] * ld(dphiw + (d * S::Q + q) * S::N + j);
+    // surface integral: + side faces carry +fbar (outward normal +e_a),
+    // - side faces -fbar
+#pragma unroll
+    for (int sd = 0; sd < S::NSIDE; ++sd) {
+      const real sg = (sd & 1) ? real(1) : real(-1);
+      real s = real(0);
+      if (!((coarse_mask >> sd) & 1)) {
+#pragma unroll
+        for (int q = 0; q < S::QF; ++q)
+          s += a.F[((size_t)v * S::QF + q) * nf + sf[sd]] *
+               ld(phifw + ((sd * S::NVAR + 0) * S::QF + q) * S::N + j);
+      } else {
+        for (int sub = 0; sub < S::NSUB; ++sub)
+#pragma unroll
+          for (int q = 0; q < S::QF; ++q)
+            s += a.F[((size_t)v * S::QF + q) * nf + sf[sd] + sub] *
+                 ld(phifw + ((sd * S::NVAR + 1 + sub) * S::QF + q) * S::N + j);
+      }
+      acc -= sg * s;
+    }
+    const real rhs = pre * acc;
+    const size_t idx = (size_t)o * nc + c;
+    for (int oo = 0; oo < a.n_out; ++oo) {
+      real val = real(a.ck[oo]) * dtv * rhs;
+      for (int r = 0; r < a.n_in; ++r) {
+        const double cr = a.C[oo][r];
+        if (cr == 0.0) continue;
+        const real x = (a.in[r] == a.U) ? sW[o * TC + tc] : a.in[r][idx];
+        val += real(cr) * x;
+      }
+      a.out[oo][idx] = val;
+    }
+  }
+}
+
+// ===========================================================================
+// Limiters (Secs. 3.2-3.4 and 4.4), one thread per cell, FP64 arithmetic.
+// Inputs come from Uin (state before limiting), the result goes to Uout.
+
+template <typename real, int DIM, int K>
+__device__ __forceinline__ void nb_mean(const LimitArgs<real>& a, int c, int dir, int s,
+                                        const double* own, double* out) {
+  using S = Shape<DIM, K>;
+  const int nc = a.m.ncells;
+  const int nb = a.m.nbr[(size_t)(2 * dir + s) * nc + c];
+  if (nb == -1) {
+    for (int v = 0; v < S::NV; ++v) out[v] = own[v];
+  } else if (nb <= -2) {
+    const int* kids = a.m.node_children + (size_t)(-(nb + 2)) * S::NCH;
+    for (int v = 0; v < S::NV; ++v) {
+      double sum = 0.0;
+      for (int ch = 0; ch < S::NCH; ++ch) sum += (double)a.Uin[(size_t)(v * S::N) * nc + kids[ch]];
+      out[v] = sum / S::NCH;
+    }
+  } else if (a.m.level[nb] == a.m.level[c]) {
+    for (int v = 0; v < S::NV; ++v) out[v] = (double)a.Uin[(size_t)(v * S::N) * nc + nb];
+  } else {
+    // coarser neighbour: mean of its polynomial over the same-size region
+    int ch = 0;
+    for (int b = 0; b < DIM; ++b) {
+      int pb = a.m.coord[(size_t)b * nc + c];
+      if (b == dir) {
+        const int ext = a.m.n[b] << a.m.level[c];
+        pb = (pb + (s ? 1 : -1) + ext) % ext;
+      }
+      ch |= (pb & 1) << b;
+    }
+    const double* row = a.tab64 + S::OFF_PREF + (size_t)(ch * S::N + 0) * S::N;
+    for (int v = 0; v < S::NV; ++v) {
+      double sum = 0.0;
+      for (int l = 0; l < S::N; ++l) sum += row[l] * (double)a.Uin[(size_t)(v * S::N + l) * nc + nb];
+      out[v] = sum;
+    }
+  }
+}
+
+__device__ __forceinline__ double minmod3(double a, double b, double c) {
+  if (a > 0.0 && b > 0.0 && c > 0.0) return fmin(a, fmin(b, c));
+  if (a < 0.0 && b < 0.0 && c < 0.0) return fmax(a, fmax(b, c));
+  return 0.0;
+}
+
+// Root tau in [0,1] of p(ubar + tau (u - ubar)) = eps: multiplying by the
+// density gives the quadratic qa tau^2 + qb tau + qc = 0; stable closed-form
+// root, then two Newton-Raphson steps (Sec. 3.4).
+template <int DIM>
+__device__ double positivity_tau(const double* ub, const double* u, double gamma, double eps) {
+  const double g1 = gamma - 1.0;
+  double dr = u[0] - ub[0], dE = u[DIM + 1] - ub[DIM + 1];
+  double mm = 0.0, md = 0.0, dd = 0.0;
+  for (int b = 0; b < DIM; ++b) {
+    const double dm = u[1 + b] - ub[1 + b];
+    mm += ub[1 + b] * ub[1 + b];
+    md += ub[1 + b] * dm;
+    dd += dm * dm;
+  }
+  const double qa = g1 * (dE * dr - 0.5 * dd);
+  const double qb = g1 * (ub[DIM + 1] * dr + ub[0] * dE - md) - eps * dr;
+  const double qc = g1 * (ub[DIM + 1] * ub[0] - 0.5 * mm) - eps * ub[0];
+  if (qc <= 0.0) return 0.0;
+  double tau;
+  if (fabs(qa) <= 1e-14 * (fabs(qb) + fabs(qc))) {
+    tau = -qc / qb;
+  } else {
+    const double disc = fmax(qb * qb - 4.0 * qa * qc, 0.0);
+    const double qq = -0.5 * (qb + copysign(sqrt(disc), qb));
+    const double r1 = qq / qa, r2 = qc / qq;
+    const bool ok1 = r1 >= 0.0 && r1 <= 1.0, ok2 = r2 >= 0.0 && r2 <= 1.0;
+    if (ok1 && ok2) tau = fmin(r1, r2);
+    else if (ok1) tau = r1;
+    else if (ok2) tau = r2;
+    else tau = fabs(r1 - 0.5) < fabs(r2 - 0.5) ? r1 : r2;
+  }
+  for (int it = 0; it < 2; ++it) {
+    const double g = (qa * tau + qb) * tau + qc;
+    const double dg = 2.0 * qa * tau + qb;
+    if (dg != 0.0) tau -= g / dg;
+  }
+  return fmin(fmax(tau, 0.0), 1.0);
+}
+
+template <typename real, int DIM, int K>
+__global__ void __launch_bounds__(128) limit_kernel(const LimitArgs<real> a) {
+  using S = Shape<DIM, K>;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nc = a.m.ncells;
+  if (c >= nc) return;
+  double w[S::NV][S::N];
+  for (int v = 0; v < S::NV; ++v)
+    for (int l = 0; l < S::N; ++l) w[v][l] = (double)a.Uin[(size_t)(v * S::N + l) * nc + c];
+  double mean[S::NV];
+  for (int v = 0; v < S::NV; ++v) mean[v] = w[v][0];
+  {
+    double m2 = 0.0;
+    for (int b = 0; b < DIM; ++b) m2 += mean[1 + b] * mean[1 + b];
+    const double pm = (a.gamma - 1.0) * (mean[DIM + 1] - 0.5 * m2 / mean[0]);
+    if (!(mean[0] > 0.0) || !(pm > 0.0)) atomicOr(a.status, 1 << DG_ERR_NONPHYSICAL_BIT);
+  }
+  const double* tab = a.tab64;
+  const double dx = cell_dx(a.m, c);
+  if (a.limiter != 0 && K > 0) {
+    const double s3 = sqrt(3.0);
+    bool changed = false;
+    double ct[DIM][S::NV];
+    for (int d = 0; d < DIM; ++d) {
+      double L[S::NV * S::NV], R[S::NV * S::NV];
+      if (a.limiter == 2) {
+        char_matrices<DIM>(mean, d, a.gamma, L, R);
+      } else {
+        for (int i = 0; i < S::NV * S::NV; ++i) L[i] = 0.0;
+        for (int i = 0; i < S::NV; ++i) L[i * S::NV + i] = 1.0;
+      }
+      double mm[S::NV], mp[S::NV];
+      nb_mean<real, DIM, K>(a, c, d, 0, mean, mm);
+      nb_mean<real, DIM, K>(a, c, d, 1, mean, mp);
+      for (int i = 0; i < S::NV; ++i) {
+        double cs = 0.0, dm = 0.0, dp = 0.0;
+        for (int v = 0; v < S::NV; ++v) {
+          const double Lv = L[i * S::NV + v];
+          cs += Lv * w[v][1 + d];
+          dm += Lv * (mean[v] - mm[v]);
+          dp += Lv * (mp[v] - mean[v]);
+        }
+        const double arg = s3 * cs;
+        const double lim = (fabs(arg) <= a.Mtilde * dx) ? arg : minmod3(arg, a.beta * dm, a.beta * dp);
+        if (lim != arg) changed = true;
+        ct[d][i] = lim / s3;
+      }
+    }
+    if (changed) {
+      for (int d = 0; d < DIM; ++d) {
+        double L[S::NV * S::NV], R[S::NV * S::NV];
+        if (a.limiter == 2) {
+          char_matrices<DIM>(mean, d, a.gamma, L, R);
+        } else {
+          for (int i = 0; i < S::NV * S::NV; ++i) R[i] = 0.0;
+          for (int i = 0; i < S::NV; ++i) R[i * S::NV + i] = 1.0;
+        }
+        for (int v = 0; v < S::NV; ++v) {
+          double s = 0.0;
+          for (int i = 0; i < S::NV; ++i) s += R[v * S::NV + i] * ct[d][i];
+          w[v][1 + d] = s;
+        }
+      }
+      for (int l = 0; l < S::N; ++l)
+        if (tab[S::OFF_DEG + l] >= 2.0)
+          for (int v = 0; v < S::NV; ++v) w[v][l] = 0.0;
+    }
+  }
+  if (a.positivity && K > 0) {
+    const double eps = a.eps;
+    // points: the union set S, plus fine sub-face points on sides with a finer neighbour
+    unsigned finer = 0;
+    for (int sd = 0; sd < S::NSIDE; ++sd)
+      if (a.m.nbr[(size_t)sd * nc + c] <= -2) finer |= 1u << sd;
+    const int npts = S::NSP + __popc(finer) * S::NSUB * S::QF;
+    auto point_row = [&](int i) -> const double* {
+      if (i < S::NSP) return tab + S::OFF_SPHI + (size_t)i * S::N;
+      int r = i - S::NSP;
+      int sd = 0;
+      for (; sd < S::NSIDE; ++sd) {
+        if (!((finer >> sd) & 1)) continue;
+        if (r < S::NSUB * S::QF) break;
+        r -= S::NSUB * S::QF;
+      }
+      const int var = 1 + r / S::QF, q = r % S::QF;
+      return tab + S::OFF_PHIF + (size_t)((sd * S::NVAR + var) * S::QF + q) * S::N;
+    };
+    double rmin = 1e300;
+    for (int i = 0; i < npts; ++i) {
+      const double* ph = point_row(i);
+      double rho = 0.0;
+      for (int l = 0; l < S::N; ++l) rho += w[0][l] * ph[l];
+      rmin = fmin(rmin, rho);
+    }
+    if (rmin < eps) {
+      const double th1 = fmin(fabs((mean[0] - eps) / (mean[0] - rmin)), 1.0);
+      for (int l = 1; l < S::N; ++l) w[0][l] *= th1;
+    }
+    double th2 = 1.0;
+    for (int i = 0; i < npts; ++i) {
+      const double* ph = point_row(i);
+      double u[S::NV];
+      for (int v = 0; v < S::NV; ++v) {
+        double s = 0.0;
+        for (int l = 0; l < S::N; ++l) s += w[v][l] * ph[l];
+        u[v] = s;
+      }
+      double m2 = 0.0;
+      for (int b = 0; b < DIM; ++b) m2 += u[1 + b] * u[1 + b];
+      const double pr = (a.gamma - 1.0) * (u[DIM + 1] - 0.5 * m2 / u[0]);
+      if (pr >= eps) continue;
+      th2 = fmin(th2, positivity_tau<DIM>(mean, u, a.gamma, eps));
+    }
+    if (th2 < 1.0)
+      for (int v = 0; v < S::NV; ++v)
+        for (int l = 1; l < S::N; ++l) w[v][l] *= th2;
+  }
+  for (int v = 0; v < S::NV; ++v)
+    for (int l = 0; l < S::N; ++l) a.Uout[(size_t)(v * S::N + l) * nc + c] = (real)w[v][l];
+}
+
+// ===========================================================================
+// Auxiliary kernels
+
+constexpr int RED_THREADS = 256;
+
+__device__ __forceinline__ double block_sum(double x, double* sh) {
+  // deterministic: fixed pairwise order
+  sh[threadIdx.x] = x;
+  __syncthreads();
+  for (int s = RED_THREADS / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  const double r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+template <typename real, int DIM, int K>
+__global__ void __launch_bounds__(RED_THREADS) dt_kernel(const AuxArgs<real> a) {
+  using S = Shape<DIM, K>;
+  __shared__ double sh[RED_THREADS];
+  const int c = blockIdx.x * RED_THREADS + threadIdx.x;
+  const int nc = a.m.ncells;
+  double dtc = 1e300;
+  if (c < nc) {
+    double u[S::NV];
+    for (int v = 0; v < S::NV; ++v) u[v] = (double)a.W[(size_t)(v * S::N) * nc + c];
+    double m2 = 0.0;
+    for (int b = 0; b < DIM; ++b) m2 += u[1 + b] * u[1 + b];
+    const double p = (a.gamma - 1.0) * (u[DIM + 1] - 0.5 * m2 / u[0]);
+    if (!(u[0] > 0.0) || !(p > 0.0)) {
+      atomicOr(a.status, 1 << DG_ERR_NONPHYSICAL_BIT);
+    } else {
+      const double cs = sqrt(a.gamma * p / u[0]);
+      const double dx = cell_dx(a.m, c);
+      double sum = 0.0;
+      for (int b = 0; b < DIM; ++b) sum += (fabs(u[1 + b] / u[0]) + cs) / dx;
+      dtc = a.dt_factor / sum;
+    }
+  }
+  sh[threadIdx.x] = dtc;
+  __syncthreads();
+  for (int s = RED_THREADS / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) sh[threadIdx.x] = fmin(sh[threadIdx.x], sh[threadIdx.x + s]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicMin(a.dt_bits, (unsigned long long)__double_as_longlong(sh[0]));
+}
+
+template <typename real, int DIM, int K>
+__global__ void __launch_bounds__(RED_THREADS) totals_kernel(const AuxArgs<real> a) {
+  using S = Shape<DIM, K>;
+  __shared__ double sh[RED_THREADS];
+  const int c = blockIdx.x * RED_THREADS + threadIdx.x;
+  const int nc = a.m.ncells;
+  double vol = 0.0;
+  if (c < nc) {
+    const double dx = cell_dx(a.m, c);
+    vol = DIM == 2 ? dx * dx : dx * dx * dx;
+  }
+  for (int v = 0; v < S::NV; ++v) {
+    const double x = (c < nc) ? vol * (double)a.W[(size_t)(v * S::N) * nc + c] : 0.0;
+    const double s = block_sum(x, sh);
+    if (threadIdx.x == 0) a.partial[(size_t)blockIdx.x * S::NV + v] = s;
+  }
+}
+
+template <typename real, int DIM, int K>
+__global__ void __launch_bounds__(RED_THREADS) l1_kernel(const AuxArgs<real> a) {
+  using S = Shape<DIM, K>;
+  __shared__ double sh[RED_THREADS];
+  const int c = blockIdx.x * RED_THREADS + threadIdx.x;
+  const int nc = a.m.ncells;
+  double cell = 0.0;
+  if (c < nc) {
+    double w[S::N];
+    for (int l = 0; l < S::N; ++l) w[l] = (double)a.W[(size_t)l * nc + c];
+    for (int q = 0; q < S::Q1; ++q) {
+      const double* ph = a.tab64 + S::OFF_L1PHI + q * S::N;
+      double rho = 0.0;
+      for (int l = 0; l < S::N; ++l) rho += w[l] * ph[l];
+      cell += fabs(rho - a.u[(size_t)q * nc + c]) * a.tab64[S::OFF_L1W + q];
+    }
+    const double hx = 0.5 * cell_dx(a.m, c);
+    cell *= DIM == 2 ? hx * hx : hx * hx * hx;
+  }
+  const double s = block_sum(cell, sh);
+  if (threadIdx.x == 0) a.partial[blockIdx.x] = s;
+}
+
+// partial[nblocks][nv] -> out[nv] (scaled), summed in block order
+static __global__ void reduce_partials_kernel(const double* partial, int nblocks, int nv, double scale,
+                                       double* out) {
+  const int v = threadIdx.x;
+  if (v >= nv) return;
+  double s = 0.0;
+  for (int b = 0; b < nblocks; ++b) s += partial[(size_t)b * nv + v];
+  out[v] = s * scale;
+}
+
+template <typename real, int DIM, int K>
+__global__ void project_kernel(const AuxArgs<real> a) {
+  using S = Shape<DIM, K>;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nc = a.m.ncells;
+  if (c >= nc) return;
+  for (int v = 0; v < S::NV; ++v) {
+    double acc[S::N];
+    for (int j = 0; j < S::N; ++j) acc[j] = 0.0;
+    for (int q = 0; q < S::Q; ++q) {
+      const double uq = a.u[((size_t)v * S::Q + q) * nc + c];
+      for (int j = 0; j < S::N; ++j) acc[j] += uq * a.tab64[S::OFF_PROJ + q * S::N + j];
+    }
+    for (int j = 0; j < S::N; ++j) a.Wout[(size_t)(v * S::N + j) * nc + c] = (real)acc[j];
+  }
+}
+
+template <typename real, int DIM, int K>
+__global__ void points_kernel(const AuxArgs<real> a, int l1rule) {
+  using S = Shape<DIM, K>;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nc = a.m.ncells;
+  if (c >= nc) return;
+  const int nq = l1rule ? S::Q1 : S::Q;
+  const double* xi = a.tab64 + (l1rule ? S::OFF_XI1 : S::OFF_XI);
+  const double dx = cell_dx(a.m, c);
+  for (int d = 0; d < DIM; ++d) {
+    const double ctr = a.m.lo[d] + ((double)a.m.coord[(size_t)d * nc + c] + 0.5) * dx;
+    for (int q = 0; q < nq; ++q) a.out[((size_t)d * nq + q) * nc + c] = ctr + 0.5 * dx * xi[q * 3 + d];
+  }
+}
+
+template <typename real, int DIM, int K>
+__global__ void node_weights_kernel(const AuxArgs<real> a) {
+  using S = Shape<DIM, K>;
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nn = a.m.nnodes, nc = a.m.ncells;
+  if (m >= nn) return;
+  const int* kids = a.m.node_children + (size_t)m * S::NCH;
+  for (int v = 0; v < S::NV; ++v)
+    for (int j = 0; j < S::N; ++j) {
+      double s = 0.0;
+      for (int ch = 0; ch < S::NCH; ++ch)
+        for (int l = 0; l < S::N; ++l)
+          s += a.tab64[S::OFF_PREF + (ch * S::N + l) * S::N + j] *
+               (double)a.W[(size_t)(v * S::N + l) * nc + kids[ch]];
+      a.Wout[(size_t)(v * S::N + j) * nn + m] = (real)(s / S::NCH);
+    }
+}
+
+// ===========================================================================
+// Launchers
+
+template <typename real, int DIM, int K>
+cudaError_t launch_face(const void* pa, cudaStream_t s) {
+  const auto& a = *static_cast<const StageArgs<real>*>(pa);
+  using S = Shape<DIM, K>;
+  constexpr int FB = FaceBlock<S::QF>::FB;
+  if (a.m.nfaces == 0) return cudaSuccess;
+  dim3 block(FB, S::QF), grid((a.m.nfaces + FB - 1) / FB);
+  face_flux_kernel<real, DIM, K><<<grid, block, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename real, int DIM, int K>
+cudaError_t launch_cell(const void* pa, cudaStream_t s) {
+  const auto& a = *static_cast<const StageArgs<real>*>(pa);
+  using T = CellTile<real, DIM, K>;
+  if (a.m.ncells == 0) return cudaSuccess;
+  dim3 grid((a.m.ncells + T::TC - 1) / T::TC);
+  cell_update_kernel<real, DIM, K><<<grid, T::THREADS, T::SMEM, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename real, int DIM, int K>
+cudaError_t prepare_kernels() {
+  using T = CellTile<real, DIM, K>;
+  return cudaFuncSetAttribute(cell_update_kernel<real, DIM, K>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::SMEM);
+}
+
+template <typename real, int DIM, int K>
+cudaError_t launch_limit(const void* pa, cudaStream_t s) {
+  const auto& a = *static_cast<const LimitArgs<real>*>(pa);
+  if (a.m.ncells == 0) return cudaSuccess;
+  limit_kernel<real, DIM, K><<<(a.m.ncells + 127) / 128, 128, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename real, int DIM, int K>
+cudaError_t launch_project(const void* pa, cudaStream_t s) {
+  const auto& a = *static_cast<const AuxArgs<real>*>(pa);
+  if (a.m.ncells == 0) return cudaSuccess;
+  project_kernel<real, DIM, K><<<(a.m.ncells + 127) / 128, 128, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename real, int DIM, int K>
+cudaError_t launch_points(const void* pa, int l1rule, cudaStream_t s) {
+  const auto& a = *static_cast<const AuxArgs<real>*>(pa);
+  if (a.m.ncells == 0) return cudaSuccess;
+  points_kernel<real, DIM, K><<<(a.m.ncells + 127) / 128, 128, 0, s>>>(a, l1rule);
+  return cudaGetLastError();
+}
+
+template <typename real, int DIM, int K>
+cudaError_t launch_dt(const void* pa, cudaStream_t s) {
+  const auto& a = *static_cast<const AuxArgs<real>*>(pa);
+  if (a.m.ncells == 0) return cudaSuccess;
+  dt_kernel<real, DIM, K><<<(a.m.ncells + RED_THREADS - 1) / RED_THREADS, RED_THREADS, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename real, int DIM, int K>
+cudaError_t launch_totals(const void* pa, cudaStream_t s) {
+  const auto& a = *static_cast<const AuxArgs<real>*>(pa);
+  using S = Shape<DIM, K>;
+  const int nb = (a.m.ncells + RED_THREADS - 1) / RED_THREADS;
+  if (nb > 0) totals_kernel<real, DIM, K><<<nb, RED_THREADS, 0, s>>>(a);
+  reduce_partials_kernel<<<1, 32, 0, s>>>(a.partial, nb, S::NV, 1.0, a.out);
+  return cudaGetLastError();
+}
+
+template <typename real, int DIM, int K>
+cudaError_t launch_l1(const void* pa, cudaStream_t s) {
+  const auto& a = *static_cast<const AuxArgs<real>*>(pa);
+  const int nb = (a.m.ncells + RED_THREADS - 1) / RED_THREADS;
+  if (nb > 0) l1_kernel<real, DIM, K><<<nb, RED_THREADS, 0, s>>>(a);
+  reduce_partials_kernel<<<1, 32, 0, s>>>(a.partial, nb, 1, 1.0 / a.volume, a.out);
+  return cudaGetLastError();
+}
+
+template <typename real, int DIM, int K>
+cudaError_t launch_node_weights(const void* pa, cudaStream_t s) {
+  const auto& a = *static_cast<const AuxArgs<real>*>(pa);
+  if (a.m.nnodes == 0) return cudaSuccess;
+  node_weights_kernel<real, DIM, K><<<(a.m.nnodes + 127) / 128, 128, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename real, int DIM, int K>
+KernelSet make_kernel_set(int prec) {
+  using S = Shape<DIM, K>;
+  KernelSet ks;
+  ks.dim = DIM;
+  ks.k = K;
+  ks.prec = prec;
+  ks.N = S::N;
+  ks.NV = S::NV;
+  ks.Q = S::Q;
+  ks.QF = S::QF;
+  ks.Q1 = S::Q1;
+  ks.NSUB = S::NSUB;
+  ks.NSP = S::NSP;
+  ks.M = S::M;
+  ks.tab_size = S::TAB_SIZE;
+  ks.fill_tables = &fill_tables<DIM, K>;
+  ks.prepare = &prepare_kernels<real, DIM, K>;
+  ks.face = &launch_face<real, DIM, K>;
+  ks.cell = &launch_cell<real, DIM, K>;
+  ks.limit = &launch_limit<real, DIM, K>;
+  ks.project = &launch_project<real, DIM, K>;
+  ks.points = &launch_points<real, DIM, K>;
+  ks.dt = &launch_dt<real, DIM, K>;
+  ks.totals = &launch_totals<real, DIM, K>;
+  ks.l1 = &launch_l1<real, DIM, K>;
+  ks.node_weights = &launch_node_weights<real, DIM, K>;
+  return ks;
+}
+
+}  // namespace dgi

@@ -1,0 +1,256 @@
+"""Thin Python binding of libdg (ctypes).
+
+Argument marshalling only: torch tensors supply device memory and the current
+CUDA stream; every step of the computation runs in libdg's kernels.  There is
+no CPU path: if ``libdg.so`` is missing this module raises on first use.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdg.so")
+
+DG_OK, DG_ERR_ARG, DG_ERR_CUDA, DG_ERR_OOM, DG_ERR_NONPHYSICAL, DG_ERR_TIMEOUT, \
+    DG_ERR_UNSUPPORTED = range(7)
+DG_BC_PERIODIC, DG_BC_TRANSMISSIVE = 0, 1
+LIMITERS = {"none": 0, "component": 1, "characteristic": 2}
+PRECISIONS = {"fp64": 0, "fp32": 1}
+
+EXPORTS = ["dg_default_options", "dg_create", "dg_destroy", "dg_last_error", "dg_sizes",
+           "dg_quad_points", "dg_l1_points", "dg_project", "dg_rhs", "dg_compute_dt",
+           "dg_rk_step", "dg_advance", "dg_rk_step_adjoint", "dg_limit", "dg_totals",
+           "dg_l1_density", "dg_node_weights", "dg_neighbor_table", "dg_cell_levels",
+           "dg_status", "dg_profile_begin", "dg_profile_end"]
+KERNEL_KINDS = ["face", "cell", "limit", "dt", "other"]
+
+
+class MeshDesc(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("lo", C.c_double * 3),
+                ("hi", C.c_double * 3), ("bc", C.c_int * 3), ("n_refine_boxes", C.c_int),
+                ("refine_boxes", C.POINTER(C.c_int32))]
+
+
+class Options(C.Structure):
+    _fields_ = [("rk_order", C.c_int), ("cfl", C.c_double), ("slope_limiter", C.c_int),
+                ("beta", C.c_double), ("Mtilde", C.c_double), ("positivity", C.c_int),
+                ("eps", C.c_double), ("precision", C.c_int)]
+
+
+class DGError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("libdg error %d: %s" % (code, msg))
+        self.code = code
+
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Load libdg.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libdg.so not found at %s: build it with "
+                           "paper_1506_06140_gb300.build.build()" % path)
+    L = C.CDLL(path)
+    vp, i32p, dp = C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_double)
+    L.dg_default_options.argtypes = [C.POINTER(Options)]
+    L.dg_create.argtypes = [C.POINTER(MeshDesc), C.c_int, C.c_double, C.POINTER(Options),
+                            C.POINTER(vp)]
+    L.dg_destroy.argtypes = [vp]
+    L.dg_last_error.restype = C.c_char_p
+    L.dg_last_error.argtypes = [vp]
+    L.dg_sizes.argtypes = [vp, C.POINTER(C.c_int64)] + [C.POINTER(C.c_int)] * 5
+    for name in ("dg_quad_points", "dg_l1_points"):
+        getattr(L, name).argtypes = [vp, vp, vp]
+    L.dg_project.argtypes = [vp, vp, vp, vp]
+    L.dg_rhs.argtypes = [vp, vp, vp, vp]
+    L.dg_compute_dt.argtypes = [vp, vp, vp, vp]
+    L.dg_rk_step.argtypes = [vp, vp, C.c_double, vp, vp]
+    L.dg_advance.argtypes = [vp, vp, C.c_int, vp, vp]
+    L.dg_rk_step_adjoint.argtypes = [vp, vp, C.c_double, vp, vp, vp]
+    L.dg_limit.argtypes = [vp, vp, vp]
+    L.dg_totals.argtypes = [vp, vp, vp, vp]
+    L.dg_l1_density.argtypes = [vp, vp, vp, vp, vp]
+    L.dg_node_weights.argtypes = [vp, vp, vp, vp]
+    L.dg_neighbor_table.argtypes = [vp, i32p]
+    L.dg_cell_levels.argtypes = [vp, i32p]
+    L.dg_status.argtypes = [vp, C.POINTER(C.c_int)]
+    L.dg_profile_begin.argtypes = [vp]
+    L.dg_profile_end.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_int]
+    for name in EXPORTS:
+        getattr(L, name).restype = C.c_int if name != "dg_last_error" else C.c_char_p
+    _lib = L
+    return L
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+class Solver:
+    """One DG problem on the current CUDA device (see include/dg.h)."""
+
+    def __init__(self, mesh, k, gamma=1.4, rk_order=3, cfl=0.2, limiter="none", beta=1.0,
+                 Mtilde=0.5, positivity=False, eps=1e-10, precision="fp64"):
+        L = load()
+        self._L = L
+        self.mesh = dict(mesh)
+        self.dim, self.k, self.gamma = mesh["dim"], k, gamma
+        md = MeshDesc()
+        md.dim = mesh["dim"]
+        for a in range(3):
+            md.n[a] = int(mesh["n"][a]) if a < md.dim else 1
+            md.lo[a] = float(mesh["lo"][a]) if a < md.dim else 0.0
+            md.hi[a] = float(mesh["hi"][a]) if a < md.dim else 1.0
+            bc = mesh.get("bc") or [DG_BC_PERIODIC] * md.dim
+            md.bc[a] = int(bc[a]) if a < md.dim else 0
+        boxes = mesh.get("refine_boxes") or []
+        self._boxes = np.ascontiguousarray(np.array(boxes, dtype=np.int32).reshape(-1))
+        md.n_refine_boxes = len(boxes)
+        md.refine_boxes = self._boxes.ctypes.data_as(C.POINTER(C.c_int32)) if len(boxes) else None
+        opt = Options()
+        L.dg_default_options(C.byref(opt))
+        opt.rk_order, opt.cfl = rk_order, cfl
+        opt.slope_limiter = LIMITERS[limiter] if isinstance(limiter, str) else int(limiter)
+        opt.beta, opt.Mtilde = beta, Mtilde
+        opt.positivity, opt.eps = int(bool(positivity)), eps
+        opt.precision = PRECISIONS[precision]
+        self.precision = precision
+        self.dtype = torch.float64 if precision == "fp64" else torch.float32
+        torch.cuda.init()
+        h = C.c_void_p()
+        r = L.dg_create(C.byref(md), k, gamma, C.byref(opt), C.byref(h))
+        if r != DG_OK:
+            raise DGError(r, L.dg_last_error(None).decode())
+        self._h = h
+        nc, N, nv, nq, nq1, nn = C.c_int64(), C.c_int(), C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        self._check(L.dg_sizes(h, C.byref(nc), C.byref(N), C.byref(nv), C.byref(nq),
+                               C.byref(nq1), C.byref(nn)))
+        self.n_cells, self.N, self.nv = nc.value, N.value, nv.value
+        self.nq, self.nq1, self.n_nodes = nq.value, nq1.value, nn.value
+        self.device = torch.device("cuda", torch.cuda.current_device())
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            self._L.dg_destroy(h)
+            self._h = None
+
+    def _check(self, r):
+        if r != DG_OK:
+            raise DGError(r, self._L.dg_last_error(self._h if hasattr(self, "_h") else None).decode())
+
+    def _state(self, W):
+        assert W.is_cuda and W.dtype == self.dtype and W.is_contiguous(), "bad state tensor"
+        assert tuple(W.shape) == (self.nv, self.N, self.n_cells), "bad state shape"
+        return _ptr(W)
+
+    # -- allocation helpers (torch owns the memory) --
+    def empty_state(self):
+        return torch.empty((self.nv, self.N, self.n_cells), dtype=self.dtype, device=self.device)
+
+    def scalar(self, n=1):
+        return torch.zeros(n, dtype=torch.float64, device=self.device)
+
+    # -- C-ABI calls --
+    def quad_points(self):
+        out = torch.empty((self.dim, self.nq, self.n_cells), dtype=torch.float64, device=self.device)
+        self._check(self._L.dg_quad_points(self._h, _ptr(out), _stream()))
+        return out
+
+    def l1_points(self):
+        out = torch.empty((self.dim, self.nq1, self.n_cells), dtype=torch.float64, device=self.device)
+        self._check(self._L.dg_l1_points(self._h, _ptr(out), _stream()))
+        return out
+
+    def project(self, u, out=None):
+        u = u.to(device=self.device, dtype=torch.float64).contiguous()
+        assert tuple(u.shape) == (self.nv, self.nq, self.n_cells)
+        W = self.empty_state() if out is None else out
+        self._check(self._L.dg_project(self._h, _ptr(u), self._state(W), _stream()))
+        return W
+
+    def rhs(self, W, out=None):
+        out = self.empty_state() if out is None else out
+        self._check(self._L.dg_rhs(self._h, self._state(W), self._state(out), _stream()))
+        return out
+
+    def compute_dt(self, W, out=None):
+        out = self.scalar() if out is None else out
+        self._check(self._L.dg_compute_dt(self._h, self._state(W), _ptr(out), _stream()))
+        return out
+
+    def rk_step(self, W, dt=0.0, dt_out=None):
+        """One RK step in place; dt <= 0 uses the CFL timestep."""
+        p = _ptr(dt_out) if dt_out is not None else None
+        self._check(self._L.dg_rk_step(self._h, self._state(W), float(dt), p, _stream()))
+        return W
+
+    def advance(self, W, n_steps, dt_hist=None):
+        """n_steps CFL steps in place through a cached CUDA graph."""
+        p = _ptr(dt_hist) if dt_hist is not None else None
+        self._check(self._L.dg_advance(self._h, self._state(W), int(n_steps), p, _stream()))
+        return W
+
+    def rk_step_adjoint(self, W_n, dt, lam_np1, out=None):
+        out = self.empty_state() if out is None else out
+        self._check(self._L.dg_rk_step_adjoint(self._h, self._state(W_n), float(dt),
+                                               self._state(lam_np1), self._state(out), _stream()))
+        return out
+
+    def limit(self, W):
+        self._check(self._L.dg_limit(self._h, self._state(W), _stream()))
+        return W
+
+    def totals(self, W, out=None):
+        out = self.scalar(self.nv) if out is None else out
+        self._check(self._L.dg_totals(self._h, self._state(W), _ptr(out), _stream()))
+        return out
+
+    def l1_density(self, W, rho_ref, out=None):
+        rho_ref = rho_ref.to(device=self.device, dtype=torch.float64).contiguous()
+        assert tuple(rho_ref.shape) == (self.nq1, self.n_cells)
+        out = self.scalar() if out is None else out
+        self._check(self._L.dg_l1_density(self._h, self._state(W), _ptr(rho_ref), _ptr(out),
+                                          _stream()))
+        return out
+
+    def node_weights(self, W):
+        out = torch.empty((self.nv, self.N, max(self.n_nodes, 1)), dtype=self.dtype,
+                          device=self.device)
+        self._check(self._L.dg_node_weights(self._h, self._state(W), _ptr(out), _stream()))
+        return out[:, :, : self.n_nodes]
+
+    def neighbor_table(self):
+        out = np.zeros((2 * self.dim, self.n_cells), np.int32)
+        self._check(self._L.dg_neighbor_table(self._h, out.ctypes.data_as(C.POINTER(C.c_int32))))
+        return out
+
+    def levels(self):
+        out = np.zeros(self.n_cells, np.int32)
+        self._check(self._L.dg_cell_levels(self._h, out.ctypes.data_as(C.POINTER(C.c_int32))))
+        return out
+
+    def profile_begin(self):
+        self._check(self._L.dg_profile_begin(self._h))
+
+    def profile_end(self):
+        """{kind: (launches, total_ms)} of the launches since profile_begin."""
+        n = len(KERNEL_KINDS)
+        cnt, ms = (C.c_int * n)(), (C.c_double * n)()
+        self._check(self._L.dg_profile_end(self._h, cnt, ms, n))
+        return {k: (cnt[i], ms[i]) for i, k in enumerate(KERNEL_KINDS)}
+
+    def status(self):
+        s = C.c_int()
+        self._check(self._L.dg_status(self._h, C.byref(s)))
+        return s.value

@@ -1,0 +1,315 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Bars: integer tables bit-exact; FP64 fields within 1e-11 of the largest
+|value| of the compared quantity (rounding-order differences of sums of
+O(N Q) terms of size ~|f| |dphi| / dx); FP32 fields within the FP32 bar
+derived in the design doc (relative 2e-5 of the largest |value|, RMS 2e-6).
+Inputs are seeded synthetic states with the paper's workload shapes.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import pyoracle as O
+from paper_1506_06140_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+GAMMA = 1.4
+TOL64 = 1e-11
+TOL32_MAX, TOL32_RMS = 2e-5, 2e-6
+
+
+@pytest.fixture(scope="session", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_1506_06140_gb300 import build
+    build.build()
+
+
+def dg_mod():
+    from paper_1506_06140_gb300 import dg
+    return dg
+
+
+# mesh cases: (name, mesh dict); sizes span several tiles of 32 cells and a ragged tail
+MESHES = {
+    "u2": wl.mesh_uniform(2, [37, 29], [0.0, 0.0], [37 / 29.0, 1.0]),
+    "u2t": wl.mesh_uniform(2, [23, 3], [0.0, 0.0], [1.0, 3 / 23.0], bc=[1, 0]),
+    "amr2": dict(wl.mesh_uniform(2, [16, 12], [0.0, 0.0], [4 / 3.0, 1.0]),
+                 refine_boxes=[[4, 3, 9, 7], [13, 0, 15, 1]]),
+    "u3": wl.mesh_uniform(3, [7, 6, 5], [0.0, 0.0, 0.0], [7 / 6.0, 1.0, 5 / 6.0]),
+    "amr3": dict(wl.mesh_uniform(3, [6, 6, 6], [0.0] * 3, [1.0] * 3), refine_boxes=[[2, 2, 1, 3, 4, 3]]),
+    "amr3t": dict(wl.mesh_uniform(3, [5, 4, 4], [0.0] * 3, [1.25, 1.0, 1.0], bc=[1, 0, 1]),
+                  refine_boxes=[[0, 1, 1, 1, 2, 2]]),
+}
+
+
+def oracle_for(mesh, k, **kw):
+    return O.Oracle(mesh["dim"], mesh["n"], mesh["lo"], mesh["hi"], k, GAMMA, bc=mesh["bc"],
+                    refine_boxes=mesh["refine_boxes"], **kw)
+
+
+def solver_for(mesh, k, **kw):
+    return dg_mod().Solver(mesh, k, GAMMA, **kw)
+
+
+def to_dev(s, W):
+    return torch.as_tensor(W, dtype=s.dtype, device="cuda").contiguous()
+
+
+def rel_err(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    scale = max(np.max(np.abs(b)), 1e-300)
+    return np.max(np.abs(a - b)) / scale, np.sqrt(np.mean((a - b) ** 2)) / scale
+
+
+def ks_for(dim):
+    return (0, 1, 2, 3) if dim == 2 else (0, 1, 2)
+
+
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", list(MESHES))
+def test_mesh_tables_bit_exact(name):
+    m = MESHES[name]
+    o = oracle_for(m, 1)
+    s = solver_for(m, 1)
+    assert s.n_cells == o.n_cells and s.n_nodes == o.n_nodes
+    np.testing.assert_array_equal(s.neighbor_table(), o.neighbor_table())
+    np.testing.assert_array_equal(s.levels(), o.levels())
+
+
+@pytest.mark.parametrize("name", ["u2", "amr2", "amr3"])
+def test_points_and_projection(name):
+    m = MESHES[name]
+    for k in ks_for(m["dim"]):
+        o = oracle_for(m, k)
+        s = solver_for(m, k)
+        xyz = s.quad_points().cpu().numpy()
+        np.testing.assert_allclose(xyz, o.quad_points(), rtol=0, atol=1e-15)
+        np.testing.assert_allclose(s.l1_points().cpu().numpy(), o.l1_points(), rtol=0, atol=2e-15)
+        U = wl.vortex(o.quad_points(), center=(0.6, 0.5), period=0) if m["dim"] == 2 else \
+            wl.acoustic3d(o.quad_points(), amp=0.1)
+        Wg = s.project(torch.as_tensor(U, device="cuda")).cpu().numpy()
+        e, _ = rel_err(Wg, o.project(U))
+        assert e < 1e-14
+
+
+@pytest.mark.parametrize("name", list(MESHES))
+def test_rhs_fp64(name):
+    m = MESHES[name]
+    for k in ks_for(m["dim"]):
+        o = oracle_for(m, k)
+        s = solver_for(m, k)
+        W = wl.random_weights(m["dim"], o.N, o.n_cells, seed=100 + k)
+        ref = o.rhs(W)
+        got = s.rhs(to_dev(s, W)).cpu().numpy()
+        e, _ = rel_err(got, ref)
+        assert e < TOL64, (name, k, e)
+
+
+@pytest.mark.parametrize("name", ["u2", "amr2", "u3", "amr3"])
+def test_rhs_fp32(name):
+    m = MESHES[name]
+    for k in ks_for(m["dim"]):
+        o = oracle_for(m, k)
+        s = solver_for(m, k, precision="fp32")
+        W = wl.random_weights(m["dim"], o.N, o.n_cells, seed=200 + k).astype(np.float32)
+        ref = o.rhs(W.astype(np.float64))
+        got = s.rhs(to_dev(s, W)).cpu().numpy()
+        e, erms = rel_err(got, ref)
+        assert e < TOL32_MAX and erms < TOL32_RMS, (name, k, e, erms)
+
+
+@pytest.mark.parametrize("order", [1, 2, 3, 4])
+@pytest.mark.parametrize("name", ["u2", "amr3"])
+def test_rk_step_fp64(order, name):
+    m = MESHES[name]
+    k = {1: 0, 2: 1, 3: 2, 4: 3}[order] if m["dim"] == 2 else min(order - 1, 2)
+    o = oracle_for(m, k, rk_order=order)
+    s = solver_for(m, k, rk_order=order)
+    W = wl.random_weights(m["dim"], o.N, o.n_cells, seed=300 + order)
+    dt = 0.5 * o.compute_dt(W)
+    ref, _ = o.rk_step(W, dt)
+    Wd = to_dev(s, W)
+    s.rk_step(Wd, dt)
+    e, _ = rel_err(Wd.cpu().numpy() - W, ref - W)  # compare the increments
+    assert e < 1e-10, (order, name, e)
+
+
+@pytest.mark.parametrize("name", ["u2", "amr2", "amr3t"])
+def test_dt_totals_l1_nodes(name):
+    m = MESHES[name]
+    k = 2
+    for pos in (False, True):
+        o = oracle_for(m, k, positivity=pos, cfl=0.3)
+        s = solver_for(m, k, positivity=pos, cfl=0.3)
+        W = wl.random_weights(m["dim"], o.N, o.n_cells, seed=400)
+        Wd = to_dev(s, W)
+        assert s.compute_dt(Wd).item() == pytest.approx(o.compute_dt(W), rel=1e-14)
+    np.testing.assert_allclose(s.totals(Wd).cpu().numpy(), o.totals(W), rtol=1e-14,
+                               atol=1e-14 * np.abs(o.totals(W)).max())
+    rho_ref = 1.0 + 0.1 * np.sin(o.l1_points()).sum(axis=0)
+    assert s.l1_density(Wd, torch.as_tensor(rho_ref)).item() == pytest.approx(
+        o.l1_density(W, rho_ref), rel=1e-13)
+    if o.n_nodes:
+        e, _ = rel_err(s.node_weights(Wd).cpu().numpy(), o.node_weights(W))
+        assert e < 1e-14
+
+
+def _rough_state(dim, N, nc, seed):
+    """Admissible means with large random jumps and large higher moments."""
+    W = wl.random_weights(dim, N, nc, seed, slope=0.6, rho_range=(0.2, 2.0), p_range=(0.05, 2.0))
+    return W
+
+
+@pytest.mark.parametrize("lim", ["component", "characteristic"])
+@pytest.mark.parametrize("name", ["u2", "u2t", "amr2", "amr3", "amr3t"])
+def test_limiters_fp64(lim, name):
+    m = MESHES[name]
+    k = 2
+    code = {"component": O.LIM_COMPONENT, "characteristic": O.LIM_CHARACTERISTIC}[lim]
+    o = oracle_for(m, k, limiter=code, positivity=True)
+    s = solver_for(m, k, limiter=lim, positivity=True)
+    W = _rough_state(m["dim"], o.N, o.n_cells, seed=500)
+    ref = o.limit(W)
+    got = s.limit(to_dev(s, W)).cpu().numpy()
+    e, _ = rel_err(got, ref)
+    assert e < 1e-12, (lim, name, e)
+    assert np.any(ref != W)
+
+
+def test_positivity_only_fp64():
+    m = MESHES["amr2"]
+    o = oracle_for(m, 2, positivity=True)
+    s = solver_for(m, 2, positivity=True)
+    W = wl.random_weights(2, o.N, o.n_cells, 9, slope=0.0, rho_range=(0.05, 0.2), p_range=(1e-3, 1e-2))
+    W[:, 1:, :] = np.random.default_rng(8).uniform(-1, 1, (o.nv, o.N - 1, o.n_cells)) * np.abs(W[:, :1, :]) * 0.8
+    ref = o.positivity_limit(W)
+    got = s.limit(to_dev(s, W)).cpu().numpy()
+    e, _ = rel_err(got, ref)
+    assert e < 1e-12
+    assert np.any(ref != W)
+
+
+@pytest.mark.parametrize("name", ["u2t", "amr3"])
+def test_limited_rk3_step_fp64(name):
+    m = MESHES[name]
+    o = oracle_for(m, 2, rk_order=3, limiter=O.LIM_CHARACTERISTIC, positivity=True)
+    s = solver_for(m, 2, rk_order=3, limiter="characteristic", positivity=True)
+    W = o.limit(_rough_state(m["dim"], o.N, o.n_cells, seed=600))
+    dt = o.compute_dt(W)
+    ref, _ = o.rk_step(W, dt)
+    Wd = to_dev(s, W)
+    s.rk_step(Wd, dt)
+    e, _ = rel_err(Wd.cpu().numpy(), ref)
+    assert e < 1e-11, e
+
+
+def test_advance_graph_equals_steps():
+    m = MESHES["u2"]
+    s = solver_for(m, 2, rk_order=3)
+    W = to_dev(s, wl.random_weights(2, s.N, s.n_cells, seed=700))
+    W2 = W.clone()
+    hist = s.scalar(5)
+    s.advance(W, 5, hist)
+    dts = []
+    for _ in range(5):
+        d = s.scalar()
+        s.rk_step(W2, 0.0, d)
+        dts.append(d.item())
+    torch.cuda.synchronize()
+    assert torch.equal(W, W2)
+    np.testing.assert_array_equal(hist.cpu().numpy(), np.array(dts))
+    s.advance(W, 5, hist)  # replay of the cached graph
+    for _ in range(5):
+        s.rk_step(W2, 0.0)
+    assert torch.equal(W, W2)
+
+
+def test_nonphysical_state_sets_status():
+    m = MESHES["u2"]
+    s = solver_for(m, 1)
+    W = wl.random_weights(2, s.N, s.n_cells, seed=1)
+    W[0, 0, 5] = -1.0  # a negative mean density, prepared on the host
+    Wd = to_dev(s, W)
+    assert s.status() == 0
+    s.compute_dt(Wd)
+    assert s.status() == dg_mod().DG_ERR_NONPHYSICAL
+    assert s.status() == 0  # cleared by the read
+
+
+def test_empty_and_single_cell_meshes():
+    # one periodic cell: the cell is its own neighbour on every side
+    m = wl.mesh_uniform(2, [1, 1], [0.0, 0.0], [1.0, 1.0])
+    o = oracle_for(m, 2)
+    s = solver_for(m, 2)
+    W = wl.random_weights(2, o.N, 1, seed=3)
+    e, _ = rel_err(s.rhs(to_dev(s, W)).cpu().numpy(), o.rhs(W))
+    assert e < TOL64
+    np.testing.assert_array_equal(s.neighbor_table(), o.neighbor_table())
+
+
+# ---------------------------------------------------------------------------
+# the workloads at their full sizes
+
+def test_wave2d_32x32_full_run_fp64():
+    """Advected density wave: 32^2, k=1, SSP-RK2, CFL 0.3, t_end = 1."""
+    m = wl.mesh_uniform(2, [32, 32], [0.0, 0.0], [1.0, 1.0])
+    o = oracle_for(m, 1, rk_order=2, cfl=0.3)
+    s = solver_for(m, 1, rk_order=2, cfl=0.3)
+    U = wl.wave2d(o.quad_points())
+    W0 = o.project(U)
+    Wd = s.project(torch.as_tensor(U, device="cuda"))
+    t, W, steps = 0.0, W0.copy(), 0
+    dtd = s.scalar()
+    while t < 1.0 - 1e-14:
+        dt = min(o.compute_dt(W), 1.0 - t)
+        W, _ = o.rk_step(W, dt)
+        s.rk_step(Wd, dt)
+        t += dt
+        steps += 1
+    assert steps > 1000
+    e, _ = rel_err(Wd.cpu().numpy(), W)
+    assert e < 1e-10, e
+    # L1 density error against the closed form, and L1 distance to the oracle
+    rho_ex = wl.wave2d(o.l1_points())[0]
+    l1_o = o.l1_density(W, rho_ex)
+    l1_g = s.l1_density(Wd, torch.as_tensor(rho_ex)).item()
+    assert abs(l1_g - l1_o) <= 1e-8 * l1_o
+    rho_o = density_at_l1_points(o, W)
+    assert o.l1_density(Wd.cpu().numpy(), rho_o) <= 1e-10 * np.abs(rho_o).mean()
+
+
+def density_at_l1_points(o, W):
+    """rho_h of state W at the (k+3)^d rule's points of every cell, [q][cell]."""
+    import itertools
+    from numpy.polynomial import legendre as npleg
+    xg, _ = npleg.leggauss(o.k + 3)
+    pts = np.array(list(itertools.product(xg, repeat=o.dim)))[:, ::-1]  # x fastest
+    Phi = np.array([[O.basis_phi(o.dim, o.k, l, p) for l in range(o.N)] for p in pts])
+    return Phi @ W[0]
+
+
+def test_vortex_256_k3_rk4_full_size_fp64():
+    """Isentropic vortex: 256^2, k=3, SSP-RK4 -- RHS and one full step vs the oracle."""
+    m = wl.mesh_uniform(2, [256, 256], [-5.0, -5.0], [5.0, 5.0])
+    o = oracle_for(m, 3, rk_order=4)
+    s = solver_for(m, 3, rk_order=4)
+    U = wl.vortex(o.quad_points())
+    W = o.project(U)
+    Wd = s.project(torch.as_tensor(U, device="cuda"))
+    e, _ = rel_err(Wd.cpu().numpy(), W)
+    assert e < 1e-14
+    e, _ = rel_err(s.rhs(Wd).cpu().numpy(), o.rhs(W))
+    assert e < TOL64
+    dt = o.compute_dt(W)
+    assert s.compute_dt(Wd).item() == pytest.approx(dt, rel=1e-14)
+    ref, _ = o.rk_step(W, dt)
+    s.rk_step(Wd, dt)
+    e, _ = rel_err(Wd.cpu().numpy() - W, ref - W)
+    assert e < 1e-10
