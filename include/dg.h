@@ -181,6 +181,32 @@ enum { DG_KERNEL_FACE = 0, DG_KERNEL_CELL = 1, DG_KERNEL_LIMIT = 2, DG_KERNEL_DT
 int dg_profile_begin(dg_handle* h);
 int dg_profile_end(dg_handle* h, int* launches, double* total_ms, int n_kinds);
 
+/* ---- allocation-free totals (no handle) --------------------------------
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory -- a host application that owns every
+ * device allocation and forbids libraries from allocating, or code running
+ * while a stream is captured in global mode, where allocation calls are not
+ * permitted.  They cannot create a handle (dg_create allocates), but can
+ * still reduce the conserved totals sum_K |K| w_{1,i} of a state they hold.
+ * It allocates nothing: its per-block partial sums live in one fixed device
+ * array inside the library (8 * 5 * DG_NOALLOC_MAX_CELLS / 256 bytes =
+ * 2.5 MiB), which every GPU that loads the library keeps until the process
+ * exits.
+ *   W_dev       state [dim+2][n_basis][n_cells], double (DG_FP64) or float
+ *               (DG_FP32), caller-owned device memory
+ *   levels_dev  optional device int32[n_cells] refinement level per cell
+ *               (NULL: all cells have edge dx0); |K| = (dx0 / 2^level)^dim
+ *   totals_dev  device double[dim+2] result
+ * Returns DG_ERR_ARG for bad arguments or n_cells > DG_NOALLOC_MAX_CELLS,
+ * DG_ERR_CUDA if a CUDA call fails.  The first call on a device looks up the
+ * array's device address (once per device, with that device current); make
+ * that first call before any stream capture.  All calls share the array:
+ * calls that overlap on the GPU (other streams, other threads) race. */
+#define DG_NOALLOC_MAX_CELLS (1 << 24)
+int dg_totals_noalloc(int dim, int n_basis, int64_t n_cells, int precision, double dx0,
+                      const int32_t* levels_dev, const void* W_dev, double* totals_dev,
+                      void* stream);
+
 /* Reads and clears the device status word (DG_OK, DG_ERR_NONPHYSICAL, ...).
  * Synchronises the handle's last stream. */
 int dg_status(dg_handle* h, int* device_status_host);

@@ -1,0 +1,117 @@
+// dg_totals_noalloc: the conserved-totals reduction without any device
+// allocation and without a handle.
+//
+// Who needs it: code that cannot call cudaMalloc -- for instance a host
+// application that owns every device allocation and forbids libraries from
+// allocating, or code running while a stream is captured in global mode,
+// where allocation calls are not permitted.  Such callers cannot create a
+// dg_handle (dg_create allocates its tables and scratch), yet may hold a
+// state array and need its totals.  The per-block partial sums, which the
+// handle-based dg_totals keeps in handle-owned scratch, live here in one
+// file-scope device array of fixed size instead.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+
+#include "dg.h"
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kMaxVars = 5;
+constexpr int64_t kMaxCells = DG_NOALLOC_MAX_CELLS;
+constexpr int kMaxBlocks = (int)((kMaxCells + kThreads - 1) / kThreads);
+
+// Scratch: one partial sum per (block, variable).  Every GPU that loads the
+// library holds this array until the process exits.  Each block writes its
+// own slots before the second pass reads them, so nothing needs clearing.
+static __device__ __align__(256) double g_partials[kMaxBlocks * kMaxVars];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+double* g_ptr[kMaxDevices] = {};
+
+// Same fixed pairwise order as the handle-based reduction.
+__device__ __forceinline__ double block_sum(double x, double* sh) {
+  sh[threadIdx.x] = x;
+  __syncthreads();
+  for (int s = kThreads / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  const double r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+template <typename real>
+__global__ void __launch_bounds__(kThreads)
+    totals_partials(const real* W, int nv, int nb, int nc, int dim, double dx0,
+                    const int32_t* levels, double* partial) {
+  __shared__ double sh[kThreads];
+  const int c = blockIdx.x * kThreads + threadIdx.x;
+  double vol = 0.0;
+  if (c < nc) {
+    const double dx = ldexp(dx0, levels ? -(int)levels[c] : 0);
+    vol = dim == 2 ? dx * dx : dx * dx * dx;
+  }
+  for (int v = 0; v < nv; ++v) {
+    const double x = (c < nc) ? vol * (double)W[(size_t)v * nb * nc + c] : 0.0;
+    const double s = block_sum(x, sh);
+    if (threadIdx.x == 0) partial[(size_t)blockIdx.x * nv + v] = s;
+  }
+}
+
+__global__ void totals_final(const double* partial, int nblocks, int nv, double* out) {
+  const int v = threadIdx.x;
+  if (v >= nv) return;
+  double s = 0.0;
+  for (int b = 0; b < nblocks; ++b) s += partial[(size_t)b * nv + v];
+  out[v] = s;
+}
+
+// Device address of the scratch array on the current device (set-up once
+// per device; the host-side symbol itself is not a device address).
+cudaError_t scratch_on_current_device(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_partials);
+    if (e != cudaSuccess) return e;
+    g_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_ptr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" int dg_totals_noalloc(int dim, int n_basis, int64_t n_cells, int precision, double dx0,
+                                 const int32_t* levels_dev, const void* W_dev, double* totals_dev,
+                                 void* stream) {
+  if (dim != 2 && dim != 3) return DG_ERR_ARG;
+  if (n_basis < 1 || n_cells < 0 || !(dx0 > 0.0) || !W_dev || !totals_dev) return DG_ERR_ARG;
+  if (precision != DG_FP64 && precision != DG_FP32) return DG_ERR_ARG;
+  if (n_cells > kMaxCells) return DG_ERR_ARG;  // beyond the fixed scratch
+  const int nv = dim + 2;
+  const int nc = (int)n_cells;
+  const int nblocks = (nc + kThreads - 1) / kThreads;
+  double* partial = nullptr;
+  if (scratch_on_current_device(&partial) != cudaSuccess) return DG_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (nblocks > 0) {
+    if (precision == DG_FP64)
+      totals_partials<double><<<nblocks, kThreads, 0, s>>>(static_cast<const double*>(W_dev), nv,
+                                                           n_basis, nc, dim, dx0, levels_dev, partial);
+    else
+      totals_partials<float><<<nblocks, kThreads, 0, s>>>(static_cast<const float*>(W_dev), nv,
+                                                          n_basis, nc, dim, dx0, levels_dev, partial);
+  }
+  totals_final<<<1, 32, 0, s>>>(partial, nblocks, nv, totals_dev);
+  return cudaGetLastError() == cudaSuccess ? DG_OK : DG_ERR_CUDA;
+}

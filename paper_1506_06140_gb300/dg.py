@@ -23,7 +23,7 @@ EXPORTS = ["dg_default_options", "dg_create", "dg_destroy", "dg_last_error", "dg
            "dg_quad_points", "dg_l1_points", "dg_project", "dg_rhs", "dg_compute_dt",
            "dg_rk_step", "dg_advance", "dg_rk_step_adjoint", "dg_limit", "dg_totals",
            "dg_l1_density", "dg_node_weights", "dg_neighbor_table", "dg_cell_levels",
-           "dg_status", "dg_profile_begin", "dg_profile_end"]
+           "dg_status", "dg_profile_begin", "dg_profile_end", "dg_totals_noalloc"]
 KERNEL_KINDS = ["face", "cell", "limit", "dt", "other"]
 
 
@@ -80,12 +80,34 @@ def load(path=LIB_PATH):
     L.dg_neighbor_table.argtypes = [vp, i32p]
     L.dg_cell_levels.argtypes = [vp, i32p]
     L.dg_status.argtypes = [vp, C.POINTER(C.c_int)]
+    L.dg_totals_noalloc.argtypes = [C.c_int, C.c_int, C.c_int64, C.c_int, C.c_double, vp, vp,
+                                     vp, vp]
     L.dg_profile_begin.argtypes = [vp]
     L.dg_profile_end.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_int]
     for name in EXPORTS:
         getattr(L, name).restype = C.c_int if name != "dg_last_error" else C.c_char_p
     _lib = L
     return L
+
+
+def totals_noalloc(W, dim, dx0, levels=None, out=None):
+    """Conserved totals of a state without a handle and without any device
+    allocation inside the library (see dg_totals_noalloc in include/dg.h).
+    W: [dim+2][N][cells] float64/float32 CUDA tensor; levels: optional int32
+    CUDA tensor of per-cell refinement levels; out: float64 CUDA tensor [dim+2]."""
+    L = load()
+    assert W.is_cuda and W.is_contiguous() and W.dim() == 3 and W.shape[0] == dim + 2
+    prec = PRECISIONS["fp64"] if W.dtype == torch.float64 else PRECISIONS["fp32"]
+    if levels is not None:
+        assert levels.is_cuda and levels.dtype == torch.int32 and levels.numel() == W.shape[2]
+    if out is None:
+        out = torch.empty(dim + 2, dtype=torch.float64, device=W.device)
+    r = L.dg_totals_noalloc(dim, W.shape[1], W.shape[2], prec, float(dx0),
+                            _ptr(levels) if levels is not None else None, _ptr(W), _ptr(out),
+                            _stream())
+    if r != DG_OK:
+        raise DGError(r, "dg_totals_noalloc failed")
+    return out
 
 
 def _stream():
