@@ -35,16 +35,49 @@ N_BASIS, NV, DIM = 10, 4, 2
 L2_BYTES = 129 * 2 ** 20
 
 
-def workload_config(precision):
-    return {"workload": "isentropic vortex 2D, 256x256 periodic [-5,5]^2, k=3 (10 coeffs/cell/var), "
-                        "SSP-RK4 (5 stages), no limiter, CFL 0.2",
-            "cells": N_CELLS_1D ** 2, "k": K_DEG, "basis": N_BASIS, "rk_stages": STAGES,
+WORKLOADS = {
+    "vortex": dict(
+        name="isentropic vortex 2D, 256x256 periodic [-5,5]^2, k=3 (10 coeffs/cell/var), "
+             "SSP-RK4 (5 stages), no limiter, CFL 0.2",
+        dim=2, k=3, rk=4, stages=5, limiter="none", positivity=False, precisions=("fp64", "fp32"),
+        tag="vortex256_k3"),
+    "sedov3d": dict(
+        name="Sedov blast 3D, 64^3 base + central 32^3 refined once (491,520 cells), k=2 "
+             "(10 coeffs/cell/var), SSP-RK3, characteristic TVB limiter + positivity limiter, "
+             "FP32 state with FP64 totals / positivity check",
+        dim=3, k=2, rk=3, stages=3, limiter="characteristic", positivity=True,
+        precisions=("fp32",), tag="sedov3d_k2"),
+}
+
+
+def workload_config(wk, precision, cells):
+    W = WORKLOADS[wk]
+    return {"workload": W["name"], "cells": cells, "k": W["k"], "rk_stages": W["stages"],
             "precision": precision, "l2": "flushed between timed steps (256 MiB write)"}
 
 
 def mesh(n=N_CELLS_1D, half=5.0):
     from paper_1506_06140_gb300 import workloads as wl
     return wl.mesh_uniform(2, [n, n], [-half, -half], [half, half])
+
+
+def make_problem(wk, precision):
+    """Solver and initial weights (on the device) of a workload."""
+    import torch
+    from paper_1506_06140_gb300 import dg
+    from paper_1506_06140_gb300 import workloads as wl
+    W = WORKLOADS[wk]
+    if wk == "vortex":
+        m, ic = mesh(), wl.vortex
+    else:
+        m, ic = wl.mesh_two_level_3d(64, 16, 47), wl.sedov3d
+    s = dg.Solver(m, W["k"], 1.4, rk_order=W["rk"], cfl=CFL, limiter=W["limiter"],
+                  positivity=W["positivity"], precision=precision)
+    U = ic(s.quad_points().cpu().numpy())  # closed-form IC at the Gauss points
+    W0 = s.project(torch.as_tensor(U))
+    if W["limiter"] != "none" or W["positivity"]:
+        s.limit(W0)
+    return s, W0
 
 
 # ---------------------------------------------------------------------------
@@ -56,18 +89,29 @@ def shape(dim, k):
     return N, Q, QF, nv
 
 
-def flops_cell_kernel(dim, k):
-    """Cell kernel flops per cell: modal->nodal (2 Q N nv), Euler fluxes
-    (~(8 + 8 dim) per point), volume contraction (2 dim Q N nv), surface
-    integral (2 * 2 dim QF N nv), stage combination (3 N nv)."""
-    N, Q, QF, nv = shape(dim, k)
-    return 2 * Q * N * nv + (8 + 8 * dim) * Q + 2 * dim * Q * N * nv + 4 * dim * QF * N * nv + 3 * N * nv
+def kernel_flops(dim, k):
+    """Flops of the sum-factorised kernels: (cell kernel per cell, face kernel per face).
 
-
-def flops_face_kernel_per_face(dim, k):
-    """Face kernel flops per face: two traces per point (2 * 2 N nv) and HLLC (~90)."""
+    Per variable (FMA counts; K1 = k+1, N2 = K1 (K1+1) / 2 pairs (a,b)):
+      modal->nodal   2D: N K1 + K1^3          3D: N K1 + N2 K1^2 + K1^4
+      volume / dir   2D: k K1^2 + (N-K1) K1   3D: k K1^3 + (N2-K1) K1^2 + (N-N2) K1
+      surface / side 2D: K1^2 + N             3D: K1^3 + N2 K1 + N
+      face trace     2D: N + K1^2             3D: N + N2 K1 + K1^3
+    plus Euler fluxes (18 | 27 flop per point), HLLC (90 | 100 flop per face
+    point) and the stage combination (5 flop per weight)."""
     N, Q, QF, nv = shape(dim, k)
-    return QF * (4 * N * nv + 90)
+    K1 = k + 1
+    if dim == 2:
+        m2n, vol = N * K1 + K1 ** 3, dim * (k * K1 * K1 + (N - K1) * K1)
+        surf, trace, flux_pt, hllc_pt = 2 * dim * (K1 * K1 + N), N + K1 * K1, 18, 90
+    else:
+        N2 = K1 * (K1 + 1) // 2
+        m2n = N * K1 + N2 * K1 * K1 + K1 ** 4
+        vol = dim * (k * K1 ** 3 + (N2 - K1) * K1 * K1 + (N - N2) * K1)
+        surf, trace, flux_pt, hllc_pt = 2 * dim * (K1 ** 3 + N2 * K1 + N), N + N2 * K1 + K1 ** 3, 27, 100
+    cell = 2 * nv * (m2n + vol + surf) + flux_pt * Q + 5 * N * nv
+    face = 2 * 2 * nv * trace + hllc_pt * QF
+    return cell, face
 
 
 def state_bytes_per_cell(dim, k, esize):
@@ -92,10 +136,14 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.th = threading.Thread(target=self._read, daemon=True)
             self.th.start()
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 10.0 and self.proc.poll() is None:
+                time.sleep(0.01)
+            self.skip = len(self.lines)  # samples taken before the measured region
         except OSError:
             self.proc = None
         return self
@@ -116,7 +164,8 @@ class ClockSampler:
     def summary(self):
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        lines = self.lines[getattr(self, "skip", 0):] or self.lines[-1:]
+        for ln in lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -190,21 +239,18 @@ def run_gpu(args, rank, world, local_rank):
 
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
     results = {}
-    for precision in ("fp64", "fp32"):
-        s = dg.Solver(mesh(), K_DEG, 1.4, rk_order=RK_ORDER, cfl=CFL, precision=precision)
-        U = wl.vortex(s.quad_points().cpu().numpy())  # closed-form IC at the Gauss points
-        W0 = s.project(torch.as_tensor(U))
+    for precision in args.precisions:
+        s, W0 = make_problem(args.workload, precision)
         W = W0.clone()
-        for _ in range(args.warmup):
-            s.rk_step(W)
-        torch.cuda.synchronize()
-        barrier()
         stream = torch.cuda.current_stream()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(args.steps)]
-        s.profile_begin()
-        with ClockSampler(local_rank) as clk:
+        with ClockSampler(local_rank) as clk:  # sampling spans the warm-up and the timed steps
+            for _ in range(args.warmup):
+                s.rk_step(W)
             torch.cuda.synchronize()
+            barrier()
+            s.profile_begin()
             for i in range(args.steps):
                 flush.zero_()  # evict the working set from L2 before each timed step
                 ev[i][0].record(stream)
@@ -238,46 +284,51 @@ def run_gpu(args, rank, world, local_rank):
 
 def summarize(args, results, world):
     hbm, peak_kind = peaks()
+    wk = WORKLOADS[args.workload]
+    dim, k, stages = wk["dim"], wk["k"], wk["stages"]
+    N, _, _, nv = shape(dim, k)
     lines = {}
     for precision, r in results.items():
         cells = r["n_cells"]
-        dof_updates = world * cells * N_BASIS * STAGES * args.steps
+        dof_updates = world * cells * N * stages * args.steps
         value = dof_updates / (r["ms"] * 1e-3)
         prof = r["prof"]
         launches = sum(c for c, _ in prof.values())
-        # dominant kernel of the timed region
-        kind = max(prof, key=lambda k: prof[k][1])
+        # roofline of the dominant kernel of the timed region
+        kind = max(prof, key=lambda kk: prof[kk][1])
         n_launch, kms = prof[kind]
         avg_s = kms / max(n_launch, 1) * 1e-3
         esize = 8 if precision == "fp64" else 4
-        kname = {"cell": "cell_update_kernel", "face": "face_flux_kernel"}.get(kind, kind)
-        wlname = "vortex256_k3_" + precision
-        if precision == "fp64":
-            if kind == "cell":
-                fl = flops_cell_kernel(DIM, K_DEG) * cells
-            else:
-                fl = flops_face_kernel_per_face(DIM, K_DEG) * DIM * cells
+        kname = {"cell": "cell_update_kernel", "face": "face_flux_kernel",
+                 "limit": "limit_kernel"}.get(kind, kind)
+        tag = "%s_%s" % (wk["tag"], precision)
+        if precision == "fp64" and kind in ("cell", "face"):
+            fc, ff = kernel_flops(dim, k)
+            fl = fc * cells if kind == "cell" else ff * dim * cells
             achieved = fl / avg_s / 1e12
             roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                    "peak_source": "nominal FP64 rate from unit counts and max clock",
-                    "traffic": dram_traffic(kname, wlname), "algorithmic_per_launch": fl}
+                    "peak_source": "FP64 rate from unit counts and max clock (152 SMs x 2 DFMA/clk "
+                                   "x 2 flop x 2.07 GHz); measured probe 1.198",
+                    "traffic": dram_traffic(kname, tag), "algorithmic_per_launch": fl,
+                    "algorithmic_unit": "flop (sum-factorised count, DESIGN.md)"}
         else:
-            # HBM roof of the stage: the minimum a stage moves is 3 state arrays
-            stage_s = sum(prof[k][1] for k in ("face", "cell")) / max(prof["cell"][0], 1) * 1e-3
-            byt = 3 * state_bytes_per_cell(DIM, K_DEG, esize) * cells
-            achieved = byt / stage_s / 1e9
-            roof = {"bound": "hbm", "kernel": "stage (face_flux_kernel + cell_update_kernel)",
-                    "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                    "peak_source": peak_kind, "traffic": dram_traffic(kname, wlname),
-                    "algorithmic_per_launch": byt}
+            # HBM: a launch of the dominant kernel processes one stage of the mesh,
+            # whose algorithmic traffic is 3 state arrays (read U_i and w^n, write U_i+1)
+            byt = 3 * state_bytes_per_cell(dim, k, esize) * cells
+            achieved = byt / avg_s / 1e9
+            roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm,
+                    "unit": "GB/s", "frac": achieved / hbm, "peak_source": peak_kind,
+                    "traffic": dram_traffic(kname, tag), "algorithmic_per_launch": byt,
+                    "algorithmic_unit": "bytes (3 state arrays per stage)"}
         e2e_value = dof_updates / (r["ms_e2e"] * 1e-3)
         lines[precision] = {
             "value": value, "ms_per_step": r["ms"] / args.steps, "roofline": roof,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": r["state_bytes"],
                     "d2h_bytes_per_step": r["state_bytes"]},
             "gpu_launches": launches, "clocks": r["clocks"],
-            "kernel_ms": {k: v[1] for k, v in prof.items()},
+            "kernel_ms": {kk: v[1] for kk, v in prof.items()},
+            "cells": cells,
         }
     return lines
 
@@ -329,7 +380,7 @@ def reference_arm(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config("fp64"),
+            "data": "synthetic", "config": workload_config("vortex", "fp64", N_CELLS_1D ** 2),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -344,7 +395,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="both", choices=["both", "fp64", "fp32"],
+                    help="run one precision only (profiling); the JSON line needs both")
+    ap.add_argument("--workload", default="vortex", choices=sorted(WORKLOADS))
     args = ap.parse_args()
+    wprec = WORKLOADS[args.workload]["precisions"]
+    args.precisions = wprec if args.precision == "both" else (args.precision,)
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -358,11 +414,22 @@ def main():
     if rank != 0:
         return 0
     lines = summarize(args, results, world)
+    if args.workload != "vortex" or len(lines) == 1:
+        prec = args.precisions[0]
+        one = lines[prec]
+        out = {"metric": METRIC, "value": one["value"], "unit": UNIT, "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": one["ms_per_step"],
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+               "dtype": "f64" if prec == "fp64" else "f32", "data": "synthetic",
+               "config": workload_config(args.workload, prec, one["cells"])}
+        out.update({kk: one[kk] for kk in ("roofline", "e2e", "gpu_launches", "clocks", "kernel_ms")})
+        print(json.dumps(out), flush=True)
+        return 0
     head = lines["fp64"]
     out = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": workload_config("fp64"),
+           "data": "synthetic", "config": workload_config("vortex", "fp64", head["cells"]),
            "roofline": head["roofline"], "e2e": head["e2e"], "gpu_launches": head["gpu_launches"],
            "clocks": head["clocks"], "kernel_ms": head["kernel_ms"],
            "variants": {"fp32": {k: lines["fp32"][k] for k in

@@ -141,8 +141,14 @@ int dg_advance(dg_handle* h, void* W_dev, int n_steps, double* dt_hist_dev, void
 
 /* Adjoint of one unlimited step with a frozen timestep dt (> 0):
  * lam_n = (d W_{n+1} / d W_n)^T lam_np1, where W_n_dev is the checkpointed
- * state the step started from.  The stage states are recomputed from W_n.
- * Requires slope_limiter = NONE and positivity = 0. */
+ * state the step started from (the paper has no adjoint; this is the exact
+ * transpose of the Butcher-form step of Appendix D).  The stage states are
+ * recomputed from W_n; the reverse sweep applies the transposed linearised
+ * right-hand side (HLLC and Euler-flux Jacobians by forward-mode dual
+ * numbers).  lam_n_dev may alias lam_np1_dev.  Requires slope_limiter = NONE
+ * and positivity = 0 (DG_ERR_ARG otherwise).  The first call allocates the
+ * handle's adjoint work arrays (2 s state arrays for s stages, plus the face
+ * cotangents). */
 int dg_rk_step_adjoint(dg_handle* h, const void* W_n_dev, double dt, const void* lam_np1_dev,
                        void* lam_n_dev, void* stream);
 
@@ -177,7 +183,7 @@ int dg_cell_levels(const dg_handle* h, int32_t* host_out);
  * returns, per kernel kind, the number of launches and the summed device
  * time in milliseconds. */
 enum { DG_KERNEL_FACE = 0, DG_KERNEL_CELL = 1, DG_KERNEL_LIMIT = 2, DG_KERNEL_DT = 3,
-       DG_KERNEL_OTHER = 4, DG_KERNEL_KINDS = 5 };
+       DG_KERNEL_OTHER = 4, DG_KERNEL_ADJOINT = 5, DG_KERNEL_KINDS = 6 };
 int dg_profile_begin(dg_handle* h);
 int dg_profile_end(dg_handle* h, int* launches, double* total_ms, int n_kinds);
 

@@ -49,6 +49,9 @@ void orc_positivity_limit(const orc_problem* p, double* W);
 void orc_limit(const orc_problem* p, double* W);
 void orc_totals(const orc_problem* p, const double* W, double* totals);
 double orc_l1_density(const orc_problem* p, const double* W, const double* rho_exact);
+/* per-cell evaluations for sampled comparisons: out[k][v][l] for cells[k] */
+void orc_rhs_cells(const orc_problem* p, const double* W, const int32_t* cells, int n, double* out);
+void orc_limit_cells(const orc_problem* p, const double* W, const int32_t* cells, int n, double* out);
 void orc_node_weights(const orc_problem* p, const double* W, double* Wnode);
 void orc_rk_step_jvp(const orc_problem* p, const double* W, const double* V, double dt,
                      double* W_out, double* JV);

@@ -82,6 +82,14 @@ void orc_totals(const orc_problem* p, const double* W, double* totals) { p->P.to
 double orc_l1_density(const orc_problem* p, const double* W, const double* rho_exact) {
   return p->P.l1_density(W, rho_exact);
 }
+void orc_rhs_cells(const orc_problem* p, const double* W, const int32_t* cells, int n, double* out) {
+  const size_t per = (size_t)p->P.nv * p->P.N;
+  for (int i = 0; i < n; ++i) p->P.rhs_one(W, cells[i], out + per * i);
+}
+void orc_limit_cells(const orc_problem* p, const double* W, const int32_t* cells, int n, double* out) {
+  const size_t per = (size_t)p->P.nv * p->P.N;
+  for (int i = 0; i < n; ++i) p->P.limit_one(W, cells[i], out + per * i);
+}
 void orc_node_weights(const orc_problem* p, const double* W, double* Wnode) {
   p->P.node_weights(W, Wnode);
 }

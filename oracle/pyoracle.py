@@ -55,6 +55,8 @@ def lib():
         L.orc_l1_density.restype = C.c_double
         L.orc_l1_density.argtypes = [C.c_void_p, _D, _D]
         L.orc_node_weights.argtypes = [C.c_void_p, _D, _D]
+        L.orc_rhs_cells.argtypes = [C.c_void_p, _D, _I32, C.c_int, _D]
+        L.orc_limit_cells.argtypes = [C.c_void_p, _D, _I32, C.c_int, _D]
         L.orc_rk_step_jvp.argtypes = [C.c_void_p, _D, _D, C.c_double, _D, _D]
         L.orc_gauss_legendre.argtypes = [C.c_int, _D, _D]
         L.orc_gauss_lobatto.argtypes = [C.c_int, _D, _D]
@@ -202,6 +204,22 @@ class Oracle:
         W, rho_exact = _f64(W), _f64(rho_exact)
         assert rho_exact.shape == (self.nq_l1, self.n_cells)
         return lib().orc_l1_density(self._h, _d(W), _d(rho_exact))
+
+    def rhs_cells(self, W, cells):
+        """dW/dt of the listed cells only, [nv][N][len(cells)]."""
+        W = _f64(W)
+        cells = np.ascontiguousarray(cells, dtype=np.int32)
+        out = np.zeros((len(cells), self.nv, self.N))
+        lib().orc_rhs_cells(self._h, _d(W), cells.ctypes.data_as(_I32), len(cells), _d(out))
+        return np.moveaxis(out, 0, 2)
+
+    def limit_cells(self, W, cells):
+        """Limited weights (slope then positivity) of the listed cells, [nv][N][len(cells)]."""
+        W = _f64(W)
+        cells = np.ascontiguousarray(cells, dtype=np.int32)
+        out = np.zeros((len(cells), self.nv, self.N))
+        lib().orc_limit_cells(self._h, _d(W), cells.ctypes.data_as(_I32), len(cells), _d(out))
+        return np.moveaxis(out, 0, 2)
 
     def node_weights(self, W):
         W = _f64(W)

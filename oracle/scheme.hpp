@@ -306,6 +306,74 @@ struct Problem {
     }
   }
 
+  // dw/dt of one cell (the same terms as rhs, gathered from the cell's side:
+  // every face of the cell, and each fine sub-face of a side with a finer
+  // neighbour, is evaluated at its own Gauss points).  Output [v][l].
+  void rhs_one(const double* W, int c, double* out) const {
+    const int nc = mesh.ncells;
+    std::vector<double> V((size_t)nv * N, 0.0), S((size_t)nv * N, 0.0);
+    double u[5], f[5], uc[5], un[5], F[5], tmp[64];
+    for (int q = 0; q < vol.n; ++q) {
+      eval(W, c, &phi_vol[(size_t)q * N], u);
+      for (int a = 0; a < dim; ++a) {
+        euler_flux(dim, gamma, u, a, f);
+        for (int v = 0; v < nv; ++v)
+          for (int j = 0; j < N; ++j)
+            V[(size_t)v * N + j] += f[v] * (dphi_vol[((size_t)a * vol.n + q) * N + j] * vol.w[q]);
+      }
+    }
+    const double sub_w = std::ldexp(1.0, -(dim - 1));
+    for (int a = 0; a < dim; ++a)
+      for (int s = 0; s < 2; ++s) {
+        const int nb = mesh.nbr[(size_t)(2 * a + s) * nc + c];
+        const double sc = s ? 1.0 : -1.0;
+        // list of (own variant, neighbour cell, neighbour variant, weight factor)
+        std::vector<std::array<int, 3>> parts;
+        std::vector<double> wf;
+        if (nb == -1) {
+          parts.push_back({0, -1, 0});
+          wf.push_back(1.0);
+        } else if (nb <= -2) {
+          const auto& kids = mesh.node_children[-(nb + 2)];
+          for (int quad = 0; quad < (1 << (dim - 1)); ++quad) {
+            int ch = s ? 0 : (1 << a);  // the layer of the node touching this side
+            for (int i = 0; i < dim - 1; ++i)
+              if ((quad >> i) & 1) ch |= 1 << tang(a, i);
+            parts.push_back({1 + quad, kids[ch], 0});
+            wf.push_back(sub_w);
+          }
+        } else if (mesh.level[nb] == mesh.level[c]) {
+          parts.push_back({0, nb, 0});
+          wf.push_back(1.0);
+        } else {
+          int quad = 0;
+          for (int i = 0; i < dim - 1; ++i) quad |= (mesh.coord[c][tang(a, i)] & 1) << i;
+          parts.push_back({0, nb, 1 + quad});
+          wf.push_back(1.0);
+        }
+        for (size_t p = 0; p < parts.size(); ++p) {
+          const int own_var = parts[p][0], n = parts[p][1], n_var = parts[p][2];
+          for (int q = 0; q < nfq; ++q) {
+            for (int l = 0; l < N; ++l) tmp[l] = pf(a, s, own_var, q, l);
+            eval(W, c, tmp, uc);
+            if (n < 0) {
+              for (int v = 0; v < nv; ++v) un[v] = uc[v];
+            } else {
+              for (int l = 0; l < N; ++l) tmp[l] = pf(a, 1 - s, n_var, q, l);
+              eval(W, n, tmp, un);
+            }
+            if (s == 1) hllc(dim, gamma, uc, un, a, F);
+            else hllc(dim, gamma, un, uc, a, F);
+            for (int v = 0; v < nv; ++v)
+              for (int j = 0; j < N; ++j)
+                S[(size_t)v * N + j] += F[v] * (sc * pf(a, s, own_var, q, j) * fw[q] * wf[p]);
+          }
+        }
+      }
+    const double pre = std::ldexp(1.0, 1 - dim) / mesh.dx(c);
+    for (size_t i = 0; i < V.size(); ++i) out[i] = pre * (V[i] - S[i]);
+  }
+
   // Timestep (eq. time_step; eq. time_step_pos when the positivity limiter
   // is on), from the cell-mean state, minimum over all cells.
   double compute_dt(const double* W) const {
@@ -378,49 +446,62 @@ struct Problem {
   void slope_limit(double* W) const {
     if (limiter == LIM_NONE || k == 0) return;
     const std::vector<double> W0(W, W + size());
-    const double s3 = std::sqrt(3.0);
+    std::vector<double> cellw((size_t)nv * N);
     for (int c = 0; c < mesh.ncells; ++c) {
-      double mean[5];
-      for (int v = 0; v < nv; ++v) mean[v] = W0[idx(v, 0, c)];
-      bool changed = false;
-      double ct[3][5];
-      double Rm[3][25];
-      for (int a = 0; a < dim; ++a) {
-        double L[25], R[25];
-        if (limiter == LIM_CHARACTERISTIC) {
-          eigen_matrices(dim, gamma, mean, a, L, R);
-        } else {
-          for (int i = 0; i < nv * nv; ++i) L[i] = R[i] = 0.0;
-          for (int i = 0; i < nv; ++i) L[i * nv + i] = R[i * nv + i] = 1.0;
-        }
-        for (int i = 0; i < nv * nv; ++i) Rm[a][i] = R[i];
-        double mm[5], mp[5];
-        neighbour_mean(W0.data(), c, a, 0, mm);
-        neighbour_mean(W0.data(), c, a, 1, mp);
-        for (int i = 0; i < nv; ++i) {
-          double cs = 0.0, dm = 0.0, dp = 0.0;
-          for (int v = 0; v < nv; ++v) {
-            cs += L[i * nv + v] * W0[idx(v, 1 + a, c)];
-            dm += L[i * nv + v] * (mean[v] - mm[v]);
-            dp += L[i * nv + v] * (mp[v] - mean[v]);
-          }
-          const double arg = s3 * cs;
-          const double lim = minmodB(arg, beta * dm, beta * dp, mesh.dx(c));
-          if (lim != arg) changed = true;
-          ct[a][i] = lim / s3;
-        }
-      }
-      if (!changed) continue;
-      for (int a = 0; a < dim; ++a)
-        for (int v = 0; v < nv; ++v) {
-          double s = 0.0;
-          for (int i = 0; i < nv; ++i) s += Rm[a][v * nv + i] * ct[a][i];
-          W[idx(v, 1 + a, c)] = s;
-        }
-      for (int l = 0; l < N; ++l)
-        if (basis.degree(l) >= 2)
-          for (int v = 0; v < nv; ++v) W[idx(v, l, c)] = 0.0;
+      if (!slope_limit_cell(W0.data(), c, cellw.data())) continue;
+      for (int v = 0; v < nv; ++v)
+        for (int l = 0; l < N; ++l) W[idx(v, l, c)] = cellw[(size_t)v * N + l];
     }
+  }
+
+  // Slope limiting of cell c with inputs from W0; writes the cell's weights
+  // [v][l] to out and returns true if they changed.
+  bool slope_limit_cell(const double* W0, int c, double* out) const {
+    for (int v = 0; v < nv; ++v)
+      for (int l = 0; l < N; ++l) out[(size_t)v * N + l] = W0[idx(v, l, c)];
+    if (limiter == LIM_NONE || k == 0) return false;
+    const double s3 = std::sqrt(3.0);
+    double mean[5];
+    for (int v = 0; v < nv; ++v) mean[v] = W0[idx(v, 0, c)];
+    bool changed = false;
+    double ct[3][5];
+    double Rm[3][25];
+    for (int a = 0; a < dim; ++a) {
+      double L[25], R[25];
+      if (limiter == LIM_CHARACTERISTIC) {
+        eigen_matrices(dim, gamma, mean, a, L, R);
+      } else {
+        for (int i = 0; i < nv * nv; ++i) L[i] = R[i] = 0.0;
+        for (int i = 0; i < nv; ++i) L[i * nv + i] = R[i * nv + i] = 1.0;
+      }
+      for (int i = 0; i < nv * nv; ++i) Rm[a][i] = R[i];
+      double mm[5], mp[5];
+      neighbour_mean(W0, c, a, 0, mm);
+      neighbour_mean(W0, c, a, 1, mp);
+      for (int i = 0; i < nv; ++i) {
+        double cs = 0.0, dm = 0.0, dp = 0.0;
+        for (int v = 0; v < nv; ++v) {
+          cs += L[i * nv + v] * W0[idx(v, 1 + a, c)];
+          dm += L[i * nv + v] * (mean[v] - mm[v]);
+          dp += L[i * nv + v] * (mp[v] - mean[v]);
+        }
+        const double arg = s3 * cs;
+        const double lim = minmodB(arg, beta * dm, beta * dp, mesh.dx(c));
+        if (lim != arg) changed = true;
+        ct[a][i] = lim / s3;
+      }
+    }
+    if (!changed) return false;
+    for (int a = 0; a < dim; ++a)
+      for (int v = 0; v < nv; ++v) {
+        double s = 0.0;
+        for (int i = 0; i < nv; ++i) s += Rm[a][v * nv + i] * ct[a][i];
+        out[(size_t)v * N + 1 + a] = s;
+      }
+    for (int l = 0; l < N; ++l)
+      if (basis.degree(l) >= 2)
+        for (int v = 0; v < nv; ++v) out[(size_t)v * N + l] = 0.0;
+    return true;
   }
 
   // Positivity limiter (Sec. 3.4, after Zhang & Shu 2010).  Points: the set S
@@ -485,32 +566,55 @@ struct Problem {
 
   void positivity_limit(double* W) const {
     if (!positivity) return;
+    std::vector<double> cellw((size_t)nv * N);
     for (int c = 0; c < mesh.ncells; ++c) {
-      const auto pts = positivity_points(c);
-      double u[5], ub[5];
-      for (int v = 0; v < nv; ++v) ub[v] = W[idx(v, 0, c)];
-      std::vector<double> row(N);
-      double rmin = 1e300;
-      for (const auto& x : pts) {
-        for (int l = 0; l < N; ++l) row[l] = basis.phi(l, x.data());
-        eval(W, c, row.data(), u);
-        rmin = std::min(rmin, u[0]);
-      }
-      double th1 = 1.0;
-      if (rmin < eps) th1 = std::min(std::fabs((ub[0] - eps) / (ub[0] - rmin)), 1.0);
-      if (th1 < 1.0)
-        for (int l = 1; l < N; ++l) W[idx(0, l, c)] *= th1;
-      double th2 = 1.0;
-      for (const auto& x : pts) {
-        for (int l = 0; l < N; ++l) row[l] = basis.phi(l, x.data());
-        eval(W, c, row.data(), u);
-        if (pressure(dim, gamma, u) >= eps) continue;
-        th2 = std::min(th2, solve_tau(ub, u));
-      }
-      if (th2 < 1.0)
-        for (int v = 0; v < nv; ++v)
-          for (int l = 1; l < N; ++l) W[idx(v, l, c)] *= th2;
+      for (int v = 0; v < nv; ++v)
+        for (int l = 0; l < N; ++l) cellw[(size_t)v * N + l] = W[idx(v, l, c)];
+      positivity_limit_cell(c, cellw.data());
+      for (int v = 0; v < nv; ++v)
+        for (int l = 0; l < N; ++l) W[idx(v, l, c)] = cellw[(size_t)v * N + l];
     }
+  }
+
+  // positivity limiting of the weights w[v][l] of cell c, in place
+  void positivity_limit_cell(int c, double* w) const {
+    if (!positivity) return;
+    const auto pts = positivity_points(c);
+    double u[5], ub[5];
+    for (int v = 0; v < nv; ++v) ub[v] = w[(size_t)v * N];
+    std::vector<double> row(N);
+    auto at = [&](const std::array<double, 3>& x) {
+      for (int l = 0; l < N; ++l) row[l] = basis.phi(l, x.data());
+      for (int v = 0; v < nv; ++v) {
+        double s = 0.0;
+        for (int l = 0; l < N; ++l) s += w[(size_t)v * N + l] * row[l];
+        u[v] = s;
+      }
+    };
+    double rmin = 1e300;
+    for (const auto& x : pts) {
+      at(x);
+      rmin = std::min(rmin, u[0]);
+    }
+    double th1 = 1.0;
+    if (rmin < eps) th1 = std::min(std::fabs((ub[0] - eps) / (ub[0] - rmin)), 1.0);
+    if (th1 < 1.0)
+      for (int l = 1; l < N; ++l) w[l] *= th1;
+    double th2 = 1.0;
+    for (const auto& x : pts) {
+      at(x);
+      if (pressure(dim, gamma, u) >= eps) continue;
+      th2 = std::min(th2, solve_tau(ub, u));
+    }
+    if (th2 < 1.0)
+      for (int v = 0; v < nv; ++v)
+        for (int l = 1; l < N; ++l) w[(size_t)v * N + l] *= th2;
+  }
+
+  // slope then positivity limiting of one cell (inputs from W), -> out[v][l]
+  void limit_one(const double* W, int c, double* out) const {
+    slope_limit_cell(W, c, out);
+    positivity_limit_cell(c, out);
   }
 
   void limit(double* W) const {

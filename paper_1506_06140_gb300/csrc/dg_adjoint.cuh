@@ -1,0 +1,555 @@
+// Adjoint (transposed linearisation) of the DG time derivative, for the
+// adjoint of one RK step with a frozen timestep.  Not in the paper: the
+// derivative of the scheme of Sec. 2.4 with respect to the weights.
+//
+// dW/dt = pre (V - S) with V_j = sum_d sum_q f_d(u(q)) dphi_j/dxi_d(q) w_q and
+// S_j the surface integral of the HLLC fluxes.  For a cotangent G on dW/dt:
+//   volume : g_d(q) = pre sum_j G_j dphi_j/dxi_d(q) w_q,
+//            ubar(q) = sum_d (df_d/du)^T g_d,   Ubar_l += sum_q ubar(q) phi_l(q);
+//   faces  : Fbar(q) = w_q (pre_p t_p(q) - pre_m t_m(q)), t = trace of G,
+//            ubar_-/+ = (dF/du_-/+)^T Fbar,     Ubar_l += sum_q ubar(q) phi_l(q)
+// (the coarse side of a hanging face carries its sub-face weight 2^-(d-1)).
+// The Jacobian-transpose products are formed with forward-mode dual numbers
+// running the same flux code as the forward kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "dg_internal.h"
+#include "dg_physics.cuh"
+#include "dg_stage.cuh"
+
+namespace dgi {
+
+// value and one directional derivative
+template <typename T>
+struct Dual {
+  T v, d;
+  __device__ __forceinline__ Dual() : v(T(0)), d(T(0)) {}
+  __device__ __forceinline__ Dual(double x) : v(T(x)), d(T(0)) {}
+  __device__ __forceinline__ Dual(T x, T dx, int) : v(x), d(dx) {}
+  // found by argument-dependent lookup only, so it does not hide ::sqrt
+  friend __device__ __forceinline__ Dual sqrt(const Dual& a) {
+    const T s = ::sqrt(a.v);
+    return Dual(s, a.d / (T(2) * s), 0);
+  }
+};
+template <typename T>
+__device__ __forceinline__ Dual<T> operator+(const Dual<T>& a, const Dual<T>& b) {
+  return Dual<T>(a.v + b.v, a.d + b.d, 0);
+}
+template <typename T>
+__device__ __forceinline__ Dual<T> operator-(const Dual<T>& a, const Dual<T>& b) {
+  return Dual<T>(a.v - b.v, a.d - b.d, 0);
+}
+template <typename T>
+__device__ __forceinline__ Dual<T> operator-(const Dual<T>& a) {
+  return Dual<T>(-a.v, -a.d, 0);
+}
+template <typename T>
+__device__ __forceinline__ Dual<T> operator*(const Dual<T>& a, const Dual<T>& b) {
+  return Dual<T>(a.v * b.v, a.d * b.v + a.v * b.d, 0);
+}
+template <typename T>
+__device__ __forceinline__ Dual<T> operator/(const Dual<T>& a, const Dual<T>& b) {
+  const T q = a.v / b.v;
+  return Dual<T>(q, (a.d - q * b.d) / b.v, 0);
+}
+template <typename T>
+__device__ __forceinline__ Dual<T>& operator+=(Dual<T>& a, const Dual<T>& b) {
+  a = a + b;
+  return a;
+}
+template <typename T>
+__device__ __forceinline__ bool operator<(const Dual<T>& a, const Dual<T>& b) { return a.v < b.v; }
+template <typename T>
+__device__ __forceinline__ bool operator>(const Dual<T>& a, const Dual<T>& b) { return a.v > b.v; }
+template <typename T>
+__device__ __forceinline__ bool operator>=(const Dual<T>& a, const Dual<T>& b) { return a.v >= b.v; }
+template <typename T>
+__device__ __forceinline__ bool operator==(const Dual<T>& a, const Dual<T>& b) { return a.v == b.v; }
+
+// (dF/du)^T fbar for the HLLC flux, with respect to the minus (L) or plus side
+template <typename real, int DIM, int DIR, bool LEFT>
+__device__ __forceinline__ void hllc_vjp(const real* uL, const real* uR, real gamma,
+                                         const real* fbar, real* out) {
+  constexpr int NV = DIM + 2;
+  using D = Dual<real>;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    D dl[NV], dr[NV], F[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      dl[v] = D(uL[v], (LEFT && v == k) ? real(1) : real(0), 0);
+      dr[v] = D(uR[v], (!LEFT && v == k) ? real(1) : real(0), 0);
+    }
+    hllc_flux<D, DIM>(dl, dr, DIR, D(double(gamma)), F);
+    real s = real(0);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) s += fbar[v] * F[v].d;
+    out[k] = s;
+  }
+}
+
+// sum_d (df_d/du)^T g_d at one point
+template <typename real, int DIM>
+__device__ __forceinline__ void flux_vjp(const real* u, const real (*g)[DIM + 2], real g1,
+                                         real* out) {
+  constexpr int NV = DIM + 2;
+  using D = Dual<real>;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    D du[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) du[v] = D(u[v], v == k ? real(1) : real(0), 0);
+    real s = real(0);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      D f[NV];
+      euler_flux<D, DIM>(du, d, D(double(g1)), f);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) s += g[d][v] * f[v].d;
+    }
+    out[k] = s;
+  }
+}
+
+// point values of sum_l c_l prod_a TAB_a[e_a][i_a] with one table per axis
+// (the factorised modal->nodal with the tables chosen per axis)
+template <typename real, int DIM, int K>
+__device__ __forceinline__ void modal_to_nodal_axes(const real (&T0)[4][4], const real (&T1)[4][4],
+                                                    const real (&T2)[4][4], const real* w,
+                                                    real* u) {
+  constexpr int K1 = K + 1;
+  if constexpr (DIM == 2) {
+    real t[K1][K1];
+#pragma unroll
+    for (int a = 0; a <= K; ++a)
+#pragma unroll
+      for (int j = 0; j < K1; ++j) {
+        real s = real(0);
+#pragma unroll
+        for (int b = 0; b <= K - a; ++b) s += w[bidx<2>(a, b, 0)] * T1[b][j];
+        t[a][j] = s;
+      }
+#pragma unroll
+    for (int j = 0; j < K1; ++j)
+#pragma unroll
+      for (int i = 0; i < K1; ++i) {
+        real s = real(0);
+#pragma unroll
+        for (int a = 0; a <= K; ++a) s += T0[a][i] * t[a][j];
+        u[i + K1 * j] = s;
+      }
+  } else {
+    real t1[K1][K1][K1];
+#pragma unroll
+    for (int a = 0; a <= K; ++a)
+#pragma unroll
+      for (int b = 0; b <= K - a; ++b)
+#pragma unroll
+        for (int kz = 0; kz < K1; ++kz) {
+          real s = real(0);
+#pragma unroll
+          for (int c = 0; c <= K - a - b; ++c) s += w[bidx<3>(a, b, c)] * T2[c][kz];
+          t1[a][b][kz] = s;
+        }
+    real t2[K1][K1][K1];
+#pragma unroll
+    for (int a = 0; a <= K; ++a)
+#pragma unroll
+      for (int j = 0; j < K1; ++j)
+#pragma unroll
+        for (int kz = 0; kz < K1; ++kz) {
+          real s = real(0);
+#pragma unroll
+          for (int b = 0; b <= K - a; ++b) s += t1[a][b][kz] * T1[b][j];
+          t2[a][j][kz] = s;
+        }
+#pragma unroll
+    for (int kz = 0; kz < K1; ++kz)
+#pragma unroll
+      for (int j = 0; j < K1; ++j)
+#pragma unroll
+        for (int i = 0; i < K1; ++i) {
+          real s = real(0);
+#pragma unroll
+          for (int a = 0; a <= K; ++a) s += T0[a][i] * t2[a][j][kz];
+          u[i + K1 * (j + K1 * kz)] = s;
+        }
+  }
+}
+
+// transpose of modal_to_nodal: c_l += sum_q u(q) phi_l(q)
+template <typename real, int DIM, int K>
+__device__ __forceinline__ void nodal_to_modal(const real (&P)[4][4], const real* u, real* c) {
+  constexpr int K1 = K + 1;
+  if constexpr (DIM == 2) {
+#pragma unroll
+    for (int a = 0; a <= K; ++a)
+#pragma unroll
+      for (int j = 0; j < K1; ++j) {
+        real h = real(0);
+#pragma unroll
+        for (int i = 0; i < K1; ++i) h += u[i + K1 * j] * P[a][i];
+#pragma unroll
+        for (int b = 0; b <= K - a; ++b) c[bidx<2>(a, b, 0)] += h * P[b][j];
+      }
+  } else {
+#pragma unroll
+    for (int a = 0; a <= K; ++a) {
+      real h1[K1][K1];  // [j][kz]
+#pragma unroll
+      for (int j = 0; j < K1; ++j)
+#pragma unroll
+        for (int kz = 0; kz < K1; ++kz) {
+          real s = real(0);
+#pragma unroll
+          for (int i = 0; i < K1; ++i) s += u[i + K1 * (j + K1 * kz)] * P[a][i];
+          h1[j][kz] = s;
+        }
+#pragma unroll
+      for (int b = 0; b <= K - a; ++b)
+#pragma unroll
+        for (int kz = 0; kz < K1; ++kz) {
+          real h2 = real(0);
+#pragma unroll
+          for (int j = 0; j < K1; ++j) h2 += h1[j][kz] * P[b][j];
+#pragma unroll
+          for (int c3 = 0; c3 <= K - a - b; ++c3) c[bidx<3>(a, b, c3)] += h2 * P[c3][kz];
+        }
+    }
+  }
+}
+
+// transpose of face_trace: c_l += sum_q u(q) phi_l(face point q) (unweighted)
+template <typename real, int DIM, int K, int DIR, int S>
+__device__ __forceinline__ void trace_transpose(const Tab1D<real>& T, const real (&PT0)[4][4],
+                                                const real (&PT1)[4][4], const real* uq,
+                                                real* c) {
+  constexpr int K1 = K + 1;
+  if constexpr (DIM == 2) {
+#pragma unroll
+    for (int et = 0; et <= K; ++et) {
+      real g = real(0);
+#pragma unroll
+      for (int q = 0; q < K1; ++q) g += uq[q] * PT0[et][q];
+#pragma unroll
+      for (int ed = 0; ed <= K - et; ++ed)
+        c[DIR == 0 ? bidx<2>(ed, et, 0) : bidx<2>(et, ed, 0)] += T.PE[S][ed] * g;
+    }
+  } else {
+    constexpr int A = DIR == 0 ? 1 : 0;
+    constexpr int B = DIR == 2 ? 1 : 2;
+    real H[K1][K1];
+#pragma unroll
+    for (int ea = 0; ea <= K; ++ea)
+#pragma unroll
+      for (int qb = 0; qb < K1; ++qb) {
+        real s = real(0);
+#pragma unroll
+        for (int qa = 0; qa < K1; ++qa) s += uq[qa + K1 * qb] * PT0[ea][qa];
+        H[ea][qb] = s;
+      }
+#pragma unroll
+    for (int ea = 0; ea <= K; ++ea)
+#pragma unroll
+      for (int eb = 0; eb <= K - ea; ++eb) {
+        real s = real(0);
+#pragma unroll
+        for (int qb = 0; qb < K1; ++qb) s += H[ea][qb] * PT1[eb][qb];
+#pragma unroll
+        for (int ed = 0; ed <= K - ea - eb; ++ed) {
+          int e[3];
+          e[DIR] = ed;
+          e[A] = ea;
+          e[B] = eb;
+          c[bidx<3>(e[0], e[1], e[2])] += T.PE[S][ed] * s;
+        }
+      }
+  }
+}
+
+// ===========================================================================
+// Adjoint face kernel: FB faces x NV threads.
+//   1. thread (face, var): traces of U and of G on both sides -> shared memory;
+//   2. thread (face, point): Fbar, then ubar on both sides -> UB[side][var][point][face].
+
+template <typename real, int DIM, int K>
+struct AdjFaceTile {
+  using S = Shape<DIM, K>;
+  static constexpr int FB = 32;
+  static constexpr int THREADS = FB * S::NV;
+  static constexpr size_t SMEM = (size_t)4 * S::NV * S::QF * FB * sizeof(real);
+};
+
+template <typename real, int DIM, int K, int DIR>
+__device__ __forceinline__ void trace_of(const AdjointArgs<real>& a, const real* X, int cell,
+                                         int s, int var, int v, real* u) {
+  using S = Shape<DIM, K>;
+  const Tab1D<real>& T = a.t1;
+  const int nc = a.m.ncells;
+  real w[S::N];
+#pragma unroll
+  for (int l = 0; l < S::N; ++l) w[l] = X[(size_t)(v * S::N + l) * nc + cell];
+  if (var == 0) {
+    face_trace<real, DIM, K, DIR>(T, w, s, T.P, T.P, u);
+  } else {
+    const int h0 = (var - 1) & 1, h1 = ((var - 1) >> 1) & 1;
+    face_trace<real, DIM, K, DIR>(T, w, s, T.PH[h0], T.PH[h1], u);
+  }
+}
+
+template <typename real, int DIM, int K>
+__global__ void __launch_bounds__(AdjFaceTile<real, DIM, K>::THREADS)
+    adjoint_face_kernel(const AdjointArgs<real> a) {
+  using S = Shape<DIM, K>;
+  using FT = AdjFaceTile<real, DIM, K>;
+  constexpr int FB = FT::FB, NV = S::NV, QF = S::QF;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  real* sU = reinterpret_cast<real*>(smem_raw);  // [2][NV][QF][FB] traces of U
+  real* sG = sU + 2 * NV * QF * FB;              // [2][NV][QF][FB] traces of G
+  const int nf = a.m.nfaces, nc = a.m.ncells;
+  const int fl = threadIdx.x % FB, v = threadIdx.x / FB;
+  const int f = blockIdx.x * FB + fl;
+  if (f < nf) {
+    const unsigned info = a.m.finfo[f];
+    const int dir = info & 3, vm = (info >> 2) & 7, vp = (info >> 5) & 7;
+    const int cm = a.m.fm[f], cp = a.m.fp[f];
+    auto tr = [&](const real* X, int cell, int s, int var, real* u) {
+      if (dir == 0) trace_of<real, DIM, K, 0>(a, X, cell, s, var, v, u);
+      else if (dir == 1) trace_of<real, DIM, K, 1>(a, X, cell, s, var, v, u);
+      else if constexpr (DIM == 3) trace_of<real, DIM, K, DIM - 1>(a, X, cell, s, var, v, u);
+    };
+    real um[QF], up[QF], gm[QF], gp[QF];
+#pragma unroll
+    for (int q = 0; q < QF; ++q) { um[q] = up[q] = gm[q] = gp[q] = real(0); }
+    if (cm >= 0) {
+      tr(a.U, cm, 1, vm, um);
+      tr(a.G, cm, 1, vm, gm);
+    }
+    if (cp >= 0) {
+      tr(a.U, cp, 0, vp, up);
+      tr(a.G, cp, 0, vp, gp);
+    }
+    if (cm < 0) {
+#pragma unroll
+      for (int q = 0; q < QF; ++q) um[q] = up[q];
+    }
+    if (cp < 0) {
+#pragma unroll
+      for (int q = 0; q < QF; ++q) up[q] = um[q];
+    }
+    // G traces scaled by the cell's prefactor and its integration weight
+    const real pm = cm >= 0 ? a.pre[a.m.level[cm]] * (vm ? real(1) / real(S::NSUB) : real(1)) : real(0);
+    const real pp = cp >= 0 ? a.pre[a.m.level[cp]] * (vp ? real(1) / real(S::NSUB) : real(1)) : real(0);
+#pragma unroll
+    for (int q = 0; q < QF; ++q) {
+      sU[((0 * NV + v) * QF + q) * FB + fl] = um[q];
+      sU[((1 * NV + v) * QF + q) * FB + fl] = up[q];
+      sG[((0 * NV + v) * QF + q) * FB + fl] = pm * gm[q];
+      sG[((1 * NV + v) * QF + q) * FB + fl] = pp * gp[q];
+    }
+  }
+  __syncthreads();
+  const real gamma = real(a.gamma);
+  const Tab1D<real>& T = a.t1;
+  for (int item = threadIdx.x; item < FB * QF; item += FT::THREADS) {
+    const int ff = item % FB, q = item / FB;
+    const int f2 = blockIdx.x * FB + ff;
+    if (f2 >= nf) continue;
+    const int d2 = a.m.finfo[f2] & 3;
+    const int cm = a.m.fm[f2], cp = a.m.fp[f2];
+    // face point weight (product of the tangential Gauss weights)
+    real wq = real(1);
+    {
+      int qq = q;
+#pragma unroll
+      for (int t = 0; t < DIM - 1; ++t) {
+        wq *= T.W[qq % (K + 1)];
+        qq /= (K + 1);
+      }
+    }
+    real uL[NV], uR[NV], fb[NV], bl[NV], br[NV];
+#pragma unroll
+    for (int vv = 0; vv < NV; ++vv) {
+      uL[vv] = sU[((0 * NV + vv) * QF + q) * FB + ff];
+      uR[vv] = sU[((1 * NV + vv) * QF + q) * FB + ff];
+      // dW_minus/dt has -pre F phi w, dW_plus/dt has +pre F phi w
+      fb[vv] = wq * (sG[((1 * NV + vv) * QF + q) * FB + ff] - sG[((0 * NV + vv) * QF + q) * FB + ff]);
+    }
+    if (d2 == 0) {
+      hllc_vjp<real, DIM, 0, true>(uL, uR, gamma, fb, bl);
+      hllc_vjp<real, DIM, 0, false>(uL, uR, gamma, fb, br);
+    } else if (d2 == 1) {
+      hllc_vjp<real, DIM, 1, true>(uL, uR, gamma, fb, bl);
+      hllc_vjp<real, DIM, 1, false>(uL, uR, gamma, fb, br);
+    } else {
+      hllc_vjp<real, DIM, DIM - 1, true>(uL, uR, gamma, fb, bl);
+      hllc_vjp<real, DIM, DIM - 1, false>(uL, uR, gamma, fb, br);
+    }
+    // a mirrored side is the other side's own trace
+    if (cm < 0) {
+#pragma unroll
+      for (int vv = 0; vv < NV; ++vv) { br[vv] += bl[vv]; bl[vv] = real(0); }
+    }
+    if (cp < 0) {
+#pragma unroll
+      for (int vv = 0; vv < NV; ++vv) { bl[vv] += br[vv]; br[vv] = real(0); }
+    }
+#pragma unroll
+    for (int vv = 0; vv < NV; ++vv) {
+      a.FG[(((size_t)0 * NV + vv) * QF + q) * nf + f2] = bl[vv];
+      a.FG[(((size_t)1 * NV + vv) * QF + q) * nf + f2] = br[vv];
+    }
+  }
+  (void)nc;
+}
+
+// ===========================================================================
+// Adjoint cell kernel: TC cells x NV threads.
+
+template <typename real, int DIM, int K>
+struct AdjCellTile {
+  using S = Shape<DIM, K>;
+  static constexpr size_t PER_CELL =
+      (size_t)(S::NV * S::Q + DIM * S::NV * S::Q + S::NV * S::Q) * sizeof(real);
+  static constexpr int TC = PER_CELL * 32 > 96 * 1024 ? 16 : 32;
+  static constexpr int THREADS = TC * S::NV;
+  static constexpr size_t SMEM = PER_CELL * TC;
+};
+
+template <typename real, int DIM, int K, int SD>
+__device__ __forceinline__ void gather_face_adjoint(const AdjointArgs<real>& a, int c, int v,
+                                                    unsigned coarse, real* acc) {
+  using S = Shape<DIM, K>;
+  constexpr int DIR = SD >> 1, SS = SD & 1;
+  const Tab1D<real>& T = a.t1;
+  const int nc = a.m.ncells, nf = a.m.nfaces;
+  const int e0 = a.m.sface[(size_t)SD * nc + c];
+  // the cell is the minus side (role 0) of faces on its + side, the plus side otherwise
+  constexpr int ROLE = SS ? 0 : 1;
+  real uq[S::QF];
+  if (!((coarse >> SD) & 1)) {
+#pragma unroll
+    for (int q = 0; q < S::QF; ++q)
+      uq[q] = a.FG[(((size_t)ROLE * S::NV + v) * S::QF + q) * nf + e0];
+    trace_transpose<real, DIM, K, DIR, SS>(T, T.P, T.P, uq, acc);
+  } else {
+#pragma unroll
+    for (int h = 0; h < S::NSUB; ++h) {
+#pragma unroll
+      for (int q = 0; q < S::QF; ++q)
+        uq[q] = a.FG[(((size_t)ROLE * S::NV + v) * S::QF + q) * nf + e0 + h];
+      trace_transpose<real, DIM, K, DIR, SS>(T, T.PH[h & 1], T.PH[(h >> 1) & 1], uq, acc);
+    }
+  }
+}
+
+template <typename real, int DIM, int K>
+__global__ void __launch_bounds__(AdjCellTile<real, DIM, K>::THREADS)
+    adjoint_cell_kernel(const AdjointArgs<real> a) {
+  using S = Shape<DIM, K>;
+  using CT = AdjCellTile<real, DIM, K>;
+  constexpr int TC = CT::TC, NV = S::NV, Q = S::Q, N = S::N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  real* sU = reinterpret_cast<real*>(smem_raw);  // [NV][Q][TC] nodal U
+  real* sG = sU + NV * Q * TC;                   // [DIM][NV][Q][TC] nodal g_d
+  real* sB = sG + DIM * NV * Q * TC;             // [NV][Q][TC] nodal ubar
+  const int tc = threadIdx.x % TC, v = threadIdx.x / TC;
+  const int nc = a.m.ncells;
+  const int c = blockIdx.x * TC + tc;
+  const bool valid = c < nc;
+  const Tab1D<real>& T = a.t1;
+  const real pre = valid ? a.pre[a.m.level[c]] : real(0);
+  {
+    real w[N], u[Q];
+#pragma unroll
+    for (int l = 0; l < N; ++l)
+      w[l] = valid ? a.U[(size_t)(v * N + l) * nc + c] : ((v == 0 && l == 0) ? real(1) : real(0));
+    modal_to_nodal<real, DIM, K>(T, w, u);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) sU[(v * Q + q) * TC + tc] = u[q];
+#pragma unroll
+    for (int l = 0; l < N; ++l) w[l] = valid ? pre * a.G[(size_t)(v * N + l) * nc + c] : real(0);
+    // g_d(q) = sum_j G_j dphi_j/dxi_d(q) w_q: derivative table on axis d, weighted elsewhere
+    modal_to_nodal_axes<real, DIM, K>(T.DW, T.PW, T.PW, w, u);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) sG[((0 * NV + v) * Q + q) * TC + tc] = u[q];
+    modal_to_nodal_axes<real, DIM, K>(T.PW, T.DW, T.PW, w, u);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) sG[((1 * NV + v) * Q + q) * TC + tc] = u[q];
+    if constexpr (DIM == 3) {
+      modal_to_nodal_axes<real, DIM, K>(T.PW, T.PW, T.DW, w, u);
+#pragma unroll
+      for (int q = 0; q < Q; ++q) sG[((2 * NV + v) * Q + q) * TC + tc] = u[q];
+    }
+  }
+  __syncthreads();
+  const real g1 = real(a.gamma) - real(1);
+  for (int q = v; q < Q; q += NV) {
+    real u[NV], g[DIM][NV], b[NV];
+#pragma unroll
+    for (int vv = 0; vv < NV; ++vv) {
+      u[vv] = sU[(vv * Q + q) * TC + tc];
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) g[d][vv] = sG[((d * NV + vv) * Q + q) * TC + tc];
+    }
+    flux_vjp<real, DIM>(u, g, g1, b);
+#pragma unroll
+    for (int vv = 0; vv < NV; ++vv) sB[(vv * Q + q) * TC + tc] = b[vv];
+  }
+  __syncthreads();
+  if (!valid) return;
+  real acc[N];
+#pragma unroll
+  for (int l = 0; l < N; ++l) acc[l] = real(0);
+  {
+    real b[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) b[q] = sB[(v * Q + q) * TC + tc];
+    nodal_to_modal<real, DIM, K>(T.P, b, acc);
+  }
+  const unsigned coarse = a.m.scoarse[c];
+  gather_face_adjoint<real, DIM, K, 0>(a, c, v, coarse, acc);
+  gather_face_adjoint<real, DIM, K, 1>(a, c, v, coarse, acc);
+  gather_face_adjoint<real, DIM, K, 2>(a, c, v, coarse, acc);
+  gather_face_adjoint<real, DIM, K, 3>(a, c, v, coarse, acc);
+  if constexpr (DIM == 3) {
+    gather_face_adjoint<real, DIM, K, 2 * DIM - 2>(a, c, v, coarse, acc);
+    gather_face_adjoint<real, DIM, K, 2 * DIM - 1>(a, c, v, coarse, acc);
+  }
+  const real sc = real(a.scale);
+#pragma unroll
+  for (int l = 0; l < N; ++l) a.acc[(size_t)(v * N + l) * nc + c] = sc * acc[l];
+}
+
+template <typename real, int DIM, int K>
+cudaError_t prepare_adjoint_kernels() {
+  cudaError_t e = cudaFuncSetAttribute(adjoint_cell_kernel<real, DIM, K>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)AdjCellTile<real, DIM, K>::SMEM);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(adjoint_face_kernel<real, DIM, K>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)AdjFaceTile<real, DIM, K>::SMEM);
+}
+
+template <typename real, int DIM, int K>
+cudaError_t launch_adj_face(const void* pa, cudaStream_t s) {
+  const auto& a = *static_cast<const AdjointArgs<real>*>(pa);
+  using FT = AdjFaceTile<real, DIM, K>;
+  if (a.m.nfaces == 0) return cudaSuccess;
+  adjoint_face_kernel<real, DIM, K><<<(a.m.nfaces + FT::FB - 1) / FT::FB, FT::THREADS, FT::SMEM, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename real, int DIM, int K>
+cudaError_t launch_adj_cell(const void* pa, cudaStream_t s) {
+  const auto& a = *static_cast<const AdjointArgs<real>*>(pa);
+  using CT = AdjCellTile<real, DIM, K>;
+  if (a.m.ncells == 0) return cudaSuccess;
+  adjoint_cell_kernel<real, DIM, K><<<(a.m.ncells + CT::TC - 1) / CT::TC, CT::THREADS, CT::SMEM, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace dgi

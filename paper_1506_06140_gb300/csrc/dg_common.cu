@@ -30,16 +30,19 @@ cudaError_t launch_set_scalar(double* dst, double value, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// the minimum timestep was accumulated as the bit pattern of a positive double
-__global__ void dt_finalize_kernel(const unsigned long long* bits, double* dt, double* dt_copy) {
-  const double v = __longlong_as_double((long long)*bits);
+// the largest signal speed was accumulated as the bit pattern of a
+// non-negative double; dt = factor / speed
+__global__ void dt_finalize_kernel(const unsigned long long* bits, double factor, double* dt,
+                                   double* dt_copy) {
+  const double speed = __longlong_as_double((long long)*bits);
+  const double v = speed > 0.0 ? factor / speed : 0.0;
   *dt = v;
   if (dt_copy) *dt_copy = v;
 }
 
-cudaError_t launch_dt_finalize(const unsigned long long* bits, double* dt, double* dt_copy,
-                               cudaStream_t s) {
-  dt_finalize_kernel<<<1, 1, 0, s>>>(bits, dt, dt_copy);
+cudaError_t launch_dt_finalize(const unsigned long long* bits, double factor, double* dt,
+                               double* dt_copy, cudaStream_t s) {
+  dt_finalize_kernel<<<1, 1, 0, s>>>(bits, factor, dt, dt_copy);
   return cudaGetLastError();
 }
 

@@ -397,6 +397,7 @@ struct dg_handle {
   std::vector<void*> allocs;
   void* tab = nullptr;
   double* tab64 = nullptr;
+  Tab1D<double> tab1d64{};
   void* F = nullptr;
   std::vector<void*> regs;   // scratch state registers 1..n
   double* scal = nullptr;    // [0] dt slot
@@ -410,6 +411,9 @@ struct dg_handle {
   std::vector<cudaGraph_t> graph_defs;
   std::string err;
   std::mutex mu;
+  // adjoint work arrays (allocated by the first dg_rk_step_adjoint call)
+  std::vector<void*> adj;
+  void* FG = nullptr;
   // instrumentation
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -633,6 +637,12 @@ template <typename real>
 StageArgs<real> stage_args(dg_handle* h, const Op& op, const void* U, void* W) {
   StageArgs<real> a;
   a.m = h->md;
+  {
+    const double* src = reinterpret_cast<const double*>(&h->tab1d64);
+    real* dst = reinterpret_cast<real*>(&a.t1);
+    for (size_t i = 0; i < sizeof(Tab1D<double>) / sizeof(double); ++i) dst[i] = (real)src[i];
+  }
+  for (int l = 0; l < 2; ++l) a.pre[l] = (real)(std::ldexp(1.0, 1 - h->dim) / std::ldexp(h->md.dx0, -l));
   a.tab = static_cast<const real*>(h->tab);
   a.U = static_cast<const real*>(U);
   a.F = static_cast<real*>(h->F);
@@ -643,8 +653,8 @@ StageArgs<real> stage_args(dg_handle* h, const Op& op, const void* U, void* W) {
   a.n_out = op.n_out;
   for (int o = 0; o < op.n_out; ++o) {
     a.out[o] = reg(op.out[o]);
-    a.ck[o] = op.ck[o];
-    for (int r = 0; r < MAX_IN; ++r) a.C[o][r] = op.C[o][r];
+    a.ck[o] = (real)op.ck[o];
+    for (int r = 0; r < MAX_IN; ++r) a.C[o][r] = (real)op.C[o][r];
   }
   a.dt = h->scal;
   return a;
@@ -676,6 +686,7 @@ AuxArgs<real> aux_args(dg_handle* h) {
   a.partial = h->partial;
   a.gamma = h->gamma;
   a.volume = h->volume;
+  for (int l = 0; l < 2; ++l) a.inv_dx[l] = 1.0 / std::ldexp(h->md.dx0, -l);
   a.dt_bits = h->dt_bits;
   a.status = h->status;
   return a;
@@ -692,12 +703,13 @@ double dt_factor(const dg_handle* h) {
 
 template <typename real>
 int compute_dt_impl(dg_handle* h, const void* W, double* copy, cudaStream_t s) {
-  DG_CUDA(h, cudaMemsetAsync(h->dt_bits, 0x7f, sizeof(unsigned long long), s));
+  DG_CUDA(h, cudaMemsetAsync(h->dt_bits, 0, sizeof(unsigned long long), s));
   AuxArgs<real> a = aux_args<real>(h);
   a.W = static_cast<const real*>(W);
-  a.dt_factor = dt_factor(h);
+  const double fac = dt_factor(h);
   DG_CUDA(h, timed(h, DG_KERNEL_DT, s, [&] { return h->ks->dt(&a, s); }));
-  DG_CUDA(h, timed(h, DG_KERNEL_OTHER, s, [&] { return launch_dt_finalize(h->dt_bits, h->scal, copy, s); }));
+  DG_CUDA(h, timed(h, DG_KERNEL_OTHER, s,
+                   [&] { return launch_dt_finalize(h->dt_bits, fac, h->scal, copy, s); }));
   return DG_OK;
 }
 
@@ -730,6 +742,105 @@ int rk_step_any(dg_handle* h, void* W, double dt, double* dt_used, cudaStream_t 
     if (r != DG_OK) return r;
   }
   return step_impl<real>(h, h->prog_step, W, s);
+}
+
+template <typename real>
+int combine_list(dg_handle* h, void* out, const std::vector<std::pair<double, const void*>>& terms,
+                 cudaStream_t s) {
+  CombineArgs<real> c;
+  c.out = static_cast<real*>(out);
+  c.n = (size_t)h->nv * h->N * h->ncells;
+  for (const auto& t : terms) {
+    if (t.first == 0.0) continue;
+    if (c.n_terms >= MAX_COMBINE) return fail(h, DG_ERR_ARG, "internal: too many combine terms");
+    c.c[c.n_terms] = (real)t.first;
+    c.x[c.n_terms] = static_cast<const real*>(t.second);
+    ++c.n_terms;
+  }
+  DG_CUDA(h, timed(h, DG_KERNEL_OTHER, s, [&] { return h->ks->combine(&c, s); }));
+  return DG_OK;
+}
+
+// dW/dt(U) -> out (no stage combination)
+template <typename real>
+int rhs_into(dg_handle* h, const void* U, void* out, cudaStream_t s) {
+  Op op;
+  op.n_in = 0;
+  op.n_out = 1;
+  op.ck[0] = 1.0;
+  StageArgs<real> a = stage_args<real>(h, op, U, nullptr);
+  a.out[0] = static_cast<real*>(out);
+  a.dt = nullptr;
+  DG_CUDA(h, timed(h, DG_KERNEL_FACE, s, [&] { return h->ks->face(&a, s); }));
+  DG_CUDA(h, timed(h, DG_KERNEL_CELL, s, [&] { return h->ks->cell(&a, s); }));
+  return DG_OK;
+}
+
+// acc = J(U)^T G, J the Jacobian of dW/dt
+template <typename real>
+int adjoint_rhs_into(dg_handle* h, const void* U, const void* G, void* acc, cudaStream_t s) {
+  AdjointArgs<real> a;
+  a.m = h->md;
+  {
+    const double* src = reinterpret_cast<const double*>(&h->tab1d64);
+    real* dst = reinterpret_cast<real*>(&a.t1);
+    for (size_t i = 0; i < sizeof(Tab1D<double>) / sizeof(double); ++i) dst[i] = (real)src[i];
+  }
+  for (int l = 0; l < 2; ++l) a.pre[l] = (real)(std::ldexp(1.0, 1 - h->dim) / std::ldexp(h->md.dx0, -l));
+  a.U = static_cast<const real*>(U);
+  a.G = static_cast<const real*>(G);
+  a.FG = static_cast<real*>(h->FG);
+  a.acc = static_cast<real*>(acc);
+  a.gamma = h->gamma;
+  a.scale = 1.0;
+  DG_CUDA(h, timed(h, DG_KERNEL_ADJOINT, s, [&] { return h->ks->adj_face(&a, s); }));
+  DG_CUDA(h, timed(h, DG_KERNEL_ADJOINT, s, [&] { return h->ks->adj_cell(&a, s); }));
+  return DG_OK;
+}
+
+// Adjoint of one step in Butcher form with frozen dt:
+//   k_i = L(U_i), U_i = w + dt sum_{j<i} a_ij k_j, w' = w + dt sum_i b_i k_i
+//   kbar_i = dt (b_i lam + sum_{m>i} a_mi Ubar_m),  Ubar_i = J(U_i)^T kbar_i,
+//   lam_n = lam + sum_i Ubar_i.
+template <typename real>
+int adjoint_step_impl(dg_handle* h, const void* Wn, double dt, const void* lam1, void* lam0,
+                      cudaStream_t s) {
+  const Tab tb = butcher(h->opt.rk_order);
+  const int S = tb.s;
+  const size_t bytes = (size_t)h->nv * h->N * h->ncells * h->esize;
+  while ((int)h->adj.size() < 2 * S) {
+    void* p = nullptr;
+    const int r = dalloc(h, bytes, &p);
+    if (r != DG_OK) return r;
+    h->adj.push_back(p);
+  }
+  if (!h->FG) {
+    const int r = dalloc(h, (size_t)2 * h->nv * h->ks->QF * std::max(h->nfaces, 1) * h->esize, &h->FG);
+    if (r != DG_OK) return r;
+  }
+  auto U = [&](int i) -> void* { return i == 0 ? const_cast<void*>(Wn) : h->adj[i - 1]; };
+  auto Kb = [&](int i) -> void* { return h->adj[S - 1 + i]; };
+  void* kbar = h->adj[2 * S - 1];
+  int r;
+  // stage states from the checkpoint
+  for (int i = 0; i < S; ++i) {
+    if ((r = rhs_into<real>(h, U(i), Kb(i), s)) != DG_OK) return r;
+    if (i + 1 < S) {
+      std::vector<std::pair<double, const void*>> t{{1.0, Wn}};
+      for (int j = 0; j <= i; ++j) t.push_back({dt * tb.A[(i + 1) * S + j], Kb(j)});
+      if ((r = combine_list<real>(h, U(i + 1), t, s)) != DG_OK) return r;
+    }
+  }
+  // reverse sweep; Ubar_i replaces k_i in Kb(i)
+  for (int i = S - 1; i >= 0; --i) {
+    std::vector<std::pair<double, const void*>> t{{dt * tb.b[i], lam1}};
+    for (int m = i + 1; m < S; ++m) t.push_back({dt * tb.A[m * S + i], Kb(m)});
+    if ((r = combine_list<real>(h, kbar, t, s)) != DG_OK) return r;
+    if ((r = adjoint_rhs_into<real>(h, U(i), kbar, Kb(i), s)) != DG_OK) return r;
+  }
+  std::vector<std::pair<double, const void*>> t{{1.0, lam1}};
+  for (int i = 0; i < S; ++i) t.push_back({1.0, Kb(i)});
+  return combine_list<real>(h, lam0, t, s);
 }
 
 int rk_step_dispatch(dg_handle* h, void* W, double dt, double* dt_used, cudaStream_t s) {
@@ -798,6 +909,7 @@ int dg_create(const dg_mesh_desc* mesh, int k, double gamma, const dg_options* o
   gauss_rule(k + 3, g3x, g3w);
   lobatto_rule(std::max(2, (k + 4) / 2), lx, lw);
   ks->fill_tables(T, gx, gw, g3x, g3w, lx);
+  std::memcpy(&h->tab1d64, &T[T.size() - sizeof(Tab1D<double>) / sizeof(double)], sizeof(Tab1D<double>));
   void* p = nullptr;
   if ((r = dalloc(h, T.size() * sizeof(double), &p)) != DG_OK) return bail(r);
   h->tab64 = static_cast<double*>(p);
@@ -986,9 +1098,14 @@ int dg_advance(dg_handle* h, void* W_dev, int n_steps, double* dt_hist_dev, void
 
 int dg_rk_step_adjoint(dg_handle* h, const void* W_n_dev, double dt, const void* lam_np1_dev,
                        void* lam_n_dev, void* stream) {
-  (void)W_n_dev; (void)dt; (void)lam_np1_dev; (void)lam_n_dev; (void)stream;
-  if (!check_handle(h)) return DG_ERR_ARG;
-  return fail(h, DG_ERR_UNSUPPORTED, "dg_rk_step_adjoint: not available in this build");
+  if (!check_handle(h) || !W_n_dev || !lam_np1_dev || !lam_n_dev) return DG_ERR_ARG;
+  if (!(dt > 0.0)) return fail(h, DG_ERR_ARG, "dg_rk_step_adjoint: dt must be positive (frozen)");
+  if (h->opt.slope_limiter != DG_LIMITER_NONE || h->opt.positivity)
+    return fail(h, DG_ERR_ARG, "dg_rk_step_adjoint: needs an unlimited handle");
+  std::lock_guard<std::mutex> lock(h->mu);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return h->prec == DG_FP64 ? adjoint_step_impl<double>(h, W_n_dev, dt, lam_np1_dev, lam_n_dev, s)
+                            : adjoint_step_impl<float>(h, W_n_dev, dt, lam_np1_dev, lam_n_dev, s);
 }
 
 int dg_limit(dg_handle* h, void* W_dev, void* stream) {

@@ -39,7 +39,22 @@ struct Shape {
   static constexpr int OFF_XI = OFF_L1W + Q1;                          // [Q][3]   volume points
   static constexpr int OFF_XI1 = OFF_XI + Q * 3;                       // [Q1][3]  L1 points
   static constexpr int OFF_DEG = OFF_XI1 + Q1 * 3;                     // [N]      degree of phi_l
-  static constexpr int TAB_SIZE = OFF_DEG + N;
+  static constexpr int OFF_PMAX = OFF_DEG + N;                         // [N] max |phi_l| on [-1,1]^d
+  static constexpr int OFF_1D = OFF_PMAX + N;                          // Tab1D (sizes of Tab1D<double>)
+  static constexpr int TAB_SIZE = OFF_1D + 92;
+};
+
+// One-dimensional tables of the tensor-product Gauss rule (k+1 <= 4 nodes),
+// passed by value inside the kernel arguments so that, with all loops
+// unrolled, every table entry is an immediate constant-bank operand.
+template <typename real>
+struct Tab1D {
+  real P[4][4];      // P[a][i]  = sqrt(2a+1) P_a(x_i)
+  real PW[4][4];     // PW[a][i] = P[a][i] w_i
+  real DW[4][4];     // DW[a][i] = sqrt(2a+1) P_a'(x_i) w_i
+  real PH[2][4][4];  // PH[h][a][i] = sqrt(2a+1) P_a((x_i + 2h - 1) / 2): node i of half h
+  real PE[2][4];     // PE[s][a] = sqrt(2a+1) P_a(2s - 1): values at -1 (s=0) and +1 (s=1)
+  real W[4];         // Gauss weights w_i
 };
 
 // ---------------------------------------------------------------------------
@@ -72,6 +87,8 @@ constexpr int MAX_OUT = 3;
 template <typename real>
 struct StageArgs {
   MeshDev m;
+  Tab1D<real> t1;
+  real pre[2] = {0, 0};         // 2^(1-d) / dx per refinement level
   const real* tab = nullptr;
   const real* U = nullptr;
   real* F = nullptr;            // face fluxes [NV][QF][nfaces]
@@ -79,8 +96,8 @@ struct StageArgs {
   int n_in = 0, n_out = 0;
   const real* in[MAX_IN] = {nullptr, nullptr, nullptr, nullptr};
   real* out[MAX_OUT] = {nullptr, nullptr, nullptr};
-  double C[MAX_OUT][MAX_IN] = {};
-  double ck[MAX_OUT] = {};
+  real C[MAX_OUT][MAX_IN] = {};
+  real ck[MAX_OUT] = {};
   const double* dt = nullptr;   // device scalar; nullptr means dt = 1
 };
 
@@ -111,6 +128,7 @@ struct AuxArgs {
   double gamma = 1.4;
   double dt_factor = 1.0;         // CFL factor of the timestep formula
   double volume = 1.0;            // domain volume (L1)
+  double inv_dx[2] = {1.0, 1.0};  // 1 / edge length per refinement level
   unsigned long long* dt_bits = nullptr;
   int* status = nullptr;
 };
@@ -120,13 +138,25 @@ struct AuxArgs {
 template <typename real>
 struct AdjointArgs {
   MeshDev m;
-  const real* tab = nullptr;
-  const real* U = nullptr;
+  Tab1D<real> t1;
+  real pre[2] = {0, 0};          // 2^(1-d) / dx per refinement level
+  const real* U = nullptr;       // state at which dW/dt is linearised
   const real* G = nullptr;       // cotangent of dW/dt (layout of W)
-  real* FG = nullptr;            // face work buffer: cotangents of face fluxes [NV][QF][nfaces]
-  real* acc = nullptr;           // output accumulator
+  real* FG = nullptr;            // face cotangents of the traces [2 sides][NV][QF][nfaces]
+  real* acc = nullptr;           // output: acc = scale * J(U)^T G
   double gamma = 1.4;
-  double scale = 1.0;            // acc += scale * J^T G
+  double scale = 1.0;
+};
+
+// out = sum_r c[r] x[r] over n elements (x[r] may alias out)
+constexpr int MAX_COMBINE = 8;
+template <typename real>
+struct CombineArgs {
+  real* out = nullptr;
+  const real* x[MAX_COMBINE] = {};
+  real c[MAX_COMBINE] = {};
+  int n_terms = 0;
+  size_t n = 0;
 };
 
 // Kernel set of one (precision, dim, k).
@@ -149,13 +179,14 @@ struct KernelSet {
   cudaError_t (*node_weights)(const void* aux, cudaStream_t s) = nullptr;
   cudaError_t (*adj_face)(const void* adj_args, cudaStream_t s) = nullptr;
   cudaError_t (*adj_cell)(const void* adj_args, cudaStream_t s) = nullptr;
+  cudaError_t (*combine)(const void* combine_args, cudaStream_t s) = nullptr;
 };
 
 const KernelSet* kernel_set(int prec, int dim, int k);
 
 // shared helper kernels (dg_common.cu)
 cudaError_t launch_set_scalar(double* dst, double value, cudaStream_t s);
-cudaError_t launch_dt_finalize(const unsigned long long* bits, double* dt, double* dt_copy,
+cudaError_t launch_dt_finalize(const unsigned long long* bits, double factor, double* dt, double* dt_copy,
                                cudaStream_t s);
 
 }  // namespace dgi

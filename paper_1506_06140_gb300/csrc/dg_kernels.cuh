@@ -13,10 +13,14 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <algorithm>
+#include <cstring>
 #include <vector>
 
 #include "dg_internal.h"
 #include "dg_physics.cuh"
+#include "dg_stage.cuh"
+#include "dg_adjoint.cuh"
 
 namespace dgi {
 
@@ -179,6 +183,35 @@ void fill_tables(std::vector<double>& T, const std::vector<double>& gx,
     for (int l = 0; l < S::N; ++l) T[S::OFF_L1PHI + q * S::N + l] = B.phi(l, xi);
   }
   for (int l = 0; l < S::N; ++l) T[S::OFF_DEG + l] = B.degree(l);
+  for (int l = 0; l < S::N; ++l) {
+    double m = 1.0;
+    for (int a = 0; a < DIM; ++a) m *= std::sqrt(2.0 * B.e[l][a] + 1.0);
+    T[S::OFF_PMAX + l] = m;  // max of |phi_l| over [-1,1]^d (attained at a corner)
+  }
+  // 1D tables (layout of Tab1D<double>)
+  Tab1D<double> t1{};
+  for (int a = 0; a <= K; ++a)
+    for (int i = 0; i <= K; ++i) {
+      double v, d;
+      HostBasis<DIM, K>::sl(a, gx[i], v, d);
+      t1.P[a][i] = v;
+      t1.PW[a][i] = v * gw[i];
+      t1.DW[a][i] = d * gw[i];
+      for (int h = 0; h < 2; ++h) {
+        double vh, dh;
+        HostBasis<DIM, K>::sl(a, 0.5 * (gx[i] + (h ? 1.0 : -1.0)), vh, dh);
+        t1.PH[h][a][i] = vh;
+      }
+    }
+  for (int a = 0; a <= K; ++a)
+    for (int s = 0; s < 2; ++s) {
+      double v, d;
+      HostBasis<DIM, K>::sl(a, s ? 1.0 : -1.0, v, d);
+      t1.PE[s][a] = v;
+    }
+  for (int i = 0; i <= K; ++i) t1.W[i] = gw[i];
+  static_assert(sizeof(Tab1D<double>) == 92 * sizeof(double), "Tab1D layout");
+  std::memcpy(&T[S::OFF_1D], &t1, sizeof(t1));
 }
 
 // ===========================================================================
@@ -189,176 +222,6 @@ __device__ __forceinline__ real ld(const real* p) { return __ldg(p); }
 
 __device__ __forceinline__ double cell_dx(const MeshDev& m, int c) {
   return ldexp(m.dx0, -(int)m.level[c]);
-}
-
-// ===========================================================================
-// Face fluxes: one thread per (face, face point).  Traces of both sides at
-// the point (eq. solution_representation), HLLC, stored once per face and
-// shared by both cells (conservative by construction).
-
-template <int QF>
-struct FaceBlock {
-  static constexpr int FB = (256 / QF) < 32 ? 32 : ((256 / QF) / 32) * 32;
-};
-
-template <typename real, int DIM, int K>
-__global__ void __launch_bounds__(FaceBlock<Shape<DIM, K>::QF>::FB * Shape<DIM, K>::QF)
-    face_flux_kernel(const StageArgs<real> a) {
-  using S = Shape<DIM, K>;
-  constexpr int FB = FaceBlock<S::QF>::FB;
-  const int q = threadIdx.y;
-  const int f = blockIdx.x * FB + threadIdx.x;
-  const int nf = a.m.nfaces;
-  if (f >= nf) return;
-  const int nc = a.m.ncells;
-  const unsigned info = a.m.finfo[f];
-  const int dir = info & 3, vm = (info >> 2) & 7, vp = (info >> 5) & 7;
-  const int cm = a.m.fm[f], cp = a.m.fp[f];
-  real uL[S::NV], uR[S::NV];
-  if (cm >= 0) {
-    const real* ph = a.tab + S::OFF_PHIF + (((2 * dir + 1) * S::NVAR + vm) * S::QF + q) * S::N;
-#pragma unroll
-    for (int v = 0; v < S::NV; ++v) {
-      real s = real(0);
-#pragma unroll
-      for (int l = 0; l < S::N; ++l) s += ld(a.U + (size_t)(v * S::N + l) * nc + cm) * ld(ph + l);
-      uL[v] = s;
-    }
-  }
-  if (cp >= 0) {
-    const real* ph = a.tab + S::OFF_PHIF + (((2 * dir + 0) * S::NVAR + vp) * S::QF + q) * S::N;
-#pragma unroll
-    for (int v = 0; v < S::NV; ++v) {
-      real s = real(0);
-#pragma unroll
-      for (int l = 0; l < S::N; ++l) s += ld(a.U + (size_t)(v * S::N + l) * nc + cp) * ld(ph + l);
-      uR[v] = s;
-    }
-  }
-  if (cm < 0) {
-#pragma unroll
-    for (int v = 0; v < S::NV; ++v) uL[v] = uR[v];
-  }
-  if (cp < 0) {
-#pragma unroll
-    for (int v = 0; v < S::NV; ++v) uR[v] = uL[v];
-  }
-  real Fl[S::NV];
-  hllc_flux<real, DIM>(uL, uR, dir, real(a.gamma), Fl);
-#pragma unroll
-  for (int v = 0; v < S::NV; ++v) a.F[((size_t)v * S::QF + q) * nf + f] = Fl[v];
-}
-
-// ===========================================================================
-// Cell kernel: a tile of TC cells per block, P threads per cell.
-//   1. stage the tile's weights in shared memory (coalesced row loads);
-//   2. at every volume Gauss point: u_q = sum_l w_l phi_l(xi_q) and the
-//      Euler fluxes f_a(u_q) -> shared memory;
-//   3. per output (var, j): volume integral sum_a sum_q f_a dphi_j w_q,
-//      minus the surface integral of the stored face fluxes, times
-//      2^(1-d)/dx (eq. spatial_discretisation);
-//   4. epilogue: out_o = sum_r C[o][r] in_r + ck[o] dt dWdt.
-
-template <typename real, int DIM, int K>
-struct CellTile {
-  using S = Shape<DIM, K>;
-  static constexpr int TC = 32;
-  static constexpr int P = (S::N * S::NV >= 32) ? 4 : 2;
-  static constexpr int THREADS = TC * P;
-  static constexpr size_t SMEM = (size_t)(S::NV * S::N + DIM * S::NV * S::Q) * TC * sizeof(real);
-};
-
-template <typename real, int DIM, int K>
-__global__ void __launch_bounds__(CellTile<real, DIM, K>::THREADS)
-    cell_update_kernel(const StageArgs<real> a) {
-  using S = Shape<DIM, K>;
-  using T = CellTile<real, DIM, K>;
-  constexpr int TC = T::TC, P = T::P;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  real* sW = reinterpret_cast<real*>(smem_raw);  // [NV*N][TC]
-  real* sF = sW + S::NV * S::N * TC;             // [DIM][NV][Q][TC]
-  const int tc = threadIdx.x % TC, p = threadIdx.x / TC;
-  const int nc = a.m.ncells;
-  const int c = blockIdx.x * TC + tc;
-  const bool valid = c < nc;
-
-  for (int i = p; i < S::NV * S::N; i += P)
-    sW[i * TC + tc] = valid ? a.U[(size_t)i * nc + c] : (i == 0 ? real(1) : real(0));
-  __syncthreads();
-
-  const real g1 = real(a.gamma) - real(1);
-  const real* phi = a.tab + S::OFF_PHI;
-  for (int q = p; q < S::Q; q += P) {
-    real u[S::NV];
-#pragma unroll
-    for (int v = 0; v < S::NV; ++v) {
-      real s = real(0);
-#pragma unroll
-      for (int l = 0; l < S::N; ++l) s += sW[(v * S::N + l) * TC + tc] * ld(phi + q * S::N + l);
-      u[v] = s;
-    }
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-      real f[S::NV];
-      euler_flux<real, DIM>(u, d, g1, f);
-#pragma unroll
-      for (int v = 0; v < S::NV; ++v) sF[((d * S::NV + v) * S::Q + q) * TC + tc] = f[v];
-    }
-  }
-  __syncthreads();
-  if (!valid) return;
-
-  const real pre = real(ldexp(1.0, 1 - DIM) / cell_dx(a.m, c));
-  const real dtv = a.dt ? real(*a.dt) : real(1);
-  const int nf = a.m.nfaces;
-  const unsigned coarse_mask = a.m.scoarse[c];
-  int sf[S::NSIDE];
-#pragma unroll
-  for (int sd = 0; sd < S::NSIDE; ++sd) sf[sd] = a.m.sface[(size_t)sd * nc + c];
-  const real* dphiw = a.tab + S::OFF_DPHIW;
-  const real* phifw = a.tab + S::OFF_PHIFW;
-
-  for (int o = p; o < S::NV * S::N; o += P) {
-    const int v = o / S::N, j = o % S::N;
-    real acc = real(0);
-#pragma unroll
-    for (int d = 0; d < DIM; ++d)
-#pragma unroll
-      for (int q = 0; q < S::Q; ++q)
-        acc += sF[((d * S::NV + v) * S::Q + q) * TC + tc] * ld(dphiw + (d * S::Q + q) * S::N + j);
-    // surface integral: + side faces carry +fbar (outward normal +e_a),
-    // - side faces -fbar
-#pragma unroll
-    for (int sd = 0; sd < S::NSIDE; ++sd) {
-      const real sg = (sd & 1) ? real(1) : real(-1);
-      real s = real(0);
-      if (!((coarse_mask >> sd) & 1)) {
-#pragma unroll
-        for (int q = 0; q < S::QF; ++q)
-          s += a.F[((size_t)v * S::QF + q) * nf + sf[sd]] *
-               ld(phifw + ((sd * S::NVAR + 0) * S::QF + q) * S::N + j);
-      } else {
-        for (int sub = 0; sub < S::NSUB; ++sub)
-#pragma unroll
-          for (int q = 0; q < S::QF; ++q)
-            s += a.F[((size_t)v * S::QF + q) * nf + sf[sd] + sub] *
-                 ld(phifw + ((sd * S::NVAR + 1 + sub) * S::QF + q) * S::N + j);
-      }
-      acc -= sg * s;
-    }
-    const real rhs = pre * acc;
-    const size_t idx = (size_t)o * nc + c;
-    for (int oo = 0; oo < a.n_out; ++oo) {
-      real val = real(a.ck[oo]) * dtv * rhs;
-      for (int r = 0; r < a.n_in; ++r) {
-        const double cr = a.C[oo][r];
-        if (cr == 0.0) continue;
-        const real x = (a.in[r] == a.U) ? sW[o * TC + tc] : a.in[r][idx];
-        val += real(cr) * x;
-      }
-      a.out[oo][idx] = val;
-    }
-  }
 }
 
 // ===========================================================================
@@ -515,7 +378,27 @@ __global__ void __launch_bounds__(128) limit_kernel(const LimitArgs<real> a) {
           for (int v = 0; v < S::NV; ++v) w[v][l] = 0.0;
     }
   }
-  if (a.positivity && K > 0) {
+  bool need_positivity = a.positivity && K > 0;
+  if (need_positivity) {
+    // Exact shortcut: |phi_l| <= prod sqrt(2e+1) on [-1,1]^d, so
+    //   rho(x) >= rho_bar - sum_{l>=1} |w_rho,l| phi_max_l  and
+    //   p(x) >= (gamma-1) (E_low - |m|_up^2 / (2 rho_low)).
+    // When both lower bounds reach eps at every point, theta_1 = theta_2 = 1.
+    double lo[S::NV], up[S::NV];
+    for (int v = 0; v < S::NV; ++v) {
+      double r = 0.0;
+      for (int l = 1; l < S::N; ++l) r += fabs(w[v][l]) * tab[S::OFF_PMAX + l];
+      lo[v] = w[v][0] - r;
+      up[v] = fabs(w[v][0]) + r;
+    }
+    if (lo[0] >= a.eps) {
+      double m2 = 0.0;
+      for (int b = 0; b < DIM; ++b) m2 += up[1 + b] * up[1 + b];
+      const double p_low = (a.gamma - 1.0) * (lo[DIM + 1] - 0.5 * m2 / lo[0]);
+      if (p_low >= a.eps) need_positivity = false;
+    }
+  }
+  if (need_positivity) {
     const double eps = a.eps;
     // points: the union set S, plus fine sub-face points on sides with a finer neighbour
     unsigned finer = 0;
@@ -586,36 +469,40 @@ __device__ __forceinline__ double block_sum(double x, double* sh) {
   return r;
 }
 
+// Timestep (eq. time_step): dt = fac / max_K s_K with the signal speed
+// s_K = sum_a (|v_a| + c) / dx_K of the cell mean; since correctly rounded
+// division is monotone, fac / max s_K equals min_K fac / s_K exactly.  The
+// maximum is accumulated as the bit pattern of a positive double.
 template <typename real, int DIM, int K>
 __global__ void __launch_bounds__(RED_THREADS) dt_kernel(const AuxArgs<real> a) {
   using S = Shape<DIM, K>;
   __shared__ double sh[RED_THREADS];
   const int c = blockIdx.x * RED_THREADS + threadIdx.x;
   const int nc = a.m.ncells;
-  double dtc = 1e300;
+  double speed = 0.0;
   if (c < nc) {
     double u[S::NV];
     for (int v = 0; v < S::NV; ++v) u[v] = (double)a.W[(size_t)(v * S::N) * nc + c];
+    const double rinv = 1.0 / u[0];
     double m2 = 0.0;
     for (int b = 0; b < DIM; ++b) m2 += u[1 + b] * u[1 + b];
-    const double p = (a.gamma - 1.0) * (u[DIM + 1] - 0.5 * m2 / u[0]);
+    const double p = (a.gamma - 1.0) * (u[DIM + 1] - 0.5 * m2 * rinv);
     if (!(u[0] > 0.0) || !(p > 0.0)) {
       atomicOr(a.status, 1 << DG_ERR_NONPHYSICAL_BIT);
     } else {
-      const double cs = sqrt(a.gamma * p / u[0]);
-      const double dx = cell_dx(a.m, c);
+      const double cs = sqrt(a.gamma * p * rinv);
       double sum = 0.0;
-      for (int b = 0; b < DIM; ++b) sum += (fabs(u[1 + b] / u[0]) + cs) / dx;
-      dtc = a.dt_factor / sum;
+      for (int b = 0; b < DIM; ++b) sum += fabs(u[1 + b] * rinv) + cs;
+      speed = sum * a.inv_dx[a.m.level[c]];
     }
   }
-  sh[threadIdx.x] = dtc;
+  sh[threadIdx.x] = speed;
   __syncthreads();
   for (int s = RED_THREADS / 2; s > 0; s >>= 1) {
-    if ((int)threadIdx.x < s) sh[threadIdx.x] = fmin(sh[threadIdx.x], sh[threadIdx.x + s]);
+    if ((int)threadIdx.x < s) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + s]);
     __syncthreads();
   }
-  if (threadIdx.x == 0) atomicMin(a.dt_bits, (unsigned long long)__double_as_longlong(sh[0]));
+  if (threadIdx.x == 0) atomicMax(a.dt_bits, (unsigned long long)__double_as_longlong(sh[0]));
 }
 
 template <typename real, int DIM, int K>
@@ -725,29 +612,53 @@ __global__ void node_weights_kernel(const AuxArgs<real> a) {
 template <typename real, int DIM, int K>
 cudaError_t launch_face(const void* pa, cudaStream_t s) {
   const auto& a = *static_cast<const StageArgs<real>*>(pa);
-  using S = Shape<DIM, K>;
-  constexpr int FB = FaceBlock<S::QF>::FB;
+  using FT = FaceTile<real, DIM, K>;
   if (a.m.nfaces == 0) return cudaSuccess;
-  dim3 block(FB, S::QF), grid((a.m.nfaces + FB - 1) / FB);
-  face_flux_kernel<real, DIM, K><<<grid, block, 0, s>>>(a);
+  const int grid = (a.m.nfaces + FT::FB - 1) / FT::FB;
+  face_flux_kernel<real, DIM, K><<<grid, FT::THREADS, FT::SMEM, s>>>(a);
   return cudaGetLastError();
 }
 
 template <typename real, int DIM, int K>
 cudaError_t launch_cell(const void* pa, cudaStream_t s) {
   const auto& a = *static_cast<const StageArgs<real>*>(pa);
-  using T = CellTile<real, DIM, K>;
+  using CT = CellTile<real, DIM, K>;
   if (a.m.ncells == 0) return cudaSuccess;
-  dim3 grid((a.m.ncells + T::TC - 1) / T::TC);
-  cell_update_kernel<real, DIM, K><<<grid, T::THREADS, T::SMEM, s>>>(a);
+  const int grid = (a.m.ncells + CT::TC - 1) / CT::TC;
+  cell_update_kernel<real, DIM, K><<<grid, CT::THREADS, CT::SMEM, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename real>
+__global__ void combine_kernel(const CombineArgs<real> a) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+    real s = real(0);
+    for (int r = 0; r < a.n_terms; ++r) s += a.c[r] * a.x[r][i];
+    a.out[i] = s;
+  }
+}
+
+template <typename real>
+cudaError_t launch_combine(const void* pa, cudaStream_t s) {
+  const auto& a = *static_cast<const CombineArgs<real>*>(pa);
+  if (a.n == 0) return cudaSuccess;
+  const size_t blocks = std::min<size_t>((a.n + 255) / 256, (size_t)152 * 16);
+  combine_kernel<real><<<(unsigned)blocks, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 
 template <typename real, int DIM, int K>
 cudaError_t prepare_kernels() {
-  using T = CellTile<real, DIM, K>;
-  return cudaFuncSetAttribute(cell_update_kernel<real, DIM, K>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::SMEM);
+  cudaError_t e0 = prepare_adjoint_kernels<real, DIM, K>();
+  if (e0 != cudaSuccess) return e0;
+  cudaError_t e = cudaFuncSetAttribute(cell_update_kernel<real, DIM, K>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)CellTile<real, DIM, K>::SMEM);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(face_flux_kernel<real, DIM, K>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)FaceTile<real, DIM, K>::SMEM);
 }
 
 template <typename real, int DIM, int K>
@@ -836,6 +747,9 @@ KernelSet make_kernel_set(int prec) {
   ks.totals = &launch_totals<real, DIM, K>;
   ks.l1 = &launch_l1<real, DIM, K>;
   ks.node_weights = &launch_node_weights<real, DIM, K>;
+  ks.adj_face = &launch_adj_face<real, DIM, K>;
+  ks.adj_cell = &launch_adj_cell<real, DIM, K>;
+  ks.combine = &launch_combine<real>;
   return ks;
 }
 

@@ -1,0 +1,511 @@
+// The two kernels of one RK stage (paper Sec. 2.4, eqs. dg_term2, dg_term3,
+// spatial_discretisation): face fluxes, then the per-cell update.
+//
+// Both exploit the tensor structure of the Gauss rules: with phi_(a,b,c) =
+// P~_a(x) P~_b(y) P~_c(z) (total degree a+b+c <= k), every contraction
+// between modal weights and point values factorises into 1D contractions
+// (sum factorisation), which cuts the multiply-adds of the direct [N x Q]
+// products roughly in half at k = 2, 3.  The 1D tables travel by value in
+// the kernel arguments (Tab1D), so with the loops unrolled each table entry
+// is a constant-bank operand of an FMA, not a load.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "dg_internal.h"
+#include "dg_physics.cuh"
+
+namespace dgi {
+
+// Index of phi_(a,b,c) in the basis order: total degree, then a descending,
+// then b descending.
+template <int DIM>
+__host__ __device__ constexpr int bidx(int a, int b, int c) {
+  if (DIM == 2) {
+    const int g = a + b;
+    return g * (g + 1) / 2 + (g - a);
+  }
+  const int g = a + b + c;
+  int pos = g * (g + 1) * (g + 2) / 6;
+  for (int aa = g; aa > a; --aa) pos += g - aa + 1;
+  return pos + (g - a - b);
+}
+
+// ---------------------------------------------------------------------------
+// modal -> nodal: u(x_i, y_j[, z_k]) = sum_l w_l phi_l, factorised
+template <typename real, int DIM, int K>
+__device__ __forceinline__ void modal_to_nodal(const Tab1D<real>& T, const real* w, real* u) {
+  constexpr int K1 = K + 1;
+  if constexpr (DIM == 2) {
+    real t[K1][K1];  // t[a][j] = sum_b w_(a,b) P_b(y_j)
+#pragma unroll
+    for (int a = 0; a <= K; ++a)
+#pragma unroll
+      for (int j = 0; j < K1; ++j) {
+        real s = real(0);
+#pragma unroll
+        for (int b = 0; b <= K - a; ++b) s += w[bidx<2>(a, b, 0)] * T.P[b][j];
+        t[a][j] = s;
+      }
+#pragma unroll
+    for (int j = 0; j < K1; ++j)
+#pragma unroll
+      for (int i = 0; i < K1; ++i) {
+        real s = real(0);
+#pragma unroll
+        for (int a = 0; a <= K; ++a) s += T.P[a][i] * t[a][j];
+        u[i + K1 * j] = s;
+      }
+  } else {
+    real t1[K1][K1][K1];  // [a][b][kz] = sum_c w_(a,b,c) P_c(z_kz)
+#pragma unroll
+    for (int a = 0; a <= K; ++a)
+#pragma unroll
+      for (int b = 0; b <= K - a; ++b)
+#pragma unroll
+        for (int kz = 0; kz < K1; ++kz) {
+          real s = real(0);
+#pragma unroll
+          for (int c = 0; c <= K - a - b; ++c) s += w[bidx<3>(a, b, c)] * T.P[c][kz];
+          t1[a][b][kz] = s;
+        }
+    real t2[K1][K1][K1];  // [a][j][kz] = sum_b t1[a][b][kz] P_b(y_j)
+#pragma unroll
+    for (int a = 0; a <= K; ++a)
+#pragma unroll
+      for (int j = 0; j < K1; ++j)
+#pragma unroll
+        for (int kz = 0; kz < K1; ++kz) {
+          real s = real(0);
+#pragma unroll
+          for (int b = 0; b <= K - a; ++b) s += t1[a][b][kz] * T.P[b][j];
+          t2[a][j][kz] = s;
+        }
+#pragma unroll
+    for (int kz = 0; kz < K1; ++kz)
+#pragma unroll
+      for (int j = 0; j < K1; ++j)
+#pragma unroll
+        for (int i = 0; i < K1; ++i) {
+          real s = real(0);
+#pragma unroll
+          for (int a = 0; a <= K; ++a) s += T.P[a][i] * t2[a][j][kz];
+          u[i + K1 * (j + K1 * kz)] = s;
+        }
+  }
+}
+
+// volume integral of one variable: acc_l += sum_d sum_q f_d(q) dphi_l/dxi_d w_q
+// (f_d given at the points, q = i + K1 (j + K1 k))
+template <typename real, int DIM, int K, int D>
+__device__ __forceinline__ void volume_dir(const Tab1D<real>& T, const real* f, real* acc) {
+  constexpr int K1 = K + 1;
+  if constexpr (DIM == 2) {
+    // derivative along axis D, weight along the other axis
+#pragma unroll
+    for (int e = 1; e <= K; ++e)
+#pragma unroll
+      for (int o = 0; o < K1; ++o) {
+        real g = real(0);
+#pragma unroll
+        for (int i = 0; i < K1; ++i) g += f[D == 0 ? (i + K1 * o) : (o + K1 * i)] * T.DW[e][i];
+#pragma unroll
+        for (int e2 = 0; e2 <= K - e; ++e2)
+          acc[D == 0 ? bidx<2>(e, e2, 0) : bidx<2>(e2, e, 0)] += g * T.PW[e2][o];
+      }
+  } else {
+    // axes: D (derivative), A and B the other two in increasing order
+    constexpr int A = D == 0 ? 1 : 0;
+    constexpr int B = D == 2 ? 1 : 2;
+    auto q_of = [](int d, int a, int b) {
+      int x[3];
+      x[D] = d;
+      x[A] = a;
+      x[B] = b;
+      return x[0] + K1 * (x[1] + K1 * x[2]);
+    };
+    auto l_of = [](int ed, int ea, int eb) {
+      int e[3];
+      e[D] = ed;
+      e[A] = ea;
+      e[B] = eb;
+      return bidx<3>(e[0], e[1], e[2]);
+    };
+#pragma unroll
+    for (int ed = 1; ed <= K; ++ed) {
+      real g1[K1][K1];  // [ia][ib] = sum_id f DW[ed][id]
+#pragma unroll
+      for (int ia = 0; ia < K1; ++ia)
+#pragma unroll
+        for (int ib = 0; ib < K1; ++ib) {
+          real s = real(0);
+#pragma unroll
+          for (int id = 0; id < K1; ++id) s += f[q_of(id, ia, ib)] * T.DW[ed][id];
+          g1[ia][ib] = s;
+        }
+#pragma unroll
+      for (int ea = 0; ea <= K - ed; ++ea)
+#pragma unroll
+        for (int ib = 0; ib < K1; ++ib) {
+          real g2 = real(0);
+#pragma unroll
+          for (int ia = 0; ia < K1; ++ia) g2 += g1[ia][ib] * T.PW[ea][ia];
+#pragma unroll
+          for (int eb = 0; eb <= K - ed - ea; ++eb) acc[l_of(ed, ea, eb)] += g2 * T.PW[eb][ib];
+        }
+    }
+  }
+}
+
+// surface integral of one variable over side (DIR, S) of the cell:
+// acc_l -= sg * sum_q fbar_q phi_l(face point q) w_q, with the face's points
+// given in PT0 (and PT1) -- the Gauss nodes, or a half of them for sub-faces.
+template <typename real, int DIM, int K, int DIR, int S>
+__device__ __forceinline__ void surface_side(const Tab1D<real>& T, const real (&PT0)[4][4],
+                                             const real (&PT1)[4][4], const real* fq, real scale,
+                                             real* acc) {
+  constexpr int K1 = K + 1;
+  const real sg = S ? real(-1) : real(1);  // minus the outward normal's sign
+  if constexpr (DIM == 2) {
+    constexpr int TA = DIR == 0 ? 1 : 0;
+    real G[K1];
+#pragma unroll
+    for (int e = 0; e <= K; ++e) {
+      real s = real(0);
+#pragma unroll
+      for (int q = 0; q < K1; ++q) s += fq[q] * T.W[q] * PT0[e][q];
+      G[e] = s * scale * sg;
+    }
+#pragma unroll
+    for (int ed = 0; ed <= K; ++ed)
+#pragma unroll
+      for (int et = 0; et <= K - ed; ++et)
+        acc[TA == 1 ? bidx<2>(ed, et, 0) : bidx<2>(et, ed, 0)] += T.PE[S][ed] * G[et];
+  } else {
+    constexpr int A = DIR == 0 ? 1 : 0;  // tangential axes, increasing
+    constexpr int B = DIR == 2 ? 1 : 2;
+    real H[K1][K1];  // [ea][qb] = sum_qa f w P_ea
+#pragma unroll
+    for (int ea = 0; ea <= K; ++ea)
+#pragma unroll
+      for (int qb = 0; qb < K1; ++qb) {
+        real s = real(0);
+#pragma unroll
+        for (int qa = 0; qa < K1; ++qa) s += fq[qa + K1 * qb] * T.W[qa] * PT0[ea][qa];
+        H[ea][qb] = s;
+      }
+#pragma unroll
+    for (int ea = 0; ea <= K; ++ea)
+#pragma unroll
+      for (int eb = 0; eb <= K - ea; ++eb) {
+        real s = real(0);
+#pragma unroll
+        for (int qb = 0; qb < K1; ++qb) s += H[ea][qb] * T.W[qb] * PT1[eb][qb];
+        s *= scale * sg;
+#pragma unroll
+        for (int ed = 0; ed <= K - ea - eb; ++ed) {
+          int e[3];
+          e[DIR] = ed;
+          e[A] = ea;
+          e[B] = eb;
+          acc[bidx<3>(e[0], e[1], e[2])] += T.PE[S][ed] * s;
+        }
+      }
+  }
+}
+
+// trace of one variable on side (DIR, S) at the face points given by PT0/PT1
+template <typename real, int DIM, int K, int DIR>
+__device__ __forceinline__ void face_trace(const Tab1D<real>& T, const real* w, int s,
+                                           const real (&PT0)[4][4], const real (&PT1)[4][4],
+                                           real* u) {
+  constexpr int K1 = K + 1;
+  if constexpr (DIM == 2) {
+    real t[K1];
+#pragma unroll
+    for (int et = 0; et <= K; ++et) {
+      real acc = real(0);
+#pragma unroll
+      for (int ed = 0; ed <= K - et; ++ed)
+        acc += w[DIR == 0 ? bidx<2>(ed, et, 0) : bidx<2>(et, ed, 0)] * T.PE[s][ed];
+      t[et] = acc;
+    }
+#pragma unroll
+    for (int q = 0; q < K1; ++q) {
+      real acc = real(0);
+#pragma unroll
+      for (int et = 0; et <= K; ++et) acc += t[et] * PT0[et][q];
+      u[q] = acc;
+    }
+  } else {
+    constexpr int A = DIR == 0 ? 1 : 0;
+    constexpr int B = DIR == 2 ? 1 : 2;
+    real t[K1][K1];
+#pragma unroll
+    for (int ea = 0; ea <= K; ++ea)
+#pragma unroll
+      for (int eb = 0; eb <= K - ea; ++eb) {
+        real acc = real(0);
+#pragma unroll
+        for (int ed = 0; ed <= K - ea - eb; ++ed) {
+          int e[3];
+          e[DIR] = ed;
+          e[A] = ea;
+          e[B] = eb;
+          acc += w[bidx<3>(e[0], e[1], e[2])] * T.PE[s][ed];
+        }
+        t[ea][eb] = acc;
+      }
+#pragma unroll
+    for (int ea = 0; ea <= K; ++ea) {
+      real h[K1];
+#pragma unroll
+      for (int qb = 0; qb < K1; ++qb) {
+        real acc = real(0);
+#pragma unroll
+        for (int eb = 0; eb <= K - ea; ++eb) acc += t[ea][eb] * PT1[eb][qb];
+        h[qb] = acc;
+      }
+#pragma unroll
+      for (int qb = 0; qb < K1; ++qb)
+#pragma unroll
+        for (int qa = 0; qa < K1; ++qa) {
+          if (ea == 0) u[qa + K1 * qb] = real(0);
+          u[qa + K1 * qb] += PT0[ea][qa] * h[qb];
+        }
+    }
+  }
+}
+
+// ===========================================================================
+// Face kernel: FB faces per block, NV threads per face.
+//   1. thread (face, var): load both cells' weights of its variable and
+//      compute the traces at all face points -> shared memory;
+//   2. thread (face, point): HLLC flux -> F[var][point][face] (coalesced).
+// A variant > 0 marks the coarse side of a hanging face: its points are a
+// half (2D) or quarter (3D) of the cell face.
+
+template <typename real, int DIM, int K>
+struct FaceTile {
+  using S = Shape<DIM, K>;
+  static constexpr int FB = 32;
+  static constexpr int THREADS = FB * S::NV;
+  static constexpr size_t SMEM = (size_t)2 * S::NV * S::QF * FB * sizeof(real);
+};
+
+template <typename real, int DIM, int K, int DIR>
+__device__ __forceinline__ void trace_side(const StageArgs<real>& a, int cell, int s, int var,
+                                           int v, real* u) {
+  using S = Shape<DIM, K>;
+  const Tab1D<real>& T = a.t1;
+  const int nc = a.m.ncells;
+  real w[S::N];
+#pragma unroll
+  for (int l = 0; l < S::N; ++l) w[l] = a.U[(size_t)(v * S::N + l) * nc + cell];
+  if (var == 0) {
+    face_trace<real, DIM, K, DIR>(T, w, s, T.P, T.P, u);
+  } else {
+    const int h0 = (var - 1) & 1, h1 = ((var - 1) >> 1) & 1;
+    face_trace<real, DIM, K, DIR>(T, w, s, T.PH[h0], T.PH[h1], u);
+  }
+}
+
+template <typename real, int DIM, int K>
+__global__ void __launch_bounds__(FaceTile<real, DIM, K>::THREADS)
+    face_flux_kernel(const StageArgs<real> a) {
+  using S = Shape<DIM, K>;
+  using FT = FaceTile<real, DIM, K>;
+  constexpr int FB = FT::FB;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  real* sT = reinterpret_cast<real*>(smem_raw);  // [2 sides][NV][QF][FB]
+  const int nf = a.m.nfaces;
+  const int fl = threadIdx.x % FB, v = threadIdx.x / FB;
+  const int f = blockIdx.x * FB + fl;
+  int dir = 0;
+  if (f < nf) {
+    const unsigned info = a.m.finfo[f];
+    dir = info & 3;
+    const int vm = (info >> 2) & 7, vp = (info >> 5) & 7;
+    const int cm = a.m.fm[f], cp = a.m.fp[f];
+    real um[S::QF], up[S::QF];
+    // the minus cell sees the face as its + side (s = 1), the plus cell as its - side
+    auto trace = [&](int cell, int s, int var, real* u) {
+      if (dir == 0) trace_side<real, DIM, K, 0>(a, cell, s, var, v, u);
+      else if (dir == 1) trace_side<real, DIM, K, 1>(a, cell, s, var, v, u);
+      else if constexpr (DIM == 3) trace_side<real, DIM, K, DIM - 1>(a, cell, s, var, v, u);
+    };
+    if (cm >= 0) trace(cm, 1, vm, um);
+    if (cp >= 0) trace(cp, 0, vp, up);
+    if (cm < 0) {
+#pragma unroll
+      for (int q = 0; q < S::QF; ++q) um[q] = up[q];
+    }
+    if (cp < 0) {
+#pragma unroll
+      for (int q = 0; q < S::QF; ++q) up[q] = um[q];
+    }
+#pragma unroll
+    for (int q = 0; q < S::QF; ++q) {
+      sT[((0 * S::NV + v) * S::QF + q) * FB + fl] = um[q];
+      sT[((1 * S::NV + v) * S::QF + q) * FB + fl] = up[q];
+    }
+  }
+  __syncthreads();
+  // HLLC at every (face, point) of the block
+  const real gamma = real(a.gamma);
+  for (int item = threadIdx.x; item < FB * S::QF; item += FT::THREADS) {
+    const int ff = item % FB, q = item / FB;
+    const int f2 = blockIdx.x * FB + ff;
+    if (f2 >= nf) continue;
+    const int d2 = a.m.finfo[f2] & 3;
+    real uL[S::NV], uR[S::NV], Fl[S::NV];
+#pragma unroll
+    for (int vv = 0; vv < S::NV; ++vv) {
+      uL[vv] = sT[((0 * S::NV + vv) * S::QF + q) * FB + ff];
+      uR[vv] = sT[((1 * S::NV + vv) * S::QF + q) * FB + ff];
+    }
+    if (d2 == 0) hllc_flux<real, DIM>(uL, uR, 0, gamma, Fl);
+    else if (d2 == 1) hllc_flux<real, DIM>(uL, uR, 1, gamma, Fl);
+    else hllc_flux<real, DIM>(uL, uR, DIM - 1, gamma, Fl);
+#pragma unroll
+    for (int vv = 0; vv < S::NV; ++vv) a.F[((size_t)vv * S::QF + q) * nf + f2] = Fl[vv];
+  }
+  (void)dir;
+}
+
+// ===========================================================================
+// Cell kernel: TC cells per block, NV threads per cell (thread <-> variable).
+//   1. thread (cell, var): its variable's weights -> nodal values at the
+//      (k+1)^d Gauss points (sum factorisation) -> shared memory;
+//   2. thread (cell, p): Euler fluxes at points p, p+NV, ... -> shared memory;
+//   3. thread (cell, var): volume integral (sum factorisation) minus the
+//      surface integral of the stored face fluxes, times 2^(1-d)/dx;
+//   4. epilogue: out_o = sum_r C[o][r] in_r + ck[o] dt dW/dt.
+
+template <typename real, int DIM, int K>
+struct CellTile {
+  using S = Shape<DIM, K>;
+  static constexpr size_t PER_CELL = (size_t)(S::NV * S::Q + DIM * S::NV * S::Q) * sizeof(real);
+  static constexpr int TC = PER_CELL * 32 > 96 * 1024 ? 16 : 32;
+  static constexpr int THREADS = TC * S::NV;
+  static constexpr size_t SMEM = PER_CELL * TC;
+};
+
+template <typename real, int DIM, int K, int SD>
+__device__ __forceinline__ void surface_from_faces(const StageArgs<real>& a, int c, int v,
+                                                   unsigned coarse, real* acc) {
+  using S = Shape<DIM, K>;
+  constexpr int DIR = SD >> 1, SS = SD & 1;
+  const Tab1D<real>& T = a.t1;
+  const int nc = a.m.ncells, nf = a.m.nfaces;
+  const int e0 = a.m.sface[(size_t)SD * nc + c];
+  real fq[S::QF];
+  if (!((coarse >> SD) & 1)) {
+#pragma unroll
+    for (int q = 0; q < S::QF; ++q) fq[q] = a.F[((size_t)v * S::QF + q) * nf + e0];
+    surface_side<real, DIM, K, DIR, SS>(T, T.P, T.P, fq, real(1), acc);
+  } else {
+    // coarse side of a hanging face: NSUB sub-faces in quadrant order
+    const real sub = real(1) / real(S::NSUB);
+#pragma unroll
+    for (int h = 0; h < S::NSUB; ++h) {
+#pragma unroll
+      for (int q = 0; q < S::QF; ++q) fq[q] = a.F[((size_t)v * S::QF + q) * nf + e0 + h];
+      surface_side<real, DIM, K, DIR, SS>(T, T.PH[h & 1], T.PH[(h >> 1) & 1], fq, sub, acc);
+    }
+  }
+}
+
+template <typename real, int DIM, int K>
+__global__ void __launch_bounds__(CellTile<real, DIM, K>::THREADS)
+    cell_update_kernel(const StageArgs<real> a) {
+  using S = Shape<DIM, K>;
+  using CT = CellTile<real, DIM, K>;
+  constexpr int TC = CT::TC, NV = S::NV, Q = S::Q, N = S::N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  real* sU = reinterpret_cast<real*>(smem_raw);  // [NV][Q][TC]
+  real* sF = sU + NV * Q * TC;                   // [DIM][NV][Q][TC]
+  const int tc = threadIdx.x % TC, v = threadIdx.x / TC;
+  const int nc = a.m.ncells;
+  const int c = blockIdx.x * TC + tc;
+  const bool valid = c < nc;
+  const Tab1D<real>& T = a.t1;
+
+  // 1. weights of this variable -> nodal values
+  real w[N];
+#pragma unroll
+  for (int l = 0; l < N; ++l)
+    w[l] = valid ? a.U[(size_t)(v * N + l) * nc + c] : ((v == 0 && l == 0) ? real(1) : real(0));
+  {
+    real u[Q];
+    modal_to_nodal<real, DIM, K>(T, w, u);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) sU[(v * Q + q) * TC + tc] = u[q];
+  }
+  __syncthreads();
+
+  // 2. Euler fluxes at the points of this thread
+  const real g1 = real(a.gamma) - real(1);
+  for (int q = v; q < Q; q += NV) {
+    real u[NV];
+#pragma unroll
+    for (int vv = 0; vv < NV; ++vv) u[vv] = sU[(vv * Q + q) * TC + tc];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      real f[NV];
+      euler_flux<real, DIM>(u, d, g1, f);
+#pragma unroll
+      for (int vv = 0; vv < NV; ++vv) sF[((d * NV + vv) * Q + q) * TC + tc] = f[vv];
+    }
+  }
+  __syncthreads();
+  if (!valid) return;
+
+  // 3. volume and surface integrals of this variable
+  real acc[N];
+#pragma unroll
+  for (int l = 0; l < N; ++l) acc[l] = real(0);
+  {
+    real f[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) f[q] = sF[((0 * NV + v) * Q + q) * TC + tc];
+    volume_dir<real, DIM, K, 0>(T, f, acc);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) f[q] = sF[((1 * NV + v) * Q + q) * TC + tc];
+    volume_dir<real, DIM, K, 1>(T, f, acc);
+    if constexpr (DIM == 3) {
+#pragma unroll
+      for (int q = 0; q < Q; ++q) f[q] = sF[((2 * NV + v) * Q + q) * TC + tc];
+      volume_dir<real, DIM, K, DIM - 1>(T, f, acc);
+    }
+  }
+  const unsigned coarse = a.m.scoarse[c];
+  surface_from_faces<real, DIM, K, 0>(a, c, v, coarse, acc);
+  surface_from_faces<real, DIM, K, 1>(a, c, v, coarse, acc);
+  surface_from_faces<real, DIM, K, 2>(a, c, v, coarse, acc);
+  surface_from_faces<real, DIM, K, 3>(a, c, v, coarse, acc);
+  if constexpr (DIM == 3) {
+    surface_from_faces<real, DIM, K, 2 * DIM - 2>(a, c, v, coarse, acc);
+    surface_from_faces<real, DIM, K, 2 * DIM - 1>(a, c, v, coarse, acc);
+  }
+
+  // 4. epilogue
+  const real pre = a.pre[a.m.level[c]];
+  const real dtv = a.dt ? real(*a.dt) : real(1);
+  const int n_out = a.n_out, n_in = a.n_in;
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    const real rhs = pre * acc[j];
+    const size_t idx = (size_t)(v * N + j) * nc + c;
+    for (int oo = 0; oo < n_out; ++oo) {
+      real val = a.ck[oo] * dtv * rhs;
+      for (int r = 0; r < n_in; ++r) {
+        const real cr = a.C[oo][r];
+        if (cr == real(0)) continue;
+        val += cr * ((a.in[r] == a.U) ? w[j] : a.in[r][idx]);
+      }
+      a.out[oo][idx] = val;
+    }
+  }
+}
+
+}  // namespace dgi

@@ -24,7 +24,7 @@ EXPORTS = ["dg_default_options", "dg_create", "dg_destroy", "dg_last_error", "dg
            "dg_rk_step", "dg_advance", "dg_rk_step_adjoint", "dg_limit", "dg_totals",
            "dg_l1_density", "dg_node_weights", "dg_neighbor_table", "dg_cell_levels",
            "dg_status", "dg_profile_begin", "dg_profile_end", "dg_totals_noalloc"]
-KERNEL_KINDS = ["face", "cell", "limit", "dt", "other"]
+KERNEL_KINDS = ["face", "cell", "limit", "dt", "other", "adjoint"]
 
 
 class MeshDesc(C.Structure):

@@ -58,11 +58,13 @@ def vortex(xyz, gamma=1.4, beta=5.0, center=(0.0, 0.0), boost=(1.0, 1.0), t=0.0,
     return conserved(rho, vel, p, gamma)
 
 
-def acoustic3d(xyz, gamma=1.4, amp=1e-3):
+def acoustic3d(xyz, gamma=1.4, amp=1e-3, vel=(0.0, 0.0, 0.0)):
+    """rho = 1 + amp sin(2 pi x) sin(2 pi y) sin(2 pi z), uniform velocity vel
+    (zero for the standing wave), p = 1/gamma (sound speed 1)."""
     x, y, z = xyz[0], xyz[1], xyz[2]
     rho = 1.0 + amp * np.sin(2 * math.pi * x) * np.sin(2 * math.pi * y) * np.sin(2 * math.pi * z)
-    zero = np.zeros_like(rho)
-    return conserved(rho, (zero, zero, zero), np.full_like(rho, 1.0 / gamma), gamma)
+    v = [np.full_like(rho, vv) for vv in vel]
+    return conserved(rho, v, np.full_like(rho, 1.0 / gamma), gamma)
 
 
 def sod(xyz, gamma=1.4, x0=0.5):

@@ -451,3 +451,17 @@ def test_step_jvp_matches_central_differences():
     h = 1e-6
     fd = (o.rk_step(W + h * V, dt)[0] - o.rk_step(W - h * V, dt)[0]) / (2 * h)
     assert np.max(np.abs(JV - fd)) < 1e-7 * np.max(np.abs(JV))
+
+
+@pytest.mark.parametrize("mesh", MESHES + [dict(dim=2, n=[5, 1], lo=[0, 0], hi=[1, 0.2])],
+                         ids=["u2", "amr2", "u3", "amr3", "strip"])
+def test_per_cell_evaluations_match_full_mesh(mesh):
+    """rhs_one / limit_one (used for sampled comparisons at full size) agree
+    with the whole-mesh rhs and limiter."""
+    o = make(mesh, 2, limiter=O.LIM_CHARACTERISTIC, positivity=True)
+    W = wl.random_weights(mesh["dim"], o.N, o.n_cells, seed=41, slope=0.5, rho_range=(0.2, 2.0),
+                          p_range=(0.05, 2.0))
+    cells = np.arange(o.n_cells)
+    np.testing.assert_allclose(o.rhs_cells(W, cells), o.rhs(W), rtol=0,
+                               atol=1e-13 * np.abs(o.rhs(W)).max())
+    np.testing.assert_array_equal(o.limit_cells(W, cells), o.limit(W))
