@@ -41,6 +41,12 @@ WORKLOADS = {
              "SSP-RK4 (5 stages), no limiter, CFL 0.2",
         dim=2, k=3, rk=4, stages=5, limiter="none", positivity=False, precisions=("fp64", "fp32"),
         tag="vortex256_k3"),
+    "ensemble": dict(
+        name="512 independent isentropic vortices (strength U(3,6)) on periodic [-5,5]^2 with "
+             "sizes drawn from {32,48,64,96,128}^2 (3.4M cells), k=2 (6 coeffs/cell/var), SSP-RK3, "
+             "per-problem CFL timestep, FP32, all steps in one CUDA-graph launch",
+        dim=2, k=2, rk=3, stages=3, limiter="none", positivity=False, precisions=("fp32",),
+        tag="ensemble512_k2", graph=True),
     "sedov3d": dict(
         name="Sedov blast 3D, 64^3 base + central 32^3 refined once (491,520 cells), k=2 "
              "(10 coeffs/cell/var), SSP-RK3, characteristic TVB limiter + positivity limiter, "
@@ -52,8 +58,10 @@ WORKLOADS = {
 
 def workload_config(wk, precision, cells):
     W = WORKLOADS[wk]
+    l2 = ("state larger than L2 (no flush); timed steps in one graph launch" if W.get("graph")
+          else "flushed between timed steps (256 MiB write)")
     return {"workload": W["name"], "cells": cells, "k": W["k"], "rk_stages": W["stages"],
-            "precision": precision, "l2": "flushed between timed steps (256 MiB write)"}
+            "precision": precision, "l2": l2}
 
 
 def mesh(n=N_CELLS_1D, half=5.0):
@@ -69,11 +77,22 @@ def make_problem(wk, precision):
     W = WORKLOADS[wk]
     if wk == "vortex":
         m, ic = mesh(), wl.vortex
+    elif wk == "ensemble":
+        probs = wl.ensemble_problems()
+        m = [wl.mesh_uniform(2, [n, n], [-5.0, -5.0], [5.0, 5.0]) for n, _ in probs]
+        ic = None
     else:
         m, ic = wl.mesh_two_level_3d(64, 16, 47), wl.sedov3d
     s = dg.Solver(m, W["k"], 1.4, rk_order=W["rk"], cfl=CFL, limiter=W["limiter"],
                   positivity=W["positivity"], precision=precision)
-    U = ic(s.quad_points().cpu().numpy())  # closed-form IC at the Gauss points
+    xyz = s.quad_points().cpu().numpy()
+    if ic is not None:
+        U = ic(xyz)  # closed-form IC at the Gauss points
+    else:
+        U = np.empty((s.nv, s.nq, s.n_cells))
+        for p, (n, beta) in enumerate(probs):
+            a, b = s.cell_offsets[p], s.cell_offsets[p + 1]
+            U[:, :, a:b] = wl.vortex(xyz[:, :, a:b], beta=beta)
     W0 = s.project(torch.as_tensor(U))
     if W["limiter"] != "none" or W["positivity"]:
         s.limit(W0)
@@ -245,17 +264,36 @@ def run_gpu(args, rank, world, local_rank):
         stream = torch.cuda.current_stream()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(args.steps)]
+        graph = WORKLOADS[args.workload].get("graph", False)
         with ClockSampler(local_rank) as clk:  # sampling spans the warm-up and the timed steps
-            for _ in range(args.warmup):
-                s.rk_step(W)
-            torch.cuda.synchronize()
-            barrier()
+            if graph:
+                # all timed steps as one graph launch; the state (> L2) is not flushed
+                s.advance(W, args.warmup)
+                s.advance(W, args.steps)  # records the timed graph (not timed)
+                torch.cuda.synchronize()
+                barrier()
+                ev[0][0].record(stream)
+                s.advance(W, args.steps)
+                ev[0][1].record(stream)
+                torch.cuda.synchronize()
+                ev = ev[:1]
+            else:
+                for _ in range(args.warmup):
+                    s.rk_step(W)
+                torch.cuda.synchronize()
+                barrier()
+                s.profile_begin()
+                for i in range(args.steps):
+                    flush.zero_()  # evict the working set from L2 before each timed step
+                    ev[i][0].record(stream)
+                    s.rk_step(W)
+                    ev[i][1].record(stream)
+                torch.cuda.synchronize()
+        if graph:
+            # per-kernel durations from a separate, instrumented pass of the same steps
             s.profile_begin()
-            for i in range(args.steps):
-                flush.zero_()  # evict the working set from L2 before each timed step
-                ev[i][0].record(stream)
+            for _ in range(args.steps):
                 s.rk_step(W)
-                ev[i][1].record(stream)
             torch.cuda.synchronize()
         prof = s.profile_end()
         barrier()
@@ -333,6 +371,66 @@ def summarize(args, results, world):
     return lines
 
 
+def run_adjoint(args):
+    """Gradient of an L2 density misfit after N frozen-dt RK3 steps of the 3D
+    acoustic wave (128^3, k=2) with respect to the initial weights, by the
+    per-step checkpointed adjoint, against a central finite difference."""
+    import torch
+    from paper_1506_06140_gb300 import dg
+    from paper_1506_06140_gb300 import workloads as wl
+    from paper_1506_06140_gb300.autograd import rk_steps
+    torch.cuda.set_device(0)
+    n, k, steps = args.size, 2, args.steps
+    m = wl.mesh_uniform(3, [n] * 3, [0.0] * 3, [1.0] * 3)
+    s = dg.Solver(m, k, 1.4, rk_order=3, cfl=CFL)
+    W0 = s.project(torch.as_tensor(wl.acoustic3d(s.quad_points().cpu().numpy())))
+    dt = s.compute_dt(W0).item()
+    g = torch.Generator(device="cuda").manual_seed(1506062)
+    target = W0[0] + 1e-4 * torch.randn(W0[0].shape, generator=g, device="cuda", dtype=W0.dtype)
+    vol = (1.0 / n) ** 3
+
+    def J(W):
+        WN = rk_steps(W, s, steps, dt)
+        return 0.5 * vol * ((WN[0] - target) ** 2).sum()
+
+    st = torch.cuda.current_stream()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    W = W0.clone().requires_grad_(True)
+    torch.cuda.synchronize()
+    e[0].record(st)
+    val = J(W)
+    e[1].record(st)
+    val.backward()
+    e[2].record(st)
+    torch.cuda.synchronize()
+    fwd_ms, bwd_ms = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+    grad = W.grad.detach()
+    W.grad = None
+    g2 = torch.Generator(device="cuda").manual_seed(1506063)
+    v = torch.randn(W0.shape, generator=g2, device="cuda", dtype=W0.dtype)
+    v /= v.norm()
+    dJ = (grad * v).sum().item()
+    res = {}
+    with torch.no_grad():
+        for rel in (1e-4, 1e-5):
+            eps = rel * W0.abs().max().item()
+            fd = (J(W0 + eps * v).item() - J(W0 - eps * v).item()) / (2 * eps)
+            res["%g" % rel] = abs(fd - dJ) / abs(dJ)
+    cells = s.n_cells
+    value = cells * s.N * 3 * steps / (fwd_ms * 1e-3)
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": steps,
+           "warmup": 0, "ms_per_step": fwd_ms / steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "adjoint: 3D acoustic wave %d^3 periodic, k=2, SSP-RK3, %d steps "
+                                  "with frozen dt, L2 density misfit, checkpoint per step" % (n, steps),
+                      "cells": cells, "dt": dt},
+           "adjoint": {"forward_ms_per_step": fwd_ms / steps, "backward_ms_per_step": bwd_ms / steps,
+                       "checkpoint_bytes": steps * W0.numel() * W0.element_size(),
+                       "grad_rel_err_vs_central_fd": res, "J": val.item()}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def cpu_baseline(n_sample=128, max_seconds=20.0):
     """The oracle, as it stands, on a bounded sample of the workload: the
     vortex on a 128^2 periodic box with the same cell size, k and RK4."""
@@ -397,8 +495,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="both", choices=["both", "fp64", "fp32"],
                     help="run one precision only (profiling); the JSON line needs both")
-    ap.add_argument("--workload", default="vortex", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="vortex", choices=sorted(WORKLOADS) + ["adjoint3d"])
+    ap.add_argument("--size", type=int, default=128, help="adjoint3d: cells per axis")
     args = ap.parse_args()
+    if args.workload == "adjoint3d":
+        from paper_1506_06140_gb300 import build
+        build.build()
+        return run_adjoint(args)
     wprec = WORKLOADS[args.workload]["precisions"]
     args.precisions = wprec if args.precision == "both" else (args.precision,)
     args.warmup = max(args.warmup, 3)

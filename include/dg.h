@@ -135,9 +135,29 @@ int dg_compute_dt(dg_handle* h, const void* W_dev, double* dt_dev, void* stream)
 int dg_rk_step(dg_handle* h, void* W_dev, double dt, double* dt_used_dev, void* stream);
 
 /* n_steps CFL steps in place, recorded once into a CUDA graph per (W_dev,
- * n_steps) and replayed; dt_hist_dev (optional, double[n_steps]) receives the
- * timesteps.  The first call for a given W_dev/n_steps records the graph. */
+ * n_steps, dt_hist_dev) and replayed; dt_hist_dev (optional,
+ * double[n_steps][n_problems]) receives the timesteps.  The first call for a
+ * given key records the graph (make it outside any stream capture). */
 int dg_advance(dg_handle* h, void* W_dev, int n_steps, double* dt_hist_dev, void* stream);
+
+/* ---- ensembles of independent problems --------------------------------
+ * dg_create_batch: one handle for n_problems independent problems (same dim,
+ * uniform meshes, equal gamma -- DG_ERR_UNSUPPORTED otherwise) advanced
+ * together.  Their cells are concatenated in problem order into one state
+ * W[var][coef][cell]; each problem keeps its own edge length, boundaries and
+ * CFL timestep (dt_used_dev / dt_hist_dev then hold one double per problem,
+ * per step).  Every other entry point accepts a batch handle; dg_totals and
+ * dg_l1_density reduce over all problems together. */
+int dg_create_batch(const dg_mesh_desc* meshes, const double* gamma, int n_problems, int k,
+                    const dg_options* opt, dg_handle** out);
+
+/* n_steps steps of every problem of a batch (each with its own CFL
+ * timestep) as one CUDA-graph launch; same as dg_advance. */
+int dg_batch_advance(dg_handle* h, void* W_dev, int n_steps, double* dt_hist_dev, void* stream);
+
+/* Number of problems and, if cell_offsets_host is not NULL, the first cell
+ * of every problem (n_problems + 1 entries, the last one = n_cells). */
+int dg_n_problems(const dg_handle* h, int* n_problems, int64_t* cell_offsets_host);
 
 /* Adjoint of one unlimited step with a frozen timestep dt (> 0):
  * lam_n = (d W_{n+1} / d W_n)^T lam_np1, where W_n_dev is the checkpointed

@@ -340,8 +340,11 @@ __global__ void __launch_bounds__(AdjFaceTile<real, DIM, K>::THREADS)
       for (int q = 0; q < QF; ++q) up[q] = um[q];
     }
     // G traces scaled by the cell's prefactor and its integration weight
-    const real pm = cm >= 0 ? a.pre[a.m.level[cm]] * (vm ? real(1) / real(S::NSUB) : real(1)) : real(0);
-    const real pp = cp >= 0 ? a.pre[a.m.level[cp]] * (vp ? real(1) / real(S::NSUB) : real(1)) : real(0);
+    auto pre_of = [&](int cell) {
+      return a.pre_prob ? a.pre_prob[cell_problem(a.m, cell)] : a.pre[a.m.level[cell]];
+    };
+    const real pm = cm >= 0 ? pre_of(cm) * (vm ? real(1) / real(S::NSUB) : real(1)) : real(0);
+    const real pp = cp >= 0 ? pre_of(cp) * (vp ? real(1) / real(S::NSUB) : real(1)) : real(0);
 #pragma unroll
     for (int q = 0; q < QF; ++q) {
       sU[((0 * NV + v) * QF + q) * FB + fl] = um[q];
@@ -460,7 +463,8 @@ __global__ void __launch_bounds__(AdjCellTile<real, DIM, K>::THREADS)
   const int c = blockIdx.x * TC + tc;
   const bool valid = c < nc;
   const Tab1D<real>& T = a.t1;
-  const real pre = valid ? a.pre[a.m.level[c]] : real(0);
+  const real pre = !valid ? real(0)
+                   : (a.pre_prob ? a.pre_prob[cell_problem(a.m, c)] : a.pre[a.m.level[c]]);
   {
     real w[N], u[Q];
 #pragma unroll

@@ -23,26 +23,30 @@ const KernelSet* kernel_set(int prec, int dim, int k) {
   return &ks;
 }
 
-__global__ void set_scalar_kernel(double* dst, double value) { *dst = value; }
+__global__ void set_scalar_kernel(double* dst, int n, double value) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = value;
+}
 
-cudaError_t launch_set_scalar(double* dst, double value, cudaStream_t s) {
-  set_scalar_kernel<<<1, 1, 0, s>>>(dst, value);
+cudaError_t launch_set_scalar(double* dst, int n, double value, cudaStream_t s) {
+  set_scalar_kernel<<<(n + 255) / 256, 256, 0, s>>>(dst, n, value);
   return cudaGetLastError();
 }
 
-// the largest signal speed was accumulated as the bit pattern of a
-// non-negative double; dt = factor / speed
-__global__ void dt_finalize_kernel(const unsigned long long* bits, double factor, double* dt,
-                                   double* dt_copy) {
-  const double speed = __longlong_as_double((long long)*bits);
-  const double v = speed > 0.0 ? factor / speed : 0.0;
-  *dt = v;
-  if (dt_copy) *dt_copy = v;
+// the largest signal speed of each problem was accumulated as the bit
+// pattern of a non-negative double; dt = factor / speed
+__global__ void dt_finalize_kernel(const unsigned long long* bits, int nprob, double factor,
+                                   double* dt, double* dt_copy) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nprob; p += gridDim.x * blockDim.x) {
+    const double speed = __longlong_as_double((long long)bits[p]);
+    const double v = speed > 0.0 ? factor / speed : 0.0;
+    dt[p] = v;
+    if (dt_copy) dt_copy[p] = v;
+  }
 }
 
-cudaError_t launch_dt_finalize(const unsigned long long* bits, double factor, double* dt,
-                               double* dt_copy, cudaStream_t s) {
-  dt_finalize_kernel<<<1, 1, 0, s>>>(bits, factor, dt, dt_copy);
+cudaError_t launch_dt_finalize(const unsigned long long* bits, int nprob, double factor,
+                               double* dt, double* dt_copy, cudaStream_t s) {
+  dt_finalize_kernel<<<(nprob + 255) / 256, 256, 0, s>>>(bits, nprob, factor, dt, dt_copy);
   return cudaGetLastError();
 }
 

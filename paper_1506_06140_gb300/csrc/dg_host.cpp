@@ -400,8 +400,14 @@ struct dg_handle {
   Tab1D<double> tab1d64{};
   void* F = nullptr;
   std::vector<void*> regs;   // scratch state registers 1..n
-  double* scal = nullptr;    // [0] dt slot
-  unsigned long long* dt_bits = nullptr;
+  double* scal = nullptr;    // dt per problem [nprob]
+  unsigned long long* dt_bits = nullptr;  // per-problem max signal speed [nprob]
+  // ensembles
+  int nprob = 1;
+  std::vector<int32_t> prob;
+  std::vector<double> dx_prob, lo_prob;
+  void* pre_prob = nullptr;       // [nprob] 2^(1-d)/dx in the handle precision
+  double* inv_dx_prob = nullptr;  // [nprob]
   double* partial = nullptr;
   int* status = nullptr;
   Program prog_step;         // limited as configured
@@ -633,6 +639,80 @@ int build_mesh(dg_handle* h, const dg_mesh_desc* m) {
   return DG_OK;
 }
 
+// Concatenates independent uniform problems into one cell list: problem p
+// owns a contiguous range of cells, faces and table entries; indices are
+// shifted by the range offsets.
+int build_batch(dg_handle* h, const dg_mesh_desc* meshes, int nprob) {
+  std::vector<dg_handle*> parts;
+  struct Guard {
+    std::vector<dg_handle*>& v;
+    ~Guard() { for (auto* p : v) delete p; }
+  } guard{parts};
+  int nc = 0, nf = 0, nn = 0;
+  for (int p = 0; p < nprob; ++p) {
+    if (meshes[p].dim != meshes[0].dim)
+      return fail(h, DG_ERR_ARG, "dg_create_batch: all problems need the same dim");
+    if (meshes[p].n_refine_boxes != 0)
+      return fail(h, DG_ERR_UNSUPPORTED, "dg_create_batch: problems must be uniform meshes");
+    auto* t = new dg_handle();
+    parts.push_back(t);
+    const int r = build_mesh(t, &meshes[p]);
+    if (r != DG_OK) return fail(h, r, "dg_create_batch: problem " + std::to_string(p) + ": " + t->err);
+    if ((int64_t)nc + t->ncells > (1LL << 30)) return fail(h, DG_ERR_ARG, "dg_create_batch: too many cells");
+    nc += t->ncells;
+    nf += t->nfaces;
+    nn += t->nnodes;
+  }
+  const int d = meshes[0].dim;
+  h->ncells = nc;
+  h->nfaces = nf;
+  h->nnodes = nn;
+  h->nprob = nprob;
+  h->level.assign(nc, 0);
+  h->coord.assign((size_t)3 * nc, 0);
+  h->nbr.assign((size_t)2 * d * nc, -1);
+  h->sface.assign((size_t)2 * d * nc, -1);
+  h->scoarse.assign(nc, 0);
+  h->prob.assign(nc, 0);
+  h->fm.clear(); h->fp.clear(); h->finfo.clear();
+  h->node_children.clear();
+  h->dx_prob.assign(nprob, 0.0);
+  h->lo_prob.assign((size_t)3 * nprob, 0.0);
+  h->volume = 0.0;
+  int c0 = 0;
+  for (int p = 0; p < nprob; ++p) {
+    const dg_handle* t = parts[p];
+    const int tc = t->ncells;
+    const int f0 = (int)h->fm.size();
+    for (int c = 0; c < tc; ++c) {
+      h->level[c0 + c] = t->level[c];
+      h->prob[c0 + c] = p;
+      h->scoarse[c0 + c] = t->scoarse[c];
+      for (int a = 0; a < 3; ++a) h->coord[(size_t)a * nc + c0 + c] = t->coord[(size_t)a * tc + c];
+      for (int sd = 0; sd < 2 * d; ++sd) {
+        const int32_t v = t->nbr[(size_t)sd * tc + c];
+        h->nbr[(size_t)sd * nc + c0 + c] = v >= 0 ? v + c0 : v;
+        h->sface[(size_t)sd * nc + c0 + c] = t->sface[(size_t)sd * tc + c] + f0;
+      }
+    }
+    for (size_t f = 0; f < t->fm.size(); ++f) {
+      h->fm.push_back(t->fm[f] >= 0 ? t->fm[f] + c0 : -1);
+      h->fp.push_back(t->fp[f] >= 0 ? t->fp[f] + c0 : -1);
+      h->finfo.push_back(t->finfo[f]);
+    }
+    h->dx_prob[p] = t->md.dx0;
+    for (int a = 0; a < 3; ++a) h->lo_prob[3 * p + a] = t->md.lo[a];
+    h->volume += t->volume;
+    c0 += tc;
+  }
+  h->md = parts[0]->md;
+  h->md.ncells = nc;
+  h->md.nfaces = nf;
+  h->md.nnodes = nn;
+  h->md.nprob = nprob;
+  return DG_OK;
+}
+
 template <typename real>
 StageArgs<real> stage_args(dg_handle* h, const Op& op, const void* U, void* W) {
   StageArgs<real> a;
@@ -643,6 +723,7 @@ StageArgs<real> stage_args(dg_handle* h, const Op& op, const void* U, void* W) {
     for (size_t i = 0; i < sizeof(Tab1D<double>) / sizeof(double); ++i) dst[i] = (real)src[i];
   }
   for (int l = 0; l < 2; ++l) a.pre[l] = (real)(std::ldexp(1.0, 1 - h->dim) / std::ldexp(h->md.dx0, -l));
+  a.pre_prob = h->nprob > 1 ? static_cast<const real*>(h->pre_prob) : nullptr;
   a.tab = static_cast<const real*>(h->tab);
   a.U = static_cast<const real*>(U);
   a.F = static_cast<real*>(h->F);
@@ -687,6 +768,7 @@ AuxArgs<real> aux_args(dg_handle* h) {
   a.gamma = h->gamma;
   a.volume = h->volume;
   for (int l = 0; l < 2; ++l) a.inv_dx[l] = 1.0 / std::ldexp(h->md.dx0, -l);
+  a.inv_dx_prob = h->nprob > 1 ? h->inv_dx_prob : nullptr;
   a.dt_bits = h->dt_bits;
   a.status = h->status;
   return a;
@@ -703,13 +785,13 @@ double dt_factor(const dg_handle* h) {
 
 template <typename real>
 int compute_dt_impl(dg_handle* h, const void* W, double* copy, cudaStream_t s) {
-  DG_CUDA(h, cudaMemsetAsync(h->dt_bits, 0, sizeof(unsigned long long), s));
+  DG_CUDA(h, cudaMemsetAsync(h->dt_bits, 0, sizeof(unsigned long long) * h->nprob, s));
   AuxArgs<real> a = aux_args<real>(h);
   a.W = static_cast<const real*>(W);
   const double fac = dt_factor(h);
   DG_CUDA(h, timed(h, DG_KERNEL_DT, s, [&] { return h->ks->dt(&a, s); }));
   DG_CUDA(h, timed(h, DG_KERNEL_OTHER, s,
-                   [&] { return launch_dt_finalize(h->dt_bits, fac, h->scal, copy, s); }));
+                   [&] { return launch_dt_finalize(h->dt_bits, h->nprob, fac, h->scal, copy, s); }));
   return DG_OK;
 }
 
@@ -734,9 +816,10 @@ int step_impl(dg_handle* h, const Program& P, void* W, cudaStream_t s) {
 template <typename real>
 int rk_step_any(dg_handle* h, void* W, double dt, double* dt_used, cudaStream_t s) {
   if (dt > 0.0) {
-    DG_CUDA(h, timed(h, DG_KERNEL_OTHER, s, [&] { return launch_set_scalar(h->scal, dt, s); }));
+    DG_CUDA(h, timed(h, DG_KERNEL_OTHER, s, [&] { return launch_set_scalar(h->scal, h->nprob, dt, s); }));
     if (dt_used)
-      DG_CUDA(h, timed(h, DG_KERNEL_OTHER, s, [&] { return launch_set_scalar(dt_used, dt, s); }));
+      DG_CUDA(h, timed(h, DG_KERNEL_OTHER, s,
+                       [&] { return launch_set_scalar(dt_used, h->nprob, dt, s); }));
   } else {
     const int r = compute_dt_impl<real>(h, W, dt_used, s);
     if (r != DG_OK) return r;
@@ -787,6 +870,7 @@ int adjoint_rhs_into(dg_handle* h, const void* U, const void* G, void* acc, cuda
     for (size_t i = 0; i < sizeof(Tab1D<double>) / sizeof(double); ++i) dst[i] = (real)src[i];
   }
   for (int l = 0; l < 2; ++l) a.pre[l] = (real)(std::ldexp(1.0, 1 - h->dim) / std::ldexp(h->md.dx0, -l));
+  a.pre_prob = h->nprob > 1 ? static_cast<const real*>(h->pre_prob) : nullptr;
   a.U = static_cast<const real*>(U);
   a.G = static_cast<const real*>(G);
   a.FG = static_cast<real*>(h->FG);
@@ -870,11 +954,12 @@ int dg_default_options(dg_options* opt) {
 
 const char* dg_last_error(const dg_handle* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
 
-int dg_create(const dg_mesh_desc* mesh, int k, double gamma, const dg_options* opt,
-              dg_handle** out) {
+static int create_impl(const dg_mesh_desc* mesh, int nprob, int k, double gamma,
+                       const dg_options* opt, dg_handle** out) {
   if (!out) return fail(nullptr, DG_ERR_ARG, "dg_create: out is NULL");
   *out = nullptr;
   if (!mesh) return fail(nullptr, DG_ERR_ARG, "dg_create: mesh is NULL");
+  if (nprob < 1) return fail(nullptr, DG_ERR_ARG, "dg_create_batch: n_problems must be >= 1");
   if (mesh->dim != 2 && mesh->dim != 3) return fail(nullptr, DG_ERR_ARG, "dg_create: dim must be 2 or 3");
   if (!(gamma > 1.0)) return fail(nullptr, DG_ERR_ARG, "dg_create: gamma must exceed 1");
   dg_options o;
@@ -901,7 +986,7 @@ int dg_create(const dg_mesh_desc* mesh, int k, double gamma, const dg_options* o
     dg_destroy(h);
     return code;
   };
-  int r = build_mesh(h, mesh);
+  int r = nprob == 1 ? build_mesh(h, mesh) : build_batch(h, mesh, nprob);
   if (r != DG_OK) return bail(r);
   // tables
   std::vector<double> gx, gw, g3x, g3w, lx, lw, T;
@@ -934,6 +1019,29 @@ int dg_create(const dg_mesh_desc* mesh, int k, double gamma, const dg_options* o
   if ((r = upload(h, h->sface, &h->md.sface)) != DG_OK) return bail(r);
   if ((r = upload(h, h->scoarse, &h->md.scoarse)) != DG_OK) return bail(r);
   if ((r = upload(h, h->node_children, &h->md.node_children)) != DG_OK) return bail(r);
+  if (h->nprob > 1) {
+    if ((r = upload(h, h->prob, &h->md.prob)) != DG_OK) return bail(r);
+    if ((r = upload(h, h->dx_prob, &h->md.dx_prob)) != DG_OK) return bail(r);
+    if ((r = upload(h, h->lo_prob, &h->md.lo_prob)) != DG_OK) return bail(r);
+    std::vector<double> pre(h->nprob), inv(h->nprob);
+    for (int p = 0; p < h->nprob; ++p) {
+      pre[p] = std::ldexp(1.0, 1 - h->dim) / h->dx_prob[p];
+      inv[p] = 1.0 / h->dx_prob[p];
+    }
+    const double* dinv = nullptr;
+    if ((r = upload(h, inv, &dinv)) != DG_OK) return bail(r);
+    h->inv_dx_prob = const_cast<double*>(dinv);
+    if (h->prec == DG_FP64) {
+      const double* dp = nullptr;
+      if ((r = upload(h, pre, &dp)) != DG_OK) return bail(r);
+      h->pre_prob = const_cast<double*>(dp);
+    } else {
+      std::vector<float> pref(pre.begin(), pre.end());
+      const float* dp = nullptr;
+      if ((r = upload(h, pref, &dp)) != DG_OK) return bail(r);
+      h->pre_prob = const_cast<float*>(dp);
+    }
+  }
   // stage programs and scratch
   std::string perr;
   const bool limited = (o.slope_limiter != DG_LIMITER_NONE && k > 0) || (o.positivity && k > 0);
@@ -947,9 +1055,9 @@ int dg_create(const dg_mesh_desc* mesh, int k, double gamma, const dg_options* o
   }
   if ((r = dalloc(h, (size_t)h->nv * ks->QF * std::max(h->nfaces, 1) * h->esize, &h->F)) != DG_OK)
     return bail(r);
-  if ((r = dalloc(h, 8 * sizeof(double), &p)) != DG_OK) return bail(r);
+  if ((r = dalloc(h, (size_t)h->nprob * sizeof(double), &p)) != DG_OK) return bail(r);
   h->scal = static_cast<double*>(p);
-  if ((r = dalloc(h, sizeof(unsigned long long), &p)) != DG_OK) return bail(r);
+  if ((r = dalloc(h, (size_t)h->nprob * sizeof(unsigned long long), &p)) != DG_OK) return bail(r);
   h->dt_bits = static_cast<unsigned long long*>(p);
   const int nblk = (h->ncells + 255) / 256 + 1;
   if ((r = dalloc(h, (size_t)nblk * 8 * sizeof(double), &p)) != DG_OK) return bail(r);
@@ -963,6 +1071,25 @@ int dg_create(const dg_mesh_desc* mesh, int k, double gamma, const dg_options* o
     return bail(cuda_fail(h, cudaGetLastError(), "cudaStreamCreate"));
   *out = h;
   return DG_OK;
+}
+
+int dg_create(const dg_mesh_desc* mesh, int k, double gamma, const dg_options* opt,
+              dg_handle** out) {
+  return create_impl(mesh, 1, k, gamma, opt, out);
+}
+
+int dg_create_batch(const dg_mesh_desc* meshes, const double* gamma, int n_problems, int k,
+                    const dg_options* opt, dg_handle** out) {
+  if (!meshes || !gamma || n_problems < 1) {
+    if (out) *out = nullptr;
+    return fail(nullptr, DG_ERR_ARG, "dg_create_batch: bad arguments");
+  }
+  for (int p = 1; p < n_problems; ++p)
+    if (gamma[p] != gamma[0]) {
+      if (out) *out = nullptr;
+      return fail(nullptr, DG_ERR_UNSUPPORTED, "dg_create_batch: problems must share gamma");
+    }
+  return create_impl(meshes, n_problems, k, gamma[0], opt, out);
 }
 
 int dg_destroy(dg_handle* h) {
@@ -1080,7 +1207,8 @@ int dg_advance(dg_handle* h, void* W_dev, int n_steps, double* dt_hist_dev, void
     if (eb != cudaSuccess) { h->profiling = prof; return cuda_fail(h, eb, "cudaStreamBeginCapture"); }
     int r = DG_OK;
     for (int i = 0; i < n_steps && r == DG_OK; ++i)
-      r = rk_step_dispatch(h, W_dev, 0.0, dt_hist_dev ? dt_hist_dev + i : nullptr, h->cap_stream);
+      r = rk_step_dispatch(h, W_dev, 0.0, dt_hist_dev ? dt_hist_dev + (size_t)i * h->nprob : nullptr,
+                           h->cap_stream);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
     h->profiling = prof;
@@ -1093,6 +1221,27 @@ int dg_advance(dg_handle* h, void* W_dev, int n_steps, double* dt_hist_dev, void
     it = h->graphs.emplace(key, ge).first;
   }
   DG_CUDA(h, cudaGraphLaunch(it->second, s));
+  return DG_OK;
+}
+
+int dg_batch_advance(dg_handle* h, void* W_dev, int n_steps, double* dt_hist_dev, void* stream) {
+  return dg_advance(h, W_dev, n_steps, dt_hist_dev, stream);
+}
+
+int dg_n_problems(const dg_handle* h, int* n_problems, int64_t* cell_offsets_host) {
+  if (!check_handle(h) || !n_problems) return DG_ERR_ARG;
+  *n_problems = h->nprob;
+  if (cell_offsets_host) {
+    int64_t off = 0;
+    int p = 0;
+    cell_offsets_host[0] = 0;
+    for (int c = 0; c < h->ncells; ++c) {
+      const int pc = h->nprob > 1 ? h->prob[c] : 0;
+      while (p < pc) cell_offsets_host[++p] = c;
+      off = c + 1;
+    }
+    while (p < h->nprob) cell_offsets_host[++p] = off;
+  }
   return DG_OK;
 }
 

@@ -73,7 +73,16 @@ struct MeshDev {
   const int32_t* sface = nullptr;        // [2*dim][ncells] first face entry of each side
   const uint8_t* scoarse = nullptr;      // [ncells] bit s: side s holds NSUB sub-face entries
   const int32_t* node_children = nullptr;// [nnodes][2^dim]
+  // ensembles of independent problems (all nullptr for a single problem)
+  int nprob = 1;
+  const int32_t* prob = nullptr;         // [ncells] problem of the cell
+  const double* dx_prob = nullptr;       // [nprob] base edge length
+  const double* lo_prob = nullptr;       // [nprob][3] domain origin
 };
+
+__host__ __device__ __forceinline__ int cell_problem(const MeshDev& m, int c) {
+  return m.prob ? m.prob[c] : 0;
+}
 
 // bits of the device status word
 constexpr int DG_ERR_NONPHYSICAL_BIT = 4;
@@ -89,6 +98,7 @@ struct StageArgs {
   MeshDev m;
   Tab1D<real> t1;
   real pre[2] = {0, 0};         // 2^(1-d) / dx per refinement level
+  const real* pre_prob = nullptr;  // [nprob] 2^(1-d) / dx per problem (ensembles)
   const real* tab = nullptr;
   const real* U = nullptr;
   real* F = nullptr;            // face fluxes [NV][QF][nfaces]
@@ -98,7 +108,7 @@ struct StageArgs {
   real* out[MAX_OUT] = {nullptr, nullptr, nullptr};
   real C[MAX_OUT][MAX_IN] = {};
   real ck[MAX_OUT] = {};
-  const double* dt = nullptr;   // device scalar; nullptr means dt = 1
+  const double* dt = nullptr;   // device timestep per problem; nullptr means dt = 1
 };
 
 template <typename real>
@@ -129,6 +139,7 @@ struct AuxArgs {
   double dt_factor = 1.0;         // CFL factor of the timestep formula
   double volume = 1.0;            // domain volume (L1)
   double inv_dx[2] = {1.0, 1.0};  // 1 / edge length per refinement level
+  const double* inv_dx_prob = nullptr;  // [nprob] 1 / base edge length (ensembles)
   unsigned long long* dt_bits = nullptr;
   int* status = nullptr;
 };
@@ -140,6 +151,7 @@ struct AdjointArgs {
   MeshDev m;
   Tab1D<real> t1;
   real pre[2] = {0, 0};          // 2^(1-d) / dx per refinement level
+  const real* pre_prob = nullptr;  // [nprob] per problem (ensembles)
   const real* U = nullptr;       // state at which dW/dt is linearised
   const real* G = nullptr;       // cotangent of dW/dt (layout of W)
   real* FG = nullptr;            // face cotangents of the traces [2 sides][NV][QF][nfaces]
@@ -185,8 +197,8 @@ struct KernelSet {
 const KernelSet* kernel_set(int prec, int dim, int k);
 
 // shared helper kernels (dg_common.cu)
-cudaError_t launch_set_scalar(double* dst, double value, cudaStream_t s);
-cudaError_t launch_dt_finalize(const unsigned long long* bits, double factor, double* dt, double* dt_copy,
-                               cudaStream_t s);
+cudaError_t launch_set_scalar(double* dst, int n, double value, cudaStream_t s);
+cudaError_t launch_dt_finalize(const unsigned long long* bits, int nprob, double factor, double* dt,
+                               double* dt_copy, cudaStream_t s);
 
 }  // namespace dgi

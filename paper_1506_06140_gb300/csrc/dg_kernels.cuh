@@ -221,7 +221,8 @@ template <typename real>
 __device__ __forceinline__ real ld(const real* p) { return __ldg(p); }
 
 __device__ __forceinline__ double cell_dx(const MeshDev& m, int c) {
-  return ldexp(m.dx0, -(int)m.level[c]);
+  const double base = m.dx_prob ? m.dx_prob[m.prob[c]] : m.dx0;
+  return ldexp(base, -(int)m.level[c]);
 }
 
 // ===========================================================================
@@ -476,11 +477,12 @@ __device__ __forceinline__ double block_sum(double x, double* sh) {
 template <typename real, int DIM, int K>
 __global__ void __launch_bounds__(RED_THREADS) dt_kernel(const AuxArgs<real> a) {
   using S = Shape<DIM, K>;
-  __shared__ double sh[RED_THREADS];
   const int c = blockIdx.x * RED_THREADS + threadIdx.x;
   const int nc = a.m.ncells;
   double speed = 0.0;
+  int pb = 0;
   if (c < nc) {
+    pb = cell_problem(a.m, c);
     double u[S::NV];
     for (int v = 0; v < S::NV; ++v) u[v] = (double)a.W[(size_t)(v * S::N) * nc + c];
     const double rinv = 1.0 / u[0];
@@ -493,16 +495,22 @@ __global__ void __launch_bounds__(RED_THREADS) dt_kernel(const AuxArgs<real> a) 
       const double cs = sqrt(a.gamma * p * rinv);
       double sum = 0.0;
       for (int b = 0; b < DIM; ++b) sum += fabs(u[1 + b] * rinv) + cs;
-      speed = sum * a.inv_dx[a.m.level[c]];
+      const double inv_dx = a.inv_dx_prob ? a.inv_dx_prob[pb] : a.inv_dx[0];
+      speed = sum * inv_dx * (double)(1 << a.m.level[c]);
     }
+  } else {
+    pb = -1;
   }
-  sh[threadIdx.x] = speed;
-  __syncthreads();
-  for (int s = RED_THREADS / 2; s > 0; s >>= 1) {
-    if ((int)threadIdx.x < s) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + s]);
-    __syncthreads();
+  // one atomic per warp when the warp's cells belong to one problem
+  const unsigned full = 0xffffffffu;
+  const int p0 = __shfl_sync(full, pb, 0);
+  if (__all_sync(full, pb == p0 || pb < 0)) {
+    for (int off = 16; off > 0; off >>= 1) speed = fmax(speed, __shfl_xor_sync(full, speed, off));
+    if ((threadIdx.x & 31) == 0 && p0 >= 0)
+      atomicMax(a.dt_bits + p0, (unsigned long long)__double_as_longlong(speed));
+  } else if (pb >= 0) {
+    atomicMax(a.dt_bits + pb, (unsigned long long)__double_as_longlong(speed));
   }
-  if (threadIdx.x == 0) atomicMax(a.dt_bits, (unsigned long long)__double_as_longlong(sh[0]));
 }
 
 template <typename real, int DIM, int K>
@@ -583,7 +591,8 @@ __global__ void points_kernel(const AuxArgs<real> a, int l1rule) {
   const double* xi = a.tab64 + (l1rule ? S::OFF_XI1 : S::OFF_XI);
   const double dx = cell_dx(a.m, c);
   for (int d = 0; d < DIM; ++d) {
-    const double ctr = a.m.lo[d] + ((double)a.m.coord[(size_t)d * nc + c] + 0.5) * dx;
+    const double lo = a.m.lo_prob ? a.m.lo_prob[3 * a.m.prob[c] + d] : a.m.lo[d];
+    const double ctr = lo + ((double)a.m.coord[(size_t)d * nc + c] + 0.5) * dx;
     for (int q = 0; q < nq; ++q) a.out[((size_t)d * nq + q) * nc + c] = ctr + 0.5 * dx * xi[q * 3 + d];
   }
 }
@@ -689,7 +698,7 @@ template <typename real, int DIM, int K>
 cudaError_t launch_dt(const void* pa, cudaStream_t s) {
   const auto& a = *static_cast<const AuxArgs<real>*>(pa);
   if (a.m.ncells == 0) return cudaSuccess;
-  dt_kernel<real, DIM, K><<<(a.m.ncells + RED_THREADS - 1) / RED_THREADS, RED_THREADS, 0, s>>>(a);
+  dt_kernel<real, DIM, K><<<(a.m.ncells + RED_THREADS - 1) / RED_THREADS, RED_THREADS, 0, s>>>(a);  // per-problem max
   return cudaGetLastError();
 }
 

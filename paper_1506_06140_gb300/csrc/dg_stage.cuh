@@ -489,8 +489,9 @@ __global__ void __launch_bounds__(CellTile<real, DIM, K>::THREADS)
   }
 
   // 4. epilogue
-  const real pre = a.pre[a.m.level[c]];
-  const real dtv = a.dt ? real(*a.dt) : real(1);
+  const int pb = cell_problem(a.m, c);
+  const real pre = a.pre_prob ? a.pre_prob[pb] : a.pre[a.m.level[c]];
+  const real dtv = a.dt ? real(a.dt[pb]) : real(1);
   const int n_out = a.n_out, n_in = a.n_in;
 #pragma unroll
   for (int j = 0; j < N; ++j) {

@@ -23,7 +23,8 @@ EXPORTS = ["dg_default_options", "dg_create", "dg_destroy", "dg_last_error", "dg
            "dg_quad_points", "dg_l1_points", "dg_project", "dg_rhs", "dg_compute_dt",
            "dg_rk_step", "dg_advance", "dg_rk_step_adjoint", "dg_limit", "dg_totals",
            "dg_l1_density", "dg_node_weights", "dg_neighbor_table", "dg_cell_levels",
-           "dg_status", "dg_profile_begin", "dg_profile_end", "dg_totals_noalloc"]
+           "dg_status", "dg_profile_begin", "dg_profile_end", "dg_totals_noalloc",
+           "dg_create_batch", "dg_batch_advance", "dg_n_problems"]
 KERNEL_KINDS = ["face", "cell", "limit", "dt", "other", "adjoint"]
 
 
@@ -80,6 +81,10 @@ def load(path=LIB_PATH):
     L.dg_neighbor_table.argtypes = [vp, i32p]
     L.dg_cell_levels.argtypes = [vp, i32p]
     L.dg_status.argtypes = [vp, C.POINTER(C.c_int)]
+    L.dg_create_batch.argtypes = [C.POINTER(MeshDesc), C.POINTER(C.c_double), C.c_int, C.c_int,
+                                  C.POINTER(Options), C.POINTER(vp)]
+    L.dg_batch_advance.argtypes = [vp, vp, C.c_int, vp, vp]
+    L.dg_n_problems.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int64)]
     L.dg_totals_noalloc.argtypes = [C.c_int, C.c_int, C.c_int64, C.c_int, C.c_double, vp, vp,
                                      vp, vp]
     L.dg_profile_begin.argtypes = [vp]
@@ -123,22 +128,29 @@ class Solver:
 
     def __init__(self, mesh, k, gamma=1.4, rk_order=3, cfl=0.2, limiter="none", beta=1.0,
                  Mtilde=0.5, positivity=False, eps=1e-10, precision="fp64"):
+        """mesh: one mesh dict, or a list of them for an ensemble of
+        independent problems advanced together (dg_create_batch)."""
         L = load()
         self._L = L
-        self.mesh = dict(mesh)
-        self.dim, self.k, self.gamma = mesh["dim"], k, gamma
-        md = MeshDesc()
-        md.dim = mesh["dim"]
-        for a in range(3):
-            md.n[a] = int(mesh["n"][a]) if a < md.dim else 1
-            md.lo[a] = float(mesh["lo"][a]) if a < md.dim else 0.0
-            md.hi[a] = float(mesh["hi"][a]) if a < md.dim else 1.0
-            bc = mesh.get("bc") or [DG_BC_PERIODIC] * md.dim
-            md.bc[a] = int(bc[a]) if a < md.dim else 0
-        boxes = mesh.get("refine_boxes") or []
-        self._boxes = np.ascontiguousarray(np.array(boxes, dtype=np.int32).reshape(-1))
-        md.n_refine_boxes = len(boxes)
-        md.refine_boxes = self._boxes.ctypes.data_as(C.POINTER(C.c_int32)) if len(boxes) else None
+        meshes = list(mesh) if isinstance(mesh, (list, tuple)) else [mesh]
+        self.batch = isinstance(mesh, (list, tuple))
+        self.mesh = dict(meshes[0])
+        self.dim, self.k, self.gamma = meshes[0]["dim"], k, gamma
+        descs = (MeshDesc * len(meshes))()
+        self._boxes = []
+        for md, m in zip(descs, meshes):
+            md.dim = m["dim"]
+            for a in range(3):
+                md.n[a] = int(m["n"][a]) if a < md.dim else 1
+                md.lo[a] = float(m["lo"][a]) if a < md.dim else 0.0
+                md.hi[a] = float(m["hi"][a]) if a < md.dim else 1.0
+                bc = m.get("bc") or [DG_BC_PERIODIC] * md.dim
+                md.bc[a] = int(bc[a]) if a < md.dim else 0
+            boxes = m.get("refine_boxes") or []
+            arr = np.ascontiguousarray(np.array(boxes, dtype=np.int32).reshape(-1))
+            self._boxes.append(arr)
+            md.n_refine_boxes = len(boxes)
+            md.refine_boxes = arr.ctypes.data_as(C.POINTER(C.c_int32)) if len(boxes) else None
         opt = Options()
         L.dg_default_options(C.byref(opt))
         opt.rk_order, opt.cfl = rk_order, cfl
@@ -150,7 +162,11 @@ class Solver:
         self.dtype = torch.float64 if precision == "fp64" else torch.float32
         torch.cuda.init()
         h = C.c_void_p()
-        r = L.dg_create(C.byref(md), k, gamma, C.byref(opt), C.byref(h))
+        if self.batch:
+            gam = (C.c_double * len(meshes))(*([gamma] * len(meshes)))
+            r = L.dg_create_batch(descs, gam, len(meshes), k, C.byref(opt), C.byref(h))
+        else:
+            r = L.dg_create(descs, k, gamma, C.byref(opt), C.byref(h))
         if r != DG_OK:
             raise DGError(r, L.dg_last_error(None).decode())
         self._h = h
@@ -160,6 +176,12 @@ class Solver:
         self.n_cells, self.N, self.nv = nc.value, N.value, nv.value
         self.nq, self.nq1, self.n_nodes = nq.value, nq1.value, nn.value
         self.device = torch.device("cuda", torch.cuda.current_device())
+        npb = C.c_int()
+        self._check(L.dg_n_problems(h, C.byref(npb), None))
+        self.n_problems = npb.value
+        offs = (C.c_int64 * (self.n_problems + 1))()
+        self._check(L.dg_n_problems(h, C.byref(npb), offs))
+        self.cell_offsets = np.array(offs[:], dtype=np.int64)
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -179,6 +201,10 @@ class Solver:
     # -- allocation helpers (torch owns the memory) --
     def empty_state(self):
         return torch.empty((self.nv, self.N, self.n_cells), dtype=self.dtype, device=self.device)
+
+    def dt_buffer(self, n_steps=1):
+        """device buffer for timesteps: one per problem and step"""
+        return torch.zeros(n_steps * self.n_problems, dtype=torch.float64, device=self.device)
 
     def scalar(self, n=1):
         return torch.zeros(n, dtype=torch.float64, device=self.device)
@@ -207,7 +233,7 @@ class Solver:
         return out
 
     def compute_dt(self, W, out=None):
-        out = self.scalar() if out is None else out
+        out = self.scalar(self.n_problems) if out is None else out
         self._check(self._L.dg_compute_dt(self._h, self._state(W), _ptr(out), _stream()))
         return out
 
