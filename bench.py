@@ -39,8 +39,8 @@ WORKLOADS = {
     "vortex": dict(
         name="isentropic vortex 2D, 256x256 periodic [-5,5]^2, k=3 (10 coeffs/cell/var), "
              "SSP-RK4 (5 stages), no limiter, CFL 0.2",
-        dim=2, k=3, rk=4, stages=5, limiter="none", positivity=False, precisions=("fp64", "fp32"),
-        tag="vortex256_k3"),
+        dim=2, k=3, rk=4, stages=5, limiter="none", positivity=False,
+        precisions=("fp64", "fp32", "fp32_tc"), tag="vortex256_k3"),
     "ensemble": dict(
         name="512 independent isentropic vortices (strength U(3,6)) on periodic [-5,5]^2 with "
              "sizes drawn from {32,48,64,96,128}^2 (3.4M cells), k=2 (6 coeffs/cell/var), SSP-RK3, "
@@ -339,6 +339,8 @@ def summarize(args, results, world):
         esize = 8 if precision == "fp64" else 4
         kname = {"cell": "cell_update_kernel", "face": "face_flux_kernel",
                  "limit": "limit_kernel"}.get(kind, kind)
+        if precision == "fp32_tc" and kind == "cell":
+            kname = "cell_update_tc_kernel"
         tag = "%s_%s" % (wk["tag"], precision)
         if precision == "fp64" and kind in ("cell", "face"):
             fc, ff = kernel_flops(dim, k)
@@ -431,6 +433,45 @@ def run_adjoint(args):
     return 0
 
 
+def run_l1_study(args):
+    """L1 density error of the vortex against its closed form after t_end,
+    per precision and resolution, with the device time per RK stage: the
+    data for comparing precisions at equal L1 error."""
+    import torch
+    from paper_1506_06140_gb300 import dg
+    from paper_1506_06140_gb300 import workloads as wl
+    torch.cuda.set_device(0)
+    t_end = args.t_end
+    rows = []
+    for precision in ("fp64", "fp32", "fp32_tc"):
+        for n in (32, 64, 128, 256):
+            s = dg.Solver(mesh(n), K_DEG, 1.4, rk_order=RK_ORDER, cfl=CFL, precision=precision)
+            W = s.project(torch.as_tensor(wl.vortex(s.quad_points().cpu().numpy())))
+            dt = s.compute_dt(W).item()  # the vortex translates; its CFL timestep stays put
+            nsteps = int(math.ceil(t_end / dt))
+            dt = t_end / nsteps
+            st = torch.cuda.current_stream()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(st)
+            for _ in range(nsteps):
+                s.rk_step(W, dt)
+            e1.record(st)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            rho_ex = wl.vortex(s.l1_points().cpu().numpy(), t=t_end)[0]
+            l1 = s.l1_density(W, torch.as_tensor(rho_ex)).item()
+            rows.append({"precision": precision, "n": n, "steps": nsteps, "L1": l1,
+                         "ms_per_stage": ms / (nsteps * STAGES),
+                         "dof_updates_per_s": n * n * N_BASIS * STAGES * nsteps / (ms * 1e-3)})
+            print(json.dumps(rows[-1]), flush=True)
+    out = {"metric": "L1 density error vs closed form and DOF-updates/s per RK stage",
+           "config": {"workload": "isentropic vortex k=3 SSP-RK4 CFL 0.2 to t=%g" % t_end},
+           "rows": rows}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def cpu_baseline(n_sample=128, max_seconds=20.0):
     """The oracle, as it stands, on a bounded sample of the workload: the
     vortex on a 128^2 periodic box with the same cell size, k and RK4."""
@@ -493,15 +534,17 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precision", default="both", choices=["both", "fp64", "fp32"],
+    ap.add_argument("--precision", default="both", choices=["both", "fp64", "fp32", "fp32_tc"],
                     help="run one precision only (profiling); the JSON line needs both")
-    ap.add_argument("--workload", default="vortex", choices=sorted(WORKLOADS) + ["adjoint3d"])
+    ap.add_argument("--workload", default="vortex",
+                    choices=sorted(WORKLOADS) + ["adjoint3d", "l1study"])
+    ap.add_argument("--t-end", type=float, default=2.0, help="l1study: final time")
     ap.add_argument("--size", type=int, default=128, help="adjoint3d: cells per axis")
     args = ap.parse_args()
-    if args.workload == "adjoint3d":
+    if args.workload in ("adjoint3d", "l1study"):
         from paper_1506_06140_gb300 import build
         build.build()
-        return run_adjoint(args)
+        return run_adjoint(args) if args.workload == "adjoint3d" else run_l1_study(args)
     wprec = WORKLOADS[args.workload]["precisions"]
     args.precisions = wprec if args.precision == "both" else (args.precision,)
     args.warmup = max(args.warmup, 3)
@@ -535,9 +578,9 @@ def main():
            "data": "synthetic", "config": workload_config("vortex", "fp64", head["cells"]),
            "roofline": head["roofline"], "e2e": head["e2e"], "gpu_launches": head["gpu_launches"],
            "clocks": head["clocks"], "kernel_ms": head["kernel_ms"],
-           "variants": {"fp32": {k: lines["fp32"][k] for k in
-                                 ("value", "ms_per_step", "roofline", "e2e", "gpu_launches",
-                                  "clocks", "kernel_ms")}}}
+           "variants": {p: {k: lines[p][k] for k in
+                            ("value", "ms_per_step", "roofline", "e2e", "gpu_launches",
+                             "clocks", "kernel_ms")} for p in ("fp32", "fp32_tc") if p in lines}}
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()
     print(json.dumps(out), flush=True)

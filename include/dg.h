@@ -49,7 +49,10 @@ enum {
 
 enum { DG_BC_PERIODIC = 0, DG_BC_TRANSMISSIVE = 1 };
 enum { DG_LIMITER_NONE = 0, DG_LIMITER_COMPONENT = 1, DG_LIMITER_CHARACTERISTIC = 2 };
-enum { DG_FP64 = 0, DG_FP32 = 1 };
+/* DG_FP32_TC: FP32 state with the cell kernel's contractions on the tensor
+ * cores (3xTF32: split operands, FP32 accumulation); 2D uniform meshes,
+ * k = 1..3 (DG_ERR_UNSUPPORTED otherwise). */
+enum { DG_FP64 = 0, DG_FP32 = 1, DG_FP32_TC = 2 };
 
 /* Mesh description (paper Secs. 2.2 and 4): cubical cells on the box
  * [lo, hi]; n[a] base cells along axis a (the base edge length must be equal
@@ -76,8 +79,8 @@ typedef struct {
   double Mtilde;     /* TVB bound: a slope is kept when |sqrt(3) slope| <= Mtilde * dx */
   int positivity;    /* 1: positivity limiter of Sec. 3.4 after every stage */
   double eps;        /* positivity floor */
-  int precision;     /* DG_FP64 or DG_FP32 (state, fluxes and contractions); the
-                        totals, L1 error, timestep and positivity check stay FP64 */
+  int precision;     /* DG_FP64, DG_FP32 or DG_FP32_TC (state, fluxes and contractions);
+                        the totals, L1 error, timestep and positivity check stay FP64 */
 } dg_options;
 
 typedef struct dg_handle dg_handle;

@@ -400,6 +400,8 @@ struct dg_handle {
   Tab1D<double> tab1d64{};
   void* F = nullptr;
   std::vector<void*> regs;   // scratch state registers 1..n
+  bool use_tc = false;       // tensor-core cell kernel (DG_FP32_TC)
+  void* tcB = nullptr;       // its B operands
   double* scal = nullptr;    // dt per problem [nprob]
   unsigned long long* dt_bits = nullptr;  // per-problem max signal speed [nprob]
   // ensembles
@@ -713,6 +715,10 @@ int build_batch(dg_handle* h, const dg_mesh_desc* meshes, int nprob) {
   return DG_OK;
 }
 
+cudaError_t cell_launch(dg_handle* h, const void* args, cudaStream_t s) {
+  return h->use_tc ? h->ks->cell_tc(args, s) : h->ks->cell(args, s);
+}
+
 template <typename real>
 StageArgs<real> stage_args(dg_handle* h, const Op& op, const void* U, void* W) {
   StageArgs<real> a;
@@ -724,6 +730,8 @@ StageArgs<real> stage_args(dg_handle* h, const Op& op, const void* U, void* W) {
   }
   for (int l = 0; l < 2; ++l) a.pre[l] = (real)(std::ldexp(1.0, 1 - h->dim) / std::ldexp(h->md.dx0, -l));
   a.pre_prob = h->nprob > 1 ? static_cast<const real*>(h->pre_prob) : nullptr;
+  a.tcB = static_cast<const real*>(h->tcB);
+  a.status = h->status;
   a.tab = static_cast<const real*>(h->tab);
   a.U = static_cast<const real*>(U);
   a.F = static_cast<real*>(h->F);
@@ -802,7 +810,7 @@ int step_impl(dg_handle* h, const Program& P, void* W, cudaStream_t s) {
     void* U = op.in_reg == 0 ? W : h->regs[op.in_reg - 1];
     StageArgs<real> a = stage_args<real>(h, op, U, W);
     DG_CUDA(h, timed(h, DG_KERNEL_FACE, s, [&] { return h->ks->face(&a, s); }));
-    DG_CUDA(h, timed(h, DG_KERNEL_CELL, s, [&] { return h->ks->cell(&a, s); }));
+    DG_CUDA(h, timed(h, DG_KERNEL_CELL, s, [&] { return cell_launch(h, &a, s); }));
     if (op.lim_src >= 0) {
       void* src = op.lim_src == 0 ? W : h->regs[op.lim_src - 1];
       void* dst = op.lim_dst == 0 ? W : h->regs[op.lim_dst - 1];
@@ -855,7 +863,7 @@ int rhs_into(dg_handle* h, const void* U, void* out, cudaStream_t s) {
   a.out[0] = static_cast<real*>(out);
   a.dt = nullptr;
   DG_CUDA(h, timed(h, DG_KERNEL_FACE, s, [&] { return h->ks->face(&a, s); }));
-  DG_CUDA(h, timed(h, DG_KERNEL_CELL, s, [&] { return h->ks->cell(&a, s); }));
+  DG_CUDA(h, timed(h, DG_KERNEL_CELL, s, [&] { return cell_launch(h, &a, s); }));
   return DG_OK;
 }
 
@@ -967,7 +975,10 @@ static int create_impl(const dg_mesh_desc* mesh, int nprob, int k, double gamma,
   if (opt) o = *opt;
   if (o.rk_order < 1 || o.rk_order > 4) return fail(nullptr, DG_ERR_ARG, "dg_create: rk_order must be 1..4");
   if (o.slope_limiter < 0 || o.slope_limiter > 2) return fail(nullptr, DG_ERR_ARG, "dg_create: bad slope_limiter");
-  if (o.precision != DG_FP64 && o.precision != DG_FP32) return fail(nullptr, DG_ERR_ARG, "dg_create: bad precision");
+  if (o.precision != DG_FP64 && o.precision != DG_FP32 && o.precision != DG_FP32_TC)
+    return fail(nullptr, DG_ERR_ARG, "dg_create: bad precision");
+  const bool use_tc = o.precision == DG_FP32_TC;
+  if (use_tc) o.precision = DG_FP32;
   if (!(o.cfl > 0.0)) return fail(nullptr, DG_ERR_ARG, "dg_create: cfl must be positive");
   const KernelSet* ks = kernel_set(o.precision, mesh->dim, k);
   if (!ks) return fail(nullptr, DG_ERR_UNSUPPORTED, "dg_create: (dim, k, precision) not compiled");
@@ -978,6 +989,7 @@ static int create_impl(const dg_mesh_desc* mesh, int nprob, int k, double gamma,
   h->gamma = gamma;
   h->opt = o;
   h->ks = ks;
+  h->use_tc = use_tc;
   h->nv = ks->NV;
   h->N = ks->N;
   h->esize = o.precision == DG_FP64 ? 8 : 4;
@@ -1067,6 +1079,19 @@ static int create_impl(const dg_mesh_desc* mesh, int nprob, int k, double gamma,
   if (cudaMemset(h->status, 0, sizeof(int)) != cudaSuccess)
     return bail(cuda_fail(h, cudaGetLastError(), "cudaMemset"));
   if (ks->prepare() != cudaSuccess) return bail(cuda_fail(h, cudaGetLastError(), "kernel attributes"));
+  if (h->use_tc) {
+    if (!ks->cell_tc || h->nnodes > 0)
+      return bail(fail(h, DG_ERR_UNSUPPORTED,
+                       "dg_create: DG_FP32_TC needs a uniform 2D mesh and k = 1..3"));
+    if (ks->prepare_tc() != cudaSuccess)
+      return bail(cuda_fail(h, cudaGetLastError(), "kernel attributes"));
+    std::vector<float> B;
+    ks->fill_tc(T, B);
+    if ((r = dalloc(h, B.size() * sizeof(float), &p)) != DG_OK) return bail(r);
+    h->tcB = p;
+    if (cudaMemcpy(p, B.data(), B.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+      return bail(cuda_fail(h, cudaGetLastError(), "cudaMemcpy tensor-core tables"));
+  }
   if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
     return bail(cuda_fail(h, cudaGetLastError(), "cudaStreamCreate"));
   *out = h;
@@ -1175,7 +1200,7 @@ int dg_rhs(dg_handle* h, const void* W_dev, void* dWdt_dev, void* stream) {
     a.out[0] = static_cast<float*>(dWdt_dev);
     a.dt = nullptr;
     DG_CUDA(h, h->ks->face(&a, s));
-    DG_CUDA(h, h->ks->cell(&a, s));
+    DG_CUDA(h, cell_launch(h, &a, s));
   }
   return DG_OK;
 }

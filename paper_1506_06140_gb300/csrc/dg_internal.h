@@ -109,6 +109,8 @@ struct StageArgs {
   real C[MAX_OUT][MAX_IN] = {};
   real ck[MAX_OUT] = {};
   const double* dt = nullptr;   // device timestep per problem; nullptr means dt = 1
+  const real* tcB = nullptr;    // tensor-core B operands (tensor-core cell kernel)
+  int* status = nullptr;        // device status word
 };
 
 template <typename real>
@@ -192,6 +194,10 @@ struct KernelSet {
   cudaError_t (*adj_face)(const void* adj_args, cudaStream_t s) = nullptr;
   cudaError_t (*adj_cell)(const void* adj_args, cudaStream_t s) = nullptr;
   cudaError_t (*combine)(const void* combine_args, cudaStream_t s) = nullptr;
+  // tensor-core cell kernel (FP32 state, 2D, k = 1..3), nullptr where not built
+  cudaError_t (*cell_tc)(const void* stage_args, cudaStream_t s) = nullptr;
+  cudaError_t (*prepare_tc)() = nullptr;
+  void (*fill_tc)(const std::vector<double>& tab, std::vector<float>& out) = nullptr;
 };
 
 const KernelSet* kernel_set(int prec, int dim, int k);

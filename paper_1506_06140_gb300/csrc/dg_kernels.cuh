@@ -15,12 +15,14 @@
 #include <cmath>
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "dg_internal.h"
 #include "dg_physics.cuh"
 #include "dg_stage.cuh"
 #include "dg_adjoint.cuh"
+#include "dg_tc.cuh"
 
 namespace dgi {
 
@@ -759,6 +761,11 @@ KernelSet make_kernel_set(int prec) {
   ks.adj_face = &launch_adj_face<real, DIM, K>;
   ks.adj_cell = &launch_adj_cell<real, DIM, K>;
   ks.combine = &launch_combine<real>;
+  if constexpr (std::is_same<real, float>::value && DIM == 2 && K >= 1 && K <= 3) {
+    ks.cell_tc = &launch_cell_tc<K>;
+    ks.prepare_tc = &prepare_cell_tc<K>;
+    ks.fill_tc = &fill_tc_tables<K>;
+  }
   return ks;
 }
 

@@ -313,3 +313,52 @@ def test_vortex_256_k3_rk4_full_size_fp64():
     s.rk_step(Wd, dt)
     e, _ = rel_err(Wd.cpu().numpy() - W, ref - W)
     assert e < 1e-10
+
+
+# ---------------------------------------------------------------------------
+# tensor-core cell kernel (FP32 state, 3xTF32 contractions)
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_rhs_fp32_tensor_cores(k):
+    m = MESHES["u2"]
+    o = oracle_for(m, k)
+    s = solver_for(m, k, precision="fp32_tc")
+    W = wl.random_weights(2, o.N, o.n_cells, seed=900 + k).astype(np.float32)
+    ref = o.rhs(W.astype(np.float64))
+    got = s.rhs(to_dev(s, W)).cpu().numpy()
+    e, erms = rel_err(got, ref)
+    assert e < TOL32_MAX and erms < TOL32_RMS, (k, e, erms)
+    assert s.status() == 0
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp32_tc"])
+def test_rk4_step_fp32_vortex_full_size(precision):
+    """On the smooth 256^2 vortex dW/dt is a strong cancellation of the volume
+    and surface terms: pre * max|f| * sum_q |dphi| w ~ 2e3 against
+    max |dW/dt| ~ 1.4, a factor ~1.4e3.  FP32 round-off (6e-8) times that
+    factor and the ~sqrt(50) terms of a sum bounds the error at ~6e-4 of
+    max |dW/dt|: both the CUDA-core FP32 sums and the split-TF32 tensor-core
+    products (about 2^-21 each) must stay within 1e-3 (RMS 5e-5)."""
+    m = wl.mesh_uniform(2, [256, 256], [-5.0, -5.0], [5.0, 5.0])
+    o = oracle_for(m, 3, rk_order=4)
+    s = solver_for(m, 3, rk_order=4, precision=precision)
+    U = wl.vortex(o.quad_points())
+    Wd = s.project(torch.as_tensor(U))
+    W = Wd.double().cpu().numpy()
+    e, erms = rel_err(s.rhs(Wd).cpu().numpy(), o.rhs(W))
+    assert e < 1e-3 and erms < 5e-5, (e, erms)
+    dt = o.compute_dt(W)
+    ref, _ = o.rk_step(W, dt)
+    s.rk_step(Wd, dt)
+    got = Wd.double().cpu().numpy()
+    assert np.max(np.abs(got - ref)) < 1e-6 * np.max(np.abs(ref))
+    assert s.status() == 0
+
+
+def test_tensor_core_variant_rejects_unsupported_meshes():
+    dg = dg_mod()
+    with pytest.raises(dg.DGError) as ei:
+        solver_for(MESHES["amr2"], 2, precision="fp32_tc")
+    assert ei.value.code == dg.DG_ERR_UNSUPPORTED
+    with pytest.raises(dg.DGError):
+        solver_for(MESHES["u3"], 2, precision="fp32_tc")
