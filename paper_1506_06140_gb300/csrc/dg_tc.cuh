@@ -26,19 +26,24 @@ namespace dgi {
 template <int K>
 struct TcShape {
   using S = Shape<2, K>;
-  static constexpr int TC = 32;                          // cells per CTA
+  static constexpr int TC = 32;                          // cells per tile
   static constexpr int M = 128;                          // rows: v * 32 + cell
   static constexpr int KP1 = (S::N + 7) / 8 * 8;         // K of MMA 1
   static constexpr int NQ = (S::Q + 15) / 16 * 16;       // N of MMA 1
-  static constexpr int KV = 2 * S::Q;                    // volume part of K of MMA 2
-  static constexpr int KS = 4 * S::QF;                   // surface part
-  static constexpr int KP2 = (KV + KS + 7) / 8 * 8;      // K of MMA 2
+  static constexpr int QP = (S::Q + 3) / 4 * 4;          // points, padded to groups of 4
+  static constexpr int QFP = (S::QF + 3) / 4 * 4;        // face points, padded
+  static constexpr int KV = 2 * QP;                      // volume part of K of MMA 2
+  static constexpr int KP2 = KV + 4 * QFP;               // K of MMA 2 (multiple of 8)
   static constexpr int NJ = (S::N + 15) / 16 * 16;       // N of MMA 2
   static constexpr int B_FLOATS = 2 * NQ * KP1 + 2 * NJ * KP2;  // B1 hi|lo, B2 hi|lo
-  static constexpr int SMEM_FLOATS = 2 * M * KP1 + 2 * M * KP2 + B_FLOATS + S::NV * S::Q * TC;
+  // A1 hi|lo (the nodal values reuse it once MMA 1 is done), A2 hi|lo, B
+  static constexpr int A1_FLOATS = 2 * M * KP1 > S::NV * S::Q * TC ? 2 * M * KP1 : S::NV * S::Q * TC;
+  static constexpr int SMEM_FLOATS = A1_FLOATS + 2 * M * KP2 + B_FLOATS;
   static constexpr size_t SMEM = (size_t)SMEM_FLOATS * 4;
   static constexpr int TMEM_COLS = 32;
   static_assert(NQ + NJ <= TMEM_COLS, "tensor memory columns");
+  static_assert(KP2 % 8 == 0 && KP1 % 8 == 0, "K steps of 8");
+  static_assert((2 * M * KP1) % 4 == 0 && A1_FLOATS % 32 == 0, "16-byte alignment");
 };
 
 // float offset of element (r, k) in the core-matrix layout of a tile with KP columns
@@ -82,13 +87,16 @@ __device__ __forceinline__ void tc_gemm_split(uint32_t dtmem, const float* Ah, c
   const float* Bs[4] = {Bl, Bh, Bl, Bh};
   uint32_t acc = 0;
 #pragma unroll
-  for (int t = 0; t < 4; ++t)
+  for (int t = 0; t < 4; ++t) {
+    // a K step of 8 is 256 bytes further: 16 in the descriptor's address
+    // field (shared addresses stay below 2^18, so the field does not overflow)
+    const uint64_t da = tc_desc(tc_smem(As[t]), KP), db = tc_desc(tc_smem(Bs[t]), KP);
 #pragma unroll
     for (int ks = 0; ks < KP / 8; ++ks) {
-      tc_mma(dtmem, tc_desc(tc_smem(As[t]) + ks * 256, KP), tc_desc(tc_smem(Bs[t]) + ks * 256, KP),
-             idesc, acc);
+      tc_mma(dtmem, da + (uint64_t)(16 * ks), db + (uint64_t)(16 * ks), idesc, acc);
       acc = 1;
     }
+  }
 }
 
 __device__ __forceinline__ void tc_commit(uint64_t* mbar) {
@@ -135,152 +143,225 @@ __device__ __forceinline__ void tc_split(float x, float& hi, float& lo) {
   lo = tc_round_tf32(x - hi);
 }
 
+__device__ __forceinline__ void tc_st4(float* base, int off, float a, float b, float c, float d) {
+  *reinterpret_cast<float4*>(base + off) = make_float4(a, b, c, d);
+}
+
+// split four consecutive K values of one row and store them (16-byte stores)
+__device__ __forceinline__ void tc_put4(float* Ah, float* Al, int off, const float* x) {
+  float h[4], l[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) tc_split(x[i], h[i], l[i]);
+  tc_st4(Ah, off, h[0], h[1], h[2], h[3]);
+  tc_st4(Al, off, l[0], l[1], l[2], l[3]);
+}
+
+// Persistent CTAs of two warpgroups: warps v and v + 4 share the TMEM lane
+// quarter (and A rows) of variable v and split each phase of a tile between
+// them.  Each CTA keeps the B operands, its tensor memory and its barriers for
+// all the tiles it processes (tile, tile + gridDim.x, ...), and loads the
+// global inputs of its next tile while the current one is in flight.
 template <int K>
-__global__ void __launch_bounds__(128) cell_update_tc_kernel(const StageArgs<float> a) {
+__global__ void __launch_bounds__(256, 3) cell_update_tc_kernel(const StageArgs<float> a) {
   using S = Shape<2, K>;
   using T = TcShape<K>;
   constexpr int TC = T::TC, M = T::M, KP1 = T::KP1, KP2 = T::KP2, NQ = T::NQ, NJ = T::NJ;
-  constexpr int N = S::N, Q = S::Q, QF = S::QF, NV = S::NV;
+  constexpr int N = S::N, Q = S::Q, QF = S::QF, NV = S::NV, QP = T::QP, QFP = T::QFP;
+  constexpr int G1H = (KP1 / 4 + 1) / 2;  // 16-byte groups of an A1 row per half
+  constexpr int WH = 4 * G1H;             // weights per thread
+  constexpr int NG = QP / 4;              // groups of 4 volume points
+  constexpr int QH = (Q + 1) / 2;         // nodal values per thread
+  constexpr int JH = (N + 1) / 2;         // output coefficients per thread
+  static_assert(2 * NG <= 8 && QH <= 16 && JH <= 16, "work split");
   extern __shared__ __align__(1024) float sm[];
   float* A1h = sm;
   float* A1l = A1h + M * KP1;
-  float* A2h = A1l + M * KP1;
+  float* sU = sm;  // [NV][Q][TC], over A1 once MMA 1 has read it
+  float* A2h = sm + T::A1_FLOATS;
   float* A2l = A2h + M * KP2;
-  float* Bs = A2l + M * KP2;  // B1h | B1l | B2h | B2l
-  float* B1h = Bs;
+  float* B1h = A2l + M * KP2;
   float* B1l = B1h + NQ * KP1;
   float* B2h = B1l + NQ * KP1;
   float* B2l = B2h + NJ * KP2;
-  float* sU = B2l + NJ * KP2;  // [NV][Q][TC]
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_base;
 
-  const int lane = threadIdx.x & 31, v = threadIdx.x >> 5;  // warp <-> variable
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int v = warp & 3, half = warp >> 2;  // variable (TMEM lane quarter), half of the work
   const int nc = a.m.ncells, nf = a.m.nfaces;
-  const int c = blockIdx.x * TC + lane;
-  const bool valid = c < nc;
+  const int ntiles = (nc + TC - 1) / TC;
   const int row = v * TC + lane;
 
-  for (int i = threadIdx.x; i < T::B_FLOATS; i += 128) Bs[i] = __ldg(a.tcB + i);
-  float w[N];
-#pragma unroll
-  for (int l = 0; l < N; ++l)
-    w[l] = valid ? a.U[(size_t)(v * N + l) * nc + c] : ((v == 0 && l == 0) ? 1.0f : 0.0f);
-#pragma unroll
-  for (int l = 0; l < KP1; ++l) {
-    float hi, lo;
-    tc_split(l < N ? w[l] : 0.0f, hi, lo);
-    A1h[tc_off(row, l, KP1)] = hi;
-    A1l[tc_off(row, l, KP1)] = lo;
-  }
+  for (int i = threadIdx.x; i < T::B_FLOATS; i += 256) B1h[i] = __ldg(a.tcB + i);
   if (threadIdx.x == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(&mbar[0])));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(&mbar[1])));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
-  if (v == 0) {
+  if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      tc_smem(&tmem_base)),
                  "r"(T::TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  asm volatile("fence.proxy.async.shared::cta;");
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
-
-  // MMA 1: nodal values at the volume points
-  if (threadIdx.x == 0) {
-    tc_gemm_split<KP1, NQ, M>(tmem, A1h, A1l, B1h, B1l);
-    tc_commit(&mbar[0]);
-  }
-  bool ok = tc_wait(&mbar[0], 0);
-  asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t trow = (uint32_t)(v * 32) << 16;
-  {
-    float u[16];
-    tc_ld16(tmem + trow, u);
-#pragma unroll
-    for (int q = 0; q < Q; ++q) sU[(v * Q + q) * TC + lane] = u[q];
-  }
-  __syncthreads();
-
-  // Euler fluxes at the points of this thread -> volume part of A2
   const float g1 = (float)a.gamma - 1.0f;
-  for (int q = v; q < Q; q += NV) {
-    float u[NV];
+  bool ok = true;
+  uint32_t phase = 0;
+
+  // this thread's share of a tile's global inputs: weights l = half*WH + i of
+  // (v, c) and the fluxes of sides 2*half, 2*half+1; loaded a tile ahead
+  float wn[WH], xn[2][QF];
+  auto load_tile = [&](int t) {
+    const int cc = t * TC + lane;
+    const bool in = t < ntiles && cc < nc;
 #pragma unroll
-    for (int vv = 0; vv < NV; ++vv) u[vv] = sU[(vv * Q + q) * TC + lane];
+    for (int i = 0; i < WH; ++i) {
+      const int l = half * WH + i;
+      wn[i] = (in && l < N) ? a.U[(size_t)(v * N + l) * nc + cc] : 0.0f;
+    }
 #pragma unroll
-    for (int d = 0; d < 2; ++d) {
-      float f[NV];
-      euler_flux<float, 2>(u, d, g1, f);
+    for (int s2 = 0; s2 < 2; ++s2) {
+      const int e = in ? a.m.sface[(size_t)(2 * half + s2) * nc + cc] : 0;
 #pragma unroll
-      for (int vv = 0; vv < NV; ++vv) {
-        float hi, lo;
-        tc_split(f[vv], hi, lo);
-        A2h[tc_off(vv * TC + lane, d * Q + q, KP2)] = hi;
-        A2l[tc_off(vv * TC + lane, d * Q + q, KP2)] = lo;
+      for (int q = 0; q < QF; ++q) xn[s2][q] = in ? a.F[((size_t)v * QF + q) * nf + e] : 0.0f;
+    }
+  };
+  load_tile(blockIdx.x);
+
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, phase ^= 1u) {
+    const int c = tile * TC + lane;
+    const bool valid = c < nc;
+    // weights -> A1 (a padding cell gets the unit density state)
+    {
+      float w[WH];
+#pragma unroll
+      for (int i = 0; i < WH; ++i) w[i] = wn[i];
+      if (!valid && v == 0 && half == 0) w[0] = 1.0f;
+#pragma unroll
+      for (int g = 0; g < G1H; ++g)
+        if ((half * G1H + g) * 4 < KP1)
+          tc_put4(A1h, A1l, tc_off(row, (half * G1H + g) * 4, KP1), &w[4 * g]);
+    }
+    asm volatile("fence.proxy.async.shared::cta;");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      tc_gemm_split<KP1, NQ, M>(tmem, A1h, A1l, B1h, B1l);
+      tc_commit(&mbar[0]);
+    }
+    // while MMA 1 runs: face fluxes of two sides -> surface part of A2
+#pragma unroll
+    for (int s2 = 0; s2 < 2; ++s2) {
+      float x[QFP];
+#pragma unroll
+      for (int q = 0; q < QFP; ++q) x[q] = q < QF ? xn[s2][q] : 0.0f;
+#pragma unroll
+      for (int g = 0; g < QFP / 4; ++g)
+        tc_put4(A2h, A2l, tc_off(row, T::KV + (2 * half + s2) * QFP + 4 * g, KP2), &x[4 * g]);
+    }
+    load_tile(tile + gridDim.x);
+    // while MMA 1 runs: the stage combination of the inputs (all but the RHS
+    // term) for coefficients j = half*JH + jj
+    float base[MAX_OUT][JH];
+    float scale = 0.0f;
+    if (valid) {
+      const int pb = cell_problem(a.m, c);
+      const float pv = a.pre_prob ? a.pre_prob[pb] : a.pre[a.m.level[c]];
+      scale = pv * (a.dt ? (float)a.dt[pb] : 1.0f);
+    }
+#pragma unroll
+    for (int oo = 0; oo < MAX_OUT; ++oo)
+#pragma unroll
+      for (int jj = 0; jj < JH; ++jj) base[oo][jj] = 0.0f;
+    for (int r = 0; r < a.n_in; ++r) {
+      float xr[JH];
+#pragma unroll
+      for (int jj = 0; jj < JH; ++jj) {
+        const int j = half * JH + jj;
+        xr[jj] = (valid && j < N) ? a.in[r][(size_t)(v * N + j) * nc + c] : 0.0f;
+      }
+#pragma unroll
+      for (int oo = 0; oo < MAX_OUT; ++oo) {
+        const float cr = a.C[oo][r];
+#pragma unroll
+        for (int jj = 0; jj < JH; ++jj) base[oo][jj] += cr * xr[jj];
       }
     }
-  }
-  // face fluxes of this variable -> surface part of A2 (zero beyond)
+    ok = tc_wait(&mbar[0], phase) && ok;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    {
+      float u[16];
+      tc_ld16(tmem + trow, u);
+      // this thread saw MMA 1 complete, so its reads of A1 are over: sU may overwrite A1
 #pragma unroll
-  for (int sd = 0; sd < 4; ++sd) {
-    const int e = valid ? a.m.sface[(size_t)sd * nc + c] : 0;
-#pragma unroll
-    for (int q = 0; q < QF; ++q) {
-      const float x = valid ? a.F[((size_t)v * QF + q) * nf + e] : 0.0f;
-      float hi, lo;
-      tc_split(x, hi, lo);
-      A2h[tc_off(row, T::KV + sd * QF + q, KP2)] = hi;
-      A2l[tc_off(row, T::KV + sd * QF + q, KP2)] = lo;
+      for (int i = 0; i < QH; ++i) {
+        const int q = half * QH + i;
+        const float val = half ? (QH + i < 16 ? u[QH + i] : 0.0f) : u[i];
+        if (q < Q) sU[(v * Q + q) * TC + lane] = val;
+      }
     }
-  }
+    __syncthreads();
+    // Euler flux in direction d at points 4g..4g+3 (task = warp) -> volume part of A2
+    if (warp < 2 * NG) {
+      const int d = warp & 1, g = warp >> 1;
+      float f[NV][4];
 #pragma unroll
-  for (int k = T::KV + T::KS; k < KP2; ++k) {
-    A2h[tc_off(row, k, KP2)] = 0.0f;
-    A2l[tc_off(row, k, KP2)] = 0.0f;
-  }
-  asm volatile("fence.proxy.async.shared::cta;");
-  asm volatile("tcgen05.fence::before_thread_sync;");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;");
-
-  // MMA 2: volume minus surface integrals
-  if (threadIdx.x == 0) {
-    tc_gemm_split<KP2, NJ, M>(tmem + NQ, A2h, A2l, B2h, B2l);
-    tc_commit(&mbar[1]);
-  }
-  ok = tc_wait(&mbar[1], 0) && ok;
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  float acc[16];
-  tc_ld16(tmem + trow + NQ, acc);
-  if (!ok && lane == 0) atomicOr(a.status, 1 << DG_ERR_TIMEOUT_BIT);
-
-  if (valid && ok) {
-    const float pre = a.pre[a.m.level[c]];
-    const float dtv = a.dt ? (float)a.dt[cell_problem(a.m, c)] : 1.0f;
-    const float pv = a.pre_prob ? a.pre_prob[cell_problem(a.m, c)] : pre;
+      for (int i = 0; i < 4; ++i) {
+        const int q = 4 * g + i;
+        float u[NV], fd[NV];
 #pragma unroll
-    for (int j = 0; j < N; ++j) {
-      const float rhs = pv * acc[j];
-      const size_t idx = (size_t)(v * N + j) * nc + c;
-      for (int oo = 0; oo < a.n_out; ++oo) {
-        float val = a.ck[oo] * dtv * rhs;
-        for (int r = 0; r < a.n_in; ++r) {
-          const float cr = a.C[oo][r];
-          if (cr == 0.0f) continue;
-          val += cr * ((a.in[r] == a.U) ? w[j] : a.in[r][idx]);
+        for (int vv = 0; vv < NV; ++vv) u[vv] = q < Q ? sU[(vv * Q + q) * TC + lane] : (vv == 0 ? 1.0f : 0.0f);
+        if (d == 0)
+          euler_flux<float, 2>(u, 0, g1, fd);
+        else
+          euler_flux<float, 2>(u, 1, g1, fd);
+#pragma unroll
+        for (int vv = 0; vv < NV; ++vv) f[vv][i] = q < Q ? fd[vv] : 0.0f;
+      }
+#pragma unroll
+      for (int vv = 0; vv < NV; ++vv)
+        tc_put4(A2h, A2l, tc_off(vv * TC + lane, d * QP + 4 * g, KP2), f[vv]);
+    }
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (threadIdx.x == 0) {
+      tc_gemm_split<KP2, NJ, M>(tmem + NQ, A2h, A2l, B2h, B2l);
+      tc_commit(&mbar[1]);
+    }
+    ok = tc_wait(&mbar[1], phase) && ok;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    float acc[16];
+    tc_ld16(tmem + trow + NQ, acc);
+    if (valid && ok) {
+#pragma unroll
+      for (int oo = 0; oo < MAX_OUT; ++oo)
+        if (oo < a.n_out) {
+          const float ckv = a.ck[oo] * scale;
+#pragma unroll
+          for (int jj = 0; jj < JH; ++jj) {
+            const int j = half * JH + jj;
+            const float rhs = half ? (JH + jj < 16 ? acc[JH + jj] : 0.0f) : acc[jj];
+            if (j < N) a.out[oo][(size_t)(v * N + j) * nc + c] = base[oo][jj] + ckv * rhs;
+          }
         }
-        a.out[oo][idx] = val;
-      }
     }
+    // all warps are done with MMA 2's operands and results before the next
+    // tile; a wait that gave up anywhere ends the CTA's work
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    ok = __syncthreads_and(ok) != 0;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (!ok) break;
   }
+  if (!ok && threadIdx.x == 0) atomicOr(a.status, 1 << DG_ERR_TIMEOUT_BIT);
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (v == 0)
+  if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(T::TMEM_COLS));
 }
 
@@ -318,33 +399,64 @@ void fill_tc_tables(const std::vector<double>& Tab, std::vector<float>& out) {
       for (int q = 0; q < S::Q; ++q) {
         float hi, lo;
         split(Tab[S::OFF_DPHIW + (d * S::Q + q) * S::N + j], hi, lo);
-        B2h[tc_off(j, d * S::Q + q, T::KP2)] = hi;
-        B2l[tc_off(j, d * S::Q + q, T::KP2)] = lo;
+        B2h[tc_off(j, d * T::QP + q, T::KP2)] = hi;
+        B2l[tc_off(j, d * T::QP + q, T::KP2)] = lo;
       }
     for (int sd = 0; sd < 4; ++sd)
       for (int q = 0; q < S::QF; ++q) {
         const double sc = (sd & 1) ? 1.0 : -1.0;  // outward normal sign of the side
         float hi, lo;
         split(-sc * Tab[S::OFF_PHIFW + ((sd * S::NVAR + 0) * S::QF + q) * S::N + j], hi, lo);
-        B2h[tc_off(j, T::KV + sd * S::QF + q, T::KP2)] = hi;
-        B2l[tc_off(j, T::KV + sd * S::QF + q, T::KP2)] = lo;
+        B2h[tc_off(j, T::KV + sd * T::QFP + q, T::KP2)] = hi;
+        B2l[tc_off(j, T::KV + sd * T::QFP + q, T::KP2)] = lo;
       }
   }
 }
+
+template <int K>
+struct TcGrid {
+  static inline int ctas = 0;  // resident CTAs on the whole device (set by prepare_cell_tc)
+};
 
 template <int K>
 cudaError_t launch_cell_tc(const void* pa, cudaStream_t s) {
   const auto& a = *static_cast<const StageArgs<float>*>(pa);
   using T = TcShape<K>;
   if (a.m.ncells == 0) return cudaSuccess;
-  cell_update_tc_kernel<K><<<(a.m.ncells + T::TC - 1) / T::TC, 128, T::SMEM, s>>>(a);
+  const int ntiles = (a.m.ncells + T::TC - 1) / T::TC;
+  const int grid = TcGrid<K>::ctas > 0 && TcGrid<K>::ctas < ntiles ? TcGrid<K>::ctas : ntiles;
+  cell_update_tc_kernel<K><<<grid, 256, T::SMEM, s>>>(a);
   return cudaGetLastError();
 }
 
 template <int K>
 cudaError_t prepare_cell_tc() {
-  return cudaFuncSetAttribute(cell_update_tc_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)TcShape<K>::SMEM);
+  cudaError_t e = cudaFuncSetAttribute(cell_update_tc_kernel<K>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)TcShape<K>::SMEM);
+  if (e != cudaSuccess) return e;
+  // all of the unified L1/shared storage as shared memory: several CTAs per SM
+  e = cudaFuncSetAttribute(cell_update_tc_kernel<K>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           (int)cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
+  // resident CTAs per SM from the kernel's registers and shared memory
+  int dev = 0, sms = 0, smem_sm = 0, smem_rsv = 0, regs_sm = 0;
+  cudaFuncAttributes fa;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess)
+    return e;
+  if ((e = cudaDeviceGetAttribute(&smem_rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev)) != cudaSuccess)
+    return e;
+  if ((e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncGetAttributes(&fa, cell_update_tc_kernel<K>)) != cudaSuccess) return e;
+  const int by_smem = smem_sm / (int)(TcShape<K>::SMEM + fa.sharedSizeBytes + smem_rsv);
+  const int by_regs = regs_sm / ((fa.numRegs > 0 ? fa.numRegs : 1) * 256);
+  int per_sm = by_smem < by_regs ? by_smem : by_regs;
+  if (per_sm > 8) per_sm = 8;  // 2048 threads per SM
+  TcGrid<K>::ctas = sms * (per_sm > 0 ? per_sm : 1);
+  return cudaSuccess;
 }
 
 }  // namespace dgi

@@ -331,6 +331,21 @@ def test_rhs_fp32_tensor_cores(k):
     assert s.status() == 0
 
 
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_rhs_fp32_tensor_cores_many_tiles(k):
+    """150 x 131 cells: 615 tiles of 32 cells with a ragged last tile, more
+    tiles than resident CTAs, so each persistent CTA runs several tiles."""
+    m = wl.mesh_uniform(2, [150, 131], [0.0, 0.0], [1.5, 1.31])
+    o = oracle_for(m, k)
+    s = solver_for(m, k, precision="fp32_tc")
+    W = wl.random_weights(2, o.N, o.n_cells, seed=950 + k).astype(np.float32)
+    ref = o.rhs(W.astype(np.float64))
+    got = s.rhs(to_dev(s, W)).cpu().numpy()
+    e, erms = rel_err(got, ref)
+    assert e < TOL32_MAX and erms < TOL32_RMS, (k, e, erms)
+    assert s.status() == 0
+
+
 @pytest.mark.parametrize("precision", ["fp32", "fp32_tc"])
 def test_rk4_step_fp32_vortex_full_size(precision):
     """On the smooth 256^2 vortex dW/dt is a strong cancellation of the volume
