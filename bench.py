@@ -40,7 +40,7 @@ WORKLOADS = {
         name="isentropic vortex 2D, 256x256 periodic [-5,5]^2, k=3 (10 coeffs/cell/var), "
              "SSP-RK4 (5 stages), no limiter, CFL 0.2",
         dim=2, k=3, rk=4, stages=5, limiter="none", positivity=False,
-        precisions=("fp64", "fp32", "fp32_tc"), tag="vortex256_k3"),
+        precisions=("fp64", "fp32", "fp32_tc", "mixed"), tag="vortex256_k3"),
     "ensemble": dict(
         name="512 independent isentropic vortices (strength U(3,6)) on periodic [-5,5]^2 with "
              "sizes drawn from {32,48,64,96,128}^2 (3.4M cells), k=2 (6 coeffs/cell/var), SSP-RK3, "
@@ -336,11 +336,13 @@ def summarize(args, results, world):
         kind = max(prof, key=lambda kk: prof[kk][1])
         n_launch, kms = prof[kind]
         avg_s = kms / max(n_launch, 1) * 1e-3
-        esize = 8 if precision == "fp64" else 4
+        esize = 8 if precision in ("fp64", "mixed") else 4
         kname = {"cell": "cell_update_kernel", "face": "face_flux_kernel",
                  "limit": "limit_kernel"}.get(kind, kind)
         if precision == "fp32_tc" and kind == "cell":
             kname = "cell_update_tc_kernel"
+        if precision == "mixed" and kind in ("cell", "face"):
+            kname = kind == "cell" and "cell_update_mixed_kernel" or "face_flux_mixed_kernel"
         tag = "%s_%s" % (wk["tag"], precision)
         if precision == "fp64" and kind in ("cell", "face"):
             fc, ff = kernel_flops(dim, k)
@@ -443,7 +445,7 @@ def run_l1_study(args):
     torch.cuda.set_device(0)
     t_end = args.t_end
     rows = []
-    for precision in ("fp64", "fp32", "fp32_tc"):
+    for precision in ("fp64", "fp32", "fp32_tc", "mixed"):
         for n in (32, 64, 128, 256):
             s = dg.Solver(mesh(n), K_DEG, 1.4, rk_order=RK_ORDER, cfl=CFL, precision=precision)
             W = s.project(torch.as_tensor(wl.vortex(s.quad_points().cpu().numpy())))
@@ -534,7 +536,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precision", default="both", choices=["both", "fp64", "fp32", "fp32_tc"],
+    ap.add_argument("--precision", default="both", choices=["both", "fp64", "fp32", "fp32_tc", "mixed"],
                     help="run one precision only (profiling); the JSON line needs both")
     ap.add_argument("--workload", default="vortex",
                     choices=sorted(WORKLOADS) + ["adjoint3d", "l1study"])
@@ -566,7 +568,7 @@ def main():
         out = {"metric": METRIC, "value": one["value"], "unit": UNIT, "n_gpus": world,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": one["ms_per_step"],
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-               "dtype": "f64" if prec == "fp64" else "f32", "data": "synthetic",
+               "dtype": {"fp64": "f64", "mixed": "f32/f64"}.get(prec, "f32"), "data": "synthetic",
                "config": workload_config(args.workload, prec, one["cells"])}
         out.update({kk: one[kk] for kk in ("roofline", "e2e", "gpu_launches", "clocks", "kernel_ms")})
         print(json.dumps(out), flush=True)
@@ -580,7 +582,7 @@ def main():
            "clocks": head["clocks"], "kernel_ms": head["kernel_ms"],
            "variants": {p: {k: lines[p][k] for k in
                             ("value", "ms_per_step", "roofline", "e2e", "gpu_launches",
-                             "clocks", "kernel_ms")} for p in ("fp32", "fp32_tc") if p in lines}}
+                             "clocks", "kernel_ms")} for p in ("fp32", "fp32_tc", "mixed") if p in lines}}
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()
     print(json.dumps(out), flush=True)

@@ -49,10 +49,20 @@ enum {
 
 enum { DG_BC_PERIODIC = 0, DG_BC_TRANSMISSIVE = 1 };
 enum { DG_LIMITER_NONE = 0, DG_LIMITER_COMPONENT = 1, DG_LIMITER_CHARACTERISTIC = 2 };
-/* DG_FP32_TC: FP32 state with the cell kernel's contractions on the tensor
- * cores (3xTF32: split operands, FP32 accumulation); 2D uniform meshes,
- * k = 1..3 (DG_ERR_UNSUPPORTED otherwise). */
-enum { DG_FP64 = 0, DG_FP32 = 1, DG_FP32_TC = 2 };
+/* Precision of a handle.
+ * DG_FP64:    FP64 state and arithmetic.
+ * DG_FP32:    FP32 state and arithmetic.
+ * DG_FP32_TC: FP32 state with the cell kernel's contractions on the tensor
+ *             cores (split TF32 operands, FP32 accumulation); 2D uniform
+ *             meshes, k = 1..3 (DG_ERR_UNSUPPORTED otherwise).
+ * DG_MIXED:   FP64 state (the W arrays are double, the stage combination is
+ *             FP64) with the right-hand side evaluated in FP32 in perturbation
+ *             form: each cell subtracts the flux of its own mean state from
+ *             the point and face fluxes it integrates, which leaves the
+ *             discrete right-hand side unchanged and makes the FP32 rounding
+ *             scale with the solution's variation rather than its size.  The
+ *             CFL timestep, limiters, totals and the adjoint run in FP64. */
+enum { DG_FP64 = 0, DG_FP32 = 1, DG_FP32_TC = 2, DG_MIXED = 3 };
 
 /* Mesh description (paper Secs. 2.2 and 4): cubical cells on the box
  * [lo, hi]; n[a] base cells along axis a (the base edge length must be equal

@@ -23,6 +23,24 @@ const KernelSet* kernel_set(int prec, int dim, int k) {
   return &ks;
 }
 
+bool mixed_set_2d(int k, MixedSet* out);
+bool mixed_set_3d(int k, MixedSet* out);
+
+const MixedSet* mixed_set(int dim, int k) {
+  static MixedSet sets[2][4];
+  static bool have[2][4] = {};
+  static std::mutex mu;
+  if ((dim != 2 && dim != 3) || k < 0 || k > 3) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  MixedSet& ms = sets[dim - 2][k];
+  if (!have[dim - 2][k]) {
+    const bool ok = dim == 2 ? mixed_set_2d(k, &ms) : mixed_set_3d(k, &ms);
+    if (!ok) return nullptr;
+    have[dim - 2][k] = true;
+  }
+  return &ms;
+}
+
 __global__ void set_scalar_kernel(double* dst, int n, double value) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = value;
 }

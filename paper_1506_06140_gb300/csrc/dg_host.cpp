@@ -10,6 +10,7 @@
 #include <mutex>
 #include <string>
 #include <tuple>
+#include <type_traits>
 #include <vector>
 
 #include "dg.h"
@@ -401,6 +402,10 @@ struct dg_handle {
   void* F = nullptr;
   std::vector<void*> regs;   // scratch state registers 1..n
   bool use_tc = false;       // tensor-core cell kernel (DG_FP32_TC)
+  const MixedSet* ms = nullptr;  // FP32 perturbation-form stage kernels (DG_MIXED)
+  Tab1D<float> tab1d32{};
+  float* Gm = nullptr;       // DG_MIXED face fluxes minus the minus cell's reference flux
+  float* Dm = nullptr;       // DG_MIXED reference flux differences per face
   void* tcB = nullptr;       // its B operands
   double* scal = nullptr;    // dt per problem [nprob]
   unsigned long long* dt_bits = nullptr;  // per-problem max signal speed [nprob]
@@ -719,6 +724,26 @@ cudaError_t cell_launch(dg_handle* h, const void* args, cudaStream_t s) {
   return h->use_tc ? h->ks->cell_tc(args, s) : h->ks->cell(args, s);
 }
 
+// face and cell kernels of one stage; DG_MIXED wraps the FP64 arguments
+template <typename real>
+int stage_launch(dg_handle* h, const StageArgs<real>& a, cudaStream_t s) {
+  if constexpr (std::is_same<real, double>::value) {
+    if (h->ms) {
+      MixedArgs x;
+      x.a = a;
+      x.t = h->tab1d32;
+      x.G = h->Gm;
+      x.D = h->Dm;
+      DG_CUDA(h, timed(h, DG_KERNEL_FACE, s, [&] { return h->ms->face(&x, s); }));
+      DG_CUDA(h, timed(h, DG_KERNEL_CELL, s, [&] { return h->ms->cell(&x, s); }));
+      return DG_OK;
+    }
+  }
+  DG_CUDA(h, timed(h, DG_KERNEL_FACE, s, [&] { return h->ks->face(&a, s); }));
+  DG_CUDA(h, timed(h, DG_KERNEL_CELL, s, [&] { return cell_launch(h, &a, s); }));
+  return DG_OK;
+}
+
 template <typename real>
 StageArgs<real> stage_args(dg_handle* h, const Op& op, const void* U, void* W) {
   StageArgs<real> a;
@@ -809,8 +834,8 @@ int step_impl(dg_handle* h, const Program& P, void* W, cudaStream_t s) {
   for (const Op& op : P.ops) {
     void* U = op.in_reg == 0 ? W : h->regs[op.in_reg - 1];
     StageArgs<real> a = stage_args<real>(h, op, U, W);
-    DG_CUDA(h, timed(h, DG_KERNEL_FACE, s, [&] { return h->ks->face(&a, s); }));
-    DG_CUDA(h, timed(h, DG_KERNEL_CELL, s, [&] { return cell_launch(h, &a, s); }));
+    const int rs = stage_launch<real>(h, a, s);
+    if (rs != DG_OK) return rs;
     if (op.lim_src >= 0) {
       void* src = op.lim_src == 0 ? W : h->regs[op.lim_src - 1];
       void* dst = op.lim_dst == 0 ? W : h->regs[op.lim_dst - 1];
@@ -862,9 +887,7 @@ int rhs_into(dg_handle* h, const void* U, void* out, cudaStream_t s) {
   StageArgs<real> a = stage_args<real>(h, op, U, nullptr);
   a.out[0] = static_cast<real*>(out);
   a.dt = nullptr;
-  DG_CUDA(h, timed(h, DG_KERNEL_FACE, s, [&] { return h->ks->face(&a, s); }));
-  DG_CUDA(h, timed(h, DG_KERNEL_CELL, s, [&] { return cell_launch(h, &a, s); }));
-  return DG_OK;
+  return stage_launch<real>(h, a, s);
 }
 
 // acc = J(U)^T G, J the Jacobian of dW/dt
@@ -975,10 +998,13 @@ static int create_impl(const dg_mesh_desc* mesh, int nprob, int k, double gamma,
   if (opt) o = *opt;
   if (o.rk_order < 1 || o.rk_order > 4) return fail(nullptr, DG_ERR_ARG, "dg_create: rk_order must be 1..4");
   if (o.slope_limiter < 0 || o.slope_limiter > 2) return fail(nullptr, DG_ERR_ARG, "dg_create: bad slope_limiter");
-  if (o.precision != DG_FP64 && o.precision != DG_FP32 && o.precision != DG_FP32_TC)
+  if (o.precision != DG_FP64 && o.precision != DG_FP32 && o.precision != DG_FP32_TC &&
+      o.precision != DG_MIXED)
     return fail(nullptr, DG_ERR_ARG, "dg_create: bad precision");
   const bool use_tc = o.precision == DG_FP32_TC;
+  const bool mixed = o.precision == DG_MIXED;
   if (use_tc) o.precision = DG_FP32;
+  if (mixed) o.precision = DG_FP64;  // FP64 state; FP32 stage kernels below
   if (!(o.cfl > 0.0)) return fail(nullptr, DG_ERR_ARG, "dg_create: cfl must be positive");
   const KernelSet* ks = kernel_set(o.precision, mesh->dim, k);
   if (!ks) return fail(nullptr, DG_ERR_UNSUPPORTED, "dg_create: (dim, k, precision) not compiled");
@@ -1079,6 +1105,20 @@ static int create_impl(const dg_mesh_desc* mesh, int nprob, int k, double gamma,
   if (cudaMemset(h->status, 0, sizeof(int)) != cudaSuccess)
     return bail(cuda_fail(h, cudaGetLastError(), "cudaMemset"));
   if (ks->prepare() != cudaSuccess) return bail(cuda_fail(h, cudaGetLastError(), "kernel attributes"));
+  if (mixed) {
+    h->ms = mixed_set(h->dim, k);
+    if (!h->ms) return bail(fail(h, DG_ERR_UNSUPPORTED, "dg_create: DG_MIXED not compiled for (dim, k)"));
+    if (h->ms->prepare() != cudaSuccess)
+      return bail(cuda_fail(h, cudaGetLastError(), "kernel attributes"));
+    const double* src = reinterpret_cast<const double*>(&h->tab1d64);
+    float* dst = reinterpret_cast<float*>(&h->tab1d32);
+    for (size_t i = 0; i < sizeof(Tab1D<double>) / sizeof(double); ++i) dst[i] = (float)src[i];
+    const size_t nf = (size_t)std::max(h->nfaces, 1);
+    if ((r = dalloc(h, (size_t)h->nv * ks->QF * nf * sizeof(float), &p)) != DG_OK) return bail(r);
+    h->Gm = static_cast<float*>(p);
+    if ((r = dalloc(h, (size_t)h->nv * nf * sizeof(float), &p)) != DG_OK) return bail(r);
+    h->Dm = static_cast<float*>(p);
+  }
   if (h->use_tc) {
     if (!ks->cell_tc || h->nnodes > 0)
       return bail(fail(h, DG_ERR_UNSUPPORTED,
@@ -1185,24 +1225,8 @@ int dg_rhs(dg_handle* h, const void* W_dev, void* dWdt_dev, void* stream) {
   if (!check_handle(h) || !W_dev || !dWdt_dev) return DG_ERR_ARG;
   if (W_dev == dWdt_dev) return fail(h, DG_ERR_ARG, "dg_rhs: W and dWdt alias");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  Op op;
-  op.n_in = 0;
-  op.n_out = 1;
-  op.ck[0] = 1.0;
-  if (h->prec == DG_FP64) {
-    StageArgs<double> a = stage_args<double>(h, op, W_dev, nullptr);
-    a.out[0] = static_cast<double*>(dWdt_dev);
-    a.dt = nullptr;
-    DG_CUDA(h, h->ks->face(&a, s));
-    DG_CUDA(h, h->ks->cell(&a, s));
-  } else {
-    StageArgs<float> a = stage_args<float>(h, op, W_dev, nullptr);
-    a.out[0] = static_cast<float*>(dWdt_dev);
-    a.dt = nullptr;
-    DG_CUDA(h, h->ks->face(&a, s));
-    DG_CUDA(h, cell_launch(h, &a, s));
-  }
-  return DG_OK;
+  return h->prec == DG_FP64 ? rhs_into<double>(h, W_dev, dWdt_dev, s)
+                            : rhs_into<float>(h, W_dev, dWdt_dev, s);
 }
 
 int dg_compute_dt(dg_handle* h, const void* W_dev, double* dt_dev, void* stream) {

@@ -113,6 +113,15 @@ struct StageArgs {
   int* status = nullptr;        // device status word
 };
 
+// Stage arguments of the mixed-precision kernels (FP64 state, FP32
+// right-hand side in perturbation form).
+struct MixedArgs {
+  StageArgs<double> a;  // mesh, FP64 state, stage program, timesteps
+  Tab1D<float> t;       // the 1D tables in FP32
+  float* G = nullptr;   // [NV][QF][nfaces] F* - f(ubar_m), m the face's minus cell
+  float* D = nullptr;   // [NV][nfaces]     f(ubar_m) - f(ubar_p)
+};
+
 template <typename real>
 struct LimitArgs {
   MeshDev m;
@@ -201,6 +210,16 @@ struct KernelSet {
 };
 
 const KernelSet* kernel_set(int prec, int dim, int k);
+
+// Stage kernels for an FP64 state with an FP32 right-hand side in
+// perturbation form (argument block MixedArgs, dg_mixed.cuh).
+struct MixedSet {
+  cudaError_t (*face)(const void* mixed_args, cudaStream_t s) = nullptr;
+  cudaError_t (*cell)(const void* mixed_args, cudaStream_t s) = nullptr;
+  cudaError_t (*prepare)() = nullptr;
+};
+
+const MixedSet* mixed_set(int dim, int k);
 
 // shared helper kernels (dg_common.cu)
 cudaError_t launch_set_scalar(double* dst, int n, double value, cudaStream_t s);

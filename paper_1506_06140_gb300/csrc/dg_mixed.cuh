@@ -1,0 +1,340 @@
+// The two kernels of one RK stage (paper Sec. 2.4, eqs. dg_term2, dg_term3,
+// spatial_discretisation) for an FP64 state whose right-hand side is
+// evaluated in FP32 in perturbation form.
+//
+// Every cell c has a reference state ubar_c = its weight w_0 (phi_0 = 1),
+// rounded to FP32.  Because the volume integral of a constant flux against
+// the basis gradients equals its surface integral (both Gauss rules are
+// exact for these polynomial degrees, also on the halves or quarters of a
+// hanging face), the cell's right-hand side is unchanged when f(ubar_c) is
+// subtracted from the point fluxes and from the face fluxes it integrates.
+// The kernels therefore carry only perturbations through FP32:
+//   * the point states are ubar_c + du with du from the weights l >= 1 plus
+//     the FP64 rounding residual of ubar_c;
+//   * the point fluxes are f(ubar_c + du) - f(ubar_c) (euler_dflux);
+//   * each face stores G = F*(uL, uR) - f(ubar_m) relative to its minus cell
+//     m (the existing cell at a domain boundary) and D = f(ubar_m) - f(ubar_p);
+//     the minus cell integrates G and the plus cell G + D.
+// Rounding errors then scale with the variation of the solution across a
+// cell and its neighbours instead of with the size of the fluxes, which is
+// what keeps an FP32 right-hand side usable on fine meshes.  The stage
+// combination and the state stay in FP64.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "dg_internal.h"
+#include "dg_physics.cuh"
+#include "dg_stage.cuh"
+
+namespace dgi {
+
+// FP32 trace of the weights l >= 1 of one variable of a cell on side s, plus
+// the residual ubar - fl32(ubar) (the trace of phi_0 is 1 at every point)
+template <int DIM, int K, int DIR>
+__device__ __forceinline__ void mixed_trace(const MixedArgs& x, int cell, int s, int var, int v,
+                                            float& ubar, double& ubar64, float* du) {
+  using S = Shape<DIM, K>;
+  const int nc = x.a.m.ncells;
+  const double* Wc = x.a.U + (size_t)v * S::N * nc + cell;
+  float w[S::N];
+  ubar64 = Wc[0];
+  ubar = (float)ubar64;
+  w[0] = 0.0f;
+#pragma unroll
+  for (int l = 1; l < S::N; ++l) w[l] = (float)Wc[(size_t)l * nc];
+  if (var == 0) {
+    face_trace<float, DIM, K, DIR>(x.t, w, s, x.t.P, x.t.P, du);
+  } else {
+    const int h0 = (var - 1) & 1, h1 = ((var - 1) >> 1) & 1;
+    face_trace<float, DIM, K, DIR>(x.t, w, s, x.t.PH[h0], x.t.PH[h1], du);
+  }
+}
+
+template <int DIM, int K>
+struct MixedFaceTile {
+  using S = Shape<DIM, K>;
+  static constexpr int FB = 32;
+  static constexpr int THREADS = FB * S::NV;
+  // reference [NV][FB], reference difference [NV][FB], perturbations [2][NV][QF][FB]
+  static constexpr size_t SMEM = (size_t)(2 * S::NV + 2 * S::NV * S::QF) * FB * sizeof(float);
+};
+
+template <int DIM, int K>
+__global__ void __launch_bounds__(MixedFaceTile<DIM, K>::THREADS)
+    face_flux_mixed_kernel(const MixedArgs x) {
+  using S = Shape<DIM, K>;
+  using FT = MixedFaceTile<DIM, K>;
+  constexpr int FB = FT::FB, NV = S::NV, QF = S::QF;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* sRef = reinterpret_cast<float*>(smem_raw);  // [NV][FB]
+  float* sDel = sRef + NV * FB;                       // [NV][FB]
+  float* sP = sDel + NV * FB;                         // [2][NV][QF][FB]
+  const StageArgs<double>& a = x.a;
+  const int nf = a.m.nfaces;
+  const int fl = threadIdx.x % FB, v = threadIdx.x / FB;
+  const int f = blockIdx.x * FB + fl;
+  if (f < nf) {
+    const unsigned info = a.m.finfo[f];
+    const int dir = info & 3;
+    const int vm = (info >> 2) & 7, vp = (info >> 5) & 7;
+    const int cm = a.m.fm[f], cp = a.m.fp[f];
+    float dm[QF], dp[QF], bm = 0.0f, bp = 0.0f;
+    double bm64 = 0.0, bp64 = 0.0;
+    // the minus cell sees the face as its + side (s = 1), the plus cell as its - side
+    auto trace = [&](int cell, int s, int var, float& ub, double& ub64, float* du) {
+      if (dir == 0) mixed_trace<DIM, K, 0>(x, cell, s, var, v, ub, ub64, du);
+      else if (dir == 1) mixed_trace<DIM, K, 1>(x, cell, s, var, v, ub, ub64, du);
+      else if constexpr (DIM == 3) mixed_trace<DIM, K, DIM - 1>(x, cell, s, var, v, ub, ub64, du);
+    };
+    if (cm >= 0) trace(cm, 1, vm, bm, bm64, dm);
+    if (cp >= 0) trace(cp, 0, vp, bp, bp64, dp);
+    float ref, del = 0.0f, om, op;  // reference; offsets of the two sides' perturbations
+    if (cm >= 0) {
+      ref = bm;
+      om = (float)(bm64 - (double)bm);
+      op = cp >= 0 ? (float)(bp64 - (double)bm) : om;
+      if (cp >= 0) del = (float)((double)bp - (double)bm);
+      else {
+#pragma unroll
+        for (int q = 0; q < QF; ++q) dp[q] = dm[q];
+      }
+    } else {
+      ref = bp;
+      op = (float)(bp64 - (double)bp);
+      om = op;
+#pragma unroll
+      for (int q = 0; q < QF; ++q) dm[q] = dp[q];
+    }
+    sRef[v * FB + fl] = ref;
+    sDel[v * FB + fl] = del;
+#pragma unroll
+    for (int q = 0; q < QF; ++q) {
+      sP[((0 * NV + v) * QF + q) * FB + fl] = dm[q] + om;
+      sP[((1 * NV + v) * QF + q) * FB + fl] = dp[q] + op;
+    }
+  }
+  __syncthreads();
+  const float gamma = (float)a.gamma, g1 = gamma - 1.0f;
+  // HLLC in perturbation form at every (face, point) of the block
+  for (int item = threadIdx.x; item < FB * QF; item += FT::THREADS) {
+    const int ff = item % FB, q = item / FB;
+    const int f2 = blockIdx.x * FB + ff;
+    if (f2 >= nf) continue;
+    const int d2 = a.m.finfo[f2] & 3;
+    float ub[NV], dL[NV], dR[NV], G[NV];
+#pragma unroll
+    for (int vv = 0; vv < NV; ++vv) {
+      ub[vv] = sRef[vv * FB + ff];
+      dL[vv] = sP[((0 * NV + vv) * QF + q) * FB + ff];
+      dR[vv] = sP[((1 * NV + vv) * QF + q) * FB + ff];
+    }
+    const RefState<float, DIM> r = ref_state<float, DIM>(ub, g1);
+    if (d2 == 0) hllc_dflux<float, DIM>(r, dL, dR, 0, gamma, G);
+    else if (d2 == 1) hllc_dflux<float, DIM>(r, dL, dR, 1, gamma, G);
+    else hllc_dflux<float, DIM>(r, dL, dR, DIM - 1, gamma, G);
+#pragma unroll
+    for (int vv = 0; vv < NV; ++vv) x.G[((size_t)vv * QF + q) * nf + f2] = G[vv];
+  }
+  // D = f(ubar_m) - f(ubar_p) = -(f(ubar_m + del) - f(ubar_m)) per face
+  for (int ff = threadIdx.x; ff < FB; ff += FT::THREADS) {
+    const int f2 = blockIdx.x * FB + ff;
+    if (f2 >= nf) continue;
+    const int d2 = a.m.finfo[f2] & 3;
+    float ub[NV], del[NV], df[NV];
+#pragma unroll
+    for (int vv = 0; vv < NV; ++vv) {
+      ub[vv] = sRef[vv * FB + ff];
+      del[vv] = sDel[vv * FB + ff];
+    }
+    const RefState<float, DIM> r = ref_state<float, DIM>(ub, g1);
+    const Pert<float, DIM> pq = perturb<float, DIM>(r, del, g1);
+    if (d2 == 0) euler_dflux<float, DIM>(r, del, pq, 0, df);
+    else if (d2 == 1) euler_dflux<float, DIM>(r, del, pq, 1, df);
+    else euler_dflux<float, DIM>(r, del, pq, DIM - 1, df);
+#pragma unroll
+    for (int vv = 0; vv < NV; ++vv) x.D[(size_t)vv * nf + f2] = -df[vv];
+  }
+}
+
+template <int DIM, int K>
+struct MixedCellTile {
+  using S = Shape<DIM, K>;
+  static constexpr size_t PER_CELL =
+      (size_t)(S::NV + S::NV * S::Q + DIM * S::NV * S::Q) * sizeof(float);
+  static constexpr int TC = PER_CELL * 32 > 96 * 1024 ? 16 : 32;
+  static constexpr int THREADS = TC * S::NV;
+  static constexpr size_t SMEM = PER_CELL * TC;
+};
+
+// surface integral of one side from G (+ D on the plus side of each face)
+template <int DIM, int K, int SD>
+__device__ __forceinline__ void surface_from_faces_mixed(const MixedArgs& x, int c, int v,
+                                                         unsigned coarse, float* acc) {
+  using S = Shape<DIM, K>;
+  constexpr int DIR = SD >> 1, SS = SD & 1;
+  const int nc = x.a.m.ncells, nf = x.a.m.nfaces;
+  const int e0 = x.a.m.sface[(size_t)SD * nc + c];
+  float fq[S::QF];
+  if (!((coarse >> SD) & 1)) {
+    const float dv = SS ? 0.0f : x.D[(size_t)v * nf + e0];
+#pragma unroll
+    for (int q = 0; q < S::QF; ++q) fq[q] = x.G[((size_t)v * S::QF + q) * nf + e0] + dv;
+    surface_side<float, DIM, K, DIR, SS>(x.t, x.t.P, x.t.P, fq, 1.0f, acc);
+  } else {
+    const float sub = 1.0f / (float)S::NSUB;
+#pragma unroll
+    for (int h = 0; h < S::NSUB; ++h) {
+      const float dv = SS ? 0.0f : x.D[(size_t)v * nf + e0 + h];
+#pragma unroll
+      for (int q = 0; q < S::QF; ++q) fq[q] = x.G[((size_t)v * S::QF + q) * nf + e0 + h] + dv;
+      surface_side<float, DIM, K, DIR, SS>(x.t, x.t.PH[h & 1], x.t.PH[(h >> 1) & 1], fq, sub, acc);
+    }
+  }
+}
+
+template <int DIM, int K>
+__global__ void __launch_bounds__(MixedCellTile<DIM, K>::THREADS)
+    cell_update_mixed_kernel(const MixedArgs x) {
+  using S = Shape<DIM, K>;
+  using CT = MixedCellTile<DIM, K>;
+  constexpr int TC = CT::TC, NV = S::NV, Q = S::Q, N = S::N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* sRef = reinterpret_cast<float*>(smem_raw);  // [NV][TC]
+  float* sU = sRef + NV * TC;                         // [NV][Q][TC] perturbations
+  float* sF = sU + NV * Q * TC;                       // [DIM][NV][Q][TC] flux perturbations
+  const StageArgs<double>& a = x.a;
+  const int tc = threadIdx.x % TC, v = threadIdx.x / TC;
+  const int nc = a.m.ncells;
+  const int c = blockIdx.x * TC + tc;
+  const bool valid = c < nc;
+
+  // 1. reference and perturbation of this variable at the points
+  double w0 = valid ? a.U[(size_t)v * N * nc + c] : (v == 0 ? 1.0 : 0.0);
+  {
+    const float ub = (float)w0;
+    const float res = (float)(w0 - (double)ub);
+    float w[N], u[Q];
+    w[0] = 0.0f;
+#pragma unroll
+    for (int l = 1; l < N; ++l) w[l] = valid ? (float)a.U[(size_t)(v * N + l) * nc + c] : 0.0f;
+    modal_to_nodal<float, DIM, K>(x.t, w, u);
+    sRef[v * TC + tc] = ub;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) sU[(v * Q + q) * TC + tc] = u[q] + res;
+  }
+  __syncthreads();
+
+  // 2. flux perturbations at the points of this thread
+  const float g1 = (float)a.gamma - 1.0f;
+  {
+    float ub[NV];
+#pragma unroll
+    for (int vv = 0; vv < NV; ++vv) ub[vv] = sRef[vv * TC + tc];
+    const RefState<float, DIM> r = ref_state<float, DIM>(ub, g1);
+    for (int q = v; q < Q; q += NV) {
+      float du[NV];
+#pragma unroll
+      for (int vv = 0; vv < NV; ++vv) du[vv] = sU[(vv * Q + q) * TC + tc];
+      const Pert<float, DIM> pq = perturb<float, DIM>(r, du, g1);
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) {
+        float f[NV];
+        euler_dflux<float, DIM>(r, du, pq, d, f);
+#pragma unroll
+        for (int vv = 0; vv < NV; ++vv) sF[((d * NV + vv) * Q + q) * TC + tc] = f[vv];
+      }
+    }
+  }
+  __syncthreads();
+  if (!valid) return;
+
+  // 3. volume and surface integrals of this variable (FP32)
+  float acc[N];
+#pragma unroll
+  for (int l = 0; l < N; ++l) acc[l] = 0.0f;
+  {
+    float f[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) f[q] = sF[((0 * NV + v) * Q + q) * TC + tc];
+    volume_dir<float, DIM, K, 0>(x.t, f, acc);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) f[q] = sF[((1 * NV + v) * Q + q) * TC + tc];
+    volume_dir<float, DIM, K, 1>(x.t, f, acc);
+    if constexpr (DIM == 3) {
+#pragma unroll
+      for (int q = 0; q < Q; ++q) f[q] = sF[((2 * NV + v) * Q + q) * TC + tc];
+      volume_dir<float, DIM, K, DIM - 1>(x.t, f, acc);
+    }
+  }
+  const unsigned coarse = a.m.scoarse[c];
+  surface_from_faces_mixed<DIM, K, 0>(x, c, v, coarse, acc);
+  surface_from_faces_mixed<DIM, K, 1>(x, c, v, coarse, acc);
+  surface_from_faces_mixed<DIM, K, 2>(x, c, v, coarse, acc);
+  surface_from_faces_mixed<DIM, K, 3>(x, c, v, coarse, acc);
+  if constexpr (DIM == 3) {
+    surface_from_faces_mixed<DIM, K, 2 * DIM - 2>(x, c, v, coarse, acc);
+    surface_from_faces_mixed<DIM, K, 2 * DIM - 1>(x, c, v, coarse, acc);
+  }
+
+  // 4. epilogue in FP64: out_o = sum_r C[o][r] in_r + ck[o] dt pre acc
+  const int pb = cell_problem(a.m, c);
+  const double pre = a.pre_prob ? a.pre_prob[pb] : a.pre[a.m.level[c]];
+  const double dtv = a.dt ? a.dt[pb] : 1.0;
+  const int n_out = a.n_out, n_in = a.n_in;
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    const double rhs = pre * (double)acc[j];
+    const size_t idx = (size_t)(v * N + j) * nc + c;
+    for (int oo = 0; oo < n_out; ++oo) {
+      double val = a.ck[oo] * dtv * rhs;
+      for (int r = 0; r < n_in; ++r) {
+        const double cr = a.C[oo][r];
+        if (cr == 0.0) continue;
+        val += cr * a.in[r][idx];
+      }
+      a.out[oo][idx] = val;
+    }
+  }
+}
+
+template <int DIM, int K>
+cudaError_t launch_face_mixed(const void* px, cudaStream_t s) {
+  const auto& x = *static_cast<const MixedArgs*>(px);
+  using FT = MixedFaceTile<DIM, K>;
+  if (x.a.m.nfaces == 0) return cudaSuccess;
+  const int grid = (x.a.m.nfaces + FT::FB - 1) / FT::FB;
+  face_flux_mixed_kernel<DIM, K><<<grid, FT::THREADS, FT::SMEM, s>>>(x);
+  return cudaGetLastError();
+}
+
+template <int DIM, int K>
+cudaError_t launch_cell_mixed(const void* px, cudaStream_t s) {
+  const auto& x = *static_cast<const MixedArgs*>(px);
+  using CT = MixedCellTile<DIM, K>;
+  if (x.a.m.ncells == 0) return cudaSuccess;
+  const int grid = (x.a.m.ncells + CT::TC - 1) / CT::TC;
+  cell_update_mixed_kernel<DIM, K><<<grid, CT::THREADS, CT::SMEM, s>>>(x);
+  return cudaGetLastError();
+}
+
+template <int DIM, int K>
+cudaError_t prepare_mixed() {
+  cudaError_t e = cudaFuncSetAttribute(cell_update_mixed_kernel<DIM, K>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)MixedCellTile<DIM, K>::SMEM);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(face_flux_mixed_kernel<DIM, K>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)MixedFaceTile<DIM, K>::SMEM);
+}
+
+template <int DIM, int K>
+MixedSet make_mixed_set() {
+  MixedSet ms;
+  ms.face = &launch_face_mixed<DIM, K>;
+  ms.cell = &launch_cell_mixed<DIM, K>;
+  ms.prepare = &prepare_mixed<DIM, K>;
+  return ms;
+}
+
+}  // namespace dgi
