@@ -445,7 +445,8 @@ def run_l1_study(args):
     torch.cuda.set_device(0)
     t_end = args.t_end
     rows = []
-    for precision in ("fp64", "fp32", "fp32_tc", "mixed"):
+    precisions = ("fp64", "fp32", "fp32_tc", "mixed") if args.precision == "both" else (args.precision,)
+    for precision in precisions:
         for n in (32, 64, 128, 256):
             s = dg.Solver(mesh(n), K_DEG, 1.4, rk_order=RK_ORDER, cfl=CFL, precision=precision)
             W = s.project(torch.as_tensor(wl.vortex(s.quad_points().cpu().numpy())))

@@ -406,6 +406,7 @@ struct dg_handle {
   Tab1D<float> tab1d32{};
   float* Gm = nullptr;       // DG_MIXED face fluxes minus the minus cell's reference flux
   float* Dm = nullptr;       // DG_MIXED reference flux differences per face
+  bool delta = false;        // DG_MIXED with FP32 delta registers (unlimited programs)
   void* tcB = nullptr;       // its B operands
   double* scal = nullptr;    // dt per problem [nprob]
   unsigned long long* dt_bits = nullptr;  // per-problem max signal speed [nprob]
@@ -724,9 +725,12 @@ cudaError_t cell_launch(dg_handle* h, const void* args, cudaStream_t s) {
   return h->use_tc ? h->ks->cell_tc(args, s) : h->ks->cell(args, s);
 }
 
-// face and cell kernels of one stage; DG_MIXED wraps the FP64 arguments
+// face and cell kernels of one stage; DG_MIXED wraps the FP64 arguments.
+// With delta registers (op given, h->delta) every scratch register holds the
+// FP32 difference between its stage state and W.
 template <typename real>
-int stage_launch(dg_handle* h, const StageArgs<real>& a, cudaStream_t s) {
+int stage_launch(dg_handle* h, const StageArgs<real>& a, cudaStream_t s, const Op* op = nullptr,
+                 void* W = nullptr) {
   if constexpr (std::is_same<real, double>::value) {
     if (h->ms) {
       MixedArgs x;
@@ -734,6 +738,21 @@ int stage_launch(dg_handle* h, const StageArgs<real>& a, cudaStream_t s) {
       x.t = h->tab1d32;
       x.G = h->Gm;
       x.D = h->Dm;
+      if (op && h->delta) {
+        auto freg = [&](int r) { return static_cast<float*>(h->regs[r - 1]); };
+        x.delta = 1;
+        x.a.U = static_cast<const double*>(W);
+        x.R = op->in_reg == 0 ? nullptr : freg(op->in_reg);
+        for (int r = 0; r < op->n_in; ++r) {
+          if (op->in[r] == 0) continue;
+          x.inR[x.n_inR] = freg(op->in[r]);
+          x.Cf[x.n_inR] = (float)op->C[0][r];
+          ++x.n_inR;
+        }
+        x.ckf = (float)op->ck[0];
+        if (op->out[0] == 0) x.a.out[0] = static_cast<double*>(W);
+        else x.outR = freg(op->out[0]);
+      }
       DG_CUDA(h, timed(h, DG_KERNEL_FACE, s, [&] { return h->ms->face(&x, s); }));
       DG_CUDA(h, timed(h, DG_KERNEL_CELL, s, [&] { return h->ms->cell(&x, s); }));
       return DG_OK;
@@ -834,7 +853,7 @@ int step_impl(dg_handle* h, const Program& P, void* W, cudaStream_t s) {
   for (const Op& op : P.ops) {
     void* U = op.in_reg == 0 ? W : h->regs[op.in_reg - 1];
     StageArgs<real> a = stage_args<real>(h, op, U, W);
-    const int rs = stage_launch<real>(h, a, s);
+    const int rs = stage_launch<real>(h, a, s, &op, W);
     if (rs != DG_OK) return rs;
     if (op.lim_src >= 0) {
       void* src = op.lim_src == 0 ? W : h->regs[op.lim_src - 1];
@@ -1114,6 +1133,14 @@ static int create_impl(const dg_mesh_desc* mesh, int nprob, int k, double gamma,
     float* dst = reinterpret_cast<float*>(&h->tab1d32);
     for (size_t i = 0; i < sizeof(Tab1D<double>) / sizeof(double); ++i) dst[i] = (float)src[i];
     const size_t nf = (size_t)std::max(h->nfaces, 1);
+    // delta registers: unlimited program whose stage states are affine
+    // combinations (coefficients summing to one) of W and earlier stage states
+    h->delta = !limited;
+    for (const Op& op : h->prog_step.ops) {
+      double sum = 0.0;
+      for (int r = 0; r < op.n_in; ++r) sum += op.C[0][r];
+      if (op.n_out != 1 || op.lim_src >= 0 || std::fabs(sum - 1.0) > 1e-12) h->delta = false;
+    }
     if ((r = dalloc(h, (size_t)h->nv * ks->QF * nf * sizeof(float), &p)) != DG_OK) return bail(r);
     h->Gm = static_cast<float*>(p);
     if ((r = dalloc(h, (size_t)h->nv * nf * sizeof(float), &p)) != DG_OK) return bail(r);

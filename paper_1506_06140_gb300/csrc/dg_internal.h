@@ -120,6 +120,15 @@ struct MixedArgs {
   Tab1D<float> t;       // the 1D tables in FP32
   float* G = nullptr;   // [NV][QF][nfaces] F* - f(ubar_m), m the face's minus cell
   float* D = nullptr;   // [NV][nfaces]     f(ubar_m) - f(ubar_p)
+  // Delta registers (unlimited stage programs): every stage state is
+  // U = W + R with W = a.U the FP64 state and R an FP32 register.
+  const float* R = nullptr;          // delta of the evaluated state (nullptr: U = W)
+  int delta = 0;                     // 1: the epilogue combines delta registers
+  int n_inR = 0;                     // inputs other than W
+  const float* inR[MAX_IN] = {};     // their deltas
+  float Cf[MAX_IN] = {};             // their coefficients
+  float ckf = 0.0f;                  // coefficient of dt dW/dt
+  float* outR = nullptr;             // output delta; nullptr: W += increment (a.out[0] = W)
 };
 
 template <typename real>

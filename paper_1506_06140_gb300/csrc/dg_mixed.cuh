@@ -28,20 +28,88 @@
 
 namespace dgi {
 
+// FP64 -> FP32, rounded to nearest (ties away from zero), with integer
+// instructions only: GB300 runs FP64 conversions on its narrow FP64 pipe.
+// Adding half an FP32 ulp to the bit pattern before truncating the low 29
+// mantissa bits rounds the magnitude (a carry moves into the exponent as it
+// should).  |d| below 2^-126 gives 0; |d| must stay below 2^127.
+__device__ __forceinline__ float f32_round(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d) + (1ull << 28);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned e = (hi >> 20) & 0x7FFu;  // biased FP64 exponent; FP32 bias is 896 lower
+  const unsigned fb = (hi & 0x80000000u) | ((e - 896u) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+  return e > 896u ? __uint_as_float(fb) : 0.0f;
+}
+
+// FP32 -> FP64 exactly with integer instructions (normal floats and zero;
+// FP32 subnormals, below 2^-126, give 0)
+__device__ __forceinline__ double f64_exact(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xFFu;
+  const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7FFFFFu) >> 3);
+  const unsigned lo = u << 29;
+  const unsigned long long b = ((unsigned long long)hi << 32) | lo;
+  return e != 0u ? __longlong_as_double((long long)b) : 0.0;
+}
+
+// d = hi + lo with hi = d truncated to FP32 and lo the remaining 29 mantissa bits,
+// rounded to FP32 (|d - hi - lo| <= 2^-47 |d|); integer instructions and one
+// integer-to-float conversion.  |d| below 2^-126 gives 0 + 0.
+__device__ __forceinline__ void df_split(double d, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned h32 = (unsigned)(b >> 32), l32 = (unsigned)b;
+  const unsigned e = (h32 >> 20) & 0x7FFu;
+  hi = e > 896u ? __uint_as_float((h32 & 0x80000000u) | ((e - 896u) << 23) | ((h32 & 0xFFFFFu) << 3) |
+                                  (l32 >> 29))
+                : 0.0f;
+  // the dropped bits are worth r 2^(e - 1075); that power of two as an FP32
+  const float scale = e > 948u ? __uint_as_float((e - 948u) << 23) : 0.0f;
+  const float rl = __uint2float_rn(l32 & 0x1FFFFFFFu) * scale;
+  lo = __uint_as_float(__float_as_uint(rl) | (h32 & 0x80000000u));
+}
+
+// exact sum s + err = a + b (Knuth's TwoSum)
+__device__ __forceinline__ float two_sum(float a, float b, float& err) {
+  const float s = a + b;
+  const float bb = s - a;
+  err = (a - (s - bb)) + (b - bb);
+  return s;
+}
+
+// mean (weight 0) of one variable of a cell as reference + residual: the
+// state is W (+ R, the FP32 delta of a stage register, when R is given)
+__device__ __forceinline__ void mixed_mean(double w0, const float* R, size_t idx, float& ub,
+                                           float& res) {
+  float hi, lo;
+  df_split(w0, hi, lo);
+  if (R) {
+    float e;
+    ub = two_sum(hi, R[idx], e);
+    res = lo + e;
+  } else {
+    ub = hi;
+    res = lo;
+  }
+}
+
 // FP32 trace of the weights l >= 1 of one variable of a cell on side s, plus
 // the residual ubar - fl32(ubar) (the trace of phi_0 is 1 at every point)
 template <int DIM, int K, int DIR>
 __device__ __forceinline__ void mixed_trace(const MixedArgs& x, int cell, int s, int var, int v,
-                                            float& ubar, double& ubar64, float* du) {
+                                            float& ubar, float& res, float* du) {
   using S = Shape<DIM, K>;
   const int nc = x.a.m.ncells;
-  const double* Wc = x.a.U + (size_t)v * S::N * nc + cell;
+  const size_t i0 = (size_t)v * S::N * nc + cell;
+  const double* Wc = x.a.U + i0;
   float w[S::N];
-  ubar64 = Wc[0];
-  ubar = (float)ubar64;
+  mixed_mean(Wc[0], x.R, i0, ubar, res);
   w[0] = 0.0f;
 #pragma unroll
-  for (int l = 1; l < S::N; ++l) w[l] = (float)Wc[(size_t)l * nc];
+  for (int l = 1; l < S::N; ++l) w[l] = f32_round(Wc[(size_t)l * nc]);
+  if (x.R) {
+#pragma unroll
+    for (int l = 1; l < S::N; ++l) w[l] += x.R[i0 + (size_t)l * nc];
+  }
   if (var == 0) {
     face_trace<float, DIM, K, DIR>(x.t, w, s, x.t.P, x.t.P, du);
   } else {
@@ -78,29 +146,32 @@ __global__ void __launch_bounds__(MixedFaceTile<DIM, K>::THREADS)
     const int dir = info & 3;
     const int vm = (info >> 2) & 7, vp = (info >> 5) & 7;
     const int cm = a.m.fm[f], cp = a.m.fp[f];
-    float dm[QF], dp[QF], bm = 0.0f, bp = 0.0f;
-    double bm64 = 0.0, bp64 = 0.0;
+    float dm[QF], dp[QF], bm = 0.0f, bp = 0.0f, rm = 0.0f, rp = 0.0f;
     // the minus cell sees the face as its + side (s = 1), the plus cell as its - side
-    auto trace = [&](int cell, int s, int var, float& ub, double& ub64, float* du) {
-      if (dir == 0) mixed_trace<DIM, K, 0>(x, cell, s, var, v, ub, ub64, du);
-      else if (dir == 1) mixed_trace<DIM, K, 1>(x, cell, s, var, v, ub, ub64, du);
-      else if constexpr (DIM == 3) mixed_trace<DIM, K, DIM - 1>(x, cell, s, var, v, ub, ub64, du);
+    auto trace = [&](int cell, int s, int var, float& ub, float& res, float* du) {
+      if (dir == 0) mixed_trace<DIM, K, 0>(x, cell, s, var, v, ub, res, du);
+      else if (dir == 1) mixed_trace<DIM, K, 1>(x, cell, s, var, v, ub, res, du);
+      else if constexpr (DIM == 3) mixed_trace<DIM, K, DIM - 1>(x, cell, s, var, v, ub, res, du);
     };
-    if (cm >= 0) trace(cm, 1, vm, bm, bm64, dm);
-    if (cp >= 0) trace(cp, 0, vp, bp, bp64, dp);
-    float ref, del = 0.0f, om, op;  // reference; offsets of the two sides' perturbations
+    if (cm >= 0) trace(cm, 1, vm, bm, rm, dm);
+    if (cp >= 0) trace(cp, 0, vp, bp, rp, dp);
+    // reference: the minus cell's (the plus cell's at a minus-side boundary);
+    // om, op: offsets of the two sides' states from it
+    float ref, del = 0.0f, om, op;
     if (cm >= 0) {
       ref = bm;
-      om = (float)(bm64 - (double)bm);
-      op = cp >= 0 ? (float)(bp64 - (double)bm) : om;
-      if (cp >= 0) del = (float)((double)bp - (double)bm);
-      else {
+      om = rm;
+      if (cp >= 0) {
+        del = bp - bm;
+        op = del + rp;
+      } else {
+        op = om;
 #pragma unroll
         for (int q = 0; q < QF; ++q) dp[q] = dm[q];
       }
     } else {
       ref = bp;
-      op = (float)(bp64 - (double)bp);
+      op = rp;
       om = op;
 #pragma unroll
       for (int q = 0; q < QF; ++q) dm[q] = dp[q];
@@ -209,14 +280,22 @@ __global__ void __launch_bounds__(MixedCellTile<DIM, K>::THREADS)
   const bool valid = c < nc;
 
   // 1. reference and perturbation of this variable at the points
-  double w0 = valid ? a.U[(size_t)v * N * nc + c] : (v == 0 ? 1.0 : 0.0);
   {
-    const float ub = (float)w0;
-    const float res = (float)(w0 - (double)ub);
+    const size_t i0 = (size_t)v * N * nc + c;
+    float ub = v == 0 ? 1.0f : 0.0f, res = 0.0f;  // padding cells: unit density at rest
     float w[N], u[Q];
     w[0] = 0.0f;
 #pragma unroll
-    for (int l = 1; l < N; ++l) w[l] = valid ? (float)a.U[(size_t)(v * N + l) * nc + c] : 0.0f;
+    for (int l = 1; l < N; ++l) w[l] = 0.0f;
+    if (valid) {
+      mixed_mean(a.U[i0], x.R, i0, ub, res);
+#pragma unroll
+      for (int l = 1; l < N; ++l) w[l] = f32_round(a.U[i0 + (size_t)l * nc]);
+      if (x.R) {
+#pragma unroll
+        for (int l = 1; l < N; ++l) w[l] += x.R[i0 + (size_t)l * nc];
+      }
+    }
     modal_to_nodal<float, DIM, K>(x.t, w, u);
     sRef[v * TC + tc] = ub;
 #pragma unroll
@@ -276,14 +355,30 @@ __global__ void __launch_bounds__(MixedCellTile<DIM, K>::THREADS)
     surface_from_faces_mixed<DIM, K, 2 * DIM - 1>(x, c, v, coarse, acc);
   }
 
-  // 4. epilogue in FP64: out_o = sum_r C[o][r] in_r + ck[o] dt pre acc
+  // 4. epilogue
   const int pb = cell_problem(a.m, c);
   const double pre = a.pre_prob ? a.pre_prob[pb] : a.pre[a.m.level[c]];
   const double dtv = a.dt ? a.dt[pb] : 1.0;
+  if (x.delta) {
+    // delta registers: R_out = sum_r C_r R_r + ck dt dW/dt in FP32 (the
+    // coefficients of a stage state sum to one, so W drops out); the last
+    // stage adds that increment to W in FP64
+    const float sc = x.ckf * f32_round(dtv * pre);
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      const size_t idx = (size_t)(v * N + j) * nc + c;
+      float val = sc * acc[j];
+      for (int r = 0; r < x.n_inR; ++r) val += x.Cf[r] * x.inR[r][idx];
+      if (x.outR) x.outR[idx] = val;
+      else a.out[0][idx] = a.U[idx] + f64_exact(val);
+    }
+    return;
+  }
+  // FP64 registers: out_o = sum_r C[o][r] in_r + ck[o] dt pre acc
   const int n_out = a.n_out, n_in = a.n_in;
 #pragma unroll
   for (int j = 0; j < N; ++j) {
-    const double rhs = pre * (double)acc[j];
+    const double rhs = pre * f64_exact(acc[j]);
     const size_t idx = (size_t)(v * N + j) * nc + c;
     for (int oo = 0; oo < n_out; ++oo) {
       double val = a.ck[oo] * dtv * rhs;
