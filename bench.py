@@ -358,11 +358,15 @@ def summarize(args, results, world):
             # HBM: a launch of the dominant kernel processes one stage of the mesh,
             # whose algorithmic traffic is 3 state arrays (read U_i and w^n, write U_i+1)
             byt = 3 * state_bytes_per_cell(dim, k, esize) * cells
+            if precision == "mixed":
+                # FP64 state read, FP32 delta registers read and written
+                byt = (state_bytes_per_cell(dim, k, 8) + 2 * state_bytes_per_cell(dim, k, 4)) * cells
             achieved = byt / avg_s / 1e9
             roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm,
                     "unit": "GB/s", "frac": achieved / hbm, "peak_source": peak_kind,
                     "traffic": dram_traffic(kname, tag), "algorithmic_per_launch": byt,
-                    "algorithmic_unit": "bytes (3 state arrays per stage)"}
+                    "algorithmic_unit": "bytes (FP64 state + 2 FP32 delta registers per stage)"
+                    if precision == "mixed" else "bytes (3 state arrays per stage)"}
         e2e_value = dof_updates / (r["ms_e2e"] * 1e-3)
         lines[precision] = {
             "value": value, "ms_per_step": r["ms"] / args.steps, "roofline": roof,
