@@ -234,27 +234,53 @@ def dram_traffic(kernel, workload):
 
 # ---------------------------------------------------------------------------
 
+class Ranks:
+    """The only cross-rank traffic of a multi-GPU run: a barrier around the
+    timed region and the maximum of the ranks' times (each rank advances its
+    own replica of the workload; no data-path collective)."""
+
+    def __init__(self, world, backend="nccl", device="cuda", local_rank=0):
+        import torch
+        self.world, self.device = world, device
+        self.dist = None
+        if world > 1:
+            import torch.distributed as dist
+            if not dist.is_initialized():
+                if backend == "nccl":
+                    dist.init_process_group(backend, device_id=torch.device("cuda", local_rank))
+                else:
+                    dist.init_process_group(backend)
+            self.dist = dist
+
+    def barrier(self):
+        if self.dist:
+            self.dist.barrier()
+
+    def max(self, x):
+        if not self.dist:
+            return x
+        import torch
+        t = torch.tensor([float(x)], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return t.item()
+
+    def sum(self, x):
+        if not self.dist:
+            return x
+        import torch
+        t = torch.tensor([float(x)], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.SUM)
+        return t.item()
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
     from paper_1506_06140_gb300 import dg
     from paper_1506_06140_gb300 import workloads as wl
 
     torch.cuda.set_device(local_rank)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-
-    def barrier():
-        if dist:
-            dist.barrier()
-
-    def max_over_ranks(x):
-        if not dist:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return t.item()
+    ranks = Ranks(world, "nccl", "cuda", local_rank)
+    barrier, max_over_ranks = ranks.barrier, ranks.max
 
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
     results = {}
