@@ -46,7 +46,7 @@ WORKLOADS = {
              "sizes drawn from {32,48,64,96,128}^2 (3.4M cells), k=2 (6 coeffs/cell/var), SSP-RK3, "
              "per-problem CFL timestep, FP32, all steps in one CUDA-graph launch",
         dim=2, k=2, rk=3, stages=3, limiter="none", positivity=False, precisions=("fp32",),
-        tag="ensemble512_k2", graph=True),
+        tag="ensemble512_k2", graph=True, autotune=True),
     "sedov3d": dict(
         name="Sedov blast 3D, 64^3 base + central 32^3 refined once (491,520 cells), k=2 "
              "(10 coeffs/cell/var), SSP-RK3, characteristic TVB limiter + positivity limiter, "
@@ -69,7 +69,7 @@ def mesh(n=N_CELLS_1D, half=5.0):
     return wl.mesh_uniform(2, [n, n], [-half, -half], [half, half])
 
 
-def make_problem(wk, precision):
+def make_problem(wk, precision, autotune=None):
     """Solver and initial weights (on the device) of a workload."""
     import torch
     from paper_1506_06140_gb300 import dg
@@ -83,8 +83,10 @@ def make_problem(wk, precision):
         ic = None
     else:
         m, ic = wl.mesh_two_level_3d(64, 16, 47), wl.sedov3d
+    if autotune is None:
+        autotune = W.get("autotune", False)
     s = dg.Solver(m, W["k"], 1.4, rk_order=W["rk"], cfl=CFL, limiter=W["limiter"],
-                  positivity=W["positivity"], precision=precision)
+                  positivity=W["positivity"], precision=precision, autotune=autotune)
     xyz = s.quad_points().cpu().numpy()
     if ic is not None:
         U = ic(xyz)  # closed-form IC at the Gauss points
@@ -340,8 +342,25 @@ def run_gpu(args, rank, world, local_rank):
         e1.record(stream)
         torch.cuda.synchronize()
         ms_e2e = max_over_ranks(e0.elapsed_time(e1))
+        tiles = None
+        if WORKLOADS[args.workload].get("autotune"):
+            # the fixed-tile baseline: the same graph launch with the default tiles
+            sf, Wf = make_problem(args.workload, precision, autotune=False)
+            sf.advance(Wf, args.warmup)
+            sf.advance(Wf, args.steps)
+            torch.cuda.synchronize()
+            barrier()
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            sf.advance(Wf, args.steps)
+            f1.record(stream)
+            torch.cuda.synchronize()
+            tiles = {"autotuned": list(s.tiles()), "fixed": list(sf.tiles()),
+                     "fixed_tile_ms": max_over_ranks(f0.elapsed_time(f1))}
+            del sf, Wf
         results[precision] = dict(solver=s, ms=ms, ms_e2e=ms_e2e, prof=prof, clocks=clk.summary(),
-                                  state_bytes=W.numel() * W.element_size(), n_cells=s.n_cells)
+                                  state_bytes=W.numel() * W.element_size(), n_cells=s.n_cells,
+                                  tiles=tiles)
         del W, W0, Wd, Wh
     return results
 
@@ -402,6 +421,11 @@ def summarize(args, results, world):
             "kernel_ms": {kk: v[1] for kk, v in prof.items()},
             "cells": cells,
         }
+        if r.get("tiles"):
+            t = dict(r["tiles"])
+            t["fixed_tile_value"] = dof_updates / (t.pop("fixed_tile_ms") * 1e-3)
+            t["unit"] = "[cells per block of the cell kernel, faces per block of the face kernel]"
+            lines[precision]["tiles"] = t
     return lines
 
 
@@ -601,6 +625,8 @@ def main():
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                "dtype": {"fp64": "f64", "mixed": "f32/f64"}.get(prec, "f32"), "data": "synthetic",
                "config": workload_config(args.workload, prec, one["cells"])}
+        if "tiles" in one:
+            out["config"]["tiles"] = one["tiles"]
         out.update({kk: one[kk] for kk in ("roofline", "e2e", "gpu_launches", "clocks", "kernel_ms")})
         print(json.dumps(out), flush=True)
         return 0

@@ -89,8 +89,13 @@ typedef struct {
   double Mtilde;     /* TVB bound: a slope is kept when |sqrt(3) slope| <= Mtilde * dx */
   int positivity;    /* 1: positivity limiter of Sec. 3.4 after every stage */
   double eps;        /* positivity floor */
-  int precision;     /* DG_FP64, DG_FP32 or DG_FP32_TC (state, fluxes and contractions);
-                        the totals, L1 error, timestep and positivity check stay FP64 */
+  int precision;     /* DG_FP64, DG_FP32, DG_FP32_TC or DG_MIXED (state, fluxes and
+                        contractions); the totals, L1 error, timestep and positivity
+                        check stay FP64 */
+  int autotune;      /* 1: dg_create times the stage kernels on the mesh at every
+                        feasible tile (16, 32 or 64 cells or faces per thread block) and keeps the
+                        fastest; 0 (default): fixed tiles.  Results do not depend on
+                        the tiles.  See dg_tiles. */
 } dg_options;
 
 typedef struct dg_handle dg_handle;
@@ -113,6 +118,12 @@ int dg_destroy(dg_handle* h);
 
 /* Last error message of a handle (or of the last failed dg_create if h is NULL). */
 const char* dg_last_error(const dg_handle* h);
+
+/* Tiles of the stage kernels in use: cells per thread block of the cell
+ * kernel and faces per block of the face kernel (the fixed defaults, or the
+ * autotuner's choice when dg_options.autotune was set).  A tensor-core cell
+ * kernel (DG_FP32_TC) reports its fixed 32 cells.  Host outputs. */
+int dg_tiles(const dg_handle* h, int* cell_tile, int* face_tile);
 
 /* Sizes: cells, basis functions N(k) (eq. nof_basis_functions and its 2D
  * analogue), variables nv, volume Gauss points per cell (k+1)^dim, points of

@@ -15,8 +15,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["dg_inst_2d.cu", "dg_inst_3d.cu", "dg_mixed_2d.cu", "dg_mixed_3d.cu", "dg_common.cu",
-           "dg_noalloc.cu", "dg_host.cpp"]
+SOURCES = ["dg_inst_3d_f64.cu", "dg_inst_3d_f32.cu", "dg_inst_2d_f64.cu", "dg_inst_2d_f32.cu",
+           "dg_mixed_3d.cu", "dg_mixed_2d.cu", "dg_common.cu", "dg_noalloc.cu", "dg_host.cpp"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-I", os.path.join(ROOT, "include"),
          "-I", CSRC]

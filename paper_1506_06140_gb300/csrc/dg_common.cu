@@ -5,8 +5,10 @@
 
 namespace dgi {
 
-bool kernel_set_2d(int prec, int k, KernelSet* out);
-bool kernel_set_3d(int prec, int k, KernelSet* out);
+bool kernel_set_2d_f64(int k, KernelSet* out);
+bool kernel_set_2d_f32(int k, KernelSet* out);
+bool kernel_set_3d_f64(int k, KernelSet* out);
+bool kernel_set_3d_f32(int k, KernelSet* out);
 
 const KernelSet* kernel_set(int prec, int dim, int k) {
   static KernelSet sets[2][2][4];
@@ -16,7 +18,8 @@ const KernelSet* kernel_set(int prec, int dim, int k) {
   std::lock_guard<std::mutex> lock(mu);
   KernelSet& ks = sets[prec][dim - 2][k];
   if (!have[prec][dim - 2][k]) {
-    const bool ok = dim == 2 ? kernel_set_2d(prec, k, &ks) : kernel_set_3d(prec, k, &ks);
+    const bool ok = dim == 2 ? (prec == 0 ? kernel_set_2d_f64(k, &ks) : kernel_set_2d_f32(k, &ks))
+                             : (prec == 0 ? kernel_set_3d_f64(k, &ks) : kernel_set_3d_f32(k, &ks));
     if (!ok) return nullptr;
     have[prec][dim - 2][k] = true;
   }
@@ -39,6 +42,20 @@ const MixedSet* mixed_set(int dim, int k) {
     have[dim - 2][k] = true;
   }
   return &ms;
+}
+
+template <typename T>
+__global__ void fill_kernel(T* dst, size_t n, T value) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = value;
+}
+
+cudaError_t launch_fill(void* dst, size_t n, double value, int esize, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const int grid = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+  if (esize == 8) fill_kernel<double><<<grid, 256, 0, s>>>(static_cast<double*>(dst), n, value);
+  else fill_kernel<float><<<grid, 256, 0, s>>>(static_cast<float*>(dst), n, (float)value);
+  return cudaGetLastError();
 }
 
 __global__ void set_scalar_kernel(double* dst, int n, double value) {

@@ -407,6 +407,7 @@ struct dg_handle {
   float* Gm = nullptr;       // DG_MIXED face fluxes minus the minus cell's reference flux
   float* Dm = nullptr;       // DG_MIXED reference flux differences per face
   bool delta = false;        // DG_MIXED with FP32 delta registers (unlimited programs)
+  int cell_tile = 0, face_tile = 0;  // stage-kernel tiles (0: the kernels' defaults)
   void* tcB = nullptr;       // its B operands
   double* scal = nullptr;    // dt per problem [nprob]
   unsigned long long* dt_bits = nullptr;  // per-problem max signal speed [nprob]
@@ -790,6 +791,8 @@ StageArgs<real> stage_args(dg_handle* h, const Op& op, const void* U, void* W) {
     for (int r = 0; r < MAX_IN; ++r) a.C[o][r] = (real)op.C[o][r];
   }
   a.dt = h->scal;
+  a.cell_tile = h->cell_tile;
+  a.face_tile = h->face_tile;
   return a;
 }
 
@@ -977,6 +980,83 @@ int adjoint_step_impl(dg_handle* h, const void* Wn, double dt, const void* lam1,
   return combine_list<real>(h, lam0, t, s);
 }
 
+// Tile autotuner: times dW/dt of a free-stream state on the handle's own mesh
+// for every feasible tile of the face kernel (cell tile fixed), then of the
+// cell kernel, keeping the fastest of each.  The tile only changes how cells
+// and faces are grouped into thread blocks, never a result.
+template <typename real>
+int autotune_tiles(dg_handle* h, cudaStream_t s) {
+  const size_t n = (size_t)h->nv * h->N * h->ncells;
+  if (n == 0) return DG_OK;
+  void *U = nullptr, *out = nullptr;
+  int r;
+  if (cudaMalloc(&U, n * h->esize) != cudaSuccess) return fail(h, DG_ERR_OOM, "autotune: out of device memory");
+  if (cudaMalloc(&out, n * h->esize) != cudaSuccess) {
+    cudaFree(U);
+    return fail(h, DG_ERR_OOM, "autotune: out of device memory");
+  }
+  struct Free {
+    void *a, *b;
+    ~Free() { cudaFree(a); cudaFree(b); }
+  } guard{U, out};
+  // rho = 1, m = 0, E = 2.5 (p = 1 at gamma = 1.4): weight 0 of each variable
+  DG_CUDA(h, launch_fill(U, n, 0.0, (int)h->esize, s));
+  const size_t row = (size_t)h->N * h->ncells;
+  DG_CUDA(h, launch_fill(U, h->ncells, 1.0, (int)h->esize, s));
+  DG_CUDA(h, launch_fill(static_cast<char*>(U) + (h->nv - 1) * row * h->esize, h->ncells,
+                         1.0 / (h->gamma - 1.0), (int)h->esize, s));
+  cudaEvent_t e0, e1;
+  DG_CUDA(h, cudaEventCreate(&e0));
+  DG_CUDA(h, cudaEventCreate(&e1));
+  auto time_rhs = [&](float& best) -> int {
+    best = 3.4e38f;
+    for (int trial = 0; trial < 3; ++trial) {
+      const int rr = rhs_into<real>(h, U, out, s);
+      if (rr != DG_OK) return rr;
+      DG_CUDA(h, cudaEventRecord(e0, s));
+      for (int rep = 0; rep < 3; ++rep) {
+        const int r2 = rhs_into<real>(h, U, out, s);
+        if (r2 != DG_OK) return r2;
+      }
+      DG_CUDA(h, cudaEventRecord(e1, s));
+      DG_CUDA(h, cudaEventSynchronize(e1));
+      float ms = 0.0f;
+      DG_CUDA(h, cudaEventElapsedTime(&ms, e0, e1));
+      best = std::min(best, ms);
+    }
+    return DG_OK;
+  };
+  const int cmax = h->ms ? h->ms->cell_tile_max : h->ks->cell_tile_max;
+  const int fmax = h->ms ? h->ms->face_tile_max : h->ks->face_tile_max;
+  const int cdef = h->ms ? h->ms->cell_tile : h->ks->cell_tile;
+  const int fdef = h->ms ? h->ms->face_tile : h->ks->face_tile;
+  h->cell_tile = cdef;
+  int best_f = fdef;
+  float best_t = 3.4e38f;
+  for (int fb = 16; fb <= fmax; fb *= 2) {
+    h->face_tile = fb;
+    float t;
+    if ((r = time_rhs(t)) != DG_OK) return r;
+    if (t < best_t) { best_t = t; best_f = fb; }
+  }
+  h->face_tile = best_f;
+  if (!h->use_tc) {
+    int best_c = cdef;
+    best_t = 3.4e38f;
+    for (int tc = 16; tc <= cmax; tc *= 2) {
+      h->cell_tile = tc;
+      float t;
+      if ((r = time_rhs(t)) != DG_OK) return r;
+      if (t < best_t) { best_t = t; best_c = tc; }
+    }
+    h->cell_tile = best_c;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  DG_CUDA(h, cudaStreamSynchronize(s));
+  return DG_OK;
+}
+
 int rk_step_dispatch(dg_handle* h, void* W, double dt, double* dt_used, cudaStream_t s) {
   return h->prec == DG_FP64 ? rk_step_any<double>(h, W, dt, dt_used, s)
                             : rk_step_any<float>(h, W, dt, dt_used, s);
@@ -999,6 +1079,7 @@ int dg_default_options(dg_options* opt) {
   opt->positivity = 0;
   opt->eps = 1e-10;
   opt->precision = DG_FP64;
+  opt->autotune = 0;
   return DG_OK;
 }
 
@@ -1161,6 +1242,13 @@ static int create_impl(const dg_mesh_desc* mesh, int nprob, int k, double gamma,
   }
   if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
     return bail(cuda_fail(h, cudaGetLastError(), "cudaStreamCreate"));
+  h->cell_tile = h->ms ? h->ms->cell_tile : ks->cell_tile;
+  h->face_tile = h->ms ? h->ms->face_tile : ks->face_tile;
+  if (o.autotune) {
+    r = h->prec == DG_FP64 ? autotune_tiles<double>(h, h->cap_stream)
+                           : autotune_tiles<float>(h, h->cap_stream);
+    if (r != DG_OK) return bail(r);
+  }
   *out = h;
   return DG_OK;
 }
@@ -1245,6 +1333,13 @@ int dg_project(dg_handle* h, const double* u_dev, void* W_dev, void* stream) {
     a.Wout = static_cast<float*>(W_dev);
     DG_CUDA(h, h->ks->project(&a, s));
   }
+  return DG_OK;
+}
+
+int dg_tiles(const dg_handle* h, int* cell_tile, int* face_tile) {
+  if (!check_handle(h) || !cell_tile || !face_tile) return DG_ERR_ARG;
+  *cell_tile = h->use_tc ? 32 : h->cell_tile;
+  *face_tile = h->face_tile;
   return DG_OK;
 }
 

@@ -109,6 +109,8 @@ struct StageArgs {
   real C[MAX_OUT][MAX_IN] = {};
   real ck[MAX_OUT] = {};
   const double* dt = nullptr;   // device timestep per problem; nullptr means dt = 1
+  int cell_tile = 0;            // cells per block of the cell kernel (0: its default)
+  int face_tile = 0;            // faces per block of the face kernel (0: its default)
   const real* tcB = nullptr;    // tensor-core B operands (tensor-core cell kernel)
   int* status = nullptr;        // device status word
 };
@@ -200,6 +202,8 @@ struct KernelSet {
                       const std::vector<double>& gw, const std::vector<double>& g3x,
                       const std::vector<double>& g3w, const std::vector<double>& lx) = nullptr;
   cudaError_t (*prepare)() = nullptr;  // one-time kernel attributes (not capturable)
+  // tiles of the stage kernels: default and largest cells / faces per block
+  int cell_tile = 32, cell_tile_max = 32, face_tile = 32, face_tile_max = 32;
   cudaError_t (*face)(const void* stage_args, cudaStream_t s) = nullptr;
   cudaError_t (*cell)(const void* stage_args, cudaStream_t s) = nullptr;
   cudaError_t (*limit)(const void* limit_args, cudaStream_t s) = nullptr;
@@ -223,6 +227,7 @@ const KernelSet* kernel_set(int prec, int dim, int k);
 // Stage kernels for an FP64 state with an FP32 right-hand side in
 // perturbation form (argument block MixedArgs, dg_mixed.cuh).
 struct MixedSet {
+  int cell_tile = 32, cell_tile_max = 32, face_tile = 32, face_tile_max = 32;
   cudaError_t (*face)(const void* mixed_args, cudaStream_t s) = nullptr;
   cudaError_t (*cell)(const void* mixed_args, cudaStream_t s) = nullptr;
   cudaError_t (*prepare)() = nullptr;
@@ -232,6 +237,8 @@ const MixedSet* mixed_set(int dim, int k);
 
 // shared helper kernels (dg_common.cu)
 cudaError_t launch_set_scalar(double* dst, int n, double value, cudaStream_t s);
+// dst[i] = value for i < n, elements of esize bytes (4: float, 8: double)
+cudaError_t launch_fill(void* dst, size_t n, double value, int esize, cudaStream_t s);
 cudaError_t launch_dt_finalize(const unsigned long long* bits, int nprob, double factor, double* dt,
                                double* dt_copy, cudaStream_t s);
 

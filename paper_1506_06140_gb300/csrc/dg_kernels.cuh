@@ -624,9 +624,13 @@ template <typename real, int DIM, int K>
 cudaError_t launch_face(const void* pa, cudaStream_t s) {
   const auto& a = *static_cast<const StageArgs<real>*>(pa);
   using FT = FaceTile<real, DIM, K>;
+  constexpr int NV = Shape<DIM, K>::NV;
   if (a.m.nfaces == 0) return cudaSuccess;
-  const int grid = (a.m.nfaces + FT::FB - 1) / FT::FB;
-  face_flux_kernel<real, DIM, K><<<grid, FT::THREADS, FT::SMEM, s>>>(a);
+  const int fb = a.face_tile == 16 || a.face_tile == 64 ? a.face_tile : 32;
+  const int grid = (a.m.nfaces + fb - 1) / fb;
+  if (fb == 16) face_flux_kernel<real, DIM, K, 16><<<grid, 16 * NV, FT::smem(16), s>>>(a);
+  else if (fb == 64) face_flux_kernel<real, DIM, K, 64><<<grid, 64 * NV, FT::smem(64), s>>>(a);
+  else face_flux_kernel<real, DIM, K, 32><<<grid, 32 * NV, FT::smem(32), s>>>(a);
   return cudaGetLastError();
 }
 
@@ -634,9 +638,19 @@ template <typename real, int DIM, int K>
 cudaError_t launch_cell(const void* pa, cudaStream_t s) {
   const auto& a = *static_cast<const StageArgs<real>*>(pa);
   using CT = CellTile<real, DIM, K>;
+  constexpr int NV = Shape<DIM, K>::NV;
   if (a.m.ncells == 0) return cudaSuccess;
-  const int grid = (a.m.ncells + CT::TC - 1) / CT::TC;
-  cell_update_kernel<real, DIM, K><<<grid, CT::THREADS, CT::SMEM, s>>>(a);
+  const int tc = (a.cell_tile == 16 || a.cell_tile == 32 || a.cell_tile == 64) && a.cell_tile <= CT::TC_MAX
+                     ? a.cell_tile
+                     : CT::TC;
+  const int grid = (a.m.ncells + tc - 1) / tc;
+  if (tc == 16) {
+    cell_update_kernel<real, DIM, K, 16><<<grid, 16 * NV, CT::smem(16), s>>>(a);
+  } else if (tc == 32) {
+    if constexpr (CT::TC_MAX >= 32) cell_update_kernel<real, DIM, K, 32><<<grid, 32 * NV, CT::smem(32), s>>>(a);
+  } else {
+    if constexpr (CT::TC_MAX >= 64) cell_update_kernel<real, DIM, K, 64><<<grid, 64 * NV, CT::smem(64), s>>>(a);
+  }
   return cudaGetLastError();
 }
 
@@ -663,13 +677,20 @@ template <typename real, int DIM, int K>
 cudaError_t prepare_kernels() {
   cudaError_t e0 = prepare_adjoint_kernels<real, DIM, K>();
   if (e0 != cudaSuccess) return e0;
-  cudaError_t e = cudaFuncSetAttribute(cell_update_kernel<real, DIM, K>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)CellTile<real, DIM, K>::SMEM);
+  using CT = CellTile<real, DIM, K>;
+  using FT = FaceTile<real, DIM, K>;
+  const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e = cudaFuncSetAttribute(cell_update_kernel<real, DIM, K, 16>, attr, (int)CT::smem(16));
+  if (e == cudaSuccess && CT::TC_MAX >= 32) {
+    if constexpr (CT::TC_MAX >= 32) e = cudaFuncSetAttribute(cell_update_kernel<real, DIM, K, 32>, attr, (int)CT::smem(32));
+  }
+  if (e == cudaSuccess && CT::TC_MAX >= 64) {
+    if constexpr (CT::TC_MAX >= 64) e = cudaFuncSetAttribute(cell_update_kernel<real, DIM, K, 64>, attr, (int)CT::smem(64));
+  }
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(face_flux_kernel<real, DIM, K>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)FaceTile<real, DIM, K>::SMEM);
+  if ((e = cudaFuncSetAttribute(face_flux_kernel<real, DIM, K, 16>, attr, (int)FT::smem(16))) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(face_flux_kernel<real, DIM, K, 32>, attr, (int)FT::smem(32))) != cudaSuccess) return e;
+  return cudaFuncSetAttribute(face_flux_kernel<real, DIM, K, 64>, attr, (int)FT::smem(64));
 }
 
 template <typename real, int DIM, int K>
@@ -749,6 +770,10 @@ KernelSet make_kernel_set(int prec) {
   ks.tab_size = S::TAB_SIZE;
   ks.fill_tables = &fill_tables<DIM, K>;
   ks.prepare = &prepare_kernels<real, DIM, K>;
+  ks.cell_tile = CellTile<real, DIM, K>::TC;
+  ks.cell_tile_max = CellTile<real, DIM, K>::TC_MAX;
+  ks.face_tile = FaceTile<real, DIM, K>::FB;
+  ks.face_tile_max = FaceTile<real, DIM, K>::FB_MAX;
   ks.face = &launch_face<real, DIM, K>;
   ks.cell = &launch_cell<real, DIM, K>;
   ks.limit = &launch_limit<real, DIM, K>;

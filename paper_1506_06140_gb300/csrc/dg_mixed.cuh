@@ -121,18 +121,17 @@ __device__ __forceinline__ void mixed_trace(const MixedArgs& x, int cell, int s,
 template <int DIM, int K>
 struct MixedFaceTile {
   using S = Shape<DIM, K>;
-  static constexpr int FB = 32;
-  static constexpr int THREADS = FB * S::NV;
+  static constexpr int FB = 32;  // default faces per block; kernels for 16, 32, 64
+  static constexpr int FB_MAX = 64;
   // reference [NV][FB], reference difference [NV][FB], perturbations [2][NV][QF][FB]
-  static constexpr size_t SMEM = (size_t)(2 * S::NV + 2 * S::NV * S::QF) * FB * sizeof(float);
+  static constexpr size_t smem(int fb) { return (size_t)(2 * S::NV + 2 * S::NV * S::QF) * fb * sizeof(float); }
 };
 
-template <int DIM, int K>
-__global__ void __launch_bounds__(MixedFaceTile<DIM, K>::THREADS)
+template <int DIM, int K, int FB>
+__global__ void __launch_bounds__(FB * Shape<DIM, K>::NV)
     face_flux_mixed_kernel(const MixedArgs x) {
   using S = Shape<DIM, K>;
-  using FT = MixedFaceTile<DIM, K>;
-  constexpr int FB = FT::FB, NV = S::NV, QF = S::QF;
+  constexpr int NV = S::NV, QF = S::QF, THREADS = FB * NV;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* sRef = reinterpret_cast<float*>(smem_raw);  // [NV][FB]
   float* sDel = sRef + NV * FB;                       // [NV][FB]
@@ -187,7 +186,7 @@ __global__ void __launch_bounds__(MixedFaceTile<DIM, K>::THREADS)
   __syncthreads();
   const float gamma = (float)a.gamma, g1 = gamma - 1.0f;
   // HLLC in perturbation form at every (face, point) of the block
-  for (int item = threadIdx.x; item < FB * QF; item += FT::THREADS) {
+  for (int item = threadIdx.x; item < FB * QF; item += THREADS) {
     const int ff = item % FB, q = item / FB;
     const int f2 = blockIdx.x * FB + ff;
     if (f2 >= nf) continue;
@@ -207,7 +206,7 @@ __global__ void __launch_bounds__(MixedFaceTile<DIM, K>::THREADS)
     for (int vv = 0; vv < NV; ++vv) x.G[((size_t)vv * QF + q) * nf + f2] = G[vv];
   }
   // D = f(ubar_m) - f(ubar_p) = -(f(ubar_m + del) - f(ubar_m)) per face
-  for (int ff = threadIdx.x; ff < FB; ff += FT::THREADS) {
+  for (int ff = threadIdx.x; ff < FB; ff += THREADS) {
     const int f2 = blockIdx.x * FB + ff;
     if (f2 >= nf) continue;
     const int d2 = a.m.finfo[f2] & 3;
@@ -232,9 +231,9 @@ struct MixedCellTile {
   using S = Shape<DIM, K>;
   static constexpr size_t PER_CELL =
       (size_t)(S::NV + S::NV * S::Q + DIM * S::NV * S::Q) * sizeof(float);
-  static constexpr int TC = PER_CELL * 32 > 96 * 1024 ? 16 : 32;
-  static constexpr int THREADS = TC * S::NV;
-  static constexpr size_t SMEM = PER_CELL * TC;
+  static constexpr int TC = PER_CELL * 32 > 96 * 1024 ? 16 : 32;  // default cells per block
+  static constexpr int TC_MAX = PER_CELL * 64 <= 200 * 1024 ? 64 : (PER_CELL * 32 <= 200 * 1024 ? 32 : 16);
+  static constexpr size_t smem(int tc) { return PER_CELL * tc; }
 };
 
 // surface integral of one side from G (+ D on the plus side of each face)
@@ -263,12 +262,11 @@ __device__ __forceinline__ void surface_from_faces_mixed(const MixedArgs& x, int
   }
 }
 
-template <int DIM, int K>
-__global__ void __launch_bounds__(MixedCellTile<DIM, K>::THREADS)
+template <int DIM, int K, int TC>
+__global__ void __launch_bounds__(TC * Shape<DIM, K>::NV)
     cell_update_mixed_kernel(const MixedArgs x) {
   using S = Shape<DIM, K>;
-  using CT = MixedCellTile<DIM, K>;
-  constexpr int TC = CT::TC, NV = S::NV, Q = S::Q, N = S::N;
+  constexpr int NV = S::NV, Q = S::Q, N = S::N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* sRef = reinterpret_cast<float*>(smem_raw);  // [NV][TC]
   float* sU = sRef + NV * TC;                         // [NV][Q][TC] perturbations
@@ -396,9 +394,13 @@ template <int DIM, int K>
 cudaError_t launch_face_mixed(const void* px, cudaStream_t s) {
   const auto& x = *static_cast<const MixedArgs*>(px);
   using FT = MixedFaceTile<DIM, K>;
+  constexpr int NV = Shape<DIM, K>::NV;
   if (x.a.m.nfaces == 0) return cudaSuccess;
-  const int grid = (x.a.m.nfaces + FT::FB - 1) / FT::FB;
-  face_flux_mixed_kernel<DIM, K><<<grid, FT::THREADS, FT::SMEM, s>>>(x);
+  const int fb = x.a.face_tile == 16 || x.a.face_tile == 64 ? x.a.face_tile : 32;
+  const int grid = (x.a.m.nfaces + fb - 1) / fb;
+  if (fb == 16) face_flux_mixed_kernel<DIM, K, 16><<<grid, 16 * NV, FT::smem(16), s>>>(x);
+  else if (fb == 64) face_flux_mixed_kernel<DIM, K, 64><<<grid, 64 * NV, FT::smem(64), s>>>(x);
+  else face_flux_mixed_kernel<DIM, K, 32><<<grid, 32 * NV, FT::smem(32), s>>>(x);
   return cudaGetLastError();
 }
 
@@ -406,26 +408,47 @@ template <int DIM, int K>
 cudaError_t launch_cell_mixed(const void* px, cudaStream_t s) {
   const auto& x = *static_cast<const MixedArgs*>(px);
   using CT = MixedCellTile<DIM, K>;
+  constexpr int NV = Shape<DIM, K>::NV;
   if (x.a.m.ncells == 0) return cudaSuccess;
-  const int grid = (x.a.m.ncells + CT::TC - 1) / CT::TC;
-  cell_update_mixed_kernel<DIM, K><<<grid, CT::THREADS, CT::SMEM, s>>>(x);
+  const int tc = (x.a.cell_tile == 16 || x.a.cell_tile == 32 || x.a.cell_tile == 64) && x.a.cell_tile <= CT::TC_MAX
+                     ? x.a.cell_tile
+                     : CT::TC;
+  const int grid = (x.a.m.ncells + tc - 1) / tc;
+  if (tc == 16) {
+    cell_update_mixed_kernel<DIM, K, 16><<<grid, 16 * NV, CT::smem(16), s>>>(x);
+  } else if (tc == 32) {
+    if constexpr (CT::TC_MAX >= 32) cell_update_mixed_kernel<DIM, K, 32><<<grid, 32 * NV, CT::smem(32), s>>>(x);
+  } else {
+    if constexpr (CT::TC_MAX >= 64) cell_update_mixed_kernel<DIM, K, 64><<<grid, 64 * NV, CT::smem(64), s>>>(x);
+  }
   return cudaGetLastError();
 }
 
 template <int DIM, int K>
 cudaError_t prepare_mixed() {
-  cudaError_t e = cudaFuncSetAttribute(cell_update_mixed_kernel<DIM, K>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)MixedCellTile<DIM, K>::SMEM);
+  using CT = MixedCellTile<DIM, K>;
+  using FT = MixedFaceTile<DIM, K>;
+  const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e = cudaFuncSetAttribute(cell_update_mixed_kernel<DIM, K, 16>, attr, (int)CT::smem(16));
+  if (e == cudaSuccess && CT::TC_MAX >= 32) {
+    if constexpr (CT::TC_MAX >= 32) e = cudaFuncSetAttribute(cell_update_mixed_kernel<DIM, K, 32>, attr, (int)CT::smem(32));
+  }
+  if (e == cudaSuccess && CT::TC_MAX >= 64) {
+    if constexpr (CT::TC_MAX >= 64) e = cudaFuncSetAttribute(cell_update_mixed_kernel<DIM, K, 64>, attr, (int)CT::smem(64));
+  }
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(face_flux_mixed_kernel<DIM, K>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)MixedFaceTile<DIM, K>::SMEM);
+  if ((e = cudaFuncSetAttribute(face_flux_mixed_kernel<DIM, K, 16>, attr, (int)FT::smem(16))) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(face_flux_mixed_kernel<DIM, K, 32>, attr, (int)FT::smem(32))) != cudaSuccess) return e;
+  return cudaFuncSetAttribute(face_flux_mixed_kernel<DIM, K, 64>, attr, (int)FT::smem(64));
 }
 
 template <int DIM, int K>
 MixedSet make_mixed_set() {
   MixedSet ms;
+  ms.cell_tile = MixedCellTile<DIM, K>::TC;
+  ms.cell_tile_max = MixedCellTile<DIM, K>::TC_MAX;
+  ms.face_tile = MixedFaceTile<DIM, K>::FB;
+  ms.face_tile_max = MixedFaceTile<DIM, K>::FB_MAX;
   ms.face = &launch_face_mixed<DIM, K>;
   ms.cell = &launch_cell_mixed<DIM, K>;
   ms.prepare = &prepare_mixed<DIM, K>;

@@ -284,12 +284,14 @@ __device__ __forceinline__ void face_trace(const Tab1D<real>& T, const real* w, 
 // A variant > 0 marks the coarse side of a hanging face: its points are a
 // half (2D) or quarter (3D) of the cell face.
 
+// Faces per block: FB (default 32) is a template parameter; instantiated for
+// 16, 32 and 64, selected at launch (StageArgs::face_tile).
 template <typename real, int DIM, int K>
 struct FaceTile {
   using S = Shape<DIM, K>;
   static constexpr int FB = 32;
-  static constexpr int THREADS = FB * S::NV;
-  static constexpr size_t SMEM = (size_t)2 * S::NV * S::QF * FB * sizeof(real);
+  static constexpr int FB_MAX = 64;
+  static constexpr size_t smem(int fb) { return (size_t)2 * S::NV * S::QF * fb * sizeof(real); }
 };
 
 template <typename real, int DIM, int K, int DIR>
@@ -309,12 +311,11 @@ __device__ __forceinline__ void trace_side(const StageArgs<real>& a, int cell, i
   }
 }
 
-template <typename real, int DIM, int K>
-__global__ void __launch_bounds__(FaceTile<real, DIM, K>::THREADS)
+template <typename real, int DIM, int K, int FB>
+__global__ void __launch_bounds__(FB * Shape<DIM, K>::NV)
     face_flux_kernel(const StageArgs<real> a) {
   using S = Shape<DIM, K>;
-  using FT = FaceTile<real, DIM, K>;
-  constexpr int FB = FT::FB;
+  constexpr int THREADS = FB * S::NV;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   real* sT = reinterpret_cast<real*>(smem_raw);  // [2 sides][NV][QF][FB]
   const int nf = a.m.nfaces;
@@ -352,7 +353,7 @@ __global__ void __launch_bounds__(FaceTile<real, DIM, K>::THREADS)
   __syncthreads();
   // HLLC at every (face, point) of the block
   const real gamma = real(a.gamma);
-  for (int item = threadIdx.x; item < FB * S::QF; item += FT::THREADS) {
+  for (int item = threadIdx.x; item < FB * S::QF; item += THREADS) {
     const int ff = item % FB, q = item / FB;
     const int f2 = blockIdx.x * FB + ff;
     if (f2 >= nf) continue;
@@ -385,9 +386,11 @@ template <typename real, int DIM, int K>
 struct CellTile {
   using S = Shape<DIM, K>;
   static constexpr size_t PER_CELL = (size_t)(S::NV * S::Q + DIM * S::NV * S::Q) * sizeof(real);
+  // cells per block: TC (the default) is a template parameter, instantiated
+  // for 16, 32 and 64 up to TC_MAX and selected at launch (StageArgs::cell_tile)
   static constexpr int TC = PER_CELL * 32 > 96 * 1024 ? 16 : 32;
-  static constexpr int THREADS = TC * S::NV;
-  static constexpr size_t SMEM = PER_CELL * TC;
+  static constexpr int TC_MAX = PER_CELL * 64 <= 200 * 1024 ? 64 : (PER_CELL * 32 <= 200 * 1024 ? 32 : 16);
+  static constexpr size_t smem(int tc) { return PER_CELL * tc; }
 };
 
 template <typename real, int DIM, int K, int SD>
@@ -415,12 +418,11 @@ __device__ __forceinline__ void surface_from_faces(const StageArgs<real>& a, int
   }
 }
 
-template <typename real, int DIM, int K>
-__global__ void __launch_bounds__(CellTile<real, DIM, K>::THREADS)
+template <typename real, int DIM, int K, int TC>
+__global__ void __launch_bounds__(TC * Shape<DIM, K>::NV)
     cell_update_kernel(const StageArgs<real> a) {
   using S = Shape<DIM, K>;
-  using CT = CellTile<real, DIM, K>;
-  constexpr int TC = CT::TC, NV = S::NV, Q = S::Q, N = S::N;
+  constexpr int NV = S::NV, Q = S::Q, N = S::N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   real* sU = reinterpret_cast<real*>(smem_raw);  // [NV][Q][TC]
   real* sF = sU + NV * Q * TC;                   // [DIM][NV][Q][TC]

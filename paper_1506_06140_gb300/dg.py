@@ -24,7 +24,7 @@ EXPORTS = ["dg_default_options", "dg_create", "dg_destroy", "dg_last_error", "dg
            "dg_rk_step", "dg_advance", "dg_rk_step_adjoint", "dg_limit", "dg_totals",
            "dg_l1_density", "dg_node_weights", "dg_neighbor_table", "dg_cell_levels",
            "dg_status", "dg_profile_begin", "dg_profile_end", "dg_totals_noalloc",
-           "dg_create_batch", "dg_batch_advance", "dg_n_problems"]
+           "dg_create_batch", "dg_batch_advance", "dg_n_problems", "dg_tiles"]
 KERNEL_KINDS = ["face", "cell", "limit", "dt", "other", "adjoint"]
 
 
@@ -37,7 +37,7 @@ class MeshDesc(C.Structure):
 class Options(C.Structure):
     _fields_ = [("rk_order", C.c_int), ("cfl", C.c_double), ("slope_limiter", C.c_int),
                 ("beta", C.c_double), ("Mtilde", C.c_double), ("positivity", C.c_int),
-                ("eps", C.c_double), ("precision", C.c_int)]
+                ("eps", C.c_double), ("precision", C.c_int), ("autotune", C.c_int)]
 
 
 class DGError(RuntimeError):
@@ -127,7 +127,7 @@ class Solver:
     """One DG problem on the current CUDA device (see include/dg.h)."""
 
     def __init__(self, mesh, k, gamma=1.4, rk_order=3, cfl=0.2, limiter="none", beta=1.0,
-                 Mtilde=0.5, positivity=False, eps=1e-10, precision="fp64"):
+                 Mtilde=0.5, positivity=False, eps=1e-10, precision="fp64", autotune=False):
         """mesh: one mesh dict, or a list of them for an ensemble of
         independent problems advanced together (dg_create_batch)."""
         L = load()
@@ -158,6 +158,7 @@ class Solver:
         opt.beta, opt.Mtilde = beta, Mtilde
         opt.positivity, opt.eps = int(bool(positivity)), eps
         opt.precision = PRECISIONS[precision]
+        opt.autotune = int(bool(autotune))
         self.precision = precision
         self.dtype = torch.float64 if precision in ("fp64", "mixed") else torch.float32
         torch.cuda.init()
@@ -297,6 +298,12 @@ class Solver:
         cnt, ms = (C.c_int * n)(), (C.c_double * n)()
         self._check(self._L.dg_profile_end(self._h, cnt, ms, n))
         return {k: (cnt[i], ms[i]) for i, k in enumerate(KERNEL_KINDS)}
+
+    def tiles(self):
+        """(cells per block of the cell kernel, faces per block of the face kernel)"""
+        ct, ft = C.c_int(), C.c_int()
+        self._check(self._L.dg_tiles(self._h, C.byref(ct), C.byref(ft)))
+        return ct.value, ft.value
 
     def status(self):
         s = C.c_int()

@@ -116,3 +116,23 @@ def test_full_ensemble_fp32_subset_vs_oracle():
         inc, ref_inc = W1[:, :, a:b] - Wp, ref - Wp
         rms = np.sqrt(np.mean((inc - ref_inc) ** 2)) / np.sqrt(np.mean(ref_inc ** 2))
         assert rms < 1e-2, (p, n, rms)  # gross errors in the increment (dt, prefactor)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "mixed"])
+def test_autotuned_tiles_change_no_result(precision):
+    """The autotuner only regroups cells and faces into thread blocks: an
+    autotuned handle steps bit-identically to one with the fixed tiles."""
+    from paper_1506_06140_gb300 import dg
+    problems = [(24, 5.0), (40, 3.5), (8, 4.5)]
+    meshes = [vortex_mesh(n) for n, _ in problems]
+    s0 = dg.Solver(meshes, 2, GAMMA, rk_order=3, precision=precision)
+    s1 = dg.Solver(meshes, 2, GAMMA, rk_order=3, precision=precision, autotune=True)
+    ct, ft = s1.tiles()
+    assert ct in (16, 32, 64) and ft in (16, 32, 64)
+    assert s0.tiles() == (32, 32)
+    W0 = s0.project(torch.as_tensor(batch_state(s0, problems)))
+    W1 = W0.clone()
+    s0.advance(W0, 3)
+    s1.advance(W1, 3)
+    torch.cuda.synchronize()
+    assert torch.equal(W0, W1)
