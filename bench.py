@@ -52,7 +52,7 @@ WORKLOADS = {
              "(10 coeffs/cell/var), SSP-RK3, characteristic TVB limiter + positivity limiter, "
              "FP32 state with FP64 totals / positivity check",
         dim=3, k=2, rk=3, stages=3, limiter="characteristic", positivity=True,
-        precisions=("fp32",), tag="sedov3d_k2"),
+        precisions=("fp32",), tag="sedov3d_k2", autotune=True),
 }
 
 

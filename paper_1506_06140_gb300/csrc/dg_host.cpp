@@ -801,6 +801,7 @@ int run_limit(dg_handle* h, const void* src, void* dst, cudaStream_t s) {
   LimitArgs<real> la;
   la.m = h->md;
   la.tab64 = h->tab64;
+  la.tabr = static_cast<const real*>(h->tab);
   la.Uin = static_cast<const real*>(src);
   la.Uout = static_cast<real*>(dst);
   la.gamma = h->gamma;

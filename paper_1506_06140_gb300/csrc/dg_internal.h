@@ -137,6 +137,7 @@ template <typename real>
 struct LimitArgs {
   MeshDev m;
   const double* tab64 = nullptr;  // FP64 tables (same layout)
+  const real* tabr = nullptr;     // the same tables in the state precision
   const real* Uin = nullptr;
   real* Uout = nullptr;
   double gamma = 1.4;

@@ -233,7 +233,7 @@ __device__ __forceinline__ double cell_dx(const MeshDev& m, int c) {
 
 template <typename real, int DIM, int K>
 __device__ __forceinline__ void nb_mean(const LimitArgs<real>& a, int c, int dir, int s,
-                                        const double* own, double* out) {
+                                        const real* own, real* out) {
   using S = Shape<DIM, K>;
   const int nc = a.m.ncells;
   const int nb = a.m.nbr[(size_t)(2 * dir + s) * nc + c];
@@ -242,12 +242,12 @@ __device__ __forceinline__ void nb_mean(const LimitArgs<real>& a, int c, int dir
   } else if (nb <= -2) {
     const int* kids = a.m.node_children + (size_t)(-(nb + 2)) * S::NCH;
     for (int v = 0; v < S::NV; ++v) {
-      double sum = 0.0;
-      for (int ch = 0; ch < S::NCH; ++ch) sum += (double)a.Uin[(size_t)(v * S::N) * nc + kids[ch]];
-      out[v] = sum / S::NCH;
+      real sum = real(0);
+      for (int ch = 0; ch < S::NCH; ++ch) sum += a.Uin[(size_t)(v * S::N) * nc + kids[ch]];
+      out[v] = sum / real(S::NCH);
     }
   } else if (a.m.level[nb] == a.m.level[c]) {
-    for (int v = 0; v < S::NV; ++v) out[v] = (double)a.Uin[(size_t)(v * S::N) * nc + nb];
+    for (int v = 0; v < S::NV; ++v) out[v] = a.Uin[(size_t)(v * S::N) * nc + nb];
   } else {
     // coarser neighbour: mean of its polynomial over the same-size region
     int ch = 0;
@@ -261,17 +261,18 @@ __device__ __forceinline__ void nb_mean(const LimitArgs<real>& a, int c, int dir
     }
     const double* row = a.tab64 + S::OFF_PREF + (size_t)(ch * S::N + 0) * S::N;
     for (int v = 0; v < S::NV; ++v) {
-      double sum = 0.0;
-      for (int l = 0; l < S::N; ++l) sum += row[l] * (double)a.Uin[(size_t)(v * S::N + l) * nc + nb];
+      real sum = real(0);
+      for (int l = 0; l < S::N; ++l) sum += real(row[l]) * a.Uin[(size_t)(v * S::N + l) * nc + nb];
       out[v] = sum;
     }
   }
 }
 
-__device__ __forceinline__ double minmod3(double a, double b, double c) {
-  if (a > 0.0 && b > 0.0 && c > 0.0) return fmin(a, fmin(b, c));
-  if (a < 0.0 && b < 0.0 && c < 0.0) return fmax(a, fmax(b, c));
-  return 0.0;
+template <typename T>
+__device__ __forceinline__ T minmod3(T a, T b, T c) {
+  if (a > T(0) && b > T(0) && c > T(0)) return rmin(a, rmin(b, c));
+  if (a < T(0) && b < T(0) && c < T(0)) return rmax(a, rmax(b, c));
+  return T(0);
 }
 
 // Root tau in [0,1] of p(ubar + tau (u - ubar)) = eps: multiplying by the
@@ -313,89 +314,154 @@ __device__ double positivity_tau(const double* ub, const double* u, double gamma
   return fmin(fmax(tau, 0.0), 1.0);
 }
 
+// characteristic (or component-wise) slopes of direction A, limited, in the
+// state's precision: ct = minmodB(sqrt(3) L w_(1+A), beta L (ubar - u_minus),
+// beta L (u_plus - ubar)) / sqrt(3)
+template <typename real, int DIM, int K, int A>
+__device__ __forceinline__ bool limit_direction(const LimitArgs<real>& a, int c, const CharState<real, DIM>& st,
+                                                const real (&w)[DIM + 2][Shape<DIM, K>::N],
+                                                const real* mean, real dx, real* ct) {
+  constexpr int NV = DIM + 2;
+  real mm[NV], mp[NV], x[NV], cs[NV], dm[NV], dp[NV];
+  nb_mean<real, DIM, K>(a, c, A, 0, mean, mm);
+  nb_mean<real, DIM, K>(a, c, A, 1, mean, mp);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) x[v] = w[v][1 + A];
+  if (a.limiter == 2) {
+    char_L<real, DIM, A>(st, x, cs);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) x[v] = mean[v] - mm[v];
+    char_L<real, DIM, A>(st, x, dm);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) x[v] = mp[v] - mean[v];
+    char_L<real, DIM, A>(st, x, dp);
+  } else {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      cs[v] = x[v];
+      dm[v] = mean[v] - mm[v];
+      dp[v] = mp[v] - mean[v];
+    }
+  }
+  const real s3 = real(1.7320508075688772);  // sqrt(3)
+  const real beta = real(a.beta), mdx = real(a.Mtilde) * dx;
+  bool changed = false;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    const real arg = s3 * cs[i];
+    const real lim = (fabs(arg) <= mdx) ? arg : minmod3<real>(arg, beta * dm[i], beta * dp[i]);
+    changed = changed || (lim != arg);
+    ct[i] = lim / s3;
+  }
+  return changed;
+}
+
+template <typename real, int DIM, int K, int A>
+__device__ __forceinline__ void unlimit_direction(const LimitArgs<real>& a, const CharState<real, DIM>& st,
+                                                  const real* ct, real (&w)[DIM + 2][Shape<DIM, K>::N]) {
+  constexpr int NV = DIM + 2;
+  real x[NV];
+  if (a.limiter == 2) {
+    char_R<real, DIM, A>(st, ct, x);
+  } else {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) x[v] = ct[v];
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v) w[v][1 + A] = x[v];
+}
+
+// One thread per cell.  The slope limiter runs in the state's precision;
+// the positivity limiter (its shortcut bound, the density and pressure
+// checks and tau) in FP64.
 template <typename real, int DIM, int K>
 __global__ void __launch_bounds__(128) limit_kernel(const LimitArgs<real> a) {
   using S = Shape<DIM, K>;
+  constexpr int NV = S::NV, N = S::N;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int nc = a.m.ncells;
   if (c >= nc) return;
-  double w[S::NV][S::N];
-  for (int v = 0; v < S::NV; ++v)
-    for (int l = 0; l < S::N; ++l) w[v][l] = (double)a.Uin[(size_t)(v * S::N + l) * nc + c];
-  double mean[S::NV];
-  for (int v = 0; v < S::NV; ++v) mean[v] = w[v][0];
+  real w[NV][N];
+#pragma unroll
+  for (int v = 0; v < NV; ++v)
+#pragma unroll
+    for (int l = 0; l < N; ++l) w[v][l] = a.Uin[(size_t)(v * N + l) * nc + c];
+  real mean[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) mean[v] = w[v][0];
   {
-    double m2 = 0.0;
+    real m2 = real(0);
+#pragma unroll
     for (int b = 0; b < DIM; ++b) m2 += mean[1 + b] * mean[1 + b];
-    const double pm = (a.gamma - 1.0) * (mean[DIM + 1] - 0.5 * m2 / mean[0]);
-    if (!(mean[0] > 0.0) || !(pm > 0.0)) atomicOr(a.status, 1 << DG_ERR_NONPHYSICAL_BIT);
+    const real pm = real(a.gamma - 1.0) * (mean[DIM + 1] - real(0.5) * m2 / mean[0]);
+    if (!(mean[0] > real(0)) || !(pm > real(0))) atomicOr(a.status, 1 << DG_ERR_NONPHYSICAL_BIT);
   }
   const double* tab = a.tab64;
-  const double dx = cell_dx(a.m, c);
-  if (a.limiter != 0 && K > 0) {
-    const double s3 = sqrt(3.0);
-    bool changed = false;
-    double ct[DIM][S::NV];
-    for (int d = 0; d < DIM; ++d) {
-      double L[S::NV * S::NV], R[S::NV * S::NV];
-      if (a.limiter == 2) {
-        char_matrices<DIM>(mean, d, a.gamma, L, R);
-      } else {
-        for (int i = 0; i < S::NV * S::NV; ++i) L[i] = 0.0;
-        for (int i = 0; i < S::NV; ++i) L[i * S::NV + i] = 1.0;
+  if constexpr (K > 0) {
+    if (a.limiter != 0) {
+      const real dx = (real)cell_dx(a.m, c);
+      const CharState<real, DIM> st =
+          a.limiter == 2 ? char_state<real, DIM>(mean, real(a.gamma)) : CharState<real, DIM>{};
+      real ct[DIM][NV];
+      bool changed = limit_direction<real, DIM, K, 0>(a, c, st, w, mean, dx, ct[0]);
+      changed = limit_direction<real, DIM, K, 1>(a, c, st, w, mean, dx, ct[1]) || changed;
+      if constexpr (DIM == 3) changed = limit_direction<real, DIM, K, DIM - 1>(a, c, st, w, mean, dx, ct[DIM - 1]) || changed;
+      if (changed) {
+        unlimit_direction<real, DIM, K, 0>(a, st, ct[0], w);
+        unlimit_direction<real, DIM, K, 1>(a, st, ct[1], w);
+        if constexpr (DIM == 3) unlimit_direction<real, DIM, K, DIM - 1>(a, st, ct[DIM - 1], w);
+        // the degree of phi_l is >= 2 exactly for l > DIM (total-degree order)
+#pragma unroll
+        for (int l = DIM + 1; l < N; ++l)
+#pragma unroll
+          for (int v = 0; v < NV; ++v) w[v][l] = real(0);
       }
-      double mm[S::NV], mp[S::NV];
-      nb_mean<real, DIM, K>(a, c, d, 0, mean, mm);
-      nb_mean<real, DIM, K>(a, c, d, 1, mean, mp);
-      for (int i = 0; i < S::NV; ++i) {
-        double cs = 0.0, dm = 0.0, dp = 0.0;
-        for (int v = 0; v < S::NV; ++v) {
-          const double Lv = L[i * S::NV + v];
-          cs += Lv * w[v][1 + d];
-          dm += Lv * (mean[v] - mm[v]);
-          dp += Lv * (mp[v] - mean[v]);
-        }
-        const double arg = s3 * cs;
-        const double lim = (fabs(arg) <= a.Mtilde * dx) ? arg : minmod3(arg, a.beta * dm, a.beta * dp);
-        if (lim != arg) changed = true;
-        ct[d][i] = lim / s3;
-      }
-    }
-    if (changed) {
-      for (int d = 0; d < DIM; ++d) {
-        double L[S::NV * S::NV], R[S::NV * S::NV];
-        if (a.limiter == 2) {
-          char_matrices<DIM>(mean, d, a.gamma, L, R);
-        } else {
-          for (int i = 0; i < S::NV * S::NV; ++i) R[i] = 0.0;
-          for (int i = 0; i < S::NV; ++i) R[i * S::NV + i] = 1.0;
-        }
-        for (int v = 0; v < S::NV; ++v) {
-          double s = 0.0;
-          for (int i = 0; i < S::NV; ++i) s += R[v * S::NV + i] * ct[d][i];
-          w[v][1 + d] = s;
-        }
-      }
-      for (int l = 0; l < S::N; ++l)
-        if (tab[S::OFF_DEG + l] >= 2.0)
-          for (int v = 0; v < S::NV; ++v) w[v][l] = 0.0;
     }
   }
   bool need_positivity = a.positivity && K > 0;
+  if constexpr (sizeof(real) == 4) {
+    // FP32 state: the bound below evaluated in FP32 with margins that cover
+    // its rounding (sums of <= 20 terms: relative error < 2e-6); a cell that
+    // passes needs no FP64 work at all
+    if (need_positivity) {
+      float lo[NV], up[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        float r = 0.0f;
+#pragma unroll
+        for (int l = 1; l < N; ++l) r += fabsf(w[v][l]) * a.tabr[S::OFF_PMAX + l];
+        r *= 1.0f + 1e-5f;
+        lo[v] = w[v][0] - r - 1e-6f * fabsf(w[v][0]);
+        up[v] = (fabsf(w[v][0]) + r) * (1.0f + 1e-5f);
+      }
+      const float feps = (float)a.eps;
+      if (lo[0] >= 2.0f * feps) {
+        float m2 = 0.0f;
+#pragma unroll
+        for (int b = 0; b < DIM; ++b) m2 += up[1 + b] * up[1 + b];
+        const float kin = 0.5f * m2 / lo[0];
+        const float p_low = (float)(a.gamma - 1.0) * (lo[DIM + 1] - kin);
+        if (p_low >= 2.0f * feps + 1e-5f * (fabsf(lo[DIM + 1]) + kin)) need_positivity = false;
+      }
+    }
+  }
   if (need_positivity) {
     // Exact shortcut: |phi_l| <= prod sqrt(2e+1) on [-1,1]^d, so
     //   rho(x) >= rho_bar - sum_{l>=1} |w_rho,l| phi_max_l  and
     //   p(x) >= (gamma-1) (E_low - |m|_up^2 / (2 rho_low)).
     // When both lower bounds reach eps at every point, theta_1 = theta_2 = 1.
-    double lo[S::NV], up[S::NV];
-    for (int v = 0; v < S::NV; ++v) {
+    double lo[NV], up[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
       double r = 0.0;
-      for (int l = 1; l < S::N; ++l) r += fabs(w[v][l]) * tab[S::OFF_PMAX + l];
-      lo[v] = w[v][0] - r;
-      up[v] = fabs(w[v][0]) + r;
+#pragma unroll
+      for (int l = 1; l < N; ++l) r += fabs((double)w[v][l]) * tab[S::OFF_PMAX + l];
+      lo[v] = (double)w[v][0] - r;
+      up[v] = fabs((double)w[v][0]) + r;
     }
     if (lo[0] >= a.eps) {
       double m2 = 0.0;
+#pragma unroll
       for (int b = 0; b < DIM; ++b) m2 += up[1 + b] * up[1 + b];
       const double p_low = (a.gamma - 1.0) * (lo[DIM + 1] - 0.5 * m2 / lo[0]);
       if (p_low >= a.eps) need_positivity = false;
@@ -403,13 +469,16 @@ __global__ void __launch_bounds__(128) limit_kernel(const LimitArgs<real> a) {
   }
   if (need_positivity) {
     const double eps = a.eps;
+    double mean64[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) mean64[v] = (double)mean[v];
     // points: the union set S, plus fine sub-face points on sides with a finer neighbour
     unsigned finer = 0;
     for (int sd = 0; sd < S::NSIDE; ++sd)
       if (a.m.nbr[(size_t)sd * nc + c] <= -2) finer |= 1u << sd;
     const int npts = S::NSP + __popc(finer) * S::NSUB * S::QF;
     auto point_row = [&](int i) -> const double* {
-      if (i < S::NSP) return tab + S::OFF_SPHI + (size_t)i * S::N;
+      if (i < S::NSP) return tab + S::OFF_SPHI + (size_t)i * N;
       int r = i - S::NSP;
       int sd = 0;
       for (; sd < S::NSIDE; ++sd) {
@@ -418,40 +487,50 @@ __global__ void __launch_bounds__(128) limit_kernel(const LimitArgs<real> a) {
         r -= S::NSUB * S::QF;
       }
       const int var = 1 + r / S::QF, q = r % S::QF;
-      return tab + S::OFF_PHIF + (size_t)((sd * S::NVAR + var) * S::QF + q) * S::N;
+      return tab + S::OFF_PHIF + (size_t)((sd * S::NVAR + var) * S::QF + q) * N;
     };
     double rmin = 1e300;
     for (int i = 0; i < npts; ++i) {
       const double* ph = point_row(i);
       double rho = 0.0;
-      for (int l = 0; l < S::N; ++l) rho += w[0][l] * ph[l];
+#pragma unroll
+      for (int l = 0; l < N; ++l) rho += (double)w[0][l] * ph[l];
       rmin = fmin(rmin, rho);
     }
     if (rmin < eps) {
-      const double th1 = fmin(fabs((mean[0] - eps) / (mean[0] - rmin)), 1.0);
-      for (int l = 1; l < S::N; ++l) w[0][l] *= th1;
+      const double th1 = fmin(fabs((mean64[0] - eps) / (mean64[0] - rmin)), 1.0);
+#pragma unroll
+      for (int l = 1; l < N; ++l) w[0][l] = (real)((double)w[0][l] * th1);
     }
     double th2 = 1.0;
     for (int i = 0; i < npts; ++i) {
       const double* ph = point_row(i);
-      double u[S::NV];
-      for (int v = 0; v < S::NV; ++v) {
+      double u[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
         double s = 0.0;
-        for (int l = 0; l < S::N; ++l) s += w[v][l] * ph[l];
+#pragma unroll
+        for (int l = 0; l < N; ++l) s += (double)w[v][l] * ph[l];
         u[v] = s;
       }
       double m2 = 0.0;
+#pragma unroll
       for (int b = 0; b < DIM; ++b) m2 += u[1 + b] * u[1 + b];
       const double pr = (a.gamma - 1.0) * (u[DIM + 1] - 0.5 * m2 / u[0]);
       if (pr >= eps) continue;
-      th2 = fmin(th2, positivity_tau<DIM>(mean, u, a.gamma, eps));
+      th2 = fmin(th2, positivity_tau<DIM>(mean64, u, a.gamma, eps));
     }
-    if (th2 < 1.0)
-      for (int v = 0; v < S::NV; ++v)
-        for (int l = 1; l < S::N; ++l) w[v][l] *= th2;
+    if (th2 < 1.0) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v)
+#pragma unroll
+        for (int l = 1; l < N; ++l) w[v][l] = (real)((double)w[v][l] * th2);
+    }
   }
-  for (int v = 0; v < S::NV; ++v)
-    for (int l = 0; l < S::N; ++l) a.Uout[(size_t)(v * S::N + l) * nc + c] = (real)w[v][l];
+#pragma unroll
+  for (int v = 0; v < NV; ++v)
+#pragma unroll
+    for (int l = 0; l < N; ++l) a.Uout[(size_t)(v * N + l) * nc + c] = w[v][l];
 }
 
 // ===========================================================================
