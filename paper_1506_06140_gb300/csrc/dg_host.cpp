@@ -407,6 +407,8 @@ struct dg_handle {
   float* Gm = nullptr;       // DG_MIXED face fluxes minus the minus cell's reference flux
   float* Dm = nullptr;       // DG_MIXED reference flux differences per face
   bool delta = false;        // DG_MIXED with FP32 delta registers (unlimited programs)
+  float* Wf = nullptr;       // delta mode: FP32 split of W within a step [NV][N][ncells]
+  float* Wlo = nullptr;      //             and the rest of weight 0 [NV][ncells]
   int cell_tile = 0, face_tile = 0;  // stage-kernel tiles (0: the kernels' defaults)
   void* tcB = nullptr;       // its B operands
   double* scal = nullptr;    // dt per problem [nprob]
@@ -753,6 +755,9 @@ int stage_launch(dg_handle* h, const StageArgs<real>& a, cudaStream_t s, const O
         x.ckf = (float)op->ck[0];
         if (op->out[0] == 0) x.a.out[0] = static_cast<double*>(W);
         else x.outR = freg(op->out[0]);
+        x.Wf = h->Wf;
+        x.Wlo = h->Wlo;
+        x.wf_mode = op->in_reg == 0 ? 1 : 2;
       }
       DG_CUDA(h, timed(h, DG_KERNEL_FACE, s, [&] { return h->ms->face(&x, s); }));
       DG_CUDA(h, timed(h, DG_KERNEL_CELL, s, [&] { return h->ms->cell(&x, s); }));
@@ -1222,6 +1227,13 @@ static int create_impl(const dg_mesh_desc* mesh, int nprob, int k, double gamma,
       double sum = 0.0;
       for (int r = 0; r < op.n_in; ++r) sum += op.C[0][r];
       if (op.n_out != 1 || op.lim_src >= 0 || std::fabs(sum - 1.0) > 1e-12) h->delta = false;
+    }
+    if (h->delta) {
+      if ((r = dalloc(h, (size_t)h->nv * h->N * std::max(h->ncells, 1) * sizeof(float), &p)) != DG_OK)
+        return bail(r);
+      h->Wf = static_cast<float*>(p);
+      if ((r = dalloc(h, (size_t)h->nv * std::max(h->ncells, 1) * sizeof(float), &p)) != DG_OK) return bail(r);
+      h->Wlo = static_cast<float*>(p);
     }
     if ((r = dalloc(h, (size_t)h->nv * ks->QF * nf * sizeof(float), &p)) != DG_OK) return bail(r);
     h->Gm = static_cast<float*>(p);

@@ -131,6 +131,12 @@ struct MixedArgs {
   float Cf[MAX_IN] = {};             // their coefficients
   float ckf = 0.0f;                  // coefficient of dt dW/dt
   float* outR = nullptr;             // output delta; nullptr: W += increment (a.out[0] = W)
+  // FP32 split of W within a step: Wf = W rounded (weight 0 truncated) and
+  // Wlo = the rest of weight 0.  wf_mode 1: the cell kernel writes them (first
+  // stage); 2: both kernels read them instead of W; 0: unused.
+  int wf_mode = 0;
+  float* Wf = nullptr;               // [NV][N][ncells]
+  float* Wlo = nullptr;              // [NV][ncells]
 };
 
 template <typename real>

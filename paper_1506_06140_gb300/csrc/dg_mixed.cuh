@@ -78,10 +78,8 @@ __device__ __forceinline__ float two_sum(float a, float b, float& err) {
 
 // mean (weight 0) of one variable of a cell as reference + residual: the
 // state is W (+ R, the FP32 delta of a stage register, when R is given)
-__device__ __forceinline__ void mixed_mean(double w0, const float* R, size_t idx, float& ub,
-                                           float& res) {
-  float hi, lo;
-  df_split(w0, hi, lo);
+__device__ __forceinline__ void mixed_mean_split(float hi, float lo, const float* R, size_t idx,
+                                                 float& ub, float& res) {
   if (R) {
     float e;
     ub = two_sum(hi, R[idx], e);
@@ -89,6 +87,35 @@ __device__ __forceinline__ void mixed_mean(double w0, const float* R, size_t idx
   } else {
     ub = hi;
     res = lo;
+  }
+}
+
+__device__ __forceinline__ void mixed_mean(double w0, const float* R, size_t idx, float& ub,
+                                           float& res) {
+  float hi, lo;
+  df_split(w0, hi, lo);
+  mixed_mean_split(hi, lo, R, idx, ub, res);
+}
+
+// FP32 weights l >= 1 of one variable of a cell (W, or W + R) and its mean
+// as reference + residual: from the FP64 state, or (wf_mode 2) from the FP32
+// split of W that the step's first cell kernel wrote
+template <int N>
+__device__ __forceinline__ void mixed_weights(const MixedArgs& x, size_t i0, int v, int c, size_t nc,
+                                              float* w, float& ub, float& res) {
+  if (x.wf_mode == 2) {
+    mixed_mean_split(x.Wf[i0], x.Wlo[(size_t)v * nc + c], x.R, i0, ub, res);
+#pragma unroll
+    for (int l = 1; l < N; ++l) w[l] = x.Wf[i0 + (size_t)l * nc];
+  } else {
+    const double* Wc = x.a.U + i0;
+    mixed_mean(Wc[0], x.R, i0, ub, res);
+#pragma unroll
+    for (int l = 1; l < N; ++l) w[l] = f32_round(Wc[(size_t)l * nc]);
+  }
+  if (x.R) {
+#pragma unroll
+    for (int l = 1; l < N; ++l) w[l] += x.R[i0 + (size_t)l * nc];
   }
 }
 
@@ -100,16 +127,9 @@ __device__ __forceinline__ void mixed_trace(const MixedArgs& x, int cell, int s,
   using S = Shape<DIM, K>;
   const int nc = x.a.m.ncells;
   const size_t i0 = (size_t)v * S::N * nc + cell;
-  const double* Wc = x.a.U + i0;
   float w[S::N];
-  mixed_mean(Wc[0], x.R, i0, ubar, res);
+  mixed_weights<S::N>(x, i0, v, cell, nc, w, ubar, res);
   w[0] = 0.0f;
-#pragma unroll
-  for (int l = 1; l < S::N; ++l) w[l] = f32_round(Wc[(size_t)l * nc]);
-  if (x.R) {
-#pragma unroll
-    for (int l = 1; l < S::N; ++l) w[l] += x.R[i0 + (size_t)l * nc];
-  }
   if (var == 0) {
     face_trace<float, DIM, K, DIR>(x.t, w, s, x.t.P, x.t.P, du);
   } else {
@@ -286,13 +306,17 @@ __global__ void __launch_bounds__(TC * Shape<DIM, K>::NV)
 #pragma unroll
     for (int l = 1; l < N; ++l) w[l] = 0.0f;
     if (valid) {
-      mixed_mean(a.U[i0], x.R, i0, ub, res);
+      if (x.wf_mode == 1) {
+        // first stage of a step: keep the FP32 split of W for the later stages
+        float hi, lo;
+        df_split(a.U[i0], hi, lo);
+        x.Wf[i0] = hi;
+        x.Wlo[(size_t)v * nc + c] = lo;
 #pragma unroll
-      for (int l = 1; l < N; ++l) w[l] = f32_round(a.U[i0 + (size_t)l * nc]);
-      if (x.R) {
-#pragma unroll
-        for (int l = 1; l < N; ++l) w[l] += x.R[i0 + (size_t)l * nc];
+        for (int l = 1; l < N; ++l) x.Wf[i0 + (size_t)l * nc] = f32_round(a.U[i0 + (size_t)l * nc]);
       }
+      mixed_weights<N>(x, i0, v, c, nc, w, ub, res);
+      w[0] = 0.0f;
     }
     modal_to_nodal<float, DIM, K>(x.t, w, u);
     sRef[v * TC + tc] = ub;
