@@ -47,6 +47,12 @@ WORKLOADS = {
              "per-problem CFL timestep, FP32, all steps in one CUDA-graph launch",
         dim=2, k=2, rk=3, stages=3, limiter="none", positivity=False, precisions=("fp32",),
         tag="ensemble512_k2", graph=True, autotune=True),
+    "wave2d": dict(
+        name="advected density wave 2D, 32x32 periodic [0,1]^2, k=1 (3 coeffs/cell/var), SSP-RK2, "
+             "CFL 0.3, FP64; all timed steps in one CUDA-graph launch (launch-bound: time per stage "
+             "of the graph replay)",
+        dim=2, k=1, rk=2, stages=2, limiter="none", positivity=False, precisions=("fp64",),
+        tag="wave2d32_k1", graph=True, cfl=0.3),
     "sedov3d": dict(
         name="Sedov blast 3D, 64^3 base + central 32^3 refined once (491,520 cells), k=2 "
              "(10 coeffs/cell/var), SSP-RK3, characteristic TVB limiter + positivity limiter, "
@@ -60,6 +66,8 @@ def workload_config(wk, precision, cells):
     W = WORKLOADS[wk]
     l2 = ("state larger than L2 (no flush); timed steps in one graph launch" if W.get("graph")
           else "flushed between timed steps (256 MiB write)")
+    if wk == "wave2d":
+        l2 = "L2-resident 98 KB state (launch-bound workload); timed steps in one graph launch"
     return {"workload": W["name"], "cells": cells, "k": W["k"], "rk_stages": W["stages"],
             "precision": precision, "l2": l2}
 
@@ -77,6 +85,8 @@ def make_problem(wk, precision, autotune=None):
     W = WORKLOADS[wk]
     if wk == "vortex":
         m, ic = mesh(), wl.vortex
+    elif wk == "wave2d":
+        m, ic = wl.mesh_uniform(2, [32, 32], [0.0, 0.0], [1.0, 1.0]), wl.wave2d
     elif wk == "ensemble":
         probs = wl.ensemble_problems()
         m = [wl.mesh_uniform(2, [n, n], [-5.0, -5.0], [5.0, 5.0]) for n, _ in probs]
@@ -85,7 +95,7 @@ def make_problem(wk, precision, autotune=None):
         m, ic = wl.mesh_two_level_3d(64, 16, 47), wl.sedov3d
     if autotune is None:
         autotune = W.get("autotune", False)
-    s = dg.Solver(m, W["k"], 1.4, rk_order=W["rk"], cfl=CFL, limiter=W["limiter"],
+    s = dg.Solver(m, W["k"], 1.4, rk_order=W["rk"], cfl=W.get("cfl", CFL), limiter=W["limiter"],
                   positivity=W["positivity"], precision=precision, autotune=autotune)
     xyz = s.quad_points().cpu().numpy()
     if ic is not None:
@@ -308,6 +318,9 @@ def run_gpu(args, rank, world, local_rank):
             else:
                 for _ in range(args.warmup):
                     s.rk_step(W)
+                limited = WORKLOADS[args.workload]["limiter"] != "none"
+                if limited:
+                    s.limiter_counts(reset=True)
                 torch.cuda.synchronize()
                 barrier()
                 s.profile_begin()
@@ -328,6 +341,18 @@ def run_gpu(args, rank, world, local_rank):
         ms = sum(a.elapsed_time(b) for a, b in ev)
         ms = max_over_ranks(ms)
         assert torch.isfinite(W).all().item(), "non-finite state"
+        diag = None
+        if WORKLOADS[args.workload]["limiter"] != "none":
+            # limiter activity over the timed steps and conservation drift from the initial state
+            cnt = s.limiter_counts(reset=True).cpu().numpy()
+            passes = s.n_cells * WORKLOADS[args.workload]["stages"] * args.steps
+            t0, t1 = s.totals(W0).cpu().numpy(), s.totals(W).cpu().numpy()
+            diag = {"slope_limited_fraction": float(cnt[0]) / passes,
+                    "positivity_limited_fraction": float(cnt[1]) / passes,
+                    "steps_since_initial_state": args.warmup + args.steps,
+                    "mass_drift_rel": float(abs(t1[0] - t0[0]) / abs(t0[0])),
+                    "energy_drift_rel": float(abs(t1[-1] - t0[-1]) / abs(t0[-1])),
+                    "momentum_abs": [float(x) for x in t1[1:-1]]}
         # end to end through the C ABI with host buffers
         Wh = W0.cpu().pin_memory()
         Wd = torch.empty_like(W0)
@@ -360,7 +385,7 @@ def run_gpu(args, rank, world, local_rank):
             del sf, Wf
         results[precision] = dict(solver=s, ms=ms, ms_e2e=ms_e2e, prof=prof, clocks=clk.summary(),
                                   state_bytes=W.numel() * W.element_size(), n_cells=s.n_cells,
-                                  tiles=tiles)
+                                  tiles=tiles, diag=diag)
         del W, W0, Wd, Wh
     return results
 
@@ -421,6 +446,8 @@ def summarize(args, results, world):
             "kernel_ms": {kk: v[1] for kk, v in prof.items()},
             "cells": cells,
         }
+        if r.get("diag"):
+            lines[precision]["diagnostics"] = r["diag"]
         if r.get("tiles"):
             t = dict(r["tiles"])
             t["fixed_tile_value"] = dof_updates / (t.pop("fixed_tile_ms") * 1e-3)
@@ -628,6 +655,8 @@ def main():
         if "tiles" in one:
             out["config"]["tiles"] = one["tiles"]
         out.update({kk: one[kk] for kk in ("roofline", "e2e", "gpu_launches", "clocks", "kernel_ms")})
+        if "diagnostics" in one:
+            out["diagnostics"] = one["diagnostics"]
         print(json.dumps(out), flush=True)
         return 0
     head = lines["fp64"]

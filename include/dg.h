@@ -119,6 +119,14 @@ int dg_destroy(dg_handle* h);
 /* Last error message of a handle (or of the last failed dg_create if h is NULL). */
 const char* dg_last_error(const dg_handle* h);
 
+/* Limiter activity since the handle was created or last reset: counts_dev[0]
+ * = cell passes in which the slope limiter (Secs. 3.2-3.3) changed the
+ * slopes, counts_dev[1] = cell passes in which the positivity limiter (Sec.
+ * 3.4) scaled the weights.  counts_dev: device memory, two int64 values,
+ * written asynchronously on the stream; reset != 0 zeroes the counters after
+ * the copy. */
+int dg_limiter_counts(dg_handle* h, int64_t* counts_dev, int reset, void* stream);
+
 /* Tiles of the stage kernels in use: cells per thread block of the cell
  * kernel and faces per block of the face kernel (the fixed defaults, or the
  * autotuner's choice when dg_options.autotune was set).  A tensor-core cell

@@ -407,6 +407,7 @@ struct dg_handle {
   float* Gm = nullptr;       // DG_MIXED face fluxes minus the minus cell's reference flux
   float* Dm = nullptr;       // DG_MIXED reference flux differences per face
   bool delta = false;        // DG_MIXED with FP32 delta registers (unlimited programs)
+  unsigned long long* lim_counts = nullptr;  // [2] cells changed by the slope / positivity limiter
   float* Wf = nullptr;       // delta mode: FP32 split of W within a step [NV][N][ncells]
   float* Wlo = nullptr;      //             and the rest of weight 0 [NV][ncells]
   int cell_tile = 0, face_tile = 0;  // stage-kernel tiles (0: the kernels' defaults)
@@ -815,6 +816,7 @@ int run_limit(dg_handle* h, const void* src, void* dst, cudaStream_t s) {
   la.Mtilde = h->opt.Mtilde;
   la.positivity = h->opt.positivity;
   la.eps = h->opt.eps;
+  la.counts = h->lim_counts;
   la.status = h->status;
   DG_CUDA(h, timed(h, DG_KERNEL_LIMIT, s, [&] { return h->ks->limit(&la, s); }));
   return DG_OK;
@@ -1208,6 +1210,10 @@ static int create_impl(const dg_mesh_desc* mesh, int nprob, int k, double gamma,
   h->partial = static_cast<double*>(p);
   if ((r = dalloc(h, sizeof(int), &p)) != DG_OK) return bail(r);
   h->status = static_cast<int*>(p);
+  if ((r = dalloc(h, 2 * sizeof(unsigned long long), &p)) != DG_OK) return bail(r);
+  h->lim_counts = static_cast<unsigned long long*>(p);
+  if (cudaMemset(h->lim_counts, 0, 2 * sizeof(unsigned long long)) != cudaSuccess)
+    return bail(cuda_fail(h, cudaGetLastError(), "cudaMemset"));
   if (cudaMemset(h->status, 0, sizeof(int)) != cudaSuccess)
     return bail(cuda_fail(h, cudaGetLastError(), "cudaMemset"));
   if (ks->prepare() != cudaSuccess) return bail(cuda_fail(h, cudaGetLastError(), "kernel attributes"));
@@ -1346,6 +1352,15 @@ int dg_project(dg_handle* h, const double* u_dev, void* W_dev, void* stream) {
     a.Wout = static_cast<float*>(W_dev);
     DG_CUDA(h, h->ks->project(&a, s));
   }
+  return DG_OK;
+}
+
+int dg_limiter_counts(dg_handle* h, int64_t* counts_dev, int reset, void* stream) {
+  if (!check_handle(h) || !counts_dev) return DG_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DG_CUDA(h, cudaMemcpyAsync(counts_dev, h->lim_counts, 2 * sizeof(unsigned long long),
+                             cudaMemcpyDeviceToDevice, s));
+  if (reset) DG_CUDA(h, cudaMemsetAsync(h->lim_counts, 0, 2 * sizeof(unsigned long long), s));
   return DG_OK;
 }
 

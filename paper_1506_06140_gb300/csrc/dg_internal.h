@@ -151,6 +151,7 @@ struct LimitArgs {
   double beta = 1.0, Mtilde = 0.5;
   int positivity = 0;
   double eps = 1e-10;
+  unsigned long long* counts = nullptr;  // [2] cells changed by the slope / positivity limiter
   int* status = nullptr;
 };
 

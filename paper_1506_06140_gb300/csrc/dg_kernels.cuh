@@ -407,6 +407,7 @@ __global__ void __launch_bounds__(128) limit_kernel(const LimitArgs<real> a) {
       changed = limit_direction<real, DIM, K, 1>(a, c, st, w, mean, dx, ct[1]) || changed;
       if constexpr (DIM == 3) changed = limit_direction<real, DIM, K, DIM - 1>(a, c, st, w, mean, dx, ct[DIM - 1]) || changed;
       if (changed) {
+        if (a.counts) atomicAdd(a.counts, 1ull);
         unlimit_direction<real, DIM, K, 0>(a, st, ct[0], w);
         unlimit_direction<real, DIM, K, 1>(a, st, ct[1], w);
         if constexpr (DIM == 3) unlimit_direction<real, DIM, K, DIM - 1>(a, st, ct[DIM - 1], w);
@@ -520,6 +521,7 @@ __global__ void __launch_bounds__(128) limit_kernel(const LimitArgs<real> a) {
       if (pr >= eps) continue;
       th2 = fmin(th2, positivity_tau<DIM>(mean64, u, a.gamma, eps));
     }
+    if ((rmin < eps || th2 < 1.0) && a.counts) atomicAdd(a.counts + 1, 1ull);
     if (th2 < 1.0) {
 #pragma unroll
       for (int v = 0; v < NV; ++v)

@@ -24,7 +24,8 @@ EXPORTS = ["dg_default_options", "dg_create", "dg_destroy", "dg_last_error", "dg
            "dg_rk_step", "dg_advance", "dg_rk_step_adjoint", "dg_limit", "dg_totals",
            "dg_l1_density", "dg_node_weights", "dg_neighbor_table", "dg_cell_levels",
            "dg_status", "dg_profile_begin", "dg_profile_end", "dg_totals_noalloc",
-           "dg_create_batch", "dg_batch_advance", "dg_n_problems", "dg_tiles"]
+           "dg_create_batch", "dg_batch_advance", "dg_n_problems", "dg_tiles",
+           "dg_limiter_counts"]
 KERNEL_KINDS = ["face", "cell", "limit", "dt", "other", "adjoint"]
 
 
@@ -298,6 +299,12 @@ class Solver:
         cnt, ms = (C.c_int * n)(), (C.c_double * n)()
         self._check(self._L.dg_profile_end(self._h, cnt, ms, n))
         return {k: (cnt[i], ms[i]) for i, k in enumerate(KERNEL_KINDS)}
+
+    def limiter_counts(self, reset=False, out=None):
+        """device int64[2]: cell passes changed by the slope / positivity limiter"""
+        out = torch.zeros(2, dtype=torch.int64, device=self.device) if out is None else out
+        self._check(self._L.dg_limiter_counts(self._h, _ptr(out), int(bool(reset)), _stream()))
+        return out
 
     def tiles(self):
         """(cells per block of the cell kernel, faces per block of the face kernel)"""

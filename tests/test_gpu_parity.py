@@ -183,6 +183,29 @@ def test_limiters_fp64(lim, name):
     assert np.any(ref != W)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_limiter_counts_match_changed_cells(precision):
+    """dg_limiter_counts: the slope-limiter count equals the number of cells
+    whose slopes the oracle's limiter changes (positivity off); reset zeroes."""
+    m = MESHES["amr2"]
+    o = oracle_for(m, 2, limiter=O.LIM_CHARACTERISTIC)
+    s = solver_for(m, 2, limiter="characteristic", precision=precision)
+    W = o.project(wl.wave2d(o.quad_points(), amp=0.1))
+    rng = np.random.default_rng(510)
+    rough = rng.random(o.n_cells) < 0.2
+    W[:, 1:, rough] *= 30.0
+    ref = o.limit(W)
+    changed = int(np.sum(np.any(ref != W, axis=(0, 1))))
+    assert 0 < changed < o.n_cells
+    s.limit(to_dev(s, W))
+    cnt = s.limiter_counts(reset=True).cpu().numpy()
+    if precision == "fp64":
+        assert cnt[0] == changed and cnt[1] == 0
+    else:  # FP32 decisions may differ on a cell whose slope sits at the minmod threshold
+        assert abs(int(cnt[0]) - changed) <= max(1, changed // 100) and cnt[1] == 0
+    assert list(s.limiter_counts().cpu().numpy()) == [0, 0]
+
+
 def test_positivity_only_fp64():
     m = MESHES["amr2"]
     o = oracle_for(m, 2, positivity=True)
