@@ -40,7 +40,7 @@ WORKLOADS = {
         name="isentropic vortex 2D, 256x256 periodic [-5,5]^2, k=3 (10 coeffs/cell/var), "
              "SSP-RK4 (5 stages), no limiter, CFL 0.2",
         dim=2, k=3, rk=4, stages=5, limiter="none", positivity=False,
-        precisions=("fp64", "fp32", "fp32_tc", "mixed"), tag="vortex256_k3"),
+        precisions=("fp64", "fp32", "fp32_tc", "mixed", "mixed_tc"), tag="vortex256_k3"),
     "ensemble": dict(
         name="512 independent isentropic vortices (strength U(3,6)) on periodic [-5,5]^2 with "
              "sizes drawn from {32,48,64,96,128}^2 (3.4M cells), k=2 (6 coeffs/cell/var), SSP-RK3, "
@@ -406,13 +406,15 @@ def summarize(args, results, world):
         kind = max(prof, key=lambda kk: prof[kk][1])
         n_launch, kms = prof[kind]
         avg_s = kms / max(n_launch, 1) * 1e-3
-        esize = 8 if precision in ("fp64", "mixed") else 4
+        esize = 8 if precision in ("fp64", "mixed", "mixed_tc") else 4
         kname = {"cell": "cell_update_kernel", "face": "face_flux_kernel",
                  "limit": "limit_kernel"}.get(kind, kind)
         if precision == "fp32_tc" and kind == "cell":
             kname = "cell_update_tc_kernel"
-        if precision == "mixed" and kind in ("cell", "face"):
+        if precision in ("mixed", "mixed_tc") and kind in ("cell", "face"):
             kname = kind == "cell" and "cell_update_mixed_kernel" or "face_flux_mixed_kernel"
+            if precision == "mixed_tc" and kind == "cell":
+                kname = "cell_update_tc_mixed_kernel"
         tag = "%s_%s" % (wk["tag"], precision)
         if precision == "fp64" and kind in ("cell", "face"):
             fc, ff = kernel_flops(dim, k)
@@ -428,7 +430,7 @@ def summarize(args, results, world):
             # HBM: a launch of the dominant kernel processes one stage of the mesh,
             # whose algorithmic traffic is 3 state arrays (read U_i and w^n, write U_i+1)
             byt = 3 * state_bytes_per_cell(dim, k, esize) * cells
-            if precision == "mixed":
+            if precision in ("mixed", "mixed_tc"):
                 # FP64 state read, FP32 delta registers read and written
                 byt = (state_bytes_per_cell(dim, k, 8) + 2 * state_bytes_per_cell(dim, k, 4)) * cells
             achieved = byt / avg_s / 1e9
@@ -436,7 +438,7 @@ def summarize(args, results, world):
                     "unit": "GB/s", "frac": achieved / hbm, "peak_source": peak_kind,
                     "traffic": dram_traffic(kname, tag), "algorithmic_per_launch": byt,
                     "algorithmic_unit": "bytes (FP64 state + 2 FP32 delta registers per stage)"
-                    if precision == "mixed" else "bytes (3 state arrays per stage)"}
+                    if precision in ("mixed", "mixed_tc") else "bytes (3 state arrays per stage)"}
         e2e_value = dof_updates / (r["ms_e2e"] * 1e-3)
         lines[precision] = {
             "value": value, "ms_per_step": r["ms"] / args.steps, "roofline": roof,
@@ -526,7 +528,8 @@ def run_l1_study(args):
     torch.cuda.set_device(0)
     t_end = args.t_end
     rows = []
-    precisions = ("fp64", "fp32", "fp32_tc", "mixed") if args.precision == "both" else (args.precision,)
+    precisions = (("fp64", "fp32", "fp32_tc", "mixed", "mixed_tc") if args.precision == "both"
+                  else (args.precision,))
     for precision in precisions:
         for n in (32, 64, 128, 256):
             s = dg.Solver(mesh(n), K_DEG, 1.4, rk_order=RK_ORDER, cfl=CFL, precision=precision)
@@ -618,7 +621,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precision", default="both", choices=["both", "fp64", "fp32", "fp32_tc", "mixed"],
+    ap.add_argument("--precision", default="both",
+                    choices=["both", "fp64", "fp32", "fp32_tc", "mixed", "mixed_tc"],
                     help="run one precision only (profiling); the JSON line needs both")
     ap.add_argument("--workload", default="vortex",
                     choices=sorted(WORKLOADS) + ["adjoint3d", "l1study"])
@@ -650,7 +654,8 @@ def main():
         out = {"metric": METRIC, "value": one["value"], "unit": UNIT, "n_gpus": world,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": one["ms_per_step"],
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-               "dtype": {"fp64": "f64", "mixed": "f32/f64"}.get(prec, "f32"), "data": "synthetic",
+               "dtype": {"fp64": "f64", "mixed": "f32/f64", "mixed_tc": "f32/f64"}.get(prec, "f32"),
+               "data": "synthetic",
                "config": workload_config(args.workload, prec, one["cells"])}
         if "tiles" in one:
             out["config"]["tiles"] = one["tiles"]
@@ -668,7 +673,8 @@ def main():
            "clocks": head["clocks"], "kernel_ms": head["kernel_ms"],
            "variants": {p: {k: lines[p][k] for k in
                             ("value", "ms_per_step", "roofline", "e2e", "gpu_launches",
-                             "clocks", "kernel_ms")} for p in ("fp32", "fp32_tc", "mixed") if p in lines}}
+                             "clocks", "kernel_ms")} for p in ("fp32", "fp32_tc", "mixed", "mixed_tc")
+                         if p in lines}}
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()
     print(json.dumps(out), flush=True)

@@ -61,8 +61,11 @@ enum { DG_LIMITER_NONE = 0, DG_LIMITER_COMPONENT = 1, DG_LIMITER_CHARACTERISTIC 
  *             the point and face fluxes it integrates, which leaves the
  *             discrete right-hand side unchanged and makes the FP32 rounding
  *             scale with the solution's variation rather than its size.  The
- *             CFL timestep, limiters, totals and the adjoint run in FP64. */
-enum { DG_FP64 = 0, DG_FP32 = 1, DG_FP32_TC = 2, DG_MIXED = 3 };
+ *             CFL timestep, limiters, totals and the adjoint run in FP64.
+ * DG_MIXED_TC: DG_MIXED with the cell kernel's two contractions on the
+ *             tensor cores (split TF32, FP32 accumulation); 2D uniform meshes,
+ *             k = 1..3. */
+enum { DG_FP64 = 0, DG_FP32 = 1, DG_FP32_TC = 2, DG_MIXED = 3, DG_MIXED_TC = 4 };
 
 /* Mesh description (paper Secs. 2.2 and 4): cubical cells on the box
  * [lo, hi]; n[a] base cells along axis a (the base edge length must be equal

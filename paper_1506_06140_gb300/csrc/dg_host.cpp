@@ -742,6 +742,7 @@ int stage_launch(dg_handle* h, const StageArgs<real>& a, cudaStream_t s, const O
       x.t = h->tab1d32;
       x.G = h->Gm;
       x.D = h->Dm;
+      x.tcB = static_cast<const float*>(h->tcB);
       if (op && h->delta) {
         auto freg = [&](int r) { return static_cast<float*>(h->regs[r - 1]); };
         x.delta = 1;
@@ -761,7 +762,8 @@ int stage_launch(dg_handle* h, const StageArgs<real>& a, cudaStream_t s, const O
         x.wf_mode = op->in_reg == 0 ? 1 : 2;
       }
       DG_CUDA(h, timed(h, DG_KERNEL_FACE, s, [&] { return h->ms->face(&x, s); }));
-      DG_CUDA(h, timed(h, DG_KERNEL_CELL, s, [&] { return h->ms->cell(&x, s); }));
+      DG_CUDA(h, timed(h, DG_KERNEL_CELL, s,
+                       [&] { return h->use_tc ? h->ms->cell_tc(&x, s) : h->ms->cell(&x, s); }));
       return DG_OK;
     }
   }
@@ -1107,10 +1109,10 @@ static int create_impl(const dg_mesh_desc* mesh, int nprob, int k, double gamma,
   if (o.rk_order < 1 || o.rk_order > 4) return fail(nullptr, DG_ERR_ARG, "dg_create: rk_order must be 1..4");
   if (o.slope_limiter < 0 || o.slope_limiter > 2) return fail(nullptr, DG_ERR_ARG, "dg_create: bad slope_limiter");
   if (o.precision != DG_FP64 && o.precision != DG_FP32 && o.precision != DG_FP32_TC &&
-      o.precision != DG_MIXED)
+      o.precision != DG_MIXED && o.precision != DG_MIXED_TC)
     return fail(nullptr, DG_ERR_ARG, "dg_create: bad precision");
-  const bool use_tc = o.precision == DG_FP32_TC;
-  const bool mixed = o.precision == DG_MIXED;
+  const bool use_tc = o.precision == DG_FP32_TC || o.precision == DG_MIXED_TC;
+  const bool mixed = o.precision == DG_MIXED || o.precision == DG_MIXED_TC;
   if (use_tc) o.precision = DG_FP32;
   if (mixed) o.precision = DG_FP64;  // FP64 state; FP32 stage kernels below
   if (!(o.cfl > 0.0)) return fail(nullptr, DG_ERR_ARG, "dg_create: cfl must be positive");
@@ -1247,13 +1249,16 @@ static int create_impl(const dg_mesh_desc* mesh, int nprob, int k, double gamma,
     h->Dm = static_cast<float*>(p);
   }
   if (h->use_tc) {
-    if (!ks->cell_tc || h->nnodes > 0)
+    auto cell_tc = h->ms ? h->ms->cell_tc : ks->cell_tc;
+    auto prepare_tc = h->ms ? h->ms->prepare_tc : ks->prepare_tc;
+    auto fill_tc = h->ms ? h->ms->fill_tc : ks->fill_tc;
+    if (!cell_tc || h->nnodes > 0)
       return bail(fail(h, DG_ERR_UNSUPPORTED,
-                       "dg_create: DG_FP32_TC needs a uniform 2D mesh and k = 1..3"));
-    if (ks->prepare_tc() != cudaSuccess)
+                       "dg_create: tensor-core precisions need a uniform 2D mesh and k = 1..3"));
+    if (prepare_tc() != cudaSuccess)
       return bail(cuda_fail(h, cudaGetLastError(), "kernel attributes"));
     std::vector<float> B;
-    ks->fill_tc(T, B);
+    fill_tc(T, B);
     if ((r = dalloc(h, B.size() * sizeof(float), &p)) != DG_OK) return bail(r);
     h->tcB = p;
     if (cudaMemcpy(p, B.data(), B.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)

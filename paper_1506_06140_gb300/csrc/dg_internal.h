@@ -137,6 +137,7 @@ struct MixedArgs {
   int wf_mode = 0;
   float* Wf = nullptr;               // [NV][N][ncells]
   float* Wlo = nullptr;              // [NV][ncells]
+  const float* tcB = nullptr;        // tensor-core B operands (DG_MIXED_TC)
 };
 
 template <typename real>
@@ -239,6 +240,10 @@ struct MixedSet {
   cudaError_t (*face)(const void* mixed_args, cudaStream_t s) = nullptr;
   cudaError_t (*cell)(const void* mixed_args, cudaStream_t s) = nullptr;
   cudaError_t (*prepare)() = nullptr;
+  // tensor-core cell kernel (2D, k = 1..3), nullptr where not built
+  cudaError_t (*cell_tc)(const void* mixed_args, cudaStream_t s) = nullptr;
+  cudaError_t (*prepare_tc)() = nullptr;
+  void (*fill_tc)(const std::vector<double>& tab, std::vector<float>& out) = nullptr;
 };
 
 const MixedSet* mixed_set(int dim, int k);

@@ -18,6 +18,9 @@
 
 #include <cstdint>
 
+#include <cstring>
+#include <vector>
+
 #include "dg_internal.h"
 #include "dg_physics.cuh"
 

@@ -17,7 +17,7 @@ DG_OK, DG_ERR_ARG, DG_ERR_CUDA, DG_ERR_OOM, DG_ERR_NONPHYSICAL, DG_ERR_TIMEOUT, 
     DG_ERR_UNSUPPORTED = range(7)
 DG_BC_PERIODIC, DG_BC_TRANSMISSIVE = 0, 1
 LIMITERS = {"none": 0, "component": 1, "characteristic": 2}
-PRECISIONS = {"fp64": 0, "fp32": 1, "fp32_tc": 2, "mixed": 3}
+PRECISIONS = {"fp64": 0, "fp32": 1, "fp32_tc": 2, "mixed": 3, "mixed_tc": 4}
 
 EXPORTS = ["dg_default_options", "dg_create", "dg_destroy", "dg_last_error", "dg_sizes",
            "dg_quad_points", "dg_l1_points", "dg_project", "dg_rhs", "dg_compute_dt",
@@ -161,7 +161,7 @@ class Solver:
         opt.precision = PRECISIONS[precision]
         opt.autotune = int(bool(autotune))
         self.precision = precision
-        self.dtype = torch.float64 if precision in ("fp64", "mixed") else torch.float32
+        self.dtype = torch.float64 if precision in ("fp64", "mixed", "mixed_tc") else torch.float32
         torch.cuda.init()
         h = C.c_void_p()
         if self.batch:

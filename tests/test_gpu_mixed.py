@@ -197,3 +197,68 @@ def test_mixed_adjoint_close_to_fp64():
     b = s64.rk_step_adjoint(W, dt, lam).cpu().numpy()
     e, _ = rel_err(a - lam.cpu().numpy(), b - lam.cpu().numpy())
     assert e < 1e-4, e
+
+
+# ---------------------------------------------------------------------------
+# DG_MIXED_TC: the same scheme with the cell kernel's contractions on the
+# tensor cores (split TF32 products, FP32 accumulation)
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_rhs_mixed_tc_random_states(k):
+    for name in ("u2", "u2t"):
+        m = MESHES[name]
+        o = oracle_for(m, k)
+        s = solver_for(m, k, precision="mixed_tc")
+        W = wl.random_weights(2, o.N, o.n_cells, seed=1700 + k)
+        ref = o.rhs(W)
+        e, erms = rel_err(s.rhs(dev(W)).cpu().numpy(), ref)
+        assert e < TOL32_MAX and erms < TOL32_RMS, (name, k, e, erms)
+        assert s.status() == 0
+
+
+def test_rhs_mixed_tc_smooth_vortex_full_size():
+    m = wl.mesh_uniform(2, [256, 256], [-5.0, -5.0], [5.0, 5.0])
+    o = oracle_for(m, 3)
+    W = o.project(wl.vortex(o.quad_points()))
+    ref = o.rhs(W)
+    s = solver_for(m, 3, precision="mixed_tc")
+    e, erms = rel_err(s.rhs(dev(W)).cpu().numpy(), ref)
+    print("mixed_tc max %.3e rms %.3e" % (e, erms))
+    assert e < 1e-5 and erms < 3e-7, (e, erms)
+
+
+@pytest.mark.parametrize("order", [3, 4])
+def test_rk_step_mixed_tc_matches_mixed(order):
+    """Delta-register steps: the tensor-core and SIMT mixed kernels agree to
+    the FP32 rounding of the right-hand side."""
+    m = MESHES["u2"]
+    k = order - 1
+    o = oracle_for(m, k, rk_order=order)
+    W = o.project(wl.wave2d(o.quad_points(), amp=0.1))
+    dt = 0.5 * o.compute_dt(W)
+    ref, _ = o.rk_step(W, dt)
+    for prec in ("mixed", "mixed_tc"):
+        s = solver_for(m, k, rk_order=order, precision=prec)
+        Wd = dev(W)
+        s.rk_step(Wd, dt)
+        got = Wd.cpu().numpy()
+        e, _ = rel_err(got - W, ref - W)
+        assert e < 1e-4, (prec, e)
+        assert s.status() == 0
+
+
+def test_mixed_tc_advance_graph_and_rejections():
+    from paper_1506_06140_gb300 import dg
+    m = wl.mesh_uniform(2, [150, 131], [0.0, 0.0], [1.5, 1.31])  # ragged last tile, many tiles
+    s = solver_for(m, 3, rk_order=4, precision="mixed_tc")
+    W = dev(wl.random_weights(2, s.N, s.n_cells, seed=1800))
+    W2 = W.clone()
+    s.advance(W, 3)
+    for _ in range(3):
+        s.rk_step(W2)
+    torch.cuda.synchronize()
+    assert torch.equal(W, W2)
+    with pytest.raises(dg.DGError):
+        solver_for(MESHES["amr2"], 2, precision="mixed_tc")
+    with pytest.raises(dg.DGError):
+        solver_for(MESHES["u3"], 2, precision="mixed_tc")
