@@ -451,13 +451,12 @@ __global__ void __launch_bounds__(TC * Shape<DIM, K>::NV)
     real u[NV];
 #pragma unroll
     for (int vv = 0; vv < NV; ++vv) u[vv] = sU[(vv * Q + q) * TC + tc];
+    real f[DIM][NV];
+    euler_flux_all<real, DIM>(u, g1, f);
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-      real f[NV];
-      euler_flux<real, DIM>(u, d, g1, f);
+    for (int d = 0; d < DIM; ++d)
 #pragma unroll
-      for (int vv = 0; vv < NV; ++vv) sF[((d * NV + vv) * Q + q) * TC + tc] = f[vv];
-    }
+      for (int vv = 0; vv < NV; ++vv) sF[((d * NV + vv) * Q + q) * TC + tc] = f[d][vv];
   }
   __syncthreads();
   if (!valid) return;
@@ -493,14 +492,13 @@ __global__ void __launch_bounds__(TC * Shape<DIM, K>::NV)
   // 4. epilogue
   const int pb = cell_problem(a.m, c);
   const real pre = a.pre_prob ? a.pre_prob[pb] : a.pre[a.m.level[c]];
-  const real dtv = a.dt ? real(a.dt[pb]) : real(1);
+  const real sc = pre * (a.dt ? real(a.dt[pb]) : real(1));
   const int n_out = a.n_out, n_in = a.n_in;
 #pragma unroll
   for (int j = 0; j < N; ++j) {
-    const real rhs = pre * acc[j];
     const size_t idx = (size_t)(v * N + j) * nc + c;
     for (int oo = 0; oo < n_out; ++oo) {
-      real val = a.ck[oo] * dtv * rhs;
+      real val = (a.ck[oo] * sc) * acc[j];
       for (int r = 0; r < n_in; ++r) {
         const real cr = a.C[oo][r];
         if (cr == real(0)) continue;
