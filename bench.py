@@ -499,7 +499,7 @@ def run_adjoint(args):
     dJ = (grad * v).sum().item()
     res = {}
     with torch.no_grad():
-        for rel in (1e-4, 1e-5):
+        for rel in (1e-4, 3e-5, 1e-5):
             eps = rel * W0.abs().max().item()
             fd = (J(W0 + eps * v).item() - J(W0 - eps * v).item()) / (2 * eps)
             res["%g" % rel] = abs(fd - dJ) / abs(dJ)

@@ -9,8 +9,8 @@
 //   faces  : Fbar(q) = w_q (pre_p t_p(q) - pre_m t_m(q)), t = trace of G,
 //            ubar_-/+ = (dF/du_-/+)^T Fbar,     Ubar_l += sum_q ubar(q) phi_l(q)
 // (the coarse side of a hanging face carries its sub-face weight 2^-(d-1)).
-// The Jacobian-transpose products are formed with forward-mode dual numbers
-// running the same flux code as the forward kernels.
+// The Jacobian-transpose products of the point flux and of HLLC are
+// reverse-mode derivatives of the same formulas, written out by hand.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -20,96 +20,232 @@
 
 namespace dgi {
 
-// value and one directional derivative
-template <typename T>
-struct Dual {
-  T v, d;
-  __device__ __forceinline__ Dual() : v(T(0)), d(T(0)) {}
-  __device__ __forceinline__ Dual(double x) : v(T(x)), d(T(0)) {}
-  __device__ __forceinline__ Dual(T x, T dx, int) : v(x), d(dx) {}
-  // found by argument-dependent lookup only, so it does not hide ::sqrt
-  friend __device__ __forceinline__ Dual sqrt(const Dual& a) {
-    const T s = ::sqrt(a.v);
-    return Dual(s, a.d / (T(2) * s), 0);
-  }
-};
-template <typename T>
-__device__ __forceinline__ Dual<T> operator+(const Dual<T>& a, const Dual<T>& b) {
-  return Dual<T>(a.v + b.v, a.d + b.d, 0);
-}
-template <typename T>
-__device__ __forceinline__ Dual<T> operator-(const Dual<T>& a, const Dual<T>& b) {
-  return Dual<T>(a.v - b.v, a.d - b.d, 0);
-}
-template <typename T>
-__device__ __forceinline__ Dual<T> operator-(const Dual<T>& a) {
-  return Dual<T>(-a.v, -a.d, 0);
-}
-template <typename T>
-__device__ __forceinline__ Dual<T> operator*(const Dual<T>& a, const Dual<T>& b) {
-  return Dual<T>(a.v * b.v, a.d * b.v + a.v * b.d, 0);
-}
-template <typename T>
-__device__ __forceinline__ Dual<T> operator/(const Dual<T>& a, const Dual<T>& b) {
-  const T q = a.v / b.v;
-  return Dual<T>(q, (a.d - q * b.d) / b.v, 0);
-}
-template <typename T>
-__device__ __forceinline__ Dual<T>& operator+=(Dual<T>& a, const Dual<T>& b) {
-  a = a + b;
-  return a;
-}
-template <typename T>
-__device__ __forceinline__ bool operator<(const Dual<T>& a, const Dual<T>& b) { return a.v < b.v; }
-template <typename T>
-__device__ __forceinline__ bool operator>(const Dual<T>& a, const Dual<T>& b) { return a.v > b.v; }
-template <typename T>
-__device__ __forceinline__ bool operator>=(const Dual<T>& a, const Dual<T>& b) { return a.v >= b.v; }
-template <typename T>
-__device__ __forceinline__ bool operator==(const Dual<T>& a, const Dual<T>& b) { return a.v == b.v; }
+// Jacobian-transpose products of the fluxes by reverse-mode differentiation
+// written out by hand: the forward formulas of euler_flux / hllc_flux are
+// evaluated once, then their adjoints are accumulated in reverse order.
 
-// (dF/du)^T fbar for the HLLC flux, with respect to the minus (L) or plus side
-template <typename real, int DIM, int DIR, bool LEFT>
-__device__ __forceinline__ void hllc_vjp(const real* uL, const real* uR, real gamma,
-                                         const real* fbar, real* out) {
-  constexpr int NV = DIM + 2;
-  using D = Dual<real>;
-#pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    D dl[NV], dr[NV], F[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      dl[v] = D(uL[v], (LEFT && v == k) ? real(1) : real(0), 0);
-      dr[v] = D(uR[v], (!LEFT && v == k) ? real(1) : real(0), 0);
-    }
-    hllc_flux<D, DIM>(dl, dr, DIR, D(double(gamma)), F);
-    real s = real(0);
-#pragma unroll
-    for (int v = 0; v < NV; ++v) s += fbar[v] * F[v].d;
-    out[k] = s;
-  }
-}
-
-// sum_d (df_d/du)^T g_d at one point
+// out = sum_d (df_d/du)^T g_d at one point (f_d the Euler flux of eqs.
+// flux_vectors and eos)
 template <typename real, int DIM>
 __device__ __forceinline__ void flux_vjp(const real* u, const real (*g)[DIM + 2], real g1,
                                          real* out) {
-  constexpr int NV = DIM + 2;
-  using D = Dual<real>;
+  constexpr int E = DIM + 1;
+  const real rinv = real(1) / u[0];
+  real v[DIM], m2 = real(0);
 #pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    D du[NV];
+  for (int b = 0; b < DIM; ++b) {
+    v[b] = u[1 + b] * rinv;
+    m2 += u[1 + b] * v[b];
+  }
+  const real p = g1 * (u[E] - real(0.5) * m2);
+  const real H = u[E] + p;
+  // forward, per direction a: f0 = m_a, f_(1+b) = m_b v_a + delta_ab p, f_E = H v_a
+  real mb[DIM], vb[DIM];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) du[v] = D(u[v], v == k ? real(1) : real(0), 0);
+  for (int b = 0; b < DIM; ++b) { mb[b] = real(0); vb[b] = real(0); }
+  real pb = real(0), Eb = real(0);
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    const real* ga = g[a];
+    mb[a] += ga[0];
     real s = real(0);
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-      D f[NV];
-      euler_flux<D, DIM>(du, d, D(double(g1)), f);
-#pragma unroll
-      for (int v = 0; v < NV; ++v) s += g[d][v] * f[v].d;
+    for (int b = 0; b < DIM; ++b) {
+      mb[b] += ga[1 + b] * v[a];
+      s += ga[1 + b] * u[1 + b];
     }
-    out[k] = s;
+    vb[a] += s + ga[E] * H;
+    pb += ga[1 + a] + ga[E] * v[a];
+    Eb += ga[E] * v[a];
+  }
+  // p = g1 (E - m2 / 2), m2 = sum_b m_b v_b, v_b = m_b / rho
+  Eb += g1 * pb;
+  const real m2b = real(-0.5) * g1 * pb;
+  real rinvb = real(0);
+#pragma unroll
+  for (int b = 0; b < DIM; ++b) {
+    mb[b] += m2b * v[b];
+    vb[b] += m2b * u[1 + b];
+    mb[b] += vb[b] * rinv;
+    rinvb += vb[b] * u[1 + b];
+  }
+  out[0] = -rinvb * rinv * rinv;
+#pragma unroll
+  for (int b = 0; b < DIM; ++b) out[1 + b] = mb[b];
+  out[E] = Eb;
+}
+
+// outL = (dF/duL)^T fbar, outR = (dF/duR)^T fbar for the HLLC flux in
+// direction A (the construction of hllc_flux, branch by branch)
+template <typename real, int DIM, int A>
+__device__ __forceinline__ void hllc_vjp(const real* uL, const real* uR, real gamma,
+                                         const real* fbar, real* outL, real* outR) {
+  constexpr int NV = DIM + 2, E = DIM + 1;
+  const real g1 = gamma - real(1);
+  // ---- forward
+  const real rL = uL[0], rR = uR[0];
+  const real iL = real(1) / rL, iR = real(1) / rR;
+  real kL = real(0), kR = real(0);
+#pragma unroll
+  for (int b = 0; b < DIM; ++b) {
+    kL += uL[1 + b] * uL[1 + b];
+    kR += uR[1 + b] * uR[1 + b];
+  }
+  const real pL = g1 * (uL[E] - real(0.5) * kL * iL);
+  const real pR = g1 * (uR[E] - real(0.5) * kR * iR);
+  const real vL = uL[1 + A] * iL, vR = uR[1 + A] * iR;
+  const real XL = gamma * pL * iL, XR = gamma * pR * iR;
+  const real cL = sqrt(XL), cR = sqrt(XR);
+  const bool minR = (vR - cR) < (vL - cL);  // S_L from the right state
+  const bool maxR = (vL + cL) < (vR + cR);  // S_R from the right state
+  const real SL = minR ? vR - cR : vL - cL;
+  const real SR = maxR ? vR + cR : vL + cL;
+  const real dL = rL * (SL - vL), dR = rR * (SR - vR);
+  const real num = pR - pL + vL * dL - vR * dR, den = dL - dR;
+  const real Ss = num / den;
+  const bool left = (SL >= real(0)) || (Ss >= real(0));
+  const bool star = left ? (SL < real(0)) : (SR > real(0));
+  const real* u = left ? uL : uR;
+  const real r = left ? rL : rR;
+  const real ir = left ? iL : iR;
+  const real v = left ? vL : vR;
+  const real p = left ? pL : pR;
+  const real S = left ? SL : SR;
+  // ---- reverse: adjoints of the side-K quantities first
+  real ub[NV];  // direct adjoint of u_K
+#pragma unroll
+  for (int i = 0; i < NV; ++i) ub[i] = real(0);
+  real vb = real(0), pb = real(0), irb = real(0), rb = real(0), Sb = real(0), Ssb = real(0);
+  if (star) {
+    const real rsv = r * (S - v);
+    const real Dn = S - Ss;
+    const real fac = rsv / Dn;
+    const real prs = p / rsv;
+    const real Y = u[E] * ir + (Ss - v) * (Ss + prs);
+    real us[NV];
+    us[0] = fac;
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) us[1 + b] = fac * (u[1 + b] * ir);
+    us[1 + A] = fac * Ss;
+    us[E] = fac * Y;
+    // F_i += S (us_i - u_i)
+    real facb = real(0);
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      Sb += fbar[i] * (us[i] - u[i]);
+      ub[i] -= S * fbar[i];
+    }
+    facb += S * fbar[0];
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) {
+      if (b == A) continue;
+      const real usb = S * fbar[1 + b];
+      facb += usb * u[1 + b] * ir;
+      ub[1 + b] += usb * fac * ir;
+      irb += usb * fac * u[1 + b];
+    }
+    {
+      const real usb = S * fbar[1 + A];
+      facb += usb * Ss;
+      Ssb += usb * fac;
+    }
+    {
+      const real usb = S * fbar[E];
+      facb += usb * Y;
+      const real Yb = usb * fac;
+      ub[E] += Yb * ir;
+      irb += Yb * u[E];
+      const real Ab = Yb * (Ss + prs), Bb = Yb * (Ss - v);
+      Ssb += Ab + Bb;
+      vb -= Ab;
+      const real prsb = Bb;
+      pb += prsb / rsv;
+      real rsvb = -prsb * prs / rsv;
+      // fac = rsv / Dn, Dn = S - Ss
+      rsvb += facb / Dn;
+      const real Dnb = -facb * fac / Dn;
+      Sb += Dnb;
+      Ssb -= Dnb;
+      // rsv = r (S - v)
+      rb += rsvb * (S - v);
+      Sb += rsvb * r;
+      vb -= rsvb * r;
+    }
+  }
+  // physical flux of side K: F0 = m_A, F_(1+b) = m_b v + delta_Ab p, F_E = (E + p) v
+  ub[1 + A] += fbar[0];
+#pragma unroll
+  for (int b = 0; b < DIM; ++b) {
+    ub[1 + b] += fbar[1 + b] * v;
+    vb += fbar[1 + b] * u[1 + b];
+  }
+  pb += fbar[1 + A] + fbar[E] * v;
+  ub[E] += fbar[E] * v;
+  vb += fbar[E] * (u[E] + p);
+  // ---- per-side accumulators
+  real bL[NV], bR[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    bL[i] = left ? ub[i] : real(0);
+    bR[i] = left ? real(0) : ub[i];
+  }
+  real vLb = left ? vb : real(0), vRb = left ? real(0) : vb;
+  real pLb = left ? pb : real(0), pRb = left ? real(0) : pb;
+  real iLb = left ? irb : real(0), iRb = left ? real(0) : irb;
+  bL[0] += left ? rb : real(0);
+  bR[0] += left ? real(0) : rb;
+  real SLb = left ? Sb : real(0), SRb = left ? real(0) : Sb;
+  // S* = num / den
+  const real numb = Ssb / den;
+  const real denb = -Ssb * Ss / den;
+  pRb += numb;
+  pLb -= numb;
+  vLb += numb * dL;
+  real dLb = numb * vL + denb;
+  vRb -= numb * dR;
+  real dRb = -numb * vR - denb;
+  // dL = rL (SL - vL), dR = rR (SR - vR)
+  bL[0] += dLb * (SL - vL);
+  SLb += dLb * rL;
+  vLb -= dLb * rL;
+  bR[0] += dRb * (SR - vR);
+  SRb += dRb * rR;
+  vRb -= dRb * rR;
+  // SL = min(vL - cL, vR - cR), SR = max(vL + cL, vR + cR)
+  real cLb = real(0), cRb = real(0);
+  if (minR) { vRb += SLb; cRb -= SLb; } else { vLb += SLb; cLb -= SLb; }
+  if (maxR) { vRb += SRb; cRb += SRb; } else { vLb += SRb; cLb += SRb; }
+  // c = sqrt(gamma p i)
+  {
+    const real XLb = cLb / (real(2) * cL), XRb = cRb / (real(2) * cR);
+    pLb += XLb * gamma * iL;
+    iLb += XLb * gamma * pL;
+    pRb += XRb * gamma * iR;
+    iRb += XRb * gamma * pR;
+  }
+  // v = m_A i
+  bL[1 + A] += vLb * iL;
+  iLb += vLb * uL[1 + A];
+  bR[1 + A] += vRb * iR;
+  iRb += vRb * uR[1 + A];
+  // p = g1 (E - k i / 2), k = |m|^2
+  bL[E] += g1 * pLb;
+  bR[E] += g1 * pRb;
+  const real kLb = real(-0.5) * g1 * pLb * iL, kRb = real(-0.5) * g1 * pRb * iR;
+  iLb += real(-0.5) * g1 * pLb * kL;
+  iRb += real(-0.5) * g1 * pRb * kR;
+#pragma unroll
+  for (int b = 0; b < DIM; ++b) {
+    bL[1 + b] += real(2) * uL[1 + b] * kLb;
+    bR[1 + b] += real(2) * uR[1 + b] * kRb;
+  }
+  // i = 1 / rho
+  bL[0] -= iLb * iL * iL;
+  bR[0] -= iRb * iR * iR;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    outL[i] = bL[i];
+    outR[i] = bR[i];
   }
 }
 
@@ -380,16 +516,9 @@ __global__ void __launch_bounds__(AdjFaceTile<real, DIM, K>::THREADS)
       // dW_minus/dt has -pre F phi w, dW_plus/dt has +pre F phi w
       fb[vv] = wq * (sG[((1 * NV + vv) * QF + q) * FB + ff] - sG[((0 * NV + vv) * QF + q) * FB + ff]);
     }
-    if (d2 == 0) {
-      hllc_vjp<real, DIM, 0, true>(uL, uR, gamma, fb, bl);
-      hllc_vjp<real, DIM, 0, false>(uL, uR, gamma, fb, br);
-    } else if (d2 == 1) {
-      hllc_vjp<real, DIM, 1, true>(uL, uR, gamma, fb, bl);
-      hllc_vjp<real, DIM, 1, false>(uL, uR, gamma, fb, br);
-    } else {
-      hllc_vjp<real, DIM, DIM - 1, true>(uL, uR, gamma, fb, bl);
-      hllc_vjp<real, DIM, DIM - 1, false>(uL, uR, gamma, fb, br);
-    }
+    if (d2 == 0) hllc_vjp<real, DIM, 0>(uL, uR, gamma, fb, bl, br);
+    else if (d2 == 1) hllc_vjp<real, DIM, 1>(uL, uR, gamma, fb, bl, br);
+    else hllc_vjp<real, DIM, DIM - 1>(uL, uR, gamma, fb, bl, br);
     // a mirrored side is the other side's own trace
     if (cm < 0) {
 #pragma unroll
