@@ -393,20 +393,48 @@ struct CellTile {
   static constexpr size_t smem(int tc) { return PER_CELL * tc; }
 };
 
+// Face fluxes of the conforming sides of a cell are loaded at the start of
+// the cell kernel (when they fit in 64 registers) so that their latency
+// overlaps the volume phase; a coarse side's sub-face fluxes load on use.
+template <typename real, int DIM, int K>
+struct FacePrefetch {
+  static constexpr bool ON = 2 * DIM * Shape<DIM, K>::QF * sizeof(real) <= 256;
+};
+
+template <typename real, int DIM, int K>
+__device__ __forceinline__ void prefetch_faces(const StageArgs<real>& a, int c, int v, unsigned coarse,
+                                               real (&fp)[2 * DIM][Shape<DIM, K>::QF]) {
+  using S = Shape<DIM, K>;
+  const int nc = a.m.ncells, nf = a.m.nfaces;
+#pragma unroll
+  for (int sd = 0; sd < 2 * DIM; ++sd) {
+    const bool conf = !((coarse >> sd) & 1);
+    const int e0 = conf ? a.m.sface[(size_t)sd * nc + c] : 0;
+#pragma unroll
+    for (int q = 0; q < S::QF; ++q) fp[sd][q] = conf ? a.F[((size_t)v * S::QF + q) * nf + e0] : real(0);
+  }
+}
+
 template <typename real, int DIM, int K, int SD>
 __device__ __forceinline__ void surface_from_faces(const StageArgs<real>& a, int c, int v,
-                                                   unsigned coarse, real* acc) {
+                                                   unsigned coarse, const real* fpre, real* acc) {
   using S = Shape<DIM, K>;
   constexpr int DIR = SD >> 1, SS = SD & 1;
   const Tab1D<real>& T = a.t1;
   const int nc = a.m.ncells, nf = a.m.nfaces;
-  const int e0 = a.m.sface[(size_t)SD * nc + c];
   real fq[S::QF];
   if (!((coarse >> SD) & 1)) {
+    if (fpre) {
 #pragma unroll
-    for (int q = 0; q < S::QF; ++q) fq[q] = a.F[((size_t)v * S::QF + q) * nf + e0];
+      for (int q = 0; q < S::QF; ++q) fq[q] = fpre[q];
+    } else {
+      const int e0 = a.m.sface[(size_t)SD * nc + c];
+#pragma unroll
+      for (int q = 0; q < S::QF; ++q) fq[q] = a.F[((size_t)v * S::QF + q) * nf + e0];
+    }
     surface_side<real, DIM, K, DIR, SS>(T, T.P, T.P, fq, real(1), acc);
   } else {
+    const int e0 = a.m.sface[(size_t)SD * nc + c];
     // coarse side of a hanging face: NSUB sub-faces in quadrant order
     const real sub = real(1) / real(S::NSUB);
 #pragma unroll
@@ -431,6 +459,12 @@ __global__ void __launch_bounds__(TC * Shape<DIM, K>::NV)
   const int c = blockIdx.x * TC + tc;
   const bool valid = c < nc;
   const Tab1D<real>& T = a.t1;
+  constexpr bool PF = FacePrefetch<real, DIM, K>::ON;
+  const unsigned coarse = valid ? a.m.scoarse[c] : 0u;
+  real fpre[PF ? 2 * DIM : 1][S::QF];
+  if constexpr (PF) {
+    if (valid) prefetch_faces<real, DIM, K>(a, c, v, coarse, fpre);
+  }
 
   // 1. weights of this variable -> nodal values
   real w[N];
@@ -479,14 +513,13 @@ __global__ void __launch_bounds__(TC * Shape<DIM, K>::NV)
       volume_dir<real, DIM, K, DIM - 1>(T, f, acc);
     }
   }
-  const unsigned coarse = a.m.scoarse[c];
-  surface_from_faces<real, DIM, K, 0>(a, c, v, coarse, acc);
-  surface_from_faces<real, DIM, K, 1>(a, c, v, coarse, acc);
-  surface_from_faces<real, DIM, K, 2>(a, c, v, coarse, acc);
-  surface_from_faces<real, DIM, K, 3>(a, c, v, coarse, acc);
+  surface_from_faces<real, DIM, K, 0>(a, c, v, coarse, PF ? fpre[0] : nullptr, acc);
+  surface_from_faces<real, DIM, K, 1>(a, c, v, coarse, PF ? fpre[1] : nullptr, acc);
+  surface_from_faces<real, DIM, K, 2>(a, c, v, coarse, PF ? fpre[2 % (PF ? 2 * DIM : 1)] : nullptr, acc);
+  surface_from_faces<real, DIM, K, 3>(a, c, v, coarse, PF ? fpre[3 % (PF ? 2 * DIM : 1)] : nullptr, acc);
   if constexpr (DIM == 3) {
-    surface_from_faces<real, DIM, K, 2 * DIM - 2>(a, c, v, coarse, acc);
-    surface_from_faces<real, DIM, K, 2 * DIM - 1>(a, c, v, coarse, acc);
+    surface_from_faces<real, DIM, K, 4>(a, c, v, coarse, PF ? fpre[4 % (PF ? 2 * DIM : 1)] : nullptr, acc);
+    surface_from_faces<real, DIM, K, 5>(a, c, v, coarse, PF ? fpre[5 % (PF ? 2 * DIM : 1)] : nullptr, acc);
   }
 
   // 4. epilogue
