@@ -112,7 +112,7 @@ def make_problem(wk, precision, autotune=None):
 
 
 # ---------------------------------------------------------------------------
-# algorithmic work per cell and stage (the formulas of the design doc)
+# algorithmic work per cell and stage (sum-factorised contraction counts)
 
 def shape(dim, k):
     N = (k + 1) * (k + 2) // 2 if dim == 2 else (k + 1) * (k + 2) * (k + 3) // 6
@@ -425,7 +425,7 @@ def summarize(args, results, world):
                     "peak_source": "FP64 rate from unit counts and max clock (152 SMs x 2 DFMA/clk "
                                    "x 2 flop x 2.07 GHz); measured probe 1.198",
                     "traffic": dram_traffic(kname, tag), "algorithmic_per_launch": fl,
-                    "algorithmic_unit": "flop (sum-factorised count, DESIGN.md)"}
+                    "algorithmic_unit": "flop (sum-factorised count of kernel_flops)"}
         else:
             # HBM: a launch of the dominant kernel processes one stage of the mesh,
             # whose algorithmic traffic is 3 state arrays (read U_i and w^n, write U_i+1)

@@ -2,8 +2,9 @@
 
 Bars: integer tables bit-exact; FP64 fields within 1e-11 of the largest
 |value| of the compared quantity (rounding-order differences of sums of
-O(N Q) terms of size ~|f| |dphi| / dx); FP32 fields within the FP32 bar
-derived in the design doc (relative 2e-5 of the largest |value|, RMS 2e-6).
+O(N Q) terms of size ~|f| |dphi| / dx); FP32 fields on random states within
+2e-5 of the largest |value| (RMS 2e-6): FP32 rounding (6e-8) of sums of
+O(N Q) terms whose size exceeds the result by up to ~30x on these states.
 Inputs are seeded synthetic states with the paper's workload shapes.
 """
 import math
