@@ -426,6 +426,12 @@ def summarize(args, results, world):
                                    "x 2 flop x 2.07 GHz); measured probe 1.198",
                     "traffic": dram_traffic(kname, tag), "algorithmic_per_launch": fl,
                     "algorithmic_unit": "flop (sum-factorised count of kernel_flops)"}
+            if kind == "cell":
+                # the same launch against the HBM roof (3 state arrays per stage)
+                byt = 3 * state_bytes_per_cell(dim, k, esize) * cells
+                roof["hbm"] = {"achieved": byt / avg_s / 1e9, "peak": hbm, "unit": "GB/s",
+                               "frac": byt / avg_s / 1e9 / hbm, "peak_source": peak_kind,
+                               "algorithmic_per_launch": byt}
         else:
             # HBM: a launch of the dominant kernel processes one stage of the mesh,
             # whose algorithmic traffic is 3 state arrays (read U_i and w^n, write U_i+1)

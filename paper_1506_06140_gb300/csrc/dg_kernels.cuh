@@ -540,15 +540,23 @@ __global__ void __launch_bounds__(128) limit_kernel(const LimitArgs<real> a) {
 
 constexpr int RED_THREADS = 256;
 
+// Block sum with warp shuffles in a fixed order (deterministic): a
+// shuffle-down tree within each warp, then one over the warps' sums.  The
+// result is valid in thread 0.
 __device__ __forceinline__ double block_sum(double x, double* sh) {
-  // deterministic: fixed pairwise order
-  sh[threadIdx.x] = x;
+  constexpr unsigned full = 0xffffffffu;
+  constexpr int NW = RED_THREADS / 32;
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(full, x, o);
+  if (l == 0) sh[w] = x;
   __syncthreads();
-  for (int s = RED_THREADS / 2; s > 0; s >>= 1) {
-    if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
-    __syncthreads();
+  double r = 0.0;
+  if (w == 0) {
+    r = l < NW ? sh[l] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(full, r, o);
   }
-  const double r = sh[0];
   __syncthreads();
   return r;
 }
@@ -638,13 +646,17 @@ __global__ void __launch_bounds__(RED_THREADS) l1_kernel(const AuxArgs<real> a) 
 }
 
 // partial[nblocks][nv] -> out[nv] (scaled), summed in block order
+// one warp per variable: lane l sums blocks l, l+32, ... in order, then a
+// fixed shuffle tree (deterministic)
 static __global__ void reduce_partials_kernel(const double* partial, int nblocks, int nv, double scale,
                                        double* out) {
-  const int v = threadIdx.x;
+  const int v = blockIdx.x, l = threadIdx.x;
   if (v >= nv) return;
   double s = 0.0;
-  for (int b = 0; b < nblocks; ++b) s += partial[(size_t)b * nv + v];
-  out[v] = s * scale;
+  for (int b = l; b < nblocks; b += 32) s += partial[(size_t)b * nv + v];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (l == 0) out[v] = s * scale;
 }
 
 template <typename real, int DIM, int K>
@@ -812,7 +824,7 @@ cudaError_t launch_totals(const void* pa, cudaStream_t s) {
   using S = Shape<DIM, K>;
   const int nb = (a.m.ncells + RED_THREADS - 1) / RED_THREADS;
   if (nb > 0) totals_kernel<real, DIM, K><<<nb, RED_THREADS, 0, s>>>(a);
-  reduce_partials_kernel<<<1, 32, 0, s>>>(a.partial, nb, S::NV, 1.0, a.out);
+  reduce_partials_kernel<<<S::NV, 32, 0, s>>>(a.partial, nb, S::NV, 1.0, a.out);
   return cudaGetLastError();
 }
 

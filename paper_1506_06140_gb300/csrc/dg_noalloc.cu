@@ -32,15 +32,22 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 double* g_ptr[kMaxDevices] = {};
 
-// Same fixed pairwise order as the handle-based reduction.
+// Same fixed order as the handle-based reduction: a shuffle-down tree within
+// each warp, then one over the warps' sums; valid in thread 0.
 __device__ __forceinline__ double block_sum(double x, double* sh) {
-  sh[threadIdx.x] = x;
+  constexpr unsigned full = 0xffffffffu;
+  constexpr int NW = kThreads / 32;
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(full, x, o);
+  if (l == 0) sh[w] = x;
   __syncthreads();
-  for (int s = kThreads / 2; s > 0; s >>= 1) {
-    if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
-    __syncthreads();
+  double r = 0.0;
+  if (w == 0) {
+    r = l < NW ? sh[l] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(full, r, o);
   }
-  const double r = sh[0];
   __syncthreads();
   return r;
 }
@@ -63,12 +70,15 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
+// one warp per variable, the order of the handle-based final pass
 __global__ void totals_final(const double* partial, int nblocks, int nv, double* out) {
-  const int v = threadIdx.x;
+  const int v = blockIdx.x, l = threadIdx.x;
   if (v >= nv) return;
   double s = 0.0;
-  for (int b = 0; b < nblocks; ++b) s += partial[(size_t)b * nv + v];
-  out[v] = s;
+  for (int b = l; b < nblocks; b += 32) s += partial[(size_t)b * nv + v];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (l == 0) out[v] = s;
 }
 
 // Device address of the scratch array on the current device (set-up once
@@ -112,6 +122,6 @@ extern "C" int dg_totals_noalloc(int dim, int n_basis, int64_t n_cells, int prec
       totals_partials<float><<<nblocks, kThreads, 0, s>>>(static_cast<const float*>(W_dev), nv,
                                                           n_basis, nc, dim, dx0, levels_dev, partial);
   }
-  totals_final<<<1, 32, 0, s>>>(partial, nblocks, nv, totals_dev);
+  totals_final<<<nv, 32, 0, s>>>(partial, nblocks, nv, totals_dev);
   return cudaGetLastError() == cudaSuccess ? DG_OK : DG_ERR_CUDA;
 }
