@@ -97,8 +97,11 @@ typedef struct {
                         check stay FP64 */
   int autotune;      /* 1: dg_create times the stage kernels on the mesh at every
                         feasible tile (16, 32 or 64 cells or faces per thread block) and keeps the
-                        fastest; 0 (default): fixed tiles.  Results do not depend on
-                        the tiles.  See dg_tiles. */
+                        fastest, FP32 2D handles also trying the one-thread-per-
+                        cell kernel; 0 (default): fixed tiles.  The tiled kernels
+                        give identical results for every tile; the one-thread-per-
+                        cell kernel sums in another order (FP32 rounding).  See
+                        dg_tiles. */
 } dg_options;
 
 typedef struct dg_handle dg_handle;
@@ -133,8 +136,17 @@ int dg_limiter_counts(dg_handle* h, int64_t* counts_dev, int reset, void* stream
 /* Tiles of the stage kernels in use: cells per thread block of the cell
  * kernel and faces per block of the face kernel (the fixed defaults, or the
  * autotuner's choice when dg_options.autotune was set).  A tensor-core cell
- * kernel (DG_FP32_TC) reports its fixed 32 cells.  Host outputs. */
+ * kernel (DG_FP32_TC) reports its fixed 32 cells; 1 means the one-thread-per-
+ * cell FP32 kernel, which the autotuner also considers.  Host outputs. */
 int dg_tiles(const dg_handle* h, int* cell_tile, int* face_tile);
+
+/* Sets the tiles by hand (the autotuner's choices can be overridden):
+ * cell_tile 16, 32 or 64 cells per block of the tiled cell kernel, or 1 for
+ * the one-thread-per-cell kernel (FP32 2D handles only); face_tile 16, 32 or
+ * 64.  DG_ERR_ARG for other values,
+ * DG_ERR_UNSUPPORTED where the (dim, k, precision) has no such kernel.  Not
+ * to be called while another call on the handle is being captured. */
+int dg_set_tiles(dg_handle* h, int cell_tile, int face_tile);
 
 /* Sizes: cells, basis functions N(k) (eq. nof_basis_functions and its 2D
  * analogue), variables nv, volume Gauss points per cell (k+1)^dim, points of

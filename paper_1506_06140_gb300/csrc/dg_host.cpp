@@ -411,6 +411,8 @@ struct dg_handle {
   float* Wf = nullptr;       // delta mode: FP32 split of W within a step [NV][N][ncells]
   float* Wlo = nullptr;      //             and the rest of weight 0 [NV][ncells]
   int cell_tile = 0, face_tile = 0;  // stage-kernel tiles (0: the kernels' defaults)
+  bool use_direct = false;   // one-thread-per-cell FP32 cell kernel
+  std::vector<unsigned char> dtab;  // its tables (host copy, passed by value at launch)
   void* tcB = nullptr;       // its B operands
   double* scal = nullptr;    // dt per problem [nprob]
   unsigned long long* dt_bits = nullptr;  // per-problem max signal speed [nprob]
@@ -726,7 +728,8 @@ int build_batch(dg_handle* h, const dg_mesh_desc* meshes, int nprob) {
 }
 
 cudaError_t cell_launch(dg_handle* h, const void* args, cudaStream_t s) {
-  return h->use_tc ? h->ks->cell_tc(args, s) : h->ks->cell(args, s);
+  if (h->use_tc) return h->ks->cell_tc(args, s);
+  return h->use_direct ? h->ks->cell_direct(args, s) : h->ks->cell(args, s);
 }
 
 // face and cell kernels of one stage; DG_MIXED wraps the FP64 arguments.
@@ -801,6 +804,7 @@ StageArgs<real> stage_args(dg_handle* h, const Op& op, const void* U, void* W) {
   a.dt = h->scal;
   a.cell_tile = h->cell_tile;
   a.face_tile = h->face_tile;
+  a.dtab = h->dtab.empty() ? nullptr : h->dtab.data();
   return a;
 }
 
@@ -990,25 +994,24 @@ int adjoint_step_impl(dg_handle* h, const void* Wn, double dt, const void* lam1,
   return combine_list<real>(h, lam0, t, s);
 }
 
-// Tile autotuner: times dW/dt of a free-stream state on the handle's own mesh
-// for every feasible tile of the face kernel (cell tile fixed), then of the
-// cell kernel, keeping the fastest of each.  The tile only changes how cells
-// and faces are grouped into thread blocks, never a result.
+// Tile autotuner: times RK steps of a free-stream state on the handle's own
+// mesh for every feasible tile of the face kernel (cell tile fixed), then of
+// the cell kernel (and, for FP32 2D handles, the one-thread-per-cell kernel),
+// keeping the fastest of each.
 template <typename real>
 int autotune_tiles(dg_handle* h, cudaStream_t s) {
   const size_t n = (size_t)h->nv * h->N * h->ncells;
   if (n == 0) return DG_OK;
-  void *U = nullptr, *out = nullptr;
+  void* U = nullptr;
   int r;
-  if (cudaMalloc(&U, n * h->esize) != cudaSuccess) return fail(h, DG_ERR_OOM, "autotune: out of device memory");
-  if (cudaMalloc(&out, n * h->esize) != cudaSuccess) {
-    cudaFree(U);
+  if (cudaMalloc(&U, n * h->esize) != cudaSuccess) {
+    cudaGetLastError();
     return fail(h, DG_ERR_OOM, "autotune: out of device memory");
   }
   struct Free {
-    void *a, *b;
-    ~Free() { cudaFree(a); cudaFree(b); }
-  } guard{U, out};
+    void* a;
+    ~Free() { cudaFree(a); }
+  } guard{U};
   // rho = 1, m = 0, E = 2.5 (p = 1 at gamma = 1.4): weight 0 of each variable
   DG_CUDA(h, launch_fill(U, n, 0.0, (int)h->esize, s));
   const size_t row = (size_t)h->N * h->ncells;
@@ -1018,14 +1021,16 @@ int autotune_tiles(dg_handle* h, cudaStream_t s) {
   cudaEvent_t e0, e1;
   DG_CUDA(h, cudaEventCreate(&e0));
   DG_CUDA(h, cudaEventCreate(&e1));
+  // a full step of the handle's own stage program (fixed dt, so no timestep
+  // reduction): the epilogues and registers the step really uses
   auto time_rhs = [&](float& best) -> int {
     best = 3.4e38f;
     for (int trial = 0; trial < 3; ++trial) {
-      const int rr = rhs_into<real>(h, U, out, s);
+      const int rr = rk_step_any<real>(h, U, 1e-9, nullptr, s);
       if (rr != DG_OK) return rr;
       DG_CUDA(h, cudaEventRecord(e0, s));
       for (int rep = 0; rep < 3; ++rep) {
-        const int r2 = rhs_into<real>(h, U, out, s);
+        const int r2 = rk_step_any<real>(h, U, 1e-9, nullptr, s);
         if (r2 != DG_OK) return r2;
       }
       DG_CUDA(h, cudaEventRecord(e1, s));
@@ -1052,6 +1057,7 @@ int autotune_tiles(dg_handle* h, cudaStream_t s) {
   h->face_tile = best_f;
   if (!h->use_tc) {
     int best_c = cdef;
+    bool best_direct = false;
     best_t = 3.4e38f;
     for (int tc = 16; tc <= cmax; tc *= 2) {
       h->cell_tile = tc;
@@ -1059,7 +1065,14 @@ int autotune_tiles(dg_handle* h, cudaStream_t s) {
       if ((r = time_rhs(t)) != DG_OK) return r;
       if (t < best_t) { best_t = t; best_c = tc; }
     }
+    if (!h->dtab.empty()) {  // one thread per cell
+      h->use_direct = true;
+      float t;
+      if ((r = time_rhs(t)) != DG_OK) return r;
+      if (t < best_t) { best_t = t; best_direct = true; }
+    }
     h->cell_tile = best_c;
+    h->use_direct = best_direct;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -1248,6 +1261,7 @@ static int create_impl(const dg_mesh_desc* mesh, int nprob, int k, double gamma,
     if ((r = dalloc(h, (size_t)h->nv * nf * sizeof(float), &p)) != DG_OK) return bail(r);
     h->Dm = static_cast<float*>(p);
   }
+  if (!h->ms && !use_tc && ks->fill_direct) ks->fill_direct(T, h->dtab);
   if (h->use_tc) {
     auto cell_tc = h->ms ? h->ms->cell_tc : ks->cell_tc;
     auto prepare_tc = h->ms ? h->ms->prepare_tc : ks->prepare_tc;
@@ -1369,9 +1383,34 @@ int dg_limiter_counts(dg_handle* h, int64_t* counts_dev, int reset, void* stream
   return DG_OK;
 }
 
+int dg_set_tiles(dg_handle* h, int cell_tile, int face_tile) {
+  if (!check_handle(h)) return DG_ERR_ARG;
+  const int cmax = h->ms ? h->ms->cell_tile_max : h->ks->cell_tile_max;
+  const int fmax = h->ms ? h->ms->face_tile_max : h->ks->face_tile_max;
+  if (face_tile != 16 && face_tile != 32 && face_tile != 64) return fail(h, DG_ERR_ARG, "dg_set_tiles: face tile");
+  if (face_tile > fmax) return fail(h, DG_ERR_UNSUPPORTED, "dg_set_tiles: face tile too large for (dim, k)");
+  if (cell_tile == 1) {
+    if (h->use_tc || h->dtab.empty())
+      return fail(h, DG_ERR_UNSUPPORTED, "dg_set_tiles: one thread per cell needs an FP32 2D handle");
+  } else {
+    if (cell_tile != 16 && cell_tile != 32 && cell_tile != 64) return fail(h, DG_ERR_ARG, "dg_set_tiles: cell tile");
+    if (cell_tile > cmax) return fail(h, DG_ERR_UNSUPPORTED, "dg_set_tiles: cell tile too large for (dim, k)");
+  }
+  std::lock_guard<std::mutex> lock(h->mu);
+  h->face_tile = face_tile;
+  h->use_direct = cell_tile == 1;
+  if (cell_tile != 1) h->cell_tile = cell_tile;
+  // cached step graphs hold the old launch configuration: record them anew
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+  h->graphs.clear();
+  for (auto g : h->graph_defs) cudaGraphDestroy(g);
+  h->graph_defs.clear();
+  return DG_OK;
+}
+
 int dg_tiles(const dg_handle* h, int* cell_tile, int* face_tile) {
   if (!check_handle(h) || !cell_tile || !face_tile) return DG_ERR_ARG;
-  *cell_tile = h->use_tc ? 32 : h->cell_tile;
+  *cell_tile = h->use_tc ? 32 : (h->use_direct ? 1 : h->cell_tile);
   *face_tile = h->face_tile;
   return DG_OK;
 }

@@ -110,6 +110,7 @@ struct StageArgs {
   real ck[MAX_OUT] = {};
   const double* dt = nullptr;   // device timestep per problem; nullptr means dt = 1
   int cell_tile = 0;            // cells per block of the cell kernel (0: its default)
+  const void* dtab = nullptr;   // host copy of the one-thread-per-cell kernel's tables
   int face_tile = 0;            // faces per block of the face kernel (0: its default)
   const real* tcB = nullptr;    // tensor-core B operands (tensor-core cell kernel)
   int* status = nullptr;        // device status word
@@ -225,6 +226,9 @@ struct KernelSet {
   cudaError_t (*adj_face)(const void* adj_args, cudaStream_t s) = nullptr;
   cudaError_t (*adj_cell)(const void* adj_args, cudaStream_t s) = nullptr;
   cudaError_t (*combine)(const void* combine_args, cudaStream_t s) = nullptr;
+  // one-thread-per-cell FP32 cell kernel (2D), nullptr where not built
+  cudaError_t (*cell_direct)(const void* stage_args, cudaStream_t s) = nullptr;
+  void (*fill_direct)(const std::vector<double>& tab, std::vector<unsigned char>& out) = nullptr;
   // tensor-core cell kernel (FP32 state, 2D, k = 1..3), nullptr where not built
   cudaError_t (*cell_tc)(const void* stage_args, cudaStream_t s) = nullptr;
   cudaError_t (*prepare_tc)() = nullptr;

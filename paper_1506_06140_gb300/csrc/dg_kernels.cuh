@@ -22,6 +22,7 @@
 #include "dg_physics.cuh"
 #include "dg_stage.cuh"
 #include "dg_adjoint.cuh"
+#include "dg_direct.cuh"
 #include "dg_tc.cuh"
 
 namespace dgi {
@@ -573,34 +574,63 @@ __global__ void __launch_bounds__(RED_THREADS) dt_kernel(const AuxArgs<real> a) 
   double speed = 0.0;
   int pb = 0;
   if (c < nc) {
+    // in the state's precision (an FP32 state's speed is FP32-accurate anyway)
     pb = cell_problem(a.m, c);
-    double u[S::NV];
-    for (int v = 0; v < S::NV; ++v) u[v] = (double)a.W[(size_t)(v * S::N) * nc + c];
-    const double rinv = 1.0 / u[0];
-    double m2 = 0.0;
+    real u[S::NV];
+#pragma unroll
+    for (int v = 0; v < S::NV; ++v) u[v] = a.W[(size_t)(v * S::N) * nc + c];
+    const real gamma = real(a.gamma);
+    const real rinv = real(1) / u[0];
+    real m2 = real(0);
+#pragma unroll
     for (int b = 0; b < DIM; ++b) m2 += u[1 + b] * u[1 + b];
-    const double p = (a.gamma - 1.0) * (u[DIM + 1] - 0.5 * m2 * rinv);
-    if (!(u[0] > 0.0) || !(p > 0.0)) {
+    const real p = (gamma - real(1)) * (u[DIM + 1] - real(0.5) * m2 * rinv);
+    if (!(u[0] > real(0)) || !(p > real(0))) {
       atomicOr(a.status, 1 << DG_ERR_NONPHYSICAL_BIT);
     } else {
-      const double cs = sqrt(a.gamma * p * rinv);
-      double sum = 0.0;
+      const real cs = sqrt(gamma * p * rinv);
+      real sum = real(0);
+#pragma unroll
       for (int b = 0; b < DIM; ++b) sum += fabs(u[1 + b] * rinv) + cs;
-      const double inv_dx = a.inv_dx_prob ? a.inv_dx_prob[pb] : a.inv_dx[0];
-      speed = sum * inv_dx * (double)(1 << a.m.level[c]);
+      const real inv_dx = real(a.inv_dx_prob ? a.inv_dx_prob[pb] : a.inv_dx[0]);
+      speed = (double)(sum * inv_dx * real(1 << a.m.level[c]));
     }
   } else {
     pb = -1;
   }
-  // one atomic per warp when the warp's cells belong to one problem
+  // a warp whose cells belong to one problem reduces with shuffles; the block
+  // then issues one atomic per run of warps with the same problem (a warp
+  // spanning two problems falls back to one atomic per cell)
+  __shared__ int sp[RED_THREADS / 32];
+  __shared__ double ss[RED_THREADS / 32];
   const unsigned full = 0xffffffffu;
-  const int p0 = __shfl_sync(full, pb, 0);
-  if (__all_sync(full, pb == p0 || pb < 0)) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int p0 = __shfl_sync(full, pb, 0);
+  if (p0 < 0) p0 = __reduce_max_sync(full, pb);  // lane 0 past the end: any valid lane's problem
+  const bool uniform = __all_sync(full, pb == p0 || pb < 0);
+  if (uniform) {
+#pragma unroll
     for (int off = 16; off > 0; off >>= 1) speed = fmax(speed, __shfl_xor_sync(full, speed, off));
-    if ((threadIdx.x & 31) == 0 && p0 >= 0)
-      atomicMax(a.dt_bits + p0, (unsigned long long)__double_as_longlong(speed));
   } else if (pb >= 0) {
     atomicMax(a.dt_bits + pb, (unsigned long long)__double_as_longlong(speed));
+  }
+  if (lane == 0) {
+    sp[w] = uniform ? p0 : -1;
+    ss[w] = speed;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int cur = -1;
+    double m = 0.0;
+    for (int i = 0; i < RED_THREADS / 32; ++i) {
+      if (sp[i] != cur) {
+        if (cur >= 0) atomicMax(a.dt_bits + cur, (unsigned long long)__double_as_longlong(m));
+        cur = sp[i];
+        m = 0.0;
+      }
+      if (cur >= 0) m = fmax(m, ss[i]);
+    }
+    if (cur >= 0) atomicMax(a.dt_bits + cur, (unsigned long long)__double_as_longlong(m));
   }
 }
 
@@ -879,6 +909,10 @@ KernelSet make_kernel_set(int prec) {
   ks.adj_face = &launch_adj_face<real, DIM, K>;
   ks.adj_cell = &launch_adj_cell<real, DIM, K>;
   ks.combine = &launch_combine<real>;
+  if constexpr (std::is_same<real, float>::value && DIM == 2) {
+    ks.cell_direct = &launch_cell_direct<DIM, K>;
+    ks.fill_direct = &fill_direct_tables<DIM, K>;
+  }
   if constexpr (std::is_same<real, float>::value && DIM == 2 && K >= 1 && K <= 3) {
     ks.cell_tc = &launch_cell_tc<K>;
     ks.prepare_tc = &prepare_cell_tc<K>;

@@ -25,7 +25,7 @@ EXPORTS = ["dg_default_options", "dg_create", "dg_destroy", "dg_last_error", "dg
            "dg_l1_density", "dg_node_weights", "dg_neighbor_table", "dg_cell_levels",
            "dg_status", "dg_profile_begin", "dg_profile_end", "dg_totals_noalloc",
            "dg_create_batch", "dg_batch_advance", "dg_n_problems", "dg_tiles",
-           "dg_limiter_counts"]
+           "dg_limiter_counts", "dg_set_tiles"]
 KERNEL_KINDS = ["face", "cell", "limit", "dt", "other", "adjoint"]
 
 
@@ -305,6 +305,10 @@ class Solver:
         out = torch.zeros(2, dtype=torch.int64, device=self.device) if out is None else out
         self._check(self._L.dg_limiter_counts(self._h, _ptr(out), int(bool(reset)), _stream()))
         return out
+
+    def set_tiles(self, cell_tile, face_tile):
+        """cell_tile 16/32/64 (or 1: one thread per cell, FP32 2D), face_tile 16/32/64"""
+        self._check(self._L.dg_set_tiles(self._h, int(cell_tile), int(face_tile)))
 
     def tiles(self):
         """(cells per block of the cell kernel, faces per block of the face kernel)"""

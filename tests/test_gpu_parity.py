@@ -401,3 +401,41 @@ def test_tensor_core_variant_rejects_unsupported_meshes():
     assert ei.value.code == dg.DG_ERR_UNSUPPORTED
     with pytest.raises(dg.DGError):
         solver_for(MESHES["u3"], 2, precision="fp32_tc")
+
+
+# ---------------------------------------------------------------------------
+# kernel variants selected by tile: one thread per cell (FP32, 2D)
+
+@pytest.mark.parametrize("name", ["u2", "u2t", "amr2"])
+def test_rhs_fp32_one_thread_per_cell(name):
+    m = MESHES[name]
+    for k in (0, 1, 2, 3):
+        o = oracle_for(m, k)
+        s = solver_for(m, k, precision="fp32")
+        s.set_tiles(1, 32)
+        assert s.tiles() == (1, 32)
+        W = wl.random_weights(2, o.N, o.n_cells, seed=1900 + k).astype(np.float32)
+        ref = o.rhs(W.astype(np.float64))
+        e, erms = rel_err(s.rhs(to_dev(s, W)).cpu().numpy(), ref)
+        assert e < TOL32_MAX and erms < TOL32_RMS, (name, k, e, erms)
+
+
+def test_one_thread_per_cell_steps_match_tiled():
+    """Different contraction orders agree to FP32 rounding; graphs are
+    re-recorded after a tile change."""
+    m = wl.mesh_uniform(2, [150, 131], [0.0, 0.0], [1.5, 1.31])
+    s = solver_for(m, 3, rk_order=4, precision="fp32")
+    W0 = to_dev(s, wl.random_weights(2, s.N, s.n_cells, seed=1950).astype(np.float32))
+    Wa, Wb = W0.clone(), W0.clone()
+    s.advance(Wa, 3)
+    s.set_tiles(1, 64)
+    s.advance(Wb, 3)
+    torch.cuda.synchronize()
+    d = (Wa - Wb).abs().max().item() / Wa.abs().max().item()
+    assert 0 < d < 1e-5, d
+    dg = dg_mod()
+    with pytest.raises(dg.DGError):
+        s.set_tiles(8, 32)
+    s64 = solver_for(m, 3, precision="fp64")
+    with pytest.raises(dg.DGError):
+        s64.set_tiles(1, 32)
