@@ -408,6 +408,7 @@ struct dg_handle {
   float* Dm = nullptr;       // DG_MIXED reference flux differences per face
   bool delta = false;        // DG_MIXED with FP32 delta registers (unlimited programs)
   unsigned long long* lim_counts = nullptr;  // [2] cells changed by the slope / positivity limiter
+  int* lim_queue = nullptr;  // [ncells + 1]: the positivity pass's cells, then their number
   float* Wf = nullptr;       // delta mode: FP32 split of W within a step [NV][N][ncells]
   float* Wlo = nullptr;      //             and the rest of weight 0 [NV][ncells]
   int cell_tile = 0, face_tile = 0;  // stage-kernel tiles (0: the kernels' defaults)
@@ -823,6 +824,8 @@ int run_limit(dg_handle* h, const void* src, void* dst, cudaStream_t s) {
   la.positivity = h->opt.positivity;
   la.eps = h->opt.eps;
   la.counts = h->lim_counts;
+  la.queue = h->lim_queue;
+  la.queue_len = h->lim_queue + std::max(h->ncells, 1);
   la.status = h->status;
   DG_CUDA(h, timed(h, DG_KERNEL_LIMIT, s, [&] { return h->ks->limit(&la, s); }));
   return DG_OK;
@@ -1227,6 +1230,8 @@ static int create_impl(const dg_mesh_desc* mesh, int nprob, int k, double gamma,
   h->status = static_cast<int*>(p);
   if ((r = dalloc(h, 2 * sizeof(unsigned long long), &p)) != DG_OK) return bail(r);
   h->lim_counts = static_cast<unsigned long long*>(p);
+  if ((r = dalloc(h, ((size_t)std::max(h->ncells, 1) + 1) * sizeof(int), &p)) != DG_OK) return bail(r);
+  h->lim_queue = static_cast<int*>(p);
   if (cudaMemset(h->lim_counts, 0, 2 * sizeof(unsigned long long)) != cudaSuccess)
     return bail(cuda_fail(h, cudaGetLastError(), "cudaMemset"));
   if (cudaMemset(h->status, 0, sizeof(int)) != cudaSuccess)

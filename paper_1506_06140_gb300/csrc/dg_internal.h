@@ -154,6 +154,8 @@ struct LimitArgs {
   int positivity = 0;
   double eps = 1e-10;
   unsigned long long* counts = nullptr;  // [2] cells changed by the slope / positivity limiter
+  int* queue = nullptr;          // [ncells] cells left to the positivity pass
+  int* queue_len = nullptr;      // their number
   int* status = nullptr;
 };
 

@@ -233,11 +233,10 @@ __device__ __forceinline__ double cell_dx(const MeshDev& m, int c) {
 // Inputs come from Uin (state before limiting), the result goes to Uout.
 
 template <typename real, int DIM, int K>
-__device__ __forceinline__ void nb_mean(const LimitArgs<real>& a, int c, int dir, int s,
+__device__ __forceinline__ void nb_mean(const LimitArgs<real>& a, int c, int dir, int s, int nb,
                                         const real* own, real* out) {
   using S = Shape<DIM, K>;
   const int nc = a.m.ncells;
-  const int nb = a.m.nbr[(size_t)(2 * dir + s) * nc + c];
   if (nb == -1) {
     for (int v = 0; v < S::NV; ++v) out[v] = own[v];
   } else if (nb <= -2) {
@@ -319,13 +318,12 @@ __device__ double positivity_tau(const double* ub, const double* u, double gamma
 // state's precision: ct = minmodB(sqrt(3) L w_(1+A), beta L (ubar - u_minus),
 // beta L (u_plus - ubar)) / sqrt(3)
 template <typename real, int DIM, int K, int A>
-__device__ __forceinline__ bool limit_direction(const LimitArgs<real>& a, int c, const CharState<real, DIM>& st,
+__device__ __forceinline__ bool limit_direction(const LimitArgs<real>& a, const CharState<real, DIM>& st,
                                                 const real (&w)[DIM + 2][Shape<DIM, K>::N],
-                                                const real* mean, real dx, real* ct) {
+                                                const real* mean, const real* mm, const real* mp, real dx,
+                                                real* ct) {
   constexpr int NV = DIM + 2;
-  real mm[NV], mp[NV], x[NV], cs[NV], dm[NV], dp[NV];
-  nb_mean<real, DIM, K>(a, c, A, 0, mean, mm);
-  nb_mean<real, DIM, K>(a, c, A, 1, mean, mp);
+  real x[NV], cs[NV], dm[NV], dp[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) x[v] = w[v][1 + A];
   if (a.limiter == 2) {
@@ -401,12 +399,21 @@ __global__ void __launch_bounds__(128) limit_kernel(const LimitArgs<real> a) {
   if constexpr (K > 0) {
     if (a.limiter != 0) {
       const real dx = (real)cell_dx(a.m, c);
+      // neighbour means of all sides first: the index loads, then the mean
+      // loads, each batch independent
+      int nbs[2 * DIM];
+#pragma unroll
+      for (int sd = 0; sd < 2 * DIM; ++sd) nbs[sd] = a.m.nbr[(size_t)sd * nc + c];
+      real nbm[2 * DIM][NV];
+#pragma unroll
+      for (int sd = 0; sd < 2 * DIM; ++sd) nb_mean<real, DIM, K>(a, c, sd >> 1, sd & 1, nbs[sd], mean, nbm[sd]);
       const CharState<real, DIM> st =
           a.limiter == 2 ? char_state<real, DIM>(mean, real(a.gamma)) : CharState<real, DIM>{};
       real ct[DIM][NV];
-      bool changed = limit_direction<real, DIM, K, 0>(a, c, st, w, mean, dx, ct[0]);
-      changed = limit_direction<real, DIM, K, 1>(a, c, st, w, mean, dx, ct[1]) || changed;
-      if constexpr (DIM == 3) changed = limit_direction<real, DIM, K, DIM - 1>(a, c, st, w, mean, dx, ct[DIM - 1]) || changed;
+      bool changed = limit_direction<real, DIM, K, 0>(a, st, w, mean, nbm[0], nbm[1], dx, ct[0]);
+      changed = limit_direction<real, DIM, K, 1>(a, st, w, mean, nbm[2], nbm[3], dx, ct[1]) || changed;
+      if constexpr (DIM == 3)
+        changed = limit_direction<real, DIM, K, DIM - 1>(a, st, w, mean, nbm[4], nbm[5], dx, ct[DIM - 1]) || changed;
       if (changed) {
         if (a.counts) atomicAdd(a.counts, 1ull);
         unlimit_direction<real, DIM, K, 0>(a, st, ct[0], w);
@@ -469,19 +476,43 @@ __global__ void __launch_bounds__(128) limit_kernel(const LimitArgs<real> a) {
       if (p_low >= a.eps) need_positivity = false;
     }
   }
-  if (need_positivity) {
+#pragma unroll
+  for (int v = 0; v < NV; ++v)
+#pragma unroll
+    for (int l = 0; l < N; ++l) a.Uout[(size_t)(v * N + l) * nc + c] = w[v][l];
+  // cells whose bound does not clear eps get the point search in a second pass
+  if (need_positivity) a.queue[atomicAdd(a.queue_len, 1)] = c;
+}
+
+// Positivity limiter of Sec. 3.4 (with the hanging-face points of Sec. 4.4)
+// for the queued cells, in FP64: theta_1 on the density, then theta_2 from
+// the pressure root tau of every point below eps.  Reads and writes Uout.
+template <typename real, int DIM, int K>
+__global__ void __launch_bounds__(128) positivity_kernel(const LimitArgs<real> a) {
+  using S = Shape<DIM, K>;
+  constexpr int NV = S::NV, N = S::N;
+  const int nc = a.m.ncells;
+  const double* tab = a.tab64;
+  const int len = *a.queue_len;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < len; i += gridDim.x * blockDim.x) {
+    const int c = a.queue[i];
+    real w[NV][N];
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+      for (int l = 0; l < N; ++l) w[v][l] = a.Uout[(size_t)(v * N + l) * nc + c];
     const double eps = a.eps;
     double mean64[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) mean64[v] = (double)mean[v];
+    for (int v = 0; v < NV; ++v) mean64[v] = (double)w[v][0];
     // points: the union set S, plus fine sub-face points on sides with a finer neighbour
     unsigned finer = 0;
     for (int sd = 0; sd < S::NSIDE; ++sd)
       if (a.m.nbr[(size_t)sd * nc + c] <= -2) finer |= 1u << sd;
     const int npts = S::NSP + __popc(finer) * S::NSUB * S::QF;
-    auto point_row = [&](int i) -> const double* {
-      if (i < S::NSP) return tab + S::OFF_SPHI + (size_t)i * N;
-      int r = i - S::NSP;
+    auto point_row = [&](int ip) -> const double* {
+      if (ip < S::NSP) return tab + S::OFF_SPHI + (size_t)ip * N;
+      int r = ip - S::NSP;
       int sd = 0;
       for (; sd < S::NSIDE; ++sd) {
         if (!((finer >> sd) & 1)) continue;
@@ -492,8 +523,8 @@ __global__ void __launch_bounds__(128) limit_kernel(const LimitArgs<real> a) {
       return tab + S::OFF_PHIF + (size_t)((sd * S::NVAR + var) * S::QF + q) * N;
     };
     double rmin = 1e300;
-    for (int i = 0; i < npts; ++i) {
-      const double* ph = point_row(i);
+    for (int ip = 0; ip < npts; ++ip) {
+      const double* ph = point_row(ip);
       double rho = 0.0;
 #pragma unroll
       for (int l = 0; l < N; ++l) rho += (double)w[0][l] * ph[l];
@@ -505,15 +536,15 @@ __global__ void __launch_bounds__(128) limit_kernel(const LimitArgs<real> a) {
       for (int l = 1; l < N; ++l) w[0][l] = (real)((double)w[0][l] * th1);
     }
     double th2 = 1.0;
-    for (int i = 0; i < npts; ++i) {
-      const double* ph = point_row(i);
+    for (int ip = 0; ip < npts; ++ip) {
+      const double* ph = point_row(ip);
       double u[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        double s = 0.0;
+        double sum = 0.0;
 #pragma unroll
-        for (int l = 0; l < N; ++l) s += (double)w[v][l] * ph[l];
-        u[v] = s;
+        for (int l = 0; l < N; ++l) sum += (double)w[v][l] * ph[l];
+        u[v] = sum;
       }
       double m2 = 0.0;
 #pragma unroll
@@ -529,11 +560,13 @@ __global__ void __launch_bounds__(128) limit_kernel(const LimitArgs<real> a) {
 #pragma unroll
         for (int l = 1; l < N; ++l) w[v][l] = (real)((double)w[v][l] * th2);
     }
+    if (rmin < eps || th2 < 1.0) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v)
+#pragma unroll
+        for (int l = 0; l < N; ++l) a.Uout[(size_t)(v * N + l) * nc + c] = w[v][l];
+    }
   }
-#pragma unroll
-  for (int v = 0; v < NV; ++v)
-#pragma unroll
-    for (int l = 0; l < N; ++l) a.Uout[(size_t)(v * N + l) * nc + c] = w[v][l];
 }
 
 // ===========================================================================
@@ -820,7 +853,15 @@ template <typename real, int DIM, int K>
 cudaError_t launch_limit(const void* pa, cudaStream_t s) {
   const auto& a = *static_cast<const LimitArgs<real>*>(pa);
   if (a.m.ncells == 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(a.queue_len, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
   limit_kernel<real, DIM, K><<<(a.m.ncells + 127) / 128, 128, 0, s>>>(a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (a.positivity && K > 0) {
+    // the queue's length is known on the device only: a fixed grid strides over it
+    const int blocks = (a.m.ncells + 127) / 128 < 608 ? (a.m.ncells + 127) / 128 : 608;
+    positivity_kernel<real, DIM, K><<<blocks, 128, 0, s>>>(a);
+  }
   return cudaGetLastError();
 }
 
