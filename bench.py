@@ -53,6 +53,13 @@ WORKLOADS = {
              "of the graph replay)",
         dim=2, k=1, rk=2, stages=2, limiter="none", positivity=False, precisions=("fp64",),
         tag="wave2d32_k1", graph=True, cfl=0.3),
+    "square64": dict(
+        name="square advection 2D, 64x64 periodic [0,1]^2, rho 4 in a 0.5-wide square, rho 1 outside, "
+             "p=2.5, v=(100,50), k=2 (6 coeffs/cell/var), SSP-RK3, characteristic TVB limiter "
+             "(beta 1, Mtilde 0.5), CFL 0.2, FP64; all timed steps in one CUDA-graph launch "
+             "(launch-bound: step rate of the graph replay)",
+        dim=2, k=2, rk=3, stages=3, limiter="characteristic", positivity=False, precisions=("fp64",),
+        tag="square64_k2", graph=True),
     "sedov3d": dict(
         name="Sedov blast 3D, 64^3 base + central 32^3 refined once (491,520 cells), k=2 "
              "(10 coeffs/cell/var), SSP-RK3, characteristic TVB limiter + positivity limiter, "
@@ -66,8 +73,8 @@ def workload_config(wk, precision, cells):
     W = WORKLOADS[wk]
     l2 = ("state larger than L2 (no flush); timed steps in one graph launch" if W.get("graph")
           else "flushed between timed steps (256 MiB write)")
-    if wk == "wave2d":
-        l2 = "L2-resident 98 KB state (launch-bound workload); timed steps in one graph launch"
+    if wk in ("wave2d", "square64"):
+        l2 = "L2-resident state (launch-bound workload); timed steps in one graph launch"
     return {"workload": W["name"], "cells": cells, "k": W["k"], "rk_stages": W["stages"],
             "precision": precision, "l2": l2}
 
@@ -87,6 +94,8 @@ def make_problem(wk, precision, autotune=None):
         m, ic = mesh(), wl.vortex
     elif wk == "wave2d":
         m, ic = wl.mesh_uniform(2, [32, 32], [0.0, 0.0], [1.0, 1.0]), wl.wave2d
+    elif wk == "square64":
+        m, ic = wl.mesh_uniform(2, [64, 64], [0.0, 0.0], [1.0, 1.0]), wl.square2d
     elif wk == "ensemble":
         probs = wl.ensemble_problems()
         m = [wl.mesh_uniform(2, [n, n], [-5.0, -5.0], [5.0, 5.0]) for n, _ in probs]
@@ -565,6 +574,54 @@ def run_l1_study(args):
     return 0
 
 
+def run_square_growth(args):
+    """Square advection (64^2, v=(100,50)): L1 density error against the
+    translated initial state over time for DG-2 (k=1, SSP-RK2) and DG-3 (k=2,
+    SSP-RK3) with the characteristic limiter, the power law of its growth, and
+    the graph-replay step rate (FP64)."""
+    import torch
+    from paper_1506_06140_gb300 import dg
+    from paper_1506_06140_gb300 import workloads as wl
+    torch.cuda.set_device(0)
+    m = wl.mesh_uniform(2, [64, 64], [0.0, 0.0], [1.0, 1.0])
+    chunk = 1000
+    out = {"metric": "square advection: L1 density error vs time and step rate",
+           "config": {"workload": WORKLOADS["square64"]["name"], "t_end": args.t_end}, "runs": []}
+    for k, rk in ((1, 2), (2, 3)):
+        s = dg.Solver(m, k, 1.4, rk_order=rk, cfl=CFL, limiter="characteristic", precision="fp64")
+        W = s.project(torch.as_tensor(wl.square2d(s.quad_points().cpu().numpy())))
+        s.limit(W)
+        xyz1 = s.l1_points().cpu().numpy()
+        hist = s.dt_buffer(chunk)
+        s.advance(W.clone(), chunk, hist)  # records the graph
+        t, steps, rows, ms = 0.0, 0, [], 0.0
+        marks = [x for x in (0.01, 0.02, 0.05, 0.1, 0.2, 0.5, 1.0, 2.0, 5.0, 10.0) if x <= args.t_end]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for mark in marks:
+            while t < mark:
+                e0.record()
+                s.advance(W, chunk, hist)
+                e1.record()
+                torch.cuda.synchronize()
+                ms += e0.elapsed_time(e1)
+                t += hist.sum().item()
+                steps += chunk
+            l1 = s.l1_density(W, torch.as_tensor(wl.square2d(xyz1, t=t)[0])).item()
+            rows.append({"t": t, "steps": steps, "L1": l1})
+        late = [r for r in rows if r["t"] >= 0.1]
+        alpha = None
+        if len(late) >= 2:
+            x = np.log([r["t"] for r in late])
+            y = np.log([r["L1"] for r in late])
+            alpha = float(np.polyfit(x, y, 1)[0])
+        run = {"k": k, "rk_order": rk, "rows": rows, "growth_exponent": alpha,
+               "us_per_step": 1e3 * ms / steps, "steps_per_s": steps / (ms * 1e-3)}
+        out["runs"].append(run)
+        print(json.dumps(run), flush=True)
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def cpu_baseline(n_sample=128, max_seconds=20.0):
     """The oracle, as it stands, on a bounded sample of the workload: the
     vortex on a 128^2 periodic box with the same cell size, k and RK4."""
@@ -631,14 +688,16 @@ def main():
                     choices=["both", "fp64", "fp32", "fp32_tc", "mixed", "mixed_tc"],
                     help="run one precision only (profiling); the JSON line needs both")
     ap.add_argument("--workload", default="vortex",
-                    choices=sorted(WORKLOADS) + ["adjoint3d", "l1study"])
-    ap.add_argument("--t-end", type=float, default=2.0, help="l1study: final time")
+                    choices=sorted(WORKLOADS) + ["adjoint3d", "l1study", "square_growth"])
+    ap.add_argument("--t-end", type=float, default=2.0, help="l1study, square_growth: final time")
     ap.add_argument("--size", type=int, default=128, help="adjoint3d: cells per axis")
     args = ap.parse_args()
-    if args.workload in ("adjoint3d", "l1study"):
+    if args.workload in ("adjoint3d", "l1study", "square_growth"):
         from paper_1506_06140_gb300 import build
         build.build()
-        return run_adjoint(args) if args.workload == "adjoint3d" else run_l1_study(args)
+        if args.workload == "adjoint3d":
+            return run_adjoint(args)
+        return run_l1_study(args) if args.workload == "l1study" else run_square_growth(args)
     wprec = WORKLOADS[args.workload]["precisions"]
     args.precisions = wprec if args.precision == "both" else (args.precision,)
     args.warmup = max(args.warmup, 3)

@@ -12,6 +12,7 @@ Workloads (shapes after the paper's tests, Sec. 5):
   * ``sedov3d``   blast wave on a static two-level mesh (Sec. 5.3)
   * ``acoustic3d`` small-amplitude standing sound wave, periodic [0,1]^3
   * ``sod``       shock tube (Sec. 5.2) as a quasi-1D strip
+  * ``square2d``  supersonic square advection (Sec. 5.4), periodic [0,1]^2
 """
 import math
 
@@ -65,6 +66,18 @@ def acoustic3d(xyz, gamma=1.4, amp=1e-3, vel=(0.0, 0.0, 0.0)):
     rho = 1.0 + amp * np.sin(2 * math.pi * x) * np.sin(2 * math.pi * y) * np.sin(2 * math.pi * z)
     v = [np.full_like(rho, vv) for vv in vel]
     return conserved(rho, v, np.full_like(rho, 1.0 / gamma), gamma)
+
+
+def square2d(xyz, gamma=1.4, rho_in=4.0, rho_out=1.0, p=2.5, vel=(100.0, 50.0), lo=0.25, hi=0.75,
+             t=0.0):
+    """Square advection (Sec. 5.4): a square overdensity in pressure equilibrium
+    moving supersonically through the periodic unit box; the exact solution is
+    the initial state translated by vel * t."""
+    x = np.mod(xyz[0] - vel[0] * t, 1.0)
+    y = np.mod(xyz[1] - vel[1] * t, 1.0)
+    inside = (x > lo) & (x < hi) & (y > lo) & (y < hi)
+    rho = np.where(inside, rho_in, rho_out)
+    return conserved(rho, vel, np.full_like(rho, p), gamma)
 
 
 def sod(xyz, gamma=1.4, x0=0.5):
