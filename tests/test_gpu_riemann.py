@@ -129,3 +129,26 @@ def test_double_rarefaction_stays_positive(precision):
     assert err < 0.02, err
     counts = s.limiter_counts().cpu().numpy()
     assert counts[1] > 0  # the positivity limiter acted near the vacuum
+
+
+@pytest.mark.parametrize("dim,axis", [(2, 0), (3, 1)], ids=["2d-x", "3d-y"])
+def test_sod_component_limiter_matches_oracle(dim, axis):
+    """The component-wise variant of the slope limiter (Sec. 3.2): same run,
+    same bars, FP64 against the oracle."""
+    from paper_1506_06140_gb300 import dg
+    n, k = 96, 2
+    m = strip(dim, axis, n)
+    left, right = (1.0, 0.0, 1.0), (0.125, 0.0, 0.1)
+    s = dg.Solver(m, k, GAMMA, rk_order=3, limiter="component", positivity=True)
+    W = s.project(torch.as_tensor(riemann_state(s.quad_points().cpu().numpy(), axis, left, right)))
+    s.limit(W)
+    W = run_gpu(s, W, T_SOD)
+    rho = W[0, 0].cpu().numpy()
+    x = s.quad_points()[axis].mean(dim=0).cpu().numpy()
+    err = np.abs(rho - density_profile(x, T_SOD)).mean()
+    print("sod component limiter %dD: L1 %.3e" % (dim, err))
+    assert err < 0.015, err
+    o = O.Oracle(m["dim"], m["n"], m["lo"], m["hi"], k, GAMMA, bc=m["bc"], rk_order=3,
+                 limiter=O.LIM_COMPONENT, positivity=True)
+    Wo = run_oracle(o, o.limit(o.project(riemann_state(o.quad_points(), axis, left, right))), T_SOD)
+    assert np.abs(Wo[0, 0] - rho).mean() < 1e-10
