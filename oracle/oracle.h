@@ -53,6 +53,13 @@ double orc_l1_density(const orc_problem* p, const double* W, const double* rho_e
 void orc_rhs_cells(const orc_problem* p, const double* W, const int32_t* cells, int n, double* out);
 void orc_limit_cells(const orc_problem* p, const double* W, const int32_t* cells, int n, double* out);
 void orc_node_weights(const orc_problem* p, const double* W, double* Wnode);
+/* base cells of the mesh (lexicographic) */
+int orc_n_base(const orc_problem* p);
+/* new refinement flag per base cell: criteria of eqs. cell_ref / node_ref plus one buffer layer */
+void orc_adapt_flags(const orc_problem* p, const double* W, double w_t, double alpha, int* flags);
+/* W_new on p_new's mesh from W_old on p_old's (same base grid): copy, refine or merge */
+void orc_adapt_project(const orc_problem* p_new, const orc_problem* p_old, const double* W_old,
+                       double* W_new);
 void orc_rk_step_jvp(const orc_problem* p, const double* W, const double* V, double dt,
                      double* W_out, double* JV);
 

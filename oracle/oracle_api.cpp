@@ -93,6 +93,15 @@ void orc_limit_cells(const orc_problem* p, const double* W, const int32_t* cells
 void orc_node_weights(const orc_problem* p, const double* W, double* Wnode) {
   p->P.node_weights(W, Wnode);
 }
+int orc_n_base(const orc_problem* p) { return p->P.mesh.n[0] * p->P.mesh.n[1] * p->P.mesh.n[2]; }
+void orc_adapt_flags(const orc_problem* p, const double* W, double w_t, double alpha, int* flags) {
+  const std::vector<int> f = p->P.adapt_flags(W, w_t, alpha);
+  for (size_t b = 0; b < f.size(); ++b) flags[b] = f[b];
+}
+void orc_adapt_project(const orc_problem* p_new, const orc_problem* p_old, const double* W_old,
+                       double* W_new) {
+  p_new->P.adapt_project(p_old->P, W_old, W_new);
+}
 void orc_rk_step_jvp(const orc_problem* p, const double* W, const double* V, double dt,
                      double* W_out, double* JV) {
   p->P.rk_step_jvp(W, V, dt, W_out, JV);

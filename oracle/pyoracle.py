@@ -55,6 +55,10 @@ def lib():
         L.orc_l1_density.restype = C.c_double
         L.orc_l1_density.argtypes = [C.c_void_p, _D, _D]
         L.orc_node_weights.argtypes = [C.c_void_p, _D, _D]
+        L.orc_n_base.restype = C.c_int
+        L.orc_n_base.argtypes = [C.c_void_p]
+        L.orc_adapt_flags.argtypes = [C.c_void_p, _D, C.c_double, C.c_double, _I]
+        L.orc_adapt_project.argtypes = [C.c_void_p, C.c_void_p, _D, _D]
         L.orc_rhs_cells.argtypes = [C.c_void_p, _D, _I32, C.c_int, _D]
         L.orc_limit_cells.argtypes = [C.c_void_p, _D, _I32, C.c_int, _D]
         L.orc_rk_step_jvp.argtypes = [C.c_void_p, _D, _D, C.c_double, _D, _D]
@@ -225,6 +229,20 @@ class Oracle:
         W = _f64(W)
         out = np.zeros((self.nv, self.N, self.n_nodes))
         lib().orc_node_weights(self._h, _d(W), _d(out))
+        return out
+
+    def adapt_flags(self, W, w_t=0.01, alpha=1.1):
+        """new refinement flag of every base cell (lexicographic, x fastest)"""
+        W = _f64(W)
+        out = np.zeros(lib().orc_n_base(self._h), dtype=np.int32)
+        lib().orc_adapt_flags(self._h, _d(W), w_t, alpha, out.ctypes.data_as(C.POINTER(C.c_int)))
+        return out
+
+    def adapt_project(self, old, W_old):
+        """this mesh's state from W_old on `old` (same base grid)"""
+        W_old = _f64(W_old)
+        out = np.zeros(self.shape)
+        lib().orc_adapt_project(self._h, old._h, _d(W_old), _d(out))
         return out
 
     def rk_step_jvp(self, W, V, dt):

@@ -12,6 +12,7 @@
 #include <cmath>
 #include <functional>
 #include <stdexcept>
+#include <map>
 #include <vector>
 
 #include "euler.hpp"
@@ -699,6 +700,102 @@ struct Problem {
       s += std::pow(0.5 * mesh.dx(c), dim) * cell;
     }
     return s / vol_total;
+  }
+
+  // ---- mesh adaptation of the two-level mesh (Secs. 4.1, 4.3, 4.4) ----
+  // Base cells in lexicographic order; first[b] = first cell of base cell b,
+  // node_of[b] = its node index or -1 when b is a leaf.
+  void base_maps(std::vector<int>& first, std::vector<int>& node_of) const {
+    const int nb = mesh.n[0] * mesh.n[1] * mesh.n[2];
+    first.assign(nb + 1, 0);
+    node_of.assign(nb, -1);
+    std::map<std::array<int, 3>, int> nodes;
+    for (int m = 0; m < mesh.nnodes; ++m) nodes[mesh.node_coord[m]] = m;
+    for (int b = 0; b < nb; ++b) {
+      const std::array<int, 3> p = {b % mesh.n[0], (b / mesh.n[0]) % mesh.n[1], b / (mesh.n[0] * mesh.n[1])};
+      auto it = nodes.find(p);
+      if (it != nodes.end()) node_of[b] = it->second;
+      first[b + 1] = first[b] + (it != nodes.end() ? (1 << dim) : 1);
+    }
+  }
+
+  // New refinement of every base cell: the criterion of eq. cell_ref on a
+  // leaf (the largest density slope weight |w_rho,1+a| above alpha w_t), of
+  // eq. node_ref on a node (its node weights' largest slope above w_t /
+  // alpha), then one buffer layer: a base cell is refined when it or any base
+  // cell around it (sharing a face, edge or corner; periodic axes wrap)
+  // meets its criterion.
+  std::vector<int> adapt_flags(const double* W, double w_t, double alpha) const {
+    std::vector<int> first, node_of;
+    base_maps(first, node_of);
+    const int nb = (int)node_of.size();
+    std::vector<double> Wn((size_t)nv * N * std::max(mesh.nnodes, 1));
+    if (mesh.nnodes > 0) node_weights(W, Wn.data());
+    std::vector<int> crit(nb, 0);
+    for (int b = 0; b < nb; ++b) {
+      double slope = 0.0;
+      for (int a = 0; a < dim; ++a) {
+        const double wa = node_of[b] < 0 ? W[idx(0, 1 + a, first[b])]
+                                         : Wn[(size_t)(1 + a) * mesh.nnodes + node_of[b]];
+        slope = std::max(slope, std::fabs(wa));
+      }
+      crit[b] = node_of[b] < 0 ? (slope > alpha * w_t) : (slope > w_t / alpha);
+    }
+    std::vector<int> flags(nb, 0);
+    const int* n = mesh.n;
+    for (int b = 0; b < nb; ++b) {
+      const int p[3] = {b % n[0], (b / n[0]) % n[1], b / (n[0] * n[1])};
+      int any = 0;
+      for (int dz = (dim == 3 ? -1 : 0); dz <= (dim == 3 ? 1 : 0); ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dx = -1; dx <= 1; ++dx) {
+            const int d[3] = {dx, dy, dz};
+            int q[3];
+            bool inside = true;
+            for (int a = 0; a < 3; ++a) {
+              q[a] = p[a] + d[a];
+              if (q[a] < 0 || q[a] >= n[a]) {
+                if (a < dim && mesh.bc[a] == BC_PERIODIC) q[a] = (q[a] + n[a]) % n[a];
+                else inside = false;
+              }
+            }
+            if (inside) any |= crit[q[0] + n[0] * (q[1] + n[1] * q[2])];
+          }
+      flags[b] = any;
+    }
+    return flags;
+  }
+
+  // The state on this mesh from the state Wold on `old` (the same base grid):
+  // unchanged cells copied, a refined leaf projected onto its children with
+  // the refinement matrices (eq. ref_weights), a derefined node's children
+  // merged with the transposed matrices (eq. deref_weights).
+  void adapt_project(const Problem& old, const double* Wold, double* W) const {
+    std::vector<int> f0, n0, f1, n1;
+    old.base_maps(f0, n0);
+    base_maps(f1, n1);
+    const int nch = 1 << dim;
+    for (size_t b = 0; b < n1.size(); ++b)
+      for (int v = 0; v < nv; ++v) {
+        if ((n0[b] < 0) == (n1[b] < 0)) {  // unchanged: copy every cell of the base cell
+          for (int k = 0; k < f1[b + 1] - f1[b]; ++k)
+            for (int l = 0; l < N; ++l) W[idx(v, l, f1[b] + k)] = Wold[old.idx(v, l, f0[b] + k)];
+        } else if (n1[b] >= 0) {  // refine: w^c = P_c w
+          for (int ch = 0; ch < nch; ++ch)
+            for (int j = 0; j < N; ++j) {
+              double s = 0.0;
+              for (int l = 0; l < N; ++l) s += Pref[((size_t)ch * N + j) * N + l] * Wold[old.idx(v, l, f0[b])];
+              W[idx(v, j, f1[b] + ch)] = s;
+            }
+        } else {  // derefine: w = 2^-d sum_c P_c^T w^c
+          for (int j = 0; j < N; ++j) {
+            double s = 0.0;
+            for (int ch = 0; ch < nch; ++ch)
+              for (int l = 0; l < N; ++l) s += Pref[((size_t)ch * N + l) * N + j] * Wold[old.idx(v, l, f0[b] + ch)];
+            W[idx(v, j, f1[b])] = std::ldexp(s, -dim);
+          }
+        }
+      }
   }
 
   // node weights w_node = 2^-d sum_c P_c^T w^c (eq. deref_weights)
