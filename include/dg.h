@@ -237,6 +237,44 @@ int dg_l1_density(dg_handle* h, const void* W_dev, const double* rho_ref_dev, do
  * refined base cell (eq. deref_weights) -> Wnode_dev [nv][N][node]. */
 int dg_node_weights(dg_handle* h, const void* W_dev, void* Wnode_dev, void* stream);
 
+/* ---- Mesh adaptation of the two-level mesh (Secs. 4.1, 4.3-4.5) ----
+ * Single problems with k >= 1 only (DG_ERR_UNSUPPORTED otherwise); the tensor-core
+ * precisions keep their uniform-mesh restriction (dg_regrid refuses a mesh
+ * with nodes).  Base cells are numbered lexicographically (x fastest).
+ *
+ * dg_adapt_mark: decides the next refinement from the state W_dev (the
+ * handle's precision and layout) on `stream`.  A leaf base cell meets the
+ * criterion when max_a |w_{rho,1+a}| > alpha * w_t (eq. cell_ref), a refined
+ * base cell (a node) when the same maximum over its node weights exceeds
+ * w_t / alpha (eq. node_ref); a base cell is refined on the next mesh when it
+ * or any of the 3^dim - 1 base cells around it (sharing a face, edge or
+ * corner; periodic axes wrap) meets its criterion, which keeps one buffer
+ * layer around every flagged cell (Sec. 4.1).  The paper takes w_t = 0.01,
+ * alpha = 1.1.  Synchronises `stream`; returns the next mesh's cell count in
+ * *n_cells_new and the number of base cells whose refinement changes in
+ * *n_changed (either may be NULL); flags_host (NULL or int32 [n_base]) gets
+ * the next refinement (1 refined, 0 leaf).  The decision is kept in the
+ * handle for dg_regrid.  DG_ERR_ARG unless w_t > 0 and alpha >= 1.
+ *
+ * dg_adapt_set: the same with the next refinement given by flags_host
+ * (int32 [n_base], nonzero = refined).
+ *
+ * dg_regrid: rebuilds the handle's mesh tables on the device for the marked
+ * refinement and writes the state on the new mesh to W_new_dev ([nv][N]
+ * [n_cells_new], caller-owned, must not alias W_old_dev): unchanged cells are
+ * copied, a newly refined cell's children get w^c = P_c w (eq. ref_weights,
+ * exact for the coarse polynomial), a derefined node's cell gets
+ * w = 2^-dim sum_c P_c^T w^c (eq. deref_weights, conserving every mean).
+ * Synchronises `stream` once (to size the face arrays); buffers that no
+ * longer fit are reallocated.  Afterwards every entry point works on the new
+ * mesh (dg_sizes reports its counts; cached step graphs are recorded anew).
+ * DG_ERR_ARG when no refinement is marked. */
+int dg_adapt_mark(dg_handle* h, const void* W_dev, double w_t, double alpha, int32_t* flags_host,
+                  int64_t* n_cells_new, int64_t* n_changed, void* stream);
+int dg_adapt_set(dg_handle* h, const int32_t* flags_host, int64_t* n_cells_new, int64_t* n_changed,
+                 void* stream);
+int dg_regrid(dg_handle* h, const void* W_old_dev, void* W_new_dev, void* stream);
+
 /* Host copies of the mesh tables, for checks:
  * neighbour table nbr[side][cell] (side = 2*axis + {0:-, 1:+}; >= 0 a leaf
  * cell, -1 no neighbour, <= -2 the node -(v+2)); levels[cell]. */

@@ -435,6 +435,26 @@ struct dg_handle {
   // adjoint work arrays (allocated by the first dg_rk_step_adjoint call)
   std::vector<void*> adj;
   void* FG = nullptr;
+  // dynamic adaptation (single problems): base grid, the base maps of the
+  // current mesh (slot cur) and of the marked next mesh (slot 1 - cur)
+  BaseGrid bg;
+  std::vector<int32_t> base_first_host, base_node_host;  // of the mesh built at creation
+  int32_t* base_first[2] = {nullptr, nullptr};  // [nbase + 1]
+  int32_t* base_node[2] = {nullptr, nullptr};   // [nbase]
+  int cur = 0;
+  uint8_t* adapt_crit = nullptr;   // [nbase] criterion
+  uint8_t* adapt_ref = nullptr;    // [nbase] new refinement
+  int32_t* adapt_cnt = nullptr;    // [nbase] cells per base cell
+  int32_t* adapt_info = nullptr;   // [1] base cells whose refinement changes
+  int32_t* scan_work = nullptr;
+  size_t scan_work_cap = 0;
+  int32_t* face_cnt = nullptr;     // regrid face counts and their prefix sums
+  int32_t* face_off = nullptr;
+  size_t face_cnt_cap = 0;
+  bool mark_pending = false;
+  int64_t next_cells = 0, next_nodes = 0;
+  size_t cap_cells = 0, cap_faces = 0, cap_nodes = 0;  // capacity of the mesh-sized buffers
+  bool tables_on_device = false;   // host mirrors are stale after a regrid
   // instrumentation
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -493,6 +513,13 @@ int upload(dg_handle* h, const std::vector<T>& v, const T** out) {
   return DG_OK;
 }
 
+void dfree(dg_handle* h, void* p) {
+  if (!p) return;
+  auto it = std::find(h->allocs.begin(), h->allocs.end(), p);
+  if (it != h->allocs.end()) h->allocs.erase(it);
+  cudaFree(p);
+}
+
 int dalloc(dg_handle* h, size_t bytes, void** out) {
   void* p = nullptr;
   if (bytes == 0) bytes = 16;
@@ -549,6 +576,14 @@ int build_mesh(dg_handle* h, const dg_mesh_desc* m) {
   const int nc = first[nbase];
   h->ncells = nc;
   h->nnodes = nn;
+  h->bg.dim = d;
+  h->bg.nbase = nbase;
+  for (int a = 0; a < 3; ++a) {
+    h->bg.n[a] = n[a];
+    h->bg.periodic[a] = a < d ? (bc[a] == DG_BC_PERIODIC) : 1;
+  }
+  h->base_first_host = first;
+  h->base_node_host = node_of;
   h->level.assign(nc, 0);
   h->coord.assign((size_t)3 * nc, 0);
   h->node_children.assign((size_t)nn * nch, 0);
@@ -726,6 +761,126 @@ int build_batch(dg_handle* h, const dg_mesh_desc* meshes, int nprob) {
   h->md.nnodes = nn;
   h->md.nprob = nprob;
   return DG_OK;
+}
+
+// ---- dynamic adaptation: buffers ----
+
+template <typename T>
+int realloc_buf(dg_handle* h, T*& ptr, size_t bytes) {
+  dfree(h, const_cast<void*>(static_cast<const void*>(ptr)));
+  ptr = nullptr;
+  void* q = nullptr;
+  const int r = dalloc(h, bytes, &q);
+  if (r != DG_OK) return r;
+  ptr = static_cast<T*>(q);
+  return DG_OK;
+}
+
+// Mesh-sized buffers for at least nc cells, nf faces and nn nodes (a negative
+// count leaves that class alone).  A class that does not fit is released and
+// allocated anew with a quarter of headroom; contents are not kept (the
+// caller rewrites every table).  cudaFree waits for the device.
+int ensure_capacity(dg_handle* h, int64_t nc, int64_t nf, int64_t nn) {
+  const int d = h->dim, nch = 1 << d;
+  auto grown = [](int64_t need, int64_t limit) { return std::min<int64_t>(limit, need + need / 4 + 64); };
+  int r;
+  if (nc > (int64_t)h->cap_cells) {
+    const size_t cap = (size_t)grown(nc, (int64_t)h->bg.nbase * nch);
+    MeshDev& m = h->md;
+    if ((r = realloc_buf(h, m.level, cap)) != DG_OK) return r;
+    if ((r = realloc_buf(h, m.coord, 3 * cap * sizeof(int32_t))) != DG_OK) return r;
+    if ((r = realloc_buf(h, m.nbr, 2 * d * cap * sizeof(int32_t))) != DG_OK) return r;
+    if ((r = realloc_buf(h, m.sface, 2 * d * cap * sizeof(int32_t))) != DG_OK) return r;
+    if ((r = realloc_buf(h, m.scoarse, cap)) != DG_OK) return r;
+    for (auto& reg : h->regs)
+      if ((r = realloc_buf(h, reg, (size_t)h->nv * h->N * cap * h->esize)) != DG_OK) return r;
+    if ((r = realloc_buf(h, h->partial, ((cap + 255) / 256 + 1) * 8 * sizeof(double))) != DG_OK) return r;
+    if ((r = realloc_buf(h, h->lim_queue, (cap + 1) * sizeof(int))) != DG_OK) return r;
+    if (h->Wf && (r = realloc_buf(h, h->Wf, (size_t)h->nv * h->N * cap * sizeof(float))) != DG_OK) return r;
+    if (h->Wlo && (r = realloc_buf(h, h->Wlo, (size_t)h->nv * cap * sizeof(float))) != DG_OK) return r;
+    h->cap_cells = cap;
+  }
+  if (nf > (int64_t)h->cap_faces) {
+    const size_t cap = (size_t)grown(nf, INT32_MAX);
+    MeshDev& m = h->md;
+    if ((r = realloc_buf(h, m.fm, cap * sizeof(int32_t))) != DG_OK) return r;
+    if ((r = realloc_buf(h, m.fp, cap * sizeof(int32_t))) != DG_OK) return r;
+    if ((r = realloc_buf(h, m.finfo, cap)) != DG_OK) return r;
+    if ((r = realloc_buf(h, h->F, (size_t)h->nv * h->ks->QF * cap * h->esize)) != DG_OK) return r;
+    if (h->Gm && (r = realloc_buf(h, h->Gm, (size_t)h->nv * h->ks->QF * cap * sizeof(float))) != DG_OK) return r;
+    if (h->Dm && (r = realloc_buf(h, h->Dm, (size_t)h->nv * cap * sizeof(float))) != DG_OK) return r;
+    h->cap_faces = cap;
+  }
+  if (nn > (int64_t)h->cap_nodes) {
+    const size_t cap = (size_t)grown(nn, h->bg.nbase);
+    if ((r = realloc_buf(h, h->md.node_children, cap * nch * sizeof(int32_t))) != DG_OK) return r;
+    h->cap_nodes = cap;
+  }
+  return DG_OK;
+}
+
+int ensure_scan_work(dg_handle* h, int64_t n) {
+  const size_t need = scan_work_ints(n);
+  if (need <= h->scan_work_cap) return DG_OK;
+  const int r = realloc_buf(h, h->scan_work, need * sizeof(int32_t));
+  if (r == DG_OK) h->scan_work_cap = need;
+  return r;
+}
+
+// base maps and work arrays of the adaptation, on first use
+int ensure_adapt(dg_handle* h) {
+  if (h->adapt_crit) return DG_OK;
+  if (h->nprob != 1) return fail(h, DG_ERR_UNSUPPORTED, "mesh adaptation needs a single problem");
+  if (h->k < 1) return fail(h, DG_ERR_UNSUPPORTED, "mesh adaptation needs k >= 1 (the slope weights)");
+  const int64_t nb = h->bg.nbase;
+  if (nb * (1 << h->dim) * 3 * h->dim >= (int64_t)INT32_MAX)
+    return fail(h, DG_ERR_UNSUPPORTED, "mesh adaptation: base grid too large for 32-bit face numbering");
+  int r;
+  for (int slot = 0; slot < 2; ++slot) {
+    if ((r = realloc_buf(h, h->base_first[slot], (size_t)(nb + 1) * sizeof(int32_t))) != DG_OK) return r;
+    if ((r = realloc_buf(h, h->base_node[slot], (size_t)std::max<int64_t>(nb, 1) * sizeof(int32_t))) != DG_OK)
+      return r;
+  }
+  h->cur = 0;
+  DG_CUDA(h, cudaMemcpy(h->base_first[0], h->base_first_host.data(), (size_t)(nb + 1) * sizeof(int32_t),
+                        cudaMemcpyHostToDevice));
+  DG_CUDA(h, cudaMemcpy(h->base_node[0], h->base_node_host.data(), (size_t)nb * sizeof(int32_t),
+                        cudaMemcpyHostToDevice));
+  if ((r = realloc_buf(h, h->adapt_ref, (size_t)nb)) != DG_OK) return r;
+  if ((r = realloc_buf(h, h->adapt_cnt, (size_t)nb * sizeof(int32_t))) != DG_OK) return r;
+  if ((r = realloc_buf(h, h->adapt_info, sizeof(int32_t))) != DG_OK) return r;
+  if ((r = ensure_scan_work(h, nb)) != DG_OK) return r;
+  return realloc_buf(h, h->adapt_crit, (size_t)nb);
+}
+
+// prefix sum of the cells per base cell into the next slot, then the new
+// sizes and the change count back to the host (synchronises the stream)
+int finish_mark(dg_handle* h, int32_t* flags_host, int64_t* n_cells_new, int64_t* n_changed, cudaStream_t s) {
+  const int nb = h->bg.nbase, nxt = 1 - h->cur;
+  DG_CUDA(h, launch_scan(h->adapt_cnt, nb, h->base_first[nxt], h->scan_work, s));
+  int32_t info[2] = {0, 0};
+  DG_CUDA(h, cudaMemcpyAsync(&info[0], h->base_first[nxt] + nb, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  DG_CUDA(h, cudaMemcpyAsync(&info[1], h->adapt_info, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  std::vector<uint8_t> fl;
+  if (flags_host) {
+    fl.resize((size_t)nb);
+    DG_CUDA(h, cudaMemcpyAsync(fl.data(), h->adapt_ref, (size_t)nb, cudaMemcpyDeviceToHost, s));
+  }
+  DG_CUDA(h, cudaStreamSynchronize(s));
+  for (size_t b = 0; b < fl.size(); ++b) flags_host[b] = fl[b];
+  h->next_cells = info[0];
+  h->next_nodes = (info[0] - nb) / ((1 << h->dim) - 1);
+  h->mark_pending = true;
+  if (n_cells_new) *n_cells_new = info[0];
+  if (n_changed) *n_changed = info[1];
+  return DG_OK;
+}
+
+void drop_graphs(dg_handle* h) {
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+  h->graphs.clear();
+  for (auto g : h->graph_defs) cudaGraphDestroy(g);
+  h->graph_defs.clear();
 }
 
 cudaError_t cell_launch(dg_handle* h, const void* args, cudaStream_t s) {
@@ -1287,6 +1442,9 @@ static int create_impl(const dg_mesh_desc* mesh, int nprob, int k, double gamma,
     return bail(cuda_fail(h, cudaGetLastError(), "cudaStreamCreate"));
   h->cell_tile = h->ms ? h->ms->cell_tile : ks->cell_tile;
   h->face_tile = h->ms ? h->ms->face_tile : ks->face_tile;
+  h->cap_cells = (size_t)h->ncells;
+  h->cap_faces = (size_t)std::max(h->nfaces, 1);
+  h->cap_nodes = (size_t)h->nnodes;
   if (o.autotune) {
     r = h->prec == DG_FP64 ? autotune_tiles<double>(h, h->cap_stream)
                            : autotune_tiles<float>(h, h->cap_stream);
@@ -1406,10 +1564,7 @@ int dg_set_tiles(dg_handle* h, int cell_tile, int face_tile) {
   h->use_direct = cell_tile == 1;
   if (cell_tile != 1) h->cell_tile = cell_tile;
   // cached step graphs hold the old launch configuration: record them anew
-  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
-  h->graphs.clear();
-  for (auto g : h->graph_defs) cudaGraphDestroy(g);
-  h->graph_defs.clear();
+  drop_graphs(h);
   return DG_OK;
 }
 
@@ -1570,13 +1725,114 @@ int dg_node_weights(dg_handle* h, const void* W_dev, void* Wnode_dev, void* stre
 
 int dg_neighbor_table(const dg_handle* h, int32_t* host_out) {
   if (!check_handle(h) || !host_out) return DG_ERR_ARG;
+  if (h->tables_on_device) {
+    const size_t n = (size_t)2 * h->dim * h->ncells;
+    return cudaMemcpy(host_out, h->md.nbr, n * sizeof(int32_t), cudaMemcpyDeviceToHost) == cudaSuccess
+               ? DG_OK : DG_ERR_CUDA;
+  }
   std::memcpy(host_out, h->nbr.data(), h->nbr.size() * sizeof(int32_t));
   return DG_OK;
 }
 
 int dg_cell_levels(const dg_handle* h, int32_t* host_out) {
   if (!check_handle(h) || !host_out) return DG_ERR_ARG;
+  if (h->tables_on_device) {
+    std::vector<int8_t> lv((size_t)h->ncells);
+    if (cudaMemcpy(lv.data(), h->md.level, lv.size(), cudaMemcpyDeviceToHost) != cudaSuccess) return DG_ERR_CUDA;
+    for (int c = 0; c < h->ncells; ++c) host_out[c] = lv[c];
+    return DG_OK;
+  }
   for (int c = 0; c < h->ncells; ++c) host_out[c] = h->level[c];
+  return DG_OK;
+}
+
+int dg_adapt_mark(dg_handle* h, const void* W_dev, double w_t, double alpha, int32_t* flags_host,
+                  int64_t* n_cells_new, int64_t* n_changed, void* stream) {
+  if (!check_handle(h) || !W_dev) return DG_ERR_ARG;
+  if (!(w_t > 0.0) || !(alpha >= 1.0)) return fail(h, DG_ERR_ARG, "dg_adapt_mark: need w_t > 0 and alpha >= 1");
+  std::lock_guard<std::mutex> lock(h->mu);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int r = ensure_adapt(h);
+  if (r != DG_OK) return r;
+  const int cur = h->cur;
+  DG_CUDA(h, cudaMemsetAsync(h->adapt_info, 0, sizeof(int32_t), s));
+  DG_CUDA(h, launch_adapt_criterion(h->bg, W_dev, (int)h->esize, h->N, h->ncells, h->base_first[cur],
+                                    h->base_node[cur], h->tab64 + h->ks->off_pref, alpha * w_t, w_t / alpha,
+                                    h->adapt_crit, s));
+  DG_CUDA(h, launch_adapt_buffer(h->bg, h->adapt_crit, h->base_node[cur], h->adapt_ref, h->adapt_cnt,
+                                 h->adapt_info, s));
+  return finish_mark(h, flags_host, n_cells_new, n_changed, s);
+}
+
+int dg_adapt_set(dg_handle* h, const int32_t* flags_host, int64_t* n_cells_new, int64_t* n_changed,
+                 void* stream) {
+  if (!check_handle(h) || !flags_host) return DG_ERR_ARG;
+  std::lock_guard<std::mutex> lock(h->mu);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int r = ensure_adapt(h);
+  if (r != DG_OK) return r;
+  std::vector<uint8_t> fl((size_t)h->bg.nbase);
+  for (size_t b = 0; b < fl.size(); ++b) fl[b] = flags_host[b] != 0;
+  DG_CUDA(h, cudaMemcpyAsync(h->adapt_ref, fl.data(), fl.size(), cudaMemcpyHostToDevice, s));
+  DG_CUDA(h, cudaMemsetAsync(h->adapt_info, 0, sizeof(int32_t), s));
+  DG_CUDA(h, launch_adapt_counts(h->bg, h->adapt_ref, h->base_node[h->cur], h->adapt_cnt, h->adapt_info, s));
+  return finish_mark(h, nullptr, n_cells_new, n_changed, s);
+}
+
+int dg_regrid(dg_handle* h, const void* W_old_dev, void* W_new_dev, void* stream) {
+  if (!check_handle(h) || !W_old_dev || !W_new_dev) return DG_ERR_ARG;
+  if (W_old_dev == W_new_dev) return fail(h, DG_ERR_ARG, "dg_regrid: W_new must not alias W_old");
+  std::lock_guard<std::mutex> lock(h->mu);
+  if (!h->mark_pending) return fail(h, DG_ERR_ARG, "dg_regrid: no refinement marked");
+  if (h->use_tc && h->next_nodes > 0)
+    return fail(h, DG_ERR_UNSUPPORTED, "dg_regrid: tensor-core precisions need a uniform mesh");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int d = h->dim, cur = h->cur, nxt = 1 - cur;
+  const int nc0 = h->ncells;
+  const int nc1 = (int)h->next_cells, nn1 = (int)h->next_nodes;
+  int r;
+  if ((r = ensure_capacity(h, nc1, -1, nn1)) != DG_OK) return r;
+  const int64_t L = (int64_t)3 * d * nc1;
+  if ((size_t)L + 1 > h->face_cnt_cap) {
+    const size_t cap = (size_t)L + L / 4 + 64;
+    if ((r = realloc_buf(h, h->face_cnt, cap * sizeof(int32_t))) != DG_OK) return r;
+    if ((r = realloc_buf(h, h->face_off, cap * sizeof(int32_t))) != DG_OK) return r;
+    h->face_cnt_cap = cap;
+  }
+  if ((r = ensure_scan_work(h, L)) != DG_OK) return r;
+  MeshDev& m = h->md;
+  auto level = const_cast<int8_t*>(m.level);
+  auto coord = const_cast<int32_t*>(m.coord);
+  auto nbr = const_cast<int32_t*>(m.nbr);
+  auto sface = const_cast<int32_t*>(m.sface);
+  auto scoarse = const_cast<uint8_t*>(m.scoarse);
+  auto children = const_cast<int32_t*>(m.node_children);
+  DG_CUDA(h, launch_regrid_cells(h->bg, h->base_first[nxt], h->base_node[nxt], nc1, level, coord, children, s));
+  DG_CUDA(h, launch_regrid_nbr(h->bg, h->base_first[nxt], h->base_node[nxt], nc1, level, coord, nbr, scoarse,
+                               h->face_cnt, s));
+  DG_CUDA(h, launch_scan(h->face_cnt, L, h->face_off, h->scan_work, s));
+  DG_CUDA(h, launch_adapt_project(h->bg, (int)h->esize, h->nv, h->N, h->tab64 + h->ks->off_pref,
+                                  h->base_first[cur], h->base_node[cur], W_old_dev, nc0, level, coord, nc1,
+                                  W_new_dev, s));
+  int32_t nf1 = 0;
+  DG_CUDA(h, cudaMemcpyAsync(&nf1, h->face_off + L, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  DG_CUDA(h, cudaStreamSynchronize(s));
+  if ((r = ensure_capacity(h, -1, nf1, -1)) != DG_OK) return r;
+  DG_CUDA(h, launch_regrid_faces(h->bg, nc1, level, nbr, children, h->face_off, const_cast<int32_t*>(m.fm),
+                                 const_cast<int32_t*>(m.fp), const_cast<uint8_t*>(m.finfo), sface, s));
+  // the handle now describes the new mesh
+  h->ncells = m.ncells = nc1;
+  h->nfaces = m.nfaces = nf1;
+  h->nnodes = m.nnodes = nn1;
+  h->cur = nxt;
+  h->mark_pending = false;
+  h->tables_on_device = true;
+  drop_graphs(h);
+  // adjoint work arrays are sized for the old mesh: allocated again on use
+  for (void* p : h->adj) dfree(h, p);
+  h->adj.clear();
+  dfree(h, h->FG);
+  h->FG = nullptr;
   return DG_OK;
 }
 

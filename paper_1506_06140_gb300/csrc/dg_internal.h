@@ -209,6 +209,7 @@ struct CombineArgs {
 struct KernelSet {
   int dim = 0, k = 0, prec = 0;
   int N = 0, NV = 0, Q = 0, QF = 0, Q1 = 0, NSUB = 0, NSP = 0, M = 0, tab_size = 0;
+  int off_pref = 0;  // offset of the refinement matrices in the table
   // host: fill the table (double) from 1D Gauss and Lobatto rules
   void (*fill_tables)(std::vector<double>& tab, const std::vector<double>& gx,
                       const std::vector<double>& gw, const std::vector<double>& g3x,
@@ -253,6 +254,50 @@ struct MixedSet {
 };
 
 const MixedSet* mixed_set(int dim, int k);
+
+// ---------------------------------------------------------------------------
+// Mesh adaptation on the device (dg_regrid.cu).  Base cells are numbered
+// lexicographically; first[b] is the first cell of base cell b (first[nbase]
+// = the cell count), node_of[b] its node index or -1 for a leaf.
+struct BaseGrid {
+  int dim = 2, nbase = 0;
+  int n[3] = {1, 1, 1};
+  int periodic[3] = {1, 1, 1};
+};
+
+// criterion per base cell (eqs. cell_ref, node_ref): crit[b] = 1 when the
+// largest density slope weight of the leaf exceeds thr_leaf, or that of the
+// node weights of a node exceeds thr_node
+cudaError_t launch_adapt_criterion(const BaseGrid& g, const void* W, int esize, int N, int ncells,
+                                   const int32_t* first, const int32_t* node_of, const double* P,
+                                   double thr_leaf, double thr_node, uint8_t* crit, cudaStream_t s);
+// one buffer layer: refined[b] = any crit in the 3^d block around b (periodic
+// axes wrap); cnt[b] = cells of base cell b on the new mesh; *changed counts
+// the base cells whose refinement differs from node_of's
+cudaError_t launch_adapt_buffer(const BaseGrid& g, const uint8_t* crit, const int32_t* node_of,
+                                uint8_t* refined, int32_t* cnt, int32_t* changed, cudaStream_t s);
+// cnt[b] from given flags (refined[b] != 0), with the same change count
+cudaError_t launch_adapt_counts(const BaseGrid& g, const uint8_t* refined, const int32_t* node_of,
+                                int32_t* cnt, int32_t* changed, cudaStream_t s);
+// out[i] = sum_{j<i} in[j] for i <= n (out[n] = the total); work: scan_work_ints(n) ints
+cudaError_t launch_scan(const int32_t* in, int64_t n, int32_t* out, int32_t* work, cudaStream_t s);
+size_t scan_work_ints(int64_t n);
+// cell tables of the new mesh from first[] (node_of[] is derived and written)
+cudaError_t launch_regrid_cells(const BaseGrid& g, const int32_t* first, int32_t* node_of, int ncells,
+                                int8_t* level, int32_t* coord, int32_t* node_children, cudaStream_t s);
+// neighbour table and coarse-side bits; face counts per (axis, cell) then per
+// (axis, cell, side) in the numbering of the host mesh builder
+cudaError_t launch_regrid_nbr(const BaseGrid& g, const int32_t* first, const int32_t* node_of, int ncells,
+                              const int8_t* level, const int32_t* coord, int32_t* nbr, uint8_t* scoarse,
+                              int32_t* face_cnt, cudaStream_t s);
+cudaError_t launch_regrid_faces(const BaseGrid& g, int ncells, const int8_t* level, const int32_t* nbr,
+                                const int32_t* node_children, const int32_t* face_off, int32_t* fm,
+                                int32_t* fp, uint8_t* finfo, int32_t* sface, cudaStream_t s);
+// the state on the new mesh (Secs. 4.4, 4.5): copy, P_c w, or 2^-d sum_c P_c^T w^c
+cudaError_t launch_adapt_project(const BaseGrid& g, int esize, int nv, int N, const double* P,
+                                 const int32_t* first0, const int32_t* node0, const void* Wold, int ncells0,
+                                 const int8_t* level1, const int32_t* coord1, int ncells1, void* Wnew,
+                                 cudaStream_t s);
 
 // shared helper kernels (dg_common.cu)
 cudaError_t launch_set_scalar(double* dst, int n, double value, cudaStream_t s);

@@ -932,6 +932,7 @@ KernelSet make_kernel_set(int prec) {
   ks.NSP = S::NSP;
   ks.M = S::M;
   ks.tab_size = S::TAB_SIZE;
+  ks.off_pref = S::OFF_PREF;
   ks.fill_tables = &fill_tables<DIM, K>;
   ks.prepare = &prepare_kernels<real, DIM, K>;
   ks.cell_tile = CellTile<real, DIM, K>::TC;

@@ -25,7 +25,7 @@ EXPORTS = ["dg_default_options", "dg_create", "dg_destroy", "dg_last_error", "dg
            "dg_l1_density", "dg_node_weights", "dg_neighbor_table", "dg_cell_levels",
            "dg_status", "dg_profile_begin", "dg_profile_end", "dg_totals_noalloc",
            "dg_create_batch", "dg_batch_advance", "dg_n_problems", "dg_tiles",
-           "dg_limiter_counts", "dg_set_tiles"]
+           "dg_limiter_counts", "dg_set_tiles", "dg_adapt_mark", "dg_adapt_set", "dg_regrid"]
 KERNEL_KINDS = ["face", "cell", "limit", "dt", "other", "adjoint"]
 
 
@@ -88,6 +88,10 @@ def load(path=LIB_PATH):
     L.dg_n_problems.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int64)]
     L.dg_totals_noalloc.argtypes = [C.c_int, C.c_int, C.c_int64, C.c_int, C.c_double, vp, vp,
                                      vp, vp]
+    i64p = C.POINTER(C.c_int64)
+    L.dg_adapt_mark.argtypes = [vp, vp, C.c_double, C.c_double, i32p, i64p, i64p, vp]
+    L.dg_adapt_set.argtypes = [vp, i32p, i64p, i64p, vp]
+    L.dg_regrid.argtypes = [vp, vp, vp, vp]
     L.dg_profile_begin.argtypes = [vp]
     L.dg_profile_end.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_int]
     for name in EXPORTS:
@@ -172,11 +176,9 @@ class Solver:
         if r != DG_OK:
             raise DGError(r, L.dg_last_error(None).decode())
         self._h = h
-        nc, N, nv, nq, nq1, nn = C.c_int64(), C.c_int(), C.c_int(), C.c_int(), C.c_int(), C.c_int()
-        self._check(L.dg_sizes(h, C.byref(nc), C.byref(N), C.byref(nv), C.byref(nq),
-                               C.byref(nq1), C.byref(nn)))
-        self.n_cells, self.N, self.nv = nc.value, N.value, nv.value
-        self.nq, self.nq1, self.n_nodes = nq.value, nq1.value, nn.value
+        self._next_cells = None
+        self._sizes()
+        self.n_base = int(np.prod([int(self.mesh["n"][a]) for a in range(self.dim)]))
         self.device = torch.device("cuda", torch.cuda.current_device())
         npb = C.c_int()
         self._check(L.dg_n_problems(h, C.byref(npb), None))
@@ -184,6 +186,15 @@ class Solver:
         offs = (C.c_int64 * (self.n_problems + 1))()
         self._check(L.dg_n_problems(h, C.byref(npb), offs))
         self.cell_offsets = np.array(offs[:], dtype=np.int64)
+
+    def _sizes(self):
+        nc, N, nv, nq, nq1, nn = C.c_int64(), C.c_int(), C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        self._check(self._L.dg_sizes(self._h, C.byref(nc), C.byref(N), C.byref(nv), C.byref(nq),
+                                     C.byref(nq1), C.byref(nn)))
+        self.n_cells, self.N, self.nv = nc.value, N.value, nv.value
+        self.nq, self.nq1, self.n_nodes = nq.value, nq1.value, nn.value
+        if hasattr(self, "cell_offsets"):
+            self.cell_offsets = np.array([0, self.n_cells], dtype=np.int64)
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -288,6 +299,58 @@ class Solver:
     def levels(self):
         out = np.zeros(self.n_cells, np.int32)
         self._check(self._L.dg_cell_levels(self._h, out.ctypes.data_as(C.POINTER(C.c_int32))))
+        return out
+
+    # -- mesh adaptation (single problems) --
+    def adapt_mark(self, W, w_t=0.01, alpha=1.1, flags=False):
+        """Decide the next refinement from W (dg_adapt_mark): returns
+        (cells of the next mesh, base cells that change[, int32 flags per base cell])."""
+        nc, ch = C.c_int64(), C.c_int64()
+        fl = np.zeros(self.n_base, np.int32) if flags else None
+        fp = fl.ctypes.data_as(C.POINTER(C.c_int32)) if flags else None
+        self._check(self._L.dg_adapt_mark(self._h, self._state(W), float(w_t), float(alpha), fp,
+                                          C.byref(nc), C.byref(ch), _stream()))
+        self._next_cells = nc.value
+        return (nc.value, ch.value, fl) if flags else (nc.value, ch.value)
+
+    def set_refinement(self, flags):
+        """Mark the next refinement explicitly (nonzero = refined base cell)."""
+        fl = np.ascontiguousarray(np.asarray(flags, dtype=np.int32).reshape(-1))
+        assert fl.size == self.n_base
+        nc, ch = C.c_int64(), C.c_int64()
+        self._check(self._L.dg_adapt_set(self._h, fl.ctypes.data_as(C.POINTER(C.c_int32)),
+                                         C.byref(nc), C.byref(ch), _stream()))
+        self._next_cells = nc.value
+        return nc.value, ch.value
+
+    def regrid(self, W_old, out=None):
+        """Move to the marked mesh; returns the state projected onto it."""
+        assert self._next_cells is not None, "no refinement marked"
+        shape = (self.nv, self.N, self._next_cells)
+        W_new = torch.empty(shape, dtype=self.dtype, device=self.device) if out is None else out
+        assert W_new.is_cuda and W_new.is_contiguous() and W_new.dtype == self.dtype
+        assert tuple(W_new.shape) == shape
+        self._check(self._L.dg_regrid(self._h, self._state(W_old), _ptr(W_new), _stream()))
+        self._next_cells = None
+        self._sizes()
+        return W_new
+
+    def adapt(self, W, w_t=0.01, alpha=1.1):
+        """One adaptation after a step (Sec. 4): returns (state on the adapted
+        mesh, base cells changed); W itself is returned when nothing changes."""
+        nc, changed = self.adapt_mark(W, w_t, alpha)
+        if changed == 0:
+            return W, 0
+        return self.regrid(W), changed
+
+    def refinement(self):
+        """int32 flag per base cell of the current mesh (1 refined)"""
+        lv = self.levels()
+        out = np.zeros(self.n_base, np.int32)
+        c, nch = 0, 1 << self.dim
+        for b in range(self.n_base):
+            out[b] = lv[c]
+            c += nch if lv[c] else 1
         return out
 
     def profile_begin(self):
