@@ -66,6 +66,16 @@ WORKLOADS = {
              "FP32 state with FP64 totals / positivity check",
         dim=3, k=2, rk=3, stages=3, limiter="characteristic", positivity=True,
         precisions=("fp32",), tag="sedov3d_k2", autotune=True),
+    "kh2d_amr": dict(
+        name="Kelvin-Helmholtz 2D (rho 2|1, v_x +-0.5, p 2.5, single-mode v_y seed), periodic [0,1]^2, "
+             "1024^2 base cells + one dynamic refinement level (effective 2048^2), k=3 (10 coeffs/cell/var), "
+             "SSP-RK4 (5 stages), characteristic TVB limiter + positivity limiter, CFL 0.2; mesh adapted "
+             "after every step (w_t 0.01, alpha 1.1, one buffer layer); a step = RK step + adaptation; "
+             "timed from t = 0.003 (untimed adaptive pre-run from the initial data: the interfaces, "
+             "aligned with cell faces at t = 0, carry slopes once the v_y seed has moved them)",
+        dim=2, k=3, rk=4, stages=5, limiter="characteristic", positivity=True,
+        precisions=("fp64", "mixed"), tag="kh1024_amr_k3", amr=True, base=1024, w_t=0.01, alpha=1.1,
+        t_pre=0.003),
 }
 
 
@@ -75,6 +85,8 @@ def workload_config(wk, precision, cells):
           else "flushed between timed steps (256 MiB write)")
     if wk in ("wave2d", "square64"):
         l2 = "L2-resident state (launch-bound workload); timed steps in one graph launch"
+    if W.get("amr"):
+        l2 = "state larger than L2 (no flush); steps launched one by one (the adaptation reads sizes back)"
     return {"workload": W["name"], "cells": cells, "k": W["k"], "rk_stages": W["stages"],
             "precision": precision, "l2": l2}
 
@@ -100,6 +112,9 @@ def make_problem(wk, precision, autotune=None):
         probs = wl.ensemble_problems()
         m = [wl.mesh_uniform(2, [n, n], [-5.0, -5.0], [5.0, 5.0]) for n, _ in probs]
         ic = None
+    elif wk == "kh2d_amr":
+        n = W["base"]
+        m, ic = wl.mesh_uniform(2, [n, n], [0.0, 0.0], [1.0, 1.0]), wl.kelvin_helmholtz
     else:
         m, ic = wl.mesh_two_level_3d(64, 16, 47), wl.sedov3d
     if autotune is None:
@@ -399,6 +414,144 @@ def run_gpu(args, rank, world, local_rank):
     return results
 
 
+def run_gpu_amr(args, rank, world, local_rank):
+    """Steps of an adaptive run: one RK step, then the adaptation of the mesh
+    (criterion, buffer layer, regrid where anything changed), as in the main
+    loop of Sec. 4.  Both halves are timed with CUDA events on the launching
+    stream; the adaptation's host round trips (sizes read back) are inside."""
+    import torch
+    torch.cuda.set_device(local_rank)
+    ranks = Ranks(world, "nccl", "cuda", local_rank)
+    wk = WORKLOADS[args.workload]
+    results = {}
+    for precision in args.precisions:
+        s, W0 = make_problem(args.workload, precision)
+        stream = torch.cuda.current_stream()
+
+        def one_step(W, ev=None):
+            cells = s.n_cells
+            if ev:
+                ev[0].record(stream)
+            s.rk_step(W)
+            if ev:
+                ev[1].record(stream)
+            W, changed = s.adapt(W, wk["w_t"], wk["alpha"])
+            if ev:
+                ev[2].record(stream)
+            return W, cells, changed
+
+        W = W0
+        # adaptive pre-run to t_pre (outside the timed steps); each adaptation
+        # is timed, split into steps that regridded and steps that only checked
+        t, pre_steps, dt_buf = 0.0, 0, s.scalar()
+        pre = {"regrid": [], "check": []}
+        while t < wk.get("t_pre", 0.0):
+            s.rk_step(W, 0.0, dt_buf)
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            W, changed = s.adapt(W, wk["w_t"], wk["alpha"])
+            a1.record(stream)
+            t += dt_buf.item()  # synchronises
+            pre["regrid" if changed else "check"].append((a0.elapsed_time(a1), changed, s.n_cells))
+            pre_steps += 1
+        with ClockSampler(local_rank) as clk:
+            for _ in range(args.warmup):
+                W, _, _ = one_step(W)
+            s.limiter_counts(reset=True)
+            t_start = s.totals(W).cpu().numpy()
+            torch.cuda.synchronize()
+            ranks.barrier()
+            s.profile_begin()
+            evs, cells, changes = [], [], []
+            for _ in range(args.steps):
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+                W, c, ch = one_step(W, ev)
+                evs.append(ev)
+                cells.append(c)
+                changes.append(ch)
+            torch.cuda.synchronize()
+        prof = s.profile_end()
+        step_ms = sum(e[0].elapsed_time(e[1]) for e in evs)
+        adapt_ms = sum(e[1].elapsed_time(e[2]) for e in evs)
+        ms = ranks.max(step_ms + adapt_ms)
+        assert torch.isfinite(W).all().item(), "non-finite state"
+        regrids = sum(1 for c in changes if c > 0)
+        cnt = s.limiter_counts(reset=True).cpu().numpy()
+        passes = sum(cells) * wk["stages"]
+        t_end = s.totals(W).cpu().numpy()
+        nbase = wk["base"] ** 2
+        rg = pre["regrid"]
+        diag = {"pre_run_steps": pre_steps, "t_pre": t, "pre_run_regrids": len(rg),
+                "pre_run_regrid_adapt_ms_mean": sum(x[0] for x in rg) / max(len(rg), 1),
+                "pre_run_regrid_base_cells_changed_mean": sum(x[1] for x in rg) / max(len(rg), 1),
+                "pre_run_check_adapt_ms_mean": sum(x[0] for x in pre["check"]) / max(len(pre["check"]), 1),
+                "cells_min": min(cells), "cells_max": max(cells), "cells_mean": sum(cells) / len(cells),
+                "refined_base_fraction_mean": (sum(cells) / len(cells) - nbase) / (3.0 * nbase),
+                "base_cells_changed_per_step": sum(changes) / len(changes),
+                "regrids": regrids, "rk_step_ms": step_ms / args.steps,
+                "adapt_ms": adapt_ms / args.steps, "adapt_share": adapt_ms / (step_ms + adapt_ms),
+                "slope_limited_fraction": float(cnt[0]) / passes,
+                "positivity_limited_fraction": float(cnt[1]) / passes,
+                "mass_drift_rel_over_timed_steps": float(abs(t_end[0] - t_start[0]) / abs(t_start[0])),
+                "energy_drift_rel_over_timed_steps": float(abs(t_end[-1] - t_start[-1]) / abs(t_start[-1]))}
+        # end to end through the C ABI: each step's input state from pinned host
+        # memory, the adapted state back to it
+        Wh = torch.empty(2 * W.numel(), dtype=W.dtype).pin_memory()
+        Wh[:W.numel()].copy_(W.view(-1))
+        moved = 0
+        torch.cuda.synchronize()
+        ranks.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            n_in = W.numel()
+            W.view(-1).copy_(Wh[:n_in], non_blocking=True)
+            W, _, _ = one_step(W)
+            assert W.numel() <= Wh.numel()
+            Wh[:W.numel()].copy_(W.view(-1), non_blocking=True)
+            moved += (n_in + W.numel()) * W.element_size()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_e2e = ranks.max(e0.elapsed_time(e1))
+        # kernels of the adaptation: criterion + buffer + 3 scan passes per
+        # step, cells + neighbours + 3 scan passes + projection + faces per regrid
+        extra = 5 * args.steps + 7 * regrids
+        results[precision] = dict(solver=s, ms=ms, ms_e2e=ms_e2e, prof=prof, clocks=clk.summary(),
+                                  state_bytes=moved // (2 * args.steps), n_cells=sum(cells) / len(cells),
+                                  tiles=None, diag=diag, extra_launches=extra)
+        del W, W0, Wh
+    return results
+
+
+def cpu_baseline_kh(max_seconds=20.0, n_base=64):
+    """The oracle on a bounded sample of the adaptive KH run: a 64^2 base grid
+    (same k, RK order, limiters, adaptation after every step)."""
+    from oracle import pyoracle as O
+    from paper_1506_06140_gb300 import workloads as wl
+    wk = WORKLOADS["kh2d_amr"]
+
+    def make(boxes):
+        return O.Oracle(2, [n_base, n_base], [0.0, 0.0], [1.0, 1.0], wk["k"], 1.4, refine_boxes=boxes,
+                        rk_order=wk["rk"], cfl=CFL, limiter=O.LIM_CHARACTERISTIC, positivity=True)
+    o = make([])
+    W = o.limit(o.project(wl.kelvin_helmholtz(o.quad_points())))
+    t0 = time.perf_counter()
+    steps, dof = 0, 0
+    while time.perf_counter() - t0 < max_seconds / 2 and steps < 200:
+        dof += o.n_cells * N_BASIS * wk["stages"]
+        W, _ = o.rk_step(W, 0.0)
+        flags = o.adapt_flags(W, wk["w_t"], wk["alpha"])
+        boxes = [[b % n_base, b // n_base] * 2 for b in np.nonzero(flags)[0]]
+        o1 = make(boxes)
+        W, o = o1.adapt_project(o, W), o1
+        steps += 1
+    sec = time.perf_counter() - t0
+    return {"value": dof / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d adaptive steps (RK4 step + adaptation) of the KH run on a %d^2 base grid, k=3, "
+                      "characteristic + positivity limiters (single-threaded FP64 C++ oracle)"
+                      % (steps, n_base), "seconds": sec}
+
+
 def summarize(args, results, world):
     hbm, peak_kind = peaks()
     wk = WORKLOADS[args.workload]
@@ -410,7 +563,7 @@ def summarize(args, results, world):
         dof_updates = world * cells * N * stages * args.steps
         value = dof_updates / (r["ms"] * 1e-3)
         prof = r["prof"]
-        launches = sum(c for c, _ in prof.values())
+        launches = sum(c for c, _ in prof.values()) + r.get("extra_launches", 0)
         # roofline of the dominant kernel of the timed region
         kind = max(prof, key=lambda kk: prof[kk][1])
         n_launch, kms = prof[kind]
@@ -709,10 +862,28 @@ def main():
     from paper_1506_06140_gb300 import build
     if rank == 0 or not os.path.exists(build.LIB):
         build.build()
-    results = run_gpu(args, rank, world, local_rank)
+    amr = WORKLOADS[args.workload].get("amr", False)
+    results = (run_gpu_amr if amr else run_gpu)(args, rank, world, local_rank)
     if rank != 0:
         return 0
     lines = summarize(args, results, world)
+    if amr and len(lines) > 1:
+        head_p = args.precisions[0]
+        head = lines[head_p]
+        out = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+               "data": "synthetic", "config": workload_config(args.workload, head_p, head["cells"]),
+               "diagnostics": head["diagnostics"]}
+        out.update({kk: head[kk] for kk in ("roofline", "e2e", "gpu_launches", "clocks", "kernel_ms")})
+        out["variants"] = {p: {kk: lines[p][kk] for kk in ("value", "ms_per_step", "roofline", "e2e",
+                                                           "gpu_launches", "clocks", "kernel_ms",
+                                                           "diagnostics")}
+                           for p in args.precisions[1:]}
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline_kh()
+        print(json.dumps(out), flush=True)
+        return 0
     if args.workload != "vortex" or len(lines) == 1:
         prec = args.precisions[0]
         one = lines[prec]

@@ -287,17 +287,17 @@ __global__ void faces_kernel(const BaseGrid g, int nc, const int8_t* __restrict_
   }
 }
 
-// one thread per output weight W_new[v][j][c]
+// one thread per output weight W_new[v][j][c]: blockIdx.y = v * N + j, cells along x
 template <typename real>
-__global__ void project_kernel(const BaseGrid g, int nv, int N, const double* __restrict__ P,
+__global__ void project_kernel(const BaseGrid g, int N, const double* __restrict__ P,
                                const int32_t* __restrict__ first0, const int32_t* __restrict__ node0,
                                const real* __restrict__ Wold, int nc0, const int8_t* __restrict__ level1,
                                const int32_t* __restrict__ coord1, int nc1, real* __restrict__ Wnew) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)nv * N * nc1) return;
-  const int c = (int)(idx % nc1);
-  const int vj = (int)(idx / nc1);
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc1) return;
+  const int vj = blockIdx.y;
   const int v = vj / N, j = vj % N;
+  const size_t idx = (size_t)vj * nc1 + c;
   const int d = g.dim, nch = 1 << d;
   const int l = level1[c];
   const int p[3] = {coord1[c], coord1[(size_t)nc1 + c], coord1[(size_t)2 * nc1 + c]};
@@ -394,16 +394,16 @@ cudaError_t launch_adapt_project(const BaseGrid& g, int esize, int nv, int N, co
                                  const int32_t* first0, const int32_t* node0, const void* Wold, int ncells0,
                                  const int8_t* level1, const int32_t* coord1, int ncells1, void* Wnew,
                                  cudaStream_t s) {
-  const int64_t n = (int64_t)nv * N * ncells1;
-  if (n == 0) return cudaSuccess;
+  if (ncells1 == 0) return cudaSuccess;
+  const dim3 grid(grid_for(ncells1), nv * N);
   if (esize == 8)
-    project_kernel<double><<<grid_for(n), RG_THREADS, 0, s>>>(g, nv, N, P, first0, node0,
-                                                              static_cast<const double*>(Wold), ncells0, level1,
-                                                              coord1, ncells1, static_cast<double*>(Wnew));
+    project_kernel<double><<<grid, RG_THREADS, 0, s>>>(g, N, P, first0, node0, static_cast<const double*>(Wold),
+                                                       ncells0, level1, coord1, ncells1,
+                                                       static_cast<double*>(Wnew));
   else
-    project_kernel<float><<<grid_for(n), RG_THREADS, 0, s>>>(g, nv, N, P, first0, node0,
-                                                             static_cast<const float*>(Wold), ncells0, level1,
-                                                             coord1, ncells1, static_cast<float*>(Wnew));
+    project_kernel<float><<<grid, RG_THREADS, 0, s>>>(g, N, P, first0, node0, static_cast<const float*>(Wold),
+                                                      ncells0, level1, coord1, ncells1,
+                                                      static_cast<float*>(Wnew));
   return cudaGetLastError();
 }
 

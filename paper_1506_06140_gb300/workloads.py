@@ -80,6 +80,20 @@ def square2d(xyz, gamma=1.4, rho_in=4.0, rho_out=1.0, p=2.5, vel=(100.0, 50.0), 
     return conserved(rho, vel, np.full_like(rho, p), gamma)
 
 
+def kelvin_helmholtz(xyz, gamma=1.4, w0=0.1, sigma=0.05 / np.sqrt(2.0)):
+    """Kelvin-Helmholtz initial data (Sec. 5.6) on the periodic
+    unit box: a dense band 0.25 < y < 0.75 (rho 2, v_x 0.5) in a lighter
+    medium (rho 1, v_x -0.5), p = 2.5 everywhere, and a single-mode v_y
+    perturbation w0 sin(4 pi x) localised at both interfaces with width sigma."""
+    x, y = xyz[0], xyz[1]
+    band = (y > 0.25) & (y < 0.75)
+    rho = np.where(band, 2.0, 1.0)
+    vx = np.where(band, 0.5, -0.5)
+    env = np.exp(-(y - 0.25) ** 2 / (2 * sigma ** 2)) + np.exp(-(y - 0.75) ** 2 / (2 * sigma ** 2))
+    vy = w0 * np.sin(4 * np.pi * x) * env
+    return conserved(rho, [vx, vy], np.full_like(rho, 2.5), gamma)
+
+
 def sod(xyz, gamma=1.4, x0=0.5):
     x = xyz[0]
     left = x < x0
