@@ -43,6 +43,10 @@ void orc_l1_points(const orc_problem* p, double* xyz);
 void orc_project(const orc_problem* p, const double* u_q, double* W);
 void orc_rhs(const orc_problem* p, const double* W, double* dWdt);
 double orc_compute_dt(const orc_problem* p, const double* W);
+/* external acceleration a = -grad Phi at the volume points, [dim][Q][cells]
+   (copied); NULL removes it.  Adds the gravity source (eq. gravity_term) to the
+   right-hand side and the gravity bound (Sec. 2.5) to the timestep. */
+void orc_set_accel(orc_problem* p, const double* accel);
 double orc_rk_step(const orc_problem* p, double* W, double dt);
 void orc_slope_limit(const orc_problem* p, double* W);
 void orc_positivity_limit(const orc_problem* p, double* W);

@@ -74,6 +74,14 @@ void orc_l1_points(const orc_problem* p, double* xyz) { p->P.rule_points(p->P.l1
 void orc_project(const orc_problem* p, const double* u_q, double* W) { p->P.project(u_q, W); }
 void orc_rhs(const orc_problem* p, const double* W, double* dWdt) { p->P.rhs(W, dWdt); }
 double orc_compute_dt(const orc_problem* p, const double* W) { return p->P.compute_dt(W); }
+void orc_set_accel(orc_problem* p, const double* accel) {
+  auto& P = p->P;
+  if (!accel) {
+    P.accel.clear();
+    return;
+  }
+  P.accel.assign(accel, accel + (size_t)P.dim * P.vol.n * P.mesh.ncells);
+}
 double orc_rk_step(const orc_problem* p, double* W, double dt) { return p->P.rk_step(W, dt); }
 void orc_slope_limit(const orc_problem* p, double* W) { p->P.slope_limit(W); }
 void orc_positivity_limit(const orc_problem* p, double* W) { p->P.positivity_limit(W); }

@@ -47,6 +47,7 @@ def lib():
         L.orc_rhs.argtypes = [C.c_void_p, _D, _D]
         L.orc_compute_dt.restype = C.c_double
         L.orc_compute_dt.argtypes = [C.c_void_p, _D]
+        L.orc_set_accel.argtypes = [C.c_void_p, C.c_void_p]
         L.orc_rk_step.restype = C.c_double
         L.orc_rk_step.argtypes = [C.c_void_p, _D, C.c_double]
         for name in ("orc_slope_limit", "orc_positivity_limit", "orc_limit"):
@@ -172,6 +173,16 @@ class Oracle:
         out = np.zeros(self.shape)
         lib().orc_rhs(self._h, _d(W), _d(out))
         return out
+
+    def set_accel(self, accel):
+        """external acceleration [dim][Q][cells] at quad_points() (None removes it)"""
+        if accel is None:
+            lib().orc_set_accel(self._h, None)
+            self._accel = None
+            return
+        self._accel = _f64(accel)
+        assert self._accel.shape == (self.dim, self.nq, self.n_cells)
+        lib().orc_set_accel(self._h, self._accel.ctypes.data_as(C.c_void_p))
 
     def compute_dt(self, W):
         W = _f64(W)

@@ -115,6 +115,9 @@ struct Problem {
   std::vector<double> Pref;      // refinement matrices [child][j][l]
   std::vector<std::array<double, 3>> Spts;  // union point set S (eq. union_quad_points)
   Tableau tb;
+  // external acceleration a = -grad Phi at the volume points, [a][q][cell];
+  // empty: no gravity (eq. gravity_term)
+  std::vector<double> accel;
 
   size_t idx(int v, int l, int c) const { return ((size_t)v * N + l) * mesh.ncells + c; }
   size_t size() const { return (size_t)nv * N * mesh.ncells; }
@@ -300,10 +303,40 @@ struct Problem {
           }
         }
     }
+    std::vector<T> G(accel.empty() ? 0 : size(), T(0.0));
+    if (!accel.empty())
+      for (int c = 0; c < nc; ++c) source_moments(W, c, &G[0], nc);
     for (int c = 0; c < nc; ++c) {
       const double pre = std::ldexp(1.0, 1 - dim) / mesh.dx(c);
       for (int v = 0; v < nv; ++v)
-        for (int j = 0; j < N; ++j) dW[idx(v, j, c)] = pre * (V[idx(v, j, c)] - S[idx(v, j, c)]);
+        for (int j = 0; j < N; ++j) {
+          dW[idx(v, j, c)] = pre * (V[idx(v, j, c)] - S[idx(v, j, c)]);
+          if (!accel.empty()) dW[idx(v, j, c)] += std::ldexp(1.0, -dim) * G[idx(v, j, c)];
+        }
+    }
+  }
+
+  // Gravity source (eq. gravity_term): s = (0, rho a, m . a) with a = -grad Phi,
+  // projected with the volume rule, sum_q s(u_q) phi_j(xi_q) w_q; the moment of
+  // cell c goes to out[(v * N + j) * stride + c] (the caller scales it by
+  // 2^-d = |K|^-1 (dx/2)^d).
+  template <class T>
+  void source_moments(const T* W, int c, T* out, int stride) const {
+    T u[5];
+    const int nc = mesh.ncells;
+    for (int q = 0; q < vol.n; ++q) {
+      eval(W, c, &phi_vol[(size_t)q * N], u);
+      T s[5];
+      s[0] = T(0.0);
+      s[nv - 1] = T(0.0);
+      for (int a = 0; a < dim; ++a) {
+        const double aq = accel[((size_t)a * vol.n + q) * nc + c];
+        s[1 + a] = u[0] * aq;
+        s[nv - 1] = s[nv - 1] + u[1 + a] * aq;
+      }
+      for (int v = 0; v < nv; ++v)
+        for (int j = 0; j < N; ++j)
+          out[((size_t)v * N + j) * stride + c] += s[v] * (phi_vol[(size_t)q * N + j] * vol.w[q]);
     }
   }
 
@@ -373,6 +406,12 @@ struct Problem {
       }
     const double pre = std::ldexp(1.0, 1 - dim) / mesh.dx(c);
     for (size_t i = 0; i < V.size(); ++i) out[i] = pre * (V[i] - S[i]);
+    if (!accel.empty()) {
+      std::vector<double> G((size_t)nv * N * nc, 0.0);
+      source_moments(W, c, G.data(), nc);
+      for (int v = 0; v < nv; ++v)
+        for (int j = 0; j < N; ++j) out[(size_t)v * N + j] += std::ldexp(1.0, -dim) * G[((size_t)v * N + j) * nc + c];
+    }
   }
 
   // Timestep (eq. time_step; eq. time_step_pos when the positivity limiter
@@ -389,6 +428,20 @@ struct Problem {
       double sum = 0.0;
       for (int a = 0; a < dim; ++a) sum += (std::fabs(u[1 + a] / u[0]) + cs) / mesh.dx(c);
       dt = std::min(dt, fac / sum);
+      if (!accel.empty()) {
+        // gravity bound (Sec. 2.5): c / (sqrt(2 gamma (gamma - 1)) |grad Phi|),
+        // with the largest |a| over the cell's volume points
+        double amax = 0.0;
+        for (int q = 0; q < vol.n; ++q) {
+          double a2 = 0.0;
+          for (int a = 0; a < dim; ++a) {
+            const double aq = accel[((size_t)a * vol.n + q) * mesh.ncells + c];
+            a2 += aq * aq;
+          }
+          amax = std::max(amax, std::sqrt(a2));
+        }
+        if (amax > 0.0) dt = std::min(dt, cs / (std::sqrt(2.0 * gamma * (gamma - 1.0)) * amax));
+      }
     }
     return dt;
   }

@@ -94,6 +94,42 @@ def kelvin_helmholtz(xyz, gamma=1.4, w0=0.1, sigma=0.05 / np.sqrt(2.0)):
     return conserved(rho, [vx, vy], np.full_like(rho, 2.5), gamma)
 
 
+def keplerian_disc(xyz, gamma=5.0 / 3.0, rho0=1e-5, p0=1e-5, rho_d=1.0, r_in=0.5, r_out=2.0, dr=0.1,
+                   center=(3.0, 3.0)):
+    """Cold Keplerian disc (Sec. 5.5) in the periodic box [0,6]^2: density
+    rho_d between r_in and r_out with linear ramps of width dr to the
+    background rho0, uniform pressure p0, Keplerian rotation
+    v = (-y', x') / r'^(3/2) for r_in - 2 dr < r' < r_out + 2 dr, at rest
+    elsewhere (primed coordinates from the box centre)."""
+    x, y = xyz[0] - center[0], xyz[1] - center[1]
+    r = np.sqrt(x * x + y * y)
+    a0, a1 = r_in - dr / 2, r_in + dr / 2
+    b0, b1 = r_out - dr / 2, r_out + dr / 2
+    rho = np.full_like(r, rho0)
+    ramp_in = (r >= a0) & (r < a1)
+    rho = np.where(ramp_in, (rho_d - rho0) / dr * (r - a0) + rho0, rho)
+    rho = np.where((r >= a1) & (r < b0), rho_d, rho)
+    ramp_out = (r >= b0) & (r < b1)
+    rho = np.where(ramp_out, (rho0 - rho_d) / dr * (r - b0) + rho_d, rho)
+    rotating = (r > r_in - 2 * dr) & (r < r_out + 2 * dr)
+    rs = np.where(rotating, r, 1.0)
+    vx = np.where(rotating, -y / rs ** 1.5, 0.0)
+    vy = np.where(rotating, x / rs ** 1.5, 0.0)
+    return conserved(rho, [vx, vy], np.full_like(r, p0), gamma)
+
+
+def keplerian_accel(xyz, r_in=0.5, dr=0.1, eps=0.25, center=(3.0, 3.0)):
+    """External acceleration a = -grad Phi of the Keplerian disc (Sec. 5.5):
+    -x'/r'^3 outside r_in - dr/2, softened to -x'/[r' (r'^2 + eps^2)] inside.
+    Returns [2][...] like xyz."""
+    x, y = xyz[0] - center[0], xyz[1] - center[1]
+    r = np.sqrt(x * x + y * y)
+    rs = np.where(r > 0, r, 1.0)
+    g = np.where(r > r_in - dr / 2, 1.0 / rs ** 3, 1.0 / (rs * (rs * rs + eps * eps)))
+    g = np.where(r > 0, g, 0.0)
+    return np.stack([-x * g, -y * g])
+
+
 def sod(xyz, gamma=1.4, x0=0.5):
     x = xyz[0]
     left = x < x0
