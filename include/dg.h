@@ -237,6 +237,20 @@ int dg_l1_density(dg_handle* h, const void* W_dev, const double* rho_ref_dev, do
  * refined base cell (eq. deref_weights) -> Wnode_dev [nv][N][node]. */
 int dg_node_weights(dg_handle* h, const void* W_dev, void* Wnode_dev, void* stream);
 
+/* Gravity (eq. gravity_term, Sec. 2.4; timestep Sec. 2.5): sets the external
+ * acceleration a = -grad Phi, given at the volume points of every cell in the
+ * order of dg_quad_points as accel_dev double [dim][Q][cell] (device; read on
+ * `stream`, copied into the handle in its state precision).  While set, every
+ * right-hand side adds the source s = (0, rho a, m . a) projected with the
+ * volume Gauss rule, 2^-dim sum_q s(u_q) phi_j(xi_q) w_q, and the timestep is
+ * the smaller of the hydro bound and c / (sqrt(2 gamma (gamma - 1)) |a|) per
+ * cell (c of the cell mean, |a| the largest over the cell's points; no CFL
+ * factor on this bound).  NULL removes the field.  DG_FP64 and DG_FP32 single
+ * problems only (DG_ERR_UNSUPPORTED otherwise); dg_regrid drops the field and
+ * the stepping calls return DG_ERR_ARG until it is set again; the adjoint
+ * refuses a handle with gravity. */
+int dg_set_gravity(dg_handle* h, const double* accel_dev, void* stream);
+
 /* ---- Mesh adaptation of the two-level mesh (Secs. 4.1, 4.3-4.5) ----
  * Single problems with k >= 1 only (DG_ERR_UNSUPPORTED otherwise); the tensor-core
  * precisions keep their uniform-mesh restriction (dg_regrid refuses a mesh

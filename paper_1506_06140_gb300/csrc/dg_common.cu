@@ -1,4 +1,5 @@
 // Small helper kernels shared by all schemes, and the kernel-set dispatch.
+#include <algorithm>
 #include <mutex>
 
 #include "dg_internal.h"
@@ -77,6 +78,19 @@ __global__ void dt_finalize_kernel(const unsigned long long* bits, int nprob, do
     dt[p] = v;
     if (dt_copy) dt_copy[p] = v;
   }
+}
+
+__global__ void convert_kernel(const double* __restrict__ src, float* __restrict__ dst, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = (float)src[i];
+}
+
+cudaError_t launch_convert(const double* src, void* dst, size_t n, int esize, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  if (esize == 8) return cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  const size_t blocks = std::min<size_t>((n + 255) / 256, 152 * 16);
+  convert_kernel<<<(unsigned)blocks, 256, 0, s>>>(src, static_cast<float*>(dst), n);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_dt_finalize(const unsigned long long* bits, int nprob, double factor,

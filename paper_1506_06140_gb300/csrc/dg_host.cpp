@@ -455,6 +455,9 @@ struct dg_handle {
   int64_t next_cells = 0, next_nodes = 0;
   size_t cap_cells = 0, cap_faces = 0, cap_nodes = 0;  // capacity of the mesh-sized buffers
   bool tables_on_device = false;   // host mirrors are stale after a regrid
+  // gravity: external acceleration [dim][Q][ncells] in the state precision
+  void* accel = nullptr;
+  bool accel_stale = false;  // dropped by a regrid: set again before stepping
   // instrumentation
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -885,7 +888,7 @@ void drop_graphs(dg_handle* h) {
 
 cudaError_t cell_launch(dg_handle* h, const void* args, cudaStream_t s) {
   if (h->use_tc) return h->ks->cell_tc(args, s);
-  return h->use_direct ? h->ks->cell_direct(args, s) : h->ks->cell(args, s);
+  return h->use_direct && !h->accel ? h->ks->cell_direct(args, s) : h->ks->cell(args, s);
 }
 
 // face and cell kernels of one stage; DG_MIXED wraps the FP64 arguments.
@@ -958,6 +961,7 @@ StageArgs<real> stage_args(dg_handle* h, const Op& op, const void* U, void* W) {
     for (int r = 0; r < MAX_IN; ++r) a.C[o][r] = (real)op.C[o][r];
   }
   a.dt = h->scal;
+  a.accel = static_cast<const real*>(h->accel);
   a.cell_tile = h->cell_tile;
   a.face_tile = h->face_tile;
   a.dtab = h->dtab.empty() ? nullptr : h->dtab.data();
@@ -998,6 +1002,7 @@ AuxArgs<real> aux_args(dg_handle* h) {
   a.inv_dx_prob = h->nprob > 1 ? h->inv_dx_prob : nullptr;
   a.dt_bits = h->dt_bits;
   a.status = h->status;
+  a.accel = static_cast<const real*>(h->accel);
   return a;
 }
 
@@ -1016,6 +1021,7 @@ int compute_dt_impl(dg_handle* h, const void* W, double* copy, cudaStream_t s) {
   AuxArgs<real> a = aux_args<real>(h);
   a.W = static_cast<const real*>(W);
   const double fac = dt_factor(h);
+  a.grav_factor = fac * std::sqrt(2.0 * h->gamma * (h->gamma - 1.0));
   DG_CUDA(h, timed(h, DG_KERNEL_DT, s, [&] { return h->ks->dt(&a, s); }));
   DG_CUDA(h, timed(h, DG_KERNEL_OTHER, s,
                    [&] { return launch_dt_finalize(h->dt_bits, h->nprob, fac, h->scal, copy, s); }));
@@ -1244,6 +1250,13 @@ int rk_step_dispatch(dg_handle* h, void* W, double dt, double* dt_used, cudaStre
 }
 
 bool check_handle(const dg_handle* h) { return h != nullptr && h->ks != nullptr; }
+
+// a handle whose gravity field was dropped by a regrid must get a new one
+int check_gravity(dg_handle* h, const char* who) {
+  if (!h->accel_stale) return DG_OK;
+  return fail(h, DG_ERR_ARG, std::string(who) + ": the gravity field was sampled on the mesh before the "
+                                                "last dg_regrid; set it again (dg_set_gravity)");
+}
 
 }  // namespace
 
@@ -1578,6 +1591,7 @@ int dg_tiles(const dg_handle* h, int* cell_tile, int* face_tile) {
 int dg_rhs(dg_handle* h, const void* W_dev, void* dWdt_dev, void* stream) {
   if (!check_handle(h) || !W_dev || !dWdt_dev) return DG_ERR_ARG;
   if (W_dev == dWdt_dev) return fail(h, DG_ERR_ARG, "dg_rhs: W and dWdt alias");
+  if (check_gravity(h, "dg_rhs") != DG_OK) return DG_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   return h->prec == DG_FP64 ? rhs_into<double>(h, W_dev, dWdt_dev, s)
                             : rhs_into<float>(h, W_dev, dWdt_dev, s);
@@ -1585,6 +1599,7 @@ int dg_rhs(dg_handle* h, const void* W_dev, void* dWdt_dev, void* stream) {
 
 int dg_compute_dt(dg_handle* h, const void* W_dev, double* dt_dev, void* stream) {
   if (!check_handle(h) || !W_dev || !dt_dev) return DG_ERR_ARG;
+  if (check_gravity(h, "dg_compute_dt") != DG_OK) return DG_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   return h->prec == DG_FP64 ? compute_dt_impl<double>(h, W_dev, dt_dev, s)
                             : compute_dt_impl<float>(h, W_dev, dt_dev, s);
@@ -1592,12 +1607,14 @@ int dg_compute_dt(dg_handle* h, const void* W_dev, double* dt_dev, void* stream)
 
 int dg_rk_step(dg_handle* h, void* W_dev, double dt, double* dt_used_dev, void* stream) {
   if (!check_handle(h) || !W_dev) return DG_ERR_ARG;
+  if (check_gravity(h, "dg_rk_step") != DG_OK) return DG_ERR_ARG;
   std::lock_guard<std::mutex> lock(h->mu);
   return rk_step_dispatch(h, W_dev, dt, dt_used_dev, static_cast<cudaStream_t>(stream));
 }
 
 int dg_advance(dg_handle* h, void* W_dev, int n_steps, double* dt_hist_dev, void* stream) {
   if (!check_handle(h) || !W_dev || n_steps < 0) return DG_ERR_ARG;
+  if (check_gravity(h, "dg_advance") != DG_OK) return DG_ERR_ARG;
   if (n_steps == 0) return DG_OK;
   std::lock_guard<std::mutex> lock(h->mu);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1654,6 +1671,8 @@ int dg_rk_step_adjoint(dg_handle* h, const void* W_n_dev, double dt, const void*
   if (!(dt > 0.0)) return fail(h, DG_ERR_ARG, "dg_rk_step_adjoint: dt must be positive (frozen)");
   if (h->opt.slope_limiter != DG_LIMITER_NONE || h->opt.positivity)
     return fail(h, DG_ERR_ARG, "dg_rk_step_adjoint: needs an unlimited handle");
+  if (h->accel || h->accel_stale)
+    return fail(h, DG_ERR_UNSUPPORTED, "dg_rk_step_adjoint: not with a gravity source");
   std::lock_guard<std::mutex> lock(h->mu);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   return h->prec == DG_FP64 ? adjoint_step_impl<double>(h, W_n_dev, dt, lam_np1_dev, lam_n_dev, s)
@@ -1746,6 +1765,29 @@ int dg_cell_levels(const dg_handle* h, int32_t* host_out) {
   return DG_OK;
 }
 
+int dg_set_gravity(dg_handle* h, const double* accel_dev, void* stream) {
+  if (!check_handle(h)) return DG_ERR_ARG;
+  std::lock_guard<std::mutex> lock(h->mu);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  drop_graphs(h);  // recorded launches carry the old field pointer
+  if (!accel_dev) {
+    dfree(h, h->accel);
+    h->accel = nullptr;
+    h->accel_stale = false;
+    return DG_OK;
+  }
+  if (h->nprob != 1 || h->ms || h->use_tc)
+    return fail(h, DG_ERR_UNSUPPORTED, "dg_set_gravity: single problems with DG_FP64 or DG_FP32 only");
+  const size_t n = (size_t)h->dim * h->ks->Q * h->ncells;
+  if (!h->accel) {
+    int r = dalloc(h, std::max<size_t>(n, 1) * h->esize, &h->accel);
+    if (r != DG_OK) return r;
+  }
+  DG_CUDA(h, launch_convert(accel_dev, h->accel, n, (int)h->esize, s));
+  h->accel_stale = false;
+  return DG_OK;
+}
+
 int dg_adapt_mark(dg_handle* h, const void* W_dev, double w_t, double alpha, int32_t* flags_host,
                   int64_t* n_cells_new, int64_t* n_changed, void* stream) {
   if (!check_handle(h) || !W_dev) return DG_ERR_ARG;
@@ -1828,6 +1870,11 @@ int dg_regrid(dg_handle* h, const void* W_old_dev, void* W_new_dev, void* stream
   h->mark_pending = false;
   h->tables_on_device = true;
   drop_graphs(h);
+  if (h->accel) {  // sampled on the old mesh
+    dfree(h, h->accel);
+    h->accel = nullptr;
+    h->accel_stale = true;
+  }
   // adjoint work arrays are sized for the old mesh: allocated again on use
   for (void* p : h->adj) dfree(h, p);
   h->adj.clear();

@@ -114,6 +114,8 @@ struct StageArgs {
   int face_tile = 0;            // faces per block of the face kernel (0: its default)
   const real* tcB = nullptr;    // tensor-core B operands (tensor-core cell kernel)
   int* status = nullptr;        // device status word
+  const real* accel = nullptr;  // [DIM][Q][ncells] external acceleration at the volume points
+                                // (gravity source, eq. gravity_term); nullptr: none
 };
 
 // Stage arguments of the mixed-precision kernels (FP64 state, FP32
@@ -176,6 +178,8 @@ struct AuxArgs {
   const double* inv_dx_prob = nullptr;  // [nprob] 1 / base edge length (ensembles)
   unsigned long long* dt_bits = nullptr;
   int* status = nullptr;
+  const real* accel = nullptr;    // [DIM][Q][ncells] external acceleration (gravity timestep bound)
+  double grav_factor = 0.0;       // dt_factor * sqrt(2 gamma (gamma - 1))
 };
 
 // Adjoint of one stage: given the stage state U and a cotangent G on dWdt(U),
@@ -303,6 +307,8 @@ cudaError_t launch_adapt_project(const BaseGrid& g, int esize, int nv, int N, co
 cudaError_t launch_set_scalar(double* dst, int n, double value, cudaStream_t s);
 // dst[i] = value for i < n, elements of esize bytes (4: float, 8: double)
 cudaError_t launch_fill(void* dst, size_t n, double value, int esize, cudaStream_t s);
+// dst[i] = src[i] converted to elements of esize bytes (4: float, 8: double)
+cudaError_t launch_convert(const double* src, void* dst, size_t n, int esize, cudaStream_t s);
 cudaError_t launch_dt_finalize(const unsigned long long* bits, int nprob, double factor, double* dt,
                                double* dt_copy, cudaStream_t s);
 

@@ -627,6 +627,22 @@ __global__ void __launch_bounds__(RED_THREADS) dt_kernel(const AuxArgs<real> a) 
       for (int b = 0; b < DIM; ++b) sum += fabs(u[1 + b] * rinv) + cs;
       const real inv_dx = real(a.inv_dx_prob ? a.inv_dx_prob[pb] : a.inv_dx[0]);
       speed = (double)(sum * inv_dx * real(1 << a.m.level[c]));
+      if (a.accel) {
+        // gravity bound (Sec. 2.5) as a speed: dt_factor sqrt(2 gamma (gamma-1)) |a|_max / c,
+        // |a| the largest over the cell's volume points
+        real a2max = real(0);
+#pragma unroll
+        for (int q = 0; q < S::Q; ++q) {
+          real a2 = real(0);
+#pragma unroll
+          for (int b = 0; b < DIM; ++b) {
+            const real aq = a.accel[((size_t)b * S::Q + q) * nc + c];
+            a2 += aq * aq;
+          }
+          a2max = fmax(a2max, a2);
+        }
+        speed = fmax(speed, (double)(real(a.grav_factor) * sqrt(a2max) / cs));
+      }
     }
   } else {
     pb = -1;
@@ -799,6 +815,11 @@ cudaError_t launch_cell(const void* pa, cudaStream_t s) {
   const int tc = (a.cell_tile == 16 || a.cell_tile == 32 || a.cell_tile == 64) && a.cell_tile <= CT::TC_MAX
                      ? a.cell_tile
                      : CT::TC;
+  if (a.accel) {  // gravity: the default tile only
+    cell_update_kernel<real, DIM, K, CT::TC, true><<<(a.m.ncells + CT::TC - 1) / CT::TC, CT::TC * NV,
+                                                     CT::smem(CT::TC), s>>>(a);
+    return cudaGetLastError();
+  }
   const int grid = (a.m.ncells + tc - 1) / tc;
   if (tc == 16) {
     cell_update_kernel<real, DIM, K, 16><<<grid, 16 * NV, CT::smem(16), s>>>(a);
@@ -844,6 +865,9 @@ cudaError_t prepare_kernels() {
     if constexpr (CT::TC_MAX >= 64) e = cudaFuncSetAttribute(cell_update_kernel<real, DIM, K, 64>, attr, (int)CT::smem(64));
   }
   if (e != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(cell_update_kernel<real, DIM, K, CT::TC, true>, attr, (int)CT::smem(CT::TC))) !=
+      cudaSuccess)
+    return e;
   if ((e = cudaFuncSetAttribute(face_flux_kernel<real, DIM, K, 16>, attr, (int)FT::smem(16))) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(face_flux_kernel<real, DIM, K, 32>, attr, (int)FT::smem(32))) != cudaSuccess) return e;
   return cudaFuncSetAttribute(face_flux_kernel<real, DIM, K, 64>, attr, (int)FT::smem(64));

@@ -156,6 +156,66 @@ __device__ __forceinline__ void volume_dir(const Tab1D<real>& T, const real* f, 
   }
 }
 
+// projection of a field given at the volume points onto the basis:
+// acc_l += h * sum_q s_q phi_l(xi_q) w_q (q = i + K1 (j + K1 k)), sum-factorised
+// with the weighted 1D tables along every axis
+template <typename real, int DIM, int K>
+__device__ __forceinline__ void source_project(const Tab1D<real>& T, const real* s, real h, real* acc) {
+  constexpr int K1 = K + 1;
+  if constexpr (DIM == 2) {
+#pragma unroll
+    for (int e1 = 0; e1 <= K; ++e1) {
+      real g[K1];
+#pragma unroll
+      for (int i2 = 0; i2 < K1; ++i2) {
+        real t = real(0);
+#pragma unroll
+        for (int i1 = 0; i1 < K1; ++i1) t += s[i1 + K1 * i2] * T.PW[e1][i1];
+        g[i2] = t;
+      }
+#pragma unroll
+      for (int e2 = 0; e2 <= K - e1; ++e2) {
+        real t = real(0);
+#pragma unroll
+        for (int i2 = 0; i2 < K1; ++i2) t += g[i2] * T.PW[e2][i2];
+        acc[bidx<2>(e1, e2, 0)] += h * t;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int e1 = 0; e1 <= K; ++e1) {
+      real g1[K1][K1];
+#pragma unroll
+      for (int i2 = 0; i2 < K1; ++i2)
+#pragma unroll
+        for (int i3 = 0; i3 < K1; ++i3) {
+          real t = real(0);
+#pragma unroll
+          for (int i1 = 0; i1 < K1; ++i1) t += s[i1 + K1 * (i2 + K1 * i3)] * T.PW[e1][i1];
+          g1[i2][i3] = t;
+        }
+#pragma unroll
+      for (int e2 = 0; e2 <= K - e1; ++e2) {
+        real g2[K1];
+#pragma unroll
+        for (int i3 = 0; i3 < K1; ++i3) {
+          real t = real(0);
+#pragma unroll
+          for (int i2 = 0; i2 < K1; ++i2) t += g1[i2][i3] * T.PW[e2][i2];
+          g2[i3] = t;
+        }
+#pragma unroll
+        for (int e3 = 0; e3 <= K - e1 - e2; ++e3) {
+          real t = real(0);
+#pragma unroll
+          for (int i3 = 0; i3 < K1; ++i3) t += g2[i3] * T.PW[e3][i3];
+          acc[bidx<3>(e1, e2, e3)] += h * t;
+        }
+      }
+    }
+  }
+}
+
 // surface integral of one variable over side (DIR, S) of the cell:
 // acc_l -= sg * sum_q fbar_q phi_l(face point q) w_q, with the face's points
 // given in PT0 (and PT1) -- the Gauss nodes, or a half of them for sub-faces.
@@ -446,7 +506,7 @@ __device__ __forceinline__ void surface_from_faces(const StageArgs<real>& a, int
   }
 }
 
-template <typename real, int DIM, int K, int TC>
+template <typename real, int DIM, int K, int TC, bool GRAV = false>
 __global__ void __launch_bounds__(TC * Shape<DIM, K>::NV)
     cell_update_kernel(const StageArgs<real> a) {
   using S = Shape<DIM, K>;
@@ -525,6 +585,25 @@ __global__ void __launch_bounds__(TC * Shape<DIM, K>::NV)
   // 4. epilogue
   const int pb = cell_problem(a.m, c);
   const real pre = a.pre_prob ? a.pre_prob[pb] : a.pre[a.m.level[c]];
+  if constexpr (GRAV) {
+    // gravity source (eq. gravity_term): s = (0, rho a, m . a) at the volume
+    // points; pre * (dx/2) * sum_q s_q phi_j w_q = 2^-d sum_q s_q phi_j w_q
+    if (v > 0) {
+      real sq[Q];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        if (v <= DIM) {
+          sq[q] = sU[(0 * Q + q) * TC + tc] * a.accel[((size_t)(v - 1) * Q + q) * nc + c];
+        } else {
+          real t = real(0);
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) t += sU[((1 + d) * Q + q) * TC + tc] * a.accel[((size_t)d * Q + q) * nc + c];
+          sq[q] = t;
+        }
+      }
+      source_project<real, DIM, K>(T, sq, real(1) / (real(1 << DIM) * pre), acc);
+    }
+  }
   const real sc = pre * (a.dt ? real(a.dt[pb]) : real(1));
   const int n_out = a.n_out, n_in = a.n_in;
 #pragma unroll

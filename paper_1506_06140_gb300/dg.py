@@ -25,7 +25,8 @@ EXPORTS = ["dg_default_options", "dg_create", "dg_destroy", "dg_last_error", "dg
            "dg_l1_density", "dg_node_weights", "dg_neighbor_table", "dg_cell_levels",
            "dg_status", "dg_profile_begin", "dg_profile_end", "dg_totals_noalloc",
            "dg_create_batch", "dg_batch_advance", "dg_n_problems", "dg_tiles",
-           "dg_limiter_counts", "dg_set_tiles", "dg_adapt_mark", "dg_adapt_set", "dg_regrid"]
+           "dg_limiter_counts", "dg_set_tiles", "dg_adapt_mark", "dg_adapt_set", "dg_regrid",
+           "dg_set_gravity"]
 KERNEL_KINDS = ["face", "cell", "limit", "dt", "other", "adjoint"]
 
 
@@ -92,6 +93,7 @@ def load(path=LIB_PATH):
     L.dg_adapt_mark.argtypes = [vp, vp, C.c_double, C.c_double, i32p, i64p, i64p, vp]
     L.dg_adapt_set.argtypes = [vp, i32p, i64p, i64p, vp]
     L.dg_regrid.argtypes = [vp, vp, vp, vp]
+    L.dg_set_gravity.argtypes = [vp, vp, vp]
     L.dg_profile_begin.argtypes = [vp]
     L.dg_profile_end.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_int]
     for name in EXPORTS:
@@ -300,6 +302,15 @@ class Solver:
         out = np.zeros(self.n_cells, np.int32)
         self._check(self._L.dg_cell_levels(self._h, out.ctypes.data_as(C.POINTER(C.c_int32))))
         return out
+
+    def set_gravity(self, accel):
+        """external acceleration [dim][nq][cells] at quad_points() (None removes it)"""
+        if accel is None:
+            self._check(self._L.dg_set_gravity(self._h, None, _stream()))
+            return
+        a = torch.as_tensor(accel).to(device=self.device, dtype=torch.float64).contiguous()
+        assert tuple(a.shape) == (self.dim, self.nq, self.n_cells)
+        self._check(self._L.dg_set_gravity(self._h, _ptr(a), _stream()))
 
     # -- mesh adaptation (single problems) --
     def adapt_mark(self, W, w_t=0.01, alpha=1.1, flags=False):
