@@ -399,6 +399,7 @@ struct dg_handle {
   void* tab = nullptr;
   double* tab64 = nullptr;
   Tab1D<double> tab1d64{};
+  float* tab32 = nullptr;    // the tables in FP32 (positivity precheck)
   void* F = nullptr;
   std::vector<void*> regs;   // scratch state registers 1..n
   bool use_tc = false;       // tensor-core cell kernel (DG_FP32_TC)
@@ -974,6 +975,7 @@ int run_limit(dg_handle* h, const void* src, void* dst, cudaStream_t s) {
   la.m = h->md;
   la.tab64 = h->tab64;
   la.tabr = static_cast<const real*>(h->tab);
+  la.tab32 = h->tab32;
   la.Uin = static_cast<const real*>(src);
   la.Uout = static_cast<real*>(dst);
   la.gamma = h->gamma;
@@ -1332,15 +1334,14 @@ static int create_impl(const dg_mesh_desc* mesh, int nprob, int k, double gamma,
   h->tab64 = static_cast<double*>(p);
   if (cudaMemcpy(h->tab64, T.data(), T.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
     return bail(cuda_fail(h, cudaGetLastError(), "cudaMemcpy tables"));
-  if (h->prec == DG_FP64) {
-    h->tab = h->tab64;
-  } else {
+  {
     std::vector<float> Tf(T.begin(), T.end());
     if ((r = dalloc(h, Tf.size() * sizeof(float), &p)) != DG_OK) return bail(r);
-    h->tab = p;
+    h->tab32 = static_cast<float*>(p);
     if (cudaMemcpy(p, Tf.data(), Tf.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
       return bail(cuda_fail(h, cudaGetLastError(), "cudaMemcpy tables"));
   }
+  h->tab = h->prec == DG_FP64 ? static_cast<void*>(h->tab64) : static_cast<void*>(h->tab32);
   // mesh tables
   if ((r = upload(h, h->level, &h->md.level)) != DG_OK) return bail(r);
   if ((r = upload(h, h->coord, &h->md.coord)) != DG_OK) return bail(r);

@@ -148,6 +148,7 @@ struct LimitArgs {
   MeshDev m;
   const double* tab64 = nullptr;  // FP64 tables (same layout)
   const real* tabr = nullptr;     // the same tables in the state precision
+  const float* tab32 = nullptr;   // the same tables in FP32 (positivity precheck)
   const real* Uin = nullptr;
   real* Uout = nullptr;
   double gamma = 1.4;

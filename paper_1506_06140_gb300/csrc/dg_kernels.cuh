@@ -373,6 +373,71 @@ __device__ __forceinline__ void unlimit_direction(const LimitArgs<real>& a, cons
 // One thread per cell.  The slope limiter runs in the state's precision;
 // the positivity limiter (its shortcut bound, the density and pressure
 // checks and tau) in FP64.
+// Positivity test of one cell at the point set of the positivity limiter
+// (the set S of eq. union_quad_points, plus the fine sub-face points of every
+// side with a finer neighbour), in FP32.  A point value is a sum of N <= 20
+// products of FP32-rounded weights and table entries: its error is at most
+// (N + 3) 2^-24 < 2e-6 times the sum A of the absolute products, so
+// rho >= u_0 - 2e-6 A_0 and likewise for |m_a| and E; the kinetic term
+// |m|_up^2 / (2 rho_lo) is rounded by at most 6 ulp (factor 1 + 1e-6) and the
+// pressure difference by 3 ulp of |E_lo| + kin (margin 1e-6).  True when
+// density and pressure clear 2 eps at every point.  The margins are tight
+// enough for cold flows (p / E ~ 1e-5, Keplerian disc).
+template <int DIM, int K>
+__device__ bool points_clear_fp32(const MeshDev& m, const float* tab32, double eps, double gamma,
+                                  const float (&wf)[Shape<DIM, K>::NV][Shape<DIM, K>::N], int c) {
+  using S = Shape<DIM, K>;
+  constexpr int NV = S::NV, N = S::N;
+  static_assert(N <= 20, "the rounding margins assume at most 20 basis functions");
+  const int nc = m.ncells;
+  unsigned finer = 0;
+  if (m.nnodes > 0)
+    for (int sd = 0; sd < S::NSIDE; ++sd)
+      if (m.nbr[(size_t)sd * nc + c] <= -2) finer |= 1u << sd;
+  const float feps2 = 2.0f * (float)eps, g1 = (float)(gamma - 1.0);
+  const int npts = S::NSP + __popc(finer) * S::NSUB * S::QF;
+  for (int ip = 0; ip < npts; ++ip) {
+    const float* ph;
+    if (ip < S::NSP) {
+      ph = tab32 + S::OFF_SPHI + (size_t)ip * N;
+    } else {
+      int r = ip - S::NSP, sd = 0;
+      for (; sd < S::NSIDE; ++sd) {
+        if (!((finer >> sd) & 1)) continue;
+        if (r < S::NSUB * S::QF) break;
+        r -= S::NSUB * S::QF;
+      }
+      ph = tab32 + S::OFF_PHIF + (size_t)((sd * S::NVAR + 1 + r / S::QF) * S::QF + r % S::QF) * N;
+    }
+    float u[NV], A[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      float s = 0.0f, t = 0.0f;
+#pragma unroll
+      for (int l = 0; l < N; ++l) {
+        const float x = wf[v][l] * ph[l];
+        s += x;
+        t += fabsf(x);
+      }
+      u[v] = s;
+      A[v] = t;
+    }
+    const float rho_lo = u[0] - 2e-6f * A[0];
+    if (!(rho_lo >= feps2)) return false;
+    float m2 = 0.0f;
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) {
+      const float mu = fabsf(u[1 + b]) + 2e-6f * A[1 + b];
+      m2 += mu * mu;
+    }
+    const float e_lo = u[DIM + 1] - 2e-6f * A[DIM + 1];
+    const float kin = 0.5f * m2 / rho_lo * (1.0f + 1e-6f);
+    const float p_lo = g1 * (e_lo - kin);
+    if (!(p_lo >= feps2 + 1e-6f * g1 * (fabsf(e_lo) + kin))) return false;
+  }
+  return true;
+}
+
 template <typename real, int DIM, int K>
 __global__ void __launch_bounds__(128) limit_kernel(const LimitArgs<real> a) {
   using S = Shape<DIM, K>;
@@ -395,7 +460,6 @@ __global__ void __launch_bounds__(128) limit_kernel(const LimitArgs<real> a) {
     const real pm = real(a.gamma - 1.0) * (mean[DIM + 1] - real(0.5) * m2 / mean[0]);
     if (!(mean[0] > real(0)) || !(pm > real(0))) atomicOr(a.status, 1 << DG_ERR_NONPHYSICAL_BIT);
   }
-  const double* tab = a.tab64;
   if constexpr (K > 0) {
     if (a.limiter != 0) {
       const real dx = (real)cell_dx(a.m, c);
@@ -427,54 +491,40 @@ __global__ void __launch_bounds__(128) limit_kernel(const LimitArgs<real> a) {
       }
     }
   }
-  bool need_positivity = a.positivity && K > 0;
-  if constexpr (sizeof(real) == 4) {
-    // FP32 state: the bound below evaluated in FP32 with margins that cover
-    // its rounding (sums of <= 20 terms: relative error < 2e-6); a cell that
-    // passes needs no FP64 work at all
-    if (need_positivity) {
-      float lo[NV], up[NV];
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        float r = 0.0f;
-#pragma unroll
-        for (int l = 1; l < N; ++l) r += fabsf(w[v][l]) * a.tabr[S::OFF_PMAX + l];
-        r *= 1.0f + 1e-5f;
-        lo[v] = w[v][0] - r - 1e-6f * fabsf(w[v][0]);
-        up[v] = (fabsf(w[v][0]) + r) * (1.0f + 1e-5f);
-      }
-      const float feps = (float)a.eps;
-      if (lo[0] >= 2.0f * feps) {
-        float m2 = 0.0f;
-#pragma unroll
-        for (int b = 0; b < DIM; ++b) m2 += up[1 + b] * up[1 + b];
-        const float kin = 0.5f * m2 / lo[0];
-        const float p_low = (float)(a.gamma - 1.0) * (lo[DIM + 1] - kin);
-        if (p_low >= 2.0f * feps + 1e-5f * (fabsf(lo[DIM + 1]) + kin)) need_positivity = false;
-      }
-    }
-  }
+  bool need_positivity = a.positivity && K > 0 && a.tab32;
   if (need_positivity) {
-    // Exact shortcut: |phi_l| <= prod sqrt(2e+1) on [-1,1]^d, so
-    //   rho(x) >= rho_bar - sum_{l>=1} |w_rho,l| phi_max_l  and
-    //   p(x) >= (gamma-1) (E_low - |m|_up^2 / (2 rho_low)).
-    // When both lower bounds reach eps at every point, theta_1 = theta_2 = 1.
-    double lo[NV], up[NV];
+    // Exact shortcuts in FP32 (for either state precision), so that only
+    // cells that may need theta < 1 reach the FP64 pass:
+    // 1. |phi_l| <= prod sqrt(2e+1) on [-1,1]^d gives rho(x) >= rho_bar -
+    //    sum_{l>=1} |w_rho,l| phi_max_l and p(x) >= (gamma-1) (E_low -
+    //    |m|_up^2 / (2 rho_low)) over the whole cell; margins 1e-5 cover the
+    //    FP32 rounding of these sums of <= 20 terms (< 2e-6);
+    // 2. failing that, the values at the limiter's own points.
+    float wf[NV][N];
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+      for (int l = 0; l < N; ++l) wf[v][l] = (float)w[v][l];
+    float lo[NV], up[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      double r = 0.0;
+      float r = 0.0f;
 #pragma unroll
-      for (int l = 1; l < N; ++l) r += fabs((double)w[v][l]) * tab[S::OFF_PMAX + l];
-      lo[v] = (double)w[v][0] - r;
-      up[v] = fabs((double)w[v][0]) + r;
+      for (int l = 1; l < N; ++l) r += fabsf(wf[v][l]) * a.tab32[S::OFF_PMAX + l];
+      r *= 1.0f + 1e-5f;
+      lo[v] = wf[v][0] - r - 1e-6f * fabsf(wf[v][0]);
+      up[v] = (fabsf(wf[v][0]) + r) * (1.0f + 1e-5f);
     }
-    if (lo[0] >= a.eps) {
-      double m2 = 0.0;
+    const float feps = (float)a.eps;
+    if (lo[0] >= 2.0f * feps) {
+      float m2 = 0.0f;
 #pragma unroll
       for (int b = 0; b < DIM; ++b) m2 += up[1 + b] * up[1 + b];
-      const double p_low = (a.gamma - 1.0) * (lo[DIM + 1] - 0.5 * m2 / lo[0]);
-      if (p_low >= a.eps) need_positivity = false;
+      const float kin = 0.5f * m2 / lo[0];
+      const float p_low = (float)(a.gamma - 1.0) * (lo[DIM + 1] - kin);
+      if (p_low >= 2.0f * feps + 1e-5f * (fabsf(lo[DIM + 1]) + kin)) need_positivity = false;
     }
+    if (need_positivity && points_clear_fp32<DIM, K>(a.m, a.tab32, a.eps, a.gamma, wf, c)) need_positivity = false;
   }
 #pragma unroll
   for (int v = 0; v < NV; ++v)
