@@ -391,9 +391,11 @@ def run_gpu(args, rank, world, local_rank):
             L0, L1 = ang(W0), ang(W)
             t0, t1 = s.totals(W0).cpu().numpy(), s.totals(W).cpu().numpy()
             passes = s.n_cells * WORKLOADS[args.workload]["stages"] * (args.steps + args.warmup)
+            cnt = s.limiter_counts(reset=True).cpu().numpy()
             diag = {"angular_momentum_drift_rel": abs(L1 - L0) / abs(L0),
                     "mass_drift_rel": float(abs(t1[0] - t0[0]) / abs(t0[0])),
-                    "positivity_limited_fraction": float(s.limiter_counts(reset=True).cpu().numpy()[1]) / passes,
+                    "positivity_limited_fraction": float(cnt[1]) / passes,
+                    "positivity_fp64_pass_fraction": float(cnt[2]) / passes,
                     "steps_since_initial_state": args.warmup + args.steps,
                     "note": "the positivity limiter does not conserve angular momentum; unlimited DG does "
                             "to rounding (GPU test)"}
@@ -404,6 +406,7 @@ def run_gpu(args, rank, world, local_rank):
             t0, t1 = s.totals(W0).cpu().numpy(), s.totals(W).cpu().numpy()
             diag = {"slope_limited_fraction": float(cnt[0]) / passes,
                     "positivity_limited_fraction": float(cnt[1]) / passes,
+                    "positivity_fp64_pass_fraction": float(cnt[2]) / passes,
                     "steps_since_initial_state": args.warmup + args.steps,
                     "mass_drift_rel": float(abs(t1[0] - t0[0]) / abs(t0[0])),
                     "energy_drift_rel": float(abs(t1[-1] - t0[-1]) / abs(t0[-1])),

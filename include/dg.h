@@ -128,9 +128,10 @@ const char* dg_last_error(const dg_handle* h);
 /* Limiter activity since the handle was created or last reset: counts_dev[0]
  * = cell passes in which the slope limiter (Secs. 3.2-3.3) changed the
  * slopes, counts_dev[1] = cell passes in which the positivity limiter (Sec.
- * 3.4) scaled the weights.  counts_dev: device memory, two int64 values,
- * written asynchronously on the stream; reset != 0 zeroes the counters after
- * the copy. */
+ * 3.4) scaled the weights, counts_dev[2] = cell passes that the exact FP32
+ * prechecks could not clear and the FP64 positivity pass examined.
+ * counts_dev: device memory, three int64 values, written asynchronously on
+ * the stream; reset != 0 zeroes the counters after the copy. */
 int dg_limiter_counts(dg_handle* h, int64_t* counts_dev, int reset, void* stream);
 
 /* Tiles of the stage kernels in use: cells per thread block of the cell

@@ -408,7 +408,8 @@ struct dg_handle {
   float* Gm = nullptr;       // DG_MIXED face fluxes minus the minus cell's reference flux
   float* Dm = nullptr;       // DG_MIXED reference flux differences per face
   bool delta = false;        // DG_MIXED with FP32 delta registers (unlimited programs)
-  unsigned long long* lim_counts = nullptr;  // [2] cells changed by the slope / positivity limiter
+  unsigned long long* lim_counts = nullptr;  // [3] cells changed by the slope / positivity limiter,
+                                             // cells examined by the FP64 positivity pass
   int* lim_queue = nullptr;  // [ncells + 1]: the positivity pass's cells, then their number
   float* Wf = nullptr;       // delta mode: FP32 split of W within a step [NV][N][ncells]
   float* Wlo = nullptr;      //             and the rest of weight 0 [NV][ncells]
@@ -1397,11 +1398,11 @@ static int create_impl(const dg_mesh_desc* mesh, int nprob, int k, double gamma,
   h->partial = static_cast<double*>(p);
   if ((r = dalloc(h, sizeof(int), &p)) != DG_OK) return bail(r);
   h->status = static_cast<int*>(p);
-  if ((r = dalloc(h, 2 * sizeof(unsigned long long), &p)) != DG_OK) return bail(r);
+  if ((r = dalloc(h, 3 * sizeof(unsigned long long), &p)) != DG_OK) return bail(r);
   h->lim_counts = static_cast<unsigned long long*>(p);
   if ((r = dalloc(h, ((size_t)std::max(h->ncells, 1) + 1) * sizeof(int), &p)) != DG_OK) return bail(r);
   h->lim_queue = static_cast<int*>(p);
-  if (cudaMemset(h->lim_counts, 0, 2 * sizeof(unsigned long long)) != cudaSuccess)
+  if (cudaMemset(h->lim_counts, 0, 3 * sizeof(unsigned long long)) != cudaSuccess)
     return bail(cuda_fail(h, cudaGetLastError(), "cudaMemset"));
   if (cudaMemset(h->status, 0, sizeof(int)) != cudaSuccess)
     return bail(cuda_fail(h, cudaGetLastError(), "cudaMemset"));
@@ -1554,9 +1555,9 @@ int dg_project(dg_handle* h, const double* u_dev, void* W_dev, void* stream) {
 int dg_limiter_counts(dg_handle* h, int64_t* counts_dev, int reset, void* stream) {
   if (!check_handle(h) || !counts_dev) return DG_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  DG_CUDA(h, cudaMemcpyAsync(counts_dev, h->lim_counts, 2 * sizeof(unsigned long long),
+  DG_CUDA(h, cudaMemcpyAsync(counts_dev, h->lim_counts, 3 * sizeof(unsigned long long),
                              cudaMemcpyDeviceToDevice, s));
-  if (reset) DG_CUDA(h, cudaMemsetAsync(h->lim_counts, 0, 2 * sizeof(unsigned long long), s));
+  if (reset) DG_CUDA(h, cudaMemsetAsync(h->lim_counts, 0, 3 * sizeof(unsigned long long), s));
   return DG_OK;
 }
 

@@ -18,6 +18,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "dg_convert.cuh"
 #include "dg_internal.h"
 #include "dg_physics.cuh"
 #include "dg_stage.cuh"
@@ -454,11 +455,12 @@ __global__ void __launch_bounds__(128) limit_kernel(const LimitArgs<real> a) {
 #pragma unroll
   for (int v = 0; v < NV; ++v) mean[v] = w[v][0];
   {
+    // mean pressure > 0 <=> rho (E - |m|^2 / (2 rho)) > 0 for rho > 0 (no division)
     real m2 = real(0);
 #pragma unroll
     for (int b = 0; b < DIM; ++b) m2 += mean[1 + b] * mean[1 + b];
-    const real pm = real(a.gamma - 1.0) * (mean[DIM + 1] - real(0.5) * m2 / mean[0]);
-    if (!(mean[0] > real(0)) || !(pm > real(0))) atomicOr(a.status, 1 << DG_ERR_NONPHYSICAL_BIT);
+    const real rp = mean[DIM + 1] * mean[0] - real(0.5) * m2;
+    if (!(mean[0] > real(0)) || !(rp > real(0))) atomicOr(a.status, 1 << DG_ERR_NONPHYSICAL_BIT);
   }
   if constexpr (K > 0) {
     if (a.limiter != 0) {
@@ -501,30 +503,41 @@ __global__ void __launch_bounds__(128) limit_kernel(const LimitArgs<real> a) {
     //    FP32 rounding of these sums of <= 20 terms (< 2e-6);
     // 2. failing that, the values at the limiter's own points.
     float wf[NV][N];
+    bool in_range = true;  // FP64 weights below 2^100 in magnitude (else: the FP64 pass decides)
 #pragma unroll
     for (int v = 0; v < NV; ++v)
 #pragma unroll
-      for (int l = 0; l < N; ++l) wf[v][l] = (float)w[v][l];
-    float lo[NV], up[NV];
+      for (int l = 0; l < N; ++l) {
+        if constexpr (sizeof(real) == 8) {
+          wf[v][l] = f32_round(w[v][l]);
+          const unsigned e = ((unsigned)(__double_as_longlong(w[v][l]) >> 52)) & 0x7FFu;
+          in_range = in_range && e < 1023u + 100u;
+        } else {
+          wf[v][l] = (float)w[v][l];
+        }
+      }
+    if (in_range) {
+      float lo[NV], up[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      float r = 0.0f;
+      for (int v = 0; v < NV; ++v) {
+        float r = 0.0f;
 #pragma unroll
-      for (int l = 1; l < N; ++l) r += fabsf(wf[v][l]) * a.tab32[S::OFF_PMAX + l];
-      r *= 1.0f + 1e-5f;
-      lo[v] = wf[v][0] - r - 1e-6f * fabsf(wf[v][0]);
-      up[v] = (fabsf(wf[v][0]) + r) * (1.0f + 1e-5f);
+        for (int l = 1; l < N; ++l) r += fabsf(wf[v][l]) * a.tab32[S::OFF_PMAX + l];
+        r *= 1.0f + 1e-5f;
+        lo[v] = wf[v][0] - r - 1e-6f * fabsf(wf[v][0]);
+        up[v] = (fabsf(wf[v][0]) + r) * (1.0f + 1e-5f);
+      }
+      const float feps = (float)a.eps;
+      if (lo[0] >= 2.0f * feps) {
+        float m2 = 0.0f;
+#pragma unroll
+        for (int b = 0; b < DIM; ++b) m2 += up[1 + b] * up[1 + b];
+        const float kin = 0.5f * m2 / lo[0];
+        const float p_low = (float)(a.gamma - 1.0) * (lo[DIM + 1] - kin);
+        if (p_low >= 2.0f * feps + 1e-5f * (fabsf(lo[DIM + 1]) + kin)) need_positivity = false;
+      }
+      if (need_positivity && points_clear_fp32<DIM, K>(a.m, a.tab32, a.eps, a.gamma, wf, c)) need_positivity = false;
     }
-    const float feps = (float)a.eps;
-    if (lo[0] >= 2.0f * feps) {
-      float m2 = 0.0f;
-#pragma unroll
-      for (int b = 0; b < DIM; ++b) m2 += up[1 + b] * up[1 + b];
-      const float kin = 0.5f * m2 / lo[0];
-      const float p_low = (float)(a.gamma - 1.0) * (lo[DIM + 1] - kin);
-      if (p_low >= 2.0f * feps + 1e-5f * (fabsf(lo[DIM + 1]) + kin)) need_positivity = false;
-    }
-    if (need_positivity && points_clear_fp32<DIM, K>(a.m, a.tab32, a.eps, a.gamma, wf, c)) need_positivity = false;
   }
 #pragma unroll
   for (int v = 0; v < NV; ++v)
@@ -536,7 +549,16 @@ __global__ void __launch_bounds__(128) limit_kernel(const LimitArgs<real> a) {
 
 // Positivity limiter of Sec. 3.4 (with the hanging-face points of Sec. 4.4)
 // for the queued cells, in FP64: theta_1 on the density, then theta_2 from
-// the pressure root tau of every point below eps.  Reads and writes Uout.
+// the pressure root tau of every point below eps.  One warp per queued cell,
+// its lanes over the points; theta_1 and theta_2 are minima over the points,
+// so the result does not depend on how the points are shared out.  Reads and
+// writes Uout.
+__device__ __forceinline__ double warp_min(double x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x = fmin(x, __shfl_xor_sync(0xffffffffu, x, o));
+  return x;
+}
+
 template <typename real, int DIM, int K>
 __global__ void __launch_bounds__(128) positivity_kernel(const LimitArgs<real> a) {
   using S = Shape<DIM, K>;
@@ -544,7 +566,11 @@ __global__ void __launch_bounds__(128) positivity_kernel(const LimitArgs<real> a
   const int nc = a.m.ncells;
   const double* tab = a.tab64;
   const int len = *a.queue_len;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < len; i += gridDim.x * blockDim.x) {
+  if (a.counts && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(a.counts + 2, (unsigned long long)len);
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  // warp-uniform loop: every lane of a warp takes the same cells
+  for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < len; i += gridDim.x * wpb) {
     const int c = a.queue[i];
     real w[NV][N];
 #pragma unroll
@@ -557,8 +583,9 @@ __global__ void __launch_bounds__(128) positivity_kernel(const LimitArgs<real> a
     for (int v = 0; v < NV; ++v) mean64[v] = (double)w[v][0];
     // points: the union set S, plus fine sub-face points on sides with a finer neighbour
     unsigned finer = 0;
-    for (int sd = 0; sd < S::NSIDE; ++sd)
-      if (a.m.nbr[(size_t)sd * nc + c] <= -2) finer |= 1u << sd;
+    if (a.m.nnodes > 0)
+      for (int sd = 0; sd < S::NSIDE; ++sd)
+        if (a.m.nbr[(size_t)sd * nc + c] <= -2) finer |= 1u << sd;
     const int npts = S::NSP + __popc(finer) * S::NSUB * S::QF;
     auto point_row = [&](int ip) -> const double* {
       if (ip < S::NSP) return tab + S::OFF_SPHI + (size_t)ip * N;
@@ -573,20 +600,21 @@ __global__ void __launch_bounds__(128) positivity_kernel(const LimitArgs<real> a
       return tab + S::OFF_PHIF + (size_t)((sd * S::NVAR + var) * S::QF + q) * N;
     };
     double rmin = 1e300;
-    for (int ip = 0; ip < npts; ++ip) {
+    for (int ip = lane; ip < npts; ip += 32) {
       const double* ph = point_row(ip);
       double rho = 0.0;
 #pragma unroll
       for (int l = 0; l < N; ++l) rho += (double)w[0][l] * ph[l];
       rmin = fmin(rmin, rho);
     }
+    rmin = warp_min(rmin);
     if (rmin < eps) {
       const double th1 = fmin(fabs((mean64[0] - eps) / (mean64[0] - rmin)), 1.0);
 #pragma unroll
       for (int l = 1; l < N; ++l) w[0][l] = (real)((double)w[0][l] * th1);
     }
     double th2 = 1.0;
-    for (int ip = 0; ip < npts; ++ip) {
+    for (int ip = lane; ip < npts; ip += 32) {
       const double* ph = point_row(ip);
       double u[NV];
 #pragma unroll
@@ -603,7 +631,8 @@ __global__ void __launch_bounds__(128) positivity_kernel(const LimitArgs<real> a
       if (pr >= eps) continue;
       th2 = fmin(th2, positivity_tau<DIM>(mean64, u, a.gamma, eps));
     }
-    if ((rmin < eps || th2 < 1.0) && a.counts) atomicAdd(a.counts + 1, 1ull);
+    th2 = warp_min(th2);
+    if (lane == 0 && (rmin < eps || th2 < 1.0) && a.counts) atomicAdd(a.counts + 1, 1ull);
     if (th2 < 1.0) {
 #pragma unroll
       for (int v = 0; v < NV; ++v)
@@ -611,10 +640,12 @@ __global__ void __launch_bounds__(128) positivity_kernel(const LimitArgs<real> a
         for (int l = 1; l < N; ++l) w[v][l] = (real)((double)w[v][l] * th2);
     }
     if (rmin < eps || th2 < 1.0) {
+      // the lanes share the stores
 #pragma unroll
       for (int v = 0; v < NV; ++v)
 #pragma unroll
-        for (int l = 0; l < N; ++l) a.Uout[(size_t)(v * N + l) * nc + c] = w[v][l];
+        for (int l = 0; l < N; ++l)
+          if ((v * N + l) % 32 == lane) a.Uout[(size_t)(v * N + l) * nc + c] = w[v][l];
     }
   }
 }

@@ -31,7 +31,7 @@ __device__ inline void base_coord(const BaseGrid& g, int b, int p[3]) {
 }
 
 template <typename real>
-__global__ void criterion_kernel(const BaseGrid g, const real* __restrict__ W, int N, int nc,
+__global__ void adapt_criterion_kernel(const BaseGrid g, const real* __restrict__ W, int N, int nc,
                                  const int32_t* __restrict__ first, const int32_t* __restrict__ node_of,
                                  const double* __restrict__ P, double thr_leaf, double thr_node,
                                  uint8_t* __restrict__ crit) {
@@ -58,7 +58,7 @@ __global__ void criterion_kernel(const BaseGrid g, const real* __restrict__ W, i
   }
 }
 
-__global__ void buffer_kernel(const BaseGrid g, const uint8_t* __restrict__ crit,
+__global__ void adapt_buffer_kernel(const BaseGrid g, const uint8_t* __restrict__ crit,
                               const int32_t* __restrict__ node_of, uint8_t* __restrict__ refined,
                               int32_t* __restrict__ cnt, int32_t* __restrict__ changed) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -87,7 +87,7 @@ __global__ void buffer_kernel(const BaseGrid g, const uint8_t* __restrict__ crit
   if (any != (node_of[b] >= 0 ? 1 : 0)) atomicAdd(changed, 1);
 }
 
-__global__ void counts_kernel(const BaseGrid g, const uint8_t* __restrict__ refined,
+__global__ void adapt_counts_kernel(const BaseGrid g, const uint8_t* __restrict__ refined,
                               const int32_t* __restrict__ node_of, int32_t* __restrict__ cnt,
                               int32_t* __restrict__ changed) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -127,7 +127,7 @@ __device__ inline int block_exclusive(int v, int* total) {
   return before;
 }
 
-__global__ void scan_reduce_kernel(const int32_t* __restrict__ in, int64_t n, int32_t* __restrict__ bsum) {
+__global__ void regrid_scan_reduce_kernel(const int32_t* __restrict__ in, int64_t n, int32_t* __restrict__ bsum) {
   const int64_t base = (int64_t)blockIdx.x * SC_B;
   int s = 0;
   for (int i = threadIdx.x; i < SC_B; i += SC_T)
@@ -138,7 +138,7 @@ __global__ void scan_reduce_kernel(const int32_t* __restrict__ in, int64_t n, in
 }
 
 // one block: exclusive scan of the block sums in place; *grand = their total
-__global__ void scan_blocks_kernel(int32_t* __restrict__ bsum, int nb, int32_t* __restrict__ grand) {
+__global__ void regrid_scan_blocks_kernel(int32_t* __restrict__ bsum, int nb, int32_t* __restrict__ grand) {
   int carry = 0;
   for (int base = 0; base < nb; base += SC_T) {
     const int i = base + threadIdx.x;
@@ -151,7 +151,7 @@ __global__ void scan_blocks_kernel(int32_t* __restrict__ bsum, int nb, int32_t* 
   if (threadIdx.x == 0) *grand = carry;
 }
 
-__global__ void scan_down_kernel(const int32_t* __restrict__ in, int64_t n, const int32_t* __restrict__ bsum,
+__global__ void regrid_scan_down_kernel(const int32_t* __restrict__ in, int64_t n, const int32_t* __restrict__ bsum,
                                  int32_t* __restrict__ out) {
   const int64_t base = (int64_t)blockIdx.x * SC_B + (int64_t)threadIdx.x * SC_V;
   int v[SC_V];
@@ -171,7 +171,7 @@ __global__ void scan_down_kernel(const int32_t* __restrict__ in, int64_t n, cons
 }
 
 // ---- tables of the new mesh ----
-__global__ void cells_kernel(const BaseGrid g, const int32_t* __restrict__ first, int32_t* __restrict__ node_of,
+__global__ void regrid_cells_kernel(const BaseGrid g, const int32_t* __restrict__ first, int32_t* __restrict__ node_of,
                              int nc, int8_t* __restrict__ level, int32_t* __restrict__ coord,
                              int32_t* __restrict__ node_children) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -205,7 +205,7 @@ __global__ void cells_kernel(const BaseGrid g, const int32_t* __restrict__ first
 // -(node + 2) for a finer node across the side of a coarse cell; face counts:
 // region 1 [dim][nc] conforming and boundary entries, region 2 [dim][nc][2]
 // sub-face entries of coarse sides
-__global__ void nbr_kernel(const BaseGrid g, const int32_t* __restrict__ first, const int32_t* __restrict__ node_of,
+__global__ void regrid_nbr_kernel(const BaseGrid g, const int32_t* __restrict__ first, const int32_t* __restrict__ node_of,
                            int nc, const int8_t* __restrict__ level, const int32_t* __restrict__ coord,
                            int32_t* __restrict__ nbr, uint8_t* __restrict__ scoarse, int32_t* __restrict__ cnt) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -241,7 +241,7 @@ __global__ void nbr_kernel(const BaseGrid g, const int32_t* __restrict__ first, 
   }
 }
 
-__global__ void faces_kernel(const BaseGrid g, int nc, const int8_t* __restrict__ level,
+__global__ void regrid_faces_kernel(const BaseGrid g, int nc, const int8_t* __restrict__ level,
                              const int32_t* __restrict__ nbr, const int32_t* __restrict__ node_children,
                              const int32_t* __restrict__ off, int32_t* __restrict__ fm, int32_t* __restrict__ fp,
                              uint8_t* __restrict__ finfo, int32_t* __restrict__ sface) {
@@ -289,7 +289,7 @@ __global__ void faces_kernel(const BaseGrid g, int nc, const int8_t* __restrict_
 
 // one thread per output weight W_new[v][j][c]: blockIdx.y = v * N + j, cells along x
 template <typename real>
-__global__ void project_kernel(const BaseGrid g, int N, const double* __restrict__ P,
+__global__ void adapt_project_kernel(const BaseGrid g, int N, const double* __restrict__ P,
                                const int32_t* __restrict__ first0, const int32_t* __restrict__ node0,
                                const real* __restrict__ Wold, int nc0, const int8_t* __restrict__ level1,
                                const int32_t* __restrict__ coord1, int nc1, real* __restrict__ Wnew) {
@@ -331,10 +331,10 @@ cudaError_t launch_adapt_criterion(const BaseGrid& g, const void* W, int esize, 
                                    double thr_leaf, double thr_node, uint8_t* crit, cudaStream_t s) {
   if (g.nbase == 0) return cudaSuccess;
   if (esize == 8)
-    criterion_kernel<double><<<grid_for(g.nbase), RG_THREADS, 0, s>>>(
+    adapt_criterion_kernel<double><<<grid_for(g.nbase), RG_THREADS, 0, s>>>(
         g, static_cast<const double*>(W), N, ncells, first, node_of, P, thr_leaf, thr_node, crit);
   else
-    criterion_kernel<float><<<grid_for(g.nbase), RG_THREADS, 0, s>>>(
+    adapt_criterion_kernel<float><<<grid_for(g.nbase), RG_THREADS, 0, s>>>(
         g, static_cast<const float*>(W), N, ncells, first, node_of, P, thr_leaf, thr_node, crit);
   return cudaGetLastError();
 }
@@ -342,14 +342,14 @@ cudaError_t launch_adapt_criterion(const BaseGrid& g, const void* W, int esize, 
 cudaError_t launch_adapt_buffer(const BaseGrid& g, const uint8_t* crit, const int32_t* node_of,
                                 uint8_t* refined, int32_t* cnt, int32_t* changed, cudaStream_t s) {
   if (g.nbase == 0) return cudaSuccess;
-  buffer_kernel<<<grid_for(g.nbase), RG_THREADS, 0, s>>>(g, crit, node_of, refined, cnt, changed);
+  adapt_buffer_kernel<<<grid_for(g.nbase), RG_THREADS, 0, s>>>(g, crit, node_of, refined, cnt, changed);
   return cudaGetLastError();
 }
 
 cudaError_t launch_adapt_counts(const BaseGrid& g, const uint8_t* refined, const int32_t* node_of,
                                 int32_t* cnt, int32_t* changed, cudaStream_t s) {
   if (g.nbase == 0) return cudaSuccess;
-  counts_kernel<<<grid_for(g.nbase), RG_THREADS, 0, s>>>(g, refined, node_of, cnt, changed);
+  adapt_counts_kernel<<<grid_for(g.nbase), RG_THREADS, 0, s>>>(g, refined, node_of, cnt, changed);
   return cudaGetLastError();
 }
 
@@ -358,16 +358,16 @@ size_t scan_work_ints(int64_t n) { return (size_t)((n + SC_B - 1) / SC_B) + 1; }
 cudaError_t launch_scan(const int32_t* in, int64_t n, int32_t* out, int32_t* work, cudaStream_t s) {
   const int nb = (int)((n + SC_B - 1) / SC_B);
   if (nb == 0) return cudaMemsetAsync(out, 0, sizeof(int32_t), s);
-  scan_reduce_kernel<<<nb, SC_T, 0, s>>>(in, n, work);
-  scan_blocks_kernel<<<1, SC_T, 0, s>>>(work, nb, out + n);
-  scan_down_kernel<<<nb, SC_T, 0, s>>>(in, n, work, out);
+  regrid_scan_reduce_kernel<<<nb, SC_T, 0, s>>>(in, n, work);
+  regrid_scan_blocks_kernel<<<1, SC_T, 0, s>>>(work, nb, out + n);
+  regrid_scan_down_kernel<<<nb, SC_T, 0, s>>>(in, n, work, out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_regrid_cells(const BaseGrid& g, const int32_t* first, int32_t* node_of, int ncells,
                                 int8_t* level, int32_t* coord, int32_t* node_children, cudaStream_t s) {
   if (g.nbase == 0) return cudaSuccess;
-  cells_kernel<<<grid_for(g.nbase), RG_THREADS, 0, s>>>(g, first, node_of, ncells, level, coord, node_children);
+  regrid_cells_kernel<<<grid_for(g.nbase), RG_THREADS, 0, s>>>(g, first, node_of, ncells, level, coord, node_children);
   return cudaGetLastError();
 }
 
@@ -375,7 +375,7 @@ cudaError_t launch_regrid_nbr(const BaseGrid& g, const int32_t* first, const int
                               const int8_t* level, const int32_t* coord, int32_t* nbr, uint8_t* scoarse,
                               int32_t* face_cnt, cudaStream_t s) {
   if (ncells == 0) return cudaSuccess;
-  nbr_kernel<<<grid_for(ncells), RG_THREADS, 0, s>>>(g, first, node_of, ncells, level, coord, nbr, scoarse,
+  regrid_nbr_kernel<<<grid_for(ncells), RG_THREADS, 0, s>>>(g, first, node_of, ncells, level, coord, nbr, scoarse,
                                                       face_cnt);
   return cudaGetLastError();
 }
@@ -385,7 +385,7 @@ cudaError_t launch_regrid_faces(const BaseGrid& g, int ncells, const int8_t* lev
                                 int32_t* fp, uint8_t* finfo, int32_t* sface, cudaStream_t s) {
   const int64_t n = (int64_t)g.dim * ncells;
   if (n == 0) return cudaSuccess;
-  faces_kernel<<<grid_for(n), RG_THREADS, 0, s>>>(g, ncells, level, nbr, node_children, face_off, fm, fp,
+  regrid_faces_kernel<<<grid_for(n), RG_THREADS, 0, s>>>(g, ncells, level, nbr, node_children, face_off, fm, fp,
                                                    finfo, sface);
   return cudaGetLastError();
 }
@@ -397,11 +397,11 @@ cudaError_t launch_adapt_project(const BaseGrid& g, int esize, int nv, int N, co
   if (ncells1 == 0) return cudaSuccess;
   const dim3 grid(grid_for(ncells1), nv * N);
   if (esize == 8)
-    project_kernel<double><<<grid, RG_THREADS, 0, s>>>(g, N, P, first0, node0, static_cast<const double*>(Wold),
+    adapt_project_kernel<double><<<grid, RG_THREADS, 0, s>>>(g, N, P, first0, node0, static_cast<const double*>(Wold),
                                                        ncells0, level1, coord1, ncells1,
                                                        static_cast<double*>(Wnew));
   else
-    project_kernel<float><<<grid, RG_THREADS, 0, s>>>(g, N, P, first0, node0, static_cast<const float*>(Wold),
+    adapt_project_kernel<float><<<grid, RG_THREADS, 0, s>>>(g, N, P, first0, node0, static_cast<const float*>(Wold),
                                                       ncells0, level1, coord1, ncells1,
                                                       static_cast<float*>(Wnew));
   return cudaGetLastError();

@@ -375,8 +375,9 @@ class Solver:
         return {k: (cnt[i], ms[i]) for i, k in enumerate(KERNEL_KINDS)}
 
     def limiter_counts(self, reset=False, out=None):
-        """device int64[2]: cell passes changed by the slope / positivity limiter"""
-        out = torch.zeros(2, dtype=torch.int64, device=self.device) if out is None else out
+        """device int64[3]: cell passes changed by the slope / positivity limiter,
+        and cell passes examined by the FP64 positivity pass"""
+        out = torch.zeros(3, dtype=torch.int64, device=self.device) if out is None else out
         self._check(self._L.dg_limiter_counts(self._h, _ptr(out), int(bool(reset)), _stream()))
         return out
 

@@ -204,7 +204,7 @@ def test_limiter_counts_match_changed_cells(precision):
         assert cnt[0] == changed and cnt[1] == 0
     else:  # FP32 decisions may differ on a cell whose slope sits at the minmod threshold
         assert abs(int(cnt[0]) - changed) <= max(1, changed // 100) and cnt[1] == 0
-    assert list(s.limiter_counts().cpu().numpy()) == [0, 0]
+    assert list(s.limiter_counts().cpu().numpy()) == [0, 0, 0]
 
 
 def test_positivity_only_fp64():
