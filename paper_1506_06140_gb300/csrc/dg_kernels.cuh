@@ -898,7 +898,7 @@ cudaError_t launch_cell(const void* pa, cudaStream_t s) {
                      : CT::TC;
   if (a.accel) {  // gravity: the default tile only
     cell_update_kernel<real, DIM, K, CT::TC, true><<<(a.m.ncells + CT::TC - 1) / CT::TC, CT::TC * NV,
-                                                     CT::smem(CT::TC), s>>>(a);
+                                                     CT::smem(CT::TC, true), s>>>(a);
     return cudaGetLastError();
   }
   const int grid = (a.m.ncells + tc - 1) / tc;
@@ -946,7 +946,7 @@ cudaError_t prepare_kernels() {
     if constexpr (CT::TC_MAX >= 64) e = cudaFuncSetAttribute(cell_update_kernel<real, DIM, K, 64>, attr, (int)CT::smem(64));
   }
   if (e != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(cell_update_kernel<real, DIM, K, CT::TC, true>, attr, (int)CT::smem(CT::TC))) !=
+  if ((e = cudaFuncSetAttribute(cell_update_kernel<real, DIM, K, CT::TC, true>, attr, (int)CT::smem(CT::TC, true))) !=
       cudaSuccess)
     return e;
   if ((e = cudaFuncSetAttribute(face_flux_kernel<real, DIM, K, 16>, attr, (int)FT::smem(16))) != cudaSuccess) return e;

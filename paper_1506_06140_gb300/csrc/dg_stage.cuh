@@ -445,12 +445,22 @@ __global__ void __launch_bounds__(FB * Shape<DIM, K>::NV)
 template <typename real, int DIM, int K>
 struct CellTile {
   using S = Shape<DIM, K>;
+  // per cell: the nodal state [NV][Q] and the point fluxes [DIM][NV][Q].  The
+  // fluxes of direction 0 overwrite the nodal state (a thread overwrites only
+  // the point values it has itself just read), except in the gravity variant,
+  // whose source term reads the nodal state after the fluxes.
   static constexpr size_t PER_CELL = (size_t)(S::NV * S::Q + DIM * S::NV * S::Q) * sizeof(real);
+  static constexpr size_t PER_CELL_ALIASED = (size_t)(DIM * S::NV * S::Q) * sizeof(real);
   // cells per block: TC (the default) is a template parameter, instantiated
   // for 16, 32 and 64 up to TC_MAX and selected at launch (StageArgs::cell_tile)
   static constexpr int TC = PER_CELL * 32 > 96 * 1024 ? 16 : 32;
   static constexpr int TC_MAX = PER_CELL * 64 <= 200 * 1024 ? 64 : (PER_CELL * 32 <= 200 * 1024 ? 32 : 16);
-  static constexpr size_t smem(int tc) { return PER_CELL * tc; }
+  static constexpr size_t smem(int tc, bool grav = false) { return (grav ? PER_CELL : PER_CELL_ALIASED) * tc; }
+  // the 3D FP32 kernels are latency-bound: ask for 20 resident warps per SM
+  // (at most ~102 registers per thread); elsewhere no register target
+  static constexpr int min_blocks(int tc) {
+    return (DIM == 3 && sizeof(real) == 4) ? (640 / (tc * S::NV) > 1 ? 640 / (tc * S::NV) : 1) : 1;
+  }
 };
 
 // Face fluxes of the conforming sides of a cell are loaded at the start of
@@ -507,13 +517,13 @@ __device__ __forceinline__ void surface_from_faces(const StageArgs<real>& a, int
 }
 
 template <typename real, int DIM, int K, int TC, bool GRAV = false>
-__global__ void __launch_bounds__(TC * Shape<DIM, K>::NV)
+__global__ void __launch_bounds__(TC * Shape<DIM, K>::NV, CellTile<real, DIM, K>::min_blocks(TC))
     cell_update_kernel(const StageArgs<real> a) {
   using S = Shape<DIM, K>;
   constexpr int NV = S::NV, Q = S::Q, N = S::N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  real* sU = reinterpret_cast<real*>(smem_raw);  // [NV][Q][TC]
-  real* sF = sU + NV * Q * TC;                   // [DIM][NV][Q][TC]
+  real* sU = reinterpret_cast<real*>(smem_raw);    // [NV][Q][TC]
+  real* sF = GRAV ? sU + NV * Q * TC : sU;         // [DIM][NV][Q][TC] (direction 0 over sU)
   const int tc = threadIdx.x % TC, v = threadIdx.x / TC;
   const int nc = a.m.ncells;
   const int c = blockIdx.x * TC + tc;
