@@ -283,7 +283,8 @@ int dg_set_gravity(dg_handle* h, const double* accel_dev, void* stream);
  * Synchronises `stream` once (to size the face arrays); buffers that no
  * longer fit are reallocated.  Afterwards every entry point works on the new
  * mesh (dg_sizes reports its counts; cached step graphs are recorded anew).
- * DG_ERR_ARG when no refinement is marked. */
+ * DG_ERR_ARG when no refinement is marked; after DG_ERR_OOM or DG_ERR_CUDA
+ * from dg_regrid the handle's tables are incomplete and it must be destroyed. */
 int dg_adapt_mark(dg_handle* h, const void* W_dev, double w_t, double alpha, int32_t* flags_host,
                   int64_t* n_cells_new, int64_t* n_changed, void* stream);
 int dg_adapt_set(dg_handle* h, const int32_t* flags_host, int64_t* n_cells_new, int64_t* n_changed,

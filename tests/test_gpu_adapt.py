@@ -132,6 +132,23 @@ def test_regrid_sequence_matches_created_handles(dim, n, k, precision):
         _same_handle(s, fresh, seed=30 + i, limiter=bool(limiter))
 
 
+@pytest.mark.parametrize("dim,n,bc", [(2, [1, 1], wl.BC_PERIODIC), (2, [1, 3], wl.BC_TRANSMISSIVE),
+                                      (3, [1, 1, 1], wl.BC_PERIODIC), (3, [2, 1, 1], wl.BC_TRANSMISSIVE)],
+                         ids=["2d-1x1", "2d-1x3-open", "3d-1x1x1", "3d-2x1x1-open"])
+def test_regrid_degenerate_meshes(dim, n, bc):
+    """a single periodic base cell (refined: its children are each other's
+    neighbours across the wrap) and one-cell-wide strips"""
+    nb = int(np.prod(n))
+    s = solver(mesh(dim, n, bc=bc), k=1)
+    W = torch.as_tensor(wl.random_weights(dim, s.N, s.n_cells, seed=3, slope=0.05), device="cuda")
+    seq = [np.ones(nb, np.int32), (np.arange(nb) % 2).astype(np.int32), np.zeros(nb, np.int32)]
+    for i, flags in enumerate(seq):
+        s.set_refinement(flags)
+        W = s.regrid(W)
+        fresh = solver(mesh(dim, n, flags, bc=bc), k=1)
+        _same_handle(s, fresh, seed=50 + i, limiter=False)
+
+
 @pytest.mark.parametrize("dim,n", [(2, [9, 7]), (3, [5, 4, 3])], ids=["2d", "3d"])
 def test_projection_matches_oracle(dim, n):
     nb = int(np.prod(n))
