@@ -814,6 +814,75 @@ def run_square_growth(args):
     return 0
 
 
+def run_sedov_taylor(args):
+    """Sedov-Taylor blast of Sec. 5.3 at the paper's resolution: 64^3 cells in
+    [0,1]^3, rho = 1, p = 1e-6, gamma = 5/3, E = 1 in the eight central
+    cells, DG-2 and DG-3 with the characteristic TVB and positivity limiters
+    (FP64 state, FP32 perturbation-form right-hand side), run to t = 0.05; shock front against R_0 (E t^2 / rho)^(1/5)
+    with the printed R_0 ~ 1.152 (0.3477 at t = 0.05)."""
+    import torch
+    from paper_1506_06140_gb300 import dg
+    from paper_1506_06140_gb300 import workloads as wl
+    torch.cuda.set_device(0)
+    n, gamma, t_end = 64, 5.0 / 3.0, 0.05
+    r_exact = 1.152 * (t_end ** 2) ** 0.2
+    m = wl.mesh_uniform(3, [n] * 3, [0.0] * 3, [1.0] * 3, bc=[wl.BC_TRANSMISSIVE] * 3)
+    out = {"metric": "Sedov-Taylor shock radius at t = 0.05 and step rate",
+           "config": {"workload": "Sedov-Taylor 3D, 64^3, rho 1, p 1e-6, gamma 5/3, E 1 in the 8 central cells, "
+                                  "characteristic TVB + positivity limiters, FP64 state with the FP32 perturbation-form "
+                                  "right-hand side (mixed), CFL 0.2", "t_end": t_end,
+                      "analytic_radius": r_exact}, "runs": []}
+    for k, rk in ((1, 2), (2, 3)):
+        s = dg.Solver(m, k, gamma, rk_order=rk, cfl=CFL, limiter="characteristic", positivity=True,
+                      precision="mixed")
+        W = s.project(torch.as_tensor(wl.sedov3d(s.quad_points().cpu().numpy(), gamma=gamma, p0=1e-6,
+                                                 energy=1.0, half_width=1.0 / n)))
+        s.limit(W)
+        tot0 = s.totals(W).cpu().numpy()
+        chunk, t, steps, last, ms = 200, 0.0, 0, 0.0, 0.0
+        hist = s.dt_buffer(chunk)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        while t + 1.5 * chunk * last < t_end:
+            e0.record()
+            s.advance(W, chunk, hist)
+            e1.record()
+            h = hist.cpu().numpy()
+            ms += e0.elapsed_time(e1)
+            t += h.sum()
+            last = h[-1]
+            steps += chunk
+        graph_steps = steps
+        dt_buf = s.scalar()
+        while t < t_end - 1e-15:
+            s.compute_dt(W, dt_buf)
+            dt = min(dt_buf.item(), t_end - t)
+            s.rk_step(W, dt)
+            t += dt
+            steps += 1
+        c = s.quad_points().mean(dim=1).cpu().numpy()
+        r = np.sqrt(((c - 0.5) ** 2).sum(axis=0))
+        rho = W[0, 0].double().cpu().numpy()
+        dr = 0.5 / n
+        b = (r / dr).astype(int)
+        prof = np.bincount(b, weights=rho) / np.maximum(np.bincount(b), 1)
+        ip = int(np.argmax(prof))
+        half = 1.0 + 0.5 * (prof[ip] - 1.0)
+        o = ip + int(np.argmax(prof[ip:] < half))
+        front = (o - 0.5) * dr + dr * (prof[o - 1] - half) / (prof[o - 1] - prof[o])
+        tot1 = s.totals(W).cpu().numpy()
+        run = {"dg": k + 1, "steps": steps, "front_radius": float(front), "peak_radius": float((ip + 0.5) * dr),
+               "front_rel_err": float(front / r_exact - 1.0), "peak_compression": float(prof[ip]),
+               "mass_drift_rel": float(abs(tot1[0] - tot0[0]) / tot0[0]),
+               "energy_drift_rel": float(abs(tot1[-1] - tot0[-1]) / tot0[-1]),
+               "status": s.status(),
+               "graph_ms_per_step": ms / max(graph_steps, 1),
+               "dof_updates_per_s": s.n_cells * s.N * rk * graph_steps / (ms * 1e-3) if ms > 0 else None}
+        out["runs"].append(run)
+        print(json.dumps(run), flush=True)
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def cpu_baseline(n_sample=128, max_seconds=20.0):
     """The oracle, as it stands, on a bounded sample of the workload: the
     vortex on a 128^2 periodic box with the same cell size, k and RK4."""
@@ -880,15 +949,17 @@ def main():
                     choices=["both", "fp64", "fp32", "fp32_tc", "mixed", "mixed_tc"],
                     help="run one precision only (profiling); the JSON line needs both")
     ap.add_argument("--workload", default="vortex",
-                    choices=sorted(WORKLOADS) + ["adjoint3d", "l1study", "square_growth"])
+                    choices=sorted(WORKLOADS) + ["adjoint3d", "l1study", "square_growth", "sedov_taylor"])
     ap.add_argument("--t-end", type=float, default=2.0, help="l1study, square_growth: final time")
     ap.add_argument("--size", type=int, default=128, help="adjoint3d: cells per axis")
     args = ap.parse_args()
-    if args.workload in ("adjoint3d", "l1study", "square_growth"):
+    if args.workload in ("adjoint3d", "l1study", "square_growth", "sedov_taylor"):
         from paper_1506_06140_gb300 import build
         build.build()
         if args.workload == "adjoint3d":
             return run_adjoint(args)
+        if args.workload == "sedov_taylor":
+            return run_sedov_taylor(args)
         return run_l1_study(args) if args.workload == "l1study" else run_square_growth(args)
     wprec = WORKLOADS[args.workload]["precisions"]
     args.precisions = wprec if args.precision == "both" else (args.precision,)
