@@ -61,7 +61,10 @@ enum { DG_LIMITER_NONE = 0, DG_LIMITER_COMPONENT = 1, DG_LIMITER_CHARACTERISTIC 
  *             the point and face fluxes it integrates, which leaves the
  *             discrete right-hand side unchanged and makes the FP32 rounding
  *             scale with the solution's variation rather than its size.  The
- *             CFL timestep, limiters, totals and the adjoint run in FP64.
+ *             CFL timestep, totals, the positivity limiter's decisions and
+ *             the adjoint run in FP64; the slope limiter's arithmetic runs in
+ *             FP32 on the rounded state (a cell it leaves alone keeps its
+ *             FP64 weights exactly).
  * DG_MIXED_TC: DG_MIXED with the cell kernel's two contractions on the
  *             tensor cores (split TF32, FP32 accumulation); 2D uniform meshes,
  *             k = 1..3. */

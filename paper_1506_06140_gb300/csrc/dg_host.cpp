@@ -985,6 +985,7 @@ int run_limit(dg_handle* h, const void* src, void* dst, cudaStream_t s) {
   la.Mtilde = h->opt.Mtilde;
   la.positivity = h->opt.positivity;
   la.eps = h->opt.eps;
+  la.fp32_slopes = h->ms != nullptr;  // DG_MIXED: FP32 slope-limiter arithmetic on the FP64 state
   la.counts = h->lim_counts;
   la.queue = h->lim_queue;
   la.queue_len = h->lim_queue + std::max(h->ncells, 1);

@@ -156,7 +156,8 @@ struct LimitArgs {
   double beta = 1.0, Mtilde = 0.5;
   int positivity = 0;
   double eps = 1e-10;
-  unsigned long long* counts = nullptr;  // [2] cells changed by the slope / positivity limiter
+  int fp32_slopes = 0;            // FP64 state: run the slope limiter on FP32-rounded values
+  unsigned long long* counts = nullptr;  // [3] cells changed by the slope / positivity limiter, FP64-pass cells
   int* queue = nullptr;          // [ncells] cells left to the positivity pass
   int* queue_len = nullptr;      // their number
   int* status = nullptr;

@@ -315,11 +315,17 @@ __device__ double positivity_tau(const double* ub, const double* u, double gamma
   return fmin(fmax(tau, 0.0), 1.0);
 }
 
+// slope-limiter parameters: 1 component-wise, 2 characteristic (Secs. 3.2-3.3)
+struct LimParams {
+  int limiter;
+  double beta, Mtilde;
+};
+
 // characteristic (or component-wise) slopes of direction A, limited, in the
-// state's precision: ct = minmodB(sqrt(3) L w_(1+A), beta L (ubar - u_minus),
+// precision `real`: ct = minmodB(sqrt(3) L w_(1+A), beta L (ubar - u_minus),
 // beta L (u_plus - ubar)) / sqrt(3)
 template <typename real, int DIM, int K, int A>
-__device__ __forceinline__ bool limit_direction(const LimitArgs<real>& a, const CharState<real, DIM>& st,
+__device__ __forceinline__ bool limit_direction(const LimParams& a, const CharState<real, DIM>& st,
                                                 const real (&w)[DIM + 2][Shape<DIM, K>::N],
                                                 const real* mean, const real* mm, const real* mp, real dx,
                                                 real* ct) {
@@ -357,7 +363,7 @@ __device__ __forceinline__ bool limit_direction(const LimitArgs<real>& a, const 
 }
 
 template <typename real, int DIM, int K, int A>
-__device__ __forceinline__ void unlimit_direction(const LimitArgs<real>& a, const CharState<real, DIM>& st,
+__device__ __forceinline__ void unlimit_direction(const LimParams& a, const CharState<real, DIM>& st,
                                                   const real* ct, real (&w)[DIM + 2][Shape<DIM, K>::N]) {
   constexpr int NV = DIM + 2;
   real x[NV];
@@ -371,9 +377,6 @@ __device__ __forceinline__ void unlimit_direction(const LimitArgs<real>& a, cons
   for (int v = 0; v < NV; ++v) w[v][1 + A] = x[v];
 }
 
-// One thread per cell.  The slope limiter runs in the state's precision;
-// the positivity limiter (its shortcut bound, the density and pressure
-// checks and tau) in FP64.
 // Positivity test of one cell at the point set of the positivity limiter
 // (the set S of eq. union_quad_points, plus the fine sub-face points of every
 // side with a finer neighbour), in FP32.  A point value is a sum of N <= 20
@@ -439,6 +442,10 @@ __device__ bool points_clear_fp32(const MeshDev& m, const float* tab32, double e
   return true;
 }
 
+// One thread per cell.  The slope limiter runs in the state's precision (in
+// FP32 for an FP64 state when fp32_slopes is set: a cell it leaves alone
+// keeps its FP64 weights bit for bit); the positivity limiter's final
+// decisions in FP64 behind exact FP32 prechecks.
 template <typename real, int DIM, int K>
 __global__ void __launch_bounds__(128) limit_kernel(const LimitArgs<real> a) {
   using S = Shape<DIM, K>;
@@ -464,7 +471,7 @@ __global__ void __launch_bounds__(128) limit_kernel(const LimitArgs<real> a) {
   }
   if constexpr (K > 0) {
     if (a.limiter != 0) {
-      const real dx = (real)cell_dx(a.m, c);
+      const LimParams lp{a.limiter, a.beta, a.Mtilde};
       // neighbour means of all sides first: the index loads, then the mean
       // loads, each batch independent
       int nbs[2 * DIM];
@@ -473,23 +480,63 @@ __global__ void __launch_bounds__(128) limit_kernel(const LimitArgs<real> a) {
       real nbm[2 * DIM][NV];
 #pragma unroll
       for (int sd = 0; sd < 2 * DIM; ++sd) nb_mean<real, DIM, K>(a, c, sd >> 1, sd & 1, nbs[sd], mean, nbm[sd]);
-      const CharState<real, DIM> st =
-          a.limiter == 2 ? char_state<real, DIM>(mean, real(a.gamma)) : CharState<real, DIM>{};
-      real ct[DIM][NV];
-      bool changed = limit_direction<real, DIM, K, 0>(a, st, w, mean, nbm[0], nbm[1], dx, ct[0]);
-      changed = limit_direction<real, DIM, K, 1>(a, st, w, mean, nbm[2], nbm[3], dx, ct[1]) || changed;
-      if constexpr (DIM == 3)
-        changed = limit_direction<real, DIM, K, DIM - 1>(a, st, w, mean, nbm[4], nbm[5], dx, ct[DIM - 1]) || changed;
-      if (changed) {
-        if (a.counts) atomicAdd(a.counts, 1ull);
-        unlimit_direction<real, DIM, K, 0>(a, st, ct[0], w);
-        unlimit_direction<real, DIM, K, 1>(a, st, ct[1], w);
-        if constexpr (DIM == 3) unlimit_direction<real, DIM, K, DIM - 1>(a, st, ct[DIM - 1], w);
-        // the degree of phi_l is >= 2 exactly for l > DIM (total-degree order)
+      bool done = false;
+      if constexpr (sizeof(real) == 8) {
+        if (a.fp32_slopes) {
+          // the same limiter on the FP32-rounded weights and means
+          float wf[NV][N], mf[NV], nf[2 * DIM][NV];
 #pragma unroll
-        for (int l = DIM + 1; l < N; ++l)
+          for (int v = 0; v < NV; ++v) {
+            mf[v] = f32_round(mean[v]);
 #pragma unroll
-          for (int v = 0; v < NV; ++v) w[v][l] = real(0);
+            for (int l = 0; l < N; ++l) wf[v][l] = f32_round(w[v][l]);
+#pragma unroll
+            for (int sd = 0; sd < 2 * DIM; ++sd) nf[sd][v] = f32_round(nbm[sd][v]);
+          }
+          const float dxf = (float)cell_dx(a.m, c);
+          const CharState<float, DIM> st =
+              a.limiter == 2 ? char_state<float, DIM>(mf, (float)a.gamma) : CharState<float, DIM>{};
+          float ct[DIM][NV];
+          bool changed = limit_direction<float, DIM, K, 0>(lp, st, wf, mf, nf[0], nf[1], dxf, ct[0]);
+          changed = limit_direction<float, DIM, K, 1>(lp, st, wf, mf, nf[2], nf[3], dxf, ct[1]) || changed;
+          if constexpr (DIM == 3)
+            changed = limit_direction<float, DIM, K, DIM - 1>(lp, st, wf, mf, nf[4], nf[5], dxf, ct[DIM - 1]) || changed;
+          if (changed) {
+            if (a.counts) atomicAdd(a.counts, 1ull);
+            unlimit_direction<float, DIM, K, 0>(lp, st, ct[0], wf);
+            unlimit_direction<float, DIM, K, 1>(lp, st, ct[1], wf);
+            if constexpr (DIM == 3) unlimit_direction<float, DIM, K, DIM - 1>(lp, st, ct[DIM - 1], wf);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+#pragma unroll
+              for (int b = 0; b < DIM; ++b) w[v][1 + b] = f64_exact(wf[v][1 + b]);
+#pragma unroll
+              for (int l = DIM + 1; l < N; ++l) w[v][l] = real(0);
+            }
+          }
+          done = true;
+        }
+      }
+      if (!done) {
+        const real dx = (real)cell_dx(a.m, c);
+        const CharState<real, DIM> st =
+            a.limiter == 2 ? char_state<real, DIM>(mean, real(a.gamma)) : CharState<real, DIM>{};
+        real ct[DIM][NV];
+        bool changed = limit_direction<real, DIM, K, 0>(lp, st, w, mean, nbm[0], nbm[1], dx, ct[0]);
+        changed = limit_direction<real, DIM, K, 1>(lp, st, w, mean, nbm[2], nbm[3], dx, ct[1]) || changed;
+        if constexpr (DIM == 3)
+          changed = limit_direction<real, DIM, K, DIM - 1>(lp, st, w, mean, nbm[4], nbm[5], dx, ct[DIM - 1]) || changed;
+        if (changed) {
+          if (a.counts) atomicAdd(a.counts, 1ull);
+          unlimit_direction<real, DIM, K, 0>(lp, st, ct[0], w);
+          unlimit_direction<real, DIM, K, 1>(lp, st, ct[1], w);
+          if constexpr (DIM == 3) unlimit_direction<real, DIM, K, DIM - 1>(lp, st, ct[DIM - 1], w);
+          // the degree of phi_l is >= 2 exactly for l > DIM (total-degree order)
+#pragma unroll
+          for (int l = DIM + 1; l < N; ++l)
+#pragma unroll
+            for (int v = 0; v < NV; ++v) w[v][l] = real(0);
+        }
       }
     }
   }
