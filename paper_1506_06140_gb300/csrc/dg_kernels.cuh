@@ -385,10 +385,10 @@ __device__ __forceinline__ void unlimit_direction(const LimParams& a, const Char
 // rho >= u_0 - 2e-6 A_0 and likewise for |m_a| and E; the kinetic term
 // |m|_up^2 / (2 rho_lo) is rounded by at most 6 ulp (factor 1 + 1e-6) and the
 // pressure difference by 3 ulp of |E_lo| + kin (margin 1e-6).  True when
-// density and pressure clear 2 eps at every point.  The margins are tight
+// density and pressure clear rho_min and p_min at every point.  The margins are tight
 // enough for cold flows (p / E ~ 1e-5, Keplerian disc).
 template <int DIM, int K>
-__device__ bool points_clear_fp32(const MeshDev& m, const float* tab32, double eps, double gamma,
+__device__ bool points_clear_fp32(const MeshDev& m, const float* tab32, float rho_min, float p_min, double gamma,
                                   const float (&wf)[Shape<DIM, K>::NV][Shape<DIM, K>::N], int c) {
   using S = Shape<DIM, K>;
   constexpr int NV = S::NV, N = S::N;
@@ -398,7 +398,7 @@ __device__ bool points_clear_fp32(const MeshDev& m, const float* tab32, double e
   if (m.nnodes > 0)
     for (int sd = 0; sd < S::NSIDE; ++sd)
       if (m.nbr[(size_t)sd * nc + c] <= -2) finer |= 1u << sd;
-  const float feps2 = 2.0f * (float)eps, g1 = (float)(gamma - 1.0);
+  const float g1 = (float)(gamma - 1.0);
   const int npts = S::NSP + __popc(finer) * S::NSUB * S::QF;
   for (int ip = 0; ip < npts; ++ip) {
     const float* ph;
@@ -427,7 +427,7 @@ __device__ bool points_clear_fp32(const MeshDev& m, const float* tab32, double e
       A[v] = t;
     }
     const float rho_lo = u[0] - 2e-6f * A[0];
-    if (!(rho_lo >= feps2)) return false;
+    if (!(rho_lo >= rho_min)) return false;
     float m2 = 0.0f;
 #pragma unroll
     for (int b = 0; b < DIM; ++b) {
@@ -437,7 +437,7 @@ __device__ bool points_clear_fp32(const MeshDev& m, const float* tab32, double e
     const float e_lo = u[DIM + 1] - 2e-6f * A[DIM + 1];
     const float kin = 0.5f * m2 / rho_lo * (1.0f + 1e-6f);
     const float p_lo = g1 * (e_lo - kin);
-    if (!(p_lo >= feps2 + 1e-6f * g1 * (fabsf(e_lo) + kin))) return false;
+    if (!(p_lo >= p_min + 1e-6f * g1 * (fabsf(e_lo) + kin))) return false;
   }
   return true;
 }
@@ -574,16 +574,30 @@ __global__ void __launch_bounds__(128) limit_kernel(const LimitArgs<real> a) {
         lo[v] = wf[v][0] - r - 1e-6f * fabsf(wf[v][0]);
         up[v] = (fabsf(wf[v][0]) + r) * (1.0f + 1e-5f);
       }
-      const float feps = (float)a.eps;
-      if (lo[0] >= 2.0f * feps) {
+      // thresholds: twice the positivity pass's floors (eps; for an FP32 state
+      // also the rounding scale 2^-20 of the absolute weight sums, see
+      // positivity_kernel), so a cell that clears them is left alone there
+      float rho_min = 2.0f * (float)a.eps, p_min = rho_min;
+      if constexpr (sizeof(real) == 4) {
+        float ar = fabsf(wf[0][0]), ae = fabsf(wf[NV - 1][0]);
+#pragma unroll
+        for (int l = 1; l < N; ++l) {
+          ar += fabsf(wf[0][l]) * a.tab32[S::OFF_PMAX + l];
+          ae += fabsf(wf[NV - 1][l]) * a.tab32[S::OFF_PMAX + l];
+        }
+        rho_min = fmaxf(rho_min, 2.0f * 0x1p-20f * 1.01f * ar);
+        p_min = fmaxf(p_min, 2.0f * (float)(a.gamma - 1.0) * 0x1p-20f * 1.01f * ae);
+      }
+      if (lo[0] >= rho_min) {
         float m2 = 0.0f;
 #pragma unroll
         for (int b = 0; b < DIM; ++b) m2 += up[1 + b] * up[1 + b];
         const float kin = 0.5f * m2 / lo[0];
         const float p_low = (float)(a.gamma - 1.0) * (lo[DIM + 1] - kin);
-        if (p_low >= 2.0f * feps + 1e-5f * (fabsf(lo[DIM + 1]) + kin)) need_positivity = false;
+        if (p_low >= p_min + 1e-5f * (fabsf(lo[DIM + 1]) + kin)) need_positivity = false;
       }
-      if (need_positivity && points_clear_fp32<DIM, K>(a.m, a.tab32, a.eps, a.gamma, wf, c)) need_positivity = false;
+      if (need_positivity && points_clear_fp32<DIM, K>(a.m, a.tab32, rho_min, p_min, a.gamma, wf, c))
+        need_positivity = false;
     }
   }
 #pragma unroll
@@ -624,10 +638,28 @@ __global__ void __launch_bounds__(128) positivity_kernel(const LimitArgs<real> a
     for (int v = 0; v < NV; ++v)
 #pragma unroll
       for (int l = 0; l < N; ++l) w[v][l] = a.Uout[(size_t)(v * N + l) * nc + c];
-    const double eps = a.eps;
     double mean64[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) mean64[v] = (double)w[v][0];
+    // floors of density and pressure at the points: eps; for an FP32 state
+    // the limited weights are stored rounded to FP32, which moves point
+    // values by up to 2^-24 of the absolute weight sums (and the kinetic
+    // energy at a near-vacuum point far more), so the floors also keep a
+    // distance 2^-20 of those sums, at most half the mean
+    double eps_r = a.eps, eps_p = a.eps;
+    if constexpr (sizeof(real) == 4) {
+      double ar = fabs(mean64[0]), ae = fabs(mean64[NV - 1]), m2 = 0.0;
+#pragma unroll
+      for (int l = 1; l < N; ++l) {
+        ar += fabs((double)w[0][l]) * tab[S::OFF_PMAX + l];
+        ae += fabs((double)w[NV - 1][l]) * tab[S::OFF_PMAX + l];
+      }
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) m2 += mean64[1 + b] * mean64[1 + b];
+      const double pbar = (a.gamma - 1.0) * (mean64[NV - 1] - 0.5 * m2 / mean64[0]);
+      eps_r = fmax(eps_r, fmin(0x1p-20 * ar, 0.5 * mean64[0]));
+      eps_p = fmax(eps_p, fmin((a.gamma - 1.0) * 0x1p-20 * ae, 0.5 * pbar));
+    }
     // points: the union set S, plus fine sub-face points on sides with a finer neighbour
     unsigned finer = 0;
     if (a.m.nnodes > 0)
@@ -655,8 +687,8 @@ __global__ void __launch_bounds__(128) positivity_kernel(const LimitArgs<real> a
       rmin = fmin(rmin, rho);
     }
     rmin = warp_min(rmin);
-    if (rmin < eps) {
-      const double th1 = fmin(fabs((mean64[0] - eps) / (mean64[0] - rmin)), 1.0);
+    if (rmin < eps_r) {
+      const double th1 = fmin(fabs((mean64[0] - eps_r) / (mean64[0] - rmin)), 1.0);
 #pragma unroll
       for (int l = 1; l < N; ++l) w[0][l] = (real)((double)w[0][l] * th1);
     }
@@ -675,18 +707,18 @@ __global__ void __launch_bounds__(128) positivity_kernel(const LimitArgs<real> a
 #pragma unroll
       for (int b = 0; b < DIM; ++b) m2 += u[1 + b] * u[1 + b];
       const double pr = (a.gamma - 1.0) * (u[DIM + 1] - 0.5 * m2 / u[0]);
-      if (pr >= eps) continue;
-      th2 = fmin(th2, positivity_tau<DIM>(mean64, u, a.gamma, eps));
+      if (pr >= eps_p) continue;
+      th2 = fmin(th2, positivity_tau<DIM>(mean64, u, a.gamma, eps_p));
     }
     th2 = warp_min(th2);
-    if (lane == 0 && (rmin < eps || th2 < 1.0) && a.counts) atomicAdd(a.counts + 1, 1ull);
+    if (lane == 0 && (rmin < eps_r || th2 < 1.0) && a.counts) atomicAdd(a.counts + 1, 1ull);
     if (th2 < 1.0) {
 #pragma unroll
       for (int v = 0; v < NV; ++v)
 #pragma unroll
         for (int l = 1; l < N; ++l) w[v][l] = (real)((double)w[v][l] * th2);
     }
-    if (rmin < eps || th2 < 1.0) {
+    if (rmin < eps_r || th2 < 1.0) {
       // the lanes share the stores
 #pragma unroll
       for (int v = 0; v < NV; ++v)

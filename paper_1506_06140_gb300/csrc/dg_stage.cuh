@@ -456,10 +456,15 @@ struct CellTile {
   static constexpr int TC = PER_CELL * 32 > 96 * 1024 ? 16 : 32;
   static constexpr int TC_MAX = PER_CELL * 64 <= 200 * 1024 ? 64 : (PER_CELL * 32 <= 200 * 1024 ? 32 : 16);
   static constexpr size_t smem(int tc, bool grav = false) { return (grav ? PER_CELL : PER_CELL_ALIASED) * tc; }
-  // the 3D FP32 kernels are latency-bound: ask for 20 resident warps per SM
-  // (at most ~102 registers per thread); elsewhere no register target
+  // register targets of the FP32 kernels (latency- or issue-bound): 3D asks
+  // for 20 resident warps per SM (at most ~102 registers per thread), 2D for
+  // 48 registers per thread up to k = 2 and 64 at k = 3; FP64 (FP64-pipe
+  // bound) has none
+  static constexpr int fit(int tc, int regs) { return 65536 / (tc * S::NV * regs); }
   static constexpr int min_blocks(int tc) {
-    return (DIM == 3 && sizeof(real) == 4) ? (640 / (tc * S::NV) > 1 ? 640 / (tc * S::NV) : 1) : 1;
+    return sizeof(real) != 4 ? 1
+           : DIM == 3        ? (640 / (tc * S::NV) > 1 ? 640 / (tc * S::NV) : 1)
+                             : (fit(tc, K <= 2 ? 48 : 64) > 1 ? fit(tc, K <= 2 ? 48 : 64) : 1);
   }
 };
 
