@@ -94,7 +94,9 @@ typedef struct {
   double beta;       /* limiter parameter beta in [0.5, 1] */
   double Mtilde;     /* TVB bound: a slope is kept when |sqrt(3) slope| <= Mtilde * dx */
   int positivity;    /* 1: positivity limiter of Sec. 3.4 after every stage */
-  double eps;        /* positivity floor */
+  double eps;        /* positivity floor of density and pressure at the limiter's points; an FP32
+                        state also keeps 2^-20 of the absolute weight sums (at most half the mean),
+                        above the FP32 rounding of the stored limited weights */
   int precision;     /* DG_FP64, DG_FP32, DG_FP32_TC or DG_MIXED (state, fluxes and
                         contractions); the totals, L1 error, timestep and positivity
                         check stay FP64 */
