@@ -418,7 +418,8 @@ struct dg_handle {
   std::vector<unsigned char> dtab;  // its tables (host copy, passed by value at launch)
   void* tcB = nullptr;       // its B operands
   double* scal = nullptr;    // dt per problem [nprob]
-  unsigned long long* dt_bits = nullptr;  // per-problem max signal speed [nprob]
+  unsigned long long* dt_bits = nullptr;  // per-problem max signal speed [nprob] (zero between launches)
+  unsigned int* dt_done = nullptr;        // blocks of the dt kernel done (zero between launches)
   // ensembles
   int nprob = 1;
   std::vector<int32_t> prob;
@@ -1021,12 +1022,21 @@ double dt_factor(const dg_handle* h) {
 
 template <typename real>
 int compute_dt_impl(dg_handle* h, const void* W, double* copy, cudaStream_t s) {
-  DG_CUDA(h, cudaMemsetAsync(h->dt_bits, 0, sizeof(unsigned long long) * h->nprob, s));
   AuxArgs<real> a = aux_args<real>(h);
   a.W = static_cast<const real*>(W);
   const double fac = dt_factor(h);
   a.grav_factor = fac * std::sqrt(2.0 * h->gamma * (h->gamma - 1.0));
-  DG_CUDA(h, timed(h, DG_KERNEL_DT, s, [&] { return h->ks->dt(&a, s); }));
+  if (h->ncells > 0) {
+    // one launch: its last block finishes the timestep (dt_bits and dt_done
+    // are zero between launches)
+    a.dt_factor = fac;
+    a.dt_out = h->scal;
+    a.dt_copy = copy;
+    a.dt_done = h->dt_done;
+    DG_CUDA(h, timed(h, DG_KERNEL_DT, s, [&] { return h->ks->dt(&a, s); }));
+    return DG_OK;
+  }
+  DG_CUDA(h, cudaMemsetAsync(h->dt_bits, 0, sizeof(unsigned long long) * h->nprob, s));
   DG_CUDA(h, timed(h, DG_KERNEL_OTHER, s,
                    [&] { return launch_dt_finalize(h->dt_bits, h->nprob, fac, h->scal, copy, s); }));
   return DG_OK;
@@ -1394,6 +1404,12 @@ static int create_impl(const dg_mesh_desc* mesh, int nprob, int k, double gamma,
   h->scal = static_cast<double*>(p);
   if ((r = dalloc(h, (size_t)h->nprob * sizeof(unsigned long long), &p)) != DG_OK) return bail(r);
   h->dt_bits = static_cast<unsigned long long*>(p);
+  if (cudaMemset(h->dt_bits, 0, (size_t)h->nprob * sizeof(unsigned long long)) != cudaSuccess)
+    return bail(cuda_fail(h, cudaGetLastError(), "cudaMemset"));
+  if ((r = dalloc(h, sizeof(unsigned int), &p)) != DG_OK) return bail(r);
+  h->dt_done = static_cast<unsigned int*>(p);
+  if (cudaMemset(h->dt_done, 0, sizeof(unsigned int)) != cudaSuccess)
+    return bail(cuda_fail(h, cudaGetLastError(), "cudaMemset"));
   const int nblk = (h->ncells + 255) / 256 + 1;
   if ((r = dalloc(h, (size_t)nblk * 8 * sizeof(double), &p)) != DG_OK) return bail(r);
   h->partial = static_cast<double*>(p);

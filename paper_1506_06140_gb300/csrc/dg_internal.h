@@ -182,6 +182,12 @@ struct AuxArgs {
   int* status = nullptr;
   const real* accel = nullptr;    // [DIM][Q][ncells] external acceleration (gravity timestep bound)
   double grav_factor = 0.0;       // dt_factor * sqrt(2 gamma (gamma - 1))
+  // timestep finished in the dt kernel itself (nullptr: a separate finalize):
+  // the last block turns dt_bits into dt_out = dt_factor / speed and resets
+  // dt_bits and dt_done for the next launch
+  double* dt_out = nullptr;       // [nprob]
+  double* dt_copy = nullptr;      // [nprob] optional second copy
+  unsigned int* dt_done = nullptr;  // blocks finished
 };
 
 // Adjoint of one stage: given the stage state U and a cotangent G on dWdt(U),

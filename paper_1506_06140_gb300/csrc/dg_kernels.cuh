@@ -841,6 +841,26 @@ __global__ void __launch_bounds__(RED_THREADS) dt_kernel(const AuxArgs<real> a) 
     }
     if (cur >= 0) atomicMax(a.dt_bits + cur, (unsigned long long)__double_as_longlong(m));
   }
+  if (a.dt_out) {
+    // every thread's maxima are visible device-wide before the block counts
+    // itself done; the last block finishes the timestep and resets the maxima
+    __shared__ int last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(a.dt_done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (last) {
+      __threadfence();
+      const int np = a.m.nprob;
+      for (int p = threadIdx.x; p < np; p += blockDim.x) {
+        const double speed = __longlong_as_double((long long)atomicExch(a.dt_bits + p, 0ull));
+        const double v = speed > 0.0 ? a.dt_factor / speed : 0.0;
+        a.dt_out[p] = v;
+        if (a.dt_copy) a.dt_copy[p] = v;
+      }
+      if (threadIdx.x == 0) *a.dt_done = 0u;
+    }
+  }
 }
 
 template <typename real, int DIM, int K>
