@@ -117,3 +117,26 @@ def test_derefinement_conserves_means():
     # a non-polynomial fine state is not restored by refining again (information is lost)
     again = fine.adapt_project(coarse, Wc)
     assert np.abs(again - W).max() > 1e-3
+
+
+def test_adaptive_run_conserves_totals():
+    """Steps and adaptations together keep the totals to rounding: the DG step
+    is conservative on a periodic two-level mesh and both projections keep the
+    cell means of every base cell (eqs. ref_weights, deref_weights)."""
+    n = [12, 12]
+    o = oracle(2, n)
+    xyz = o.quad_points()
+    r2 = (xyz[0] - 0.4) ** 2 + (xyz[1] - 0.5) ** 2
+    rho = 1.0 + 0.6 * np.exp(-r2 / 0.15 ** 2)
+    W = o.project(wl.conserved(rho, [np.full_like(rho, 1.0), np.full_like(rho, 0.4)], np.ones_like(rho), 1.4))
+    t0 = o.totals(W)
+    refined_any = False
+    for _ in range(8):
+        W, _ = o.rk_step(W, 0.0)
+        flags = o.adapt_flags(W, WT, ALPHA)
+        o_new = oracle(2, n, boxes=boxes_of(flags, n))
+        W = o_new.adapt_project(o, W)
+        o = o_new
+        refined_any |= bool(flags.any())
+        np.testing.assert_allclose(o.totals(W), t0, rtol=1e-13, atol=1e-13)
+    assert refined_any
