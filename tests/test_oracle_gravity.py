@@ -154,3 +154,29 @@ def test_timestep_takes_the_gravity_bound():
         grav = cs / (np.sqrt(2 * GAMMA * (GAMMA - 1)) * 1.5 * g)
         assert o.compute_dt(W) == pytest.approx(min(hydro, grav), rel=1e-14)
         assert (grav < hydro) == expect_grav
+
+
+@pytest.mark.parametrize("rk", [2, 3, 4])
+def test_rk_step_with_constant_field_is_exact(rk):
+    """A uniform state in a constant field: no flux divergence, so
+    m(dt) = m0 + rho g dt and E(dt) = E0 + rho (v0 . g) dt + rho |g|^2 dt^2 / 2
+    (SSP-RK of order >= 2 integrates these polynomials in t exactly)."""
+    n, k = 6, 2
+    o = O.Oracle(2, [n, n], [0.0, 0.0], [1.0, 1.0], k, GAMMA, rk_order=rk)
+    xyz = o.quad_points()
+    rho0, p0, v0, g = 1.3, 0.8, np.array([0.3, -0.2]), np.array([0.7, -1.1])
+    o.set_accel(np.stack([np.full(xyz[0].shape, g[0]), np.full(xyz[0].shape, g[1])]))
+    W = o.project(wl.conserved(np.full(xyz[0].shape, rho0), [np.full(xyz[0].shape, v) for v in v0],
+                               np.full(xyz[0].shape, p0), GAMMA))
+    dt = 0.01
+    W1, _ = o.rk_step(W, dt)
+    dm = rho0 * g * dt
+    dE = rho0 * (v0 @ g) * dt + 0.5 * rho0 * (g @ g) * dt ** 2
+    # the increments; RK4 uses the tableau's printed digits, whose weights sum
+    # to 1 only to ~1e-10
+    rtol = 1e-11 if rk < 4 else 2e-10
+    np.testing.assert_allclose(W1[1, 0] - W[1, 0], dm[0], rtol=rtol)
+    np.testing.assert_allclose(W1[2, 0] - W[2, 0], dm[1], rtol=rtol)
+    np.testing.assert_allclose(W1[-1, 0] - W[-1, 0], dE, rtol=rtol)
+    np.testing.assert_allclose(W1[0], W[0], atol=1e-14)
+    np.testing.assert_allclose(W1[:, 1:], 0.0, atol=1e-13)  # still uniform
