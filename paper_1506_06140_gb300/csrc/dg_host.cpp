@@ -1223,24 +1223,31 @@ int autotune_tiles(dg_handle* h, cudaStream_t s) {
   const int fmax = h->ms ? h->ms->face_tile_max : h->ks->face_tile_max;
   const int cdef = h->ms ? h->ms->cell_tile : h->ks->cell_tile;
   const int fdef = h->ms ? h->ms->face_tile : h->ks->face_tile;
+  // a candidate replaces the default only when it is faster by more than the
+  // trials' noise (3%)
+  constexpr float kMargin = 0.97f;
   h->cell_tile = cdef;
   int best_f = fdef;
-  float best_t = 3.4e38f;
+  float best_t = 3.4e38f, def_t = 3.4e38f;
   for (int fb = 16; fb <= fmax; fb *= 2) {
     h->face_tile = fb;
     float t;
     if ((r = time_rhs(t)) != DG_OK) return r;
+    if (fb == fdef) def_t = t;
     if (t < best_t) { best_t = t; best_f = fb; }
   }
+  if (best_f != fdef && !(best_t < kMargin * def_t)) best_f = fdef;
   h->face_tile = best_f;
   if (!h->use_tc) {
     int best_c = cdef;
     bool best_direct = false;
     best_t = 3.4e38f;
+    def_t = 3.4e38f;
     for (int tc = 16; tc <= cmax; tc *= 2) {
       h->cell_tile = tc;
       float t;
       if ((r = time_rhs(t)) != DG_OK) return r;
+      if (tc == cdef) def_t = t;
       if (t < best_t) { best_t = t; best_c = tc; }
     }
     if (!h->dtab.empty()) {  // one thread per cell
@@ -1248,6 +1255,10 @@ int autotune_tiles(dg_handle* h, cudaStream_t s) {
       float t;
       if ((r = time_rhs(t)) != DG_OK) return r;
       if (t < best_t) { best_t = t; best_direct = true; }
+    }
+    if ((best_direct || best_c != cdef) && !(best_t < kMargin * def_t)) {
+      best_c = cdef;
+      best_direct = false;
     }
     h->cell_tile = best_c;
     h->use_direct = best_direct;
