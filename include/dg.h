@@ -217,8 +217,9 @@ int dg_n_problems(const dg_handle* h, int* n_problems, int64_t* cell_offsets_hos
  * state the step started from (the paper has no adjoint; this is the exact
  * transpose of the Butcher-form step of Appendix D).  The stage states are
  * recomputed from W_n; the reverse sweep applies the transposed linearised
- * right-hand side (HLLC and Euler-flux Jacobians by forward-mode dual
- * numbers).  lam_n_dev may alias lam_np1_dev.  Requires slope_limiter = NONE
+ * right-hand side, whose HLLC and Euler-flux Jacobian-transpose products are
+ * hand-written reverse-mode derivatives (one forward evaluation, then the
+ * adjoints in reverse order).  lam_n_dev may alias lam_np1_dev.  Requires slope_limiter = NONE
  * and positivity = 0 (DG_ERR_ARG otherwise).  The first call allocates the
  * handle's adjoint work arrays (2 s state arrays for s stages, plus the face
  * cotangents). */
@@ -324,16 +325,22 @@ int dg_profile_end(dg_handle* h, int* launches, double* total_ms, int n_kinds);
  * array inside the library (8 * 5 * DG_NOALLOC_MAX_CELLS / 256 bytes =
  * 2.5 MiB), which every GPU that loads the library keeps until the process
  * exits.
- *   W_dev       state [dim+2][n_basis][n_cells], double (DG_FP64) or float
- *               (DG_FP32), caller-owned device memory
+ *   W_dev       state [dim+2][n_basis][n_cells], caller-owned device memory:
+ *               double for precision DG_FP64, DG_MIXED or DG_MIXED_TC, float
+ *               for DG_FP32 or DG_FP32_TC
  *   levels_dev  optional device int32[n_cells] refinement level per cell
  *               (NULL: all cells have edge dx0); |K| = (dx0 / 2^level)^dim
  *   totals_dev  device double[dim+2] result
  * Returns DG_ERR_ARG for bad arguments or n_cells > DG_NOALLOC_MAX_CELLS,
- * DG_ERR_CUDA if a CUDA call fails.  The first call on a device looks up the
+ * DG_ERR_CUDA if one of its own CUDA calls or launches fails (errors left by
+ * earlier, unrelated calls of the thread are neither returned nor cleared).
+ * It runs on the current device, which must be the one holding W_dev,
+ * levels_dev and totals_dev.  The first call on a device looks up the
  * array's device address (once per device, with that device current); make
- * that first call before any stream capture.  All calls share the array:
- * calls that overlap on the GPU (other streams, other threads) race. */
+ * that first call before any stream capture.  The cached address does not
+ * survive cudaDeviceReset: do not call this again in a process that has
+ * reset the device.  All calls share the array: calls that overlap on the
+ * GPU (other streams, other threads) race. */
 #define DG_NOALLOC_MAX_CELLS (1 << 24)
 int dg_totals_noalloc(int dim, int n_basis, int64_t n_cells, int precision, double dx0,
                       const int32_t* levels_dev, const void* W_dev, double* totals_dev,

@@ -1196,9 +1196,17 @@ int autotune_tiles(dg_handle* h, cudaStream_t s) {
   DG_CUDA(h, launch_fill(U, h->ncells, 1.0, (int)h->esize, s));
   DG_CUDA(h, launch_fill(static_cast<char*>(U) + (h->nv - 1) * row * h->esize, h->ncells,
                          1.0 / (h->gamma - 1.0), (int)h->esize, s));
-  cudaEvent_t e0, e1;
-  DG_CUDA(h, cudaEventCreate(&e0));
-  DG_CUDA(h, cudaEventCreate(&e1));
+  // the two timing events, destroyed on every return path
+  struct Events {
+    cudaEvent_t e[2] = {nullptr, nullptr};
+    ~Events() {
+      for (cudaEvent_t x : e)
+        if (x) cudaEventDestroy(x);
+    }
+  } ev;
+  DG_CUDA(h, cudaEventCreate(&ev.e[0]));
+  DG_CUDA(h, cudaEventCreate(&ev.e[1]));
+  cudaEvent_t e0 = ev.e[0], e1 = ev.e[1];
   // a full step of the handle's own stage program (fixed dt, so no timestep
   // reduction): the epilogues and registers the step really uses
   auto time_rhs = [&](float& best) -> int {
@@ -1263,8 +1271,6 @@ int autotune_tiles(dg_handle* h, cudaStream_t s) {
     h->cell_tile = best_c;
     h->use_direct = best_direct;
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   DG_CUDA(h, cudaStreamSynchronize(s));
   return DG_OK;
 }

@@ -99,6 +99,18 @@ cudaError_t scratch_on_current_device(double** out) {
   return cudaSuccess;
 }
 
+// Launches through cudaLaunchKernel, whose return value is the status of
+// this launch alone: cudaGetLastError would also return (and clear) an
+// earlier, unrelated error of the calling thread.
+template <typename real>
+cudaError_t launch_partials(int nblocks, cudaStream_t s, const void* W, int nv, int nb, int nc,
+                            int dim, double dx0, const int32_t* levels, double* partial) {
+  const real* Wr = static_cast<const real*>(W);
+  void* args[] = {(void*)&Wr, (void*)&nv, (void*)&nb, (void*)&nc, (void*)&dim, (void*)&dx0,
+                  (void*)&levels, (void*)&partial};
+  return cudaLaunchKernel((const void*)totals_partials<real>, dim3(nblocks), dim3(kThreads), args, 0, s);
+}
+
 }  // namespace
 
 extern "C" int dg_totals_noalloc(int dim, int n_basis, int64_t n_cells, int precision, double dx0,
@@ -106,22 +118,25 @@ extern "C" int dg_totals_noalloc(int dim, int n_basis, int64_t n_cells, int prec
                                  void* stream) {
   if (dim != 2 && dim != 3) return DG_ERR_ARG;
   if (n_basis < 1 || n_cells < 0 || !(dx0 > 0.0) || !W_dev || !totals_dev) return DG_ERR_ARG;
-  if (precision != DG_FP64 && precision != DG_FP32) return DG_ERR_ARG;
+  // the state's element type: double for DG_FP64 and the FP64-state mixed
+  // modes, float for DG_FP32 and DG_FP32_TC
+  const bool dbl = precision == DG_FP64 || precision == DG_MIXED || precision == DG_MIXED_TC;
+  if (!dbl && precision != DG_FP32 && precision != DG_FP32_TC) return DG_ERR_ARG;
   if (n_cells > kMaxCells) return DG_ERR_ARG;  // beyond the fixed scratch
-  const int nv = dim + 2;
+  int nv = dim + 2;
   const int nc = (int)n_cells;
-  const int nblocks = (nc + kThreads - 1) / kThreads;
+  int nblocks = (nc + kThreads - 1) / kThreads;
   double* partial = nullptr;
   if (scratch_on_current_device(&partial) != cudaSuccess) return DG_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (nblocks > 0) {
-    if (precision == DG_FP64)
-      totals_partials<double><<<nblocks, kThreads, 0, s>>>(static_cast<const double*>(W_dev), nv,
-                                                           n_basis, nc, dim, dx0, levels_dev, partial);
-    else
-      totals_partials<float><<<nblocks, kThreads, 0, s>>>(static_cast<const float*>(W_dev), nv,
-                                                          n_basis, nc, dim, dx0, levels_dev, partial);
+    const cudaError_t e =
+        dbl ? launch_partials<double>(nblocks, s, W_dev, nv, n_basis, nc, dim, dx0, levels_dev, partial)
+            : launch_partials<float>(nblocks, s, W_dev, nv, n_basis, nc, dim, dx0, levels_dev, partial);
+    if (e != cudaSuccess) return DG_ERR_CUDA;
   }
-  totals_final<<<nv, 32, 0, s>>>(partial, nblocks, nv, totals_dev);
-  return cudaGetLastError() == cudaSuccess ? DG_OK : DG_ERR_CUDA;
+  void* args[] = {(void*)&partial, (void*)&nblocks, (void*)&nv, (void*)&totals_dev};
+  return cudaLaunchKernel((const void*)totals_final, dim3(nv), dim3(32), args, 0, s) == cudaSuccess
+             ? DG_OK
+             : DG_ERR_CUDA;
 }

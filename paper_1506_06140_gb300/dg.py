@@ -111,12 +111,17 @@ def totals_noalloc(W, dim, dx0, levels=None, out=None):
     assert W.is_cuda and W.is_contiguous() and W.dim() == 3 and W.shape[0] == dim + 2
     prec = PRECISIONS["fp64"] if W.dtype == torch.float64 else PRECISIONS["fp32"]
     if levels is not None:
-        assert levels.is_cuda and levels.dtype == torch.int32 and levels.numel() == W.shape[2]
+        assert levels.device == W.device and levels.dtype == torch.int32
+        assert levels.numel() == W.shape[2]
     if out is None:
         out = torch.empty(dim + 2, dtype=torch.float64, device=W.device)
-    r = L.dg_totals_noalloc(dim, W.shape[1], W.shape[2], prec, float(dx0),
-                            _ptr(levels) if levels is not None else None, _ptr(W), _ptr(out),
-                            _stream())
+    assert out.device == W.device and out.dtype == torch.float64 and out.numel() >= dim + 2
+    # the library runs on the current device and looks up its scratch there:
+    # make W's device current and launch on that device's current stream
+    with torch.cuda.device(W.device):
+        r = L.dg_totals_noalloc(dim, W.shape[1], W.shape[2], prec, float(dx0),
+                                _ptr(levels) if levels is not None else None, _ptr(W), _ptr(out),
+                                torch.cuda.current_stream(W.device).cuda_stream)
     if r != DG_OK:
         raise DGError(r, "dg_totals_noalloc failed")
     return out

@@ -46,7 +46,11 @@ def _rank_main(rank, world, port, out):
     send_l = torch.from_numpy(own[:, :, :, 0].copy())
     send_r = torch.from_numpy(own[:, :, :, -1].copy())
     recv_l, recv_r = torch.empty_like(send_l), torch.empty_like(send_r)
-    reqs = [dist.isend(send_l, left), dist.isend(send_r, right), dist.irecv(recv_r, right), dist.irecv(recv_l, left)]
+    # tag 0: leftward messages (a rank's first column, received by its left
+    # neighbour as that rank's right ghost); tag 1: rightward ones.  With two
+    # ranks left == right, so the tags, not the posting order, pair them.
+    reqs = [dist.isend(send_l, left, tag=0), dist.isend(send_r, right, tag=1),
+            dist.irecv(recv_r, right, tag=0), dist.irecv(recv_l, left, tag=1)]
     for q in reqs:
         q.wait()
     slab = np.concatenate([recv_l.numpy()[..., None], own, recv_r.numpy()[..., None]], axis=3)

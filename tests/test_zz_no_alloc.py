@@ -8,9 +8,10 @@ callers cannot create a dg_handle (dg_create allocates), so the entry point
 keeps its per-block partial sums in a fixed device array of the library.
 
 The test calls it through the C ABI twice in a row, on different states and
-meshes, and compares each result with the handle-based dg_totals at the
-tolerance the parity tests use for totals (relative 1e-14).  It lives in a
-file that pytest collects last.
+meshes, and compares each result with the handle-based dg_totals and with
+the FP64 CPU oracle's totals of the same state, at the tolerance the parity
+tests use for totals (relative 1e-14).  It lives in a file that pytest
+collects last.
 """
 import ctypes
 
@@ -36,6 +37,13 @@ def _close(a, b):
     np.testing.assert_allclose(a, b, rtol=1e-14, atol=1e-14 * np.abs(b).max())
 
 
+def _oracle_totals(mesh, k, W):
+    from oracle import pyoracle as O
+    o = O.Oracle(mesh["dim"], mesh["n"], mesh["lo"], mesh["hi"], k,
+                 refine_boxes=mesh.get("refine_boxes") or [])
+    return torch.as_tensor(o.totals(W.double().cpu().numpy()))
+
+
 def test_noalloc_totals_match_handle_totals_two_calls():
     from paper_1506_06140_gb300 import dg
     m2 = wl.mesh_uniform(2, [61, 47], [0.0, 0.0], [61 / 47.0, 1.0])
@@ -58,8 +66,27 @@ def test_noalloc_totals_match_handle_totals_two_calls():
     torch.cuda.synchronize()
     _close(got_a, ref_a)
     _close(got_b, ref_b)
+    _close(got_a, _oracle_totals(m2, 3, Wa))
+    _close(got_b, _oracle_totals(m3, 2, Wb))
     # and once more on the first state: the shared scratch keeps no stale sums
     _close(dg.totals_noalloc(Wa, 2, dx2), ref_a)
+
+
+def test_noalloc_accepts_the_mixed_state():
+    # DG_MIXED keeps a double state: the entry point reads it as such
+    from paper_1506_06140_gb300 import dg
+    m = wl.mesh_uniform(2, [40, 24], [0.0, 0.0], [5.0, 3.0])
+    s = dg.Solver(m, 2, 1.4, precision="mixed")
+    W = torch.as_tensor(wl.random_weights(2, s.N, s.n_cells, seed=3), device="cuda")
+    L = dg.load()
+    out = torch.zeros(4, dtype=torch.float64, device="cuda")
+    r = L.dg_totals_noalloc(2, s.N, s.n_cells, dg.PRECISIONS["mixed"], 0.125, None,
+                            ctypes.c_void_p(W.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                            ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert r == dg.DG_OK
+    torch.cuda.synchronize()
+    _close(out, s.totals(W))
+    _close(out, _oracle_totals(m, 2, W))
 
 
 def test_noalloc_rejects_sizes_beyond_the_maximum():
