@@ -725,20 +725,22 @@ def run_adjoint(args):
     return 0
 
 
-def run_l1_study(args):
-    """L1 density error of the vortex against its closed form after t_end,
-    per precision and resolution, with the device time per RK stage: the
-    data for comparing precisions at equal L1 error."""
+L1_SIZES = (64, 128, 256)
+L1_T_END = 2.0
+L1_EQUAL_TOL = 1.05  # "equal" L1: within 5% of the FP64 error
+
+
+def l1_ladder(precisions, sizes, t_end, verbose=False):
+    """L1 density error of the vortex against its closed form after t_end
+    (fixed timestep: the CFL value of the initial state, rounded so that
+    t_end is reached exactly), per precision and resolution, with the device
+    time per RK stage measured by CUDA events around the steps."""
     import torch
     from paper_1506_06140_gb300 import dg
     from paper_1506_06140_gb300 import workloads as wl
-    torch.cuda.set_device(0)
-    t_end = args.t_end
     rows = []
-    precisions = (("fp64", "fp32", "fp32_tc", "mixed", "mixed_tc") if args.precision == "both"
-                  else (args.precision,))
     for precision in precisions:
-        for n in (32, 64, 128, 256):
+        for n in sizes:
             s = dg.Solver(mesh(n), K_DEG, 1.4, rk_order=RK_ORDER, cfl=CFL, precision=precision)
             W = s.project(torch.as_tensor(wl.vortex(s.quad_points().cpu().numpy())))
             dt = s.compute_dt(W).item()  # the vortex translates; its CFL timestep stays put
@@ -758,10 +760,47 @@ def run_l1_study(args):
             rows.append({"precision": precision, "n": n, "steps": nsteps, "L1": l1,
                          "ms_per_stage": ms / (nsteps * STAGES),
                          "dof_updates_per_s": n * n * N_BASIS * STAGES * nsteps / (ms * 1e-3)})
-            print(json.dumps(rows[-1]), flush=True)
+            if verbose:
+                print(json.dumps(rows[-1]), flush=True)
+            del s, W
+    return rows
+
+
+def equal_l1(rows, tol=L1_EQUAL_TOL):
+    """For every FP64 rung of the ladder (its L1 error is the target) and
+    every other precision: the coarsest resolution at which that precision's
+    L1 error is within tol of the target, its device time per RK stage, and
+    the FP64 time per stage over it (> 1: faster at equal error); None where
+    the ladder has no such resolution."""
+    ref = {r["n"]: r for r in rows if r["precision"] == "fp64"}
+    out = []
+    for n, r64 in sorted(ref.items()):
+        entry = {"fp64_n": n, "target_L1": r64["L1"], "fp64_ms_per_stage": r64["ms_per_stage"]}
+        for p in sorted({r["precision"] for r in rows} - {"fp64"}):
+            ok = sorted((r for r in rows if r["precision"] == p and r["L1"] <= tol * r64["L1"]),
+                        key=lambda r: r["ms_per_stage"])
+            if ok:
+                b = ok[0]
+                entry[p] = {"n": b["n"], "L1": b["L1"], "ms_per_stage": b["ms_per_stage"],
+                            "speedup_vs_fp64": r64["ms_per_stage"] / b["ms_per_stage"]}
+            else:
+                entry[p] = None
+        out.append(entry)
+    return out
+
+
+def run_l1_study(args):
+    """L1 density error of the vortex against its closed form after t_end,
+    per precision and resolution (32^2 ... 256^2), with the device time per
+    RK stage: the data for comparing precisions at equal L1 error."""
+    import torch
+    torch.cuda.set_device(0)
+    precisions = (("fp64", "fp32", "fp32_tc", "mixed", "mixed_tc") if args.precision == "both"
+                  else (args.precision,))
+    rows = l1_ladder(precisions, (32,) + L1_SIZES, args.t_end, verbose=True)
     out = {"metric": "L1 density error vs closed form and DOF-updates/s per RK stage",
-           "config": {"workload": "isentropic vortex k=3 SSP-RK4 CFL 0.2 to t=%g" % t_end},
-           "rows": rows}
+           "config": {"workload": "isentropic vortex k=3 SSP-RK4 CFL 0.2 to t=%g" % args.t_end},
+           "rows": rows, "equal_l1": equal_l1(rows)}
     print(json.dumps(out), flush=True)
     return 0
 
@@ -883,40 +922,78 @@ def run_sedov_taylor(args):
     return 0
 
 
-def cpu_baseline(n_sample=128, max_seconds=20.0):
-    """The oracle, as it stands, on a bounded sample of the workload: the
-    vortex on a 128^2 periodic box with the same cell size, k and RK4."""
+def host_cpu():
+    """(threads available to this process, CPU model name) of the host."""
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":")[0].strip() == "Model name":
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None and os.path.exists("/proc/cpuinfo"):
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu model")):
+                model = ln.split(":", 1)[1].strip()
+                break
+    return cores, model or "unknown"
+
+
+def oracle_vortex_rate(n_sample, threads, max_seconds, max_steps):
+    """RK4 steps of the vortex on an n_sample^2 periodic box with the bench's
+    cell size, timed on the oracle with `threads` OpenMP threads."""
     from oracle import pyoracle as O
     from paper_1506_06140_gb300 import workloads as wl
     half = 5.0 * n_sample / N_CELLS_1D
     m = mesh(n_sample, half)
     o = O.Oracle(2, m["n"], m["lo"], m["hi"], K_DEG, 1.4, rk_order=RK_ORDER, cfl=CFL)
+    o.set_threads(threads)
     W = o.project(wl.vortex(o.quad_points()))
     t0 = time.perf_counter()
     steps = 0
     while True:
         W, _ = o.rk_step(W, 0.0)
         steps += 1
-        if time.perf_counter() - t0 > max_seconds / 2 or steps >= 50:
+        if time.perf_counter() - t0 > max_seconds or steps >= max_steps:
             break
-    dt = time.perf_counter() - t0
-    value = n_sample ** 2 * N_BASIS * STAGES * steps / dt
-    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d RK4 steps of the vortex on a %dx%d periodic box with the same cell size, "
-                      "k=3 (single-threaded FP64 C++ oracle)" % (steps, n_sample, n_sample),
-            "seconds": dt}
+    sec = time.perf_counter() - t0
+    return n_sample ** 2 * N_BASIS * STAGES * steps / sec, steps, sec
+
+
+def cpu_baseline(max_seconds=10.0):
+    """The oracle, as it stands, on the host cores: all cores on the bench's
+    own 256^2 workload (the right-hand side in its gather form, one OpenMP
+    thread per core), and one core on a 128^2 box with the same cell size."""
+    cores, model = host_cpu()
+    v_all, s_all, t_all = oracle_vortex_rate(N_CELLS_1D, cores, max_seconds, 400)
+    v_one, s_one, t_one = oracle_vortex_rate(128, 1, max_seconds, 50)
+    return {"value": v_all, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": model,
+            "sample": "%d RK4 steps of the 256x256 vortex, k=3 (FP64 C++ oracle, right-hand side "
+                      "cell by cell on %d OpenMP threads)" % (s_all, cores),
+            "seconds": t_all,
+            "single_thread": {"value": v_one, "unit": UNIT, "cores": 1,
+                              "sample": "%d RK4 steps of the vortex on a 128x128 periodic box with the "
+                                        "same cell size, k=3 (serial oracle)" % s_one,
+                              "seconds": t_one}}
 
 
 def reference_arm(args, rank, world):
-    """--impl reference: the oracle timed on the host cores (rank 0 only)."""
+    """--impl reference: the oracle timed on all host cores (rank 0 only),
+    each step one RK4 step of the bench's 256^2 vortex."""
     if rank != 0:
         return 0
     from oracle import pyoracle as O
     from paper_1506_06140_gb300 import workloads as wl
-    n_sample = 64
-    half = 5.0 * n_sample / N_CELLS_1D
-    m = mesh(n_sample, half)
+    cores, model = host_cpu()
+    m = mesh()
     o = O.Oracle(2, m["n"], m["lo"], m["hi"], K_DEG, 1.4, rk_order=RK_ORDER, cfl=CFL)
+    o.set_threads(cores)
     W = o.project(wl.vortex(o.quad_points()))
     for _ in range(args.warmup):
         W, _ = o.rk_step(W, 0.0)
@@ -924,15 +1001,15 @@ def reference_arm(args, rank, world):
     for _ in range(args.steps):
         W, _ = o.rk_step(W, 0.0)
     sec = time.perf_counter() - t0
-    value = n_sample ** 2 * N_BASIS * STAGES * args.steps / sec
-    sample = ("each step: one RK4 step of the vortex on a %dx%d periodic box with the same cell "
-              "size, k=3 (single-threaded FP64 C++ oracle)" % (n_sample, n_sample))
+    value = N_CELLS_1D ** 2 * N_BASIS * STAGES * args.steps / sec
+    sample = ("each step: one RK4 step of the 256x256 vortex, k=3 (FP64 C++ oracle, right-hand side "
+              "cell by cell on %d OpenMP threads)" % cores)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config("vortex", "fp64", N_CELLS_1D ** 2),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "cpu_model": model, "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -945,6 +1022,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-l1", action="store_true", help="vortex: skip the L1 / equal-L1 study")
     ap.add_argument("--precision", default="both",
                     choices=["both", "fp64", "fp32", "fp32_tc", "mixed", "mixed_tc"],
                     help="run one precision only (profiling); the JSON line needs both")
@@ -1022,6 +1100,24 @@ def main():
                             ("value", "ms_per_step", "roofline", "e2e", "gpu_launches",
                              "clocks", "kernel_ms")} for p in ("fp32", "fp32_tc", "mixed", "mixed_tc")
                          if p in lines}}
+    if not args.no_l1:
+        # accuracy of every variant (vortex against its closed form after
+        # t = 2 on the 64^2 ... 256^2 ladder) and the comparison at equal L1 error
+        rows = l1_ladder([p for p in ("fp64", "fp32", "fp32_tc", "mixed", "mixed_tc") if p in lines],
+                         L1_SIZES, L1_T_END)
+        at_n = {r["precision"]: r for r in rows if r["n"] == N_CELLS_1D}
+        out["l1"] = at_n["fp64"]["L1"]
+        for p in out["variants"]:
+            out["variants"][p]["l1"] = at_n[p]["L1"]
+        out["equal_l1"] = {"t_end": L1_T_END, "tol": L1_EQUAL_TOL,
+                           "definition": "L1 density error against the closed-form vortex (Sec. 5.1) after "
+                                         "t_end with a fixed timestep; per FP64 rung the coarsest resolution "
+                                         "where each precision is within tol of the FP64 error, its device "
+                                         "time per RK stage and the FP64 time per stage over it",
+                           "ladder": rows, "comparison": equal_l1(rows)}
+        out["config"]["l1"] = ("L1 density error after t=%g with a fixed timestep on the %s ladder "
+                               "(\"l1\" and variants' \"l1\": at 256^2)"
+                               % (L1_T_END, "/".join("%d^2" % n for n in L1_SIZES)))
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()
     print(json.dumps(out), flush=True)

@@ -23,7 +23,8 @@ def build(force=False, verbose=False):
     """Build liboracle.so if it is missing or older than its sources."""
     if not force and not _stale():
         return LIB
-    cmd = ["g++", "-O2", "-ffp-contract=off", "-std=c++17", "-shared", "-fPIC", "-o", LIB + ".tmp"]
+    cmd = ["g++", "-O2", "-ffp-contract=off", "-fopenmp", "-std=c++17", "-shared", "-fPIC", "-o",
+           LIB + ".tmp"]
     cmd += [os.path.join(HERE, s) for s in SOURCES]
     if verbose:
         print(" ".join(cmd))

@@ -48,6 +48,9 @@ double orc_compute_dt(const orc_problem* p, const double* W);
    right-hand side and the gravity bound (Sec. 2.5) to the timestep. */
 void orc_set_accel(orc_problem* p, const double* accel);
 double orc_rk_step(const orc_problem* p, double* W, double dt);
+/* OpenMP threads of orc_rk_step's right-hand side: n > 1 evaluates it cell by
+ * cell (gather form, no races), n <= 1 with the face scatter (default). */
+void orc_set_threads(orc_problem* p, int n);
 void orc_slope_limit(const orc_problem* p, double* W);
 void orc_positivity_limit(const orc_problem* p, double* W);
 void orc_limit(const orc_problem* p, double* W);

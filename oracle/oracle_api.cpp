@@ -83,6 +83,7 @@ void orc_set_accel(orc_problem* p, const double* accel) {
   P.accel.assign(accel, accel + (size_t)P.dim * P.vol.n * P.mesh.ncells);
 }
 double orc_rk_step(const orc_problem* p, double* W, double dt) { return p->P.rk_step(W, dt); }
+void orc_set_threads(orc_problem* p, int n) { p->P.threads = n > 1 ? n : 1; }
 void orc_slope_limit(const orc_problem* p, double* W) { p->P.slope_limit(W); }
 void orc_positivity_limit(const orc_problem* p, double* W) { p->P.positivity_limit(W); }
 void orc_limit(const orc_problem* p, double* W) { p->P.limit(W); }

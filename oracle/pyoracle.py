@@ -50,6 +50,7 @@ def lib():
         L.orc_set_accel.argtypes = [C.c_void_p, C.c_void_p]
         L.orc_rk_step.restype = C.c_double
         L.orc_rk_step.argtypes = [C.c_void_p, _D, C.c_double]
+        L.orc_set_threads.argtypes = [C.c_void_p, C.c_int]
         for name in ("orc_slope_limit", "orc_positivity_limit", "orc_limit"):
             getattr(L, name).argtypes = [C.c_void_p, _D]
         L.orc_totals.argtypes = [C.c_void_p, _D, _D]
@@ -187,6 +188,10 @@ class Oracle:
     def compute_dt(self, W):
         W = _f64(W)
         return lib().orc_compute_dt(self._h, _d(W))
+
+    def set_threads(self, n):
+        """OpenMP threads of rk_step's right-hand side (gather form when n > 1)."""
+        lib().orc_set_threads(self._h, int(n))
 
     def rk_step(self, W, dt=0.0):
         """Advance a copy of W by one step; returns (W_new, dt_used)."""

@@ -96,6 +96,7 @@ struct Problem {
   int rk_order = 2;
   double cfl = 0.2;
   int limiter = LIM_NONE;
+  int threads = 1;               // OpenMP threads of rk_step's right-hand side (gather form if > 1)
   double beta = 1.0, Mtilde = 0.5;
   int positivity = 0;
   double eps = 1e-10;
@@ -676,13 +677,40 @@ struct Problem {
     positivity_limit(W);
   }
 
+  // dw/dt of every cell in the gather form: rhs_one per cell, the cells
+  // shared among `threads` OpenMP threads.  Each cell writes only its own
+  // weights, so the loop has no races and its result does not depend on the
+  // thread count (the scatter form `rhs` adds each face term to both
+  // neighbours and cannot be split over cells; the two forms sum the same
+  // terms in a different order, so they agree to rounding).
+  void rhs_parallel(const double* W, double* dW) const {
+    const int nc = mesh.ncells;
+#pragma omp parallel num_threads(threads)
+    {
+      std::vector<double> out((size_t)nv * N);
+#pragma omp for schedule(static)
+      for (int c = 0; c < nc; ++c) {
+        rhs_one(W, c, out.data());
+        for (int v = 0; v < nv; ++v)
+          for (int j = 0; j < N; ++j) dW[idx(v, j, c)] = out[(size_t)v * N + j];
+      }
+    }
+  }
+
   // One time step (Sec. 4.5, steps 5a-5b); dt <= 0 takes the CFL timestep.
+  // With threads > 1 the right-hand side is the gather form on that many
+  // threads (timing of the oracle on all host cores); otherwise the scatter
+  // form `rhs`.
   double rk_step(double* W, double dt) const {
     if (dt <= 0.0) dt = compute_dt(W);
     std::vector<double> w(W, W + size());
     const bool lim = (limiter != LIM_NONE && k > 0) || positivity;
     rk_butcher<double>(
-        tb, w, dt, [&](const std::vector<double>& U, std::vector<double>& K) { rhs(U.data(), K.data()); },
+        tb, w, dt,
+        [&](const std::vector<double>& U, std::vector<double>& K) {
+          if (threads > 1) rhs_parallel(U.data(), K.data());
+          else rhs(U.data(), K.data());
+        },
         lim ? std::function<void(std::vector<double>&)>([&](std::vector<double>& U) { limit(U.data()); })
             : std::function<void(std::vector<double>&)>());
     std::copy(w.begin(), w.end(), W);

@@ -465,3 +465,26 @@ def test_per_cell_evaluations_match_full_mesh(mesh):
     np.testing.assert_allclose(o.rhs_cells(W, cells), o.rhs(W), rtol=0,
                                atol=1e-13 * np.abs(o.rhs(W)).max())
     np.testing.assert_array_equal(o.limit_cells(W, cells), o.limit(W))
+
+
+# ---------------------------------------------------------------------------
+# the oracle's all-core step (gather form on OpenMP threads) against its
+# serial scatter form
+
+@pytest.mark.parametrize("dim,n,k,boxes", [(2, [9, 7], 3, [[2, 2, 5, 4]]), (3, [4, 3, 3], 2, [[1, 0, 1, 2, 1, 1]])])
+def test_parallel_step_matches_serial_step(dim, n, k, boxes):
+    lo, hi = [-1.0] * dim, [-1.0 + 0.5 * m for m in n]
+    rk = {2: 3, 3: 4}[k]
+    o = O.Oracle(dim, n, lo, hi, k, GAMMA, rk_order=rk, refine_boxes=boxes)
+    W = wl.random_weights(dim, o.N, o.n_cells, seed=31 + dim)
+    dt = 0.5 * o.compute_dt(W)
+    ref, _ = o.rk_step(W, dt)
+    o.set_threads(4)
+    par4, _ = o.rk_step(W, dt)
+    o.set_threads(3)
+    par3, _ = o.rk_step(W, dt)
+    # the gather form's result does not depend on the thread count
+    np.testing.assert_array_equal(par3, par4)
+    # and agrees with the scatter form to rounding (same terms, another order)
+    d = np.abs(par4 - W).max()
+    np.testing.assert_allclose(par4 - W, ref - W, rtol=0, atol=1e-13 * d)
