@@ -346,6 +346,19 @@ int dg_totals_noalloc(int dim, int n_basis, int64_t n_cells, int precision, doub
                       const int32_t* levels_dev, const void* W_dev, double* totals_dev,
                       void* stream);
 
+/* Test hook for the status path of the tensor-core cell kernel's bounded
+ * waits (no counterpart in the paper).  Arms the handle's next tensor-core
+ * cell-kernel launch made outside a CUDA graph (dg_rhs, dg_rk_step, ...):
+ * in that launch the first CTA does not issue its first tensor-core multiply
+ * nor the commit that would complete its barrier, and polls that barrier
+ * with a short limit (2^12 tries instead of 2^24).  The wait therefore gives
+ * up while none of the CTA's tensor-core work is in flight; the CTA stops,
+ * frees its tensor memory and latches DG_ERR_TIMEOUT, which dg_status then
+ * returns.  The outputs of that launch are invalid; later launches run
+ * normally.  DG_ERR_UNSUPPORTED for handles without the tensor-core kernel
+ * (precisions other than DG_FP32_TC and DG_MIXED_TC). */
+int dg_test_force_timeout(dg_handle* h);
+
 /* Reads and clears the device status word (DG_OK, DG_ERR_NONPHYSICAL, ...).
  * Synchronises the handle's last stream. */
 int dg_status(dg_handle* h, int* device_status_host);

@@ -402,7 +402,8 @@ struct dg_handle {
   float* tab32 = nullptr;    // the tables in FP32 (positivity precheck)
   void* F = nullptr;
   std::vector<void*> regs;   // scratch state registers 1..n
-  bool use_tc = false;       // tensor-core cell kernel (DG_FP32_TC)
+  bool use_tc = false;       // tensor-core cell kernel (DG_FP32_TC, DG_MIXED_TC)
+  int tc_hook = 0;           // dg_test_force_timeout: armed for the next tensor-core cell launch
   const MixedSet* ms = nullptr;  // FP32 perturbation-form stage kernels (DG_MIXED)
   Tab1D<float> tab1d32{};
   float* Gm = nullptr;       // DG_MIXED face fluxes minus the minus cell's reference flux
@@ -890,7 +891,10 @@ void drop_graphs(dg_handle* h) {
 }
 
 cudaError_t cell_launch(dg_handle* h, const void* args, cudaStream_t s) {
-  if (h->use_tc) return h->ks->cell_tc(args, s);
+  if (h->use_tc) {
+    h->tc_hook = 0;  // the hook (if armed) went with this launch's arguments
+    return h->ks->cell_tc(args, s);
+  }
   return h->use_direct && !h->accel ? h->ks->cell_direct(args, s) : h->ks->cell(args, s);
 }
 
@@ -927,6 +931,7 @@ int stage_launch(dg_handle* h, const StageArgs<real>& a, cudaStream_t s, const O
         x.wf_mode = op->in_reg == 0 ? 1 : 2;
       }
       DG_CUDA(h, timed(h, DG_KERNEL_FACE, s, [&] { return h->ms->face(&x, s); }));
+      if (h->use_tc) h->tc_hook = 0;  // the hook (if armed) went with this launch's arguments
       DG_CUDA(h, timed(h, DG_KERNEL_CELL, s,
                        [&] { return h->use_tc ? h->ms->cell_tc(&x, s) : h->ms->cell(&x, s); }));
       return DG_OK;
@@ -949,6 +954,7 @@ StageArgs<real> stage_args(dg_handle* h, const Op& op, const void* U, void* W) {
   for (int l = 0; l < 2; ++l) a.pre[l] = (real)(std::ldexp(1.0, 1 - h->dim) / std::ldexp(h->md.dx0, -l));
   a.pre_prob = h->nprob > 1 ? static_cast<const real*>(h->pre_prob) : nullptr;
   a.tcB = static_cast<const real*>(h->tcB);
+  a.tc_hook = h->use_tc ? h->tc_hook : 0;
   a.status = h->status;
   a.tab = static_cast<const real*>(h->tab);
   a.U = static_cast<const real*>(U);
@@ -1942,6 +1948,13 @@ int dg_profile_end(dg_handle* h, int* launches, double* total_ms, int n_kinds) {
   }
   h->ev_marks.clear();
   h->ev_used = 0;
+  return DG_OK;
+}
+
+int dg_test_force_timeout(dg_handle* h) {
+  if (!check_handle(h)) return DG_ERR_ARG;
+  if (!h->use_tc) return fail(h, DG_ERR_UNSUPPORTED, "dg_test_force_timeout: no tensor-core cell kernel");
+  h->tc_hook = 1;
   return DG_OK;
 }
 

@@ -114,6 +114,8 @@ struct StageArgs {
   int face_tile = 0;            // faces per block of the face kernel (0: its default)
   const real* tcB = nullptr;    // tensor-core B operands (tensor-core cell kernel)
   int* status = nullptr;        // device status word
+  int tc_hook = 0;              // test hook of the tensor-core cell kernel: 1 = its first CTA skips
+                                // its first MMA and commit and waits with a short limit
   const real* accel = nullptr;  // [DIM][Q][ncells] external acceleration at the volume points
                                 // (gravity source, eq. gravity_term); nullptr: none
 };

@@ -1160,8 +1160,8 @@ KernelSet make_kernel_set(int prec) {
     ks.fill_direct = &fill_direct_tables<DIM, K>;
   }
   if constexpr (std::is_same<real, float>::value && DIM == 2 && K >= 1 && K <= 3) {
-    ks.cell_tc = &launch_cell_tc<K>;
-    ks.prepare_tc = &prepare_cell_tc<K>;
+    ks.cell_tc = &launch_cell_tc<K, false>;
+    ks.prepare_tc = &prepare_cell_tc<K, false>;
     ks.fill_tc = &fill_tc_tables<K>;
   }
   return ks;

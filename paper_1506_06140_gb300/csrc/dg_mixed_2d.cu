@@ -1,7 +1,7 @@
 // Mixed-precision stage kernels (FP64 state, FP32 right-hand side in
 // perturbation form) for dim = 2, k = 0..3, with the tensor-core cell kernel
 // for k = 1..3.
-#include "dg_tc_mixed.cuh"
+#include "dg_tc.cuh"
 
 namespace dgi {
 
@@ -9,8 +9,8 @@ template <int K>
 MixedSet make_mixed_set_2d() {
   MixedSet ms = make_mixed_set<2, K>();
   if constexpr (K >= 1) {
-    ms.cell_tc = &launch_cell_tc_mixed<K>;
-    ms.prepare_tc = &prepare_cell_tc_mixed<K>;
+    ms.cell_tc = &launch_cell_tc<K, true>;
+    ms.prepare_tc = &prepare_cell_tc<K, true>;
     ms.fill_tc = &fill_tc_tables<K>;
   }
   return ms;

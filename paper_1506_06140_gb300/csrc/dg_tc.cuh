@@ -1,27 +1,47 @@
-// Tensor-core form of the cell kernel (FP32 state, 2D uniform meshes): the two
-// contractions of a tile of 32 cells run on the 5th-generation tensor cores
-// (tcgen05.mma, accumulators in tensor memory), rows = (variable, cell):
-//   MMA 1 (modal -> nodal)   D1[v,c][q] = sum_l W[v,c][l] phi_l(xi_q)
-//   MMA 2 (volume - surface) D2[v,c][j] = sum_{d,q} f_d,v(q) dphi_j/dxi_d w_q
-//                                        - sum_{side,q} sc fbar_v(q) phi_j w_q
-// The pointwise Euler fluxes stay on the CUDA cores.  Near-FP32 accuracy with
-// the TF32 tensor datapath by operand splitting: x = hi + lo with hi the
-// nearest TF32 value of x and lo the nearest TF32 value of x - hi; the four
-// products lo*lo + lo*hi + hi*lo + hi*hi accumulate in FP32 (four MMAs per
-// contraction), leaving a relative error of about 2^-21 per product.
+// Tensor-core form of the cell kernel (2D uniform meshes, k = 1..3): the two
+// contractions of the cell update (paper Sec. 2.4, eqs. dg_term2, dg_term3)
+// run on the 5th-generation tensor cores (tcgen05.mma, accumulators in
+// tensor memory) for tiles of 128 cells, one MMA row (TMEM lane) per cell:
+//   MMA 1, per variable v (modal -> nodal)
+//       D1_v[c][q] = sum_l W[v][l][c] phi_l(xi_q)
+//   MMA 2, per variable v (volume - surface)
+//       D2_v[c][j] = sum_{d,q} f_d,v(q) dphi_j/dxi_d w_q - sum_{side,q} sc fbar_v(q) phi_j w_q
+// The pointwise Euler fluxes stay on the CUDA cores.  Because a TMEM lane
+// holds every variable of its cell, the four threads of a cell read the
+// nodal values they need straight from tensor memory (no exchange through
+// shared memory).
+//
+// Two state forms share the kernel: an FP32 state (DG_FP32_TC) and the
+// mixed mode's FP64 state with its right-hand side in perturbation form
+// (DG_MIXED_TC; dg_mixed.cuh): there MMA 1 sees the perturbation weights,
+// the fluxes are f(ubar + du) - f(ubar) and the face values G (+ D).
+//
+// Near-FP32 accuracy with the TF32 tensor datapath by operand splitting:
+// x = hi + lo with hi the nearest TF32 value of x and lo the nearest TF32
+// value of x - hi.  Three products per contraction, lo*hi + hi*lo + hi*hi,
+// accumulate in FP32; the dropped lo*lo term and the rounding of lo are
+// each below 2^-22 of |a||b| per product.
 //
 // Operands are staged in shared memory in the K-major, no-swizzle layout:
 // 8-row x 16-byte core matrices stored contiguously, core matrices adjacent
 // along K 128 bytes apart, 8-row groups (K/4)*128 bytes apart.
+//
+// Work split: 512 threads per CTA, four per cell; thread t of a cell (the
+// warp's index over 4) handles variable t for the weights and the epilogue,
+// volume points PT*t .. PT*t+PT-1 for the fluxes, and side t for the face
+// values.  One CTA per SM (200 KB of shared memory at k = 3), persistent over
+// tiles; the inputs of a CTA's next tile are loaded while MMA 1 runs.
 #pragma once
 #include <cuda_runtime.h>
 
 #include <cstdint>
-
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
+#include "dg_convert.cuh"
 #include "dg_internal.h"
+#include "dg_mixed.cuh"
 #include "dg_physics.cuh"
 
 namespace dgi {
@@ -29,24 +49,31 @@ namespace dgi {
 template <int K>
 struct TcShape {
   using S = Shape<2, K>;
-  static constexpr int TC = 32;                          // cells per tile
-  static constexpr int M = 128;                          // rows: v * 32 + cell
-  static constexpr int KP1 = (S::N + 7) / 8 * 8;         // K of MMA 1
-  static constexpr int NQ = (S::Q + 15) / 16 * 16;       // N of MMA 1
-  static constexpr int QP = (S::Q + 3) / 4 * 4;          // points, padded to groups of 4
-  static constexpr int QFP = (S::QF + 3) / 4 * 4;        // face points, padded
+  static constexpr int TM = 128;                         // cells per tile = MMA rows = TMEM lanes
+  static constexpr int THREADS = 512;                    // four threads per cell
+  static constexpr int PT = (S::Q + 3) / 4;              // volume points per thread
+  static constexpr int QP = 4 * PT;                      // volume points, padded
+  static constexpr int KP1 = (S::N + 7) / 8 * 8;         // K of MMA 1 (coefficients, steps of 8)
+  static constexpr int NQ = 16;                          // N of MMA 1 (points)
+  static constexpr int QFP = 4;                          // face points per side, padded
   static constexpr int KV = 2 * QP;                      // volume part of K of MMA 2
-  static constexpr int KP2 = KV + 4 * QFP;               // K of MMA 2 (multiple of 8)
-  static constexpr int NJ = (S::N + 15) / 16 * 16;       // N of MMA 2
+  static constexpr int KP2 = KV + 4 * QFP;               // K of MMA 2
+  static constexpr int NJ = 16;                          // N of MMA 2 (coefficients)
+  static constexpr int A1_BLK = TM * KP1;                // floats of one (variable, hi|lo) block
+  static constexpr int A2_BLK = TM * KP2;
+  static constexpr int A2_FLOATS = 2 * S::NV * A2_BLK;   // [variable][hi|lo][TM x KP2]
+  static constexpr int A1_OFF = 2 * 2 * A2_BLK;          // A1 over the A2 blocks of variables 2, 3
   static constexpr int B_FLOATS = 2 * NQ * KP1 + 2 * NJ * KP2;  // B1 hi|lo, B2 hi|lo
-  // A1 hi|lo (the nodal values reuse it once MMA 1 is done), A2 hi|lo, B
-  static constexpr int A1_FLOATS = 2 * M * KP1 > S::NV * S::Q * TC ? 2 * M * KP1 : S::NV * S::Q * TC;
-  static constexpr int SMEM_FLOATS = A1_FLOATS + 2 * M * KP2 + B_FLOATS;
+  static constexpr int SMEM_FLOATS = A2_FLOATS + B_FLOATS;
   static constexpr size_t SMEM = (size_t)SMEM_FLOATS * 4;
-  static constexpr int TMEM_COLS = 32;
-  static_assert(NQ + NJ <= TMEM_COLS, "tensor memory columns");
-  static_assert(KP2 % 8 == 0 && KP1 % 8 == 0, "K steps of 8");
-  static_assert((2 * M * KP1) % 4 == 0 && A1_FLOATS % 32 == 0, "16-byte alignment");
+  static constexpr int D1_COL = 0;                       // TMEM columns of D1_v: 16 v ..
+  static constexpr int D2_COL = 16 * S::NV;              // and of D2_v: 64 + 16 v ..
+  static constexpr int TMEM_COLS = 128;
+  static_assert(S::NV == 4 && QP <= NQ && S::N <= NJ && S::QF <= QFP, "2D shapes");
+  static_assert(2 * S::NV * A1_BLK <= A2_FLOATS - A1_OFF, "A1 fits over the A2 blocks of variables 2, 3");
+  static_assert(KP1 % 8 == 0 && KP2 % 8 == 0, "K steps of 8");
+  static_assert(D2_COL + 16 * S::NV <= TMEM_COLS, "tensor memory columns");
+  static_assert(SMEM + 8 * 1024 <= 227 * 1024, "shared memory of one CTA");
 };
 
 // float offset of element (r, k) in the core-matrix layout of a tile with KP columns
@@ -80,26 +107,48 @@ __device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t da, uint64_t db,
       "l"(da), "l"(db), "r"(idesc), "r"(acc));
 }
 
-// D[0:M, 0:N) = A[0:M, 0:KP) B[0:N, 0:KP)^T with split operands, small
-// products first: A_lo B_lo + A_lo B_hi + A_hi B_lo + A_hi B_hi; K steps of 8
-template <int KP, int N, int M>
-__device__ __forceinline__ void tc_gemm_split(uint32_t dtmem, const float* Ah, const float* Al,
-                                              const float* Bh, const float* Bl) {
-  constexpr uint32_t idesc = tc_idesc(N, M);
-  const float* As[4] = {Al, Al, Ah, Ah};
-  const float* Bs[4] = {Bl, Bh, Bl, Bh};
-  uint32_t acc = 0;
+// The four per-variable contractions D_v = A_v B^T (v = 0..3; D_v at TMEM
+// column dcol + 16 v, A_v hi|lo at Ab + 2 v blk, Ab + (2 v + 1) blk) with
+// split operands, issued so that consecutive multiplies accumulate into
+// different variables' columns (four independent chains)
+template <int KP>
+__device__ __forceinline__ void tc_gemm3_x4(uint32_t dcol, const float* Ab, int blk, const float* Bh,
+                                            const float* Bl) {
+  constexpr uint32_t idesc = tc_idesc(16, 128);
+  uint64_t dah[4], dal[4];
 #pragma unroll
-  for (int t = 0; t < 4; ++t) {
-    // a K step of 8 is 256 bytes further: 16 in the descriptor's address
-    // field (shared addresses stay below 2^18, so the field does not overflow)
-    const uint64_t da = tc_desc(tc_smem(As[t]), KP), db = tc_desc(tc_smem(Bs[t]), KP);
+  for (int v = 0; v < 4; ++v) {
+    dah[v] = tc_desc(tc_smem(Ab + (2 * v) * blk), KP);
+    dal[v] = tc_desc(tc_smem(Ab + (2 * v + 1) * blk), KP);
+  }
+  const uint64_t dbh = tc_desc(tc_smem(Bh), KP), dbl = tc_desc(tc_smem(Bl), KP);
+#pragma unroll
+  for (int t = 0; t < 3; ++t)
+#pragma unroll
+    for (int ks = 0; ks < KP / 8; ++ks)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const uint64_t da = (t == 0 ? dal[v] : dah[v]) + (uint64_t)(16 * ks);
+        const uint64_t db = (t == 1 ? dbl : dbh) + (uint64_t)(16 * ks);
+        tc_mma(dcol + 16 * v, da, db, idesc, (t == 0 && ks == 0) ? 0u : 1u);
+      }
+}
+
+// D_v = A_v B^T for one variable (D_v at TMEM column dcol, A_v hi|lo at Ah, Al)
+template <int KP>
+__device__ __forceinline__ void tc_gemm3(uint32_t dcol, const float* Ah, const float* Al, const float* Bh,
+                                         const float* Bl) {
+  constexpr uint32_t idesc = tc_idesc(16, 128);
+  const uint64_t dah = tc_desc(tc_smem(Ah), KP), dal = tc_desc(tc_smem(Al), KP);
+  const uint64_t dbh = tc_desc(tc_smem(Bh), KP), dbl = tc_desc(tc_smem(Bl), KP);
+#pragma unroll
+  for (int t = 0; t < 3; ++t)
 #pragma unroll
     for (int ks = 0; ks < KP / 8; ++ks) {
-      tc_mma(dtmem, da + (uint64_t)(16 * ks), db + (uint64_t)(16 * ks), idesc, acc);
-      acc = 1;
+      const uint64_t da = (t == 0 ? dal : dah) + (uint64_t)(16 * ks);
+      const uint64_t db = (t == 1 ? dbl : dbh) + (uint64_t)(16 * ks);
+      tc_mma(dcol, da, db, idesc, (t == 0 && ks == 0) ? 0u : 1u);
     }
-  }
 }
 
 __device__ __forceinline__ void tc_commit(uint64_t* mbar) {
@@ -107,10 +156,10 @@ __device__ __forceinline__ void tc_commit(uint64_t* mbar) {
       tc_smem(mbar)));
 }
 
-// bounded wait on an mbarrier phase; false if it gave up
-__device__ __forceinline__ bool tc_wait(uint64_t* mbar, uint32_t parity) {
+// bounded wait on an mbarrier phase; false if it gave up after `limit` polls
+__device__ __forceinline__ bool tc_wait(uint64_t* mbar, uint32_t parity, int limit) {
   uint32_t done = 0;
-  for (int it = 0; it < (1 << 24) && !done; ++it) {
+  for (int it = 0; it < limit && !done; ++it) {
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
         " selp.u32 %0, 1, 0, p;\n}"
@@ -118,6 +167,22 @@ __device__ __forceinline__ bool tc_wait(uint64_t* mbar, uint32_t parity) {
         : "r"(tc_smem(mbar)), "r"(parity));
   }
   return done != 0;
+}
+
+// tensor memory -> registers: lane of this thread, columns taddr .. (+1, +4, +16)
+__device__ __forceinline__ float tc_ld1(uint32_t taddr) {
+  uint32_t v;
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(v) : "r"(taddr));
+  return __uint_as_float(v);
+}
+
+__device__ __forceinline__ void tc_ld4(uint32_t taddr, float* out) {
+  uint32_t v[4];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
+               : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 4; ++i) out[i] = __uint_as_float(v[i]);
 }
 
 __device__ __forceinline__ void tc_ld16(uint32_t taddr, float* out) {
@@ -129,10 +194,11 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float* out) {
         "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
         "=r"(v[14]), "=r"(v[15])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
   for (int i = 0; i < 16; ++i) out[i] = __uint_as_float(v[i]);
 }
+
+__device__ __forceinline__ void tc_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ float tc_round_tf32(float x) {
   uint32_t r;
@@ -146,59 +212,60 @@ __device__ __forceinline__ void tc_split(float x, float& hi, float& lo) {
   lo = tc_round_tf32(x - hi);
 }
 
-__device__ __forceinline__ void tc_st4(float* base, int off, float a, float b, float c, float d) {
-  *reinterpret_cast<float4*>(base + off) = make_float4(a, b, c, d);
-}
-
 // split four consecutive K values of one row and store them (16-byte stores)
 __device__ __forceinline__ void tc_put4(float* Ah, float* Al, int off, const float* x) {
   float h[4], l[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) tc_split(x[i], h[i], l[i]);
-  tc_st4(Ah, off, h[0], h[1], h[2], h[3]);
-  tc_st4(Al, off, l[0], l[1], l[2], l[3]);
+  *reinterpret_cast<float4*>(Ah + off) = make_float4(h[0], h[1], h[2], h[3]);
+  *reinterpret_cast<float4*>(Al + off) = make_float4(l[0], l[1], l[2], l[3]);
 }
 
-// Persistent CTAs of two warpgroups: warps v and v + 4 share the TMEM lane
-// quarter (and A rows) of variable v and split each phase of a tile between
-// them.  Each CTA keeps the B operands, its tensor memory and its barriers for
-// all the tiles it processes (tile, tile + gridDim.x, ...), and loads the
-// global inputs of its next tile while the current one is in flight.
-template <int K>
-__global__ void __launch_bounds__(256, 3) cell_update_tc_kernel(const StageArgs<float> a) {
+__device__ __forceinline__ void tc_put1(float* Ah, float* Al, int off, float x) {
+  float h, l;
+  tc_split(x, h, l);
+  Ah[off] = h;
+  Al[off] = l;
+}
+
+template <bool MIXED>
+using TcArgs = typename std::conditional<MIXED, MixedArgs, StageArgs<float>>::type;
+
+__host__ __device__ __forceinline__ const StageArgs<float>& tc_stage(const StageArgs<float>& a) { return a; }
+__host__ __device__ __forceinline__ const StageArgs<double>& tc_stage(const MixedArgs& x) { return x.a; }
+
+template <int K, bool MIXED>
+__global__ void __launch_bounds__(512, 1) cell_tc_kernel(const TcArgs<MIXED> x) {
   using S = Shape<2, K>;
   using T = TcShape<K>;
-  constexpr int TC = T::TC, M = T::M, KP1 = T::KP1, KP2 = T::KP2, NQ = T::NQ, NJ = T::NJ;
-  constexpr int N = S::N, Q = S::Q, QF = S::QF, NV = S::NV, QP = T::QP, QFP = T::QFP;
-  constexpr int G1H = (KP1 / 4 + 1) / 2;  // 16-byte groups of an A1 row per half
-  constexpr int WH = 4 * G1H;             // weights per thread
-  constexpr int NG = QP / 4;              // groups of 4 volume points
-  constexpr int QH = (Q + 1) / 2;         // nodal values per thread
-  constexpr int JH = (N + 1) / 2;         // output coefficients per thread
-  static_assert(2 * NG <= 8 && QH <= 16 && JH <= 16, "work split");
+  constexpr int N = S::N, Q = S::Q, QF = S::QF, NV = S::NV;
+  constexpr int TM = T::TM, PT = T::PT, QP = T::QP, KP1 = T::KP1, KP2 = T::KP2, NQ = T::NQ, NJ = T::NJ;
+  constexpr int QFP = T::QFP;
+  const auto& a = tc_stage(x);
   extern __shared__ __align__(1024) float sm[];
-  float* A1h = sm;
-  float* A1l = A1h + M * KP1;
-  float* sU = sm;  // [NV][Q][TC], over A1 once MMA 1 has read it
-  float* A2h = sm + T::A1_FLOATS;
-  float* A2l = A2h + M * KP2;
-  float* B1h = A2l + M * KP2;
-  float* B1l = B1h + NQ * KP1;
-  float* B2h = B1l + NQ * KP1;
-  float* B2l = B2h + NJ * KP2;
-  __shared__ __align__(8) uint64_t mbar[2];
+  float* const A2 = sm;               // block (v, h) at (2 v + h) A2_BLK
+  float* const A1 = sm + T::A1_OFF;   // block (v, h) at (2 v + h) A1_BLK, over A2 of variables 2, 3
+  float* const B1h = sm + T::A2_FLOATS;
+  float* const B1l = B1h + NQ * KP1;
+  float* const B2h = B1l + NQ * KP1;
+  float* const B2l = B2h + NJ * KP2;
+  // mbar[0]: MMA 1 done; mbar[1 + v]: MMA 2 of variable v (and those before it) done
+  __shared__ __align__(8) uint64_t mbar[5];
   __shared__ uint32_t tmem_base;
+  // mixed: reference state and residual of every (variable, cell) of the tile
+  __shared__ float sRef[MIXED ? NV * TM : 1], sRes[MIXED ? NV * TM : 1];
 
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int v = warp & 3, half = warp >> 2;  // variable (TMEM lane quarter), half of the work
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int row = ((warp & 3) << 5) | lane;  // the cell within the tile (TMEM lane)
+  const int t = warp >> 2;                   // variable, point group and side of this thread
   const int nc = a.m.ncells, nf = a.m.nfaces;
-  const int ntiles = (nc + TC - 1) / TC;
-  const int row = v * TC + lane;
+  const int ntiles = (nc + TM - 1) / TM;
+  const bool hook = a.tc_hook != 0 && blockIdx.x == 0;
+  const int limit = hook ? (1 << 12) : (1 << 24);
 
-  for (int i = threadIdx.x; i < T::B_FLOATS; i += 256) B1h[i] = __ldg(a.tcB + i);
-  if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(&mbar[0])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(&mbar[1])));
+  for (int i = tid; i < T::B_FLOATS; i += T::THREADS) B1h[i] = __ldg(x.tcB + i);
+  if (tid == 0) {
+    for (int i = 0; i < 5; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(&mbar[i])));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   if (warp == 0) {
@@ -211,159 +278,292 @@ __global__ void __launch_bounds__(256, 3) cell_update_tc_kernel(const StageArgs<
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
-  const uint32_t trow = (uint32_t)(v * 32) << 16;
+  const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16);  // this warp's lane quarter
   const float g1 = (float)a.gamma - 1.0f;
-  bool ok = true;
-  uint32_t phase = 0;
 
-  // this thread's share of a tile's global inputs: weights l = half*WH + i of
-  // (v, c) and the fluxes of sides 2*half, 2*half+1; loaded a tile ahead
-  float wn[WH], xn[2][QF];
-  auto load_tile = [&](int t) {
-    const int cc = t * TC + lane;
-    const bool in = t < ntiles && cc < nc;
+  // This thread's inputs of a tile, loaded a tile ahead: the weights of
+  // variable t (FP32: as stored, a padding cell gets the unit density state;
+  // mixed: the perturbation weights l >= 1, the mean as reference + residual)
+  // and the face values of side t for every variable.
+  float wn[KP1], xn[NV][QFP], ubn = 0.0f, resn = 0.0f;
+  auto load_tile = [&](int tt) {
+    const int cc = tt * TM + row;
+    const bool in = tt < ntiles && cc < nc;
+    const size_t i0 = (size_t)t * N * nc + cc;
 #pragma unroll
-    for (int i = 0; i < WH; ++i) {
-      const int l = half * WH + i;
-      wn[i] = (in && l < N) ? a.U[(size_t)(v * N + l) * nc + cc] : 0.0f;
+    for (int l = 0; l < KP1; ++l) wn[l] = 0.0f;
+    if constexpr (!MIXED) {
+#pragma unroll
+      for (int l = 0; l < N; ++l) wn[l] = in ? a.U[i0 + (size_t)l * nc] : 0.0f;
+      if (!in && t == 0) wn[0] = 1.0f;
+    } else {
+      ubn = (!in && t == 0) ? 1.0f : 0.0f;
+      resn = 0.0f;
+      if (in) {
+        float hi, lo;
+        if (x.wf_mode == 2) {
+          hi = x.Wf[i0];
+          lo = x.Wlo[(size_t)t * nc + cc];
+        } else {
+          df_split(a.U[i0], hi, lo);
+          if (x.wf_mode == 1) {
+            x.Wf[i0] = hi;
+            x.Wlo[(size_t)t * nc + cc] = lo;
+          }
+        }
+        mixed_mean_split(hi, lo, x.R, i0, ubn, resn);
+#pragma unroll
+        for (int l = 1; l < N; ++l) {
+          const size_t il = i0 + (size_t)l * nc;
+          float wl;
+          if (x.wf_mode == 2) {
+            wl = x.Wf[il];
+          } else {
+            wl = f32_round(a.U[il]);
+            if (x.wf_mode == 1) x.Wf[il] = wl;
+          }
+          wn[l] = x.R ? wl + x.R[il] : wl;
+        }
+      }
     }
+    const int e = in ? a.m.sface[(size_t)t * nc + cc] : 0;
 #pragma unroll
-    for (int s2 = 0; s2 < 2; ++s2) {
-      const int e = in ? a.m.sface[(size_t)(2 * half + s2) * nc + cc] : 0;
+    for (int v = 0; v < NV; ++v) {
+      float dv = 0.0f;
+      if constexpr (MIXED) dv = (in && !(t & 1)) ? x.D[(size_t)v * nf + e] : 0.0f;
 #pragma unroll
-      for (int q = 0; q < QF; ++q) xn[s2][q] = in ? a.F[((size_t)v * QF + q) * nf + e] : 0.0f;
+      for (int q = 0; q < QFP; ++q) {
+        if constexpr (MIXED) xn[v][q] = (in && q < QF) ? x.G[((size_t)v * QF + q) * nf + e] + dv : 0.0f;
+        else xn[v][q] = (in && q < QF) ? a.F[((size_t)v * QF + q) * nf + e] : 0.0f;
+      }
     }
   };
   load_tile(blockIdx.x);
 
+  bool ok = true;
+  uint32_t phase = 0;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, phase ^= 1u) {
-    const int c = tile * TC + lane;
+    const int c = tile * TM + row;
     const bool valid = c < nc;
-    // weights -> A1 (a padding cell gets the unit density state)
-    {
-      float w[WH];
+    // ---- A. weights of variable t -> A1; face values of variables 0, 1 -> A2
+    // (the A2 blocks of variables 2, 3 hold A1 until MMA 1 is done).  The
+    // previous tile's last MMA-2 chain (and so every one before it) must be
+    // done reading A2 first: this thread waited only for its own variable's.
+    if (tile != (int)blockIdx.x) ok = tc_wait(&mbar[NV], phase ^ 1u, limit) && ok;
+    float wcur[MIXED ? 1 : N];
+    if constexpr (!MIXED) {
 #pragma unroll
-      for (int i = 0; i < WH; ++i) w[i] = wn[i];
-      if (!valid && v == 0 && half == 0) w[0] = 1.0f;
+      for (int l = 0; l < N; ++l) wcur[l] = wn[l];
+    } else {
+      sRef[t * TM + row] = ubn;
+      sRes[t * TM + row] = resn;
+    }
 #pragma unroll
-      for (int g = 0; g < G1H; ++g)
-        if ((half * G1H + g) * 4 < KP1)
-          tc_put4(A1h, A1l, tc_off(row, (half * G1H + g) * 4, KP1), &w[4 * g]);
+    for (int g = 0; g < KP1 / 4; ++g)
+      tc_put4(A1 + (2 * t) * T::A1_BLK, A1 + (2 * t + 1) * T::A1_BLK, tc_off(row, 4 * g, KP1), &wn[4 * g]);
+    float xlate[2][QFP];
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      tc_put4(A2 + (2 * v) * T::A2_BLK, A2 + (2 * v + 1) * T::A2_BLK, tc_off(row, T::KV + 4 * t, KP2), xn[v]);
+#pragma unroll
+      for (int q = 0; q < QFP; ++q) xlate[v][q] = xn[2 + v][q];
     }
     asm volatile("fence.proxy.async.shared::cta;");
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      tc_gemm_split<KP1, NQ, M>(tmem, A1h, A1l, B1h, B1l);
+    // all stores of the tile are visible; a failed wait of the previous tile
+    // (carried in ok) ends the CTA's work
+    if (!__syncthreads_and(ok)) {
+      ok = false;
+      break;
+    }
+    if (tid == 0 && !(hook && tile == (int)blockIdx.x)) {
+      tc_gemm3_x4<KP1>(tmem + T::D1_COL, A1, T::A1_BLK, B1h, B1l);
       tc_commit(&mbar[0]);
     }
-    // while MMA 1 runs: face fluxes of two sides -> surface part of A2
-#pragma unroll
-    for (int s2 = 0; s2 < 2; ++s2) {
-      float x[QFP];
-#pragma unroll
-      for (int q = 0; q < QFP; ++q) x[q] = q < QF ? xn[s2][q] : 0.0f;
-#pragma unroll
-      for (int g = 0; g < QFP / 4; ++g)
-        tc_put4(A2h, A2l, tc_off(row, T::KV + (2 * half + s2) * QFP + 4 * g, KP2), &x[4 * g]);
-    }
+    // while MMA 1 runs: the inputs of the next tile
     load_tile(tile + gridDim.x);
-    // while MMA 1 runs: the stage combination of the inputs (all but the RHS
-    // term) for coefficients j = half*JH + jj
-    float base[MAX_OUT][JH];
-    float scale = 0.0f;
-    if (valid) {
-      const int pb = cell_problem(a.m, c);
-      const float pv = a.pre_prob ? a.pre_prob[pb] : a.pre[a.m.level[c]];
-      scale = pv * (a.dt ? (float)a.dt[pb] : 1.0f);
-    }
-#pragma unroll
-    for (int oo = 0; oo < MAX_OUT; ++oo)
-#pragma unroll
-      for (int jj = 0; jj < JH; ++jj) base[oo][jj] = 0.0f;
-    for (int r = 0; r < a.n_in; ++r) {
-      float xr[JH];
-#pragma unroll
-      for (int jj = 0; jj < JH; ++jj) {
-        const int j = half * JH + jj;
-        xr[jj] = (valid && j < N) ? a.in[r][(size_t)(v * N + j) * nc + c] : 0.0f;
-      }
-#pragma unroll
-      for (int oo = 0; oo < MAX_OUT; ++oo) {
-        const float cr = a.C[oo][r];
-#pragma unroll
-        for (int jj = 0; jj < JH; ++jj) base[oo][jj] += cr * xr[jj];
-      }
-    }
-    ok = tc_wait(&mbar[0], phase) && ok;
+    ok = tc_wait(&mbar[0], phase, limit) && ok;
     asm volatile("tcgen05.fence::after_thread_sync;");
-    {
-      float u[16];
-      tc_ld16(tmem + trow, u);
-      // this thread saw MMA 1 complete, so its reads of A1 are over: sU may overwrite A1
+
+    // ---- B. nodal values at this thread's points (tensor memory) -> fluxes -> A2
+    float u[NV][PT];
 #pragma unroll
-      for (int i = 0; i < QH; ++i) {
-        const int q = half * QH + i;
-        const float val = half ? (QH + i < 16 ? u[QH + i] : 0.0f) : u[i];
-        if (q < Q) sU[(v * Q + q) * TC + lane] = val;
+    for (int v = 0; v < NV; ++v) {
+      if constexpr (PT == 4) {
+        tc_ld4(tl + T::D1_COL + 16 * v + 4 * t, u[v]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < PT; ++i) u[v][i] = tc_ld1(tl + T::D1_COL + 16 * v + PT * t + i);
       }
     }
-    __syncthreads();
-    // Euler flux in direction d at points 4g..4g+3 (task = warp) -> volume part of A2
-    if (warp < 2 * NG) {
-      const int d = warp & 1, g = warp >> 1;
-      float f[NV][4];
+    tc_ld_wait();
+    float fx[NV][PT], fy[NV][PT];
+    {
+      float ub[NV], res[NV];
+      if constexpr (MIXED) {
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int q = 4 * g + i;
-        float u[NV], fd[NV];
-#pragma unroll
-        for (int vv = 0; vv < NV; ++vv) u[vv] = q < Q ? sU[(vv * Q + q) * TC + lane] : (vv == 0 ? 1.0f : 0.0f);
-        if (d == 0)
-          euler_flux<float, 2>(u, 0, g1, fd);
-        else
-          euler_flux<float, 2>(u, 1, g1, fd);
-#pragma unroll
-        for (int vv = 0; vv < NV; ++vv) f[vv][i] = q < Q ? fd[vv] : 0.0f;
+        for (int v = 0; v < NV; ++v) {
+          ub[v] = sRef[v * TM + row];
+          res[v] = sRes[v * TM + row];
+        }
       }
 #pragma unroll
-      for (int vv = 0; vv < NV; ++vv)
-        tc_put4(A2h, A2l, tc_off(vv * TC + lane, d * QP + 4 * g, KP2), f[vv]);
+      for (int i = 0; i < PT; ++i) {
+        const bool live = PT * t + i < Q;
+        if constexpr (!MIXED) {
+          float uu[NV], f[2][NV];
+#pragma unroll
+          for (int v = 0; v < NV; ++v) uu[v] = live ? u[v][i] : (v == 0 ? 1.0f : 0.0f);
+          euler_flux_all<float, 2>(uu, g1, f);
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            fx[v][i] = live ? f[0][v] : 0.0f;
+            fy[v][i] = live ? f[1][v] : 0.0f;
+          }
+        } else {
+          const RefState<float, 2> rs = ref_state<float, 2>(ub, g1);
+          float du[NV], f0[NV], f1[NV];
+#pragma unroll
+          for (int v = 0; v < NV; ++v) du[v] = live ? u[v][i] + res[v] : 0.0f;
+          const Pert<float, 2> pq = perturb<float, 2>(rs, du, g1);
+          euler_dflux<float, 2>(rs, du, pq, 0, f0);
+          euler_dflux<float, 2>(rs, du, pq, 1, f1);
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            fx[v][i] = live ? f0[v] : 0.0f;
+            fy[v][i] = live ? f1[v] : 0.0f;
+          }
+        }
+      }
+    }
+    // MMA 1 is complete (this thread saw its barrier), so A1 may be overwritten
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      float* Ah = A2 + (2 * v) * T::A2_BLK;
+      float* Al = A2 + (2 * v + 1) * T::A2_BLK;
+      if constexpr (PT == 4) {
+        tc_put4(Ah, Al, tc_off(row, 4 * t, KP2), fx[v]);
+        tc_put4(Ah, Al, tc_off(row, QP + 4 * t, KP2), fy[v]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < PT; ++i) {
+          tc_put1(Ah, Al, tc_off(row, PT * t + i, KP2), fx[v][i]);
+          tc_put1(Ah, Al, tc_off(row, QP + PT * t + i, KP2), fy[v][i]);
+        }
+      }
+      if (v >= 2) tc_put4(Ah, Al, tc_off(row, T::KV + 4 * t, KP2), xlate[v - 2]);
     }
     asm volatile("fence.proxy.async.shared::cta;");
     asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
+    const bool all_ok = __syncthreads_and(ok) != 0;
     asm volatile("tcgen05.fence::after_thread_sync;");
-    if (threadIdx.x == 0) {
-      tc_gemm_split<KP2, NJ, M>(tmem + NQ, A2h, A2l, B2h, B2l);
-      tc_commit(&mbar[1]);
+    if (!all_ok) {
+      ok = false;
+      break;
     }
-    ok = tc_wait(&mbar[1], phase) && ok;
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    float acc[16];
-    tc_ld16(tmem + trow + NQ, acc);
-    if (valid && ok) {
+    if (tid == 0) {
+      // one chain per variable, each with its own barrier: the threads of
+      // variable v start their epilogue once chain v is done
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        tc_gemm3<KP2>(tmem + T::D2_COL + 16 * v, A2 + (2 * v) * T::A2_BLK, A2 + (2 * v + 1) * T::A2_BLK, B2h, B2l);
+        tc_commit(&mbar[1 + v]);
+      }
+    }
+
+    // ---- C. while MMA 2 runs: the stage combination of the inputs for
+    // variable t (all but the right-hand side term)
+    const size_t iv = (size_t)t * N * nc + c;
+    if constexpr (!MIXED) {
+      float base[MAX_OUT][N];
 #pragma unroll
       for (int oo = 0; oo < MAX_OUT; ++oo)
-        if (oo < a.n_out) {
-          const float ckv = a.ck[oo] * scale;
 #pragma unroll
-          for (int jj = 0; jj < JH; ++jj) {
-            const int j = half * JH + jj;
-            const float rhs = half ? (JH + jj < 16 ? acc[JH + jj] : 0.0f) : acc[jj];
-            if (j < N) a.out[oo][(size_t)(v * N + j) * nc + c] = base[oo][jj] + ckv * rhs;
+        for (int j = 0; j < N; ++j) base[oo][j] = 0.0f;
+      float scale = 0.0f;
+      if (valid) {
+        const int pb = cell_problem(a.m, c);
+        scale = (a.pre_prob ? a.pre_prob[pb] : a.pre[a.m.level[c]]) * (a.dt ? (float)a.dt[pb] : 1.0f);
+#pragma unroll
+        for (int r = 0; r < MAX_IN; ++r) {
+          if (r >= a.n_in) break;
+          const float* src = a.in[r];
+          const bool own = src == a.U;
+#pragma unroll
+          for (int j = 0; j < N; ++j) {
+            const float xr = own ? wcur[j] : src[iv + (size_t)j * nc];
+#pragma unroll
+            for (int oo = 0; oo < MAX_OUT; ++oo) base[oo][j] += a.C[oo][r] * xr;
           }
         }
+      }
+      ok = tc_wait(&mbar[1 + t], phase, limit) && ok;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      float acc[16];
+      tc_ld16(tl + T::D2_COL + 16 * t, acc);
+      tc_ld_wait();
+      if (valid && ok) {
+#pragma unroll
+        for (int oo = 0; oo < MAX_OUT; ++oo) {
+          if (oo >= a.n_out) break;
+          const float ckv = a.ck[oo] * scale;
+#pragma unroll
+          for (int j = 0; j < N; ++j) a.out[oo][iv + (size_t)j * nc] = base[oo][j] + ckv * acc[j];
+        }
+      }
+    } else {
+      float base[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) base[j] = 0.0f;
+      if (x.delta && valid) {
+        for (int r = 0; r < x.n_inR; ++r) {
+          const float cr = x.Cf[r];
+#pragma unroll
+          for (int j = 0; j < N; ++j) base[j] += cr * x.inR[r][iv + (size_t)j * nc];
+        }
+      }
+      ok = tc_wait(&mbar[1 + t], phase, limit) && ok;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      float acc[16];
+      tc_ld16(tl + T::D2_COL + 16 * t, acc);
+      tc_ld_wait();
+      if (valid && ok) {
+        const int pb = cell_problem(a.m, c);
+        const double pre = a.pre_prob ? a.pre_prob[pb] : a.pre[a.m.level[c]];
+        const double dtv = a.dt ? a.dt[pb] : 1.0;
+        if (x.delta) {
+          const float sc = x.ckf * f32_round(dtv * pre);
+#pragma unroll
+          for (int j = 0; j < N; ++j) {
+            const size_t idx = iv + (size_t)j * nc;
+            const float val = base[j] + sc * acc[j];
+            if (x.outR) x.outR[idx] = val;
+            else a.out[0][idx] = a.U[idx] + f64_exact(val);
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < N; ++j) {
+            const size_t idx = iv + (size_t)j * nc;
+            const double rhs = pre * f64_exact(acc[j]);
+            for (int oo = 0; oo < a.n_out; ++oo) {
+              double val = a.ck[oo] * dtv * rhs;
+              for (int r = 0; r < a.n_in; ++r) {
+                const double cr = a.C[oo][r];
+                if (cr != 0.0) val += cr * a.in[r][idx];
+              }
+              a.out[oo][idx] = val;
+            }
+          }
+        }
+      }
     }
-    // all warps are done with MMA 2's operands and results before the next
-    // tile; a wait that gave up anywhere ends the CTA's work
     asm volatile("tcgen05.fence::before_thread_sync;");
-    ok = __syncthreads_and(ok) != 0;
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    if (!ok) break;
   }
-  if (!ok && threadIdx.x == 0) atomicOr(a.status, 1 << DG_ERR_TIMEOUT_BIT);
-  asm volatile("tcgen05.fence::before_thread_sync;");
-  __syncthreads();
+  // a wait that gave up anywhere: the CTA stopped early; report it.  No
+  // tensor-core work of this CTA is in flight unless a multiply it issued
+  // never completed.
+  ok = __syncthreads_and(ok) != 0;
+  if (!ok && tid == 0) atomicOr(a.status, 1 << DG_ERR_TIMEOUT_BIT);
+  asm volatile("tcgen05.fence::after_thread_sync;");
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(T::TMEM_COLS));
 }
@@ -416,49 +616,40 @@ void fill_tc_tables(const std::vector<double>& Tab, std::vector<float>& out) {
   }
 }
 
-template <int K>
+template <int K, bool MIXED>
 struct TcGrid {
   static inline int ctas = 0;  // resident CTAs on the whole device (set by prepare_cell_tc)
 };
 
-template <int K>
+template <int K, bool MIXED>
 cudaError_t launch_cell_tc(const void* pa, cudaStream_t s) {
-  const auto& a = *static_cast<const StageArgs<float>*>(pa);
+  const auto& x = *static_cast<const TcArgs<MIXED>*>(pa);
   using T = TcShape<K>;
-  if (a.m.ncells == 0) return cudaSuccess;
-  const int ntiles = (a.m.ncells + T::TC - 1) / T::TC;
-  const int grid = TcGrid<K>::ctas > 0 && TcGrid<K>::ctas < ntiles ? TcGrid<K>::ctas : ntiles;
-  cell_update_tc_kernel<K><<<grid, 256, T::SMEM, s>>>(a);
+  const int nc = tc_stage(x).m.ncells;
+  if (nc == 0) return cudaSuccess;
+  const int ntiles = (nc + T::TM - 1) / T::TM;
+  const int ctas = TcGrid<K, MIXED>::ctas;
+  const int grid = ctas > 0 && ctas < ntiles ? ctas : ntiles;
+  cell_tc_kernel<K, MIXED><<<grid, T::THREADS, T::SMEM, s>>>(x);
   return cudaGetLastError();
 }
 
-template <int K>
+template <int K, bool MIXED>
 cudaError_t prepare_cell_tc() {
-  cudaError_t e = cudaFuncSetAttribute(cell_update_tc_kernel<K>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(cell_tc_kernel<K, MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)TcShape<K>::SMEM);
   if (e != cudaSuccess) return e;
-  // all of the unified L1/shared storage as shared memory: several CTAs per SM
-  e = cudaFuncSetAttribute(cell_update_tc_kernel<K>, cudaFuncAttributePreferredSharedMemoryCarveout,
+  e = cudaFuncSetAttribute(cell_tc_kernel<K, MIXED>, cudaFuncAttributePreferredSharedMemoryCarveout,
                            (int)cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
-  // resident CTAs per SM from the kernel's registers and shared memory
-  int dev = 0, sms = 0, smem_sm = 0, smem_rsv = 0, regs_sm = 0;
-  cudaFuncAttributes fa;
+  // one persistent CTA per resident slot: the occupancy calculator's count
+  int dev = 0, sms = 0, per_sm = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  if ((e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess)
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cell_tc_kernel<K, MIXED>, TcShape<K>::THREADS,
+                                                         TcShape<K>::SMEM)) != cudaSuccess)
     return e;
-  if ((e = cudaDeviceGetAttribute(&smem_rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev)) != cudaSuccess)
-    return e;
-  if ((e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev)) != cudaSuccess)
-    return e;
-  if ((e = cudaFuncGetAttributes(&fa, cell_update_tc_kernel<K>)) != cudaSuccess) return e;
-  const int by_smem = smem_sm / (int)(TcShape<K>::SMEM + fa.sharedSizeBytes + smem_rsv);
-  const int by_regs = regs_sm / ((fa.numRegs > 0 ? fa.numRegs : 1) * 256);
-  int per_sm = by_smem < by_regs ? by_smem : by_regs;
-  if (per_sm > 8) per_sm = 8;  // 2048 threads per SM
-  TcGrid<K>::ctas = sms * (per_sm > 0 ? per_sm : 1);
+  TcGrid<K, MIXED>::ctas = sms * (per_sm > 0 ? per_sm : 1);
   return cudaSuccess;
 }
 

@@ -26,7 +26,7 @@ EXPORTS = ["dg_default_options", "dg_create", "dg_destroy", "dg_last_error", "dg
            "dg_status", "dg_profile_begin", "dg_profile_end", "dg_totals_noalloc",
            "dg_create_batch", "dg_batch_advance", "dg_n_problems", "dg_tiles",
            "dg_limiter_counts", "dg_set_tiles", "dg_adapt_mark", "dg_adapt_set", "dg_regrid",
-           "dg_set_gravity"]
+           "dg_set_gravity", "dg_test_force_timeout"]
 KERNEL_KINDS = ["face", "cell", "limit", "dt", "other", "adjoint"]
 
 
@@ -94,6 +94,7 @@ def load(path=LIB_PATH):
     L.dg_adapt_set.argtypes = [vp, i32p, i64p, i64p, vp]
     L.dg_regrid.argtypes = [vp, vp, vp, vp]
     L.dg_set_gravity.argtypes = [vp, vp, vp]
+    L.dg_test_force_timeout.argtypes = [vp]
     L.dg_profile_begin.argtypes = [vp]
     L.dg_profile_end.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_int]
     for name in EXPORTS:
@@ -395,6 +396,11 @@ class Solver:
         ct, ft = C.c_int(), C.c_int()
         self._check(self._L.dg_tiles(self._h, C.byref(ct), C.byref(ft)))
         return ct.value, ft.value
+
+    def force_timeout(self):
+        """Test hook: the next tensor-core cell launch outside a graph gives up
+        a bounded wait in its first CTA (see dg_test_force_timeout)."""
+        self._check(self._L.dg_test_force_timeout(self._h))
 
     def status(self):
         s = C.c_int()

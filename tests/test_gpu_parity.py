@@ -357,9 +357,10 @@ def test_rhs_fp32_tensor_cores(k):
 
 @pytest.mark.parametrize("k", [1, 2, 3])
 def test_rhs_fp32_tensor_cores_many_tiles(k):
-    """150 x 131 cells: 615 tiles of 32 cells with a ragged last tile, more
-    tiles than resident CTAs, so each persistent CTA runs several tiles."""
-    m = wl.mesh_uniform(2, [150, 131], [0.0, 0.0], [1.5, 1.31])
+    """300 x 211 cells: 495 tiles of 128 cells with a ragged last tile (68
+    cells), more tiles than resident CTAs (one per SM), so each persistent
+    CTA runs several tiles."""
+    m = wl.mesh_uniform(2, [300, 211], [0.0, 0.0], [3.0, 2.11])
     o = oracle_for(m, k)
     s = solver_for(m, k, precision="fp32_tc")
     W = wl.random_weights(2, o.N, o.n_cells, seed=950 + k).astype(np.float32)
