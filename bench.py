@@ -365,6 +365,24 @@ def run_gpu(args, rank, world, local_rank):
                     s.rk_step(W)
                     ev[i][1].record(stream)
                 torch.cuda.synchronize()
+        paths = None
+        if graph and args.workload in ("wave2d", "square64"):
+            # the same steps as one persistent cooperative kernel (dg_set_advance_mode)
+            Wp = W.clone()
+            s.set_advance_mode("persistent")
+            s.advance(Wp, args.warmup)
+            torch.cuda.synchronize()
+            p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            p0.record(stream)
+            s.advance(Wp, args.steps)
+            p1.record(stream)
+            torch.cuda.synchronize()
+            s.set_advance_mode("graph")
+            paths = {"graph_ms_per_step": ev[0][0].elapsed_time(ev[0][1]) / args.steps,
+                     "persistent_ms_per_step": p0.elapsed_time(p1) / args.steps,
+                     "note": "dg_advance as a CUDA graph of the stage kernels (default, timed above) "
+                             "or as one persistent cooperative kernel with grid barriers"}
+            del Wp
         if graph:
             # per-kernel durations from a separate, instrumented pass of the same steps
             s.profile_begin()
@@ -443,7 +461,7 @@ def run_gpu(args, rank, world, local_rank):
             del sf, Wf
         results[precision] = dict(solver=s, ms=ms, ms_e2e=ms_e2e, prof=prof, clocks=clk.summary(),
                                   state_bytes=W.numel() * W.element_size(), n_cells=s.n_cells,
-                                  tiles=tiles, diag=diag)
+                                  tiles=tiles, diag=diag, paths=paths)
         del W, W0, Wd, Wh
     return results
 
@@ -652,6 +670,8 @@ def summarize(args, results, world):
         }
         if r.get("diag"):
             lines[precision]["diagnostics"] = r["diag"]
+        if r.get("paths"):
+            lines[precision]["advance_paths"] = r["paths"]
         if r.get("tiles"):
             t = dict(r["tiles"])
             t["fixed_tile_value"] = dof_updates / (t.pop("fixed_tile_ms") * 1e-3)
@@ -1092,6 +1112,8 @@ def main():
         out.update({kk: one[kk] for kk in ("roofline", "e2e", "gpu_launches", "clocks", "kernel_ms")})
         if "diagnostics" in one:
             out["diagnostics"] = one["diagnostics"]
+        if "advance_paths" in one:
+            out["advance_paths"] = one["advance_paths"]
         print(json.dumps(out), flush=True)
         return 0
     head = lines["fp64"]

@@ -208,6 +208,31 @@ int dg_create_batch(const dg_mesh_desc* meshes, const double* gamma, int n_probl
  * timestep) as one CUDA-graph launch; same as dg_advance. */
 int dg_batch_advance(dg_handle* h, void* W_dev, int n_steps, double* dt_hist_dev, void* stream);
 
+/* How dg_advance (and dg_batch_advance) run their steps.
+ *   DG_ADVANCE_GRAPH       one CUDA graph per (W, n_steps, dt_hist) holding
+ *                          every kernel launch of the steps (recorded on first
+ *                          use, replayed afterwards);
+ *   DG_ADVANCE_PERSISTENT  one cooperative launch of a persistent kernel that
+ *                          runs all phases of the steps (timestep, face fluxes,
+ *                          cell updates, limiters) separated by grid-wide
+ *                          barriers; bit-identical results.  Its barrier waits
+ *                          are bounded: a wait that gives up stops the kernel
+ *                          and latches DG_ERR_TIMEOUT (dg_status).
+ * The persistent kernel serves 2D handles with an FP64 or FP32 state and the
+ * CUDA-core stage kernels (not DG_FP32_TC / DG_MIXED / DG_MIXED_TC, not the
+ * one-thread-per-cell tile), without a gravity source, with at most 5 RK
+ * stages.  DG_ADVANCE_GRAPH is the default on every handle: on one GB300 a
+ * graph's kernel boundary costs about as much as the persistent kernel's
+ * grid barrier, and the graph measured faster from 32^2 to 128^2 cells.
+ * Setting DG_ADVANCE_PERSISTENT on a handle that does not support it
+ * returns DG_ERR_UNSUPPORTED; dg_advance_mode reports the path dg_advance
+ * takes now.  The first persistent dg_advance on a state
+ * builds a step plan in device memory (synchronous copy; make that first call
+ * outside any stream capture). */
+enum { DG_ADVANCE_GRAPH = 0, DG_ADVANCE_PERSISTENT = 1 };
+int dg_set_advance_mode(dg_handle* h, int mode);
+int dg_advance_mode(const dg_handle* h, int* mode);
+
 /* Number of problems and, if cell_offsets_host is not NULL, the first cell
  * of every problem (n_problems + 1 entries, the last one = n_cells). */
 int dg_n_problems(const dg_handle* h, int* n_problems, int64_t* cell_offsets_host);

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <memory>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -434,6 +435,11 @@ struct dg_handle {
   cudaStream_t cap_stream = nullptr;
   std::map<std::tuple<void*, int, void*>, cudaGraphExec_t> graphs;
   std::vector<cudaGraph_t> graph_defs;
+  // dg_advance as one persistent kernel: mode, plans per (W, dt history)
+  // with their largest phase's block count, the grid barrier's words
+  int advance_mode = DG_ADVANCE_GRAPH;
+  std::map<std::pair<void*, void*>, std::pair<void*, int>> plans;
+  unsigned* bar = nullptr;
   std::string err;
   std::mutex mu;
   // adjoint work arrays (allocated by the first dg_rk_step_adjoint call)
@@ -888,6 +894,8 @@ void drop_graphs(dg_handle* h) {
   h->graphs.clear();
   for (auto g : h->graph_defs) cudaGraphDestroy(g);
   h->graph_defs.clear();
+  for (auto& kv : h->plans) cudaFree(kv.second.first);  // (synchronises the device)
+  h->plans.clear();
 }
 
 cudaError_t cell_launch(dg_handle* h, const void* args, cudaStream_t s) {
@@ -978,7 +986,7 @@ StageArgs<real> stage_args(dg_handle* h, const Op& op, const void* U, void* W) {
 }
 
 template <typename real>
-int run_limit(dg_handle* h, const void* src, void* dst, cudaStream_t s) {
+LimitArgs<real> limit_args(dg_handle* h, const void* src, void* dst) {
   LimitArgs<real> la;
   la.m = h->md;
   la.tab64 = h->tab64;
@@ -997,6 +1005,12 @@ int run_limit(dg_handle* h, const void* src, void* dst, cudaStream_t s) {
   la.queue = h->lim_queue;
   la.queue_len = h->lim_queue + std::max(h->ncells, 1);
   la.status = h->status;
+  return la;
+}
+
+template <typename real>
+int run_limit(dg_handle* h, const void* src, void* dst, cudaStream_t s) {
+  const LimitArgs<real> la = limit_args<real>(h, src, dst);
   DG_CUDA(h, timed(h, DG_KERNEL_LIMIT, s, [&] { return h->ks->limit(&la, s); }));
   return DG_OK;
 }
@@ -1078,6 +1092,76 @@ int rk_step_any(dg_handle* h, void* W, double dt, double* dt_used, cudaStream_t 
     if (r != DG_OK) return r;
   }
   return step_impl<real>(h, h->prog_step, W, s);
+}
+
+// dg_advance with the persistent whole-step kernel: the handle supports it
+// (2D, an FP64 or FP32 state with the CUDA-core stage kernels, no gravity
+// source, at most PERSIST_MAX_OPS stages)
+bool persist_supported(const dg_handle* h) {
+  return h->ks->persist && !h->ms && !h->use_tc && !h->use_direct && !h->accel && h->ncells > 0 &&
+         (int)h->prog_step.ops.size() <= PERSIST_MAX_OPS;
+}
+
+// the plan of one step on state W (dt history at hist, or none), built once
+// per (W, hist) and kept in device memory until the graphs are dropped
+template <typename real>
+int persist_plan(dg_handle* h, void* W, double* hist, void** plan_dev, int* max_blocks) {
+  const auto key = std::make_pair(W, static_cast<void*>(hist));
+  auto it = h->plans.find(key);
+  if (it == h->plans.end()) {
+    std::unique_ptr<PersistPlan<real>> P(new PersistPlan<real>());
+    const Program& prog = h->prog_step;
+    P->n_ops = (int)prog.ops.size();
+    for (int i = 0; i < P->n_ops; ++i) {
+      const Op& op = prog.ops[i];
+      void* U = op.in_reg == 0 ? W : h->regs[op.in_reg - 1];
+      P->op[i].st = stage_args<real>(h, op, U, W);
+      if (op.lim_src >= 0) {
+        void* src = op.lim_src == 0 ? W : h->regs[op.lim_src - 1];
+        void* dst = op.lim_dst == 0 ? W : h->regs[op.lim_dst - 1];
+        P->op[i].lim = 1;
+        P->op[i].la = limit_args<real>(h, src, dst);
+      }
+    }
+    AuxArgs<real> a = aux_args<real>(h);
+    a.W = static_cast<const real*>(W);
+    const double fac = dt_factor(h);
+    a.grav_factor = fac * std::sqrt(2.0 * h->gamma * (h->gamma - 1.0));
+    a.dt_factor = fac;
+    a.dt_out = h->scal;
+    a.dt_copy = hist;
+    a.dt_done = h->dt_done;
+    P->dt = a;
+    const int nc = h->ncells, nf = std::max(h->nfaces, 0);
+    P->face_blocks = (nf + 31) / 32;
+    P->cell_blocks = (nc + 31) / 32;
+    P->lim_blocks = (nc + 127) / 128;
+    P->pos_blocks = std::min((nc + 127) / 128, 608);
+    P->dt_blocks = (nc + 127) / 128;
+    const int mb = std::max({P->face_blocks, P->cell_blocks, P->lim_blocks, P->pos_blocks, P->dt_blocks});
+    void* d = nullptr;
+    DG_CUDA(h, cudaMalloc(&d, sizeof(PersistPlan<real>)));
+    const cudaError_t e = cudaMemcpy(d, P.get(), sizeof(PersistPlan<real>), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaFree(d);
+      return cuda_fail(h, e, "cudaMemcpy step plan");
+    }
+    it = h->plans.emplace(key, std::make_pair(d, mb)).first;
+  }
+  *plan_dev = it->second.first;
+  *max_blocks = it->second.second;
+  return DG_OK;
+}
+
+template <typename real>
+int advance_persistent(dg_handle* h, void* W, int n_steps, double* hist, cudaStream_t s) {
+  void* plan = nullptr;
+  int mb = 0;
+  const int r = persist_plan<real>(h, W, hist, &plan, &mb);
+  if (r != DG_OK) return r;
+  DG_CUDA(h, cudaMemsetAsync(h->bar, 0, 4 * sizeof(unsigned), s));
+  DG_CUDA(h, timed(h, DG_KERNEL_OTHER, s, [&] { return h->ks->persist(plan, mb, n_steps, h->bar, h->status, s); }));
+  return DG_OK;
 }
 
 template <typename real>
@@ -1505,6 +1589,14 @@ static int create_impl(const dg_mesh_desc* mesh, int nprob, int k, double gamma,
                            : autotune_tiles<float>(h, h->cap_stream);
     if (r != DG_OK) return bail(r);
   }
+  // the persistent whole-step kernel, an alternative for dg_advance
+  // (dg_set_advance_mode); the graph stays the default: it measured faster
+  // on every mesh size tried, down to 32^2 cells
+  if (ks->persist && ks->prepare_persist) {
+    if ((r = dalloc(h, 4 * sizeof(unsigned), &p)) != DG_OK) return bail(r);
+    h->bar = static_cast<unsigned*>(p);
+    if (ks->prepare_persist() != cudaSuccess) return bail(cuda_fail(h, cudaGetLastError(), "kernel attributes"));
+  }
   *out = h;
   return DG_OK;
 }
@@ -1534,6 +1626,7 @@ int dg_destroy(dg_handle* h) {
   for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
   for (auto e : h->ev_pool) cudaEventDestroy(e);
   for (auto g : h->graph_defs) cudaGraphDestroy(g);
+  for (auto& kv : h->plans) cudaFree(kv.second.first);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   for (void* p : h->allocs) cudaFree(p);
   delete h;
@@ -1660,6 +1753,9 @@ int dg_advance(dg_handle* h, void* W_dev, int n_steps, double* dt_hist_dev, void
   if (n_steps == 0) return DG_OK;
   std::lock_guard<std::mutex> lock(h->mu);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (h->advance_mode == DG_ADVANCE_PERSISTENT && persist_supported(h))
+    return h->prec == DG_FP64 ? advance_persistent<double>(h, W_dev, n_steps, dt_hist_dev, s)
+                              : advance_persistent<float>(h, W_dev, n_steps, dt_hist_dev, s);
   auto key = std::make_tuple(W_dev, n_steps, (void*)dt_hist_dev);
   auto it = h->graphs.find(key);
   if (it == h->graphs.end()) {
@@ -1948,6 +2044,25 @@ int dg_profile_end(dg_handle* h, int* launches, double* total_ms, int n_kinds) {
   }
   h->ev_marks.clear();
   h->ev_used = 0;
+  return DG_OK;
+}
+
+int dg_set_advance_mode(dg_handle* h, int mode) {
+  if (!check_handle(h)) return DG_ERR_ARG;
+  if (mode != DG_ADVANCE_GRAPH && mode != DG_ADVANCE_PERSISTENT) return fail(h, DG_ERR_ARG, "dg_set_advance_mode: mode");
+  if (mode == DG_ADVANCE_PERSISTENT && !persist_supported(h))
+    return fail(h, DG_ERR_UNSUPPORTED,
+                "dg_set_advance_mode: the persistent step kernel needs a 2D FP64 or FP32 handle with the "
+                "CUDA-core stage kernels, no gravity source and at most 5 stages");
+  std::lock_guard<std::mutex> lock(h->mu);
+  h->advance_mode = mode;
+  return DG_OK;
+}
+
+int dg_advance_mode(const dg_handle* h, int* mode) {
+  if (!check_handle(h) || !mode) return DG_ERR_ARG;
+  *mode = h->advance_mode == DG_ADVANCE_PERSISTENT && persist_supported(h) ? DG_ADVANCE_PERSISTENT
+                                                                           : DG_ADVANCE_GRAPH;
   return DG_OK;
 }
 

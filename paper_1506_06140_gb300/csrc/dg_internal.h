@@ -208,6 +208,26 @@ struct AdjointArgs {
   double scale = 1.0;
 };
 
+// Plan of the persistent whole-step kernel (dg_persist.cuh): the arguments
+// of every phase of one RK step, in device memory.  Records are 16-byte
+// aligned (the kernel copies them into shared memory in 16-byte chunks).
+constexpr int PERSIST_MAX_OPS = 5;
+
+template <typename real>
+struct PersistOp {
+  alignas(16) StageArgs<real> st;  // face and cell phases
+  alignas(16) LimitArgs<real> la;  // limiter phases (lim != 0)
+  int lim = 0;
+};
+
+template <typename real>
+struct PersistPlan {
+  PersistOp<real> op[PERSIST_MAX_OPS];
+  alignas(16) AuxArgs<real> dt;    // timestep phase; dt_copy (if set) advances by nprob per step
+  int n_ops = 0;
+  int face_blocks = 0, cell_blocks = 0, lim_blocks = 0, pos_blocks = 0, dt_blocks = 0;
+};
+
 // out = sum_r c[r] x[r] over n elements (x[r] may alias out)
 constexpr int MAX_COMBINE = 8;
 template <typename real>
@@ -250,6 +270,12 @@ struct KernelSet {
   cudaError_t (*cell_tc)(const void* stage_args, cudaStream_t s) = nullptr;
   cudaError_t (*prepare_tc)() = nullptr;
   void (*fill_tc)(const std::vector<double>& tab, std::vector<float>& out) = nullptr;
+  // persistent whole-step kernel (2D), nullptr where not built: n_steps steps
+  // of the plan (a PersistPlan<real> in device memory) in one cooperative
+  // launch of at most max_phase_blocks blocks; bar: 3 zeroed words
+  cudaError_t (*persist)(const void* plan_dev, int max_phase_blocks, int n_steps, unsigned* bar, int* status,
+                         cudaStream_t s) = nullptr;
+  cudaError_t (*prepare_persist)() = nullptr;
 };
 
 const KernelSet* kernel_set(int prec, int dim, int k);

@@ -447,10 +447,10 @@ __device__ bool points_clear_fp32(const MeshDev& m, const float* tab32, float rh
 // keeps its FP64 weights bit for bit); the positivity limiter's final
 // decisions in FP64 behind exact FP32 prechecks.
 template <typename real, int DIM, int K>
-__global__ void __launch_bounds__(128) limit_kernel(const LimitArgs<real> a) {
+__device__ __forceinline__ void limit_body(const LimitArgs<real>& a, int bid) {
   using S = Shape<DIM, K>;
   constexpr int NV = S::NV, N = S::N;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = bid * blockDim.x + threadIdx.x;
   const int nc = a.m.ncells;
   if (c >= nc) return;
   real w[NV][N];
@@ -608,6 +608,11 @@ __global__ void __launch_bounds__(128) limit_kernel(const LimitArgs<real> a) {
   if (need_positivity) a.queue[atomicAdd(a.queue_len, 1)] = c;
 }
 
+template <typename real, int DIM, int K>
+__global__ void __launch_bounds__(128) limit_kernel(const LimitArgs<real> a) {
+  limit_body<real, DIM, K>(a, blockIdx.x);
+}
+
 // Positivity limiter of Sec. 3.4 (with the hanging-face points of Sec. 4.4)
 // for the queued cells, in FP64: theta_1 on the density, then theta_2 from
 // the pressure root tau of every point below eps.  One warp per queued cell,
@@ -620,18 +625,19 @@ __device__ __forceinline__ double warp_min(double x) {
   return x;
 }
 
+// blocks bid of nblk striding over the queue
 template <typename real, int DIM, int K>
-__global__ void __launch_bounds__(128) positivity_kernel(const LimitArgs<real> a) {
+__device__ __forceinline__ void positivity_body(const LimitArgs<real>& a, int bid, int nblk) {
   using S = Shape<DIM, K>;
   constexpr int NV = S::NV, N = S::N;
   const int nc = a.m.ncells;
   const double* tab = a.tab64;
   const int len = *a.queue_len;
-  if (a.counts && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(a.counts + 2, (unsigned long long)len);
+  if (a.counts && bid == 0 && threadIdx.x == 0) atomicAdd(a.counts + 2, (unsigned long long)len);
   const int lane = threadIdx.x & 31;
   const int wpb = blockDim.x >> 5;
   // warp-uniform loop: every lane of a warp takes the same cells
-  for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < len; i += gridDim.x * wpb) {
+  for (int i = bid * wpb + (threadIdx.x >> 5); i < len; i += nblk * wpb) {
     const int c = a.queue[i];
     real w[NV][N];
 #pragma unroll
@@ -729,6 +735,11 @@ __global__ void __launch_bounds__(128) positivity_kernel(const LimitArgs<real> a
   }
 }
 
+template <typename real, int DIM, int K>
+__global__ void __launch_bounds__(128) positivity_kernel(const LimitArgs<real> a) {
+  positivity_body<real, DIM, K>(a, blockIdx.x, gridDim.x);
+}
+
 // ===========================================================================
 // Auxiliary kernels
 
@@ -759,10 +770,11 @@ __device__ __forceinline__ double block_sum(double x, double* sh) {
 // s_K = sum_a (|v_a| + c) / dx_K of the cell mean; since correctly rounded
 // division is monotone, fac / max s_K equals min_K fac / s_K exactly.  The
 // maximum is accumulated as the bit pattern of a positive double.
-template <typename real, int DIM, int K>
-__global__ void __launch_bounds__(RED_THREADS) dt_kernel(const AuxArgs<real> a) {
+// the work of block bid of nblk, THREADS threads per block
+template <typename real, int DIM, int K, int THREADS>
+__device__ __forceinline__ void dt_body(const AuxArgs<real>& a, int bid, int nblk) {
   using S = Shape<DIM, K>;
-  const int c = blockIdx.x * RED_THREADS + threadIdx.x;
+  const int c = bid * THREADS + threadIdx.x;
   const int nc = a.m.ncells;
   double speed = 0.0;
   int pb = 0;
@@ -810,8 +822,8 @@ __global__ void __launch_bounds__(RED_THREADS) dt_kernel(const AuxArgs<real> a) 
   // a warp whose cells belong to one problem reduces with shuffles; the block
   // then issues one atomic per run of warps with the same problem (a warp
   // spanning two problems falls back to one atomic per cell)
-  __shared__ int sp[RED_THREADS / 32];
-  __shared__ double ss[RED_THREADS / 32];
+  __shared__ int sp[THREADS / 32];
+  __shared__ double ss[THREADS / 32];
   const unsigned full = 0xffffffffu;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int p0 = __shfl_sync(full, pb, 0);
@@ -831,7 +843,7 @@ __global__ void __launch_bounds__(RED_THREADS) dt_kernel(const AuxArgs<real> a) 
   if (threadIdx.x == 0) {
     int cur = -1;
     double m = 0.0;
-    for (int i = 0; i < RED_THREADS / 32; ++i) {
+    for (int i = 0; i < THREADS / 32; ++i) {
       if (sp[i] != cur) {
         if (cur >= 0) atomicMax(a.dt_bits + cur, (unsigned long long)__double_as_longlong(m));
         cur = sp[i];
@@ -847,7 +859,7 @@ __global__ void __launch_bounds__(RED_THREADS) dt_kernel(const AuxArgs<real> a) 
     __shared__ int last;
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(a.dt_done, 1u) == gridDim.x - 1;
+    if (threadIdx.x == 0) last = atomicAdd(a.dt_done, 1u) == (unsigned)nblk - 1u;
     __syncthreads();
     if (last) {
       __threadfence();
@@ -861,6 +873,11 @@ __global__ void __launch_bounds__(RED_THREADS) dt_kernel(const AuxArgs<real> a) 
       if (threadIdx.x == 0) *a.dt_done = 0u;
     }
   }
+}
+
+template <typename real, int DIM, int K>
+__global__ void __launch_bounds__(RED_THREADS) dt_kernel(const AuxArgs<real> a) {
+  dt_body<real, DIM, K, RED_THREADS>(a, blockIdx.x, gridDim.x);
 }
 
 template <typename real, int DIM, int K>
@@ -1120,6 +1137,12 @@ cudaError_t launch_node_weights(const void* pa, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+}  // namespace dgi
+
+#include "dg_persist.cuh"
+
+namespace dgi {
+
 template <typename real, int DIM, int K>
 KernelSet make_kernel_set(int prec) {
   using S = Shape<DIM, K>;
@@ -1158,6 +1181,10 @@ KernelSet make_kernel_set(int prec) {
   if constexpr (std::is_same<real, float>::value && DIM == 2) {
     ks.cell_direct = &launch_cell_direct<DIM, K>;
     ks.fill_direct = &fill_direct_tables<DIM, K>;
+  }
+  if constexpr (DIM == 2) {
+    ks.persist = &launch_persist<real, DIM, K>;
+    ks.prepare_persist = &prepare_persist<real, DIM, K>;
   }
   if constexpr (std::is_same<real, float>::value && DIM == 2 && K >= 1 && K <= 3) {
     ks.cell_tc = &launch_cell_tc<K, false>;

@@ -371,16 +371,17 @@ __device__ __forceinline__ void trace_side(const StageArgs<real>& a, int cell, i
   }
 }
 
+// the work of one block (faces bid*FB ..) with FB*NV threads; the kernel
+// below and the persistent step kernel run it
 template <typename real, int DIM, int K, int FB>
-__global__ void __launch_bounds__(FB * Shape<DIM, K>::NV)
-    face_flux_kernel(const StageArgs<real> a) {
+__device__ __forceinline__ void face_flux_body(const StageArgs<real>& a, int bid) {
   using S = Shape<DIM, K>;
   constexpr int THREADS = FB * S::NV;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   real* sT = reinterpret_cast<real*>(smem_raw);  // [2 sides][NV][QF][FB]
   const int nf = a.m.nfaces;
   const int fl = threadIdx.x % FB, v = threadIdx.x / FB;
-  const int f = blockIdx.x * FB + fl;
+  const int f = bid * FB + fl;
   int dir = 0;
   if (f < nf) {
     const unsigned info = a.m.finfo[f];
@@ -415,7 +416,7 @@ __global__ void __launch_bounds__(FB * Shape<DIM, K>::NV)
   const real gamma = real(a.gamma);
   for (int item = threadIdx.x; item < FB * S::QF; item += THREADS) {
     const int ff = item % FB, q = item / FB;
-    const int f2 = blockIdx.x * FB + ff;
+    const int f2 = bid * FB + ff;
     if (f2 >= nf) continue;
     const int d2 = a.m.finfo[f2] & 3;
     real uL[S::NV], uR[S::NV], Fl[S::NV];
@@ -431,6 +432,12 @@ __global__ void __launch_bounds__(FB * Shape<DIM, K>::NV)
     for (int vv = 0; vv < S::NV; ++vv) a.F[((size_t)vv * S::QF + q) * nf + f2] = Fl[vv];
   }
   (void)dir;
+}
+
+template <typename real, int DIM, int K, int FB>
+__global__ void __launch_bounds__(FB * Shape<DIM, K>::NV)
+    face_flux_kernel(const StageArgs<real> a) {
+  face_flux_body<real, DIM, K, FB>(a, blockIdx.x);
 }
 
 // ===========================================================================
@@ -521,9 +528,10 @@ __device__ __forceinline__ void surface_from_faces(const StageArgs<real>& a, int
   }
 }
 
+// the work of one block (cells bid*TC ..) with TC*NV threads; the kernel
+// below and the persistent step kernel run it
 template <typename real, int DIM, int K, int TC, bool GRAV = false>
-__global__ void __launch_bounds__(TC * Shape<DIM, K>::NV, CellTile<real, DIM, K>::min_blocks(TC))
-    cell_update_kernel(const StageArgs<real> a) {
+__device__ __forceinline__ void cell_update_body(const StageArgs<real>& a, int bid) {
   using S = Shape<DIM, K>;
   constexpr int NV = S::NV, Q = S::Q, N = S::N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -531,7 +539,7 @@ __global__ void __launch_bounds__(TC * Shape<DIM, K>::NV, CellTile<real, DIM, K>
   real* sF = GRAV ? sU + NV * Q * TC : sU;         // [DIM][NV][Q][TC] (direction 0 over sU)
   const int tc = threadIdx.x % TC, v = threadIdx.x / TC;
   const int nc = a.m.ncells;
-  const int c = blockIdx.x * TC + tc;
+  const int c = bid * TC + tc;
   const bool valid = c < nc;
   const Tab1D<real>& T = a.t1;
   constexpr bool PF = FacePrefetch<real, DIM, K>::ON;
@@ -634,6 +642,12 @@ __global__ void __launch_bounds__(TC * Shape<DIM, K>::NV, CellTile<real, DIM, K>
       a.out[oo][idx] = val;
     }
   }
+}
+
+template <typename real, int DIM, int K, int TC, bool GRAV = false>
+__global__ void __launch_bounds__(TC * Shape<DIM, K>::NV, CellTile<real, DIM, K>::min_blocks(TC))
+    cell_update_kernel(const StageArgs<real> a) {
+  cell_update_body<real, DIM, K, TC, GRAV>(a, blockIdx.x);
 }
 
 }  // namespace dgi

@@ -26,8 +26,9 @@ EXPORTS = ["dg_default_options", "dg_create", "dg_destroy", "dg_last_error", "dg
            "dg_status", "dg_profile_begin", "dg_profile_end", "dg_totals_noalloc",
            "dg_create_batch", "dg_batch_advance", "dg_n_problems", "dg_tiles",
            "dg_limiter_counts", "dg_set_tiles", "dg_adapt_mark", "dg_adapt_set", "dg_regrid",
-           "dg_set_gravity", "dg_test_force_timeout"]
+           "dg_set_gravity", "dg_test_force_timeout", "dg_set_advance_mode", "dg_advance_mode"]
 KERNEL_KINDS = ["face", "cell", "limit", "dt", "other", "adjoint"]
+ADVANCE_MODES = {"graph": 0, "persistent": 1}
 
 
 class MeshDesc(C.Structure):
@@ -95,6 +96,8 @@ def load(path=LIB_PATH):
     L.dg_regrid.argtypes = [vp, vp, vp, vp]
     L.dg_set_gravity.argtypes = [vp, vp, vp]
     L.dg_test_force_timeout.argtypes = [vp]
+    L.dg_set_advance_mode.argtypes = [vp, C.c_int]
+    L.dg_advance_mode.argtypes = [vp, C.POINTER(C.c_int)]
     L.dg_profile_begin.argtypes = [vp]
     L.dg_profile_end.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_int]
     for name in EXPORTS:
@@ -396,6 +399,15 @@ class Solver:
         ct, ft = C.c_int(), C.c_int()
         self._check(self._L.dg_tiles(self._h, C.byref(ct), C.byref(ft)))
         return ct.value, ft.value
+
+    def set_advance_mode(self, mode):
+        """"graph" or "persistent": how advance() runs its steps (see dg_set_advance_mode)"""
+        self._check(self._L.dg_set_advance_mode(self._h, ADVANCE_MODES[mode]))
+
+    def advance_mode(self):
+        m = C.c_int()
+        self._check(self._L.dg_advance_mode(self._h, C.byref(m)))
+        return {v: k for k, v in ADVANCE_MODES.items()}[m.value]
 
     def force_timeout(self):
         """Test hook: the next tensor-core cell launch outside a graph gives up
