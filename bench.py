@@ -726,7 +726,7 @@ def run_adjoint(args):
     dJ = (grad * v).sum().item()
     res = {}
     with torch.no_grad():
-        for rel in (1e-4, 3e-5, 1e-5):
+        for rel in (1e-3, 1e-4, 1e-5):
             eps = rel * W0.abs().max().item()
             fd = (J(W0 + eps * v).item() - J(W0 - eps * v).item()) / (2 * eps)
             res["%g" % rel] = abs(fd - dJ) / abs(dJ)
@@ -740,7 +740,11 @@ def run_adjoint(args):
                       "cells": cells, "dt": dt},
            "adjoint": {"forward_ms_per_step": fwd_ms / steps, "backward_ms_per_step": bwd_ms / steps,
                        "checkpoint_bytes": steps * W0.numel() * W0.element_size(),
-                       "grad_rel_err_vs_central_fd": res, "J": val.item()}}
+                       "max_memory_allocated_bytes": torch.cuda.max_memory_allocated(),
+                       "grad_rel_err_vs_central_fd": res,
+                       "fd": "central differences of J along one seeded unit direction (rng 1506063), "
+                             "eps = rel * max|W0| for each rel",
+                       "J": val.item()}}
     print(json.dumps(out), flush=True)
     return 0
 
