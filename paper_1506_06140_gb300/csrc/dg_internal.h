@@ -41,7 +41,7 @@ struct Shape {
   static constexpr int OFF_DEG = OFF_XI1 + Q1 * 3;                     // [N]      degree of phi_l
   static constexpr int OFF_PMAX = OFF_DEG + N;                         // [N] max |phi_l| on [-1,1]^d
   static constexpr int OFF_1D = OFF_PMAX + N;                          // Tab1D (sizes of Tab1D<double>)
-  static constexpr int TAB_SIZE = OFF_1D + 92;
+  static constexpr int TAB_SIZE = OFF_1D + 124;
 };
 
 // One-dimensional tables of the tensor-product Gauss rule (k+1 <= 4 nodes),
@@ -53,6 +53,7 @@ struct Tab1D {
   real PW[4][4];     // PW[a][i] = P[a][i] w_i
   real DW[4][4];     // DW[a][i] = sqrt(2a+1) P_a'(x_i) w_i
   real PH[2][4][4];  // PH[h][a][i] = sqrt(2a+1) P_a((x_i + 2h - 1) / 2): node i of half h
+  real PWH[2][4][4]; // PWH[h][a][i] = PH[h][a][i] w_i
   real PE[2][4];     // PE[s][a] = sqrt(2a+1) P_a(2s - 1): values at -1 (s=0) and +1 (s=1)
   real W[4];         // Gauss weights w_i
 };

@@ -205,6 +205,7 @@ void fill_tables(std::vector<double>& T, const std::vector<double>& gx,
         double vh, dh;
         HostBasis<DIM, K>::sl(a, 0.5 * (gx[i] + (h ? 1.0 : -1.0)), vh, dh);
         t1.PH[h][a][i] = vh;
+        t1.PWH[h][a][i] = vh * gw[i];
       }
     }
   for (int a = 0; a <= K; ++a)
@@ -214,7 +215,7 @@ void fill_tables(std::vector<double>& T, const std::vector<double>& gx,
       t1.PE[s][a] = v;
     }
   for (int i = 0; i <= K; ++i) t1.W[i] = gw[i];
-  static_assert(sizeof(Tab1D<double>) == 92 * sizeof(double), "Tab1D layout");
+  static_assert(sizeof(Tab1D<double>) == 124 * sizeof(double), "Tab1D layout");
   std::memcpy(&T[S::OFF_1D], &t1, sizeof(t1));
 }
 

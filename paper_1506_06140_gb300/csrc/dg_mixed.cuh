@@ -246,7 +246,7 @@ __device__ __forceinline__ void surface_from_faces_mixed(const MixedArgs& x, int
     const float dv = SS ? 0.0f : x.D[(size_t)v * nf + e0];
 #pragma unroll
     for (int q = 0; q < S::QF; ++q) fq[q] = x.G[((size_t)v * S::QF + q) * nf + e0] + dv;
-    surface_side<float, DIM, K, DIR, SS>(x.t, x.t.P, x.t.P, fq, 1.0f, acc);
+    surface_side<float, DIM, K, DIR, SS>(x.t, x.t.PW, x.t.PW, fq, 1.0f, acc);
   } else {
     const float sub = 1.0f / (float)S::NSUB;
 #pragma unroll
@@ -254,7 +254,7 @@ __device__ __forceinline__ void surface_from_faces_mixed(const MixedArgs& x, int
       const float dv = SS ? 0.0f : x.D[(size_t)v * nf + e0 + h];
 #pragma unroll
       for (int q = 0; q < S::QF; ++q) fq[q] = x.G[((size_t)v * S::QF + q) * nf + e0 + h] + dv;
-      surface_side<float, DIM, K, DIR, SS>(x.t, x.t.PH[h & 1], x.t.PH[(h >> 1) & 1], fq, sub, acc);
+      surface_side<float, DIM, K, DIR, SS>(x.t, x.t.PWH[h & 1], x.t.PWH[(h >> 1) & 1], fq, sub, acc);
     }
   }
 }
@@ -358,36 +358,52 @@ __global__ void __launch_bounds__(TC * Shape<DIM, K>::NV)
   const int pb = cell_problem(a.m, c);
   const double pre = a.pre_prob ? a.pre_prob[pb] : a.pre[a.m.level[c]];
   const double dtv = a.dt ? a.dt[pb] : 1.0;
+  const size_t i0 = (size_t)(v * N) * nc + c;
   if (x.delta) {
     // delta registers: R_out = sum_r C_r R_r + ck dt dW/dt in FP32 (the
     // coefficients of a stage state sum to one, so W drops out); the last
-    // stage adds that increment to W in FP64
+    // stage adds that increment to W in FP64.  The terms are added in that
+    // order; the loop over the inputs runs outside the coefficient loop.
     const float sc = x.ckf * f32_round(dtv * pre);
+    float val[N];
 #pragma unroll
-    for (int j = 0; j < N; ++j) {
-      const size_t idx = (size_t)(v * N + j) * nc + c;
-      float val = sc * acc[j];
-      for (int r = 0; r < x.n_inR; ++r) val += x.Cf[r] * x.inR[r][idx];
-      if (x.outR) x.outR[idx] = val;
-      else a.out[0][idx] = a.U[idx] + f64_exact(val);
+    for (int j = 0; j < N; ++j) val[j] = sc * acc[j];
+#pragma unroll
+    for (int r = 0; r < MAX_IN; ++r) {
+      if (r >= x.n_inR) break;
+      const float cr = x.Cf[r];
+      const float* src = x.inR[r];
+#pragma unroll
+      for (int j = 0; j < N; ++j) val[j] += cr * src[i0 + (size_t)j * nc];
+    }
+    if (x.outR) {
+#pragma unroll
+      for (int j = 0; j < N; ++j) x.outR[i0 + (size_t)j * nc] = val[j];
+    } else {
+#pragma unroll
+      for (int j = 0; j < N; ++j) a.out[0][i0 + (size_t)j * nc] = a.U[i0 + (size_t)j * nc] + f64_exact(val[j]);
     }
     return;
   }
-  // FP64 registers: out_o = sum_r C[o][r] in_r + ck[o] dt pre acc
-  const int n_out = a.n_out, n_in = a.n_in;
+  // FP64 registers: out_o = ck[o] dt pre acc + sum_r C[o][r] in_r, in that order
 #pragma unroll
-  for (int j = 0; j < N; ++j) {
-    const double rhs = pre * f64_exact(acc[j]);
-    const size_t idx = (size_t)(v * N + j) * nc + c;
-    for (int oo = 0; oo < n_out; ++oo) {
-      double val = a.ck[oo] * dtv * rhs;
-      for (int r = 0; r < n_in; ++r) {
-        const double cr = a.C[oo][r];
-        if (cr == 0.0) continue;
-        val += cr * a.in[r][idx];
-      }
-      a.out[oo][idx] = val;
+  for (int oo = 0; oo < MAX_OUT; ++oo) {
+    if (oo >= a.n_out) break;
+    const double ckv = a.ck[oo] * dtv;
+    double val[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) val[j] = ckv * (pre * f64_exact(acc[j]));
+#pragma unroll
+    for (int r = 0; r < MAX_IN; ++r) {
+      if (r >= a.n_in) break;
+      const double cr = a.C[oo][r];
+      if (cr == 0.0) continue;
+      const double* src = a.in[r];
+#pragma unroll
+      for (int j = 0; j < N; ++j) val[j] += cr * src[i0 + (size_t)j * nc];
     }
+#pragma unroll
+    for (int j = 0; j < N; ++j) a.out[oo][i0 + (size_t)j * nc] = val[j];
   }
 }
 

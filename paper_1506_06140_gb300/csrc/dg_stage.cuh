@@ -218,13 +218,14 @@ __device__ __forceinline__ void source_project(const Tab1D<real>& T, const real*
 
 // surface integral of one variable over side (DIR, S) of the cell:
 // acc_l -= sg * sum_q fbar_q phi_l(face point q) w_q, with the face's points
-// given in PT0 (and PT1) -- the Gauss nodes, or a half of them for sub-faces.
+// given by the weighted tables PW0 (and PW1): PW[e][q] = P_e(x_q) w_q at the
+// Gauss nodes (T.PW), or at a half of them for sub-faces (T.PWH[h]).
 template <typename real, int DIM, int K, int DIR, int S>
-__device__ __forceinline__ void surface_side(const Tab1D<real>& T, const real (&PT0)[4][4],
-                                             const real (&PT1)[4][4], const real* fq, real scale,
+__device__ __forceinline__ void surface_side(const Tab1D<real>& T, const real (&PW0)[4][4],
+                                             const real (&PW1)[4][4], const real* fq, real scale,
                                              real* acc) {
   constexpr int K1 = K + 1;
-  const real sg = S ? real(-1) : real(1);  // minus the outward normal's sign
+  const real ssg = S ? -scale : scale;  // times minus the outward normal's sign
   if constexpr (DIM == 2) {
     constexpr int TA = DIR == 0 ? 1 : 0;
     real G[K1];
@@ -232,8 +233,8 @@ __device__ __forceinline__ void surface_side(const Tab1D<real>& T, const real (&
     for (int e = 0; e <= K; ++e) {
       real s = real(0);
 #pragma unroll
-      for (int q = 0; q < K1; ++q) s += fq[q] * T.W[q] * PT0[e][q];
-      G[e] = s * scale * sg;
+      for (int q = 0; q < K1; ++q) s += fq[q] * PW0[e][q];
+      G[e] = s * ssg;
     }
 #pragma unroll
     for (int ed = 0; ed <= K; ++ed)
@@ -250,7 +251,7 @@ __device__ __forceinline__ void surface_side(const Tab1D<real>& T, const real (&
       for (int qb = 0; qb < K1; ++qb) {
         real s = real(0);
 #pragma unroll
-        for (int qa = 0; qa < K1; ++qa) s += fq[qa + K1 * qb] * T.W[qa] * PT0[ea][qa];
+        for (int qa = 0; qa < K1; ++qa) s += fq[qa + K1 * qb] * PW0[ea][qa];
         H[ea][qb] = s;
       }
 #pragma unroll
@@ -259,8 +260,8 @@ __device__ __forceinline__ void surface_side(const Tab1D<real>& T, const real (&
       for (int eb = 0; eb <= K - ea; ++eb) {
         real s = real(0);
 #pragma unroll
-        for (int qb = 0; qb < K1; ++qb) s += H[ea][qb] * T.W[qb] * PT1[eb][qb];
-        s *= scale * sg;
+        for (int qb = 0; qb < K1; ++qb) s += H[ea][qb] * PW1[eb][qb];
+        s *= ssg;
 #pragma unroll
         for (int ed = 0; ed <= K - ea - eb; ++ed) {
           int e[3];
@@ -514,7 +515,7 @@ __device__ __forceinline__ void surface_from_faces(const StageArgs<real>& a, int
 #pragma unroll
       for (int q = 0; q < S::QF; ++q) fq[q] = a.F[((size_t)v * S::QF + q) * nf + e0];
     }
-    surface_side<real, DIM, K, DIR, SS>(T, T.P, T.P, fq, real(1), acc);
+    surface_side<real, DIM, K, DIR, SS>(T, T.PW, T.PW, fq, real(1), acc);
   } else {
     const int e0 = a.m.sface[(size_t)SD * nc + c];
     // coarse side of a hanging face: NSUB sub-faces in quadrant order
@@ -523,7 +524,7 @@ __device__ __forceinline__ void surface_from_faces(const StageArgs<real>& a, int
     for (int h = 0; h < S::NSUB; ++h) {
 #pragma unroll
       for (int q = 0; q < S::QF; ++q) fq[q] = a.F[((size_t)v * S::QF + q) * nf + e0 + h];
-      surface_side<real, DIM, K, DIR, SS>(T, T.PH[h & 1], T.PH[(h >> 1) & 1], fq, sub, acc);
+      surface_side<real, DIM, K, DIR, SS>(T, T.PWH[h & 1], T.PWH[(h >> 1) & 1], fq, sub, acc);
     }
   }
 }
@@ -628,19 +629,34 @@ __device__ __forceinline__ void cell_update_body(const StageArgs<real>& a, int b
     }
   }
   const real sc = pre * (a.dt ? real(a.dt[pb]) : real(1));
-  const int n_out = a.n_out, n_in = a.n_in;
+  // out_o = ck_o dt pre acc + sum_r C[o][r] in_r, the terms added in that
+  // order; the stage-program loops run outside the coefficient loop, so each
+  // coefficient costs one load and one FMA per input
+  const size_t i0 = (size_t)(v * N) * nc + c;
 #pragma unroll
-  for (int j = 0; j < N; ++j) {
-    const size_t idx = (size_t)(v * N + j) * nc + c;
-    for (int oo = 0; oo < n_out; ++oo) {
-      real val = (a.ck[oo] * sc) * acc[j];
-      for (int r = 0; r < n_in; ++r) {
-        const real cr = a.C[oo][r];
-        if (cr == real(0)) continue;
-        val += cr * ((a.in[r] == a.U) ? w[j] : a.in[r][idx]);
+  for (int oo = 0; oo < MAX_OUT; ++oo) {
+    if (oo >= a.n_out) break;
+    const real ckv = a.ck[oo] * sc;
+    real val[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) val[j] = ckv * acc[j];
+#pragma unroll
+    for (int r = 0; r < MAX_IN; ++r) {
+      if (r >= a.n_in) break;
+      const real cr = a.C[oo][r];
+      if (cr == real(0)) continue;
+      const real* src = a.in[r];
+      if (src == a.U) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) val[j] += cr * w[j];
+      } else {
+#pragma unroll
+        for (int j = 0; j < N; ++j) val[j] += cr * src[i0 + (size_t)j * nc];
       }
-      a.out[oo][idx] = val;
     }
+    real* dst = a.out[oo];
+#pragma unroll
+    for (int j = 0; j < N; ++j) dst[i0 + (size_t)j * nc] = val[j];
   }
 }
 
