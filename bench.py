@@ -623,12 +623,10 @@ def summarize(args, results, world):
         esize = 8 if precision in ("fp64", "mixed", "mixed_tc") else 4
         kname = {"cell": "cell_update_kernel", "face": "face_flux_kernel",
                  "limit": "limit_kernel"}.get(kind, kind)
-        if precision == "fp32_tc" and kind == "cell":
-            kname = "cell_update_tc_kernel"
         if precision in ("mixed", "mixed_tc") and kind in ("cell", "face"):
             kname = kind == "cell" and "cell_update_mixed_kernel" or "face_flux_mixed_kernel"
-            if precision == "mixed_tc" and kind == "cell":
-                kname = "cell_update_tc_mixed_kernel"
+        if precision in ("fp32_tc", "mixed_tc") and kind == "cell":
+            kname = "cell_tc_kernel"
         tag = "%s_%s" % (wk["tag"], precision)
         if precision == "fp64" and kind in ("cell", "face"):
             fc, ff = kernel_flops(dim, k)
