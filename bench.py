@@ -657,6 +657,16 @@ def summarize(args, results, world):
                     "traffic": dram_traffic(kname, tag), "algorithmic_per_launch": byt,
                     "algorithmic_unit": "bytes (FP64 state + 2 FP32 delta registers per stage)"
                     if precision in ("mixed", "mixed_tc") else "bytes (3 state arrays per stage)"}
+        if roof["unit"] == "GB/s" or "hbm" in roof:
+            # the whole stage against the HBM roof: algorithmic bytes of one
+            # stage over the measured time per stage (every kernel and gap)
+            byt_stage = 3 * state_bytes_per_cell(dim, k, esize) * cells
+            if precision in ("mixed", "mixed_tc"):
+                byt_stage = (state_bytes_per_cell(dim, k, 8) + 2 * state_bytes_per_cell(dim, k, 4)) * cells
+            t_stage = r["ms"] / args.steps / stages * 1e-3
+            roof["stage"] = {"achieved": byt_stage / t_stage / 1e9, "peak": hbm, "unit": "GB/s",
+                             "frac": byt_stage / t_stage / 1e9 / hbm,
+                             "note": "algorithmic bytes of a stage over the time per stage of the timed steps"}
         e2e_value = dof_updates / (r["ms_e2e"] * 1e-3)
         lines[precision] = {
             "value": value, "ms_per_step": r["ms"] / args.steps, "roofline": roof,
