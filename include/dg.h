@@ -142,16 +142,24 @@ int dg_limiter_counts(dg_handle* h, int64_t* counts_dev, int reset, void* stream
 /* Tiles of the stage kernels in use: cells per thread block of the cell
  * kernel and faces per block of the face kernel (the fixed defaults, or the
  * autotuner's choice when dg_options.autotune was set).  A tensor-core cell
- * kernel (DG_FP32_TC) reports its fixed 32 cells; 1 means the one-thread-per-
- * cell FP32 kernel, which the autotuner also considers.  Host outputs. */
+ * kernel (DG_FP32_TC) reports its fixed 32 cells; cell tile 1 means the one-
+ * thread-per-cell FP32 kernel, which the autotuner also considers; face tile
+ * 0 means the fused face + cell kernel (tiles of 8 x 4 cells computing their
+ * own faces, no separate face kernel).  Host outputs. */
 int dg_tiles(const dg_handle* h, int* cell_tile, int* face_tile);
 
 /* Sets the tiles by hand (the autotuner's choices can be overridden):
  * cell_tile 16, 32 or 64 cells per block of the tiled cell kernel, or 1 for
  * the one-thread-per-cell kernel (FP32 2D handles only); face_tile 16, 32 or
- * 64.  DG_ERR_ARG for other values,
- * DG_ERR_UNSUPPORTED where the (dim, k, precision) has no such kernel.  Not
- * to be called while another call on the handle is being captured. */
+ * 64, or 0 for the fused face + cell kernel: each block takes a tile of 8 x 4
+ * cells, computes the fluxes of the tile's faces in shared memory (the
+ * neighbours' traces across the tile's edges from their weights) and then
+ * the cell update -- one launch per stage and no face-flux array, with the
+ * same results to rounding (single 2D uniform meshes, FP64 or FP32 state,
+ * not with cell_tile 1; the cell tile value is then unused).  DG_ERR_ARG for
+ * other values, DG_ERR_UNSUPPORTED where the (dim, k, precision, mesh) has
+ * no such kernel.  Not to be called while another call on the handle is
+ * being captured. */
 int dg_set_tiles(dg_handle* h, int cell_tile, int face_tile);
 
 /* Sizes: cells, basis functions N(k) (eq. nof_basis_functions and its 2D

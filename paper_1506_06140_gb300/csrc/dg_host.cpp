@@ -417,6 +417,7 @@ struct dg_handle {
   float* Wlo = nullptr;      //             and the rest of weight 0 [NV][ncells]
   int cell_tile = 0, face_tile = 0;  // stage-kernel tiles (0: the kernels' defaults)
   bool use_direct = false;   // one-thread-per-cell FP32 cell kernel
+  bool use_fused = false;    // fused face + cell kernel (face tile 0)
   std::vector<unsigned char> dtab;  // its tables (host copy, passed by value at launch)
   void* tcB = nullptr;       // its B operands
   double* scal = nullptr;    // dt per problem [nprob]
@@ -944,6 +945,11 @@ int stage_launch(dg_handle* h, const StageArgs<real>& a, cudaStream_t s, const O
                        [&] { return h->use_tc ? h->ms->cell_tc(&x, s) : h->ms->cell(&x, s); }));
       return DG_OK;
     }
+  }
+  if (h->use_fused && !h->use_tc && !h->use_direct && !h->accel && h->nnodes == 0 && h->nprob == 1) {
+    // faces computed inside the cell kernel's tiles: one launch per stage
+    DG_CUDA(h, timed(h, DG_KERNEL_CELL, s, [&] { return h->ks->stage_fused(&a, s); }));
+    return DG_OK;
   }
   DG_CUDA(h, timed(h, DG_KERNEL_FACE, s, [&] { return h->ks->face(&a, s); }));
   DG_CUDA(h, timed(h, DG_KERNEL_CELL, s, [&] { return cell_launch(h, &a, s); }));
@@ -1597,6 +1603,8 @@ static int create_impl(const dg_mesh_desc* mesh, int nprob, int k, double gamma,
     h->bar = static_cast<unsigned*>(p);
     if (ks->prepare_persist() != cudaSuccess) return bail(cuda_fail(h, cudaGetLastError(), "kernel attributes"));
   }
+  if (ks->prepare_fused && !h->ms && !h->use_tc && ks->prepare_fused() != cudaSuccess)
+    return bail(cuda_fail(h, cudaGetLastError(), "kernel attributes"));
   *out = h;
   return DG_OK;
 }
@@ -1698,8 +1706,15 @@ int dg_set_tiles(dg_handle* h, int cell_tile, int face_tile) {
   if (!check_handle(h)) return DG_ERR_ARG;
   const int cmax = h->ms ? h->ms->cell_tile_max : h->ks->cell_tile_max;
   const int fmax = h->ms ? h->ms->face_tile_max : h->ks->face_tile_max;
-  if (face_tile != 16 && face_tile != 32 && face_tile != 64) return fail(h, DG_ERR_ARG, "dg_set_tiles: face tile");
-  if (face_tile > fmax) return fail(h, DG_ERR_UNSUPPORTED, "dg_set_tiles: face tile too large for (dim, k)");
+  if (face_tile == 0) {
+    if (!h->ks->stage_fused || h->ms || h->use_tc || h->nnodes > 0 || h->nprob != 1 || cell_tile == 1)
+      return fail(h, DG_ERR_UNSUPPORTED,
+                  "dg_set_tiles: the fused face + cell kernel needs a single 2D uniform mesh with an FP64 or "
+                  "FP32 state and the CUDA-core cell kernel");
+  } else {
+    if (face_tile != 16 && face_tile != 32 && face_tile != 64) return fail(h, DG_ERR_ARG, "dg_set_tiles: face tile");
+    if (face_tile > fmax) return fail(h, DG_ERR_UNSUPPORTED, "dg_set_tiles: face tile too large for (dim, k)");
+  }
   if (cell_tile == 1) {
     if (h->use_tc || h->dtab.empty())
       return fail(h, DG_ERR_UNSUPPORTED, "dg_set_tiles: one thread per cell needs an FP32 2D handle");
@@ -1708,7 +1723,8 @@ int dg_set_tiles(dg_handle* h, int cell_tile, int face_tile) {
     if (cell_tile > cmax) return fail(h, DG_ERR_UNSUPPORTED, "dg_set_tiles: cell tile too large for (dim, k)");
   }
   std::lock_guard<std::mutex> lock(h->mu);
-  h->face_tile = face_tile;
+  h->use_fused = face_tile == 0;
+  if (face_tile != 0) h->face_tile = face_tile;
   h->use_direct = cell_tile == 1;
   if (cell_tile != 1) h->cell_tile = cell_tile;
   // cached step graphs hold the old launch configuration: record them anew
@@ -1718,8 +1734,8 @@ int dg_set_tiles(dg_handle* h, int cell_tile, int face_tile) {
 
 int dg_tiles(const dg_handle* h, int* cell_tile, int* face_tile) {
   if (!check_handle(h) || !cell_tile || !face_tile) return DG_ERR_ARG;
-  *cell_tile = h->use_tc ? 32 : (h->use_direct ? 1 : h->cell_tile);
-  *face_tile = h->face_tile;
+  *cell_tile = h->use_tc ? 32 : (h->use_direct ? 1 : (h->use_fused ? 32 : h->cell_tile));
+  *face_tile = h->use_fused ? 0 : h->face_tile;
   return DG_OK;
 }
 

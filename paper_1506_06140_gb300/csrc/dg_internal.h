@@ -271,6 +271,9 @@ struct KernelSet {
   cudaError_t (*cell_tc)(const void* stage_args, cudaStream_t s) = nullptr;
   cudaError_t (*prepare_tc)() = nullptr;
   void (*fill_tc)(const std::vector<double>& tab, std::vector<float>& out) = nullptr;
+  // fused face + cell kernel (2D uniform meshes), nullptr where not built
+  cudaError_t (*stage_fused)(const void* stage_args, cudaStream_t s) = nullptr;
+  cudaError_t (*prepare_fused)() = nullptr;
   // persistent whole-step kernel (2D), nullptr where not built: n_steps steps
   // of the plan (a PersistPlan<real> in device memory) in one cooperative
   // launch of at most max_phase_blocks blocks; bar: 3 zeroed words

@@ -610,7 +610,7 @@ __device__ __forceinline__ void limit_body(const LimitArgs<real>& a, int bid) {
 }
 
 template <typename real, int DIM, int K>
-__global__ void __launch_bounds__(128) limit_kernel(const LimitArgs<real> a) {
+__global__ void __launch_bounds__(128, sizeof(real) == 4 && DIM == 3 ? 4 : 1) limit_kernel(const LimitArgs<real> a) {
   limit_body<real, DIM, K>(a, blockIdx.x);
 }
 
@@ -1140,6 +1140,7 @@ cudaError_t launch_node_weights(const void* pa, cudaStream_t s) {
 
 }  // namespace dgi
 
+#include "dg_fused.cuh"
 #include "dg_persist.cuh"
 
 namespace dgi {
@@ -1186,6 +1187,8 @@ KernelSet make_kernel_set(int prec) {
   if constexpr (DIM == 2) {
     ks.persist = &launch_persist<real, DIM, K>;
     ks.prepare_persist = &prepare_persist<real, DIM, K>;
+    ks.stage_fused = &launch_stage_fused<real, K>;
+    ks.prepare_fused = &prepare_stage_fused<real, K>;
   }
   if constexpr (std::is_same<real, float>::value && DIM == 2 && K >= 1 && K <= 3) {
     ks.cell_tc = &launch_cell_tc<K, false>;

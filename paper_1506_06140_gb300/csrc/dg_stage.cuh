@@ -529,6 +529,42 @@ __device__ __forceinline__ void surface_from_faces(const StageArgs<real>& a, int
   }
 }
 
+// out_o = ck_o sc acc + sum_r C[o][r] in_r for the weights of variable v of
+// cell c (sc = dt * 2^(1-d)/dx), the terms added in that order; the
+// stage-program loops run outside the coefficient loop, so each coefficient
+// costs one load and one FMA per input; w: the cell's weights of U
+template <typename real, int N>
+__device__ __forceinline__ void stage_epilogue(const StageArgs<real>& a, int c, int v, real sc, const real* acc,
+                                               const real* w) {
+  const int nc = a.m.ncells;
+  const size_t i0 = (size_t)(v * N) * nc + c;
+#pragma unroll
+  for (int oo = 0; oo < MAX_OUT; ++oo) {
+    if (oo >= a.n_out) break;
+    const real ckv = a.ck[oo] * sc;
+    real val[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) val[j] = ckv * acc[j];
+#pragma unroll
+    for (int r = 0; r < MAX_IN; ++r) {
+      if (r >= a.n_in) break;
+      const real cr = a.C[oo][r];
+      if (cr == real(0)) continue;
+      const real* src = a.in[r];
+      if (src == a.U) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) val[j] += cr * w[j];
+      } else {
+#pragma unroll
+        for (int j = 0; j < N; ++j) val[j] += cr * src[i0 + (size_t)j * nc];
+      }
+    }
+    real* dst = a.out[oo];
+#pragma unroll
+    for (int j = 0; j < N; ++j) dst[i0 + (size_t)j * nc] = val[j];
+  }
+}
+
 // the work of one block (cells bid*TC ..) with TC*NV threads; the kernel
 // below and the persistent step kernel run it
 template <typename real, int DIM, int K, int TC, bool GRAV = false>
@@ -628,36 +664,7 @@ __device__ __forceinline__ void cell_update_body(const StageArgs<real>& a, int b
       source_project<real, DIM, K>(T, sq, real(1) / (real(1 << DIM) * pre), acc);
     }
   }
-  const real sc = pre * (a.dt ? real(a.dt[pb]) : real(1));
-  // out_o = ck_o dt pre acc + sum_r C[o][r] in_r, the terms added in that
-  // order; the stage-program loops run outside the coefficient loop, so each
-  // coefficient costs one load and one FMA per input
-  const size_t i0 = (size_t)(v * N) * nc + c;
-#pragma unroll
-  for (int oo = 0; oo < MAX_OUT; ++oo) {
-    if (oo >= a.n_out) break;
-    const real ckv = a.ck[oo] * sc;
-    real val[N];
-#pragma unroll
-    for (int j = 0; j < N; ++j) val[j] = ckv * acc[j];
-#pragma unroll
-    for (int r = 0; r < MAX_IN; ++r) {
-      if (r >= a.n_in) break;
-      const real cr = a.C[oo][r];
-      if (cr == real(0)) continue;
-      const real* src = a.in[r];
-      if (src == a.U) {
-#pragma unroll
-        for (int j = 0; j < N; ++j) val[j] += cr * w[j];
-      } else {
-#pragma unroll
-        for (int j = 0; j < N; ++j) val[j] += cr * src[i0 + (size_t)j * nc];
-      }
-    }
-    real* dst = a.out[oo];
-#pragma unroll
-    for (int j = 0; j < N; ++j) dst[i0 + (size_t)j * nc] = val[j];
-  }
+  stage_epilogue<real, N>(a, c, v, pre * (a.dt ? real(a.dt[pb]) : real(1)), acc, w);
 }
 
 template <typename real, int DIM, int K, int TC, bool GRAV = false>

@@ -391,7 +391,8 @@ class Solver:
         return out
 
     def set_tiles(self, cell_tile, face_tile):
-        """cell_tile 16/32/64 (or 1: one thread per cell, FP32 2D), face_tile 16/32/64"""
+        """cell_tile 16/32/64 (or 1: one thread per cell, FP32 2D), face_tile 16/32/64
+        (or 0: the fused face + cell kernel, single 2D uniform meshes)"""
         self._check(self._L.dg_set_tiles(self._h, int(cell_tile), int(face_tile)))
 
     def tiles(self):
