@@ -22,7 +22,7 @@ typedef struct orc_problem orc_problem;
 orc_problem* orc_create(int dim, const int* n, const double* lo, const double* hi, const int* bc,
                         int n_boxes, const int* boxes, int k, double gamma, int rk_order,
                         double cfl, int limiter, double beta, double Mtilde, int positivity,
-                        double eps);
+                        double eps, int tensor);
 void orc_destroy(orc_problem* p);
 const char* orc_last_error(void);
 
@@ -75,6 +75,9 @@ void orc_gauss_legendre(int n, double* x, double* w);
 void orc_gauss_lobatto(int n, double* x, double* w);
 void orc_legendre(int n, double x, double* P, double* dP);
 void orc_basis_exponents(int dim, int k, int* e); /* [N][3] */
+/* the same for the tensor-product basis Q_k ((k+1)^dim functions) */
+void orc_basis_exponents_tensor(int dim, int k, int* e);
+double orc_basis_phi_tensor(int dim, int k, int l, const double* xi);
 double orc_basis_phi(int dim, int k, int l, const double* xi);
 double orc_basis_dphi(int dim, int k, int l, int a, const double* xi);
 void orc_refinement_matrix(int dim, int k, int child, double* P); /* [N][N], (j,l) */

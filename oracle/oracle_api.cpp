@@ -20,7 +20,7 @@ const char* orc_last_error(void) { return g_err.c_str(); }
 orc_problem* orc_create(int dim, const int* n, const double* lo, const double* hi, const int* bc,
                         int n_boxes, const int* boxes, int k, double gamma, int rk_order,
                         double cfl, int limiter, double beta, double Mtilde, int positivity,
-                        double eps) {
+                        double eps, int tensor) {
   try {
     if (dim != 2 && dim != 3) throw std::runtime_error("dim must be 2 or 3");
     if (k < 0 || k > 6) throw std::runtime_error("k must be 0..6");
@@ -36,6 +36,7 @@ orc_problem* orc_create(int dim, const int* n, const double* lo, const double* h
     P.Mtilde = Mtilde;
     P.positivity = positivity;
     P.eps = eps;
+    P.tensor = tensor != 0;
     P.mesh.build(dim, n, lo, hi, bc, n_boxes, boxes);
     P.setup();
     return o;
@@ -132,6 +133,12 @@ void orc_basis_exponents(int dim, int k, int* e) {
   for (int l = 0; l < b.N; ++l)
     for (int a = 0; a < 3; ++a) e[l * 3 + a] = b.e[l][a];
 }
+void orc_basis_exponents_tensor(int dim, int k, int* e) {
+  const orc::Basis B(dim, k, true);
+  for (int l = 0; l < B.N; ++l)
+    for (int a = 0; a < 3; ++a) e[3 * l + a] = B.e[l][a];
+}
+double orc_basis_phi_tensor(int dim, int k, int l, const double* xi) { return orc::Basis(dim, k, true).phi(l, xi); }
 double orc_basis_phi(int dim, int k, int l, const double* xi) { return orc::Basis(dim, k).phi(l, xi); }
 double orc_basis_dphi(int dim, int k, int l, int a, const double* xi) {
   return orc::Basis(dim, k).dphi(l, a, xi);

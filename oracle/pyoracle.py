@@ -27,7 +27,7 @@ def lib():
         L.orc_create.restype = C.c_void_p
         L.orc_create.argtypes = [C.c_int, _I, _D, _D, _I, C.c_int, _I, C.c_int, C.c_double,
                                  C.c_int, C.c_double, C.c_int, C.c_double, C.c_double, C.c_int,
-                                 C.c_double]
+                                 C.c_double, C.c_int]
         L.orc_destroy.argtypes = [C.c_void_p]
         L.orc_last_error.restype = C.c_char_p
         for name in ("orc_n_cells",):
@@ -68,6 +68,9 @@ def lib():
         L.orc_gauss_lobatto.argtypes = [C.c_int, _D, _D]
         L.orc_legendre.argtypes = [C.c_int, C.c_double, _D, _D]
         L.orc_basis_exponents.argtypes = [C.c_int, C.c_int, _I]
+        L.orc_basis_exponents_tensor.argtypes = [C.c_int, C.c_int, _I]
+        L.orc_basis_phi_tensor.restype = C.c_double
+        L.orc_basis_phi_tensor.argtypes = [C.c_int, C.c_int, C.c_int, _D]
         L.orc_basis_phi.restype = C.c_double
         L.orc_basis_phi.argtypes = [C.c_int, C.c_int, C.c_int, _D]
         L.orc_basis_dphi.restype = C.c_double
@@ -101,7 +104,9 @@ class Oracle:
     """One DG problem on the CPU oracle."""
 
     def __init__(self, dim, n, lo, hi, k, gamma=1.4, bc=None, refine_boxes=(), rk_order=2,
-                 cfl=0.2, limiter=LIM_NONE, beta=1.0, Mtilde=0.5, positivity=False, eps=1e-10):
+                 cfl=0.2, limiter=LIM_NONE, beta=1.0, Mtilde=0.5, positivity=False, eps=1e-10,
+                 basis="total"):
+        """basis: "total" (total degree <= k, the paper's) or "tensor" (Q_k)"""
         L = lib()
         self.dim, self.k, self.gamma = dim, k, gamma
         n3 = (C.c_int * 3)(*(list(n) + [1] * (3 - len(n))))
@@ -112,8 +117,11 @@ class Oracle:
         boxes = np.ascontiguousarray(np.array(refine_boxes, dtype=np.int32).reshape(-1))
         nb = len(refine_boxes)
         bptr = boxes.ctypes.data_as(_I) if nb else None
+        if basis not in ("total", "tensor"):
+            raise ValueError("basis: 'total' or 'tensor'")
         self._h = L.orc_create(dim, n3, lo3, hi3, bc3, nb, bptr, k, gamma, rk_order, cfl,
-                               limiter, beta, Mtilde, int(bool(positivity)), eps)
+                               limiter, beta, Mtilde, int(bool(positivity)), eps,
+                               int(basis == "tensor"))
         if not self._h:
             raise ValueError(L.orc_last_error().decode())
         self.n_cells = L.orc_n_cells(self._h)
@@ -293,6 +301,17 @@ def basis_exponents(dim, k):
     e = np.zeros((N, 3), np.int32)
     lib().orc_basis_exponents(dim, k, e.ctypes.data_as(_I))
     return e
+
+
+def basis_exponents_tensor(dim, k):
+    e = np.zeros(((k + 1) ** dim, 3), np.int32)
+    lib().orc_basis_exponents_tensor(dim, k, e.ctypes.data_as(_I))
+    return e
+
+
+def basis_phi_tensor(dim, k, l, xi):
+    x = _f64(list(xi) + [0.0] * (3 - len(xi)))
+    return lib().orc_basis_phi_tensor(dim, k, l, _d(x))
 
 
 def basis_phi(dim, k, l, xi):

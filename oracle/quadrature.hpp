@@ -108,16 +108,29 @@ inline void gauss_lobatto(int n, std::vector<double>& x, std::vector<double>& w)
 // y exponent descending.
 struct Basis {
   int dim = 0, k = 0, N = 0;
+  bool tensor = false;
   std::vector<std::array<int, 3>> e;
 
   Basis() = default;
-  Basis(int dim_, int k_) : dim(dim_), k(k_) {
-    for (int g = 0; g <= k; ++g) {
+  // total degree <= k (the paper's basis, eq. set_basis_functions), or, with
+  // tensor set, every exponent <= k (the tensor-product space Q_k).  Either
+  // way the order is by total degree, then the x exponent descending, then
+  // the y exponent descending, so phi_1 = 1 and phi_2.. phi_(1+dim) are the
+  // linear functions x, y (, z).
+  Basis(int dim_, int k_, bool tensor_ = false) : dim(dim_), k(k_), tensor(tensor_) {
+    const int gmax = tensor ? dim * k : k;
+    for (int g = 0; g <= gmax; ++g) {
       if (dim == 2) {
-        for (int nx = g; nx >= 0; --nx) e.push_back({nx, g - nx, 0});
+        for (int nx = g; nx >= 0; --nx) {
+          const int ny = g - nx;
+          if (nx <= k && ny <= k) e.push_back({nx, ny, 0});
+        }
       } else {
         for (int nx = g; nx >= 0; --nx)
-          for (int ny = g - nx; ny >= 0; --ny) e.push_back({nx, ny, g - nx - ny});
+          for (int ny = g - nx; ny >= 0; --ny) {
+            const int nz = g - nx - ny;
+            if (nx <= k && ny <= k && nz <= k) e.push_back({nx, ny, nz});
+          }
       }
     }
     N = (int)e.size();

@@ -97,6 +97,7 @@ struct Problem {
   double cfl = 0.2;
   int limiter = LIM_NONE;
   int threads = 1;               // OpenMP threads of rk_step's right-hand side (gather form if > 1)
+  bool tensor = false;           // tensor-product basis Q_k instead of the total-degree basis
   double beta = 1.0, Mtilde = 0.5;
   int positivity = 0;
   double eps = 1e-10;
@@ -152,7 +153,7 @@ struct Problem {
   }
 
   void setup() {
-    basis = Basis(dim, k);
+    basis = Basis(dim, k, tensor);
     N = basis.N;
     nv = dim + 2;
     gauss_legendre(k + 1, gx, gw);
