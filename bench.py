@@ -41,6 +41,11 @@ WORKLOADS = {
              "SSP-RK4 (5 stages), no limiter, CFL 0.2",
         dim=2, k=3, rk=4, stages=5, limiter="none", positivity=False,
         precisions=("fp64", "fp32", "fp32_tc", "mixed", "mixed_tc"), tag="vortex256_k3"),
+    "vortex_tensor": dict(
+        name="isentropic vortex 2D, 256x256 periodic [-5,5]^2, k=3 with the tensor-product basis Q_3 "
+             "(16 coeffs/cell/var), SSP-RK4 (5 stages), no limiter, CFL 0.2",
+        dim=2, k=3, rk=4, stages=5, limiter="none", positivity=False, precisions=("fp64", "fp32"),
+        tag="vortex256_k3_tensor", basis="tensor"),
     "ensemble": dict(
         name="512 independent isentropic vortices (strength U(3,6)) on periodic [-5,5]^2 with "
              "sizes drawn from {32,48,64,96,128}^2 (3.4M cells), k=2 (6 coeffs/cell/var), SSP-RK3, "
@@ -109,7 +114,7 @@ def make_problem(wk, precision, autotune=None):
     from paper_1506_06140_gb300 import dg
     from paper_1506_06140_gb300 import workloads as wl
     W = WORKLOADS[wk]
-    if wk == "vortex":
+    if wk in ("vortex", "vortex_tensor"):
         m, ic = mesh(), wl.vortex
     elif wk == "wave2d":
         m, ic = wl.mesh_uniform(2, [32, 32], [0.0, 0.0], [1.0, 1.0]), wl.wave2d
@@ -129,7 +134,8 @@ def make_problem(wk, precision, autotune=None):
     if autotune is None:
         autotune = W.get("autotune", False)
     s = dg.Solver(m, W["k"], W.get("gamma", 1.4), rk_order=W["rk"], cfl=W.get("cfl", CFL),
-                  limiter=W["limiter"], positivity=W["positivity"], precision=precision, autotune=autotune)
+                  limiter=W["limiter"], positivity=W["positivity"], precision=precision, autotune=autotune,
+                  basis=W.get("basis", "total"))
     xyz = s.quad_points().cpu().numpy()
     if W.get("gravity"):
         s.set_gravity(torch.as_tensor(wl.keplerian_accel(xyz)))
@@ -149,13 +155,15 @@ def make_problem(wk, precision, autotune=None):
 # ---------------------------------------------------------------------------
 # algorithmic work per cell and stage (sum-factorised contraction counts)
 
-def shape(dim, k):
+def shape(dim, k, basis="total"):
     N = (k + 1) * (k + 2) // 2 if dim == 2 else (k + 1) * (k + 2) * (k + 3) // 6
+    if basis == "tensor":
+        N = (k + 1) ** dim
     Q, QF, nv = (k + 1) ** dim, (k + 1) ** (dim - 1), dim + 2
     return N, Q, QF, nv
 
 
-def kernel_flops(dim, k):
+def kernel_flops(dim, k, basis="total"):
     """Flops of the sum-factorised kernels: (cell kernel per cell, face kernel per face).
 
     Per variable (FMA counts; K1 = k+1, N2 = K1 (K1+1) / 2 pairs (a,b)):
@@ -164,8 +172,9 @@ def kernel_flops(dim, k):
       surface / side 2D: K1^2 + N             3D: K1^3 + N2 K1 + N
       face trace     2D: N + K1^2             3D: N + N2 K1 + K1^3
     plus Euler fluxes (18 | 27 flop per point), HLLC (90 | 100 flop per face
-    point) and the stage combination (5 flop per weight)."""
-    N, Q, QF, nv = shape(dim, k)
+    point) and the stage combination (5 flop per weight).  The 2D counts hold
+    for the tensor-product basis too (N = K1^2 there)."""
+    N, Q, QF, nv = shape(dim, k, basis)
     K1 = k + 1
     if dim == 2:
         m2n, vol = N * K1 + K1 ** 3, dim * (k * K1 * K1 + (N - K1) * K1)
@@ -180,8 +189,8 @@ def kernel_flops(dim, k):
     return cell, face
 
 
-def state_bytes_per_cell(dim, k, esize):
-    N, Q, QF, nv = shape(dim, k)
+def state_bytes_per_cell(dim, k, esize, basis="total"):
+    N, Q, QF, nv = shape(dim, k, basis)
     return nv * N * esize
 
 
@@ -608,7 +617,8 @@ def summarize(args, results, world):
     hbm, peak_kind = peaks()
     wk = WORKLOADS[args.workload]
     dim, k, stages = wk["dim"], wk["k"], wk["stages"]
-    N, _, _, nv = shape(dim, k)
+    basis = wk.get("basis", "total")
+    N, _, _, nv = shape(dim, k, basis)
     lines = {}
     for precision, r in results.items():
         cells = r["n_cells"]
@@ -629,7 +639,7 @@ def summarize(args, results, world):
             kname = "cell_tc_kernel"
         tag = "%s_%s" % (wk["tag"], precision)
         if precision == "fp64" and kind in ("cell", "face"):
-            fc, ff = kernel_flops(dim, k)
+            fc, ff = kernel_flops(dim, k, basis)
             fl = fc * cells if kind == "cell" else ff * dim * cells
             achieved = fl / avg_s / 1e12
             roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
@@ -640,17 +650,17 @@ def summarize(args, results, world):
                     "algorithmic_unit": "flop (sum-factorised count of kernel_flops)"}
             if kind == "cell":
                 # the same launch against the HBM roof (3 state arrays per stage)
-                byt = 3 * state_bytes_per_cell(dim, k, esize) * cells
+                byt = 3 * state_bytes_per_cell(dim, k, esize, basis) * cells
                 roof["hbm"] = {"achieved": byt / avg_s / 1e9, "peak": hbm, "unit": "GB/s",
                                "frac": byt / avg_s / 1e9 / hbm, "peak_source": peak_kind,
                                "algorithmic_per_launch": byt}
         else:
             # HBM: a launch of the dominant kernel processes one stage of the mesh,
             # whose algorithmic traffic is 3 state arrays (read U_i and w^n, write U_i+1)
-            byt = 3 * state_bytes_per_cell(dim, k, esize) * cells
+            byt = 3 * state_bytes_per_cell(dim, k, esize, basis) * cells
             if precision in ("mixed", "mixed_tc"):
                 # FP64 state read, FP32 delta registers read and written
-                byt = (state_bytes_per_cell(dim, k, 8) + 2 * state_bytes_per_cell(dim, k, 4)) * cells
+                byt = (state_bytes_per_cell(dim, k, 8, basis) + 2 * state_bytes_per_cell(dim, k, 4, basis)) * cells
             achieved = byt / avg_s / 1e9
             roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm,
                     "unit": "GB/s", "frac": achieved / hbm, "peak_source": peak_kind,
@@ -660,9 +670,9 @@ def summarize(args, results, world):
         if roof["unit"] == "GB/s" or "hbm" in roof:
             # the whole stage against the HBM roof: algorithmic bytes of one
             # stage over the measured time per stage (every kernel and gap)
-            byt_stage = 3 * state_bytes_per_cell(dim, k, esize) * cells
+            byt_stage = 3 * state_bytes_per_cell(dim, k, esize, basis) * cells
             if precision in ("mixed", "mixed_tc"):
-                byt_stage = (state_bytes_per_cell(dim, k, 8) + 2 * state_bytes_per_cell(dim, k, 4)) * cells
+                byt_stage = (state_bytes_per_cell(dim, k, 8, basis) + 2 * state_bytes_per_cell(dim, k, 4, basis)) * cells
             t_stage = r["ms"] / args.steps / stages * 1e-3
             roof["stage"] = {"achieved": byt_stage / t_stage / 1e9, "peak": hbm, "unit": "GB/s",
                              "frac": byt_stage / t_stage / 1e9 / hbm,
@@ -762,18 +772,19 @@ L1_T_END = 2.0
 L1_EQUAL_TOL = 1.05  # "equal" L1: within 5% of the FP64 error
 
 
-def l1_ladder(precisions, sizes, t_end, verbose=False):
+def l1_ladder(precisions, sizes, t_end, verbose=False, basis="total"):
     """L1 density error of the vortex against its closed form after t_end
     (fixed timestep: the CFL value of the initial state, rounded so that
     t_end is reached exactly), per precision and resolution, with the device
-    time per RK stage measured by CUDA events around the steps."""
+    time per RK stage measured by CUDA events around the steps.  With the
+    tensor-product basis the rows' precision reads "tensor_<precision>"."""
     import torch
     from paper_1506_06140_gb300 import dg
     from paper_1506_06140_gb300 import workloads as wl
     rows = []
     for precision in precisions:
         for n in sizes:
-            s = dg.Solver(mesh(n), K_DEG, 1.4, rk_order=RK_ORDER, cfl=CFL, precision=precision)
+            s = dg.Solver(mesh(n), K_DEG, 1.4, rk_order=RK_ORDER, cfl=CFL, precision=precision, basis=basis)
             W = s.project(torch.as_tensor(wl.vortex(s.quad_points().cpu().numpy())))
             dt = s.compute_dt(W).item()  # the vortex translates; its CFL timestep stays put
             nsteps = int(math.ceil(t_end / dt))
@@ -789,9 +800,9 @@ def l1_ladder(precisions, sizes, t_end, verbose=False):
             ms = e0.elapsed_time(e1)
             rho_ex = wl.vortex(s.l1_points().cpu().numpy(), t=t_end)[0]
             l1 = s.l1_density(W, torch.as_tensor(rho_ex)).item()
-            rows.append({"precision": precision, "n": n, "steps": nsteps, "L1": l1,
-                         "ms_per_stage": ms / (nsteps * STAGES),
-                         "dof_updates_per_s": n * n * N_BASIS * STAGES * nsteps / (ms * 1e-3)})
+            rows.append({"precision": precision if basis == "total" else "%s_%s" % (basis, precision),
+                         "n": n, "steps": nsteps, "L1": l1, "ms_per_stage": ms / (nsteps * STAGES),
+                         "dof_updates_per_s": n * n * s.N * STAGES * nsteps / (ms * 1e-3)})
             if verbose:
                 print(json.dumps(rows[-1]), flush=True)
             del s, W
@@ -1106,6 +1117,26 @@ def main():
                            for p in args.precisions[1:]}
         for p in args.precisions[1:]:
             out["variants"][p]["diagnostics"] = lines[p].get("diagnostics")
+        if args.workload == "vortex_tensor" and not args.no_l1:
+            # accuracy against the paper's total-degree basis at FP64: L1 errors
+            # on the ladder and the comparison at equal L1 error
+            rows = l1_ladder(["fp64"], L1_SIZES, L1_T_END) + \
+                l1_ladder([p for p in ("fp64", "fp32") if p in lines], L1_SIZES, L1_T_END, basis="tensor")
+            at_n = {r["precision"]: r for r in rows if r["n"] == N_CELLS_1D}
+            out["l1"] = at_n["tensor_fp64"]["L1"]
+            for p in out["variants"]:
+                out["variants"][p]["l1"] = at_n["tensor_" + p]["L1"]
+            out["equal_l1"] = {"t_end": L1_T_END, "tol": L1_EQUAL_TOL,
+                               "definition": "L1 density error against the closed-form vortex (Sec. 5.1) "
+                                             "after t_end with a fixed timestep; \"fp64\" rows: the paper's "
+                                             "total-degree basis (10 coeffs), \"tensor_*\" rows: Q_3 (16 "
+                                             "coeffs); per total-degree FP64 rung the coarsest resolution "
+                                             "where each tensor variant is within tol of its error, and the "
+                                             "total-degree FP64 times over the variant's",
+                               "ladder": rows, "comparison": equal_l1(rows)}
+            out["config"]["l1"] = ("L1 density error after t=%g with a fixed timestep on the %s ladder "
+                                   "(\"l1\" and variants' \"l1\": at 256^2)"
+                                   % (L1_T_END, "/".join("%d^2" % n for n in L1_SIZES)))
         if amr and world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline_kh()
         print(json.dumps(out), flush=True)

@@ -44,7 +44,7 @@ enum {
   DG_ERR_OOM = 3,          /* device allocation failed */
   DG_ERR_NONPHYSICAL = 4,  /* device flag: a cell mean with rho <= 0 or p <= 0 was seen */
   DG_ERR_TIMEOUT = 5,      /* device flag: a bounded wait gave up */
-  DG_ERR_UNSUPPORTED = 6   /* (dim, k, precision) combination not compiled */
+  DG_ERR_UNSUPPORTED = 6   /* (dim, k, precision, basis) combination, or a call on a handle, not built */
 };
 
 enum { DG_BC_PERIODIC = 0, DG_BC_TRANSMISSIVE = 1 };
@@ -69,6 +69,22 @@ enum { DG_LIMITER_NONE = 0, DG_LIMITER_COMPONENT = 1, DG_LIMITER_CHARACTERISTIC 
  *             tensor cores (split TF32, FP32 accumulation); 2D uniform meshes,
  *             k = 1..3. */
 enum { DG_FP64 = 0, DG_FP32 = 1, DG_FP32_TC = 2, DG_MIXED = 3, DG_MIXED_TC = 4 };
+
+/* Polynomial space of a cell (dg_options.basis).
+ * DG_BASIS_TOTAL: the paper's basis (Sec. 2.2, eq. set_basis_functions): the
+ *             products of scaled Legendre polynomials of total degree <= k,
+ *             N(k) = (k+1)(k+2)/2 in 2D, (k+1)(k+2)(k+3)/6 in 3D.
+ * DG_BASIS_TENSOR: the same products with every exponent <= k (the tensor
+ *             product space Q_k, N = (k+1)^2 in 2D), ordered by total degree,
+ *             then x exponent descending, so that its first N(k) functions are
+ *             those of DG_BASIS_TOTAL.  Same quadrature rules (the (k+1)-point
+ *             Gauss rule integrates the mass products of Q_k exactly).  Built
+ *             for dim 2, k = 1..3, DG_FP64 and DG_FP32, without the slope or
+ *             positivity limiter; dg_limit, dg_rk_step_adjoint,
+ *             dg_node_weights, dg_set_gravity, dg_adapt_mark, dg_adapt_set
+ *             and dg_regrid return DG_ERR_UNSUPPORTED on such a handle.  At k = 0 both
+ *             spaces are the constants and the handle is a DG_BASIS_TOTAL one. */
+enum { DG_BASIS_TOTAL = 0, DG_BASIS_TENSOR = 1 };
 
 /* Mesh description (paper Secs. 2.2 and 4): cubical cells on the box
  * [lo, hi]; n[a] base cells along axis a (the base edge length must be equal
@@ -107,11 +123,15 @@ typedef struct {
                         give identical results for every tile; the one-thread-per-
                         cell kernel sums in another order (FP32 rounding).  See
                         dg_tiles. */
+  int basis;         /* DG_BASIS_TOTAL (default) or DG_BASIS_TENSOR; the weight
+                        arrays W[var][coef][cell] then hold N = (k+1)^2 coefficients
+                        per variable (dg_sizes) */
 } dg_options;
 
 typedef struct dg_handle dg_handle;
 
-/* Fills *opt with the defaults above (rk_order = 3, no limiter, FP64). */
+/* Fills *opt with the defaults above (rk_order = 3, no limiter, FP64, the
+ * total-degree basis). */
 int dg_default_options(dg_options* opt);
 
 /* Creates a solver for a mesh, polynomial degree k and adiabatic index gamma
@@ -150,20 +170,20 @@ int dg_tiles(const dg_handle* h, int* cell_tile, int* face_tile);
 
 /* Sets the tiles by hand (the autotuner's choices can be overridden):
  * cell_tile 16, 32 or 64 cells per block of the tiled cell kernel, or 1 for
- * the one-thread-per-cell kernel (FP32 2D handles only); face_tile 16, 32 or
+ * the one-thread-per-cell kernel (FP32 2D handles of the total-degree basis only); face_tile 16, 32 or
  * 64, or 0 for the fused face + cell kernel: each block takes a tile of 8 x 4
  * cells, computes the fluxes of the tile's faces in shared memory (the
  * neighbours' traces across the tile's edges from their weights) and then
  * the cell update -- one launch per stage and no face-flux array, with the
  * same results to rounding (single 2D uniform meshes, FP64 or FP32 state,
- * not with cell_tile 1; the cell tile value is then unused).  DG_ERR_ARG for
- * other values, DG_ERR_UNSUPPORTED where the (dim, k, precision, mesh) has
- * no such kernel.  Not to be called while another call on the handle is
+ * the total-degree basis, not with cell_tile 1; the cell tile value is then
+ * unused).  DG_ERR_ARG for other values, DG_ERR_UNSUPPORTED where the (dim,
+ * k, precision, basis, mesh) has no such kernel.  Not to be called while another call on the handle is
  * being captured. */
 int dg_set_tiles(dg_handle* h, int cell_tile, int face_tile);
 
 /* Sizes: cells, basis functions N(k) (eq. nof_basis_functions and its 2D
- * analogue), variables nv, volume Gauss points per cell (k+1)^dim, points of
+ * analogue; (k+1)^2 for DG_BASIS_TENSOR), variables nv, volume Gauss points per cell (k+1)^dim, points of
  * the (k+3)^dim rule used by dg_l1_density, refined base cells (nodes). */
 int dg_sizes(const dg_handle* h, int64_t* n_cells, int* n_basis, int* n_vars, int* n_qpoints,
              int* n_l1points, int* n_nodes);
@@ -226,8 +246,8 @@ int dg_batch_advance(dg_handle* h, void* W_dev, int n_steps, double* dt_hist_dev
  *                          barriers; bit-identical results.  Its barrier waits
  *                          are bounded: a wait that gives up stops the kernel
  *                          and latches DG_ERR_TIMEOUT (dg_status).
- * The persistent kernel serves 2D handles with an FP64 or FP32 state and the
- * CUDA-core stage kernels (not DG_FP32_TC / DG_MIXED / DG_MIXED_TC, not the
+ * The persistent kernel serves 2D handles with the total-degree basis, an
+ * FP64 or FP32 state and the CUDA-core stage kernels (not DG_FP32_TC / DG_MIXED / DG_MIXED_TC, not the
  * one-thread-per-cell tile), without a gravity source, with at most 5 RK
  * stages.  DG_ADVANCE_GRAPH is the default on every handle: on one GB300 a
  * graph's kernel boundary costs about as much as the persistent kernel's

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["dg_inst_3d_f64.cu", "dg_inst_3d_f32.cu", "dg_inst_2d_f64.cu", "dg_inst_2d_f32.cu",
+SOURCES = ["dg_inst_3d_f64.cu", "dg_inst_3d_f32.cu", "dg_inst_2d_f64.cu", "dg_inst_2d_f32.cu", "dg_inst_2d_tensor.cu",
            "dg_mixed_3d.cu", "dg_mixed_2d.cu", "dg_common.cu", "dg_noalloc.cu", "dg_regrid.cu",
            "dg_host.cpp"]
 NVCC = os.environ.get("NVCC", "nvcc")

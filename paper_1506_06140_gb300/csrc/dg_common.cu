@@ -11,12 +11,27 @@ bool kernel_set_2d_f32(int k, KernelSet* out);
 bool kernel_set_3d_f64(int k, KernelSet* out);
 bool kernel_set_3d_f32(int k, KernelSet* out);
 
-const KernelSet* kernel_set(int prec, int dim, int k) {
+bool kernel_set_2d_tensor(int prec, int k, KernelSet* out);
+
+// basis 1 (tensor product Q_k): 2D, k = 1..3; at k = 0 both bases are the constant
+const KernelSet* kernel_set(int prec, int dim, int k, int basis) {
   static KernelSet sets[2][2][4];
   static bool have[2][2][4] = {};
+  static KernelSet tsets[2][4];
+  static bool thave[2][4] = {};
   static std::mutex mu;
   if (prec < 0 || prec > 1 || (dim != 2 && dim != 3) || k < 0 || k > 3) return nullptr;
+  if (basis != 0 && (basis != 1 || dim != 2)) return nullptr;
+  if (k == 0) basis = 0;
   std::lock_guard<std::mutex> lock(mu);
+  if (basis == 1) {
+    KernelSet& ts = tsets[prec][k];
+    if (!thave[prec][k]) {
+      if (!kernel_set_2d_tensor(prec, k, &ts)) return nullptr;
+      thave[prec][k] = true;
+    }
+    return &ts;
+  }
   KernelSet& ks = sets[prec][dim - 2][k];
   if (!have[prec][dim - 2][k]) {
     const bool ok = dim == 2 ? (prec == 0 ? kernel_set_2d_f64(k, &ks) : kernel_set_2d_f32(k, &ks))

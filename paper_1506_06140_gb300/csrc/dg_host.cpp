@@ -1401,10 +1401,18 @@ int dg_default_options(dg_options* opt) {
   opt->eps = 1e-10;
   opt->precision = DG_FP64;
   opt->autotune = 0;
+  opt->basis = DG_BASIS_TOTAL;
   return DG_OK;
 }
 
 const char* dg_last_error(const dg_handle* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+// the tensor-product basis has the stage, timestep, projection and
+// diagnostic kernels only
+static int tensor_unsupported(dg_handle* h, const char* what) {
+  if (h->ks->basis == 0) return DG_OK;
+  return fail(h, DG_ERR_UNSUPPORTED, std::string(what) + ": not built for the tensor-product basis");
+}
 
 static int create_impl(const dg_mesh_desc* mesh, int nprob, int k, double gamma,
                        const dg_options* opt, dg_handle** out) {
@@ -1427,8 +1435,13 @@ static int create_impl(const dg_mesh_desc* mesh, int nprob, int k, double gamma,
   if (use_tc) o.precision = DG_FP32;
   if (mixed) o.precision = DG_FP64;  // FP64 state; FP32 stage kernels below
   if (!(o.cfl > 0.0)) return fail(nullptr, DG_ERR_ARG, "dg_create: cfl must be positive");
-  const KernelSet* ks = kernel_set(o.precision, mesh->dim, k);
-  if (!ks) return fail(nullptr, DG_ERR_UNSUPPORTED, "dg_create: (dim, k, precision) not compiled");
+  if (o.basis != DG_BASIS_TOTAL && o.basis != DG_BASIS_TENSOR) return fail(nullptr, DG_ERR_ARG, "dg_create: bad basis");
+  if (o.basis == DG_BASIS_TENSOR && k > 0 &&
+      (mesh->dim != 2 || use_tc || mixed || o.slope_limiter != DG_LIMITER_NONE || o.positivity))
+    return fail(nullptr, DG_ERR_UNSUPPORTED,
+                "dg_create: the tensor-product basis needs dim 2, an FP64 or FP32 state and no limiter");
+  const KernelSet* ks = kernel_set(o.precision, mesh->dim, k, o.basis);
+  if (!ks) return fail(nullptr, DG_ERR_UNSUPPORTED, "dg_create: (dim, k, precision, basis) not compiled");
   auto* h = new dg_handle();
   h->dim = mesh->dim;
   h->k = k;
@@ -1822,6 +1835,7 @@ int dg_n_problems(const dg_handle* h, int* n_problems, int64_t* cell_offsets_hos
 int dg_rk_step_adjoint(dg_handle* h, const void* W_n_dev, double dt, const void* lam_np1_dev,
                        void* lam_n_dev, void* stream) {
   if (!check_handle(h) || !W_n_dev || !lam_np1_dev || !lam_n_dev) return DG_ERR_ARG;
+  if (int r = tensor_unsupported(h, "dg_rk_step_adjoint")) return r;
   if (!(dt > 0.0)) return fail(h, DG_ERR_ARG, "dg_rk_step_adjoint: dt must be positive (frozen)");
   if (h->opt.slope_limiter != DG_LIMITER_NONE || h->opt.positivity)
     return fail(h, DG_ERR_ARG, "dg_rk_step_adjoint: needs an unlimited handle");
@@ -1835,6 +1849,7 @@ int dg_rk_step_adjoint(dg_handle* h, const void* W_n_dev, double dt, const void*
 
 int dg_limit(dg_handle* h, void* W_dev, void* stream) {
   if (!check_handle(h) || !W_dev) return DG_ERR_ARG;
+  if (int r = tensor_unsupported(h, "dg_limit")) return r;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t bytes = (size_t)h->nv * h->N * h->ncells * h->esize;
   void* tmp = h->regs.back();
@@ -1881,6 +1896,7 @@ int dg_l1_density(dg_handle* h, const void* W_dev, const double* rho_ref_dev, do
 
 int dg_node_weights(dg_handle* h, const void* W_dev, void* Wnode_dev, void* stream) {
   if (!check_handle(h) || !W_dev || !Wnode_dev) return DG_ERR_ARG;
+  if (int r = tensor_unsupported(h, "dg_node_weights")) return r;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (h->prec == DG_FP64) {
     AuxArgs<double> a = aux_args<double>(h);
@@ -1921,6 +1937,7 @@ int dg_cell_levels(const dg_handle* h, int32_t* host_out) {
 
 int dg_set_gravity(dg_handle* h, const double* accel_dev, void* stream) {
   if (!check_handle(h)) return DG_ERR_ARG;
+  if (int r = tensor_unsupported(h, "dg_set_gravity")) return r;
   std::lock_guard<std::mutex> lock(h->mu);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   drop_graphs(h);  // recorded launches carry the old field pointer
@@ -1945,6 +1962,7 @@ int dg_set_gravity(dg_handle* h, const double* accel_dev, void* stream) {
 int dg_adapt_mark(dg_handle* h, const void* W_dev, double w_t, double alpha, int32_t* flags_host,
                   int64_t* n_cells_new, int64_t* n_changed, void* stream) {
   if (!check_handle(h) || !W_dev) return DG_ERR_ARG;
+  if (int r = tensor_unsupported(h, "dg_adapt_mark")) return r;
   if (!(w_t > 0.0) || !(alpha >= 1.0)) return fail(h, DG_ERR_ARG, "dg_adapt_mark: need w_t > 0 and alpha >= 1");
   std::lock_guard<std::mutex> lock(h->mu);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1963,6 +1981,7 @@ int dg_adapt_mark(dg_handle* h, const void* W_dev, double w_t, double alpha, int
 int dg_adapt_set(dg_handle* h, const int32_t* flags_host, int64_t* n_cells_new, int64_t* n_changed,
                  void* stream) {
   if (!check_handle(h) || !flags_host) return DG_ERR_ARG;
+  if (int r = tensor_unsupported(h, "dg_adapt_set")) return r;
   std::lock_guard<std::mutex> lock(h->mu);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int r = ensure_adapt(h);
@@ -1977,6 +1996,7 @@ int dg_adapt_set(dg_handle* h, const int32_t* flags_host, int64_t* n_cells_new, 
 
 int dg_regrid(dg_handle* h, const void* W_old_dev, void* W_new_dev, void* stream) {
   if (!check_handle(h) || !W_old_dev || !W_new_dev) return DG_ERR_ARG;
+  if (int r = tensor_unsupported(h, "dg_regrid")) return r;
   if (W_old_dev == W_new_dev) return fail(h, DG_ERR_ARG, "dg_regrid: W_new must not alias W_old");
   std::lock_guard<std::mutex> lock(h->mu);
   if (!h->mark_pending) return fail(h, DG_ERR_ARG, "dg_regrid: no refinement marked");

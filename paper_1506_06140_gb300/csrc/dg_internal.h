@@ -9,10 +9,13 @@
 namespace dgi {
 
 // ---------------------------------------------------------------------------
-// Compile-time sizes of a (dim, k) scheme.
-template <int DIM, int K>
+// Compile-time sizes of a (dim, k) scheme.  B = 0: the paper's basis of
+// total degree <= k; B = 1: the tensor-product basis Q_k (every exponent
+// <= k, (k+1)^dim functions; 2D kernels only).
+template <int DIM, int K, int B = 0>
 struct Shape {
-  static constexpr int N = DIM == 2 ? (K + 1) * (K + 2) / 2 : (K + 1) * (K + 2) * (K + 3) / 6;
+  static constexpr int N = B ? (DIM == 2 ? (K + 1) * (K + 1) : (K + 1) * (K + 1) * (K + 1))
+                             : (DIM == 2 ? (K + 1) * (K + 2) / 2 : (K + 1) * (K + 2) * (K + 3) / 6);
   static constexpr int NV = DIM + 2;
   static constexpr int K1 = K + 1;
   static constexpr int Q = DIM == 2 ? K1 * K1 : K1 * K1 * K1;          // volume points
@@ -242,7 +245,7 @@ struct CombineArgs {
 
 // Kernel set of one (precision, dim, k).
 struct KernelSet {
-  int dim = 0, k = 0, prec = 0;
+  int dim = 0, k = 0, prec = 0, basis = 0;  // basis: 0 total degree <= k, 1 tensor product Q_k
   int N = 0, NV = 0, Q = 0, QF = 0, Q1 = 0, NSUB = 0, NSP = 0, M = 0, tab_size = 0;
   int off_pref = 0;  // offset of the refinement matrices in the table
   // host: fill the table (double) from 1D Gauss and Lobatto rules
@@ -282,7 +285,7 @@ struct KernelSet {
   cudaError_t (*prepare_persist)() = nullptr;
 };
 
-const KernelSet* kernel_set(int prec, int dim, int k);
+const KernelSet* kernel_set(int prec, int dim, int k, int basis = 0);
 
 // Stage kernels for an FP64 state with an FP32 right-hand side in
 // perturbation form (argument block MixedArgs, dg_mixed.cuh).

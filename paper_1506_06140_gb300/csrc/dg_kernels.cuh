@@ -41,18 +41,24 @@ inline void host_legendre(int n, double x, double* P, double* dP) {
   }
 }
 
-template <int DIM, int K>
+template <int DIM, int K, int B = 0>
 struct HostBasis {
-  using S = Shape<DIM, K>;
+  using S = Shape<DIM, K, B>;
   int e[S::N][3];
+  // by total degree, then the x exponent descending, then y descending;
+  // every exponent <= K for the tensor-product basis (B = 1)
   HostBasis() {
     int n = 0;
-    for (int g = 0; g <= K; ++g) {
+    for (int g = 0; g <= (B ? DIM * K : K); ++g) {
       if (DIM == 2) {
-        for (int nx = g; nx >= 0; --nx) { e[n][0] = nx; e[n][1] = g - nx; e[n][2] = 0; ++n; }
+        for (int nx = g; nx >= 0; --nx) {
+          if (nx > K || g - nx > K) continue;
+          e[n][0] = nx; e[n][1] = g - nx; e[n][2] = 0; ++n;
+        }
       } else {
         for (int nx = g; nx >= 0; --nx)
           for (int ny = g - nx; ny >= 0; --ny) {
+            if (nx > K || ny > K || g - nx - ny > K) continue;
             e[n][0] = nx; e[n][1] = ny; e[n][2] = g - nx - ny; ++n;
           }
       }
@@ -108,12 +114,12 @@ inline void face_point(int dir, int s, int variant, int q, const std::vector<dou
   }
 }
 
-template <int DIM, int K>
+template <int DIM, int K, int BA = 0>
 void fill_tables(std::vector<double>& T, const std::vector<double>& gx,
                  const std::vector<double>& gw, const std::vector<double>& g3x,
                  const std::vector<double>& g3w, const std::vector<double>& lx) {
-  using S = Shape<DIM, K>;
-  HostBasis<DIM, K> B;
+  using S = Shape<DIM, K, BA>;
+  HostBasis<DIM, K, BA> B;
   T.assign(S::TAB_SIZE, 0.0);
   const double two_d = std::ldexp(1.0, DIM);
   // volume rule, x fastest
@@ -772,9 +778,9 @@ __device__ __forceinline__ double block_sum(double x, double* sh) {
 // division is monotone, fac / max s_K equals min_K fac / s_K exactly.  The
 // maximum is accumulated as the bit pattern of a positive double.
 // the work of block bid of nblk, THREADS threads per block
-template <typename real, int DIM, int K, int THREADS>
+template <typename real, int DIM, int K, int THREADS, int B = 0>
 __device__ __forceinline__ void dt_body(const AuxArgs<real>& a, int bid, int nblk) {
-  using S = Shape<DIM, K>;
+  using S = Shape<DIM, K, B>;
   const int c = bid * THREADS + threadIdx.x;
   const int nc = a.m.ncells;
   double speed = 0.0;
@@ -876,14 +882,14 @@ __device__ __forceinline__ void dt_body(const AuxArgs<real>& a, int bid, int nbl
   }
 }
 
-template <typename real, int DIM, int K>
+template <typename real, int DIM, int K, int B = 0>
 __global__ void __launch_bounds__(RED_THREADS) dt_kernel(const AuxArgs<real> a) {
-  dt_body<real, DIM, K, RED_THREADS>(a, blockIdx.x, gridDim.x);
+  dt_body<real, DIM, K, RED_THREADS, B>(a, blockIdx.x, gridDim.x);
 }
 
-template <typename real, int DIM, int K>
+template <typename real, int DIM, int K, int B = 0>
 __global__ void __launch_bounds__(RED_THREADS) totals_kernel(const AuxArgs<real> a) {
-  using S = Shape<DIM, K>;
+  using S = Shape<DIM, K, B>;
   __shared__ double sh[RED_THREADS];
   const int c = blockIdx.x * RED_THREADS + threadIdx.x;
   const int nc = a.m.ncells;
@@ -899,9 +905,9 @@ __global__ void __launch_bounds__(RED_THREADS) totals_kernel(const AuxArgs<real>
   }
 }
 
-template <typename real, int DIM, int K>
+template <typename real, int DIM, int K, int B = 0>
 __global__ void __launch_bounds__(RED_THREADS) l1_kernel(const AuxArgs<real> a) {
-  using S = Shape<DIM, K>;
+  using S = Shape<DIM, K, B>;
   __shared__ double sh[RED_THREADS];
   const int c = blockIdx.x * RED_THREADS + threadIdx.x;
   const int nc = a.m.ncells;
@@ -936,9 +942,9 @@ static __global__ void reduce_partials_kernel(const double* partial, int nblocks
   if (l == 0) out[v] = s * scale;
 }
 
-template <typename real, int DIM, int K>
+template <typename real, int DIM, int K, int B = 0>
 __global__ void project_kernel(const AuxArgs<real> a) {
-  using S = Shape<DIM, K>;
+  using S = Shape<DIM, K, B>;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int nc = a.m.ncells;
   if (c >= nc) return;
@@ -953,9 +959,9 @@ __global__ void project_kernel(const AuxArgs<real> a) {
   }
 }
 
-template <typename real, int DIM, int K>
+template <typename real, int DIM, int K, int B = 0>
 __global__ void points_kernel(const AuxArgs<real> a, int l1rule) {
-  using S = Shape<DIM, K>;
+  using S = Shape<DIM, K, B>;  // the table offsets depend on the basis size
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int nc = a.m.ncells;
   if (c >= nc) return;
@@ -990,7 +996,7 @@ __global__ void node_weights_kernel(const AuxArgs<real> a) {
 // ===========================================================================
 // Launchers
 
-template <typename real, int DIM, int K>
+template <typename real, int DIM, int K, int B = 0>
 cudaError_t launch_face(const void* pa, cudaStream_t s) {
   const auto& a = *static_cast<const StageArgs<real>*>(pa);
   using FT = FaceTile<real, DIM, K>;
@@ -998,13 +1004,13 @@ cudaError_t launch_face(const void* pa, cudaStream_t s) {
   if (a.m.nfaces == 0) return cudaSuccess;
   const int fb = a.face_tile == 16 || a.face_tile == 64 ? a.face_tile : 32;
   const int grid = (a.m.nfaces + fb - 1) / fb;
-  if (fb == 16) face_flux_kernel<real, DIM, K, 16><<<grid, 16 * NV, FT::smem(16), s>>>(a);
-  else if (fb == 64) face_flux_kernel<real, DIM, K, 64><<<grid, 64 * NV, FT::smem(64), s>>>(a);
-  else face_flux_kernel<real, DIM, K, 32><<<grid, 32 * NV, FT::smem(32), s>>>(a);
+  if (fb == 16) face_flux_kernel<real, DIM, K, 16, B><<<grid, 16 * NV, FT::smem(16), s>>>(a);
+  else if (fb == 64) face_flux_kernel<real, DIM, K, 64, B><<<grid, 64 * NV, FT::smem(64), s>>>(a);
+  else face_flux_kernel<real, DIM, K, 32, B><<<grid, 32 * NV, FT::smem(32), s>>>(a);
   return cudaGetLastError();
 }
 
-template <typename real, int DIM, int K>
+template <typename real, int DIM, int K, int B = 0>
 cudaError_t launch_cell(const void* pa, cudaStream_t s) {
   const auto& a = *static_cast<const StageArgs<real>*>(pa);
   using CT = CellTile<real, DIM, K>;
@@ -1013,18 +1019,22 @@ cudaError_t launch_cell(const void* pa, cudaStream_t s) {
   const int tc = (a.cell_tile == 16 || a.cell_tile == 32 || a.cell_tile == 64) && a.cell_tile <= CT::TC_MAX
                      ? a.cell_tile
                      : CT::TC;
-  if (a.accel) {  // gravity: the default tile only
-    cell_update_kernel<real, DIM, K, CT::TC, true><<<(a.m.ncells + CT::TC - 1) / CT::TC, CT::TC * NV,
-                                                     CT::smem(CT::TC, true), s>>>(a);
-    return cudaGetLastError();
+  if (a.accel) {  // gravity: the default tile only (not built for the tensor-product basis)
+    if constexpr (B == 0) {
+      cell_update_kernel<real, DIM, K, CT::TC, true><<<(a.m.ncells + CT::TC - 1) / CT::TC, CT::TC * NV,
+                                                       CT::smem(CT::TC, true), s>>>(a);
+      return cudaGetLastError();
+    } else {
+      return cudaErrorNotSupported;
+    }
   }
   const int grid = (a.m.ncells + tc - 1) / tc;
   if (tc == 16) {
-    cell_update_kernel<real, DIM, K, 16><<<grid, 16 * NV, CT::smem(16), s>>>(a);
+    cell_update_kernel<real, DIM, K, 16, false, B><<<grid, 16 * NV, CT::smem(16), s>>>(a);
   } else if (tc == 32) {
-    if constexpr (CT::TC_MAX >= 32) cell_update_kernel<real, DIM, K, 32><<<grid, 32 * NV, CT::smem(32), s>>>(a);
+    if constexpr (CT::TC_MAX >= 32) cell_update_kernel<real, DIM, K, 32, false, B><<<grid, 32 * NV, CT::smem(32), s>>>(a);
   } else {
-    if constexpr (CT::TC_MAX >= 64) cell_update_kernel<real, DIM, K, 64><<<grid, 64 * NV, CT::smem(64), s>>>(a);
+    if constexpr (CT::TC_MAX >= 64) cell_update_kernel<real, DIM, K, 64, false, B><<<grid, 64 * NV, CT::smem(64), s>>>(a);
   }
   return cudaGetLastError();
 }
@@ -1048,27 +1058,35 @@ cudaError_t launch_combine(const void* pa, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <typename real, int DIM, int K>
+template <typename real, int DIM, int K, int B = 0>
 cudaError_t prepare_kernels() {
-  cudaError_t e0 = prepare_adjoint_kernels<real, DIM, K>();
-  if (e0 != cudaSuccess) return e0;
+  if constexpr (B == 0) {
+    cudaError_t e0 = prepare_adjoint_kernels<real, DIM, K>();
+    if (e0 != cudaSuccess) return e0;
+  }
   using CT = CellTile<real, DIM, K>;
   using FT = FaceTile<real, DIM, K>;
   const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  cudaError_t e = cudaFuncSetAttribute(cell_update_kernel<real, DIM, K, 16>, attr, (int)CT::smem(16));
+  cudaError_t e = cudaFuncSetAttribute(cell_update_kernel<real, DIM, K, 16, false, B>, attr, (int)CT::smem(16));
   if (e == cudaSuccess && CT::TC_MAX >= 32) {
-    if constexpr (CT::TC_MAX >= 32) e = cudaFuncSetAttribute(cell_update_kernel<real, DIM, K, 32>, attr, (int)CT::smem(32));
+    if constexpr (CT::TC_MAX >= 32)
+      e = cudaFuncSetAttribute(cell_update_kernel<real, DIM, K, 32, false, B>, attr, (int)CT::smem(32));
   }
   if (e == cudaSuccess && CT::TC_MAX >= 64) {
-    if constexpr (CT::TC_MAX >= 64) e = cudaFuncSetAttribute(cell_update_kernel<real, DIM, K, 64>, attr, (int)CT::smem(64));
+    if constexpr (CT::TC_MAX >= 64)
+      e = cudaFuncSetAttribute(cell_update_kernel<real, DIM, K, 64, false, B>, attr, (int)CT::smem(64));
   }
   if (e != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(cell_update_kernel<real, DIM, K, CT::TC, true>, attr, (int)CT::smem(CT::TC, true))) !=
-      cudaSuccess)
+  if constexpr (B == 0) {
+    if ((e = cudaFuncSetAttribute(cell_update_kernel<real, DIM, K, CT::TC, true>, attr,
+                                  (int)CT::smem(CT::TC, true))) != cudaSuccess)
+      return e;
+  }
+  if ((e = cudaFuncSetAttribute(face_flux_kernel<real, DIM, K, 16, B>, attr, (int)FT::smem(16))) != cudaSuccess)
     return e;
-  if ((e = cudaFuncSetAttribute(face_flux_kernel<real, DIM, K, 16>, attr, (int)FT::smem(16))) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(face_flux_kernel<real, DIM, K, 32>, attr, (int)FT::smem(32))) != cudaSuccess) return e;
-  return cudaFuncSetAttribute(face_flux_kernel<real, DIM, K, 64>, attr, (int)FT::smem(64));
+  if ((e = cudaFuncSetAttribute(face_flux_kernel<real, DIM, K, 32, B>, attr, (int)FT::smem(32))) != cudaSuccess)
+    return e;
+  return cudaFuncSetAttribute(face_flux_kernel<real, DIM, K, 64, B>, attr, (int)FT::smem(64));
 }
 
 template <typename real, int DIM, int K>
@@ -1087,45 +1105,45 @@ cudaError_t launch_limit(const void* pa, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <typename real, int DIM, int K>
+template <typename real, int DIM, int K, int B = 0>
 cudaError_t launch_project(const void* pa, cudaStream_t s) {
   const auto& a = *static_cast<const AuxArgs<real>*>(pa);
   if (a.m.ncells == 0) return cudaSuccess;
-  project_kernel<real, DIM, K><<<(a.m.ncells + 127) / 128, 128, 0, s>>>(a);
+  project_kernel<real, DIM, K, B><<<(a.m.ncells + 127) / 128, 128, 0, s>>>(a);
   return cudaGetLastError();
 }
 
-template <typename real, int DIM, int K>
+template <typename real, int DIM, int K, int B = 0>
 cudaError_t launch_points(const void* pa, int l1rule, cudaStream_t s) {
   const auto& a = *static_cast<const AuxArgs<real>*>(pa);
   if (a.m.ncells == 0) return cudaSuccess;
-  points_kernel<real, DIM, K><<<(a.m.ncells + 127) / 128, 128, 0, s>>>(a, l1rule);
+  points_kernel<real, DIM, K, B><<<(a.m.ncells + 127) / 128, 128, 0, s>>>(a, l1rule);
   return cudaGetLastError();
 }
 
-template <typename real, int DIM, int K>
+template <typename real, int DIM, int K, int B = 0>
 cudaError_t launch_dt(const void* pa, cudaStream_t s) {
   const auto& a = *static_cast<const AuxArgs<real>*>(pa);
   if (a.m.ncells == 0) return cudaSuccess;
-  dt_kernel<real, DIM, K><<<(a.m.ncells + RED_THREADS - 1) / RED_THREADS, RED_THREADS, 0, s>>>(a);  // per-problem max
+  dt_kernel<real, DIM, K, B><<<(a.m.ncells + RED_THREADS - 1) / RED_THREADS, RED_THREADS, 0, s>>>(a);  // per-problem max
   return cudaGetLastError();
 }
 
-template <typename real, int DIM, int K>
+template <typename real, int DIM, int K, int B = 0>
 cudaError_t launch_totals(const void* pa, cudaStream_t s) {
   const auto& a = *static_cast<const AuxArgs<real>*>(pa);
-  using S = Shape<DIM, K>;
+  using S = Shape<DIM, K, B>;
   const int nb = (a.m.ncells + RED_THREADS - 1) / RED_THREADS;
-  if (nb > 0) totals_kernel<real, DIM, K><<<nb, RED_THREADS, 0, s>>>(a);
+  if (nb > 0) totals_kernel<real, DIM, K, B><<<nb, RED_THREADS, 0, s>>>(a);
   reduce_partials_kernel<<<S::NV, 32, 0, s>>>(a.partial, nb, S::NV, 1.0, a.out);
   return cudaGetLastError();
 }
 
-template <typename real, int DIM, int K>
+template <typename real, int DIM, int K, int B = 0>
 cudaError_t launch_l1(const void* pa, cudaStream_t s) {
   const auto& a = *static_cast<const AuxArgs<real>*>(pa);
   const int nb = (a.m.ncells + RED_THREADS - 1) / RED_THREADS;
-  if (nb > 0) l1_kernel<real, DIM, K><<<nb, RED_THREADS, 0, s>>>(a);
+  if (nb > 0) l1_kernel<real, DIM, K, B><<<nb, RED_THREADS, 0, s>>>(a);
   reduce_partials_kernel<<<1, 32, 0, s>>>(a.partial, nb, 1, 1.0 / a.volume, a.out);
   return cudaGetLastError();
 }
@@ -1145,13 +1163,14 @@ cudaError_t launch_node_weights(const void* pa, cudaStream_t s) {
 
 namespace dgi {
 
-template <typename real, int DIM, int K>
+template <typename real, int DIM, int K, int B = 0>
 KernelSet make_kernel_set(int prec) {
-  using S = Shape<DIM, K>;
+  using S = Shape<DIM, K, B>;
   KernelSet ks;
   ks.dim = DIM;
   ks.k = K;
   ks.prec = prec;
+  ks.basis = B;
   ks.N = S::N;
   ks.NV = S::NV;
   ks.Q = S::Q;
@@ -1162,38 +1181,42 @@ KernelSet make_kernel_set(int prec) {
   ks.M = S::M;
   ks.tab_size = S::TAB_SIZE;
   ks.off_pref = S::OFF_PREF;
-  ks.fill_tables = &fill_tables<DIM, K>;
-  ks.prepare = &prepare_kernels<real, DIM, K>;
+  ks.fill_tables = &fill_tables<DIM, K, B>;
+  ks.prepare = &prepare_kernels<real, DIM, K, B>;
   ks.cell_tile = CellTile<real, DIM, K>::TC;
   ks.cell_tile_max = CellTile<real, DIM, K>::TC_MAX;
   ks.face_tile = FaceTile<real, DIM, K>::FB;
   ks.face_tile_max = FaceTile<real, DIM, K>::FB_MAX;
-  ks.face = &launch_face<real, DIM, K>;
-  ks.cell = &launch_cell<real, DIM, K>;
-  ks.limit = &launch_limit<real, DIM, K>;
-  ks.project = &launch_project<real, DIM, K>;
-  ks.points = &launch_points<real, DIM, K>;
-  ks.dt = &launch_dt<real, DIM, K>;
-  ks.totals = &launch_totals<real, DIM, K>;
-  ks.l1 = &launch_l1<real, DIM, K>;
-  ks.node_weights = &launch_node_weights<real, DIM, K>;
-  ks.adj_face = &launch_adj_face<real, DIM, K>;
-  ks.adj_cell = &launch_adj_cell<real, DIM, K>;
+  ks.face = &launch_face<real, DIM, K, B>;
+  ks.cell = &launch_cell<real, DIM, K, B>;
+  ks.project = &launch_project<real, DIM, K, B>;
+  ks.points = &launch_points<real, DIM, K, B>;
+  ks.dt = &launch_dt<real, DIM, K, B>;
+  ks.totals = &launch_totals<real, DIM, K, B>;
+  ks.l1 = &launch_l1<real, DIM, K, B>;
   ks.combine = &launch_combine<real>;
-  if constexpr (std::is_same<real, float>::value && DIM == 2) {
-    ks.cell_direct = &launch_cell_direct<DIM, K>;
-    ks.fill_direct = &fill_direct_tables<DIM, K>;
-  }
-  if constexpr (DIM == 2) {
-    ks.persist = &launch_persist<real, DIM, K>;
-    ks.prepare_persist = &prepare_persist<real, DIM, K>;
-    ks.stage_fused = &launch_stage_fused<real, K>;
-    ks.prepare_fused = &prepare_stage_fused<real, K>;
-  }
-  if constexpr (std::is_same<real, float>::value && DIM == 2 && K >= 1 && K <= 3) {
-    ks.cell_tc = &launch_cell_tc<K, false>;
-    ks.prepare_tc = &prepare_cell_tc<K, false>;
-    ks.fill_tc = &fill_tc_tables<K>;
+  // the tensor-product basis has the stage, timestep, projection and
+  // diagnostic kernels only
+  if constexpr (B == 0) {
+    ks.limit = &launch_limit<real, DIM, K>;
+    ks.node_weights = &launch_node_weights<real, DIM, K>;
+    ks.adj_face = &launch_adj_face<real, DIM, K>;
+    ks.adj_cell = &launch_adj_cell<real, DIM, K>;
+    if constexpr (std::is_same<real, float>::value && DIM == 2) {
+      ks.cell_direct = &launch_cell_direct<DIM, K>;
+      ks.fill_direct = &fill_direct_tables<DIM, K>;
+    }
+    if constexpr (DIM == 2) {
+      ks.persist = &launch_persist<real, DIM, K>;
+      ks.prepare_persist = &prepare_persist<real, DIM, K>;
+      ks.stage_fused = &launch_stage_fused<real, K>;
+      ks.prepare_fused = &prepare_stage_fused<real, K>;
+    }
+    if constexpr (std::is_same<real, float>::value && DIM == 2 && K >= 1 && K <= 3) {
+      ks.cell_tc = &launch_cell_tc<K, false>;
+      ks.prepare_tc = &prepare_cell_tc<K, false>;
+      ks.fill_tc = &fill_tc_tables<K>;
+    }
   }
   return ks;
 }

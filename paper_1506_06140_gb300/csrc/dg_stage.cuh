@@ -30,11 +30,27 @@ __host__ __device__ constexpr int bidx(int a, int b, int c) {
   return pos + (g - a - b);
 }
 
+// The 2D basis as seen by the sum-factorised loops: for x exponent a the y
+// exponents run to lim(a) (K - a for total degree, K for the tensor product),
+// and idx(a, b) is the position of phi_(a,b): by total degree, then a
+// descending (the tensor product continues the order past degree K).
+template <int K, int B>
+struct Basis2 {
+  __host__ __device__ static constexpr int lim(int a) { return B ? K : K - a; }
+  __host__ __device__ static constexpr int idx(int a, int b) {
+    if (B == 0 || a + b <= K) return bidx<2>(a, b, 0);
+    const int m = a + b - 1 - K;  // complete degrees above K before a + b
+    return (K + 1) * (K + 2) / 2 + m * K - m * (m - 1) / 2 + (K - a);
+  }
+};
+
 // ---------------------------------------------------------------------------
 // modal -> nodal: u(x_i, y_j[, z_k]) = sum_l w_l phi_l, factorised
-template <typename real, int DIM, int K>
+template <typename real, int DIM, int K, int B = 0>
 __device__ __forceinline__ void modal_to_nodal(const Tab1D<real>& T, const real* w, real* u) {
   constexpr int K1 = K + 1;
+  static_assert(DIM == 2 || B == 0, "tensor-product basis: 2D");
+  using BS = Basis2<K, B>;
   if constexpr (DIM == 2) {
     real t[K1][K1];  // t[a][j] = sum_b w_(a,b) P_b(y_j)
 #pragma unroll
@@ -43,7 +59,7 @@ __device__ __forceinline__ void modal_to_nodal(const Tab1D<real>& T, const real*
       for (int j = 0; j < K1; ++j) {
         real s = real(0);
 #pragma unroll
-        for (int b = 0; b <= K - a; ++b) s += w[bidx<2>(a, b, 0)] * T.P[b][j];
+        for (int b = 0; b <= BS::lim(a); ++b) s += w[BS::idx(a, b)] * T.P[b][j];
         t[a][j] = s;
       }
 #pragma unroll
@@ -96,9 +112,11 @@ __device__ __forceinline__ void modal_to_nodal(const Tab1D<real>& T, const real*
 
 // volume integral of one variable: acc_l += sum_d sum_q f_d(q) dphi_l/dxi_d w_q
 // (f_d given at the points, q = i + K1 (j + K1 k))
-template <typename real, int DIM, int K, int D>
+template <typename real, int DIM, int K, int D, int B = 0>
 __device__ __forceinline__ void volume_dir(const Tab1D<real>& T, const real* f, real* acc) {
   constexpr int K1 = K + 1;
+  static_assert(DIM == 2 || B == 0, "tensor-product basis: 2D");
+  using BS = Basis2<K, B>;
   if constexpr (DIM == 2) {
     // derivative along axis D, weight along the other axis
 #pragma unroll
@@ -109,25 +127,25 @@ __device__ __forceinline__ void volume_dir(const Tab1D<real>& T, const real* f, 
 #pragma unroll
         for (int i = 0; i < K1; ++i) g += f[D == 0 ? (i + K1 * o) : (o + K1 * i)] * T.DW[e][i];
 #pragma unroll
-        for (int e2 = 0; e2 <= K - e; ++e2)
-          acc[D == 0 ? bidx<2>(e, e2, 0) : bidx<2>(e2, e, 0)] += g * T.PW[e2][o];
+        for (int e2 = 0; e2 <= BS::lim(e); ++e2)
+          acc[D == 0 ? BS::idx(e, e2) : BS::idx(e2, e)] += g * T.PW[e2][o];
       }
   } else {
-    // axes: D (derivative), A and B the other two in increasing order
+    // axes: D (derivative), A and BB the other two in increasing order
     constexpr int A = D == 0 ? 1 : 0;
-    constexpr int B = D == 2 ? 1 : 2;
+    constexpr int BB = D == 2 ? 1 : 2;
     auto q_of = [](int d, int a, int b) {
       int x[3];
       x[D] = d;
       x[A] = a;
-      x[B] = b;
+      x[BB] = b;
       return x[0] + K1 * (x[1] + K1 * x[2]);
     };
     auto l_of = [](int ed, int ea, int eb) {
       int e[3];
       e[D] = ed;
       e[A] = ea;
-      e[B] = eb;
+      e[BB] = eb;
       return bidx<3>(e[0], e[1], e[2]);
     };
 #pragma unroll
@@ -159,9 +177,11 @@ __device__ __forceinline__ void volume_dir(const Tab1D<real>& T, const real* f, 
 // projection of a field given at the volume points onto the basis:
 // acc_l += h * sum_q s_q phi_l(xi_q) w_q (q = i + K1 (j + K1 k)), sum-factorised
 // with the weighted 1D tables along every axis
-template <typename real, int DIM, int K>
+template <typename real, int DIM, int K, int B = 0>
 __device__ __forceinline__ void source_project(const Tab1D<real>& T, const real* s, real h, real* acc) {
   constexpr int K1 = K + 1;
+  static_assert(DIM == 2 || B == 0, "tensor-product basis: 2D");
+  using BS = Basis2<K, B>;
   if constexpr (DIM == 2) {
 #pragma unroll
     for (int e1 = 0; e1 <= K; ++e1) {
@@ -174,11 +194,11 @@ __device__ __forceinline__ void source_project(const Tab1D<real>& T, const real*
         g[i2] = t;
       }
 #pragma unroll
-      for (int e2 = 0; e2 <= K - e1; ++e2) {
+      for (int e2 = 0; e2 <= BS::lim(e1); ++e2) {
         real t = real(0);
 #pragma unroll
         for (int i2 = 0; i2 < K1; ++i2) t += g[i2] * T.PW[e2][i2];
-        acc[bidx<2>(e1, e2, 0)] += h * t;
+        acc[BS::idx(e1, e2)] += h * t;
       }
     }
   } else {
@@ -220,11 +240,13 @@ __device__ __forceinline__ void source_project(const Tab1D<real>& T, const real*
 // acc_l -= sg * sum_q fbar_q phi_l(face point q) w_q, with the face's points
 // given by the weighted tables PW0 (and PW1): PW[e][q] = P_e(x_q) w_q at the
 // Gauss nodes (T.PW), or at a half of them for sub-faces (T.PWH[h]).
-template <typename real, int DIM, int K, int DIR, int S>
+template <typename real, int DIM, int K, int DIR, int S, int B = 0>
 __device__ __forceinline__ void surface_side(const Tab1D<real>& T, const real (&PW0)[4][4],
                                              const real (&PW1)[4][4], const real* fq, real scale,
                                              real* acc) {
   constexpr int K1 = K + 1;
+  static_assert(DIM == 2 || B == 0, "tensor-product basis: 2D");
+  using BS = Basis2<K, B>;
   const real ssg = S ? -scale : scale;  // times minus the outward normal's sign
   if constexpr (DIM == 2) {
     constexpr int TA = DIR == 0 ? 1 : 0;
@@ -239,11 +261,11 @@ __device__ __forceinline__ void surface_side(const Tab1D<real>& T, const real (&
 #pragma unroll
     for (int ed = 0; ed <= K; ++ed)
 #pragma unroll
-      for (int et = 0; et <= K - ed; ++et)
-        acc[TA == 1 ? bidx<2>(ed, et, 0) : bidx<2>(et, ed, 0)] += T.PE[S][ed] * G[et];
+      for (int et = 0; et <= BS::lim(ed); ++et)
+        acc[TA == 1 ? BS::idx(ed, et) : BS::idx(et, ed)] += T.PE[S][ed] * G[et];
   } else {
     constexpr int A = DIR == 0 ? 1 : 0;  // tangential axes, increasing
-    constexpr int B = DIR == 2 ? 1 : 2;
+    constexpr int BB = DIR == 2 ? 1 : 2;
     real H[K1][K1];  // [ea][qb] = sum_qa f w P_ea
 #pragma unroll
     for (int ea = 0; ea <= K; ++ea)
@@ -267,7 +289,7 @@ __device__ __forceinline__ void surface_side(const Tab1D<real>& T, const real (&
           int e[3];
           e[DIR] = ed;
           e[A] = ea;
-          e[B] = eb;
+          e[BB] = eb;
           acc[bidx<3>(e[0], e[1], e[2])] += T.PE[S][ed] * s;
         }
       }
@@ -275,19 +297,21 @@ __device__ __forceinline__ void surface_side(const Tab1D<real>& T, const real (&
 }
 
 // trace of one variable on side (DIR, S) at the face points given by PT0/PT1
-template <typename real, int DIM, int K, int DIR>
+template <typename real, int DIM, int K, int DIR, int B = 0>
 __device__ __forceinline__ void face_trace(const Tab1D<real>& T, const real* w, int s,
                                            const real (&PT0)[4][4], const real (&PT1)[4][4],
                                            real* u) {
   constexpr int K1 = K + 1;
+  static_assert(DIM == 2 || B == 0, "tensor-product basis: 2D");
+  using BS = Basis2<K, B>;
   if constexpr (DIM == 2) {
     real t[K1];
 #pragma unroll
     for (int et = 0; et <= K; ++et) {
       real acc = real(0);
 #pragma unroll
-      for (int ed = 0; ed <= K - et; ++ed)
-        acc += w[DIR == 0 ? bidx<2>(ed, et, 0) : bidx<2>(et, ed, 0)] * T.PE[s][ed];
+      for (int ed = 0; ed <= BS::lim(et); ++ed)
+        acc += w[DIR == 0 ? BS::idx(ed, et) : BS::idx(et, ed)] * T.PE[s][ed];
       t[et] = acc;
     }
 #pragma unroll
@@ -299,7 +323,7 @@ __device__ __forceinline__ void face_trace(const Tab1D<real>& T, const real* w, 
     }
   } else {
     constexpr int A = DIR == 0 ? 1 : 0;
-    constexpr int B = DIR == 2 ? 1 : 2;
+    constexpr int BB = DIR == 2 ? 1 : 2;
     real t[K1][K1];
 #pragma unroll
     for (int ea = 0; ea <= K; ++ea)
@@ -311,7 +335,7 @@ __device__ __forceinline__ void face_trace(const Tab1D<real>& T, const real* w, 
           int e[3];
           e[DIR] = ed;
           e[A] = ea;
-          e[B] = eb;
+          e[BB] = eb;
           acc += w[bidx<3>(e[0], e[1], e[2])] * T.PE[s][ed];
         }
         t[ea][eb] = acc;
@@ -355,28 +379,28 @@ struct FaceTile {
   static constexpr size_t smem(int fb) { return (size_t)2 * S::NV * S::QF * fb * sizeof(real); }
 };
 
-template <typename real, int DIM, int K, int DIR>
+template <typename real, int DIM, int K, int DIR, int B = 0>
 __device__ __forceinline__ void trace_side(const StageArgs<real>& a, int cell, int s, int var,
                                            int v, real* u) {
-  using S = Shape<DIM, K>;
+  using S = Shape<DIM, K, B>;
   const Tab1D<real>& T = a.t1;
   const int nc = a.m.ncells;
   real w[S::N];
 #pragma unroll
   for (int l = 0; l < S::N; ++l) w[l] = a.U[(size_t)(v * S::N + l) * nc + cell];
   if (var == 0) {
-    face_trace<real, DIM, K, DIR>(T, w, s, T.P, T.P, u);
+    face_trace<real, DIM, K, DIR, B>(T, w, s, T.P, T.P, u);
   } else {
     const int h0 = (var - 1) & 1, h1 = ((var - 1) >> 1) & 1;
-    face_trace<real, DIM, K, DIR>(T, w, s, T.PH[h0], T.PH[h1], u);
+    face_trace<real, DIM, K, DIR, B>(T, w, s, T.PH[h0], T.PH[h1], u);
   }
 }
 
 // the work of one block (faces bid*FB ..) with FB*NV threads; the kernel
 // below and the persistent step kernel run it
-template <typename real, int DIM, int K, int FB>
+template <typename real, int DIM, int K, int FB, int B = 0>
 __device__ __forceinline__ void face_flux_body(const StageArgs<real>& a, int bid) {
-  using S = Shape<DIM, K>;
+  using S = Shape<DIM, K, B>;
   constexpr int THREADS = FB * S::NV;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   real* sT = reinterpret_cast<real*>(smem_raw);  // [2 sides][NV][QF][FB]
@@ -392,9 +416,9 @@ __device__ __forceinline__ void face_flux_body(const StageArgs<real>& a, int bid
     real um[S::QF], up[S::QF];
     // the minus cell sees the face as its + side (s = 1), the plus cell as its - side
     auto trace = [&](int cell, int s, int var, real* u) {
-      if (dir == 0) trace_side<real, DIM, K, 0>(a, cell, s, var, v, u);
-      else if (dir == 1) trace_side<real, DIM, K, 1>(a, cell, s, var, v, u);
-      else if constexpr (DIM == 3) trace_side<real, DIM, K, DIM - 1>(a, cell, s, var, v, u);
+      if (dir == 0) trace_side<real, DIM, K, 0, B>(a, cell, s, var, v, u);
+      else if (dir == 1) trace_side<real, DIM, K, 1, B>(a, cell, s, var, v, u);
+      else if constexpr (DIM == 3) trace_side<real, DIM, K, DIM - 1, B>(a, cell, s, var, v, u);
     };
     if (cm >= 0) trace(cm, 1, vm, um);
     if (cp >= 0) trace(cp, 0, vp, up);
@@ -435,10 +459,10 @@ __device__ __forceinline__ void face_flux_body(const StageArgs<real>& a, int bid
   (void)dir;
 }
 
-template <typename real, int DIM, int K, int FB>
+template <typename real, int DIM, int K, int FB, int B = 0>
 __global__ void __launch_bounds__(FB * Shape<DIM, K>::NV)
     face_flux_kernel(const StageArgs<real> a) {
-  face_flux_body<real, DIM, K, FB>(a, blockIdx.x);
+  face_flux_body<real, DIM, K, FB, B>(a, blockIdx.x);
 }
 
 // ===========================================================================
@@ -498,7 +522,7 @@ __device__ __forceinline__ void prefetch_faces(const StageArgs<real>& a, int c, 
   }
 }
 
-template <typename real, int DIM, int K, int SD>
+template <typename real, int DIM, int K, int SD, int B = 0>
 __device__ __forceinline__ void surface_from_faces(const StageArgs<real>& a, int c, int v,
                                                    unsigned coarse, const real* fpre, real* acc) {
   using S = Shape<DIM, K>;
@@ -515,7 +539,7 @@ __device__ __forceinline__ void surface_from_faces(const StageArgs<real>& a, int
 #pragma unroll
       for (int q = 0; q < S::QF; ++q) fq[q] = a.F[((size_t)v * S::QF + q) * nf + e0];
     }
-    surface_side<real, DIM, K, DIR, SS>(T, T.PW, T.PW, fq, real(1), acc);
+    surface_side<real, DIM, K, DIR, SS, B>(T, T.PW, T.PW, fq, real(1), acc);
   } else {
     const int e0 = a.m.sface[(size_t)SD * nc + c];
     // coarse side of a hanging face: NSUB sub-faces in quadrant order
@@ -524,7 +548,7 @@ __device__ __forceinline__ void surface_from_faces(const StageArgs<real>& a, int
     for (int h = 0; h < S::NSUB; ++h) {
 #pragma unroll
       for (int q = 0; q < S::QF; ++q) fq[q] = a.F[((size_t)v * S::QF + q) * nf + e0 + h];
-      surface_side<real, DIM, K, DIR, SS>(T, T.PWH[h & 1], T.PWH[(h >> 1) & 1], fq, sub, acc);
+      surface_side<real, DIM, K, DIR, SS, B>(T, T.PWH[h & 1], T.PWH[(h >> 1) & 1], fq, sub, acc);
     }
   }
 }
@@ -567,9 +591,9 @@ __device__ __forceinline__ void stage_epilogue(const StageArgs<real>& a, int c, 
 
 // the work of one block (cells bid*TC ..) with TC*NV threads; the kernel
 // below and the persistent step kernel run it
-template <typename real, int DIM, int K, int TC, bool GRAV = false>
+template <typename real, int DIM, int K, int TC, bool GRAV = false, int B = 0>
 __device__ __forceinline__ void cell_update_body(const StageArgs<real>& a, int bid) {
-  using S = Shape<DIM, K>;
+  using S = Shape<DIM, K, B>;
   constexpr int NV = S::NV, Q = S::Q, N = S::N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   real* sU = reinterpret_cast<real*>(smem_raw);    // [NV][Q][TC]
@@ -593,7 +617,7 @@ __device__ __forceinline__ void cell_update_body(const StageArgs<real>& a, int b
     w[l] = valid ? a.U[(size_t)(v * N + l) * nc + c] : ((v == 0 && l == 0) ? real(1) : real(0));
   {
     real u[Q];
-    modal_to_nodal<real, DIM, K>(T, w, u);
+    modal_to_nodal<real, DIM, K, B>(T, w, u);
 #pragma unroll
     for (int q = 0; q < Q; ++q) sU[(v * Q + q) * TC + tc] = u[q];
   }
@@ -623,23 +647,23 @@ __device__ __forceinline__ void cell_update_body(const StageArgs<real>& a, int b
     real f[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) f[q] = sF[((0 * NV + v) * Q + q) * TC + tc];
-    volume_dir<real, DIM, K, 0>(T, f, acc);
+    volume_dir<real, DIM, K, 0, B>(T, f, acc);
 #pragma unroll
     for (int q = 0; q < Q; ++q) f[q] = sF[((1 * NV + v) * Q + q) * TC + tc];
-    volume_dir<real, DIM, K, 1>(T, f, acc);
+    volume_dir<real, DIM, K, 1, B>(T, f, acc);
     if constexpr (DIM == 3) {
 #pragma unroll
       for (int q = 0; q < Q; ++q) f[q] = sF[((2 * NV + v) * Q + q) * TC + tc];
-      volume_dir<real, DIM, K, DIM - 1>(T, f, acc);
+      volume_dir<real, DIM, K, DIM - 1, B>(T, f, acc);
     }
   }
-  surface_from_faces<real, DIM, K, 0>(a, c, v, coarse, PF ? fpre[0] : nullptr, acc);
-  surface_from_faces<real, DIM, K, 1>(a, c, v, coarse, PF ? fpre[1] : nullptr, acc);
-  surface_from_faces<real, DIM, K, 2>(a, c, v, coarse, PF ? fpre[2 % (PF ? 2 * DIM : 1)] : nullptr, acc);
-  surface_from_faces<real, DIM, K, 3>(a, c, v, coarse, PF ? fpre[3 % (PF ? 2 * DIM : 1)] : nullptr, acc);
+  surface_from_faces<real, DIM, K, 0, B>(a, c, v, coarse, PF ? fpre[0] : nullptr, acc);
+  surface_from_faces<real, DIM, K, 1, B>(a, c, v, coarse, PF ? fpre[1] : nullptr, acc);
+  surface_from_faces<real, DIM, K, 2, B>(a, c, v, coarse, PF ? fpre[2 % (PF ? 2 * DIM : 1)] : nullptr, acc);
+  surface_from_faces<real, DIM, K, 3, B>(a, c, v, coarse, PF ? fpre[3 % (PF ? 2 * DIM : 1)] : nullptr, acc);
   if constexpr (DIM == 3) {
-    surface_from_faces<real, DIM, K, 4>(a, c, v, coarse, PF ? fpre[4 % (PF ? 2 * DIM : 1)] : nullptr, acc);
-    surface_from_faces<real, DIM, K, 5>(a, c, v, coarse, PF ? fpre[5 % (PF ? 2 * DIM : 1)] : nullptr, acc);
+    surface_from_faces<real, DIM, K, 4, B>(a, c, v, coarse, PF ? fpre[4 % (PF ? 2 * DIM : 1)] : nullptr, acc);
+    surface_from_faces<real, DIM, K, 5, B>(a, c, v, coarse, PF ? fpre[5 % (PF ? 2 * DIM : 1)] : nullptr, acc);
   }
 
   // 4. epilogue
@@ -661,16 +685,16 @@ __device__ __forceinline__ void cell_update_body(const StageArgs<real>& a, int b
           sq[q] = t;
         }
       }
-      source_project<real, DIM, K>(T, sq, real(1) / (real(1 << DIM) * pre), acc);
+      source_project<real, DIM, K, B>(T, sq, real(1) / (real(1 << DIM) * pre), acc);
     }
   }
   stage_epilogue<real, N>(a, c, v, pre * (a.dt ? real(a.dt[pb]) : real(1)), acc, w);
 }
 
-template <typename real, int DIM, int K, int TC, bool GRAV = false>
+template <typename real, int DIM, int K, int TC, bool GRAV = false, int B = 0>
 __global__ void __launch_bounds__(TC * Shape<DIM, K>::NV, CellTile<real, DIM, K>::min_blocks(TC))
     cell_update_kernel(const StageArgs<real> a) {
-  cell_update_body<real, DIM, K, TC, GRAV>(a, blockIdx.x);
+  cell_update_body<real, DIM, K, TC, GRAV, B>(a, blockIdx.x);
 }
 
 }  // namespace dgi

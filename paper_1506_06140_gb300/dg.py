@@ -18,6 +18,7 @@ DG_OK, DG_ERR_ARG, DG_ERR_CUDA, DG_ERR_OOM, DG_ERR_NONPHYSICAL, DG_ERR_TIMEOUT, 
 DG_BC_PERIODIC, DG_BC_TRANSMISSIVE = 0, 1
 LIMITERS = {"none": 0, "component": 1, "characteristic": 2}
 PRECISIONS = {"fp64": 0, "fp32": 1, "fp32_tc": 2, "mixed": 3, "mixed_tc": 4}
+BASES = {"total": 0, "tensor": 1}
 
 EXPORTS = ["dg_default_options", "dg_create", "dg_destroy", "dg_last_error", "dg_sizes",
            "dg_quad_points", "dg_l1_points", "dg_project", "dg_rhs", "dg_compute_dt",
@@ -40,7 +41,8 @@ class MeshDesc(C.Structure):
 class Options(C.Structure):
     _fields_ = [("rk_order", C.c_int), ("cfl", C.c_double), ("slope_limiter", C.c_int),
                 ("beta", C.c_double), ("Mtilde", C.c_double), ("positivity", C.c_int),
-                ("eps", C.c_double), ("precision", C.c_int), ("autotune", C.c_int)]
+                ("eps", C.c_double), ("precision", C.c_int), ("autotune", C.c_int),
+                ("basis", C.c_int)]
 
 
 class DGError(RuntimeError):
@@ -143,9 +145,12 @@ class Solver:
     """One DG problem on the current CUDA device (see include/dg.h)."""
 
     def __init__(self, mesh, k, gamma=1.4, rk_order=3, cfl=0.2, limiter="none", beta=1.0,
-                 Mtilde=0.5, positivity=False, eps=1e-10, precision="fp64", autotune=False):
+                 Mtilde=0.5, positivity=False, eps=1e-10, precision="fp64", autotune=False,
+                 basis="total"):
         """mesh: one mesh dict, or a list of them for an ensemble of
-        independent problems advanced together (dg_create_batch)."""
+        independent problems advanced together (dg_create_batch).
+        basis: "total" (the paper's total-degree space) or "tensor" (Q_k,
+        (k+1)^2 coefficients per variable; 2D, fp64/fp32, no limiter)."""
         L = load()
         self._L = L
         meshes = list(mesh) if isinstance(mesh, (list, tuple)) else [mesh]
@@ -175,7 +180,9 @@ class Solver:
         opt.positivity, opt.eps = int(bool(positivity)), eps
         opt.precision = PRECISIONS[precision]
         opt.autotune = int(bool(autotune))
+        opt.basis = BASES[basis]
         self.precision = precision
+        self.basis = basis
         self.dtype = torch.float64 if precision in ("fp64", "mixed", "mixed_tc") else torch.float32
         torch.cuda.init()
         h = C.c_void_p()
