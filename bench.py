@@ -360,18 +360,19 @@ def run_gpu(args, rank, world, local_rank):
                 torch.cuda.synchronize()
                 ev = ev[:1]
             else:
+                # each timed step is one dg_advance of one step (a CUDA graph of
+                # the step's kernels, recorded in the warm-up), L2 flushed before it
                 for _ in range(args.warmup):
-                    s.rk_step(W)
+                    s.advance(W, 1)
                 limited = WORKLOADS[args.workload]["limiter"] != "none"
                 if limited:
                     s.limiter_counts(reset=True)
                 torch.cuda.synchronize()
                 barrier()
-                s.profile_begin()
                 for i in range(args.steps):
                     flush.zero_()  # evict the working set from L2 before each timed step
                     ev[i][0].record(stream)
-                    s.rk_step(W)
+                    s.advance(W, 1)
                     ev[i][1].record(stream)
                 torch.cuda.synchronize()
         paths = None
@@ -392,13 +393,18 @@ def run_gpu(args, rank, world, local_rank):
                      "note": "dg_advance as a CUDA graph of the stage kernels (default, timed above) "
                              "or as one persistent cooperative kernel with grid barriers"}
             del Wp
-        if graph:
-            # per-kernel durations from a separate, instrumented pass of the same steps
-            s.profile_begin()
-            for _ in range(args.steps):
-                s.rk_step(W)
-            torch.cuda.synchronize()
+        # per-kernel durations from a separate pass of the same one-step graphs,
+        # recorded with an event pair around every kernel (dg_profile_begin)
+        cnt_snap = s.limiter_counts().cpu().numpy()  # limiter activity up to here
+        Wp = W.clone()
+        s.profile_begin()
+        for _ in range(args.steps):
+            if not graph:
+                flush.zero_()
+            s.advance(Wp, 1)
+        torch.cuda.synchronize()
         prof = s.profile_end()
+        del Wp
         barrier()
         ms = sum(a.elapsed_time(b) for a, b in ev)
         ms = max_over_ranks(ms)
@@ -418,7 +424,7 @@ def run_gpu(args, rank, world, local_rank):
             L0, L1 = ang(W0), ang(W)
             t0, t1 = s.totals(W0).cpu().numpy(), s.totals(W).cpu().numpy()
             passes = s.n_cells * WORKLOADS[args.workload]["stages"] * (args.steps + args.warmup)
-            cnt = s.limiter_counts(reset=True).cpu().numpy()
+            cnt = cnt_snap
             diag = {"angular_momentum_drift_rel": abs(L1 - L0) / abs(L0),
                     "mass_drift_rel": float(abs(t1[0] - t0[0]) / abs(t0[0])),
                     "positivity_limited_fraction": float(cnt[1]) / passes,
@@ -428,7 +434,7 @@ def run_gpu(args, rank, world, local_rank):
                             "to rounding (GPU test)"}
         if WORKLOADS[args.workload]["limiter"] != "none":
             # limiter activity over the timed steps and conservation drift from the initial state
-            cnt = s.limiter_counts(reset=True).cpu().numpy()
+            cnt = cnt_snap
             passes = s.n_cells * WORKLOADS[args.workload]["stages"] * args.steps
             t0, t1 = s.totals(W0).cpu().numpy(), s.totals(W).cpu().numpy()
             diag = {"slope_limited_fraction": float(cnt[0]) / passes,
@@ -770,14 +776,17 @@ def run_adjoint(args):
 L1_SIZES = (64, 128, 256)
 L1_T_END = 2.0
 L1_EQUAL_TOL = 1.05  # "equal" L1: within 5% of the FP64 error
+L1_CHUNK = 100  # steps per graph launch in the L1 ladder
 
 
 def l1_ladder(precisions, sizes, t_end, verbose=False, basis="total"):
     """L1 density error of the vortex against its closed form after t_end
     (fixed timestep: the CFL value of the initial state, rounded so that
     t_end is reached exactly), per precision and resolution, with the device
-    time per RK stage measured by CUDA events around the steps.  With the
-    tensor-product basis the rows' precision reads "tensor_<precision>"."""
+    time per RK stage measured by CUDA events around the steps (run as
+    dg_advance_dt graphs of L1_CHUNK steps, recorded before the timed run).
+    With the tensor-product basis the rows' precision reads
+    "tensor_<precision>"."""
     import torch
     from paper_1506_06140_gb300 import dg
     from paper_1506_06140_gb300 import workloads as wl
@@ -789,12 +798,17 @@ def l1_ladder(precisions, sizes, t_end, verbose=False, basis="total"):
             dt = s.compute_dt(W).item()  # the vortex translates; its CFL timestep stays put
             nsteps = int(math.ceil(t_end / dt))
             dt = t_end / nsteps
+            chunks = [L1_CHUNK] * (nsteps // L1_CHUNK) + ([nsteps % L1_CHUNK] if nsteps % L1_CHUNK else [])
+            W0 = W.clone()
+            for c in sorted(set(chunks)):  # record the graphs (keyed by W, steps, dt)
+                s.advance(W, c, dt=dt)
+            W.copy_(W0)
             st = torch.cuda.current_stream()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
             e0.record(st)
-            for _ in range(nsteps):
-                s.rk_step(W, dt)
+            for c in chunks:
+                s.advance(W, c, dt=dt)
             e1.record(st)
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1)

@@ -221,6 +221,12 @@ int dg_rk_step(dg_handle* h, void* W_dev, double dt, double* dt_used_dev, void* 
  * given key records the graph (make it outside any stream capture). */
 int dg_advance(dg_handle* h, void* W_dev, int n_steps, double* dt_hist_dev, void* stream);
 
+/* n_steps steps in place with the fixed timestep dt (> 0, else DG_ERR_ARG),
+ * as dg_rk_step with that dt, recorded once into a CUDA graph per (W_dev,
+ * n_steps, dt) and replayed (convergence and accuracy studies that must end
+ * at a given time).  Always a graph, whatever dg_set_advance_mode says. */
+int dg_advance_dt(dg_handle* h, void* W_dev, int n_steps, double dt, void* stream);
+
 /* ---- ensembles of independent problems --------------------------------
  * dg_create_batch: one handle for n_problems independent problems (same dim,
  * uniform meshes, equal gamma -- DG_ERR_UNSUPPORTED otherwise) advanced
@@ -358,10 +364,12 @@ int dg_cell_levels(const dg_handle* h, int32_t* host_out);
 
 /* ---- instrumentation ---------------------------------------------------
  * Per-kernel timing: while enabled, every kernel launch of the handle is
- * bracketed by two CUDA events recorded on the launch stream (not inside
- * dg_advance's graphs).  dg_profile_end waits for the recorded events and
- * returns, per kernel kind, the number of launches and the summed device
- * time in milliseconds. */
+ * bracketed by two CUDA events recorded on the launch stream.  dg_advance and
+ * dg_advance_dt then replay graphs recorded with those event pairs as
+ * event-record nodes (kept apart from the unprofiled graphs) and wait for
+ * each replay on the host (synchronous while profiling).  dg_profile_end
+ * waits for the recorded events and returns, per kernel kind, the number of
+ * launches and the summed device time in milliseconds. */
 enum { DG_KERNEL_FACE = 0, DG_KERNEL_CELL = 1, DG_KERNEL_LIMIT = 2, DG_KERNEL_DT = 3,
        DG_KERNEL_OTHER = 4, DG_KERNEL_ADJOINT = 5, DG_KERNEL_KINDS = 6 };
 int dg_profile_begin(dg_handle* h);

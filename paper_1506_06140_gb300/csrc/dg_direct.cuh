@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(DIRECT_THREADS) cell_update_direct_kernel(cons
       w[v][l] = a.U[(size_t)(v * N + l) * nc + c];
       acc[v][l] = 0.0f;
     }
-  const float g1 = (float)a.gamma - 1.0f;
+  const float g1 = a.gm1;
   // volume: at each point, the state, the fluxes of all directions, and their
   // products with the weighted basis gradients
 #pragma unroll

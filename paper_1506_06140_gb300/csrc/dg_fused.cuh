@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(FusedTile<real, K>::THREADS) stage_fused_kerne
   __syncthreads();
 
   // 2. HLLC at the points of every face the tile owns; item (cell, side, point)
-  const real gamma = real(a.gamma);
+  const real gamma = a.gam;
   for (int item = threadIdx.x; item < TC * 4 * QF; item += FT::THREADS) {
     const int ti = item % TC, s = (item / TC) % 4, q = item / (4 * TC);
     const int gxi = x0 + ti % FT::TX, gyi = y0 + ti / FT::TX;
@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(FusedTile<real, K>::THREADS) stage_fused_kerne
   }
 
   // 3. point fluxes (the nodal values are read before this thread overwrites them)
-  const real g1 = real(a.gamma) - real(1);
+  const real g1 = a.gm1;
   for (int q = v; q < Q; q += NV) {
     real u[NV];
 #pragma unroll

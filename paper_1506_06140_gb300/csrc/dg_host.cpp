@@ -434,7 +434,8 @@ struct dg_handle {
   Program prog_step;         // limited as configured
   Program prog_free;         // unlimited (adjoint recomputation)
   cudaStream_t cap_stream = nullptr;
-  std::map<std::tuple<void*, int, void*>, cudaGraphExec_t> graphs;
+  // dg_advance / dg_advance_dt graphs per (W, n_steps, dt history, fixed dt; 0 = CFL)
+  std::map<std::tuple<void*, int, void*, double>, cudaGraphExec_t> graphs;
   std::vector<cudaGraph_t> graph_defs;
   // dg_advance as one persistent kernel: mode, plans per (W, dt history)
   // with their largest phase's block count, the grid barrier's words
@@ -474,6 +475,17 @@ struct dg_handle {
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
   std::vector<std::pair<int, size_t>> ev_marks;  // (kind, index of the start event)
+  // dg_advance while profiling: graphs recorded with their event pairs as
+  // event-record nodes (each with its own events), and the device times of
+  // their replays summed per kernel kind
+  struct ProfGraph {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<cudaEvent_t> ev;
+    std::vector<std::pair<int, size_t>> marks;
+  };
+  std::map<std::tuple<void*, int, void*, double>, ProfGraph> pgraphs;
+  double prof_ms[DG_KERNEL_KINDS] = {};
+  int prof_n[DG_KERNEL_KINDS] = {};
 };
 
 namespace {
@@ -505,11 +517,13 @@ cudaError_t timed(dg_handle* h, int kind, cudaStream_t s, F&& launch) {
   }
   const size_t i0 = h->ev_used;
   h->ev_used += 2;
-  cudaError_t r = cudaEventRecord(h->ev_pool[i0], s);
+  // external records: inside a stream capture they become event-record
+  // nodes of the graph (recorded at every replay), elsewhere plain records
+  cudaError_t r = cudaEventRecordWithFlags(h->ev_pool[i0], s, cudaEventRecordExternal);
   if (r != cudaSuccess) return r;
   r = launch();
   if (r != cudaSuccess) return r;
-  r = cudaEventRecord(h->ev_pool[i0 + 1], s);
+  r = cudaEventRecordWithFlags(h->ev_pool[i0 + 1], s, cudaEventRecordExternal);
   h->ev_marks.push_back({kind, i0});
   return r;
 }
@@ -893,6 +907,11 @@ int finish_mark(dg_handle* h, int32_t* flags_host, int64_t* n_cells_new, int64_t
 void drop_graphs(dg_handle* h) {
   for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
   h->graphs.clear();
+  for (auto& kv : h->pgraphs) {
+    cudaGraphExecDestroy(kv.second.exec);
+    for (cudaEvent_t e : kv.second.ev) cudaEventDestroy(e);
+  }
+  h->pgraphs.clear();
   for (auto g : h->graph_defs) cudaGraphDestroy(g);
   h->graph_defs.clear();
   for (auto& kv : h->plans) cudaFree(kv.second.first);  // (synchronises the device)
@@ -921,6 +940,8 @@ int stage_launch(dg_handle* h, const StageArgs<real>& a, cudaStream_t s, const O
       x.G = h->Gm;
       x.D = h->Dm;
       x.tcB = static_cast<const float*>(h->tcB);
+      x.gamf = (float)h->gamma;
+      x.g1f = x.gamf - 1.0f;
       if (op && h->delta) {
         auto freg = [&](int r) { return static_cast<float*>(h->regs[r - 1]); };
         x.delta = 1;
@@ -974,6 +995,8 @@ StageArgs<real> stage_args(dg_handle* h, const Op& op, const void* U, void* W) {
   a.U = static_cast<const real*>(U);
   a.F = static_cast<real*>(h->F);
   a.gamma = h->gamma;
+  a.gam = (real)h->gamma;
+  a.gm1 = (real)h->gamma - (real)1;
   auto reg = [&](int r) -> real* { return static_cast<real*>(r == 0 ? W : h->regs[r - 1]); };
   a.n_in = op.n_in;
   for (int r = 0; r < op.n_in; ++r) a.in[r] = reg(op.in[r]);
@@ -1645,6 +1668,10 @@ int dg_destroy(dg_handle* h) {
   if (!h) return DG_OK;
   cudaDeviceSynchronize();
   for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+  for (auto& kv : h->pgraphs) {
+    cudaGraphExecDestroy(kv.second.exec);
+    for (cudaEvent_t e : kv.second.ev) cudaEventDestroy(e);
+  }
   for (auto e : h->ev_pool) cudaEventDestroy(e);
   for (auto g : h->graph_defs) cudaGraphDestroy(g);
   for (auto& kv : h->plans) cudaFree(kv.second.first);
@@ -1776,6 +1803,8 @@ int dg_rk_step(dg_handle* h, void* W_dev, double dt, double* dt_used_dev, void* 
   return rk_step_dispatch(h, W_dev, dt, dt_used_dev, static_cast<cudaStream_t>(stream));
 }
 
+static int advance_graph(dg_handle* h, void* W_dev, int n_steps, double dt, double* dt_hist_dev, cudaStream_t s);
+
 int dg_advance(dg_handle* h, void* W_dev, int n_steps, double* dt_hist_dev, void* stream) {
   if (!check_handle(h) || !W_dev || n_steps < 0) return DG_ERR_ARG;
   if (check_gravity(h, "dg_advance") != DG_OK) return DG_ERR_ARG;
@@ -1785,26 +1814,80 @@ int dg_advance(dg_handle* h, void* W_dev, int n_steps, double* dt_hist_dev, void
   if (h->advance_mode == DG_ADVANCE_PERSISTENT && persist_supported(h))
     return h->prec == DG_FP64 ? advance_persistent<double>(h, W_dev, n_steps, dt_hist_dev, s)
                               : advance_persistent<float>(h, W_dev, n_steps, dt_hist_dev, s);
-  auto key = std::make_tuple(W_dev, n_steps, (void*)dt_hist_dev);
+  return advance_graph(h, W_dev, n_steps, 0.0, dt_hist_dev, s);
+}
+
+int dg_advance_dt(dg_handle* h, void* W_dev, int n_steps, double dt, void* stream) {
+  if (!check_handle(h) || !W_dev || n_steps < 0) return DG_ERR_ARG;
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(h, DG_ERR_ARG, "dg_advance_dt: dt must be positive");
+  if (check_gravity(h, "dg_advance_dt") != DG_OK) return DG_ERR_ARG;
+  if (n_steps == 0) return DG_OK;
+  std::lock_guard<std::mutex> lock(h->mu);
+  return advance_graph(h, W_dev, n_steps, dt, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+// records n_steps steps into a graph (on the handle's capture stream)
+static int capture_steps(dg_handle* h, void* W_dev, int n_steps, double dt, double* dt_hist_dev,
+                         cudaGraphExec_t* out) {
+  cudaError_t eb = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (eb != cudaSuccess) return cuda_fail(h, eb, "cudaStreamBeginCapture");
+  int r = DG_OK;
+  for (int i = 0; i < n_steps && r == DG_OK; ++i)
+    r = rk_step_dispatch(h, W_dev, dt, dt_hist_dev ? dt_hist_dev + (size_t)i * h->nprob : nullptr, h->cap_stream);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+  if (r != DG_OK) { if (g) cudaGraphDestroy(g); return r; }
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(out, g, 0);
+  if (e != cudaSuccess) { cudaGraphDestroy(g); return cuda_fail(h, e, "cudaGraphInstantiate"); }
+  h->graph_defs.push_back(g);
+  return DG_OK;
+}
+
+// With profiling on: the steps' graph with an event pair around every kernel
+// (event-record nodes), replayed, waited for, and its kernels' device times
+// added to the handle's sums.
+static int advance_graph_profiled(dg_handle* h, void* W_dev, int n_steps, double dt, double* dt_hist_dev,
+                                  cudaStream_t s) {
+  auto key = std::make_tuple(W_dev, n_steps, (void*)dt_hist_dev, dt);
+  auto it = h->pgraphs.find(key);
+  if (it == h->pgraphs.end()) {
+    dg_handle::ProfGraph pg;
+    // the capture brackets launches with events of its own pool and marks
+    std::swap(h->ev_pool, pg.ev);
+    std::swap(h->ev_marks, pg.marks);
+    const size_t used = h->ev_used;
+    h->ev_used = 0;
+    const int r = capture_steps(h, W_dev, n_steps, dt, dt_hist_dev, &pg.exec);
+    std::swap(h->ev_pool, pg.ev);
+    std::swap(h->ev_marks, pg.marks);
+    h->ev_used = used;
+    if (r != DG_OK) {
+      for (cudaEvent_t e : pg.ev) cudaEventDestroy(e);
+      return r;
+    }
+    it = h->pgraphs.emplace(key, std::move(pg)).first;
+  }
+  DG_CUDA(h, cudaGraphLaunch(it->second.exec, s));
+  DG_CUDA(h, cudaStreamSynchronize(s));
+  for (const auto& mk : it->second.marks) {
+    float ms = 0.0f;
+    DG_CUDA(h, cudaEventElapsedTime(&ms, it->second.ev[mk.second], it->second.ev[mk.second + 1]));
+    h->prof_ms[mk.first] += ms;
+    h->prof_n[mk.first] += 1;
+  }
+  return DG_OK;
+}
+
+// n_steps steps (dt > 0 fixed, else CFL) as one graph launch, recorded on first use
+static int advance_graph(dg_handle* h, void* W_dev, int n_steps, double dt, double* dt_hist_dev, cudaStream_t s) {
+  if (h->profiling) return advance_graph_profiled(h, W_dev, n_steps, dt, dt_hist_dev, s);
+  auto key = std::make_tuple(W_dev, n_steps, (void*)dt_hist_dev, dt);
   auto it = h->graphs.find(key);
   if (it == h->graphs.end()) {
-    const bool prof = h->profiling;
-    h->profiling = false;  // no event records inside a captured graph
-    cudaError_t eb = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
-    if (eb != cudaSuccess) { h->profiling = prof; return cuda_fail(h, eb, "cudaStreamBeginCapture"); }
-    int r = DG_OK;
-    for (int i = 0; i < n_steps && r == DG_OK; ++i)
-      r = rk_step_dispatch(h, W_dev, 0.0, dt_hist_dev ? dt_hist_dev + (size_t)i * h->nprob : nullptr,
-                           h->cap_stream);
-    cudaGraph_t g = nullptr;
-    cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
-    h->profiling = prof;
-    if (r != DG_OK) { if (g) cudaGraphDestroy(g); return r; }
-    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
     cudaGraphExec_t ge = nullptr;
-    e = cudaGraphInstantiate(&ge, g, 0);
-    if (e != cudaSuccess) { cudaGraphDestroy(g); return cuda_fail(h, e, "cudaGraphInstantiate"); }
-    h->graph_defs.push_back(g);
+    const int r = capture_steps(h, W_dev, n_steps, dt, dt_hist_dev, &ge);
+    if (r != DG_OK) return r;
     it = h->graphs.emplace(key, ge).first;
   }
   DG_CUDA(h, cudaGraphLaunch(it->second, s));
@@ -2062,6 +2145,7 @@ int dg_profile_begin(dg_handle* h) {
   h->profiling = true;
   h->ev_used = 0;
   h->ev_marks.clear();
+  for (int i = 0; i < DG_KERNEL_KINDS; ++i) { h->prof_ms[i] = 0.0; h->prof_n[i] = 0; }
   return DG_OK;
 }
 
@@ -2080,6 +2164,14 @@ int dg_profile_end(dg_handle* h, int* launches, double* total_ms, int n_kinds) {
   }
   h->ev_marks.clear();
   h->ev_used = 0;
+  for (int i = 0; i < DG_KERNEL_KINDS; ++i) {  // replays of profiled graphs
+    if (i < n_kinds) {
+      launches[i] += h->prof_n[i];
+      total_ms[i] += h->prof_ms[i];
+    }
+    h->prof_ms[i] = 0.0;
+    h->prof_n[i] = 0;
+  }
   return DG_OK;
 }
 

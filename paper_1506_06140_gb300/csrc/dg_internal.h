@@ -107,6 +107,7 @@ struct StageArgs {
   const real* U = nullptr;
   real* F = nullptr;            // face fluxes [NV][QF][nfaces]
   double gamma = 1.4;
+  real gam = real(1.4), gm1 = real(0.4);  // gamma and gamma - 1 in the state precision (set on the host)
   int n_in = 0, n_out = 0;
   const real* in[MAX_IN] = {nullptr, nullptr, nullptr, nullptr};
   real* out[MAX_OUT] = {nullptr, nullptr, nullptr};
@@ -139,6 +140,7 @@ struct MixedArgs {
   const float* inR[MAX_IN] = {};     // their deltas
   float Cf[MAX_IN] = {};             // their coefficients
   float ckf = 0.0f;                  // coefficient of dt dW/dt
+  float gamf = 1.4f, g1f = 0.4f;     // gamma and gamma - 1 in FP32 (set on the host)
   float* outR = nullptr;             // output delta; nullptr: W += increment (a.out[0] = W)
   // FP32 split of W within a step: Wf = W rounded (weight 0 truncated) and
   // Wlo = the rest of weight 0.  wf_mode 1: the cell kernel writes them (first

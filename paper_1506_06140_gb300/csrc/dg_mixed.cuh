@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(FB * Shape<DIM, K>::NV)
     }
   }
   __syncthreads();
-  const float gamma = (float)a.gamma, g1 = gamma - 1.0f;
+  const float gamma = x.gamf, g1 = x.g1f;
   // HLLC in perturbation form at every (face, point) of the block
   for (int item = threadIdx.x; item < FB * QF; item += THREADS) {
     const int ff = item % FB, q = item / FB;
@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(TC * Shape<DIM, K>::NV)
   __syncthreads();
 
   // 2. flux perturbations at the points of this thread
-  const float g1 = (float)a.gamma - 1.0f;
+  const float g1 = x.g1f;
   {
     float ub[NV];
 #pragma unroll

@@ -438,7 +438,7 @@ __device__ __forceinline__ void face_flux_body(const StageArgs<real>& a, int bid
   }
   __syncthreads();
   // HLLC at every (face, point) of the block
-  const real gamma = real(a.gamma);
+  const real gamma = a.gam;
   for (int item = threadIdx.x; item < FB * S::QF; item += THREADS) {
     const int ff = item % FB, q = item / FB;
     const int f2 = bid * FB + ff;
@@ -624,7 +624,7 @@ __device__ __forceinline__ void cell_update_body(const StageArgs<real>& a, int b
   __syncthreads();
 
   // 2. Euler fluxes at the points of this thread
-  const real g1 = real(a.gamma) - real(1);
+  const real g1 = a.gm1;
   for (int q = v; q < Q; q += NV) {
     real u[NV];
 #pragma unroll

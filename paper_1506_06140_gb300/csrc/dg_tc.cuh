@@ -233,6 +233,9 @@ using TcArgs = typename std::conditional<MIXED, MixedArgs, StageArgs<float>>::ty
 
 __host__ __device__ __forceinline__ const StageArgs<float>& tc_stage(const StageArgs<float>& a) { return a; }
 __host__ __device__ __forceinline__ const StageArgs<double>& tc_stage(const MixedArgs& x) { return x.a; }
+// gamma - 1 in FP32, rounded as (float)gamma - 1.0f on the host
+__host__ __device__ __forceinline__ float tc_g1(const StageArgs<float>& a) { return a.gm1; }
+__host__ __device__ __forceinline__ float tc_g1(const MixedArgs& x) { return x.g1f; }
 
 template <int K, bool MIXED>
 __global__ void __launch_bounds__(512, 1) cell_tc_kernel(const TcArgs<MIXED> x) {
@@ -279,7 +282,7 @@ __global__ void __launch_bounds__(512, 1) cell_tc_kernel(const TcArgs<MIXED> x) 
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
   const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16);  // this warp's lane quarter
-  const float g1 = (float)a.gamma - 1.0f;
+  const float g1 = tc_g1(x);
 
   // This thread's inputs of a tile, loaded a tile ahead: the weights of
   // variable t (FP32: as stored, a padding cell gets the unit density state;

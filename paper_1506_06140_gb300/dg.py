@@ -27,7 +27,8 @@ EXPORTS = ["dg_default_options", "dg_create", "dg_destroy", "dg_last_error", "dg
            "dg_status", "dg_profile_begin", "dg_profile_end", "dg_totals_noalloc",
            "dg_create_batch", "dg_batch_advance", "dg_n_problems", "dg_tiles",
            "dg_limiter_counts", "dg_set_tiles", "dg_adapt_mark", "dg_adapt_set", "dg_regrid",
-           "dg_set_gravity", "dg_test_force_timeout", "dg_set_advance_mode", "dg_advance_mode"]
+           "dg_set_gravity", "dg_test_force_timeout", "dg_set_advance_mode", "dg_advance_mode",
+           "dg_advance_dt"]
 KERNEL_KINDS = ["face", "cell", "limit", "dt", "other", "adjoint"]
 ADVANCE_MODES = {"graph": 0, "persistent": 1}
 
@@ -78,6 +79,7 @@ def load(path=LIB_PATH):
     L.dg_compute_dt.argtypes = [vp, vp, vp, vp]
     L.dg_rk_step.argtypes = [vp, vp, C.c_double, vp, vp]
     L.dg_advance.argtypes = [vp, vp, C.c_int, vp, vp]
+    L.dg_advance_dt.argtypes = [vp, vp, C.c_int, C.c_double, vp]
     L.dg_rk_step_adjoint.argtypes = [vp, vp, C.c_double, vp, vp, vp]
     L.dg_limit.argtypes = [vp, vp, vp]
     L.dg_totals.argtypes = [vp, vp, vp, vp]
@@ -274,8 +276,13 @@ class Solver:
         self._check(self._L.dg_rk_step(self._h, self._state(W), float(dt), p, _stream()))
         return W
 
-    def advance(self, W, n_steps, dt_hist=None):
-        """n_steps CFL steps in place through a cached CUDA graph."""
+    def advance(self, W, n_steps, dt_hist=None, dt=None):
+        """n_steps steps in place through a cached CUDA graph: CFL steps, or
+        steps of the fixed timestep dt (dg_advance_dt; no dt_hist then)."""
+        if dt is not None:
+            assert dt_hist is None
+            self._check(self._L.dg_advance_dt(self._h, self._state(W), int(n_steps), float(dt), _stream()))
+            return W
         p = _ptr(dt_hist) if dt_hist is not None else None
         self._check(self._L.dg_advance(self._h, self._state(W), int(n_steps), p, _stream()))
         return W

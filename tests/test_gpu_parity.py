@@ -309,6 +309,57 @@ def test_wave2d_32x32_full_run_fp64():
     assert o.l1_density(Wd.cpu().numpy(), rho_o) <= 1e-10 * np.abs(rho_o).mean()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "mixed"])
+def test_advance_dt_repeats_rk_step(precision):
+    """dg_advance_dt (fixed-dt steps as one graph) is bit-identical to the
+    same number of dg_rk_step calls with that dt, and to the oracle's steps
+    within the step bar; a non-positive dt is refused."""
+    dg = dg_mod()
+    m = MESHES["amr2"]
+    k = 2
+    s = solver_for(m, k, rk_order=3, precision=precision)
+    o = oracle_for(m, k, rk_order=3)
+    W = wl.random_weights(2, o.N, o.n_cells, seed=330)
+    dt = 0.4 * o.compute_dt(W)
+    Wa, Wb = to_dev(s, W), to_dev(s, W)
+    s.advance(Wa, 3, dt=dt)
+    s.advance(Wa, 3, dt=dt)  # the recorded graph replayed
+    for _ in range(6):
+        s.rk_step(Wb, dt)
+    np.testing.assert_array_equal(Wa.cpu().numpy(), Wb.cpu().numpy())
+    if precision == "fp64":
+        ref = W
+        for _ in range(6):
+            ref, _ = o.rk_step(ref, dt)
+        e, _ = rel_err(Wa.cpu().numpy() - W, ref - W)
+        assert e < 1e-10, e
+    for bad in (0.0, -1.0, float("nan")):
+        with pytest.raises(dg.DGError) as ei:
+            s.advance(Wa, 1, dt=bad)
+        assert ei.value.code == dg.DG_ERR_ARG
+
+
+def test_profiled_advance_counts_every_kernel():
+    """With profiling on, dg_advance replays a graph carrying event pairs:
+    the counts are the step program's launches, the times positive, and the
+    state equals the unprofiled graph's."""
+    dg = dg_mod()
+    m = MESHES["u2"]
+    s = solver_for(m, 2, rk_order=3)
+    W = wl.random_weights(2, s.N, s.n_cells, seed=340)
+    Wa, Wb = to_dev(s, W), to_dev(s, W)
+    s.advance(Wa, 2)
+    s.profile_begin()
+    s.advance(Wb, 2)
+    s.advance(Wb, 2, dt=1e-4)
+    prof = s.profile_end()
+    assert prof["face"][0] == 12 and prof["cell"][0] == 12 and prof["dt"][0] == 2, prof
+    assert all(ms > 0.0 for n, ms in prof.values() if n > 0)
+    s.advance(Wa, 2, dt=1e-4)
+    np.testing.assert_array_equal(Wa.cpu().numpy(), Wb.cpu().numpy())
+    assert s.status() == dg.DG_OK
+
+
 def density_at_l1_points(o, W):
     """rho_h of state W at the (k+3)^d rule's points of every cell, [q][cell]."""
     import itertools
