@@ -444,16 +444,21 @@ def run_gpu(args, rank, world, local_rank):
                     "mass_drift_rel": float(abs(t1[0] - t0[0]) / abs(t0[0])),
                     "energy_drift_rel": float(abs(t1[-1] - t0[-1]) / abs(t0[-1])),
                     "momentum_abs": [float(x) for x in t1[1:-1]]}
-        # end to end through the C ABI with host buffers
+        # end to end through the C ABI with host buffers: every step copies the
+        # state in from pinned host memory, advances it one step (dg_advance:
+        # the step's graph, recorded for this buffer by one untimed step) and
+        # copies it back
         Wh = W0.cpu().pin_memory()
         Wd = torch.empty_like(W0)
+        Wd.copy_(Wh)
+        s.advance(Wd, 1)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         barrier()
         e0.record(stream)
         for i in range(args.steps):
             Wd.copy_(Wh, non_blocking=True)
-            s.rk_step(Wd)
+            s.advance(Wd, 1)
             Wh.copy_(Wd, non_blocking=True)
         e1.record(stream)
         torch.cuda.synchronize()

@@ -163,20 +163,25 @@ int dg_limiter_counts(dg_handle* h, int64_t* counts_dev, int reset, void* stream
  * kernel and faces per block of the face kernel (the fixed defaults, or the
  * autotuner's choice when dg_options.autotune was set).  A tensor-core cell
  * kernel (DG_FP32_TC) reports its fixed 32 cells; cell tile 1 means the one-
- * thread-per-cell FP32 kernel, which the autotuner also considers; face tile
+ * thread-per-cell FP32 kernel and cell tile 2 the packed-pair FP32 kernel,
+ * both of which the autotuner also considers; face tile
  * 0 means the fused face + cell kernel (tiles of 8 x 4 cells computing their
  * own faces, no separate face kernel).  Host outputs. */
 int dg_tiles(const dg_handle* h, int* cell_tile, int* face_tile);
 
 /* Sets the tiles by hand (the autotuner's choices can be overridden):
  * cell_tile 16, 32 or 64 cells per block of the tiled cell kernel, or 1 for
- * the one-thread-per-cell kernel (FP32 2D handles of the total-degree basis only); face_tile 16, 32 or
+ * the one-thread-per-cell kernel (FP32 2D handles of the total-degree basis
+ * only), or 2 for the packed-pair kernel (same handles: 64 cells per block,
+ * two variables per thread in paired FP32 multiply-adds, each lane rounded as
+ * the one-variable-per-thread kernel rounds it, so bit-identical results);
+ * face_tile 16, 32 or
  * 64, or 0 for the fused face + cell kernel: each block takes a tile of 8 x 4
  * cells, computes the fluxes of the tile's faces in shared memory (the
  * neighbours' traces across the tile's edges from their weights) and then
  * the cell update -- one launch per stage and no face-flux array, with the
  * same results to rounding (single 2D uniform meshes, FP64 or FP32 state,
- * the total-degree basis, not with cell_tile 1; the cell tile value is then
+ * the total-degree basis, not with cell_tile 1 or 2; the cell tile value is then
  * unused).  DG_ERR_ARG for other values, DG_ERR_UNSUPPORTED where the (dim,
  * k, precision, basis, mesh) has no such kernel.  Not to be called while another call on the handle is
  * being captured. */

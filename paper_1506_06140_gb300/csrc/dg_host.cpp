@@ -417,6 +417,7 @@ struct dg_handle {
   float* Wlo = nullptr;      //             and the rest of weight 0 [NV][ncells]
   int cell_tile = 0, face_tile = 0;  // stage-kernel tiles (0: the kernels' defaults)
   bool use_direct = false;   // one-thread-per-cell FP32 cell kernel
+  bool use_x2 = false;       // packed-pair FP32 cell kernel (two variables per thread)
   bool use_fused = false;    // fused face + cell kernel (face tile 0)
   std::vector<unsigned char> dtab;  // its tables (host copy, passed by value at launch)
   void* tcB = nullptr;       // its B operands
@@ -517,13 +518,17 @@ cudaError_t timed(dg_handle* h, int kind, cudaStream_t s, F&& launch) {
   }
   const size_t i0 = h->ev_used;
   h->ev_used += 2;
-  // external records: inside a stream capture they become event-record
-  // nodes of the graph (recorded at every replay), elsewhere plain records
-  cudaError_t r = cudaEventRecordWithFlags(h->ev_pool[i0], s, cudaEventRecordExternal);
+  // inside a stream capture the records are external: they become
+  // event-record nodes of the graph (recorded at every replay)
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t r = cudaStreamIsCapturing(s, &cs);
+  if (r != cudaSuccess) return r;
+  const unsigned flags = cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
+  r = cudaEventRecordWithFlags(h->ev_pool[i0], s, flags);
   if (r != cudaSuccess) return r;
   r = launch();
   if (r != cudaSuccess) return r;
-  r = cudaEventRecordWithFlags(h->ev_pool[i0 + 1], s, cudaEventRecordExternal);
+  r = cudaEventRecordWithFlags(h->ev_pool[i0 + 1], s, flags);
   h->ev_marks.push_back({kind, i0});
   return r;
 }
@@ -923,6 +928,7 @@ cudaError_t cell_launch(dg_handle* h, const void* args, cudaStream_t s) {
     h->tc_hook = 0;  // the hook (if armed) went with this launch's arguments
     return h->ks->cell_tc(args, s);
   }
+  if (h->use_x2 && !h->accel) return h->ks->cell_x2(args, s);
   return h->use_direct && !h->accel ? h->ks->cell_direct(args, s) : h->ks->cell(args, s);
 }
 
@@ -967,7 +973,7 @@ int stage_launch(dg_handle* h, const StageArgs<real>& a, cudaStream_t s, const O
       return DG_OK;
     }
   }
-  if (h->use_fused && !h->use_tc && !h->use_direct && !h->accel && h->nnodes == 0 && h->nprob == 1) {
+  if (h->use_fused && !h->use_tc && !h->use_direct && !h->use_x2 && !h->accel && h->nnodes == 0 && h->nprob == 1) {
     // faces computed inside the cell kernel's tiles: one launch per stage
     DG_CUDA(h, timed(h, DG_KERNEL_CELL, s, [&] { return h->ks->stage_fused(&a, s); }));
     return DG_OK;
@@ -1127,7 +1133,7 @@ int rk_step_any(dg_handle* h, void* W, double dt, double* dt_used, cudaStream_t 
 // (2D, an FP64 or FP32 state with the CUDA-core stage kernels, no gravity
 // source, at most PERSIST_MAX_OPS stages)
 bool persist_supported(const dg_handle* h) {
-  return h->ks->persist && !h->ms && !h->use_tc && !h->use_direct && !h->accel && h->ncells > 0 &&
+  return h->ks->persist && !h->ms && !h->use_tc && !h->use_direct && !h->use_x2 && !h->accel && h->ncells > 0 &&
          (int)h->prog_step.ops.size() <= PERSIST_MAX_OPS;
 }
 
@@ -1382,13 +1388,24 @@ int autotune_tiles(dg_handle* h, cudaStream_t s) {
       float t;
       if ((r = time_rhs(t)) != DG_OK) return r;
       if (t < best_t) { best_t = t; best_direct = true; }
+      h->use_direct = false;
     }
-    if ((best_direct || best_c != cdef) && !(best_t < kMargin * def_t)) {
+    bool best_x2 = false;
+    if (h->ks->cell_x2 && !h->ms) {  // two variables per thread, packed FP32 pairs
+      h->use_x2 = true;
+      float t;
+      if ((r = time_rhs(t)) != DG_OK) return r;
+      if (t < best_t) { best_t = t; best_x2 = true; best_direct = false; }
+      h->use_x2 = false;
+    }
+    if ((best_direct || best_x2 || best_c != cdef) && !(best_t < kMargin * def_t)) {
       best_c = cdef;
       best_direct = false;
+      best_x2 = false;
     }
     h->cell_tile = best_c;
     h->use_direct = best_direct;
+    h->use_x2 = best_x2;
   }
   DG_CUDA(h, cudaStreamSynchronize(s));
   return DG_OK;
@@ -1747,7 +1764,8 @@ int dg_set_tiles(dg_handle* h, int cell_tile, int face_tile) {
   const int cmax = h->ms ? h->ms->cell_tile_max : h->ks->cell_tile_max;
   const int fmax = h->ms ? h->ms->face_tile_max : h->ks->face_tile_max;
   if (face_tile == 0) {
-    if (!h->ks->stage_fused || h->ms || h->use_tc || h->nnodes > 0 || h->nprob != 1 || cell_tile == 1)
+    if (!h->ks->stage_fused || h->ms || h->use_tc || h->nnodes > 0 || h->nprob != 1 || cell_tile == 1 ||
+        cell_tile == 2)
       return fail(h, DG_ERR_UNSUPPORTED,
                   "dg_set_tiles: the fused face + cell kernel needs a single 2D uniform mesh with an FP64 or "
                   "FP32 state and the CUDA-core cell kernel");
@@ -1758,6 +1776,9 @@ int dg_set_tiles(dg_handle* h, int cell_tile, int face_tile) {
   if (cell_tile == 1) {
     if (h->use_tc || h->dtab.empty())
       return fail(h, DG_ERR_UNSUPPORTED, "dg_set_tiles: one thread per cell needs an FP32 2D handle");
+  } else if (cell_tile == 2) {
+    if (h->use_tc || h->ms || !h->ks->cell_x2)
+      return fail(h, DG_ERR_UNSUPPORTED, "dg_set_tiles: the packed-pair cell kernel needs an FP32 2D handle");
   } else {
     if (cell_tile != 16 && cell_tile != 32 && cell_tile != 64) return fail(h, DG_ERR_ARG, "dg_set_tiles: cell tile");
     if (cell_tile > cmax) return fail(h, DG_ERR_UNSUPPORTED, "dg_set_tiles: cell tile too large for (dim, k)");
@@ -1766,7 +1787,8 @@ int dg_set_tiles(dg_handle* h, int cell_tile, int face_tile) {
   h->use_fused = face_tile == 0;
   if (face_tile != 0) h->face_tile = face_tile;
   h->use_direct = cell_tile == 1;
-  if (cell_tile != 1) h->cell_tile = cell_tile;
+  h->use_x2 = cell_tile == 2;
+  if (cell_tile != 1 && cell_tile != 2) h->cell_tile = cell_tile;
   // cached step graphs hold the old launch configuration: record them anew
   drop_graphs(h);
   return DG_OK;
@@ -1774,7 +1796,7 @@ int dg_set_tiles(dg_handle* h, int cell_tile, int face_tile) {
 
 int dg_tiles(const dg_handle* h, int* cell_tile, int* face_tile) {
   if (!check_handle(h) || !cell_tile || !face_tile) return DG_ERR_ARG;
-  *cell_tile = h->use_tc ? 32 : (h->use_direct ? 1 : (h->use_fused ? 32 : h->cell_tile));
+  *cell_tile = h->use_tc ? 32 : (h->use_direct ? 1 : (h->use_x2 ? 2 : (h->use_fused ? 32 : h->cell_tile)));
   *face_tile = h->use_fused ? 0 : h->face_tile;
   return DG_OK;
 }

@@ -269,6 +269,8 @@ struct KernelSet {
   cudaError_t (*adj_face)(const void* adj_args, cudaStream_t s) = nullptr;
   cudaError_t (*adj_cell)(const void* adj_args, cudaStream_t s) = nullptr;
   cudaError_t (*combine)(const void* combine_args, cudaStream_t s) = nullptr;
+  // packed-pair FP32 cell kernel (2D: two variables per thread), nullptr where not built
+  cudaError_t (*cell_x2)(const void* stage_args, cudaStream_t s) = nullptr;
   // one-thread-per-cell FP32 cell kernel (2D), nullptr where not built
   cudaError_t (*cell_direct)(const void* stage_args, cudaStream_t s) = nullptr;
   void (*fill_direct)(const std::vector<double>& tab, std::vector<unsigned char>& out) = nullptr;

@@ -783,7 +783,9 @@ __device__ __forceinline__ void dt_body(const AuxArgs<real>& a, int bid, int nbl
   using S = Shape<DIM, K, B>;
   const int c = bid * THREADS + threadIdx.x;
   const int nc = a.m.ncells;
-  double speed = 0.0;
+  // the speeds are reduced in the state's precision and widened to FP64 at
+  // the atomics (the widening is monotonic, so the maximum is the same)
+  real speed = real(0);
   int pb = 0;
   if (c < nc) {
     // in the state's precision (an FP32 state's speed is FP32-accurate anyway)
@@ -805,7 +807,7 @@ __device__ __forceinline__ void dt_body(const AuxArgs<real>& a, int bid, int nbl
 #pragma unroll
       for (int b = 0; b < DIM; ++b) sum += fabs(u[1 + b] * rinv) + cs;
       const real inv_dx = real(a.inv_dx_prob ? a.inv_dx_prob[pb] : a.inv_dx[0]);
-      speed = (double)(sum * inv_dx * real(1 << a.m.level[c]));
+      speed = sum * inv_dx * real(1 << a.m.level[c]);
       if (a.accel) {
         // gravity bound (Sec. 2.5) as a speed: dt_factor sqrt(2 gamma (gamma-1)) |a|_max / c,
         // |a| the largest over the cell's volume points
@@ -820,7 +822,7 @@ __device__ __forceinline__ void dt_body(const AuxArgs<real>& a, int bid, int nbl
           }
           a2max = fmax(a2max, a2);
         }
-        speed = fmax(speed, (double)(real(a.grav_factor) * sqrt(a2max) / cs));
+        speed = fmax(speed, real(a.grav_factor) * sqrt(a2max) / cs);
       }
     }
   } else {
@@ -830,17 +832,19 @@ __device__ __forceinline__ void dt_body(const AuxArgs<real>& a, int bid, int nbl
   // then issues one atomic per run of warps with the same problem (a warp
   // spanning two problems falls back to one atomic per cell)
   __shared__ int sp[THREADS / 32];
-  __shared__ double ss[THREADS / 32];
+  __shared__ real ss[THREADS / 32];
   const unsigned full = 0xffffffffu;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int p0 = __shfl_sync(full, pb, 0);
   if (p0 < 0) p0 = __reduce_max_sync(full, pb);  // lane 0 past the end: any valid lane's problem
   const bool uniform = __all_sync(full, pb == p0 || pb < 0);
+  bool wrote = false;  // this thread issued a maximum atomic
   if (uniform) {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) speed = fmax(speed, __shfl_xor_sync(full, speed, off));
   } else if (pb >= 0) {
-    atomicMax(a.dt_bits + pb, (unsigned long long)__double_as_longlong(speed));
+    atomicMax(a.dt_bits + pb, (unsigned long long)__double_as_longlong((double)speed));
+    wrote = true;
   }
   if (lane == 0) {
     sp[w] = uniform ? p0 : -1;
@@ -849,22 +853,24 @@ __device__ __forceinline__ void dt_body(const AuxArgs<real>& a, int bid, int nbl
   __syncthreads();
   if (threadIdx.x == 0) {
     int cur = -1;
-    double m = 0.0;
+    real m = real(0);
     for (int i = 0; i < THREADS / 32; ++i) {
       if (sp[i] != cur) {
-        if (cur >= 0) atomicMax(a.dt_bits + cur, (unsigned long long)__double_as_longlong(m));
+        if (cur >= 0) atomicMax(a.dt_bits + cur, (unsigned long long)__double_as_longlong((double)m));
         cur = sp[i];
-        m = 0.0;
+        m = real(0);
       }
       if (cur >= 0) m = fmax(m, ss[i]);
     }
-    if (cur >= 0) atomicMax(a.dt_bits + cur, (unsigned long long)__double_as_longlong(m));
+    if (cur >= 0) atomicMax(a.dt_bits + cur, (unsigned long long)__double_as_longlong((double)m));
+    wrote = true;
   }
   if (a.dt_out) {
-    // every thread's maxima are visible device-wide before the block counts
-    // itself done; the last block finishes the timestep and resets the maxima
+    // every maximum this block issued is visible device-wide before the block
+    // counts itself done (a fence by each thread that issued one); the last
+    // block finishes the timestep and resets the maxima
     __shared__ int last;
-    __threadfence();
+    if (wrote) __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) last = atomicAdd(a.dt_done, 1u) == (unsigned)nblk - 1u;
     __syncthreads();
@@ -1160,6 +1166,7 @@ cudaError_t launch_node_weights(const void* pa, cudaStream_t s) {
 
 #include "dg_fused.cuh"
 #include "dg_persist.cuh"
+#include "dg_x2.cuh"
 
 namespace dgi {
 
@@ -1203,6 +1210,7 @@ KernelSet make_kernel_set(int prec) {
     ks.adj_face = &launch_adj_face<real, DIM, K>;
     ks.adj_cell = &launch_adj_cell<real, DIM, K>;
     if constexpr (std::is_same<real, float>::value && DIM == 2) {
+      ks.cell_x2 = &launch_cell_x2<K>;
       ks.cell_direct = &launch_cell_direct<DIM, K>;
       ks.fill_direct = &fill_direct_tables<DIM, K>;
     }

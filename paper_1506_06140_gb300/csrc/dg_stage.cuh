@@ -16,6 +16,11 @@
 
 namespace dgi {
 
+// a * b + c with one rounding: the contractions below spell their
+// multiply-adds out, so that a packed pair type can supply its own
+__device__ __forceinline__ float fmac(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmac(double a, double b, double c) { return fma(a, b, c); }
+
 // Index of phi_(a,b,c) in the basis order: total degree, then a descending,
 // then b descending.
 template <int DIM>
@@ -59,7 +64,7 @@ __device__ __forceinline__ void modal_to_nodal(const Tab1D<real>& T, const real*
       for (int j = 0; j < K1; ++j) {
         real s = real(0);
 #pragma unroll
-        for (int b = 0; b <= BS::lim(a); ++b) s += w[BS::idx(a, b)] * T.P[b][j];
+        for (int b = 0; b <= BS::lim(a); ++b) s = fmac(w[BS::idx(a, b)], T.P[b][j], s);
         t[a][j] = s;
       }
 #pragma unroll
@@ -68,7 +73,7 @@ __device__ __forceinline__ void modal_to_nodal(const Tab1D<real>& T, const real*
       for (int i = 0; i < K1; ++i) {
         real s = real(0);
 #pragma unroll
-        for (int a = 0; a <= K; ++a) s += T.P[a][i] * t[a][j];
+        for (int a = 0; a <= K; ++a) s = fmac(T.P[a][i], t[a][j], s);
         u[i + K1 * j] = s;
       }
   } else {
@@ -81,7 +86,7 @@ __device__ __forceinline__ void modal_to_nodal(const Tab1D<real>& T, const real*
         for (int kz = 0; kz < K1; ++kz) {
           real s = real(0);
 #pragma unroll
-          for (int c = 0; c <= K - a - b; ++c) s += w[bidx<3>(a, b, c)] * T.P[c][kz];
+          for (int c = 0; c <= K - a - b; ++c) s = fmac(w[bidx<3>(a, b, c)], T.P[c][kz], s);
           t1[a][b][kz] = s;
         }
     real t2[K1][K1][K1];  // [a][j][kz] = sum_b t1[a][b][kz] P_b(y_j)
@@ -93,7 +98,7 @@ __device__ __forceinline__ void modal_to_nodal(const Tab1D<real>& T, const real*
         for (int kz = 0; kz < K1; ++kz) {
           real s = real(0);
 #pragma unroll
-          for (int b = 0; b <= K - a; ++b) s += t1[a][b][kz] * T.P[b][j];
+          for (int b = 0; b <= K - a; ++b) s = fmac(t1[a][b][kz], T.P[b][j], s);
           t2[a][j][kz] = s;
         }
 #pragma unroll
@@ -104,7 +109,7 @@ __device__ __forceinline__ void modal_to_nodal(const Tab1D<real>& T, const real*
         for (int i = 0; i < K1; ++i) {
           real s = real(0);
 #pragma unroll
-          for (int a = 0; a <= K; ++a) s += T.P[a][i] * t2[a][j][kz];
+          for (int a = 0; a <= K; ++a) s = fmac(T.P[a][i], t2[a][j][kz], s);
           u[i + K1 * (j + K1 * kz)] = s;
         }
   }
@@ -125,10 +130,10 @@ __device__ __forceinline__ void volume_dir(const Tab1D<real>& T, const real* f, 
       for (int o = 0; o < K1; ++o) {
         real g = real(0);
 #pragma unroll
-        for (int i = 0; i < K1; ++i) g += f[D == 0 ? (i + K1 * o) : (o + K1 * i)] * T.DW[e][i];
+        for (int i = 0; i < K1; ++i) g = fmac(f[D == 0 ? (i + K1 * o) : (o + K1 * i)], T.DW[e][i], g);
 #pragma unroll
         for (int e2 = 0; e2 <= BS::lim(e); ++e2)
-          acc[D == 0 ? BS::idx(e, e2) : BS::idx(e2, e)] += g * T.PW[e2][o];
+          acc[D == 0 ? BS::idx(e, e2) : BS::idx(e2, e)] = fmac(g, T.PW[e2][o], acc[D == 0 ? BS::idx(e, e2) : BS::idx(e2, e)]);
       }
   } else {
     // axes: D (derivative), A and BB the other two in increasing order
@@ -157,7 +162,7 @@ __device__ __forceinline__ void volume_dir(const Tab1D<real>& T, const real* f, 
         for (int ib = 0; ib < K1; ++ib) {
           real s = real(0);
 #pragma unroll
-          for (int id = 0; id < K1; ++id) s += f[q_of(id, ia, ib)] * T.DW[ed][id];
+          for (int id = 0; id < K1; ++id) s = fmac(f[q_of(id, ia, ib)], T.DW[ed][id], s);
           g1[ia][ib] = s;
         }
 #pragma unroll
@@ -166,9 +171,9 @@ __device__ __forceinline__ void volume_dir(const Tab1D<real>& T, const real* f, 
         for (int ib = 0; ib < K1; ++ib) {
           real g2 = real(0);
 #pragma unroll
-          for (int ia = 0; ia < K1; ++ia) g2 += g1[ia][ib] * T.PW[ea][ia];
+          for (int ia = 0; ia < K1; ++ia) g2 = fmac(g1[ia][ib], T.PW[ea][ia], g2);
 #pragma unroll
-          for (int eb = 0; eb <= K - ed - ea; ++eb) acc[l_of(ed, ea, eb)] += g2 * T.PW[eb][ib];
+          for (int eb = 0; eb <= K - ed - ea; ++eb) acc[l_of(ed, ea, eb)] = fmac(g2, T.PW[eb][ib], acc[l_of(ed, ea, eb)]);
         }
     }
   }
@@ -190,15 +195,15 @@ __device__ __forceinline__ void source_project(const Tab1D<real>& T, const real*
       for (int i2 = 0; i2 < K1; ++i2) {
         real t = real(0);
 #pragma unroll
-        for (int i1 = 0; i1 < K1; ++i1) t += s[i1 + K1 * i2] * T.PW[e1][i1];
+        for (int i1 = 0; i1 < K1; ++i1) t = fmac(s[i1 + K1 * i2], T.PW[e1][i1], t);
         g[i2] = t;
       }
 #pragma unroll
       for (int e2 = 0; e2 <= BS::lim(e1); ++e2) {
         real t = real(0);
 #pragma unroll
-        for (int i2 = 0; i2 < K1; ++i2) t += g[i2] * T.PW[e2][i2];
-        acc[BS::idx(e1, e2)] += h * t;
+        for (int i2 = 0; i2 < K1; ++i2) t = fmac(g[i2], T.PW[e2][i2], t);
+        acc[BS::idx(e1, e2)] = fmac(h, t, acc[BS::idx(e1, e2)]);
       }
     }
   } else {
@@ -211,7 +216,7 @@ __device__ __forceinline__ void source_project(const Tab1D<real>& T, const real*
         for (int i3 = 0; i3 < K1; ++i3) {
           real t = real(0);
 #pragma unroll
-          for (int i1 = 0; i1 < K1; ++i1) t += s[i1 + K1 * (i2 + K1 * i3)] * T.PW[e1][i1];
+          for (int i1 = 0; i1 < K1; ++i1) t = fmac(s[i1 + K1 * (i2 + K1 * i3)], T.PW[e1][i1], t);
           g1[i2][i3] = t;
         }
 #pragma unroll
@@ -221,15 +226,15 @@ __device__ __forceinline__ void source_project(const Tab1D<real>& T, const real*
         for (int i3 = 0; i3 < K1; ++i3) {
           real t = real(0);
 #pragma unroll
-          for (int i2 = 0; i2 < K1; ++i2) t += g1[i2][i3] * T.PW[e2][i2];
+          for (int i2 = 0; i2 < K1; ++i2) t = fmac(g1[i2][i3], T.PW[e2][i2], t);
           g2[i3] = t;
         }
 #pragma unroll
         for (int e3 = 0; e3 <= K - e1 - e2; ++e3) {
           real t = real(0);
 #pragma unroll
-          for (int i3 = 0; i3 < K1; ++i3) t += g2[i3] * T.PW[e3][i3];
-          acc[bidx<3>(e1, e2, e3)] += h * t;
+          for (int i3 = 0; i3 < K1; ++i3) t = fmac(g2[i3], T.PW[e3][i3], t);
+          acc[bidx<3>(e1, e2, e3)] = fmac(h, t, acc[bidx<3>(e1, e2, e3)]);
         }
       }
     }
@@ -255,14 +260,14 @@ __device__ __forceinline__ void surface_side(const Tab1D<real>& T, const real (&
     for (int e = 0; e <= K; ++e) {
       real s = real(0);
 #pragma unroll
-      for (int q = 0; q < K1; ++q) s += fq[q] * PW0[e][q];
+      for (int q = 0; q < K1; ++q) s = fmac(fq[q], PW0[e][q], s);
       G[e] = s * ssg;
     }
 #pragma unroll
     for (int ed = 0; ed <= K; ++ed)
 #pragma unroll
       for (int et = 0; et <= BS::lim(ed); ++et)
-        acc[TA == 1 ? BS::idx(ed, et) : BS::idx(et, ed)] += T.PE[S][ed] * G[et];
+        acc[TA == 1 ? BS::idx(ed, et) : BS::idx(et, ed)] = fmac(T.PE[S][ed], G[et], acc[TA == 1 ? BS::idx(ed, et) : BS::idx(et, ed)]);
   } else {
     constexpr int A = DIR == 0 ? 1 : 0;  // tangential axes, increasing
     constexpr int BB = DIR == 2 ? 1 : 2;
@@ -273,7 +278,7 @@ __device__ __forceinline__ void surface_side(const Tab1D<real>& T, const real (&
       for (int qb = 0; qb < K1; ++qb) {
         real s = real(0);
 #pragma unroll
-        for (int qa = 0; qa < K1; ++qa) s += fq[qa + K1 * qb] * PW0[ea][qa];
+        for (int qa = 0; qa < K1; ++qa) s = fmac(fq[qa + K1 * qb], PW0[ea][qa], s);
         H[ea][qb] = s;
       }
 #pragma unroll
@@ -282,7 +287,7 @@ __device__ __forceinline__ void surface_side(const Tab1D<real>& T, const real (&
       for (int eb = 0; eb <= K - ea; ++eb) {
         real s = real(0);
 #pragma unroll
-        for (int qb = 0; qb < K1; ++qb) s += H[ea][qb] * PW1[eb][qb];
+        for (int qb = 0; qb < K1; ++qb) s = fmac(H[ea][qb], PW1[eb][qb], s);
         s *= ssg;
 #pragma unroll
         for (int ed = 0; ed <= K - ea - eb; ++ed) {
@@ -290,7 +295,7 @@ __device__ __forceinline__ void surface_side(const Tab1D<real>& T, const real (&
           e[DIR] = ed;
           e[A] = ea;
           e[BB] = eb;
-          acc[bidx<3>(e[0], e[1], e[2])] += T.PE[S][ed] * s;
+          acc[bidx<3>(e[0], e[1], e[2])] = fmac(T.PE[S][ed], s, acc[bidx<3>(e[0], e[1], e[2])]);
         }
       }
   }
@@ -311,14 +316,14 @@ __device__ __forceinline__ void face_trace(const Tab1D<real>& T, const real* w, 
       real acc = real(0);
 #pragma unroll
       for (int ed = 0; ed <= BS::lim(et); ++ed)
-        acc += w[DIR == 0 ? BS::idx(ed, et) : BS::idx(et, ed)] * T.PE[s][ed];
+        acc = fmac(w[DIR == 0 ? BS::idx(ed, et) : BS::idx(et, ed)], T.PE[s][ed], acc);
       t[et] = acc;
     }
 #pragma unroll
     for (int q = 0; q < K1; ++q) {
       real acc = real(0);
 #pragma unroll
-      for (int et = 0; et <= K; ++et) acc += t[et] * PT0[et][q];
+      for (int et = 0; et <= K; ++et) acc = fmac(t[et], PT0[et][q], acc);
       u[q] = acc;
     }
   } else {
@@ -336,7 +341,7 @@ __device__ __forceinline__ void face_trace(const Tab1D<real>& T, const real* w, 
           e[DIR] = ed;
           e[A] = ea;
           e[BB] = eb;
-          acc += w[bidx<3>(e[0], e[1], e[2])] * T.PE[s][ed];
+          acc = fmac(w[bidx<3>(e[0], e[1], e[2])], T.PE[s][ed], acc);
         }
         t[ea][eb] = acc;
       }
@@ -347,7 +352,7 @@ __device__ __forceinline__ void face_trace(const Tab1D<real>& T, const real* w, 
       for (int qb = 0; qb < K1; ++qb) {
         real acc = real(0);
 #pragma unroll
-        for (int eb = 0; eb <= K - ea; ++eb) acc += t[ea][eb] * PT1[eb][qb];
+        for (int eb = 0; eb <= K - ea; ++eb) acc = fmac(t[ea][eb], PT1[eb][qb], acc);
         h[qb] = acc;
       }
 #pragma unroll
@@ -355,7 +360,7 @@ __device__ __forceinline__ void face_trace(const Tab1D<real>& T, const real* w, 
 #pragma unroll
         for (int qa = 0; qa < K1; ++qa) {
           if (ea == 0) u[qa + K1 * qb] = real(0);
-          u[qa + K1 * qb] += PT0[ea][qa] * h[qb];
+          u[qa + K1 * qb] = fmac(PT0[ea][qa], h[qb], u[qa + K1 * qb]);
         }
     }
   }

@@ -405,8 +405,9 @@ class Solver:
         return out
 
     def set_tiles(self, cell_tile, face_tile):
-        """cell_tile 16/32/64 (or 1: one thread per cell, FP32 2D), face_tile 16/32/64
-        (or 0: the fused face + cell kernel, single 2D uniform meshes)"""
+        """cell_tile 16/32/64 (or 1: one thread per cell, FP32 2D; 2: two variables
+        per thread as packed FP32 pairs, FP32 2D), face_tile 16/32/64 (or 0: the
+        fused face + cell kernel, single 2D uniform meshes)"""
         self._check(self._L.dg_set_tiles(self._h, int(cell_tile), int(face_tile)))
 
     def tiles(self):
