@@ -272,6 +272,17 @@ enum { DG_ADVANCE_GRAPH = 0, DG_ADVANCE_PERSISTENT = 1 };
 int dg_set_advance_mode(dg_handle* h, int mode);
 int dg_advance_mode(const dg_handle* h, int* mode);
 
+/* Kernel-boundary overlap (on by default): the face, cell, timestep and
+ * limiter kernels of a step are launched with programmatic stream
+ * serialization, so the device may schedule a kernel while the one ahead of
+ * it drains; each kernel waits (griddepcontrol.wait) until its predecessor has
+ * completed and its writes are visible before touching any state, so results
+ * do not change.  on = 0 launches them with plain stream order.  Cached step
+ * graphs are recorded anew.  Not to be called while another call on the
+ * handle is being captured. */
+int dg_set_overlap(dg_handle* h, int on);
+int dg_overlap(const dg_handle* h, int* on);
+
 /* Number of problems and, if cell_offsets_host is not NULL, the first cell
  * of every problem (n_problems + 1 entries, the last one = n_cells). */
 int dg_n_problems(const dg_handle* h, int* n_problems, int64_t* cell_offsets_host);

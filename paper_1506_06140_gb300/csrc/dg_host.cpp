@@ -418,6 +418,7 @@ struct dg_handle {
   int cell_tile = 0, face_tile = 0;  // stage-kernel tiles (0: the kernels' defaults)
   bool use_direct = false;   // one-thread-per-cell FP32 cell kernel
   bool use_x2 = false;       // packed-pair FP32 cell kernel (two variables per thread)
+  int pdl = 1;               // stage kernels launched as programmatic dependents (dg_set_overlap)
   bool use_fused = false;    // fused face + cell kernel (face tile 0)
   std::vector<unsigned char> dtab;  // its tables (host copy, passed by value at launch)
   void* tcB = nullptr;       // its B operands
@@ -1001,6 +1002,7 @@ StageArgs<real> stage_args(dg_handle* h, const Op& op, const void* U, void* W) {
   a.U = static_cast<const real*>(U);
   a.F = static_cast<real*>(h->F);
   a.gamma = h->gamma;
+  a.pdl = h->pdl;
   a.gam = (real)h->gamma;
   a.gm1 = (real)h->gamma - (real)1;
   auto reg = [&](int r) -> real* { return static_cast<real*>(r == 0 ? W : h->regs[r - 1]); };
@@ -1030,6 +1032,7 @@ LimitArgs<real> limit_args(dg_handle* h, const void* src, void* dst) {
   la.Uin = static_cast<const real*>(src);
   la.Uout = static_cast<real*>(dst);
   la.gamma = h->gamma;
+  la.pdl = h->pdl;
   la.limiter = h->opt.slope_limiter;
   la.beta = h->opt.beta;
   la.Mtilde = h->opt.Mtilde;
@@ -1057,6 +1060,7 @@ AuxArgs<real> aux_args(dg_handle* h) {
   a.tab64 = h->tab64;
   a.partial = h->partial;
   a.gamma = h->gamma;
+  a.pdl = h->pdl;
   a.volume = h->volume;
   for (int l = 0; l < 2; ++l) a.inv_dx[l] = 1.0 / std::ldexp(h->md.dx0, -l);
   a.inv_dx_prob = h->nprob > 1 ? h->inv_dx_prob : nullptr;
@@ -2213,6 +2217,21 @@ int dg_advance_mode(const dg_handle* h, int* mode) {
   if (!check_handle(h) || !mode) return DG_ERR_ARG;
   *mode = h->advance_mode == DG_ADVANCE_PERSISTENT && persist_supported(h) ? DG_ADVANCE_PERSISTENT
                                                                            : DG_ADVANCE_GRAPH;
+  return DG_OK;
+}
+
+int dg_set_overlap(dg_handle* h, int on) {
+  if (!check_handle(h)) return DG_ERR_ARG;
+  if (on != 0 && on != 1) return fail(h, DG_ERR_ARG, "dg_set_overlap: on must be 0 or 1");
+  std::lock_guard<std::mutex> lock(h->mu);
+  h->pdl = on;
+  drop_graphs(h);  // recorded launches carry the old launch attributes
+  return DG_OK;
+}
+
+int dg_overlap(const dg_handle* h, int* on) {
+  if (!check_handle(h) || !on) return DG_ERR_ARG;
+  *on = h->pdl;
   return DG_OK;
 }
 

@@ -123,6 +123,7 @@ struct StageArgs {
                                 // its first MMA and commit and waits with a short limit
   const real* accel = nullptr;  // [DIM][Q][ncells] external acceleration at the volume points
                                 // (gravity source, eq. gravity_term); nullptr: none
+  int pdl = 0;                  // 1: launched as a programmatic dependent of the previous kernel
 };
 
 // Stage arguments of the mixed-precision kernels (FP64 state, FP32
@@ -154,6 +155,7 @@ struct MixedArgs {
 template <typename real>
 struct LimitArgs {
   MeshDev m;
+  int pdl = 0;  // 1: launched as a programmatic dependent of the previous kernel
   const double* tab64 = nullptr;  // FP64 tables (same layout)
   const real* tabr = nullptr;     // the same tables in the state precision
   const float* tab32 = nullptr;   // the same tables in FP32 (positivity precheck)
@@ -174,6 +176,7 @@ struct LimitArgs {
 template <typename real>
 struct AuxArgs {
   MeshDev m;
+  int pdl = 0;  // 1: launched as a programmatic dependent of the previous kernel
   const double* tab64 = nullptr;
   const real* W = nullptr;
   real* Wout = nullptr;

@@ -617,6 +617,7 @@ __device__ __forceinline__ void limit_body(const LimitArgs<real>& a, int bid) {
 
 template <typename real, int DIM, int K>
 __global__ void __launch_bounds__(128, sizeof(real) == 4 && DIM == 3 ? 4 : 1) limit_kernel(const LimitArgs<real> a) {
+  pdl_wait();
   limit_body<real, DIM, K>(a, blockIdx.x);
 }
 
@@ -744,6 +745,7 @@ __device__ __forceinline__ void positivity_body(const LimitArgs<real>& a, int bi
 
 template <typename real, int DIM, int K>
 __global__ void __launch_bounds__(128) positivity_kernel(const LimitArgs<real> a) {
+  pdl_wait();
   positivity_body<real, DIM, K>(a, blockIdx.x, gridDim.x);
 }
 
@@ -890,6 +892,7 @@ __device__ __forceinline__ void dt_body(const AuxArgs<real>& a, int bid, int nbl
 
 template <typename real, int DIM, int K, int B = 0>
 __global__ void __launch_bounds__(RED_THREADS) dt_kernel(const AuxArgs<real> a) {
+  pdl_wait();
   dt_body<real, DIM, K, RED_THREADS, B>(a, blockIdx.x, gridDim.x);
 }
 
@@ -1010,9 +1013,9 @@ cudaError_t launch_face(const void* pa, cudaStream_t s) {
   if (a.m.nfaces == 0) return cudaSuccess;
   const int fb = a.face_tile == 16 || a.face_tile == 64 ? a.face_tile : 32;
   const int grid = (a.m.nfaces + fb - 1) / fb;
-  if (fb == 16) face_flux_kernel<real, DIM, K, 16, B><<<grid, 16 * NV, FT::smem(16), s>>>(a);
-  else if (fb == 64) face_flux_kernel<real, DIM, K, 64, B><<<grid, 64 * NV, FT::smem(64), s>>>(a);
-  else face_flux_kernel<real, DIM, K, 32, B><<<grid, 32 * NV, FT::smem(32), s>>>(a);
+  if (fb == 16) return launch_pdl(a.pdl, face_flux_kernel<real, DIM, K, 16, B>, grid, 16 * NV, FT::smem(16), s, a);
+  if (fb == 64) return launch_pdl(a.pdl, face_flux_kernel<real, DIM, K, 64, B>, grid, 64 * NV, FT::smem(64), s, a);
+  return launch_pdl(a.pdl, face_flux_kernel<real, DIM, K, 32, B>, grid, 32 * NV, FT::smem(32), s, a);
   return cudaGetLastError();
 }
 
@@ -1036,11 +1039,13 @@ cudaError_t launch_cell(const void* pa, cudaStream_t s) {
   }
   const int grid = (a.m.ncells + tc - 1) / tc;
   if (tc == 16) {
-    cell_update_kernel<real, DIM, K, 16, false, B><<<grid, 16 * NV, CT::smem(16), s>>>(a);
+    return launch_pdl(a.pdl, cell_update_kernel<real, DIM, K, 16, false, B>, grid, 16 * NV, CT::smem(16), s, a);
   } else if (tc == 32) {
-    if constexpr (CT::TC_MAX >= 32) cell_update_kernel<real, DIM, K, 32, false, B><<<grid, 32 * NV, CT::smem(32), s>>>(a);
+    if constexpr (CT::TC_MAX >= 32)
+      return launch_pdl(a.pdl, cell_update_kernel<real, DIM, K, 32, false, B>, grid, 32 * NV, CT::smem(32), s, a);
   } else {
-    if constexpr (CT::TC_MAX >= 64) cell_update_kernel<real, DIM, K, 64, false, B><<<grid, 64 * NV, CT::smem(64), s>>>(a);
+    if constexpr (CT::TC_MAX >= 64)
+      return launch_pdl(a.pdl, cell_update_kernel<real, DIM, K, 64, false, B>, grid, 64 * NV, CT::smem(64), s, a);
   }
   return cudaGetLastError();
 }
@@ -1101,12 +1106,13 @@ cudaError_t launch_limit(const void* pa, cudaStream_t s) {
   if (a.m.ncells == 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(a.queue_len, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
-  limit_kernel<real, DIM, K><<<(a.m.ncells + 127) / 128, 128, 0, s>>>(a);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = launch_pdl(a.pdl, limit_kernel<real, DIM, K>, (a.m.ncells + 127) / 128, 128, 0, s, a)) != cudaSuccess)
+    return e;
   if (a.positivity && K > 0) {
     // the queue's length is known on the device only: a fixed grid strides over it
     const int blocks = (a.m.ncells + 127) / 128 < 608 ? (a.m.ncells + 127) / 128 : 608;
-    positivity_kernel<real, DIM, K><<<blocks, 128, 0, s>>>(a);
+    cudaError_t e2 = launch_pdl(a.pdl, positivity_kernel<real, DIM, K>, blocks, 128, 0, s, a);
+    if (e2 != cudaSuccess) return e2;
   }
   return cudaGetLastError();
 }
@@ -1131,7 +1137,8 @@ template <typename real, int DIM, int K, int B = 0>
 cudaError_t launch_dt(const void* pa, cudaStream_t s) {
   const auto& a = *static_cast<const AuxArgs<real>*>(pa);
   if (a.m.ncells == 0) return cudaSuccess;
-  dt_kernel<real, DIM, K, B><<<(a.m.ncells + RED_THREADS - 1) / RED_THREADS, RED_THREADS, 0, s>>>(a);  // per-problem max
+  return launch_pdl(a.pdl, dt_kernel<real, DIM, K, B>, (a.m.ncells + RED_THREADS - 1) / RED_THREADS, RED_THREADS, 0, s,
+                    a);  // per-problem max
   return cudaGetLastError();
 }
 

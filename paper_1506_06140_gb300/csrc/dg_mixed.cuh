@@ -127,6 +127,7 @@ struct MixedFaceTile {
 template <int DIM, int K, int FB>
 __global__ void __launch_bounds__(FB * Shape<DIM, K>::NV)
     face_flux_mixed_kernel(const MixedArgs x) {
+  pdl_wait();
   using S = Shape<DIM, K>;
   constexpr int NV = S::NV, QF = S::QF, THREADS = FB * NV;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -262,6 +263,7 @@ __device__ __forceinline__ void surface_from_faces_mixed(const MixedArgs& x, int
 template <int DIM, int K, int TC>
 __global__ void __launch_bounds__(TC * Shape<DIM, K>::NV)
     cell_update_mixed_kernel(const MixedArgs x) {
+  pdl_wait();
   using S = Shape<DIM, K>;
   constexpr int NV = S::NV, Q = S::Q, N = S::N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -415,10 +417,10 @@ cudaError_t launch_face_mixed(const void* px, cudaStream_t s) {
   if (x.a.m.nfaces == 0) return cudaSuccess;
   const int fb = x.a.face_tile == 16 || x.a.face_tile == 64 ? x.a.face_tile : 32;
   const int grid = (x.a.m.nfaces + fb - 1) / fb;
-  if (fb == 16) face_flux_mixed_kernel<DIM, K, 16><<<grid, 16 * NV, FT::smem(16), s>>>(x);
-  else if (fb == 64) face_flux_mixed_kernel<DIM, K, 64><<<grid, 64 * NV, FT::smem(64), s>>>(x);
-  else face_flux_mixed_kernel<DIM, K, 32><<<grid, 32 * NV, FT::smem(32), s>>>(x);
-  return cudaGetLastError();
+  const bool pdl = x.a.pdl != 0;
+  if (fb == 16) return launch_pdl(pdl, face_flux_mixed_kernel<DIM, K, 16>, grid, 16 * NV, FT::smem(16), s, x);
+  if (fb == 64) return launch_pdl(pdl, face_flux_mixed_kernel<DIM, K, 64>, grid, 64 * NV, FT::smem(64), s, x);
+  return launch_pdl(pdl, face_flux_mixed_kernel<DIM, K, 32>, grid, 32 * NV, FT::smem(32), s, x);
 }
 
 template <int DIM, int K>
@@ -432,11 +434,13 @@ cudaError_t launch_cell_mixed(const void* px, cudaStream_t s) {
                      : CT::TC;
   const int grid = (x.a.m.ncells + tc - 1) / tc;
   if (tc == 16) {
-    cell_update_mixed_kernel<DIM, K, 16><<<grid, 16 * NV, CT::smem(16), s>>>(x);
+    return launch_pdl(x.a.pdl != 0, cell_update_mixed_kernel<DIM, K, 16>, grid, 16 * NV, CT::smem(16), s, x);
   } else if (tc == 32) {
-    if constexpr (CT::TC_MAX >= 32) cell_update_mixed_kernel<DIM, K, 32><<<grid, 32 * NV, CT::smem(32), s>>>(x);
+    if constexpr (CT::TC_MAX >= 32)
+      return launch_pdl(x.a.pdl != 0, cell_update_mixed_kernel<DIM, K, 32>, grid, 32 * NV, CT::smem(32), s, x);
   } else {
-    if constexpr (CT::TC_MAX >= 64) cell_update_mixed_kernel<DIM, K, 64><<<grid, 64 * NV, CT::smem(64), s>>>(x);
+    if constexpr (CT::TC_MAX >= 64)
+      return launch_pdl(x.a.pdl != 0, cell_update_mixed_kernel<DIM, K, 64>, grid, 64 * NV, CT::smem(64), s, x);
   }
   return cudaGetLastError();
 }

@@ -11,10 +11,40 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <utility>
+
 #include "dg_internal.h"
 #include "dg_physics.cuh"
 
 namespace dgi {
+
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization may be scheduled before the kernel ahead of it in the stream
+// has finished; pdl_wait() returns once that kernel has completed and its
+// writes are visible (a no-op for a kernel launched without the attribute).
+// Every stage kernel calls it before its first access to global state.  No
+// kernel signals its dependents early (griddepcontrol.launch_dependents): a
+// dependent is released as the blocks of this grid exit.  Signalling at the
+// start of every block measured slower (square advection 64^2: 0.220 against
+// 0.118 ms per step), the waiting dependents' blocks holding SM slots.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
 
 // a * b + c with one rounding: the contractions below spell their
 // multiply-adds out, so that a packed pair type can supply its own
@@ -467,6 +497,7 @@ __device__ __forceinline__ void face_flux_body(const StageArgs<real>& a, int bid
 template <typename real, int DIM, int K, int FB, int B = 0>
 __global__ void __launch_bounds__(FB * Shape<DIM, K>::NV)
     face_flux_kernel(const StageArgs<real> a) {
+  pdl_wait();
   face_flux_body<real, DIM, K, FB, B>(a, blockIdx.x);
 }
 
@@ -699,6 +730,7 @@ __device__ __forceinline__ void cell_update_body(const StageArgs<real>& a, int b
 template <typename real, int DIM, int K, int TC, bool GRAV = false, int B = 0>
 __global__ void __launch_bounds__(TC * Shape<DIM, K>::NV, CellTile<real, DIM, K>::min_blocks(TC))
     cell_update_kernel(const StageArgs<real> a) {
+  pdl_wait();
   cell_update_body<real, DIM, K, TC, GRAV, B>(a, blockIdx.x);
 }
 

@@ -28,7 +28,7 @@ EXPORTS = ["dg_default_options", "dg_create", "dg_destroy", "dg_last_error", "dg
            "dg_create_batch", "dg_batch_advance", "dg_n_problems", "dg_tiles",
            "dg_limiter_counts", "dg_set_tiles", "dg_adapt_mark", "dg_adapt_set", "dg_regrid",
            "dg_set_gravity", "dg_test_force_timeout", "dg_set_advance_mode", "dg_advance_mode",
-           "dg_advance_dt"]
+           "dg_advance_dt", "dg_set_overlap", "dg_overlap"]
 KERNEL_KINDS = ["face", "cell", "limit", "dt", "other", "adjoint"]
 ADVANCE_MODES = {"graph": 0, "persistent": 1}
 
@@ -80,6 +80,8 @@ def load(path=LIB_PATH):
     L.dg_rk_step.argtypes = [vp, vp, C.c_double, vp, vp]
     L.dg_advance.argtypes = [vp, vp, C.c_int, vp, vp]
     L.dg_advance_dt.argtypes = [vp, vp, C.c_int, C.c_double, vp]
+    L.dg_set_overlap.argtypes = [vp, C.c_int]
+    L.dg_overlap.argtypes = [vp, C.POINTER(C.c_int)]
     L.dg_rk_step_adjoint.argtypes = [vp, vp, C.c_double, vp, vp, vp]
     L.dg_limit.argtypes = [vp, vp, vp]
     L.dg_totals.argtypes = [vp, vp, vp, vp]
@@ -419,6 +421,15 @@ class Solver:
     def set_advance_mode(self, mode):
         """"graph" or "persistent": how advance() runs its steps (see dg_set_advance_mode)"""
         self._check(self._L.dg_set_advance_mode(self._h, ADVANCE_MODES[mode]))
+
+    def set_overlap(self, on):
+        """launch the step's kernels as programmatic dependents (dg_set_overlap)"""
+        self._check(self._L.dg_set_overlap(self._h, int(bool(on))))
+
+    def overlap(self):
+        v = C.c_int()
+        self._check(self._L.dg_overlap(self._h, C.byref(v)))
+        return bool(v.value)
 
     def advance_mode(self):
         m = C.c_int()

@@ -362,6 +362,25 @@ def test_profiled_advance_counts_every_kernel():
     assert s.status() == dg.DG_OK
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "mixed"])
+def test_overlap_off_gives_the_same_steps(precision):
+    """dg_set_overlap(0) (plain stream order) and the default overlapped
+    launches give the same states, limiters on, through rk_step and advance."""
+    m = MESHES["amr2"]
+    a = solver_for(m, 2, rk_order=3, precision=precision, limiter="characteristic", positivity=True)
+    b = solver_for(m, 2, rk_order=3, precision=precision, limiter="characteristic", positivity=True)
+    assert a.overlap() and b.overlap()
+    b.set_overlap(False)
+    assert not b.overlap()
+    W = wl.random_weights(2, a.N, a.n_cells, seed=350, slope=0.3)
+    Wa, Wb = to_dev(a, W), to_dev(b, W)
+    a.rk_step(Wa)
+    b.rk_step(Wb)
+    a.advance(Wa, 3)
+    b.advance(Wb, 3)
+    np.testing.assert_array_equal(Wa.cpu().numpy(), Wb.cpu().numpy())
+
+
 def density_at_l1_points(o, W):
     """rho_h of state W at the (k+3)^d rule's points of every cell, [q][cell]."""
     import itertools
