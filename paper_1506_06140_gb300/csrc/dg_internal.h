@@ -44,7 +44,12 @@ struct Shape {
   static constexpr int OFF_DEG = OFF_XI1 + Q1 * 3;                     // [N]      degree of phi_l
   static constexpr int OFF_PMAX = OFF_DEG + N;                         // [N] max |phi_l| on [-1,1]^d
   static constexpr int OFF_1D = OFF_PMAX + N;                          // Tab1D (sizes of Tab1D<double>)
-  static constexpr int TAB_SIZE = OFF_1D + 124;
+  static constexpr int TAB_SIZE = OFF_1D + 156;
+  // values per variable and face in the face-flux array: the flux at the
+  // face's Gauss points (2D), or its moments against the face's Legendre
+  // products of total degree <= k (3D, eq. dg_term3 restricted to a face)
+  static constexpr int NM = K1 * (K1 + 1) / 2;
+  static constexpr int FV = DIM == 3 ? NM : QF;
 };
 
 // One-dimensional tables of the tensor-product Gauss rule (k+1 <= 4 nodes),
@@ -59,6 +64,7 @@ struct Tab1D {
   real PWH[2][4][4]; // PWH[h][a][i] = PH[h][a][i] w_i
   real PE[2][4];     // PE[s][a] = sqrt(2a+1) P_a(2s - 1): values at -1 (s=0) and +1 (s=1)
   real W[4];         // Gauss weights w_i
+  real TH[2][4][4];  // TH[h][a][b]: P~_a((x + 2h - 1) / 2) = sum_{b <= a} TH[h][a][b] P~_b(x)
 };
 
 // ---------------------------------------------------------------------------

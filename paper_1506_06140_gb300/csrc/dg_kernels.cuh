@@ -221,7 +221,16 @@ void fill_tables(std::vector<double>& T, const std::vector<double>& gx,
       t1.PE[s][a] = v;
     }
   for (int i = 0; i <= K; ++i) t1.W[i] = gw[i];
-  static_assert(sizeof(Tab1D<double>) == 124 * sizeof(double), "Tab1D layout");
+  // half-interval maps: (1/2) sum_i P~_a(half node i) P~_b(x_i) w_i, exact for
+  // a + b <= 2k (the (k+1)-point rule), zero above the diagonal
+  for (int h = 0; h < 2; ++h)
+    for (int a = 0; a <= K; ++a)
+      for (int b = 0; b <= a; ++b) {
+        double s = 0.0;
+        for (int i = 0; i <= K; ++i) s += t1.PH[h][a][i] * t1.P[b][i] * gw[i];
+        t1.TH[h][a][b] = 0.5 * s;
+      }
+  static_assert(sizeof(Tab1D<double>) == 156 * sizeof(double), "Tab1D layout");
   std::memcpy(&T[S::OFF_1D], &t1, sizeof(t1));
 }
 

@@ -331,6 +331,92 @@ __device__ __forceinline__ void surface_side(const Tab1D<real>& T, const real (&
   }
 }
 
+// 3D faces: the face-flux array holds, per variable, the moments
+//   M(ea, eb) = sum_q f(q) P~_ea(x_qa) P~_eb(x_qb) w_qa w_qb,  ea + eb <= k,
+// of the flux at the face's Gauss points (q = qa + (k+1) qb along the two
+// tangential axes in increasing order): the sum-factorised first two
+// contractions of surface_side, done once per face instead of once per side.
+template <int K>
+__host__ __device__ constexpr int face_moment(int ea, int eb) {
+  return ea * (K + 1) - ea * (ea - 1) / 2 + eb;
+}
+
+template <typename real, int K>
+__device__ __forceinline__ void face_moments(const Tab1D<real>& T, const real* fq, real* M) {
+  constexpr int K1 = K + 1;
+  real H[K1][K1];  // [ea][qb] = sum_qa f w P_ea
+#pragma unroll
+  for (int ea = 0; ea <= K; ++ea)
+#pragma unroll
+    for (int qb = 0; qb < K1; ++qb) {
+      real s = real(0);
+#pragma unroll
+      for (int qa = 0; qa < K1; ++qa) s = fmac(fq[qa + K1 * qb], T.PW[ea][qa], s);
+      H[ea][qb] = s;
+    }
+#pragma unroll
+  for (int ea = 0; ea <= K; ++ea)
+#pragma unroll
+    for (int eb = 0; eb <= K - ea; ++eb) {
+      real s = real(0);
+#pragma unroll
+      for (int qb = 0; qb < K1; ++qb) s = fmac(H[ea][qb], T.PW[eb][qb], s);
+      M[face_moment<K>(ea, eb)] = s;
+    }
+}
+
+// acc_l -= sg * scale * sum over the face of f phi_l, from the face moments:
+// phi_(ed, ea, eb) restricted to side (DIR, S) is P~_ed(+-1) P~_ea P~_eb
+template <typename real, int K, int DIR, int S>
+__device__ __forceinline__ void surface_side_moments(const Tab1D<real>& T, const real* M, real scale, real* acc) {
+  constexpr int A = DIR == 0 ? 1 : 0;  // tangential axes, increasing
+  constexpr int BB = DIR == 2 ? 1 : 2;
+  const real ssg = S ? -scale : scale;
+#pragma unroll
+  for (int ea = 0; ea <= K; ++ea)
+#pragma unroll
+    for (int eb = 0; eb <= K - ea; ++eb) {
+      const real s = M[face_moment<K>(ea, eb)] * ssg;
+#pragma unroll
+      for (int ed = 0; ed <= K - ea - eb; ++ed) {
+        int e[3];
+        e[DIR] = ed;
+        e[A] = ea;
+        e[BB] = eb;
+        acc[bidx<3>(e[0], e[1], e[2])] = fmac(T.PE[S][ed], s, acc[bidx<3>(e[0], e[1], e[2])]);
+      }
+    }
+}
+
+// the moments of a sub-face (quadrant h of the coarse face, in the sub-face's
+// own coordinates) as moments against the coarse face's Legendre products:
+// P~_a on a half interval is sum_{b <= a} TH[half][a][b] P~_b of the half's
+// own coordinate, exactly
+template <typename real, int K>
+__device__ __forceinline__ void sub_to_coarse_moments(const Tab1D<real>& T, int h, const real* Ms, real* Mc) {
+  constexpr int K1 = K + 1;
+  const int h0 = h & 1, h1 = (h >> 1) & 1;
+  real G[K1][K1];  // [ea'][eb] = sum_{eb' <= eb} TH[h1][eb][eb'] Ms(ea', eb'), ea' + eb <= K
+#pragma unroll
+  for (int ea = 0; ea <= K; ++ea)
+#pragma unroll
+    for (int eb = 0; eb <= K - ea; ++eb) {
+      real s = real(0);
+#pragma unroll
+      for (int eb2 = 0; eb2 <= eb; ++eb2) s = fmac(T.TH[h1][eb][eb2], Ms[face_moment<K>(ea, eb2)], s);
+      G[ea][eb] = s;
+    }
+#pragma unroll
+  for (int ea = 0; ea <= K; ++ea)
+#pragma unroll
+    for (int eb = 0; eb <= K - ea; ++eb) {
+      real s = real(0);
+#pragma unroll
+      for (int ea2 = 0; ea2 <= ea; ++ea2) s = fmac(T.TH[h0][ea][ea2], G[ea2][eb], s);
+      Mc[face_moment<K>(ea, eb)] = s;
+    }
+}
+
 // trace of one variable on side (DIR, S) at the face points given by PT0/PT1
 template <typename real, int DIM, int K, int DIR, int B = 0>
 __device__ __forceinline__ void face_trace(const Tab1D<real>& T, const real* w, int s,
@@ -488,8 +574,26 @@ __device__ __forceinline__ void face_flux_body(const StageArgs<real>& a, int bid
     if (d2 == 0) hllc_flux<real, DIM>(uL, uR, 0, gamma, Fl);
     else if (d2 == 1) hllc_flux<real, DIM>(uL, uR, 1, gamma, Fl);
     else hllc_flux<real, DIM>(uL, uR, DIM - 1, gamma, Fl);
+    if constexpr (DIM == 3) {
+      // over the minus trace of this point, which only this item reads
 #pragma unroll
-    for (int vv = 0; vv < S::NV; ++vv) a.F[((size_t)vv * S::QF + q) * nf + f2] = Fl[vv];
+      for (int vv = 0; vv < S::NV; ++vv) sT[((0 * S::NV + vv) * S::QF + q) * FB + ff] = Fl[vv];
+    } else {
+#pragma unroll
+      for (int vv = 0; vv < S::NV; ++vv) a.F[((size_t)vv * S::QF + q) * nf + f2] = Fl[vv];
+    }
+  }
+  if constexpr (DIM == 3) {
+    // thread (face, variable): the face moments of its variable's flux
+    __syncthreads();
+    if (f < nf) {
+      real fq[S::QF], M[S::NM];
+#pragma unroll
+      for (int q = 0; q < S::QF; ++q) fq[q] = sT[((0 * S::NV + v) * S::QF + q) * FB + fl];
+      face_moments<real, K>(a.t1, fq, M);
+#pragma unroll
+      for (int m = 0; m < S::NM; ++m) a.F[((size_t)v * S::NM + m) * nf + f] = M[m];
+    }
   }
   (void)dir;
 }
@@ -541,12 +645,12 @@ struct CellTile {
 // overlaps the volume phase; a coarse side's sub-face fluxes load on use.
 template <typename real, int DIM, int K>
 struct FacePrefetch {
-  static constexpr bool ON = 2 * DIM * Shape<DIM, K>::QF * sizeof(real) <= 256;
+  static constexpr bool ON = 2 * DIM * Shape<DIM, K>::FV * sizeof(real) <= 256;
 };
 
 template <typename real, int DIM, int K>
 __device__ __forceinline__ void prefetch_faces(const StageArgs<real>& a, int c, int v, unsigned coarse,
-                                               real (&fp)[2 * DIM][Shape<DIM, K>::QF]) {
+                                               real (&fp)[2 * DIM][Shape<DIM, K>::FV]) {
   using S = Shape<DIM, K>;
   const int nc = a.m.ncells, nf = a.m.nfaces;
 #pragma unroll
@@ -554,7 +658,7 @@ __device__ __forceinline__ void prefetch_faces(const StageArgs<real>& a, int c, 
     const bool conf = !((coarse >> sd) & 1);
     const int e0 = conf ? a.m.sface[(size_t)sd * nc + c] : 0;
 #pragma unroll
-    for (int q = 0; q < S::QF; ++q) fp[sd][q] = conf ? a.F[((size_t)v * S::QF + q) * nf + e0] : real(0);
+    for (int q = 0; q < S::FV; ++q) fp[sd][q] = conf ? a.F[((size_t)v * S::FV + q) * nf + e0] : real(0);
   }
 }
 
@@ -565,17 +669,18 @@ __device__ __forceinline__ void surface_from_faces(const StageArgs<real>& a, int
   constexpr int DIR = SD >> 1, SS = SD & 1;
   const Tab1D<real>& T = a.t1;
   const int nc = a.m.ncells, nf = a.m.nfaces;
-  real fq[S::QF];
+  real fq[S::FV];
   if (!((coarse >> SD) & 1)) {
     if (fpre) {
 #pragma unroll
-      for (int q = 0; q < S::QF; ++q) fq[q] = fpre[q];
+      for (int q = 0; q < S::FV; ++q) fq[q] = fpre[q];
     } else {
       const int e0 = a.m.sface[(size_t)SD * nc + c];
 #pragma unroll
-      for (int q = 0; q < S::QF; ++q) fq[q] = a.F[((size_t)v * S::QF + q) * nf + e0];
+      for (int q = 0; q < S::FV; ++q) fq[q] = a.F[((size_t)v * S::FV + q) * nf + e0];
     }
-    surface_side<real, DIM, K, DIR, SS, B>(T, T.PW, T.PW, fq, real(1), acc);
+    if constexpr (DIM == 3) surface_side_moments<real, K, DIR, SS>(T, fq, real(1), acc);
+    else surface_side<real, DIM, K, DIR, SS, B>(T, T.PW, T.PW, fq, real(1), acc);
   } else {
     const int e0 = a.m.sface[(size_t)SD * nc + c];
     // coarse side of a hanging face: NSUB sub-faces in quadrant order
@@ -583,8 +688,14 @@ __device__ __forceinline__ void surface_from_faces(const StageArgs<real>& a, int
 #pragma unroll
     for (int h = 0; h < S::NSUB; ++h) {
 #pragma unroll
-      for (int q = 0; q < S::QF; ++q) fq[q] = a.F[((size_t)v * S::QF + q) * nf + e0 + h];
-      surface_side<real, DIM, K, DIR, SS, B>(T, T.PWH[h & 1], T.PWH[(h >> 1) & 1], fq, sub, acc);
+      for (int q = 0; q < S::FV; ++q) fq[q] = a.F[((size_t)v * S::FV + q) * nf + e0 + h];
+      if constexpr (DIM == 3) {
+        real Mc[S::NM];
+        sub_to_coarse_moments<real, K>(T, h, fq, Mc);
+        surface_side_moments<real, K, DIR, SS>(T, Mc, sub, acc);
+      } else {
+        surface_side<real, DIM, K, DIR, SS, B>(T, T.PWH[h & 1], T.PWH[(h >> 1) & 1], fq, sub, acc);
+      }
     }
   }
 }
@@ -641,7 +752,7 @@ __device__ __forceinline__ void cell_update_body(const StageArgs<real>& a, int b
   const Tab1D<real>& T = a.t1;
   constexpr bool PF = FacePrefetch<real, DIM, K>::ON;
   const unsigned coarse = valid ? a.m.scoarse[c] : 0u;
-  real fpre[PF ? 2 * DIM : 1][S::QF];
+  real fpre[PF ? 2 * DIM : 1][S::FV];
   if constexpr (PF) {
     if (valid) prefetch_faces<real, DIM, K>(a, c, v, coarse, fpre);
   }

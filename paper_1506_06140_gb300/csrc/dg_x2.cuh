@@ -185,11 +185,11 @@ cudaError_t launch_cell_x2(const void* pa, cudaStream_t s) {
   X2Args x;
   x.a = *static_cast<const StageArgs<float>*>(pa);
   if (x.a.m.ncells == 0) return cudaSuccess;
-  static_assert(sizeof(Tab1D<float>) == 124 * sizeof(float) && sizeof(Tab1D<f32x2>) == 124 * sizeof(f32x2),
-                "Tab1D layout");
+  constexpr int NT = sizeof(Tab1D<float>) / sizeof(float);
+  static_assert(sizeof(Tab1D<f32x2>) == NT * sizeof(f32x2), "Tab1D layout");
   const float* src = reinterpret_cast<const float*>(&x.a.t1);
   f32x2* dst = reinterpret_cast<f32x2*>(&x.t2);
-  for (int i = 0; i < 124; ++i) dst[i] = f32x2(src[i]);
+  for (int i = 0; i < NT; ++i) dst[i] = f32x2(src[i]);
   using XT = X2Tile<K, X2_TC>;
   cell_update_x2_kernel<K, X2_TC><<<(x.a.m.ncells + X2_TC - 1) / X2_TC, XT::THREADS, XT::SMEM, s>>>(x);
   return cudaGetLastError();
