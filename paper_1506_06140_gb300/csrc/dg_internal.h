@@ -111,7 +111,7 @@ struct StageArgs {
   const real* pre_prob = nullptr;  // [nprob] 2^(1-d) / dx per problem (ensembles)
   const real* tab = nullptr;
   const real* U = nullptr;
-  real* F = nullptr;            // face fluxes [NV][QF][nfaces]
+  real* F = nullptr;            // face fluxes [NV][FV][nfaces]: point values (2D), moments (3D)
   double gamma = 1.4;
   real gam = real(1.4), gm1 = real(0.4);  // gamma and gamma - 1 in the state precision (set on the host)
   int n_in = 0, n_out = 0;

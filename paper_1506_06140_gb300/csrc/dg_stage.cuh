@@ -486,7 +486,9 @@ __device__ __forceinline__ void face_trace(const Tab1D<real>& T, const real* w, 
 // Face kernel: FB faces per block, NV threads per face.
 //   1. thread (face, var): load both cells' weights of its variable and
 //      compute the traces at all face points -> shared memory;
-//   2. thread (face, point): HLLC flux -> F[var][point][face] (coalesced).
+//   2. thread (face, point): HLLC flux -> F[var][point][face] (coalesced);
+//      in 3D into shared memory, and then
+//   3. (3D) thread (face, var): the face moments of the flux -> F[var][moment][face].
 // A variant > 0 marks the coarse side of a hanging face: its points are a
 // half (2D) or quarter (3D) of the cell face.
 
