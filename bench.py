@@ -163,7 +163,7 @@ def shape(dim, k, basis="total"):
     return N, Q, QF, nv
 
 
-def kernel_flops(dim, k, basis="total"):
+def kernel_flops(dim, k, basis="total", moments=False):
     """Flops of the sum-factorised kernels: (cell kernel per cell, face kernel per face).
 
     Per variable (FMA counts; K1 = k+1, N2 = K1 (K1+1) / 2 pairs (a,b)):
@@ -173,7 +173,10 @@ def kernel_flops(dim, k, basis="total"):
       face trace     2D: N + K1^2             3D: N + N2 K1 + K1^3
     plus Euler fluxes (18 | 27 flop per point), HLLC (90 | 100 flop per face
     point) and the stage combination (5 flop per weight).  The 2D counts hold
-    for the tensor-product basis too (N = K1^2 there)."""
+    for the tensor-product basis too (N = K1^2 there).  With face moments
+    (3D, and 2D FP64) the face kernel contracts each face's flux once
+    (2D: K1^2, 3D: K1^3 + N2 K1 per variable) and a cell side costs
+    N + (number of moments)."""
     N, Q, QF, nv = shape(dim, k, basis)
     K1 = k + 1
     if dim == 2:
@@ -184,8 +187,15 @@ def kernel_flops(dim, k, basis="total"):
         m2n = N * K1 + N2 * K1 * K1 + K1 ** 4
         vol = dim * (k * K1 ** 3 + (N2 - K1) * K1 * K1 + (N - N2) * K1)
         surf, trace, flux_pt, hllc_pt = 2 * dim * (K1 ** 3 + N2 * K1 + N), N + N2 * K1 + K1 ** 3, 27, 100
+    face_mom = 0
+    if moments:
+        if dim == 2:
+            surf, face_mom = 2 * dim * (N + K1), K1 * K1
+        else:
+            N2 = K1 * (K1 + 1) // 2
+            surf, face_mom = 2 * dim * (N + N2), K1 ** 3 + N2 * K1
     cell = 2 * nv * (m2n + vol + surf) + flux_pt * Q + 5 * N * nv
-    face = 2 * 2 * nv * trace + hllc_pt * QF
+    face = 2 * 2 * nv * trace + hllc_pt * QF + 2 * nv * face_mom
     return cell, face
 
 
@@ -650,7 +660,7 @@ def summarize(args, results, world):
             kname = "cell_tc_kernel"
         tag = "%s_%s" % (wk["tag"], precision)
         if precision == "fp64" and kind in ("cell", "face"):
-            fc, ff = kernel_flops(dim, k, basis)
+            fc, ff = kernel_flops(dim, k, basis, moments=(dim == 3 or precision == "fp64"))
             fl = fc * cells if kind == "cell" else ff * dim * cells
             achieved = fl / avg_s / 1e12
             roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,

@@ -11,6 +11,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <type_traits>
 #include <utility>
 
 #include "dg_internal.h"
@@ -417,6 +418,55 @@ __device__ __forceinline__ void sub_to_coarse_moments(const Tab1D<real>& T, int 
     }
 }
 
+// Whether the face-flux array holds face moments: always in 3D, and in 2D
+// for an FP64 state (2D: M(e) = sum_q f(q) P~_e(x_q) w_q, e <= k, as many as
+// points; the FP32 2D kernels -- tensor-core, one thread per cell, packed
+// pairs -- read point values).
+template <typename real, int DIM>
+struct FaceMoments {
+  static constexpr bool ON = DIM == 3 || std::is_same<real, double>::value;
+};
+
+template <typename real, int K>
+__device__ __forceinline__ void face_moments_2d(const Tab1D<real>& T, const real* fq, real* M) {
+#pragma unroll
+  for (int e = 0; e <= K; ++e) {
+    real s = real(0);
+#pragma unroll
+    for (int q = 0; q <= K; ++q) s = fmac(fq[q], T.PW[e][q], s);
+    M[e] = s;
+  }
+}
+
+// the second half of surface_side (2D) from the face moments
+template <typename real, int K, int DIR, int S, int B = 0>
+__device__ __forceinline__ void surface_side_moments_2d(const Tab1D<real>& T, const real* M, real scale, real* acc) {
+  using BS = Basis2<K, B>;
+  constexpr int TA = DIR == 0 ? 1 : 0;
+  const real ssg = S ? -scale : scale;
+  real G[K + 1];
+#pragma unroll
+  for (int e = 0; e <= K; ++e) G[e] = M[e] * ssg;
+#pragma unroll
+  for (int ed = 0; ed <= K; ++ed)
+#pragma unroll
+    for (int et = 0; et <= BS::lim(ed); ++et)
+      acc[TA == 1 ? BS::idx(ed, et) : BS::idx(et, ed)] = fmac(T.PE[S][ed], G[et], acc[TA == 1 ? BS::idx(ed, et) : BS::idx(et, ed)]);
+}
+
+// sub-face moments (half h of the coarse face, own coordinate) as moments
+// against the coarse face's Legendre polynomials
+template <typename real, int K>
+__device__ __forceinline__ void sub_to_coarse_moments_2d(const Tab1D<real>& T, int h, const real* Ms, real* Mc) {
+#pragma unroll
+  for (int e = 0; e <= K; ++e) {
+    real s = real(0);
+#pragma unroll
+    for (int e2 = 0; e2 <= e; ++e2) s = fmac(T.TH[h][e][e2], Ms[e2], s);
+    Mc[e] = s;
+  }
+}
+
 // trace of one variable on side (DIR, S) at the face points given by PT0/PT1
 template <typename real, int DIM, int K, int DIR, int B = 0>
 __device__ __forceinline__ void face_trace(const Tab1D<real>& T, const real* w, int s,
@@ -576,7 +626,7 @@ __device__ __forceinline__ void face_flux_body(const StageArgs<real>& a, int bid
     if (d2 == 0) hllc_flux<real, DIM>(uL, uR, 0, gamma, Fl);
     else if (d2 == 1) hllc_flux<real, DIM>(uL, uR, 1, gamma, Fl);
     else hllc_flux<real, DIM>(uL, uR, DIM - 1, gamma, Fl);
-    if constexpr (DIM == 3) {
+    if constexpr (FaceMoments<real, DIM>::ON) {
       // over the minus trace of this point, which only this item reads
 #pragma unroll
       for (int vv = 0; vv < S::NV; ++vv) sT[((0 * S::NV + vv) * S::QF + q) * FB + ff] = Fl[vv];
@@ -585,16 +635,17 @@ __device__ __forceinline__ void face_flux_body(const StageArgs<real>& a, int bid
       for (int vv = 0; vv < S::NV; ++vv) a.F[((size_t)vv * S::QF + q) * nf + f2] = Fl[vv];
     }
   }
-  if constexpr (DIM == 3) {
+  if constexpr (FaceMoments<real, DIM>::ON) {
     // thread (face, variable): the face moments of its variable's flux
     __syncthreads();
     if (f < nf) {
-      real fq[S::QF], M[S::NM];
+      real fq[S::QF], M[S::FV];
 #pragma unroll
       for (int q = 0; q < S::QF; ++q) fq[q] = sT[((0 * S::NV + v) * S::QF + q) * FB + fl];
-      face_moments<real, K>(a.t1, fq, M);
+      if constexpr (DIM == 3) face_moments<real, K>(a.t1, fq, M);
+      else face_moments_2d<real, K>(a.t1, fq, M);
 #pragma unroll
-      for (int m = 0; m < S::NM; ++m) a.F[((size_t)v * S::NM + m) * nf + f] = M[m];
+      for (int m = 0; m < S::FV; ++m) a.F[((size_t)v * S::FV + m) * nf + f] = M[m];
     }
   }
   (void)dir;
@@ -682,6 +733,7 @@ __device__ __forceinline__ void surface_from_faces(const StageArgs<real>& a, int
       for (int q = 0; q < S::FV; ++q) fq[q] = a.F[((size_t)v * S::FV + q) * nf + e0];
     }
     if constexpr (DIM == 3) surface_side_moments<real, K, DIR, SS>(T, fq, real(1), acc);
+    else if constexpr (FaceMoments<real, DIM>::ON) surface_side_moments_2d<real, K, DIR, SS, B>(T, fq, real(1), acc);
     else surface_side<real, DIM, K, DIR, SS, B>(T, T.PW, T.PW, fq, real(1), acc);
   } else {
     const int e0 = a.m.sface[(size_t)SD * nc + c];
@@ -695,6 +747,10 @@ __device__ __forceinline__ void surface_from_faces(const StageArgs<real>& a, int
         real Mc[S::NM];
         sub_to_coarse_moments<real, K>(T, h, fq, Mc);
         surface_side_moments<real, K, DIR, SS>(T, Mc, sub, acc);
+      } else if constexpr (FaceMoments<real, DIM>::ON) {
+        real Mc[S::FV];
+        sub_to_coarse_moments_2d<real, K>(T, h, fq, Mc);
+        surface_side_moments_2d<real, K, DIR, SS, B>(T, Mc, sub, acc);
       } else {
         surface_side<real, DIM, K, DIR, SS, B>(T, T.PWH[h & 1], T.PWH[(h >> 1) & 1], fq, sub, acc);
       }
