@@ -3,6 +3,7 @@
 #include <mutex>
 
 #include "dg_internal.h"
+#include "dg_physics.cuh"
 
 namespace dgi {
 
@@ -111,6 +112,18 @@ cudaError_t launch_convert(const double* src, void* dst, size_t n, int esize, cu
 cudaError_t launch_dt_finalize(const unsigned long long* bits, int nprob, double factor,
                                double* dt, double* dt_copy, cudaStream_t s) {
   dt_finalize_kernel<<<(nprob + 255) / 256, 256, 0, s>>>(bits, nprob, factor, dt, dt_copy);
+  return cudaGetLastError();
+}
+
+__global__ void recip_kernel(const double* x, double* out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = recip(x[i]);
+}
+
+cudaError_t launch_recip(const double* x, double* out, int64_t n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const int64_t b = (n + 255) / 256;
+  recip_kernel<<<(unsigned)(b < 4096 ? b : 4096), 256, 0, s>>>(x, out, n);
   return cudaGetLastError();
 }
 

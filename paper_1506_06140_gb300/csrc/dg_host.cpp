@@ -2235,6 +2235,11 @@ int dg_overlap(const dg_handle* h, int* on) {
   return DG_OK;
 }
 
+int dg_test_recip(const double* x_dev, double* out_dev, int64_t n, void* stream) {
+  if (!x_dev || !out_dev || n < 0) return DG_ERR_ARG;
+  return launch_recip(x_dev, out_dev, n, static_cast<cudaStream_t>(stream)) == cudaSuccess ? DG_OK : DG_ERR_CUDA;
+}
+
 int dg_test_force_timeout(dg_handle* h) {
   if (!check_handle(h)) return DG_ERR_ARG;
   if (!h->use_tc) return fail(h, DG_ERR_UNSUPPORTED, "dg_test_force_timeout: no tensor-core cell kernel");

@@ -512,3 +512,20 @@ def test_one_thread_per_cell_steps_match_tiled():
     s64 = solver_for(m, 3, precision="fp64")
     with pytest.raises(dg.DGError):
         s64.set_tiles(1, 32)
+
+
+def test_fp64_reciprocal_within_two_ulp():
+    """The FP64 flux formulas' reciprocal (a Newton-Raphson refinement of the
+    hardware approximation) against numpy's correctly rounded 1/x, over
+    log-uniform x in [1e-12, 1e12] and around powers of two."""
+    dg = dg_mod()
+    rng = np.random.default_rng(360)
+    x = np.exp(rng.uniform(np.log(1e-12), np.log(1e12), 200000))
+    p2 = np.ldexp(1.0, np.arange(-40, 41))
+    x = np.concatenate([x, p2, np.nextafter(p2, 0.0), np.nextafter(p2, np.inf), [1.4, 0.4, 5e-6, 3.0]])
+    got = dg.recip_check(torch.as_tensor(x, device="cuda")).cpu().numpy()
+    exact = 1.0 / x
+    ulp = np.spacing(np.abs(exact))
+    err = np.abs(got - exact) / ulp
+    assert err.max() <= 2.0, err.max()
+    assert np.mean(got == exact) > 0.5  # mostly the correctly rounded value
