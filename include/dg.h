@@ -436,13 +436,14 @@ int dg_totals_noalloc(int dim, int n_basis, int64_t n_cells, int precision, doub
  * (precisions other than DG_FP32_TC and DG_MIXED_TC). */
 int dg_test_force_timeout(dg_handle* h);
 
-/* Test hook (no counterpart in the paper): out_dev[i] = the reciprocal that
- * the FP64 flux formulas use (Euler flux 1/rho, HLLC), for n device doubles
- * x_dev[i] > 0 (normal).  It refines the hardware's approximate reciprocal by
- * one Newton-Raphson step of third order and is within an ulp or two of 1/x;
- * the test checks that bound.  Asynchronous on the stream; DG_ERR_ARG for NULL
- * pointers or n < 0. */
-int dg_test_recip(const double* x_dev, double* out_dev, int64_t n, void* stream);
+/* Test hook (no counterpart in the paper): the FP64 flux formulas' own
+ * reciprocal (op 0: Euler flux 1/rho, HLLC) and square root (op 1: HLLC sound
+ * speeds) of n device doubles x_dev[i] > 0 (normal), into out_dev.  Both
+ * refine the hardware's approximations (a third-order step, then for the
+ * root a Newton step) and stay within an ulp or two of the correctly rounded
+ * value; the test checks that bound.  Asynchronous on the stream;
+ * DG_ERR_ARG for NULL pointers, n < 0 or another op. */
+int dg_test_flux_math(int op, const double* x_dev, double* out_dev, int64_t n, void* stream);
 
 /* Reads and clears the device status word (DG_OK, DG_ERR_NONPHYSICAL, ...).
  * Synchronises the handle's last stream. */

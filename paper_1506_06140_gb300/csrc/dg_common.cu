@@ -115,15 +115,15 @@ cudaError_t launch_dt_finalize(const unsigned long long* bits, int nprob, double
   return cudaGetLastError();
 }
 
-__global__ void recip_kernel(const double* x, double* out, int64_t n) {
+__global__ void flux_math_kernel(int op, const double* x, double* out, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = recip(x[i]);
+    out[i] = op == 0 ? recip(x[i]) : sqrt_pos(x[i]);
 }
 
-cudaError_t launch_recip(const double* x, double* out, int64_t n, cudaStream_t s) {
+cudaError_t launch_flux_math(int op, const double* x, double* out, int64_t n, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   const int64_t b = (n + 255) / 256;
-  recip_kernel<<<(unsigned)(b < 4096 ? b : 4096), 256, 0, s>>>(x, out, n);
+  flux_math_kernel<<<(unsigned)(b < 4096 ? b : 4096), 256, 0, s>>>(op, x, out, n);
   return cudaGetLastError();
 }
 

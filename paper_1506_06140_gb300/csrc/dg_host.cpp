@@ -2235,9 +2235,10 @@ int dg_overlap(const dg_handle* h, int* on) {
   return DG_OK;
 }
 
-int dg_test_recip(const double* x_dev, double* out_dev, int64_t n, void* stream) {
-  if (!x_dev || !out_dev || n < 0) return DG_ERR_ARG;
-  return launch_recip(x_dev, out_dev, n, static_cast<cudaStream_t>(stream)) == cudaSuccess ? DG_OK : DG_ERR_CUDA;
+int dg_test_flux_math(int op, const double* x_dev, double* out_dev, int64_t n, void* stream) {
+  if ((op != 0 && op != 1) || !x_dev || !out_dev || n < 0) return DG_ERR_ARG;
+  return launch_flux_math(op, x_dev, out_dev, n, static_cast<cudaStream_t>(stream)) == cudaSuccess ? DG_OK
+                                                                                                : DG_ERR_CUDA;
 }
 
 int dg_test_force_timeout(dg_handle* h) {

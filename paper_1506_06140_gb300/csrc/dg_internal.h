@@ -363,7 +363,7 @@ cudaError_t launch_adapt_project(const BaseGrid& g, int esize, int nv, int N, co
 cudaError_t launch_set_scalar(double* dst, int n, double value, cudaStream_t s);
 // dst[i] = value for i < n, elements of esize bytes (4: float, 8: double)
 cudaError_t launch_fill(void* dst, size_t n, double value, int esize, cudaStream_t s);
-cudaError_t launch_recip(const double* x, double* out, int64_t n, cudaStream_t s);
+cudaError_t launch_flux_math(int op, const double* x, double* out, int64_t n, cudaStream_t s);
 // dst[i] = src[i] converted to elements of esize bytes (4: float, 8: double)
 cudaError_t launch_convert(const double* src, void* dst, size_t n, int esize, cudaStream_t s);
 cudaError_t launch_dt_finalize(const unsigned long long* bits, int nprob, double factor, double* dt,

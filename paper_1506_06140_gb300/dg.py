@@ -28,7 +28,7 @@ EXPORTS = ["dg_default_options", "dg_create", "dg_destroy", "dg_last_error", "dg
            "dg_create_batch", "dg_batch_advance", "dg_n_problems", "dg_tiles",
            "dg_limiter_counts", "dg_set_tiles", "dg_adapt_mark", "dg_adapt_set", "dg_regrid",
            "dg_set_gravity", "dg_test_force_timeout", "dg_set_advance_mode", "dg_advance_mode",
-           "dg_advance_dt", "dg_set_overlap", "dg_overlap", "dg_test_recip"]
+           "dg_advance_dt", "dg_set_overlap", "dg_overlap", "dg_test_flux_math"]
 KERNEL_KINDS = ["face", "cell", "limit", "dt", "other", "adjoint"]
 ADVANCE_MODES = {"graph": 0, "persistent": 1}
 
@@ -81,7 +81,7 @@ def load(path=LIB_PATH):
     L.dg_advance.argtypes = [vp, vp, C.c_int, vp, vp]
     L.dg_advance_dt.argtypes = [vp, vp, C.c_int, C.c_double, vp]
     L.dg_set_overlap.argtypes = [vp, C.c_int]
-    L.dg_test_recip.argtypes = [vp, vp, C.c_int64, vp]
+    L.dg_test_flux_math.argtypes = [C.c_int, vp, vp, C.c_int64, vp]
     L.dg_overlap.argtypes = [vp, C.POINTER(C.c_int)]
     L.dg_rk_step_adjoint.argtypes = [vp, vp, C.c_double, vp, vp, vp]
     L.dg_limit.argtypes = [vp, vp, vp]
@@ -113,16 +113,16 @@ def load(path=LIB_PATH):
     return L
 
 
-def recip_check(x):
-    """Test hook: the FP64 flux formulas' reciprocal of every entry of the
-    float64 CUDA tensor x (dg_test_recip)."""
+def flux_math_check(op, x):
+    """Test hook: the FP64 flux formulas' reciprocal ("recip") or square root
+    ("sqrt") of every entry of the float64 CUDA tensor x (dg_test_flux_math)."""
     L = load()
     assert x.is_cuda and x.dtype == torch.float64
     x = x.contiguous()
     out = torch.empty_like(x)
-    r = L.dg_test_recip(_ptr(x), _ptr(out), x.numel(), _stream())
+    r = L.dg_test_flux_math({"recip": 0, "sqrt": 1}[op], _ptr(x), _ptr(out), x.numel(), _stream())
     if r != DG_OK:
-        raise DGError(r, "dg_test_recip")
+        raise DGError(r, "dg_test_flux_math")
     return out
 
 

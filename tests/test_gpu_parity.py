@@ -514,17 +514,19 @@ def test_one_thread_per_cell_steps_match_tiled():
         s64.set_tiles(1, 32)
 
 
-def test_fp64_reciprocal_within_two_ulp():
-    """The FP64 flux formulas' reciprocal (a Newton-Raphson refinement of the
-    hardware approximation) against numpy's correctly rounded 1/x, over
-    log-uniform x in [1e-12, 1e12] and around powers of two."""
+@pytest.mark.parametrize("op", ["recip", "sqrt"])
+def test_fp64_flux_math_within_two_ulp(op):
+    """The FP64 flux formulas' reciprocal and square root (refinements of the
+    hardware approximations) against numpy's correctly rounded 1/x and
+    sqrt(x), over log-uniform x in [1e-12, 1e12] and around powers of two
+    (odd and even exponents for the root)."""
     dg = dg_mod()
     rng = np.random.default_rng(360)
     x = np.exp(rng.uniform(np.log(1e-12), np.log(1e12), 200000))
     p2 = np.ldexp(1.0, np.arange(-40, 41))
     x = np.concatenate([x, p2, np.nextafter(p2, 0.0), np.nextafter(p2, np.inf), [1.4, 0.4, 5e-6, 3.0]])
-    got = dg.recip_check(torch.as_tensor(x, device="cuda")).cpu().numpy()
-    exact = 1.0 / x
+    got = dg.flux_math_check(op, torch.as_tensor(x, device="cuda")).cpu().numpy()
+    exact = 1.0 / x if op == "recip" else np.sqrt(x)
     ulp = np.spacing(np.abs(exact))
     err = np.abs(got - exact) / ulp
     assert err.max() <= 2.0, err.max()
