@@ -438,7 +438,8 @@ int dg_test_force_timeout(dg_handle* h);
 
 /* Test hook (no counterpart in the paper): the FP64 flux formulas' own
  * reciprocal (op 0: Euler flux 1/rho, HLLC) and square root (op 1: HLLC sound
- * speeds) of n device doubles x_dev[i] > 0 (normal), into out_dev.  Both
+ * speeds) of n device doubles x_dev[i] (normal; nonzero for op 0, positive
+ * for op 1), into out_dev.  Both
  * refine the hardware's approximations (a third-order step, then for the
  * root a Newton step) and stay within an ulp or two of the correctly rounded
  * value; the test checks that bound.  Asynchronous on the stream;

@@ -30,7 +30,7 @@ template <typename real, int DIM>
 __device__ __forceinline__ void flux_vjp(const real* u, const real (*g)[DIM + 2], real g1,
                                          real* out) {
   constexpr int E = DIM + 1;
-  const real rinv = real(1) / u[0];
+  const real rinv = recip(u[0]);
   real v[DIM], m2 = real(0);
 #pragma unroll
   for (int b = 0; b < DIM; ++b) {
@@ -84,7 +84,7 @@ __device__ __forceinline__ void hllc_vjp(const real* uL, const real* uR, real ga
   const real g1 = gamma - real(1);
   // ---- forward
   const real rL = uL[0], rR = uR[0];
-  const real iL = real(1) / rL, iR = real(1) / rR;
+  const real iL = recip(rL), iR = recip(rR);
   real kL = real(0), kR = real(0);
 #pragma unroll
   for (int b = 0; b < DIM; ++b) {
@@ -95,14 +95,15 @@ __device__ __forceinline__ void hllc_vjp(const real* uL, const real* uR, real ga
   const real pR = g1 * (uR[E] - real(0.5) * kR * iR);
   const real vL = uL[1 + A] * iL, vR = uR[1 + A] * iR;
   const real XL = gamma * pL * iL, XR = gamma * pR * iR;
-  const real cL = sqrt(XL), cR = sqrt(XR);
+  const real cL = sqrt_pos(XL), cR = sqrt_pos(XR);
   const bool minR = (vR - cR) < (vL - cL);  // S_L from the right state
   const bool maxR = (vL + cL) < (vR + cR);  // S_R from the right state
   const real SL = minR ? vR - cR : vL - cL;
   const real SR = maxR ? vR + cR : vL + cL;
   const real dL = rL * (SL - vL), dR = rR * (SR - vR);
   const real num = pR - pL + vL * dL - vR * dR, den = dL - dR;
-  const real Ss = num / den;
+  const real iden = recip(den);
+  const real Ss = num * iden;
   const bool left = (SL >= real(0)) || (Ss >= real(0));
   const bool star = left ? (SL < real(0)) : (SR > real(0));
   const real* u = left ? uL : uR;
@@ -119,8 +120,9 @@ __device__ __forceinline__ void hllc_vjp(const real* uL, const real* uR, real ga
   if (star) {
     const real rsv = r * (S - v);
     const real Dn = S - Ss;
-    const real fac = rsv / Dn;
-    const real prs = p / rsv;
+    const real irsv = recip(rsv), iDn = recip(Dn);
+    const real fac = rsv * iDn;
+    const real prs = p * irsv;
     const real Y = u[E] * ir + (Ss - v) * (Ss + prs);
     real us[NV];
     us[0] = fac;
@@ -159,11 +161,11 @@ __device__ __forceinline__ void hllc_vjp(const real* uL, const real* uR, real ga
       Ssb += Ab + Bb;
       vb -= Ab;
       const real prsb = Bb;
-      pb += prsb / rsv;
-      real rsvb = -prsb * prs / rsv;
+      pb += prsb * irsv;
+      real rsvb = -prsb * prs * irsv;
       // fac = rsv / Dn, Dn = S - Ss
-      rsvb += facb / Dn;
-      const real Dnb = -facb * fac / Dn;
+      rsvb += facb * iDn;
+      const real Dnb = -facb * fac * iDn;
       Sb += Dnb;
       Ssb -= Dnb;
       // rsv = r (S - v)
@@ -196,8 +198,8 @@ __device__ __forceinline__ void hllc_vjp(const real* uL, const real* uR, real ga
   bR[0] += left ? real(0) : rb;
   real SLb = left ? Sb : real(0), SRb = left ? real(0) : Sb;
   // S* = num / den
-  const real numb = Ssb / den;
-  const real denb = -Ssb * Ss / den;
+  const real numb = Ssb * iden;
+  const real denb = -Ssb * Ss * iden;
   pRb += numb;
   pLb -= numb;
   vLb += numb * dL;
@@ -217,7 +219,7 @@ __device__ __forceinline__ void hllc_vjp(const real* uL, const real* uR, real ga
   if (maxR) { vRb += SRb; cRb += SRb; } else { vLb += SRb; cLb += SRb; }
   // c = sqrt(gamma p i)
   {
-    const real XLb = cLb / (real(2) * cL), XRb = cRb / (real(2) * cR);
+    const real XLb = cLb * recip(real(2) * cL), XRb = cRb * recip(real(2) * cR);
     pLb += XLb * gamma * iL;
     iLb += XLb * gamma * pL;
     pRb += XRb * gamma * iR;

@@ -525,6 +525,8 @@ def test_fp64_flux_math_within_two_ulp(op):
     x = np.exp(rng.uniform(np.log(1e-12), np.log(1e12), 200000))
     p2 = np.ldexp(1.0, np.arange(-40, 41))
     x = np.concatenate([x, p2, np.nextafter(p2, 0.0), np.nextafter(p2, np.inf), [1.4, 0.4, 5e-6, 3.0]])
+    if op == "recip":  # HLLC takes reciprocals of signed wave-speed products too
+        x = np.concatenate([x, -x])
     got = dg.flux_math_check(op, torch.as_tensor(x, device="cuda")).cpu().numpy()
     exact = 1.0 / x if op == "recip" else np.sqrt(x)
     ulp = np.spacing(np.abs(exact))
