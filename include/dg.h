@@ -436,14 +436,14 @@ int dg_totals_noalloc(int dim, int n_basis, int64_t n_cells, int precision, doub
  * (precisions other than DG_FP32_TC and DG_MIXED_TC). */
 int dg_test_force_timeout(dg_handle* h);
 
-/* Test hook (no counterpart in the paper): the FP64 flux formulas' own
- * reciprocal (op 0: Euler flux 1/rho, HLLC) and square root (op 1: HLLC sound
- * speeds) of n device doubles x_dev[i] (normal; nonzero for op 0, positive
- * for op 1), into out_dev.  Both
- * refine the hardware's approximations (a third-order step, then for the
- * root a Newton step) and stay within an ulp or two of the correctly rounded
- * value; the test checks that bound.  Asynchronous on the stream;
- * DG_ERR_ARG for NULL pointers, n < 0 or another op. */
+/* Test hook (no counterpart in the paper): the flux formulas' own reciprocal
+ * (Euler flux 1/rho, HLLC) and square root (HLLC sound speeds) of n device
+ * doubles x_dev[i] (normal; nonzero for a reciprocal, positive for a root),
+ * into out_dev: op 0 FP64 reciprocal, 1 FP64 root, 2 FP32 reciprocal and 3
+ * FP32 root of (float)x, widened.  All refine the hardware's approximations
+ * and stay within an ulp or two of the correctly rounded value; the test
+ * checks that bound.  Asynchronous on the stream; DG_ERR_ARG for NULL
+ * pointers, n < 0 or another op. */
 int dg_test_flux_math(int op, const double* x_dev, double* out_dev, int64_t n, void* stream);
 
 /* Reads and clears the device status word (DG_OK, DG_ERR_NONPHYSICAL, ...).

@@ -117,7 +117,10 @@ cudaError_t launch_dt_finalize(const unsigned long long* bits, int nprob, double
 
 __global__ void flux_math_kernel(int op, const double* x, double* out, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = op == 0 ? recip(x[i]) : sqrt_pos(x[i]);
+    out[i] = op == 0 ? recip(x[i])
+             : op == 1 ? sqrt_pos(x[i])
+             : op == 2 ? (double)recip((float)x[i])
+                       : (double)sqrt_pos((float)x[i]);
 }
 
 cudaError_t launch_flux_math(int op, const double* x, double* out, int64_t n, cudaStream_t s) {

@@ -2236,7 +2236,7 @@ int dg_overlap(const dg_handle* h, int* on) {
 }
 
 int dg_test_flux_math(int op, const double* x_dev, double* out_dev, int64_t n, void* stream) {
-  if ((op != 0 && op != 1) || !x_dev || !out_dev || n < 0) return DG_ERR_ARG;
+  if (op < 0 || op > 3 || !x_dev || !out_dev || n < 0) return DG_ERR_ARG;
   return launch_flux_math(op, x_dev, out_dev, n, static_cast<cudaStream_t>(stream)) == cudaSuccess ? DG_OK
                                                                                                 : DG_ERR_CUDA;
 }

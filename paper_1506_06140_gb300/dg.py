@@ -114,13 +114,15 @@ def load(path=LIB_PATH):
 
 
 def flux_math_check(op, x):
-    """Test hook: the FP64 flux formulas' reciprocal ("recip") or square root
-    ("sqrt") of every entry of the float64 CUDA tensor x (dg_test_flux_math)."""
+    """Test hook: the flux formulas' reciprocal ("recip", FP64; "recip32", FP32)
+    or square root ("sqrt", "sqrt32") of every entry of the float64 CUDA
+    tensor x (dg_test_flux_math; the FP32 ones of float(x), widened)."""
     L = load()
     assert x.is_cuda and x.dtype == torch.float64
     x = x.contiguous()
     out = torch.empty_like(x)
-    r = L.dg_test_flux_math({"recip": 0, "sqrt": 1}[op], _ptr(x), _ptr(out), x.numel(), _stream())
+    r = L.dg_test_flux_math({"recip": 0, "sqrt": 1, "recip32": 2, "sqrt32": 3}[op], _ptr(x), _ptr(out),
+                             x.numel(), _stream())
     if r != DG_OK:
         raise DGError(r, "dg_test_flux_math")
     return out

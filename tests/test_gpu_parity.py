@@ -514,8 +514,8 @@ def test_one_thread_per_cell_steps_match_tiled():
         s64.set_tiles(1, 32)
 
 
-@pytest.mark.parametrize("op", ["recip", "sqrt"])
-def test_fp64_flux_math_within_two_ulp(op):
+@pytest.mark.parametrize("op", ["recip", "sqrt", "recip32", "sqrt32"])
+def test_flux_math_within_two_ulp(op):
     """The FP64 flux formulas' reciprocal and square root (refinements of the
     hardware approximations) against numpy's correctly rounded 1/x and
     sqrt(x), over log-uniform x in [1e-12, 1e12] and around powers of two
@@ -525,11 +525,18 @@ def test_fp64_flux_math_within_two_ulp(op):
     x = np.exp(rng.uniform(np.log(1e-12), np.log(1e12), 200000))
     p2 = np.ldexp(1.0, np.arange(-40, 41))
     x = np.concatenate([x, p2, np.nextafter(p2, 0.0), np.nextafter(p2, np.inf), [1.4, 0.4, 5e-6, 3.0]])
-    if op == "recip":  # HLLC takes reciprocals of signed wave-speed products too
+    if op.startswith("recip"):  # HLLC takes reciprocals of signed wave-speed products too
         x = np.concatenate([x, -x])
+    if op.endswith("32"):
+        x = x.astype(np.float32).astype(np.float64)
     got = dg.flux_math_check(op, torch.as_tensor(x, device="cuda")).cpu().numpy()
-    exact = 1.0 / x if op == "recip" else np.sqrt(x)
-    ulp = np.spacing(np.abs(exact))
+    if op.endswith("32"):
+        x32 = x.astype(np.float32)
+        exact = (np.float32(1) / x32 if op == "recip32" else np.sqrt(x32)).astype(np.float64)
+        ulp = np.spacing(np.abs(exact).astype(np.float32)).astype(np.float64)
+    else:
+        exact = 1.0 / x if op == "recip" else np.sqrt(x)
+        ulp = np.spacing(np.abs(exact))
     err = np.abs(got - exact) / ulp
     assert err.max() <= 2.0, err.max()
     assert np.mean(got == exact) > 0.5  # mostly the correctly rounded value
