@@ -113,13 +113,14 @@ typedef struct {
   double eps;        /* positivity floor of density and pressure at the limiter's points; an FP32
                         state also keeps 2^-20 of the absolute weight sums (at most half the mean),
                         above the FP32 rounding of the stored limited weights */
-  int precision;     /* DG_FP64, DG_FP32, DG_FP32_TC or DG_MIXED (state, fluxes and
-                        contractions); the totals, L1 error, timestep and positivity
-                        check stay FP64 */
+  int precision;     /* DG_FP64, DG_FP32, DG_FP32_TC, DG_MIXED or DG_MIXED_TC (state,
+                        fluxes and contractions); the totals, L1 error, timestep and
+                        positivity check stay FP64 */
   int autotune;      /* 1: dg_create times the stage kernels on the mesh at every
                         feasible tile (16, 32 or 64 cells or faces per thread block) and keeps the
                         fastest, FP32 2D handles also trying the one-thread-per-
-                        cell kernel; 0 (default): fixed tiles.  The tiled kernels
+                        cell kernel and the packed-pair cell kernel; 0 (default):
+                        fixed tiles.  The tiled kernels and the packed-pair kernel
                         give identical results for every tile; the one-thread-per-
                         cell kernel sums in another order (FP32 rounding).  See
                         dg_tiles. */

@@ -187,6 +187,41 @@ def test_advance_repeats_rk_step():
     np.testing.assert_allclose(t1, t0, rtol=0, atol=1e-12 * np.abs(t0).max())
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_vortex_256_k3_rk4_full_size(precision):
+    """The benchmarked workload itself: the 256^2 vortex with Q_3 (16
+    coefficients per variable), SSP-RK4.  Right-hand side, timestep and one
+    CFL step through advance() -- the one-step graph the benchmark replays --
+    against the oracle with the same basis.  FP64 at the total-degree bars;
+    FP32 at the full-size FP32 bars (dW/dt is a ~1.4e3-fold cancellation of
+    volume and surface terms on this smooth state, so FP32 rounding bounds the
+    error near 6e-4 of max |dW/dt|)."""
+    m = wl.mesh_uniform(2, [256, 256], [-5.0, -5.0], [5.0, 5.0])
+    o = oracle_for(m, 3, rk_order=4)
+    s = solver_for(m, 3, rk_order=4, precision=precision)
+    assert s.N == 16
+    U = wl.vortex(o.quad_points())
+    Wd = s.project(torch.as_tensor(U, device="cuda"))
+    W = Wd.double().cpu().numpy()
+    ref_rhs = o.rhs(W)
+    e, erms = rel_err(s.rhs(Wd).cpu().numpy(), ref_rhs)
+    dt = o.compute_dt(W)
+    dt_hist = torch.zeros(1, dtype=torch.float64, device="cuda")
+    s.advance(Wd, 1, dt_hist)
+    got = Wd.double().cpu().numpy()
+    ref, _ = o.rk_step(W, dt)
+    if precision == "fp64":
+        assert e < TOL64, e
+        assert dt_hist.item() == pytest.approx(dt, rel=1e-14)
+        e_step, _ = rel_err(got - W, ref - W)
+        assert e_step < 1e-10, e_step
+    else:
+        assert e < 1e-3 and erms < 5e-5, (e, erms)
+        assert dt_hist.item() == pytest.approx(dt, rel=1e-6)
+        assert np.max(np.abs(got - ref)) < 1e-6 * np.max(np.abs(ref))
+    assert s.status() == 0
+
+
 def test_vortex_error_below_the_total_degree_basis():
     """Q_3 contains P_3: on the isentropic vortex after one time unit the
     tensor basis' L1 density error is below the total-degree basis' (both
