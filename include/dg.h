@@ -447,6 +447,45 @@ int dg_test_force_timeout(dg_handle* h);
  * pointers, n < 0 or another op. */
 int dg_test_flux_math(int op, const double* x_dev, double* out_dev, int64_t n, void* stream);
 
+/* Test hook (host only: no device work, usable without a GPU): the mesh
+ * tables dg_create builds for mesh (Sec. 4: base cells, refined base cells
+ * replaced by their 2^dim children, hanging faces).  counts[3] receives the
+ * numbers of cells, faces and refined base cells.  Each non-NULL array is
+ * filled (caller-owned host memory; call first with NULL arrays to size them):
+ *   nbr[2*dim][cells]   as dg_neighbor_table;
+ *   levels[cells]       as dg_cell_levels;
+ *   faces[3][faces]     minus cell, plus cell (-1 for the missing cell of a
+ *                       face on a transmissive boundary), and the packed
+ *                       face info axis | vm << 2 |
+ *                       vp << 5, where a nonzero variant vm (vp) marks the
+ *                       minus (plus) side as the coarse side of a hanging
+ *                       face and gives 1 + the quadrant of that side's face
+ *                       the sub-face covers;
+ *   sface[2*dim][cells] the face of each cell side (side = 2*axis + {0:-, 1:+});
+ *                       on the coarse side of a hanging face its first
+ *                       sub-face, the others following in quadrant order.
+ * DG_ERR_ARG for a NULL mesh or counts, or a mesh dg_create rejects. */
+int dg_test_mesh_tables(const dg_mesh_desc* mesh, int64_t* counts, int32_t* nbr, int32_t* levels,
+                        int32_t* faces, int32_t* sface);
+
+/* Test hook (host only): the stage program dg_create derives from the SSP
+ * Runge-Kutta tableau of order rk_order (1..4; Appendix D), unlimited
+ * (limited = 0) or with the limiter pass after every stage (limited = 1).
+ * A step runs the program's ops in order on registers R[0] = the caller's
+ * state W and scratch registers R[1..n_regs]: op i evaluates K = dW/dt at
+ * R[in_reg]; then, for each output o in order,
+ *   R[out[o]] = ck[o] * dt * K + sum_r C[o][r] * R[in[r]],
+ * an input equal to in_reg reading that register's value at the start of
+ * the op; then, when lim_src >= 0, R[lim_dst] = limit(R[lim_src]).  (The
+ * FP64-state mixed modes keep the unlimited registers as FP32 differences
+ * from W; the program is the same.)  With ops_out non-NULL it receives
+ * max_ops records of DG_TEST_OP_DOUBLES doubles each: in_reg, n_in, n_out,
+ * lim_src, lim_dst, in[4], out[3] (-1 past n_in, n_out), C[3][4]
+ * (row-major), ck[3].  *n_ops and *n_regs are always written.  DG_ERR_ARG for
+ * a bad order or flag, NULL counters or max_ops below the op count. */
+#define DG_TEST_OP_DOUBLES 27
+int dg_test_stage_program(int rk_order, int limited, double* ops_out, int max_ops, int* n_ops, int* n_regs);
+
 /* Reads and clears the device status word (DG_OK, DG_ERR_NONPHYSICAL, ...).
  * Synchronises the handle's last stream. */
 int dg_status(dg_handle* h, int* device_status_host);

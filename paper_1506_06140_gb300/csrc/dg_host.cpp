@@ -2241,6 +2241,61 @@ int dg_test_flux_math(int op, const double* x_dev, double* out_dev, int64_t n, v
                                                                                                 : DG_ERR_CUDA;
 }
 
+int dg_test_mesh_tables(const dg_mesh_desc* mesh, int64_t* counts, int32_t* nbr, int32_t* levels,
+                        int32_t* faces, int32_t* sface) {
+  if (!mesh || !counts) return DG_ERR_ARG;
+  if (mesh->dim != 2 && mesh->dim != 3) return DG_ERR_ARG;
+  // a handle without device state: build_mesh is host work only
+  dg_handle h;
+  h.dim = mesh->dim;
+  if (build_mesh(&h, mesh) != DG_OK) return DG_ERR_ARG;
+  const size_t nc = (size_t)h.ncells, nf = (size_t)h.nfaces, sides = (size_t)2 * h.dim;
+  counts[0] = (int64_t)nc;
+  counts[1] = (int64_t)nf;
+  counts[2] = (int64_t)h.nnodes;
+  if (nbr) std::copy(h.nbr.begin(), h.nbr.end(), nbr);
+  if (levels)
+    for (size_t c = 0; c < nc; ++c) levels[c] = h.level[c];
+  if (faces)
+    for (size_t f = 0; f < nf; ++f) {
+      faces[f] = h.fm[f];
+      faces[nf + f] = h.fp[f];
+      faces[2 * nf + f] = h.finfo[f];
+    }
+  if (sface) std::copy(h.sface.begin(), h.sface.begin() + sides * nc, sface);
+  return DG_OK;
+}
+
+static_assert(MAX_IN == 4 && MAX_OUT == 3 && DG_TEST_OP_DOUBLES == 5 + MAX_IN + MAX_OUT + MAX_OUT * MAX_IN + MAX_OUT,
+              "dg_test_stage_program record layout");
+
+int dg_test_stage_program(int rk_order, int limited, double* ops_out, int max_ops, int* n_ops, int* n_regs) {
+  if (rk_order < 1 || rk_order > 4 || (limited != 0 && limited != 1) || !n_ops || !n_regs || max_ops < 0)
+    return DG_ERR_ARG;
+  Program P;
+  std::string err;
+  if (!build_program(rk_order, limited == 1, P, err)) return DG_ERR_ARG;
+  *n_ops = (int)P.ops.size();
+  *n_regs = P.n_phys;
+  if (!ops_out) return DG_OK;
+  if (max_ops < (int)P.ops.size()) return DG_ERR_ARG;
+  for (size_t i = 0; i < P.ops.size(); ++i) {
+    const Op& op = P.ops[i];
+    double* r = ops_out + i * DG_TEST_OP_DOUBLES;
+    r[0] = op.in_reg;
+    r[1] = op.n_in;
+    r[2] = op.n_out;
+    r[3] = op.lim_src;
+    r[4] = op.lim_dst;
+    for (int j = 0; j < MAX_IN; ++j) r[5 + j] = j < op.n_in ? op.in[j] : -1;
+    for (int o = 0; o < MAX_OUT; ++o) r[9 + o] = o < op.n_out ? op.out[o] : -1;
+    for (int o = 0; o < MAX_OUT; ++o)
+      for (int j = 0; j < MAX_IN; ++j) r[12 + 4 * o + j] = op.C[o][j];
+    for (int o = 0; o < MAX_OUT; ++o) r[24 + o] = op.ck[o];
+  }
+  return DG_OK;
+}
+
 int dg_test_force_timeout(dg_handle* h) {
   if (!check_handle(h)) return DG_ERR_ARG;
   if (!h->use_tc) return fail(h, DG_ERR_UNSUPPORTED, "dg_test_force_timeout: no tensor-core cell kernel");

@@ -28,7 +28,9 @@ EXPORTS = ["dg_default_options", "dg_create", "dg_destroy", "dg_last_error", "dg
            "dg_create_batch", "dg_batch_advance", "dg_n_problems", "dg_tiles",
            "dg_limiter_counts", "dg_set_tiles", "dg_adapt_mark", "dg_adapt_set", "dg_regrid",
            "dg_set_gravity", "dg_test_force_timeout", "dg_set_advance_mode", "dg_advance_mode",
-           "dg_advance_dt", "dg_set_overlap", "dg_overlap", "dg_test_flux_math"]
+           "dg_advance_dt", "dg_set_overlap", "dg_overlap", "dg_test_flux_math",
+           "dg_test_mesh_tables", "dg_test_stage_program"]
+DG_TEST_OP_DOUBLES = 27
 KERNEL_KINDS = ["face", "cell", "limit", "dt", "other", "adjoint"]
 ADVANCE_MODES = {"graph": 0, "persistent": 1}
 
@@ -103,6 +105,9 @@ def load(path=LIB_PATH):
     L.dg_regrid.argtypes = [vp, vp, vp, vp]
     L.dg_set_gravity.argtypes = [vp, vp, vp]
     L.dg_test_force_timeout.argtypes = [vp]
+    L.dg_test_mesh_tables.argtypes = [C.POINTER(MeshDesc), i64p, i32p, i32p, i32p, i32p]
+    L.dg_test_stage_program.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_double), C.c_int,
+                                        C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.dg_set_advance_mode.argtypes = [vp, C.c_int]
     L.dg_advance_mode.argtypes = [vp, C.POINTER(C.c_int)]
     L.dg_profile_begin.argtypes = [vp]
@@ -111,6 +116,73 @@ def load(path=LIB_PATH):
         getattr(L, name).restype = C.c_int if name != "dg_last_error" else C.c_char_p
     _lib = L
     return L
+
+
+def _fill_desc(md, m):
+    """Fills the MeshDesc md from a mesh dict; returns the refinement-box
+    array md points into (keep it alive while md is used)."""
+    md.dim = m["dim"]
+    for a in range(3):
+        md.n[a] = int(m["n"][a]) if a < md.dim else 1
+        md.lo[a] = float(m["lo"][a]) if a < md.dim else 0.0
+        md.hi[a] = float(m["hi"][a]) if a < md.dim else 1.0
+        bc = m.get("bc") or [DG_BC_PERIODIC] * md.dim
+        md.bc[a] = int(bc[a]) if a < md.dim else 0
+    boxes = m.get("refine_boxes") or []
+    arr = np.ascontiguousarray(np.array(boxes, dtype=np.int32).reshape(-1))
+    md.n_refine_boxes = len(boxes)
+    md.refine_boxes = arr.ctypes.data_as(C.POINTER(C.c_int32)) if len(boxes) else None
+    return arr
+
+
+def mesh_tables(mesh):
+    """Test hook, host only: the mesh tables the library builds for a mesh
+    dict (dg_test_mesh_tables), as numpy arrays: nbr [2 dim][cells], levels
+    [cells], faces [3][faces] (minus cell, plus cell, packed info) and sface
+    [2 dim][cells], plus the node count."""
+    L = load()
+    md = MeshDesc()
+    keep = _fill_desc(md, mesh)
+    counts = (C.c_int64 * 3)()
+    r = L.dg_test_mesh_tables(C.byref(md), counts, None, None, None, None)
+    if r != DG_OK:
+        raise DGError(r, "dg_test_mesh_tables")
+    nc, nf, nn = counts[0], counts[1], counts[2]
+    d = mesh["dim"]
+    nbr = np.empty((2 * d, nc), np.int32)
+    lev = np.empty(nc, np.int32)
+    faces = np.empty((3, nf), np.int32)
+    sface = np.empty((2 * d, nc), np.int32)
+    p32 = lambda a: a.ctypes.data_as(C.POINTER(C.c_int32))
+    r = L.dg_test_mesh_tables(C.byref(md), counts, p32(nbr), p32(lev), p32(faces), p32(sface))
+    del keep
+    if r != DG_OK:
+        raise DGError(r, "dg_test_mesh_tables")
+    return dict(nbr=nbr, levels=lev, faces=faces, sface=sface, n_nodes=nn)
+
+
+def stage_program(rk_order, limited):
+    """Test hook, host only: the stage program of one RK step
+    (dg_test_stage_program) as a list of dicts (in_reg, ins, outs, C, ck,
+    lim_src, lim_dst) and the number of scratch registers."""
+    L = load()
+    n_ops, n_regs = C.c_int(), C.c_int()
+    r = L.dg_test_stage_program(int(rk_order), int(limited), None, 0, C.byref(n_ops), C.byref(n_regs))
+    if r != DG_OK:
+        raise DGError(r, "dg_test_stage_program")
+    buf = np.zeros((n_ops.value, DG_TEST_OP_DOUBLES))
+    r = L.dg_test_stage_program(int(rk_order), int(limited), buf.ctypes.data_as(C.POINTER(C.c_double)),
+                                n_ops.value, C.byref(n_ops), C.byref(n_regs))
+    if r != DG_OK:
+        raise DGError(r, "dg_test_stage_program")
+    ops = []
+    for rec in buf:
+        n_in, n_out = int(rec[1]), int(rec[2])
+        ops.append(dict(in_reg=int(rec[0]), ins=[int(x) for x in rec[5:5 + n_in]],
+                        outs=[int(x) for x in rec[9:9 + n_out]],
+                        C=rec[12:24].reshape(3, 4)[:n_out, :n_in].copy(), ck=rec[24:24 + n_out].copy(),
+                        lim_src=int(rec[3]), lim_dst=int(rec[4])))
+    return ops, n_regs.value
 
 
 def flux_math_check(op, x):
@@ -178,20 +250,7 @@ class Solver:
         self.mesh = dict(meshes[0])
         self.dim, self.k, self.gamma = meshes[0]["dim"], k, gamma
         descs = (MeshDesc * len(meshes))()
-        self._boxes = []
-        for md, m in zip(descs, meshes):
-            md.dim = m["dim"]
-            for a in range(3):
-                md.n[a] = int(m["n"][a]) if a < md.dim else 1
-                md.lo[a] = float(m["lo"][a]) if a < md.dim else 0.0
-                md.hi[a] = float(m["hi"][a]) if a < md.dim else 1.0
-                bc = m.get("bc") or [DG_BC_PERIODIC] * md.dim
-                md.bc[a] = int(bc[a]) if a < md.dim else 0
-            boxes = m.get("refine_boxes") or []
-            arr = np.ascontiguousarray(np.array(boxes, dtype=np.int32).reshape(-1))
-            self._boxes.append(arr)
-            md.n_refine_boxes = len(boxes)
-            md.refine_boxes = arr.ctypes.data_as(C.POINTER(C.c_int32)) if len(boxes) else None
+        self._boxes = [_fill_desc(md, m) for md, m in zip(descs, meshes)]
         opt = Options()
         L.dg_default_options(C.byref(opt))
         opt.rk_order, opt.cfl = rk_order, cfl
