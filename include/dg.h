@@ -448,10 +448,13 @@ int dg_test_force_timeout(dg_handle* h);
 int dg_test_flux_math(int op, const double* x_dev, double* out_dev, int64_t n, void* stream);
 
 /* Test hook (host only: no device work, usable without a GPU): the mesh
- * tables dg_create builds for mesh (Sec. 4: base cells, refined base cells
- * replaced by their 2^dim children, hanging faces).  counts[3] receives the
- * numbers of cells, faces and refined base cells.  Each non-NULL array is
- * filled (caller-owned host memory; call first with NULL arrays to size them):
+ * tables dg_create builds for meshes[0] (n_problems = 1; Sec. 4: base cells,
+ * refined base cells replaced by their 2^dim children, hanging faces), or
+ * dg_create_batch for n_problems meshes (cells, faces and table entries
+ * concatenated in problem order, indices shifted by the offsets).
+ * counts[3] receives the numbers of cells, faces and refined base cells.
+ * Each non-NULL array is filled (caller-owned host memory; call first with
+ * NULL arrays to size them):
  *   nbr[2*dim][cells]   as dg_neighbor_table;
  *   levels[cells]       as dg_cell_levels;
  *   faces[3][faces]     minus cell, plus cell (-1 for the missing cell of a
@@ -463,10 +466,13 @@ int dg_test_flux_math(int op, const double* x_dev, double* out_dev, int64_t n, v
  *                       the sub-face covers;
  *   sface[2*dim][cells] the face of each cell side (side = 2*axis + {0:-, 1:+});
  *                       on the coarse side of a hanging face its first
- *                       sub-face, the others following in quadrant order.
- * DG_ERR_ARG for a NULL mesh or counts, or a mesh dg_create rejects. */
-int dg_test_mesh_tables(const dg_mesh_desc* mesh, int64_t* counts, int32_t* nbr, int32_t* levels,
-                        int32_t* faces, int32_t* sface);
+ *                       sub-face, the others following in quadrant order;
+ *   prob[cells]         the problem of each cell.
+ * DG_ERR_ARG for NULL meshes or counts, n_problems < 1, or meshes that
+ * dg_create / dg_create_batch reject with DG_ERR_ARG; DG_ERR_UNSUPPORTED for a
+ * batch with refined meshes. */
+int dg_test_mesh_tables(const dg_mesh_desc* meshes, int n_problems, int64_t* counts, int32_t* nbr,
+                        int32_t* levels, int32_t* faces, int32_t* sface, int32_t* prob);
 
 /* Test hook (host only): the stage program dg_create derives from the SSP
  * Runge-Kutta tableau of order rk_order (1..4; Appendix D), unlimited

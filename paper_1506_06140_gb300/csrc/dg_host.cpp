@@ -2241,14 +2241,15 @@ int dg_test_flux_math(int op, const double* x_dev, double* out_dev, int64_t n, v
                                                                                                 : DG_ERR_CUDA;
 }
 
-int dg_test_mesh_tables(const dg_mesh_desc* mesh, int64_t* counts, int32_t* nbr, int32_t* levels,
-                        int32_t* faces, int32_t* sface) {
-  if (!mesh || !counts) return DG_ERR_ARG;
-  if (mesh->dim != 2 && mesh->dim != 3) return DG_ERR_ARG;
-  // a handle without device state: build_mesh is host work only
+int dg_test_mesh_tables(const dg_mesh_desc* meshes, int n_problems, int64_t* counts, int32_t* nbr,
+                        int32_t* levels, int32_t* faces, int32_t* sface, int32_t* prob) {
+  if (!meshes || !counts || n_problems < 1) return DG_ERR_ARG;
+  if (meshes[0].dim != 2 && meshes[0].dim != 3) return DG_ERR_ARG;
+  // a handle without device state: the builders are host work only
   dg_handle h;
-  h.dim = mesh->dim;
-  if (build_mesh(&h, mesh) != DG_OK) return DG_ERR_ARG;
+  h.dim = meshes[0].dim;
+  const int r = n_problems == 1 ? build_mesh(&h, meshes) : build_batch(&h, meshes, n_problems);
+  if (r != DG_OK) return r;
   const size_t nc = (size_t)h.ncells, nf = (size_t)h.nfaces, sides = (size_t)2 * h.dim;
   counts[0] = (int64_t)nc;
   counts[1] = (int64_t)nf;
@@ -2263,6 +2264,8 @@ int dg_test_mesh_tables(const dg_mesh_desc* mesh, int64_t* counts, int32_t* nbr,
       faces[2 * nf + f] = h.finfo[f];
     }
   if (sface) std::copy(h.sface.begin(), h.sface.begin() + sides * nc, sface);
+  if (prob)
+    for (size_t c = 0; c < nc; ++c) prob[c] = n_problems == 1 ? 0 : h.prob[c];
   return DG_OK;
 }
 

@@ -105,7 +105,7 @@ def load(path=LIB_PATH):
     L.dg_regrid.argtypes = [vp, vp, vp, vp]
     L.dg_set_gravity.argtypes = [vp, vp, vp]
     L.dg_test_force_timeout.argtypes = [vp]
-    L.dg_test_mesh_tables.argtypes = [C.POINTER(MeshDesc), i64p, i32p, i32p, i32p, i32p]
+    L.dg_test_mesh_tables.argtypes = [C.POINTER(MeshDesc), C.c_int, i64p, i32p, i32p, i32p, i32p, i32p]
     L.dg_test_stage_program.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_double), C.c_int,
                                         C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.dg_set_advance_mode.argtypes = [vp, C.c_int]
@@ -137,28 +137,32 @@ def _fill_desc(md, m):
 
 def mesh_tables(mesh):
     """Test hook, host only: the mesh tables the library builds for a mesh
-    dict (dg_test_mesh_tables), as numpy arrays: nbr [2 dim][cells], levels
-    [cells], faces [3][faces] (minus cell, plus cell, packed info) and sface
-    [2 dim][cells], plus the node count."""
+    dict, or a list of them for an ensemble (dg_test_mesh_tables), as numpy
+    arrays: nbr [2 dim][cells], levels [cells], faces [3][faces] (minus cell,
+    plus cell, packed info), sface [2 dim][cells] and prob [cells], plus the
+    node count."""
     L = load()
-    md = MeshDesc()
-    keep = _fill_desc(md, mesh)
+    meshes = list(mesh) if isinstance(mesh, (list, tuple)) else [mesh]
+    descs = (MeshDesc * len(meshes))()
+    keep = [_fill_desc(md, m) for md, m in zip(descs, meshes)]
     counts = (C.c_int64 * 3)()
-    r = L.dg_test_mesh_tables(C.byref(md), counts, None, None, None, None)
+    r = L.dg_test_mesh_tables(descs, len(meshes), counts, None, None, None, None, None)
     if r != DG_OK:
         raise DGError(r, "dg_test_mesh_tables")
     nc, nf, nn = counts[0], counts[1], counts[2]
-    d = mesh["dim"]
+    d = meshes[0]["dim"]
     nbr = np.empty((2 * d, nc), np.int32)
     lev = np.empty(nc, np.int32)
     faces = np.empty((3, nf), np.int32)
     sface = np.empty((2 * d, nc), np.int32)
+    prob = np.empty(nc, np.int32)
     p32 = lambda a: a.ctypes.data_as(C.POINTER(C.c_int32))
-    r = L.dg_test_mesh_tables(C.byref(md), counts, p32(nbr), p32(lev), p32(faces), p32(sface))
+    r = L.dg_test_mesh_tables(descs, len(meshes), counts, p32(nbr), p32(lev), p32(faces), p32(sface),
+                              p32(prob))
     del keep
     if r != DG_OK:
         raise DGError(r, "dg_test_mesh_tables")
-    return dict(nbr=nbr, levels=lev, faces=faces, sface=sface, n_nodes=nn)
+    return dict(nbr=nbr, levels=lev, faces=faces, sface=sface, prob=prob, n_nodes=nn)
 
 
 def stage_program(rk_order, limited):

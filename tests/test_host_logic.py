@@ -111,6 +111,37 @@ def test_face_lists(dg, name):
     assert nf - n_whole == nsub * int((nbr <= -2).sum())
 
 
+def test_batch_tables_concatenate_the_problems(dg):
+    """An ensemble's tables are its problems' own tables in problem order,
+    cell and face indices shifted by the offsets (node and boundary codes
+    unchanged), with each cell's problem index."""
+    meshes = [wl.mesh_uniform(2, [n, n], [-5.0, -5.0], [5.0, 5.0]) for n in (5, 3, 8)]
+    meshes.append(wl.mesh_uniform(2, [4, 2], [0.0, 0.0], [2.0, 1.0], bc=[TRN, PER]))
+    b = dg.mesh_tables(meshes)
+    c0 = f0 = 0
+    for p, m in enumerate(meshes):
+        t = dg.mesh_tables(m)
+        nc, nf = t["nbr"].shape[1], t["faces"].shape[1]
+        sl = slice(c0, c0 + nc)
+        np.testing.assert_array_equal(b["nbr"][:, sl], np.where(t["nbr"] >= 0, t["nbr"] + c0, t["nbr"]))
+        np.testing.assert_array_equal(b["levels"][sl], t["levels"])
+        np.testing.assert_array_equal(b["sface"][:, sl], t["sface"] + f0)
+        np.testing.assert_array_equal(b["prob"][sl], p)
+        fb = b["faces"][:, f0:f0 + nf]
+        np.testing.assert_array_equal(fb[:2], np.where(t["faces"][:2] >= 0, t["faces"][:2] + c0, -1))
+        np.testing.assert_array_equal(fb[2], t["faces"][2])
+        c0 += nc
+        f0 += nf
+    assert c0 == b["nbr"].shape[1] and f0 == b["faces"].shape[1]
+    # ensembles are uniform meshes of one dimension
+    with pytest.raises(dg.DGError) as ei:
+        dg.mesh_tables([meshes[0], MESHES["amr2"]])
+    assert ei.value.code == dg.DG_ERR_UNSUPPORTED
+    with pytest.raises(dg.DGError) as ei:
+        dg.mesh_tables([meshes[0], MESHES["u3"]])
+    assert ei.value.code == dg.DG_ERR_ARG
+
+
 def test_mesh_tables_reject_bad_meshes(dg):
     for bad in (dict(wl.mesh_uniform(2, [4, 4], [0.0, 0.0], [1.0, 2.0])),  # non-cubical cells
                 dict(wl.mesh_uniform(2, [0, 4], [0.0, 0.0], [1.0, 1.0]))):
