@@ -12,7 +12,8 @@
  *   weights   W[var][coef][cell]    var = rho, rho v_1..rho v_dim, rho e
  *             (nv = dim + 2), coef = basis function index (N of them),
  *             cell = cell index (fastest).  Element type: double for
- *             DG_FP64 handles, float for DG_FP32 handles.
+ *             DG_FP64, DG_MIXED and DG_MIXED_TC handles, float for DG_FP32
+ *             and DG_FP32_TC handles.
  *   points    u[var][q][cell] (double), xyz[axis][q][cell] (double)
  * Cells are listed by base cell in lexicographic order (x fastest); a refined
  * base cell is replaced by its 2^dim children in the order A..H of the paper's
@@ -20,7 +21,9 @@
  * Basis functions: products of scaled Legendre polynomials sqrt(2n+1) P_n of
  * total degree <= k (eq. set_basis_functions), ordered by total degree, then
  * x exponent descending, then y exponent descending; coefficient 0 is the
- * cell mean (eq. weights), coefficients 1..dim are the x, y, z slopes.
+ * cell mean (eq. weights), coefficients 1..dim are the x, y, z slopes.  (The
+ * optional tensor-product space DG_BASIS_TENSOR continues this order past
+ * total degree k; see below.)
  *
  * Streams: every call that touches device data takes a cudaStream_t passed
  * as `void* stream` (NULL = legacy default stream) and is asynchronous with
@@ -163,7 +166,8 @@ int dg_limiter_counts(dg_handle* h, int64_t* counts_dev, int reset, void* stream
 /* Tiles of the stage kernels in use: cells per thread block of the cell
  * kernel and faces per block of the face kernel (the fixed defaults, or the
  * autotuner's choice when dg_options.autotune was set).  A tensor-core cell
- * kernel (DG_FP32_TC) reports its fixed 32 cells; cell tile 1 means the one-
+ * kernel (DG_FP32_TC, DG_MIXED_TC) reports its fixed tile of 128 cells (one
+ * MMA row per cell); cell tile 1 means the one-
  * thread-per-cell FP32 kernel and cell tile 2 the packed-pair FP32 kernel,
  * both of which the autotuner also considers; face tile
  * 0 means the fused face + cell kernel (tiles of 8 x 4 cells computing their

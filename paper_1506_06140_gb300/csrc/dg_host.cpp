@@ -1800,7 +1800,7 @@ int dg_set_tiles(dg_handle* h, int cell_tile, int face_tile) {
 
 int dg_tiles(const dg_handle* h, int* cell_tile, int* face_tile) {
   if (!check_handle(h) || !cell_tile || !face_tile) return DG_ERR_ARG;
-  *cell_tile = h->use_tc ? 32 : (h->use_direct ? 1 : (h->use_x2 ? 2 : (h->use_fused ? 32 : h->cell_tile)));
+  *cell_tile = h->use_tc ? 128 : (h->use_direct ? 1 : (h->use_x2 ? 2 : (h->use_fused ? 32 : h->cell_tile)));
   *face_tile = h->use_fused ? 0 : h->face_tile;
   return DG_OK;
 }
