@@ -419,6 +419,7 @@ def test_rhs_fp32_tensor_cores(k):
     m = MESHES["u2"]
     o = oracle_for(m, k)
     s = solver_for(m, k, precision="fp32_tc")
+    assert s.tiles()[0] == 128  # one MMA row per cell, 128 cells per tile
     W = wl.random_weights(2, o.N, o.n_cells, seed=900 + k).astype(np.float32)
     ref = o.rhs(W.astype(np.float64))
     got = s.rhs(to_dev(s, W)).cpu().numpy()
