@@ -228,7 +228,9 @@ int dg_rk_step(dg_handle* h, void* W_dev, double dt, double* dt_used_dev, void* 
 /* n_steps CFL steps in place, recorded once into a CUDA graph per (W_dev,
  * n_steps, dt_hist_dev) and replayed; dt_hist_dev (optional,
  * double[n_steps][n_problems]) receives the timesteps.  The first call for a
- * given key records the graph (make it outside any stream capture). */
+ * given key records the graph (make it outside any stream capture).  A
+ * handle keeps at most 64 recorded graphs (with dg_advance_dt's); recording
+ * one more drops them all, to be recorded anew on their next use. */
 int dg_advance(dg_handle* h, void* W_dev, int n_steps, double* dt_hist_dev, void* stream);
 
 /* n_steps steps in place with the fixed timestep dt (> 0, else DG_ERR_ARG),

@@ -1830,6 +1830,8 @@ int dg_rk_step(dg_handle* h, void* W_dev, double dt, double* dt_used_dev, void* 
 }
 
 static int advance_graph(dg_handle* h, void* W_dev, int n_steps, double dt, double* dt_hist_dev, cudaStream_t s);
+// recorded step graphs kept per handle (dg_advance, dg_advance_dt)
+constexpr size_t GRAPH_CACHE_MAX = 64;
 
 int dg_advance(dg_handle* h, void* W_dev, int n_steps, double* dt_hist_dev, void* stream) {
   if (!check_handle(h) || !W_dev || n_steps < 0) return DG_ERR_ARG;
@@ -1878,6 +1880,7 @@ static int advance_graph_profiled(dg_handle* h, void* W_dev, int n_steps, double
   auto key = std::make_tuple(W_dev, n_steps, (void*)dt_hist_dev, dt);
   auto it = h->pgraphs.find(key);
   if (it == h->pgraphs.end()) {
+    if (h->pgraphs.size() >= GRAPH_CACHE_MAX) drop_graphs(h);
     dg_handle::ProfGraph pg;
     // the capture brackets launches with events of its own pool and marks
     std::swap(h->ev_pool, pg.ev);
@@ -1911,6 +1914,10 @@ static int advance_graph(dg_handle* h, void* W_dev, int n_steps, double dt, doub
   auto key = std::make_tuple(W_dev, n_steps, (void*)dt_hist_dev, dt);
   auto it = h->graphs.find(key);
   if (it == h->graphs.end()) {
+    // a bounded cache: callers that vary dt or the buffer every call would
+    // otherwise accumulate graphs (an executable graph still in flight is
+    // freed when it completes)
+    if (h->graphs.size() >= GRAPH_CACHE_MAX) drop_graphs(h);
     cudaGraphExec_t ge = nullptr;
     const int r = capture_steps(h, W_dev, n_steps, dt, dt_hist_dev, &ge);
     if (r != DG_OK) return r;

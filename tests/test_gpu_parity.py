@@ -309,6 +309,23 @@ def test_wave2d_32x32_full_run_fp64():
     assert o.l1_density(Wd.cpu().numpy(), rho_o) <= 1e-10 * np.abs(rho_o).mean()
 
 
+def test_graph_cache_stays_bounded():
+    """A caller that changes dt every call records a graph per call; past the
+    handle's cap of 64 recorded graphs they are all dropped and recorded anew,
+    and every step stays bit-identical to dg_rk_step."""
+    m = wl.mesh_uniform(2, [16, 16], [0.0, 0.0], [1.0, 1.0])
+    s = solver_for(m, 1, rk_order=2)
+    Wa = s.project(torch.as_tensor(wl.wave2d(s.quad_points().cpu().numpy())))
+    Wb = Wa.clone()
+    dt0 = 0.5 * s.compute_dt(Wa).item()
+    for i in range(150):
+        dt = dt0 * (1.0 + 0.003 * (i % 75))  # 75 distinct timesteps, each used twice
+        s.advance(Wa, 1, dt=dt)
+        s.rk_step(Wb, dt)
+    np.testing.assert_array_equal(Wa.cpu().numpy(), Wb.cpu().numpy())
+    assert s.status() == 0
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32", "mixed"])
 def test_advance_dt_repeats_rk_step(precision):
     """dg_advance_dt (fixed-dt steps as one graph) is bit-identical to the
