@@ -15,11 +15,12 @@ import numpy as np
 import pytest
 import torch
 
+import golden_values
 from paper_1506_06140_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
 GAMMA = 5.0 / 3.0
-R0 = 1.152
+R0 = golden_values.validation_figures()["sedov_taylor_R0"]  # Sec. 5.3
 T_END = 0.05
 
 

@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 import torch
 
+import golden_values
 from paper_1506_06140_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -21,8 +22,14 @@ def built():
     build.build()
 
 
-@pytest.mark.parametrize("k,rk,lo,hi", [(1, 2, 0.24, 0.32), (2, 3, 0.08, 0.15)], ids=["DG-2", "DG-3"])
-def test_square_error_growth_exponent(k, rk, lo, hi):
+PRINTED = golden_values.validation_figures()  # Sec. 5.4: t^0.28 (DG-2), t^0.12 (DG-3)
+
+
+@pytest.mark.parametrize("k,rk,key", [(1, 2, "square_l1_exponent_dg2"), (2, 3, "square_l1_exponent_dg3")],
+                         ids=["DG-2", "DG-3"])
+def test_square_error_growth_exponent(k, rk, key):
+    """The fitted exponent within 0.04 of the printed one (two printed digits,
+    a fit over t in [0.1, 0.5] here against the paper's longer runs)."""
     from paper_1506_06140_gb300 import dg
     m = wl.mesh_uniform(2, [64, 64], [0.0, 0.0], [1.0, 1.0])
     s = dg.Solver(m, k, 1.4, rk_order=rk, cfl=0.2, limiter="characteristic")
@@ -42,7 +49,7 @@ def test_square_error_growth_exponent(k, rk, lo, hi):
         rows.append((t, l1))
     alpha = np.polyfit(np.log([r[0] for r in rows]), np.log([r[1] for r in rows]), 1)[0]
     print("DG-%d: L1 %s, exponent %.3f" % (k + 1, ["%.3e" % r[1] for r in rows], alpha))
-    assert lo < alpha < hi, alpha
+    assert abs(alpha - PRINTED[key]) < 0.04, alpha
     assert abs(s.totals(W)[0].item() - mass0) <= 1e-12 * mass0
     assert s.limiter_counts()[0].item() > 0
     assert s.status() == 0
