@@ -33,6 +33,11 @@ MESHES = {
     "amr3": dict(wl.mesh_uniform(3, [6, 6, 6], [0.0] * 3, [1.0] * 3, bc=[PER, TRN, PER]),
                  refine_boxes=[[1, 1, 1, 3, 3, 2], [5, 0, 0, 5, 0, 5]]),
     "sedov_like": wl.mesh_two_level_3d(8, 2, 5),
+    # degenerate: one cell (its own neighbour on every side), one row, one open column
+    "one_cell_2d": wl.mesh_uniform(2, [1, 1], [0.0, 0.0], [1.0, 1.0]),
+    "one_cell_3d": wl.mesh_uniform(3, [1, 1, 1], [0.0] * 3, [1.0] * 3),
+    "one_row_open": wl.mesh_uniform(2, [6, 1], [0.0, 0.0], [6.0, 1.0], bc=[TRN, TRN]),
+    "one_refined_cell": dict(wl.mesh_uniform(2, [1, 1], [0.0, 0.0], [1.0, 1.0]), refine_boxes=[[0, 0, 0, 0]]),
 }
 
 
