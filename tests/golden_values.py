@@ -55,3 +55,8 @@ def rk_tableaux():
 def validation_figures():
     """{key: value} of the figures the paper prints for its validation runs."""
     return {row[0]: float(row[1]) for row in _rows("validation_figures.txt")}
+
+
+def lobatto_first_weight():
+    """{k: first GLL weight} printed in Sec. 3.4."""
+    return {int(row[0]): float(Fraction(row[1])) for row in _rows("lobatto_first_weight.txt")}

@@ -89,9 +89,10 @@ def test_lobatto_small_rules():
     np.testing.assert_allclose(w, [1 / 3, 4 / 3, 1 / 3], atol=1e-15)
 
 
-@pytest.mark.parametrize("k,w1", [(1, 1.0), (2, 1 / 3), (3, 1 / 3)])
+@pytest.mark.parametrize("k,w1", sorted(golden_values.lobatto_first_weight().items()))
 def test_first_lobatto_weight_per_order(k, w1):
-    # Sec. 3.4: m = smallest integer >= (k+3)/2; first GLL weight 1 for k=1, 1/3 for k=2,3
+    # Sec. 3.4: m = smallest integer >= (k+3)/2; the printed first GLL weight
+    # (tests/golden/lobatto_first_weight.txt: 1 for k=1, 1/3 for k=2,3)
     m = math.ceil((k + 3) / 2)
     x, w = O.gauss_lobatto(m)
     assert w[0] == pytest.approx(w1, abs=1e-15)
