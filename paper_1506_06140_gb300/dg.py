@@ -5,6 +5,7 @@ CUDA stream; every step of the computation runs in libdg's kernels.  There is
 no CPU path: if ``libdg.so`` is missing this module raises on first use.
 """
 import ctypes as C
+import json
 import os
 
 import numpy as np
@@ -116,6 +117,18 @@ def load(path=LIB_PATH):
         getattr(L, name).restype = C.c_int if name != "dg_last_error" else C.c_char_p
     _lib = L
     return L
+
+
+CHECKPOINT_VERSION = 1
+
+
+def _plain_mesh(m):
+    """A mesh dict with plain JSON values (for checkpoints)."""
+    d = int(m["dim"])
+    return dict(dim=d, n=[int(x) for x in m["n"][:d]], lo=[float(x) for x in m["lo"][:d]],
+                hi=[float(x) for x in m["hi"][:d]],
+                bc=[int(x) for x in (m.get("bc") or [DG_BC_PERIODIC] * d)[:d]],
+                refine_boxes=[[int(x) for x in b] for b in (m.get("refine_boxes") or [])])
 
 
 def _fill_desc(md, m):
@@ -251,6 +264,10 @@ class Solver:
         self._L = L
         meshes = list(mesh) if isinstance(mesh, (list, tuple)) else [mesh]
         self.batch = isinstance(mesh, (list, tuple))
+        # the arguments save_checkpoint records to rebuild the handle
+        self._args = dict(meshes=[dict(m) for m in meshes], k=k, gamma=gamma, rk_order=rk_order, cfl=cfl, limiter=limiter,
+                          beta=beta, Mtilde=Mtilde, positivity=positivity, eps=eps, precision=precision,
+                          basis=basis)
         self.mesh = dict(meshes[0])
         self.dim, self.k, self.gamma = meshes[0]["dim"], k, gamma
         descs = (MeshDesc * len(meshes))()
@@ -467,6 +484,51 @@ class Solver:
             out[b] = lv[c]
             c += nch if lv[c] else 1
         return out
+
+    # -- checkpoint / resume --
+    def save_checkpoint(self, path, W, **meta):
+        """Writes what resuming needs to one .npz file: the state W (copied to
+        the host), the constructor's arguments, the current refinement of the
+        base cells (a single problem's mesh after adaptation) and meta (JSON
+        values, e.g. t= and step=).  Not recorded: the tiles (from_checkpoint
+        can autotune again), the advance mode and a gravity field (set it
+        again after resuming)."""
+        assert tuple(W.shape) == (self.nv, self.N, self.n_cells), "bad state shape"
+        a = self._args
+        limiter = a["limiter"] if isinstance(a["limiter"], str) else int(a["limiter"])
+        config = dict(meshes=[_plain_mesh(m) for m in a["meshes"]], batch=self.batch, k=int(a["k"]),
+                      gamma=float(a["gamma"]), rk_order=int(a["rk_order"]), cfl=float(a["cfl"]),
+                      limiter=limiter, beta=float(a["beta"]), Mtilde=float(a["Mtilde"]),
+                      positivity=bool(a["positivity"]), eps=float(a["eps"]), precision=a["precision"],
+                      basis=a["basis"])
+        ref = np.zeros(0, np.int32) if self.batch else self.refinement()
+        with open(path, "wb") as f:
+            np.savez(f, version=np.int64(CHECKPOINT_VERSION), config=np.array(json.dumps(config)),
+                     refinement=ref, W=W.detach().cpu().numpy(), meta=np.array(json.dumps(meta)))
+
+    @classmethod
+    def from_checkpoint(cls, path, autotune=False):
+        """(solver, W, meta) from a save_checkpoint file: the handle is built
+        from the recorded arguments, moved to the recorded refinement, and W
+        is the recorded state on this device."""
+        with np.load(path, allow_pickle=False) as d:
+            version = int(d["version"])
+            if version != CHECKPOINT_VERSION:
+                raise ValueError("checkpoint version %d, expected %d" % (version, CHECKPOINT_VERSION))
+            cfg = json.loads(str(d["config"]))
+            ref = np.array(d["refinement"], dtype=np.int32)
+            Wh = np.array(d["W"])
+            meta = json.loads(str(d["meta"]))
+        meshes, batch = cfg.pop("meshes"), cfg.pop("batch")
+        s = cls(meshes if batch else meshes[0], autotune=autotune, **cfg)
+        if not batch and not np.array_equal(s.refinement(), ref):
+            s.set_refinement(ref)
+            s.regrid(s.empty_state().zero_())  # the projected values are replaced by W below
+        W = torch.as_tensor(Wh).to(device=s.device, dtype=s.dtype).contiguous()
+        if tuple(W.shape) != (s.nv, s.N, s.n_cells):
+            raise ValueError("checkpoint state %s does not fit the rebuilt mesh %s"
+                             % (tuple(W.shape), (s.nv, s.N, s.n_cells)))
+        return s, W, meta
 
     def profile_begin(self):
         self._check(self._L.dg_profile_begin(self._h))

@@ -238,3 +238,19 @@ def test_stage_program_rejects_bad_arguments(dg):
         dg.stage_program(5, 0)
     with pytest.raises(dg.DGError):
         dg.stage_program(3, 2)
+
+
+def test_checkpoint_version_is_checked_before_any_device_work(dg, tmp_path):
+    """A checkpoint of another format version is refused while reading the
+    file, before a handle is built."""
+    import json
+    path = tmp_path / "old.npz"
+    with open(path, "wb") as f:
+        np.savez(f, version=np.int64(dg.CHECKPOINT_VERSION + 1), config=np.array(json.dumps({})),
+                 refinement=np.zeros(0, np.int32), W=np.zeros((4, 3, 1)), meta=np.array("{}"))
+    with pytest.raises(ValueError, match="version"):
+        dg.Solver.from_checkpoint(path)
+    m = dict(wl.mesh_uniform(2, [3, 2], [0.0, 0.0], [1.5, 1.0], bc=[TRN, PER]), refine_boxes=[(1, 0, 2, 1)])
+    plain = dg._plain_mesh(m)
+    assert plain == json.loads(json.dumps(plain))
+    assert plain["refine_boxes"] == [[1, 0, 2, 1]] and plain["bc"] == [TRN, PER]
